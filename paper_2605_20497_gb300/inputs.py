@@ -1,0 +1,162 @@
+"""Seeded synthetic hypergraphs (inputs only; none of the partitioner's arithmetic).
+
+Every generator draws from numpy's PCG64 (``numpy.random.default_rng``), whose
+output is identical on x86-64 and aarch64, so the same seed gives the same
+hypergraph on the build host and on the GPU host.  Hypergraphs are plain
+int32 CSR: ``offsets[E+1]``, ``pins[offsets[E]]``; each hyperedge lists its
+source pins first (``src_counts[e]`` of them; ``None`` means exactly one, the
+first pin), then its destinations in ascending id order.
+
+The shapes follow the spiking-network workloads of the paper's Table I
+(random "-rand" nets and regular layered "-model" nets):
+
+* :func:`random_snn` -- every node owns one hyperedge: itself plus ``k``
+  distinct uniform-random targets (4,096 x 31 and 16,384 x 127 workloads).
+* :func:`layered_snn` -- ``layers`` grids of ``h x w x ch`` neurons; a neuron
+  of every layer but the last owns a hyperedge to all channels of the 3x3
+  window (border-clipped) around its position in the next layer
+  (8 x 32 x 32 x 32 = 262,144 nodes, ~63.6M pins).
+* :func:`random_hypergraph` -- small irregular hypergraphs for tests
+  (optional multi-source hyperedges, weights, isolated nodes).
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+
+
+@dataclass
+class Hypergraph:
+    num_nodes: int
+    offsets: np.ndarray            # int32 [E+1]
+    pins: np.ndarray               # int32 [offsets[-1]]
+    src_counts: np.ndarray | None = None   # int32 [E] or None (one source each)
+    weights: np.ndarray | None = None      # int32 [E] or None (unit weights)
+    name: str = ""
+
+    @property
+    def num_hedges(self) -> int:
+        return len(self.offsets) - 1
+
+    @property
+    def num_pins(self) -> int:
+        return int(self.offsets[-1])
+
+    def edges(self):
+        """Yields (src list, dst list) per hyperedge (for small test graphs)."""
+        for e in range(self.num_hedges):
+            seg = self.pins[self.offsets[e]:self.offsets[e + 1]].tolist()
+            k = 1 if self.src_counts is None else int(self.src_counts[e])
+            yield seg[:k], seg[k:]
+
+
+def _csr(rows, n, name="", src_counts=None, weights=None) -> Hypergraph:
+    sizes = np.fromiter((len(r) for r in rows), dtype=np.int64, count=len(rows))
+    off = np.zeros(len(rows) + 1, dtype=np.int64)
+    np.cumsum(sizes, out=off[1:])
+    pins = np.concatenate([np.asarray(r, dtype=np.int32) for r in rows]) if rows else np.zeros(0, np.int32)
+    return Hypergraph(n, off.astype(np.int32), pins.astype(np.int32), src_counts, weights, name)
+
+
+def random_snn(n: int, k: int, seed: int = 0) -> Hypergraph:
+    """Node i owns hyperedge {i} + k distinct uniform targets != i (sorted)."""
+    rng = np.random.default_rng(seed)
+    pins = np.empty((n, k + 1), dtype=np.int32)
+    pins[:, 0] = np.arange(n, dtype=np.int32)
+    for i in range(n):
+        t = rng.choice(n - 1, size=k, replace=False)
+        t = t + (t >= i)          # skip the source itself
+        t.sort()
+        pins[i, 1:] = t
+    off = np.arange(0, n * (k + 1) + 1, k + 1, dtype=np.int64)
+    return Hypergraph(n, off.astype(np.int32), pins.reshape(-1), None, None, f"random_snn_{n}x{k}")
+
+
+def layered_snn(layers: int = 8, h: int = 32, w: int = 32, ch: int = 32) -> Hypergraph:
+    """Locally connected layered net; node id = ((L*h + y)*w + x)*ch + c."""
+    n = layers * h * w * ch
+    rows_sizes = []
+    pin_blocks = []
+    ys, xs = np.meshgrid(np.arange(h), np.arange(w), indexing="ij")
+    for L in range(layers - 1):
+        base_next = (L + 1) * h * w * ch
+        for y in range(h):
+            y0, y1 = max(0, y - 1), min(h, y + 2)
+            for x in range(w):
+                x0, x1 = max(0, x - 1), min(w, x + 2)
+                tgt = ((base_next + (ys[y0:y1, x0:x1] * w + xs[y0:y1, x0:x1]) * ch)[..., None]
+                       + np.arange(ch)[None, None, :]).reshape(-1)
+                src = ((L * h + y) * w + x) * ch + np.arange(ch)
+                blk = np.empty((ch, 1 + tgt.size), dtype=np.int32)
+                blk[:, 0] = src
+                blk[:, 1:] = tgt[None, :]
+                pin_blocks.append(blk.reshape(-1))
+                rows_sizes.append(np.full(ch, 1 + tgt.size, dtype=np.int64))
+    sizes = np.concatenate(rows_sizes)
+    off = np.zeros(sizes.size + 1, dtype=np.int64)
+    np.cumsum(sizes, out=off[1:])
+    pins = np.concatenate(pin_blocks)
+    return Hypergraph(n, off.astype(np.int32), pins, None, None, f"layered_snn_{layers}x{h}x{w}x{ch}")
+
+
+def random_hypergraph(n: int, e: int, max_size: int, seed: int = 0, multi_src: bool = False,
+                      weights: bool = False, isolated: int = 0, max_weight: int = 5) -> Hypergraph:
+    """Small irregular hypergraph: e hyperedges of 1..max_size distinct pins
+    over the first n - isolated nodes (the last ``isolated`` nodes touch none)."""
+    rng = np.random.default_rng(seed)
+    live = max(n - isolated, 1)
+    rows, src = [], []
+    for _ in range(e):
+        s = int(rng.integers(1, min(max_size, live) + 1))
+        pins = rng.choice(live, size=s, replace=False).astype(np.int32)
+        k = int(rng.integers(0, s + 1)) if multi_src else 1
+        head, tail = np.sort(pins[:k]), np.sort(pins[k:])
+        rows.append(np.concatenate([head, tail]))
+        src.append(k)
+    g = _csr(rows, n, f"random_hg_{n}_{e}_{seed}",
+             np.asarray(src, dtype=np.int32) if multi_src else None,
+             rng.integers(1, max_weight + 1, size=e).astype(np.int32) if weights else None)
+    return g
+
+
+def planted_components(sizes, edges_per_comp: int, edge_size: int, seed: int = 0) -> Hypergraph:
+    """Disjoint components (node blocks of the given sizes); every hyperedge
+    stays inside one component."""
+    rng = np.random.default_rng(seed)
+    rows = []
+    base = 0
+    for s in sizes:
+        for _ in range(edges_per_comp):
+            k = min(edge_size, s)
+            rows.append(np.sort(base + rng.choice(s, size=k, replace=False)).astype(np.int32))
+        base += s
+    perm = rng.permutation(len(rows))
+    rows = [rows[i] for i in perm]
+    return _csr(rows, int(sum(sizes)), "planted")
+
+
+def workload(name: str, seed: int = 0) -> Hypergraph:
+    """Named workloads used by the benchmark and the parity tests."""
+    if name == "random_snn_4k":
+        return random_snn(4096, 31, seed)
+    if name == "random_snn_16k":
+        return random_snn(16384, 127, seed)
+    if name == "layered_snn_262k":
+        return layered_snn(8, 32, 32, 32)
+    if name == "layered_snn_16k":
+        return layered_snn(4, 16, 16, 16)
+    if name == "layered_snn_65k":
+        return layered_snn(8, 16, 16, 32)
+    raise KeyError(name)
+
+
+# Omega, Delta of each named workload (paper Table I: 2^10/2^12 for the random
+# nets, 2^12/2^16 for the layered nets; 256/1024 for the small random net)
+CONSTRAINTS = {
+    "random_snn_4k": (256, 1024),
+    "random_snn_16k": (1 << 10, 1 << 12),
+    "layered_snn_262k": (1 << 12, 1 << 16),
+    "layered_snn_16k": (1 << 10, 1 << 14),
+    "layered_snn_65k": (1 << 12, 1 << 16),
+}
