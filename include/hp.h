@@ -1,0 +1,193 @@
+/*
+ * hp.h -- C ABI of the GB300 (sm_103a) constrained multilevel hypergraph
+ * partitioner.
+ *
+ * The operation is the one of Ronzani & Silvano, "Hypergraph Partitioning on
+ * GPU with Distinct Incident Hyperedges and Size Constraints":
+ *   Sec. II-A  a directed, weighted hypergraph: each hyperedge e has source
+ *              pins src(e) and destination pins dst(e); in(n) is the set of
+ *              hyperedges that hold n as a destination.
+ *   Sec. II-B  find a partitioning rho that minimises the connectivity
+ *              Conn = sum_e w(e) * (lambda(e) - 1)   (Eq. 1)
+ *              subject to |p| <= Omega and |U_{n in p} in(n)| <= Delta for
+ *              every part p.
+ *   Sec. III   by multilevel coarsening (Sec. V) and refinement (Sec. VI).
+ *
+ * Conventions (all calls):
+ *   - ids are 0-based int32; a hypergraph has num_nodes nodes and num_hedges
+ *     hyperedges in CSR form: offsets[num_hedges + 1] (offsets[0] = 0,
+ *     strictly increasing, so every hyperedge has at least one pin) and
+ *     pins[offsets[num_hedges]]; pins within a hyperedge are distinct; the
+ *     first src_counts[e] pins of hyperedge e are its sources (Sec. IV-B
+ *     stores sources first), the rest its destinations.  src_counts == NULL
+ *     means exactly one source per hyperedge, its first pin.
+ *   - weights == NULL means w(e) = 1; otherwise 1 <= w(e) <= 65536 and
+ *     sum_e w(e) <= 2^37.
+ *   - Omega >= 1, Delta >= 0.  A node with |in(n)| > Delta makes the problem
+ *     infeasible (HP_ERR_INFEASIBLE).
+ *   - The caller owns every buffer it passes; the library never frees caller
+ *     memory and releases all of its own device memory before returning.
+ *   - Outputs are written only when the call returns HP_OK.
+ *   - Results are deterministic: the same inputs, Omega, Delta, seed and
+ *     options give the same part vector on every run, and it is the part
+ *     vector of the method as specified by the readings listed with
+ *     hp_options below.
+ *   - A call is synchronous with respect to the host (it returns after the
+ *     results are in place); calls on different streams may run from
+ *     different host threads.
+ */
+#ifndef HP_H
+#define HP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define HP_API __attribute__((visibility("default")))
+#else
+#define HP_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    HP_OK = 0,
+    HP_ERR_INVALID_ARG = 1,  /* bad scalar argument, option, weight or NULL pointer */
+    HP_ERR_BAD_CSR = 2,      /* offsets not strictly increasing from 0, pin out of range,
+                                src count outside [0, |e|], duplicate pin in a hyperedge */
+    HP_ERR_INFEASIBLE = 3,   /* some node alone exceeds Delta */
+    HP_ERR_OOM = 4,          /* device allocation failed */
+    HP_ERR_CUDA = 5,         /* CUDA runtime error (see hp_last_error) */
+    HP_ERR_TIMEOUT = 6,      /* a bounded device loop ran out of iterations */
+    HP_ERR_INTERNAL = 7      /* an internal consistency check failed */
+} hp_status;
+
+typedef enum {
+    HP_COUNT_INBOUND = 0,   /* Delta bounds distinct inbound hyperedges (Sec. II-B) */
+    HP_COUNT_INCIDENT = 1   /* Delta bounds distinct incident hyperedges (Sec. II-B, last
+                               paragraph): every pin counts as a destination */
+} hp_count_kind;
+
+/*
+ * Options (hp_default_options gives the paper's defaults):
+ *   pi             candidates per node and matching rounds per level (Sec. V-D, 4)
+ *   theta          refinement repetitions per level (Sec. VI-A, 16); repetitions
+ *                  in the second half only propose moves that keep the
+ *                  destination within Omega (Sec. VI-B)
+ *   chain_window   successor candidates a chain end examines (Sec. VI-C, 256)
+ *   chain_rounds   chaining rounds (Sec. VI-C, 16)
+ *   noise_permille pairing noise cap in permille of the mean fixed-point
+ *                  hyperedge weight (Sec. V-C, 100 = 10%)
+ *   count_kind     hp_count_kind
+ *   max_levels     coarsening levels at most (256)
+ *   debug_table_cap  0 in normal use; a positive power of two caps the shared-
+ *                  memory neighbour table of the proposal kernel so that tests
+ *                  can force its overflow path on small inputs (result-neutral)
+ */
+typedef struct {
+    int32_t pi;
+    int32_t theta;
+    int32_t chain_window;
+    int32_t chain_rounds;
+    int32_t noise_permille;
+    int32_t count_kind;
+    int32_t max_levels;
+    int32_t debug_table_cap;
+} hp_options;
+
+/* Per-call statistics (host struct filled on HP_OK). */
+typedef struct {
+    int64_t connectivity;      /* Eq. 1 of the returned part vector */
+    int64_t cut_net;           /* Eq. 16 */
+    int32_t num_parts;
+    int32_t max_part_size;
+    int32_t max_part_distinct; /* max over parts of distinct inbound (or incident) hyperedges */
+    int32_t violations;        /* parts over Omega or Delta (0 on success) */
+    int32_t levels;            /* hypergraphs in the hierarchy, level 0 included */
+    int32_t reserved0;
+    int64_t moves_applied;     /* refinement moves applied over all levels */
+    int64_t pin_visits;        /* sum over coarsening levels of sum_e |e|^2 (proposal traversal) */
+    double ms_total;           /* device time of the call, input checks included */
+    double ms_coarsen;
+    double ms_refine;
+} hp_stats;
+
+/* Per-level trace record (optional output of hp_partition_ex). */
+typedef struct {
+    int32_t n;             /* nodes of the level */
+    int32_t pairs;         /* clusters of two formed at this level (0 at the coarsest) */
+    int32_t iso_pairs;     /* of which by the best-effort pairing of Sec. V-C */
+    int32_t reps;          /* refinement repetitions run at this level */
+    int64_t pins;          /* sum_e |e| of the level */
+    int64_t conn;          /* connectivity after refining this level */
+    int64_t moves;         /* moves applied at this level */
+} hp_level_trace;
+
+HP_API void hp_default_options(hp_options *opt);
+
+/*
+ * hp_partition -- partition a hypergraph held in device memory.
+ *   pins, offsets, src_counts, weights: device pointers, layout above.
+ *   part_out: device int32[num_nodes]; part ids compacted to
+ *             0..num_parts-1 in ascending order of the internal id.
+ *   stats:    host pointer or NULL.
+ *   stream:   cudaStream_t (NULL = legacy default stream).
+ * Errors: see hp_status; on error nothing is written.
+ */
+HP_API hp_status hp_partition(const int32_t *pins, const int32_t *offsets, int32_t num_hedges, int32_t num_nodes,
+                       const int32_t *src_counts, const int32_t *weights, int32_t omega, int32_t delta,
+                       uint64_t seed, const hp_options *opt, int32_t *part_out, hp_stats *stats,
+                       void *stream);
+
+/*
+ * hp_partition_ex -- hp_partition plus an optional per-level trace:
+ *   trace: host array of trace_cap records or NULL; levels beyond trace_cap
+ *          are not recorded (hp_stats.levels tells how many exist).
+ */
+HP_API hp_status hp_partition_ex(const int32_t *pins, const int32_t *offsets, int32_t num_hedges, int32_t num_nodes,
+                          const int32_t *src_counts, const int32_t *weights, int32_t omega, int32_t delta,
+                          uint64_t seed, const hp_options *opt, int32_t *part_out, hp_stats *stats,
+                          hp_level_trace *trace, int32_t trace_cap, void *stream);
+
+/*
+ * hp_partition_host -- the same with every array in host memory: the call
+ * copies the hypergraph to the device once and the part vector back once
+ * (the two transfers of Sec. VII-C).  part_out is host int32[num_nodes].
+ */
+HP_API hp_status hp_partition_host(const int32_t *pins, const int32_t *offsets, int32_t num_hedges, int32_t num_nodes,
+                            const int32_t *src_counts, const int32_t *weights, int32_t omega, int32_t delta,
+                            uint64_t seed, const hp_options *opt, int32_t *part_out, hp_stats *stats,
+                            void *stream);
+
+/*
+ * hp_set_allocator -- route the library's device workspace through a caller
+ * allocator (e.g. a framework's caching allocator).  alloc(bytes, ctx) returns
+ * a device pointer aligned to 256 bytes or NULL; free(ptr, ctx) releases it.
+ * Passing NULL functions restores stream-ordered cudaMallocAsync/cudaFreeAsync.
+ * Process-wide; not to be changed while a call is running.
+ */
+HP_API hp_status hp_set_allocator(void *(*alloc_fn)(size_t bytes, void *ctx), void (*free_fn)(void *ptr, void *ctx),
+                           void *ctx);
+
+/* Static description of a status code. */
+HP_API const char *hp_status_string(hp_status status);
+
+/* Message of the last error raised on the calling host thread ("" if none). */
+HP_API const char *hp_last_error(void);
+
+/*
+ * hp_connectivity -- Eq. 1 and Eq. 16 of a given part vector, on the device.
+ *   pins, offsets, weights (nullable), part: device pointers; num_parts > max part id.
+ *   conn_out, cutnet_out: host pointers.
+ */
+HP_API hp_status hp_connectivity(const int32_t *pins, const int32_t *offsets, int32_t num_hedges, const int32_t *weights,
+                          const int32_t *part, int32_t num_nodes, int32_t num_parts, int64_t *conn_out,
+                          int64_t *cutnet_out, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HP_H */

@@ -1,0 +1,759 @@
+// hp_coarsen.cu -- one coarsening level: candidate-pair proposal (Sec. V-C,
+// Eq. 5-6, deterministic noise, best-effort pairing of nodes without a valid
+// neighbour) and maximum-weight matching on the proposal pseudo-forest
+// (Sec. V-D, Eq. 7-12), repeated for Pi proposal graphs.
+//
+// The proposal fuses neighbour deduplication with the eta/inter histogram:
+// one CTA per node walks I(n) and the pins of every incident hyperedge and
+// accumulates into a shared-memory table (direct-indexed when the level has
+// at most 16384 nodes, open-addressing otherwise; nodes whose neighbourhood
+// outgrows the table are redone with a larger table and finally with a table
+// in global memory).  Sums and counts are integers, so the result does not
+// depend on the order of the atomic updates.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "hp_internal.cuh"
+
+namespace hp {
+
+static int grid_of(int64_t n, int block) {
+    int64_t g = cdiv(n, block);
+    int64_t cap = (int64_t)num_sms() * 32;
+    if (g > cap) g = cap;
+    return (int)(g < 1 ? 1 : g);
+}
+#define GRID_STRIDE(i, n) \
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (n); i += (int64_t)gridDim.x * blockDim.x)
+
+constexpr int PT = 256;          // proposal CTA size
+constexpr int DENSE_N = 16384;   // direct-indexed table up to this many nodes (12 B per node)
+
+// ---------------------------------------------------------------- noise
+// SplitMix64 finaliser (Steele, Lea, Flood 2014) keyed by (seed, level,
+// min(n,m), max(n,m)), reduced modulo cap+1: symmetric by construction.
+__device__ __forceinline__ uint64_t sm64_mix(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+__device__ __forceinline__ uint64_t pair_noise(uint64_t level_key, int32_t a, int32_t b, uint64_t cap) {
+    uint32_t lo = (uint32_t)min(a, b), hi = (uint32_t)max(a, b);
+    uint64_t h = sm64_mix(level_key ^ (((uint64_t)lo << 32) | (uint64_t)hi));
+    return h % (cap + 1);
+}
+
+struct PropCtx {
+    int32_t n, pi;
+    const int32_t *off, *pin, *nsrc, *size, *ioff, *inc, *nin;
+    const uint64_t *q;
+    const uint64_t *cap;   // device scalar
+    uint64_t level_key;
+    int32_t omega, delta;
+    int32_t *cand;         // [n*pi]
+    uint64_t *cscore;      // [n*pi]
+    int32_t *nbcnt;        // [n] unique neighbours found
+};
+
+// ---------------------------------------------------------------- per-level weights
+__global__ void k_level_q(const int32_t *off, const int32_t *w, int32_t e, uint64_t *q, unsigned long long *sum) {
+    __shared__ unsigned long long s;
+    if (threadIdx.x == 0) s = 0;
+    __syncthreads();
+    unsigned long long loc = 0;
+    GRID_STRIDE(i, (int64_t)e) {
+        uint64_t qi = ((uint64_t)w[i] << 24) / (uint64_t)(off[i + 1] - off[i]);
+        q[i] = qi;
+        loc += qi;
+    }
+    atomicAdd(&s, loc);
+    __syncthreads();
+    if (threadIdx.x == 0) atomicAdd(sum, s);
+}
+
+__global__ void k_level_cap(const unsigned long long *sum, int32_t e, int32_t permille, uint64_t *cap) {
+    *cap = e > 0 ? (uint64_t)((*sum / (unsigned long long)e) * (unsigned long long)permille / 1000ull) : 0ull;
+}
+
+// per node: bound on |N(v)| and the pin visits of its traversal
+__global__ void k_node_bounds(const int32_t *off, const int32_t *ioff, const int32_t *inc, int32_t n,
+                              int32_t *bound, unsigned long long *visits) {
+    unsigned long long loc = 0;
+    GRID_STRIDE(v, (int64_t)n) {
+        int64_t s = 0;
+        for (int32_t t = ioff[v]; t < ioff[v + 1]; t++) {
+            int32_t e = inc[t];
+            int32_t sz = off[e + 1] - off[e];
+            s += sz - 1;
+            loc += (unsigned long long)sz;
+        }
+        int64_t b = bound[v];
+        if (s < b) b = s;
+        if (n - 1 < b) b = n - 1;
+        bound[v] = (int32_t)b;
+    }
+    atomicAdd(visits, loc);
+}
+
+// ---------------------------------------------------------------- top-Pi selection
+struct Cand {
+    uint64_t eta;
+    int32_t id;
+};
+__device__ __forceinline__ bool cand_gt(const Cand &a, const Cand &b) {
+    return a.eta > b.eta || (a.eta == b.eta && a.id > b.id);
+}
+
+template <int PIMAX> struct TopList {
+    Cand c[PIMAX];
+    __device__ void init() {
+#pragma unroll
+        for (int i = 0; i < PIMAX; i++) c[i] = Cand{0, -1};
+    }
+    __device__ void push(Cand x) {
+#pragma unroll
+        for (int i = 0; i < PIMAX; i++) {
+            if (cand_gt(x, c[i])) {
+                Cand t = c[i];
+                c[i] = x;
+                x = t;
+            }
+        }
+    }
+    __device__ void pop() {
+#pragma unroll
+        for (int i = 0; i < PIMAX - 1; i++) c[i] = c[i + 1];
+        c[PIMAX - 1] = Cand{0, -1};
+    }
+};
+
+// block-wide: write the pi best of the per-thread lists to cand/cscore of v
+template <int PIMAX>
+__device__ void block_emit_top(TopList<PIMAX> &tl, const PropCtx &C, int32_t v, Cand *s_red) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int r = 0; r < C.pi; r++) {
+        Cand best = tl.c[0];
+        int owner = threadIdx.x;
+        for (int o = 16; o > 0; o >>= 1) {
+            Cand ob{__shfl_down_sync(0xffffffffu, best.eta, o), __shfl_down_sync(0xffffffffu, best.id, o)};
+            int oo = __shfl_down_sync(0xffffffffu, owner, o);
+            if (cand_gt(ob, best)) {
+                best = ob;
+                owner = oo;
+            }
+        }
+        if (lane == 0) {
+            s_red[wid] = best;
+            reinterpret_cast<int *>(s_red + 16)[wid] = owner;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            Cand b = s_red[0];
+            int ow = reinterpret_cast<int *>(s_red + 16)[0];
+            for (int k = 1; k < (int)(blockDim.x >> 5); k++) {
+                if (cand_gt(s_red[k], b)) {
+                    b = s_red[k];
+                    ow = reinterpret_cast<int *>(s_red + 16)[k];
+                }
+            }
+            C.cand[(int64_t)v * C.pi + r] = b.id;
+            C.cscore[(int64_t)v * C.pi + r] = b.id >= 0 ? b.eta : 0;
+            reinterpret_cast<int *>(s_red + 16)[15] = b.id >= 0 ? ow : -1;
+        }
+        __syncthreads();
+        if (threadIdx.x == reinterpret_cast<int *>(s_red + 16)[15]) tl.pop();
+        __syncthreads();
+    }
+}
+
+__device__ __forceinline__ bool pair_valid(const PropCtx &C, int32_t v, int32_t m, int32_t inter) {
+    if ((int64_t)C.size[v] + C.size[m] > C.omega) return false;
+    return (int64_t)C.nin[v] + C.nin[m] - inter <= C.delta;
+}
+
+__device__ __forceinline__ int32_t block_sum_i32(int32_t x, int32_t *s_tmp) {
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    if ((threadIdx.x & 31) == 0) s_tmp[threadIdx.x >> 5] = x;
+    __syncthreads();
+    int32_t t = 0;
+    if (threadIdx.x == 0)
+        for (int k = 0; k < (int)(blockDim.x >> 5); k++) t += s_tmp[k];
+    __syncthreads();
+    return t;
+}
+
+// ---------------------------------------------------------------- dense table
+// eta[m], inter[m] for every node of the level in shared memory.
+template <int PIMAX> __global__ void __launch_bounds__(PT) k_propose_dense(PropCtx C) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    unsigned long long *eta = reinterpret_cast<unsigned long long *>(smem);
+    uint32_t *inter = reinterpret_cast<uint32_t *>(eta + C.n);
+    __shared__ Cand s_red[16 + 8];
+    __shared__ int32_t s_tmp[32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = PT / 32;
+    for (int32_t i = threadIdx.x; i < C.n; i += PT) {
+        eta[i] = 0;
+        inter[i] = 0;
+    }
+    __syncthreads();
+    const uint64_t cap = *C.cap;
+    for (int32_t v = blockIdx.x; v < C.n; v += gridDim.x) {
+        const int32_t i0 = C.ioff[v], deg = C.ioff[v + 1] - i0, nin_v = C.nin[v];
+        for (int32_t t = wid; t < deg; t += nw) {
+            int32_t e = C.inc[i0 + t];
+            int32_t a = C.off[e], b = C.off[e + 1];
+            if (b - a < 2) continue;
+            int32_t dst0 = a + C.nsrc[e];
+            unsigned long long qe = C.q[e];
+            bool vin = t < nin_v;
+            for (int32_t j = a + lane; j < b; j += 32) {
+                int32_t m = C.pin[j];
+                if (m == v) continue;
+                atomicAdd(&eta[m], qe);
+                if (vin && j >= dst0) atomicAdd(&inter[m], 1u);
+            }
+        }
+        __syncthreads();
+        TopList<PIMAX> tl;
+        tl.init();
+        int32_t cnt = 0;
+        for (int32_t m = threadIdx.x; m < C.n; m += PT) {
+            unsigned long long em = eta[m];
+            if (em) {
+                cnt++;
+                int32_t it = (int32_t)inter[m];
+                if (pair_valid(C, v, m, it)) tl.push(Cand{em + pair_noise(C.level_key, v, m, cap), m});
+                eta[m] = 0;
+                inter[m] = 0;
+            }
+        }
+        int32_t tot = block_sum_i32(cnt, s_tmp);
+        if (threadIdx.x == 0) C.nbcnt[v] = tot;
+        block_emit_top<PIMAX>(tl, C, v, s_red);
+    }
+}
+
+// ---------------------------------------------------------------- hashed table
+__device__ __forceinline__ uint32_t hslot(int32_t m, uint32_t mask) {
+    return ((uint32_t)m * 0x9E3779B1u) & mask;
+}
+
+// Table of `cap` slots at keys/eta/inter (shared or global).  Nodes from
+// list[0..count) are processed; a node whose distinct neighbours exceed
+// limit is appended to ovf (and its table cleared).
+template <int PIMAX>
+__device__ void propose_hashed_node(const PropCtx &C, int32_t v, int32_t *keys, unsigned long long *eta,
+                                    uint32_t *inter, uint32_t cap, uint32_t limit, int32_t *ovf, int32_t *ovf_n,
+                                    int *s_flag, int32_t *s_cnt, Cand *s_red, int32_t *s_tmp) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const uint32_t mask = cap - 1;
+    const int32_t i0 = C.ioff[v], deg = C.ioff[v + 1] - i0, nin_v = C.nin[v];
+    for (int32_t t = wid; t < deg; t += nw) {
+        if (*(volatile int *)s_flag) break;
+        int32_t e = C.inc[i0 + t];
+        int32_t a = C.off[e], b = C.off[e + 1];
+        if (b - a < 2) continue;
+        int32_t dst0 = a + C.nsrc[e];
+        unsigned long long qe = C.q[e];
+        bool vin = t < nin_v;
+        for (int32_t j = a + lane; j < b; j += 32) {
+            int32_t m = C.pin[j];
+            if (m == v) continue;
+            uint32_t h = hslot(m, mask);
+            for (uint32_t probe = 0; probe < cap; probe++) {
+                int32_t k = ((volatile int32_t *)keys)[h];
+                if (k == -1) {
+                    int32_t old = atomicCAS(&keys[h], -1, m);
+                    if (old == -1) {
+                        if ((uint32_t)atomicAdd(s_cnt, 1) + 1 > limit) *(volatile int *)s_flag = 1;
+                        k = m;
+                    } else {
+                        k = old;
+                    }
+                }
+                if (k == m) {
+                    atomicAdd(&eta[h], qe);
+                    if (vin && j >= dst0) atomicAdd(&inter[h], 1u);
+                    break;
+                }
+                h = (h + 1) & mask;
+            }
+        }
+    }
+    __syncthreads();
+    const int overflow = *s_flag;
+    const uint64_t capn = *C.cap;
+    TopList<PIMAX> tl;
+    tl.init();
+    int32_t cnt = 0;
+    for (uint32_t h = threadIdx.x; h < cap; h += blockDim.x) {
+        int32_t m = keys[h];
+        if (m >= 0) {
+            if (!overflow) {
+                cnt++;
+                int32_t it = (int32_t)inter[h];
+                if (pair_valid(C, v, m, it)) tl.push(Cand{eta[h] + pair_noise(C.level_key, v, m, capn), m});
+            }
+            keys[h] = -1;
+            eta[h] = 0;
+            inter[h] = 0;
+        }
+    }
+    if (overflow) {
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            ovf[atomicAdd(ovf_n, 1)] = v;
+            *s_flag = 0;
+            *s_cnt = 0;
+        }
+        __syncthreads();
+        return;
+    }
+    int32_t tot = block_sum_i32(cnt, s_tmp);
+    if (threadIdx.x == 0) {
+        C.nbcnt[v] = tot;
+        *s_cnt = 0;
+    }
+    block_emit_top<PIMAX>(tl, C, v, s_red);
+}
+
+template <int PIMAX>
+__global__ void __launch_bounds__(PT) k_propose_smem(PropCtx C, const int32_t *list, int32_t count, uint32_t cap,
+                                                     uint32_t limit, int32_t *ovf, int32_t *ovf_n) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    unsigned long long *eta = reinterpret_cast<unsigned long long *>(smem);
+    uint32_t *inter = reinterpret_cast<uint32_t *>(eta + cap);
+    int32_t *keys = reinterpret_cast<int32_t *>(inter + cap);
+    __shared__ Cand s_red[16 + 8];
+    __shared__ int32_t s_tmp[32];
+    __shared__ int s_flag;
+    __shared__ int32_t s_cnt;
+    for (uint32_t i = threadIdx.x; i < cap; i += PT) {
+        keys[i] = -1;
+        eta[i] = 0;
+        inter[i] = 0;
+    }
+    if (threadIdx.x == 0) {
+        s_flag = 0;
+        s_cnt = 0;
+    }
+    __syncthreads();
+    for (int32_t k = blockIdx.x; k < count; k += gridDim.x)
+        propose_hashed_node<PIMAX>(C, list[k], keys, eta, inter, cap, limit, ovf, ovf_n, &s_flag, &s_cnt, s_red,
+                                   s_tmp);
+}
+
+// one CTA per node, table of capacity gcap[k] at global offset goff[k]
+template <int PIMAX>
+__global__ void __launch_bounds__(PT) k_propose_global(PropCtx C, const int32_t *list, int32_t count,
+                                                       const int64_t *goff, const int32_t *gcap, int32_t *gkeys,
+                                                       unsigned long long *geta, uint32_t *ginter, int32_t *err_list,
+                                                       int32_t *err_n) {
+    __shared__ Cand s_red[16 + 8];
+    __shared__ int32_t s_tmp[32];
+    __shared__ int s_flag;
+    __shared__ int32_t s_cnt;
+    for (int32_t k = blockIdx.x; k < count; k += gridDim.x) {
+        if (threadIdx.x == 0) {
+            s_flag = 0;
+            s_cnt = 0;
+        }
+        __syncthreads();
+        int64_t o = goff[k];
+        uint32_t cap = (uint32_t)gcap[k];
+        propose_hashed_node<PIMAX>(C, list[k], gkeys + o, geta + o, ginter + o, cap, cap - 1, err_list, err_n,
+                                   &s_flag, &s_cnt, s_red, s_tmp);
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------- node tiers
+__global__ void k_tiers(const int32_t *bound, int32_t n, uint32_t small_limit, int32_t *lA, int32_t *nA, int32_t *lB,
+                        int32_t *nB) {
+    GRID_STRIDE(v, (int64_t)n) {
+        if ((uint32_t)bound[v] <= small_limit) lA[atomicAdd(nA, 1)] = (int32_t)v;
+        else lB[atomicAdd(nB, 1)] = (int32_t)v;
+    }
+}
+
+__global__ void k_global_caps(const int32_t *list, int32_t count, const int32_t *bound, int32_t *gcap,
+                              int64_t *gsz) {
+    GRID_STRIDE(k, (int64_t)count) {
+        uint32_t b = (uint32_t)bound[list[k]];
+        uint32_t c = 64;
+        while (c < 2u * b + 2u && c < (1u << 30)) c <<= 1;
+        gcap[k] = (int32_t)c;
+        gsz[k] = c;
+    }
+}
+
+static size_t table_bytes(uint32_t cap) { return (size_t)cap * 16; }
+
+template <int PIMAX>
+static void run_proposal(const PropCtx &C, Level &L, const Params &P, Arena &A, uint32_t *err_dev) {
+    cudaStream_t s = A.stream();
+    const int sms = num_sms();
+    int32_t dbg = P.o.debug_table_cap;
+    if (C.n <= DENSE_N && dbg == 0) {
+        size_t sm = (size_t)C.n * 12;
+        HPC(cudaFuncSetAttribute(k_propose_dense<PIMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        int occ = 0;
+        HPC(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_propose_dense<PIMAX>, PT, sm));
+        int grid = std::max(1, std::min<int>(C.n, sms * std::max(occ, 1)));
+        k_propose_dense<PIMAX><<<grid, PT, sm, s>>>(C);
+        HP_LAUNCH_CHECK();
+        return;
+    }
+    // tiered hashed tables
+    uint32_t capA = 512, capB = 4096, capC = 8192;
+    if (dbg > 0) capA = capB = capC = (uint32_t)dbg;
+    int32_t *cnts = A.get<int32_t>(8);
+    HPC(cudaMemsetAsync(cnts, 0, 8 * sizeof(int32_t), s));
+    int32_t *lA = A.get<int32_t>(C.n), *lB = A.get<int32_t>(C.n), *lC = A.get<int32_t>(C.n), *lG = A.get<int32_t>(C.n);
+    k_tiers<<<grid_of(C.n, 256), 256, 0, s>>>(L.nbnd, C.n, capA / 2, lA, cnts + 0, lB, cnts + 1);
+    HP_LAUNCH_CHECK();
+    int32_t hc[8];
+    fetch_bytes(hc, cnts, sizeof hc, s);
+    auto launch_smem = [&](const int32_t *list, int32_t count, uint32_t cap, int32_t *ovf, int32_t *ovf_n) {
+        if (count <= 0) return;
+        size_t sm = table_bytes(cap);
+        HPC(cudaFuncSetAttribute(k_propose_smem<PIMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        int occ = 0;
+        HPC(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_propose_smem<PIMAX>, PT, sm));
+        int grid = std::max(1, std::min<int>(count, sms * std::max(occ, 1)));
+        k_propose_smem<PIMAX><<<grid, PT, sm, s>>>(C, list, count, cap, cap * 3 / 4, ovf, ovf_n);
+        HP_LAUNCH_CHECK();
+    };
+    // tier A nodes cannot overflow (bound <= capA/2); tier B may (optimistic)
+    launch_smem(lA, hc[0], capA, lC, cnts + 2);
+    launch_smem(lB, hc[1], capB, lC, cnts + 2);
+    fetch_bytes(hc, cnts, sizeof hc, s);
+    launch_smem(lC, hc[2], capC, lG, cnts + 3);
+    fetch_bytes(hc, cnts, sizeof hc, s);
+    int32_t ng = hc[3];
+    if (ng > 0) {
+        int32_t *gcap = A.get<int32_t>(ng);
+        int64_t *gsz = A.get<int64_t>(ng + 1);
+        int64_t *goff = A.get<int64_t>(ng + 1);
+        k_global_caps<<<grid_of(ng, 256), 256, 0, s>>>(lG, ng, L.nbnd, gcap, gsz);
+        HP_LAUNCH_CHECK();
+        scan_excl(gsz, goff, ng, goff + ng, A);
+        int64_t total = fetch<int64_t>(goff + ng, s);
+        int32_t *gkeys = A.get<int32_t>(total);
+        unsigned long long *geta = A.get<unsigned long long>(total);
+        uint32_t *ginter = A.get<uint32_t>(total);
+        HPC(cudaMemsetAsync(gkeys, 0xff, sizeof(int32_t) * total, s));
+        HPC(cudaMemsetAsync(geta, 0, sizeof(unsigned long long) * total, s));
+        HPC(cudaMemsetAsync(ginter, 0, sizeof(uint32_t) * total, s));
+        k_propose_global<PIMAX><<<std::min<int>(ng, sms * 4), PT, 0, s>>>(C, lG, ng, goff, gcap, gkeys, geta, ginter,
+                                                                         lA, cnts + 4);
+        HP_LAUNCH_CHECK();
+        int32_t bad = fetch<int32_t>(cnts + 4, s);
+        if (bad) throw Error(HP_ERR_INTERNAL, "neighbour table in global memory overflowed");
+        A.release(gkeys);
+        A.release(geta);
+        A.release(ginter);
+        A.release(gcap);
+        A.release(gsz);
+        A.release(goff);
+    }
+    A.release(lA);
+    A.release(lB);
+    A.release(lC);
+    A.release(lG);
+    A.release(cnts);
+    (void)err_dev;
+}
+
+// ---------------------------------------------------------------- best-effort pairing
+__global__ void k_iso_flags(const int32_t *cand, int32_t pi, int32_t n, int32_t *flag) {
+    GRID_STRIDE(v, (int64_t)n) flag[v] = cand[(int64_t)v * pi] < 0 ? 1 : 0;
+}
+__global__ void k_iso_compact(const int32_t *flag, const int32_t *pos, const int32_t *size, int32_t n, uint32_t *keys,
+                              uint32_t *vals) {
+    GRID_STRIDE(v, (int64_t)n) {
+        if (flag[v]) {
+            keys[pos[v]] = (uint32_t)size[v];
+            vals[pos[v]] = (uint32_t)v;
+        }
+    }
+}
+__global__ void k_iso_pair(const uint32_t *ids, const int32_t *cntp, const int32_t *size, const int32_t *nin,
+                           int32_t omega, int32_t delta, int32_t *mate, unsigned long long *pairs) {
+    int32_t k = *cntp;
+    GRID_STRIDE(i, (int64_t)(k / 2)) {
+        int32_t a = (int32_t)ids[i], b = (int32_t)ids[k - 1 - i];
+        if ((int64_t)size[a] + size[b] <= omega && (int64_t)nin[a] + nin[b] <= delta) {
+            mate[a] = b;
+            mate[b] = a;
+            atomicAdd(pairs, 1ull);
+        }
+    }
+}
+
+// ---------------------------------------------------------------- matching
+__global__ void k_targets(const int32_t *cand, const uint64_t *cscore, int32_t pi, const int32_t *mate, int32_t n,
+                          int32_t *target, uint64_t *score) {
+    GRID_STRIDE(v, (int64_t)n) {
+        int32_t t = -1;
+        uint64_t sc = 0;
+        if (mate[v] < 0) {
+            for (int32_t i = 0; i < pi; i++) {
+                int32_t c = cand[(int64_t)v * pi + i];
+                if (c < 0) break;
+                if (mate[c] < 0) {
+                    t = c;
+                    sc = cscore[(int64_t)v * pi + i];
+                    break;
+                }
+            }
+        }
+        target[v] = t;
+        score[v] = sc;
+    }
+}
+
+// child(n) \ R: count, then fill
+__global__ void k_child_count(const int32_t *target, int32_t n, int32_t *ccount) {
+    GRID_STRIDE(v, (int64_t)n) {
+        int32_t t = target[v];
+        if (t >= 0 && target[t] != v) atomicAdd(&ccount[t], 1);
+    }
+}
+__global__ void k_child_fill(const int32_t *target, int32_t n, const int32_t *coff, int32_t *fillpos, int32_t *kids) {
+    GRID_STRIDE(v, (int64_t)n) {
+        int32_t t = target[v];
+        if (t >= 0 && target[t] != v) kids[coff[t] + atomicAdd(&fillpos[t], 1)] = (int32_t)v;
+    }
+}
+
+struct DpCtx {
+    int32_t n;
+    const int32_t *target, *coff, *kids;
+    const uint64_t *score;
+    int32_t *pending;
+    long long *ss0, *ss10, *sum0;
+    int32_t *best;
+    uint32_t *err;
+};
+
+// Bottom-up (Eq. 7, 8, 10): a thread starts at every leaf and climbs; the
+// thread completing the last child of a node continues with that node, so a
+// node is evaluated once, after all of its children.
+__global__ void k_dp_up(DpCtx D) {
+    GRID_STRIDE(v0, (int64_t)D.n) {
+        int32_t v = (int32_t)v0;
+        if (D.coff[v + 1] != D.coff[v]) continue;   // not a leaf
+        if (D.target[v] < 0) continue;              // isolated, no proposal edge
+        int32_t cur = v;
+        for (int32_t steps = 0;; steps++) {
+            if (steps > D.n) {
+                atomicOr(D.err, E_TIMEOUT);
+                break;
+            }
+            long long s0 = 0, bss = 0;
+            int32_t b = -1;
+            for (int32_t k = D.coff[cur]; k < D.coff[cur + 1]; k++) {
+                int32_t c = D.kids[k];
+                long long c0 = __ldcg(&D.ss0[c]), c10 = __ldcg(&D.ss10[c]);
+                s0 += c0;
+                if (b < 0 || c10 > bss || (c10 == bss && c > b)) {
+                    b = c;
+                    bss = c10;
+                }
+            }
+            long long my0 = s0 + ((b >= 0 && bss > 0) ? bss : 0);
+            __stcg(&D.sum0[cur], s0);
+            __stcg(&D.ss0[cur], my0);
+            D.best[cur] = b;
+            int32_t t = D.target[cur];
+            if (t < 0 || D.target[t] == cur) break;   // a root
+            __stcg(&D.ss10[cur], (long long)D.score[cur] + s0 - my0);
+            __threadfence();
+            if (atomicSub(&D.pending[t], 1) != 1) break;
+            __threadfence();
+            cur = t;
+        }
+    }
+}
+
+// Top-down (Eq. 11, 12): up(v) = v matched to target(v).  A node is up iff
+// it is its parent's best child with ss1-0 > 0 and the parent is not up; the
+// chain of such links ends at a node that is not up or at a root.
+__global__ void k_dp_down(DpCtx D, const int32_t *target, int32_t *mate, unsigned long long *pairs) {
+    GRID_STRIDE(v0, (int64_t)D.n) {
+        int32_t v = (int32_t)v0;
+        if (target[v] < 0) continue;
+        int32_t cur = v, k = 0;
+        bool base = false;
+        for (int32_t steps = 0;; steps++) {
+            if (steps > D.n) {
+                atomicOr(D.err, E_TIMEOUT);
+                break;
+            }
+            int32_t t = target[cur];
+            if (t < 0) {
+                base = false;
+                break;
+            }
+            if (target[t] == cur) {
+                long long ss1 = (long long)D.score[cur] + __ldcg(&D.sum0[cur]) + __ldcg(&D.sum0[t]);
+                base = ss1 > __ldcg(&D.ss0[cur]) + __ldcg(&D.ss0[t]);
+                break;
+            }
+            if (D.best[t] != cur || __ldcg(&D.ss10[cur]) <= 0) {
+                base = false;
+                break;
+            }
+            cur = t;
+            k++;
+        }
+        bool up = base ^ (k & 1);
+        if (up) {
+            int32_t t = target[v];
+            mate[v] = t;
+            mate[t] = v;
+            if (target[t] != v || v < t) atomicAdd(pairs, 1ull);
+        }
+    }
+}
+
+CoarsenOut coarsen_level(Level &L, int32_t level, const int32_t *w, const Params &P, int32_t *mate, Arena &A,
+                         uint32_t *err_dev) {
+    cudaStream_t s = A.stream();
+    const int32_t n = L.n, pi = P.o.pi;
+    CoarsenOut out;
+    struct Box {
+        unsigned long long qsum, visits, pairs, iso;
+        uint64_t cap;
+    };
+    Box *box = A.get<Box>(1);
+    HPC(cudaMemsetAsync(box, 0, sizeof(Box), s));
+    uint64_t *q = A.get<uint64_t>(L.e);
+    if (L.e > 0) {
+        k_level_q<<<grid_of(L.e, 256), 256, 0, s>>>(L.off, w, L.e, q, &box->qsum);
+        HP_LAUNCH_CHECK();
+    }
+    k_level_cap<<<1, 1, 0, s>>>(&box->qsum, L.e, P.o.noise_permille, &box->cap);
+    HP_LAUNCH_CHECK();
+    if (n > 0) {
+        k_node_bounds<<<grid_of(n, 256), 256, 0, s>>>(L.off, L.ioff, L.inc, n, L.nbnd, &box->visits);
+        HP_LAUNCH_CHECK();
+    }
+    int32_t *cand = A.get<int32_t>((int64_t)n * pi);
+    uint64_t *cscore = A.get<uint64_t>((int64_t)n * pi);
+    PropCtx C;
+    C.n = n;
+    C.pi = pi;
+    C.off = L.off;
+    C.pin = L.pin;
+    C.nsrc = L.nsrc;
+    C.size = L.size;
+    C.ioff = L.ioff;
+    C.inc = L.inc;
+    C.nin = L.nin;
+    C.q = q;
+    C.cap = &box->cap;
+    {
+        // the level key folds seed and level exactly as the oracle's noise
+        uint64_t z = P.seed + 0x9E3779B97F4A7C15ull * (uint64_t)(level + 1);
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        C.level_key = z ^ (z >> 31);
+    }
+    C.omega = P.omega;
+    C.delta = P.delta;
+    C.cand = cand;
+    C.cscore = cscore;
+    C.nbcnt = L.nbnd;   // exact counts replace the bounds (used to size the next level)
+    if (n > 0) {
+        if (pi <= 4) run_proposal<4>(C, L, P, A, err_dev);
+        else run_proposal<16>(C, L, P, A, err_dev);
+    }
+    A.release(q);
+
+    // best-effort pairing of nodes with no valid neighbour (Sec. V-C)
+    fill_i32(mate, n, -1, s);
+    if (n > 0) {
+        int32_t *flag = A.get<int32_t>(n);
+        int32_t *pos = A.get<int32_t>(n + 1);
+        k_iso_flags<<<grid_of(n, 256), 256, 0, s>>>(cand, pi, n, flag);
+        HP_LAUNCH_CHECK();
+        scan_excl(flag, pos, n, pos + n, A);
+        int32_t niso = fetch<int32_t>(pos + n, s);
+        if (niso > 1) {
+            uint32_t *keys = A.get<uint32_t>(niso);
+            uint32_t *ids = A.get<uint32_t>(niso);
+            k_iso_compact<<<grid_of(n, 256), 256, 0, s>>>(flag, pos, L.size, n, keys, ids);
+            HP_LAUNCH_CHECK();
+            radix_sort(keys, ids, niso, bits_for((uint64_t)P.omega), A);
+            k_iso_pair<<<grid_of(niso / 2 + 1, 256), 256, 0, s>>>(ids, pos + n, L.size, L.nin, P.omega, P.delta, mate,
+                                                                  &box->iso);
+            HP_LAUNCH_CHECK();
+            A.release(keys);
+            A.release(ids);
+        }
+        A.release(flag);
+        A.release(pos);
+
+        // Pi rounds of maximum-weight matching (Sec. V-D)
+        int32_t *target = A.get<int32_t>(n);
+        uint64_t *score = A.get<uint64_t>(n);
+        int32_t *ccount = A.get<int32_t>(n + 1);
+        int32_t *coff = A.get<int32_t>(n + 1);
+        int32_t *fillpos = A.get<int32_t>(n);
+        int32_t *kids = A.get<int32_t>(n);
+        long long *ss0 = A.get<long long>(n), *ss10 = A.get<long long>(n), *sum0 = A.get<long long>(n);
+        int32_t *best = A.get<int32_t>(n);
+        DpCtx D;
+        D.n = n;
+        D.target = target;
+        D.coff = coff;
+        D.kids = kids;
+        D.score = score;
+        D.pending = fillpos;
+        D.ss0 = ss0;
+        D.ss10 = ss10;
+        D.sum0 = sum0;
+        D.best = best;
+        D.err = err_dev;
+        for (int32_t r = 0; r < pi; r++) {
+            k_targets<<<grid_of(n, 256), 256, 0, s>>>(cand, cscore, pi, mate, n, target, score);
+            HP_LAUNCH_CHECK();
+            HPC(cudaMemsetAsync(ccount, 0, sizeof(int32_t) * (n + 1), s));
+            k_child_count<<<grid_of(n, 256), 256, 0, s>>>(target, n, ccount);
+            HP_LAUNCH_CHECK();
+            scan_excl(ccount, coff, n + 1, nullptr, A);
+            HPC(cudaMemsetAsync(fillpos, 0, sizeof(int32_t) * n, s));
+            k_child_fill<<<grid_of(n, 256), 256, 0, s>>>(target, n, coff, fillpos, kids);
+            HP_LAUNCH_CHECK();
+            HPC(cudaMemcpyAsync(fillpos, ccount, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s));
+            k_dp_up<<<grid_of(n, 256), 256, 0, s>>>(D);
+            HP_LAUNCH_CHECK();
+            k_dp_down<<<grid_of(n, 256), 256, 0, s>>>(D, target, mate, &box->pairs);
+            HP_LAUNCH_CHECK();
+        }
+        A.release(target);
+        A.release(score);
+        A.release(ccount);
+        A.release(coff);
+        A.release(fillpos);
+        A.release(kids);
+        A.release(ss0);
+        A.release(ss10);
+        A.release(sum0);
+        A.release(best);
+    }
+    A.release(cand);
+    A.release(cscore);
+    Box hb;
+    fetch_bytes(&hb, box, sizeof hb, s);
+    A.release(box);
+    out.pairs = (int64_t)(hb.pairs + hb.iso);
+    out.iso_pairs = (int64_t)hb.iso;
+    out.pin_visits = (int64_t)hb.visits;
+    return out;
+}
+
+}  // namespace hp

@@ -1,0 +1,184 @@
+"""Thin ctypes binding of libhp.so (include/hp.h): argument marshalling only.
+
+Every function named ``hp_*`` forwards to the C function of the same name.
+Device buffers are plain integers (device addresses), e.g. from
+``torch.Tensor.data_ptr()``; ``stream`` is a ``cudaStream_t`` as an integer
+(``torch.cuda.current_stream().cuda_stream``) or 0.  :func:`partition` is a
+convenience wrapper that moves a numpy CSR hypergraph to the GPU with torch,
+calls :func:`hp_partition_ex` and returns numpy results.
+
+There is no CPU fallback: :func:`load` raises when the library has not been
+built (``python -c "import __graft_entry__ as g; g.build()"``).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libhp.so")
+
+HP_OK, HP_ERR_INVALID_ARG, HP_ERR_BAD_CSR, HP_ERR_INFEASIBLE = 0, 1, 2, 3
+HP_ERR_OOM, HP_ERR_CUDA, HP_ERR_TIMEOUT, HP_ERR_INTERNAL = 4, 5, 6, 7
+HP_COUNT_INBOUND, HP_COUNT_INCIDENT = 0, 1
+
+EXPORTS = ("hp_default_options", "hp_partition", "hp_partition_ex", "hp_partition_host", "hp_set_allocator",
+           "hp_status_string", "hp_last_error", "hp_connectivity")
+
+
+class hp_options(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_int32) for k in ("pi", "theta", "chain_window", "chain_rounds", "noise_permille",
+                                               "count_kind", "max_levels", "debug_table_cap")]
+
+
+class hp_stats(ctypes.Structure):
+    _fields_ = [("connectivity", ctypes.c_int64), ("cut_net", ctypes.c_int64), ("num_parts", ctypes.c_int32),
+                ("max_part_size", ctypes.c_int32), ("max_part_distinct", ctypes.c_int32),
+                ("violations", ctypes.c_int32), ("levels", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+                ("moves_applied", ctypes.c_int64), ("pin_visits", ctypes.c_int64), ("ms_total", ctypes.c_double),
+                ("ms_coarsen", ctypes.c_double), ("ms_refine", ctypes.c_double)]
+
+
+class hp_level_trace(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("pairs", ctypes.c_int32), ("iso_pairs", ctypes.c_int32),
+                ("reps", ctypes.c_int32), ("pins", ctypes.c_int64), ("conn", ctypes.c_int64),
+                ("moves", ctypes.c_int64)]
+
+
+_lib = None
+P, I32, U64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_uint64
+
+
+def load() -> ctypes.CDLL:
+    """Load libhp.so; raises if it is missing (no fallback path exists)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_2605_20497_gb300.build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        L.hp_default_options.argtypes = [ctypes.POINTER(hp_options)]
+        L.hp_default_options.restype = None
+        part_args = [P, P, I32, I32, P, P, I32, I32, U64, ctypes.POINTER(hp_options), P, ctypes.POINTER(hp_stats)]
+        L.hp_partition.argtypes = part_args + [P]
+        L.hp_partition.restype = ctypes.c_int
+        L.hp_partition_ex.argtypes = part_args + [ctypes.POINTER(hp_level_trace), I32, P]
+        L.hp_partition_ex.restype = ctypes.c_int
+        L.hp_partition_host.argtypes = part_args + [P]
+        L.hp_partition_host.restype = ctypes.c_int
+        L.hp_set_allocator.argtypes = [P, P, P]
+        L.hp_set_allocator.restype = ctypes.c_int
+        L.hp_status_string.argtypes = [ctypes.c_int]
+        L.hp_status_string.restype = ctypes.c_char_p
+        L.hp_last_error.argtypes = []
+        L.hp_last_error.restype = ctypes.c_char_p
+        L.hp_connectivity.argtypes = [P, P, I32, P, P, I32, I32, ctypes.POINTER(ctypes.c_int64),
+                                      ctypes.POINTER(ctypes.c_int64), P]
+        L.hp_connectivity.restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+# ------------------------------------------------------------- same-name calls
+def hp_default_options() -> hp_options:
+    o = hp_options()
+    load().hp_default_options(ctypes.byref(o))
+    return o
+
+
+def hp_partition(pins, offsets, num_hedges, num_nodes, src_counts, weights, omega, delta, seed, opt, part_out,
+                 stats, stream=0) -> int:
+    return load().hp_partition(pins, offsets, num_hedges, num_nodes, src_counts, weights, omega, delta,
+                               ctypes.c_uint64(seed), opt, part_out, stats, stream)
+
+
+def hp_partition_ex(pins, offsets, num_hedges, num_nodes, src_counts, weights, omega, delta, seed, opt, part_out,
+                    stats, trace, trace_cap, stream=0) -> int:
+    return load().hp_partition_ex(pins, offsets, num_hedges, num_nodes, src_counts, weights, omega, delta,
+                                  ctypes.c_uint64(seed), opt, part_out, stats, trace, trace_cap, stream)
+
+
+def hp_partition_host(pins, offsets, num_hedges, num_nodes, src_counts, weights, omega, delta, seed, opt, part_out,
+                      stats, stream=0) -> int:
+    return load().hp_partition_host(pins, offsets, num_hedges, num_nodes, src_counts, weights, omega, delta,
+                                    ctypes.c_uint64(seed), opt, part_out, stats, stream)
+
+
+def hp_connectivity(pins, offsets, num_hedges, weights, part, num_nodes, num_parts, stream=0):
+    c, cn = ctypes.c_int64(0), ctypes.c_int64(0)
+    st = load().hp_connectivity(pins, offsets, num_hedges, weights, part, num_nodes, num_parts, ctypes.byref(c),
+                                ctypes.byref(cn), stream)
+    return st, int(c.value), int(cn.value)
+
+
+def hp_status_string(status: int) -> str:
+    return load().hp_status_string(status).decode()
+
+
+def hp_last_error() -> str:
+    return load().hp_last_error().decode()
+
+
+# ------------------------------------------------------------- convenience
+@dataclass
+class Result:
+    status: int
+    part: np.ndarray
+    stats: dict
+    trace: list
+
+
+def options(**kw) -> hp_options:
+    o = hp_default_options()
+    for k, v in kw.items():
+        setattr(o, k, int(v))
+    return o
+
+
+def _stats_dict(s: hp_stats) -> dict:
+    return {k: getattr(s, k) for k, _ in hp_stats._fields_ if k != "reserved0"}
+
+
+def to_device(g, device="cuda"):
+    """numpy CSR hypergraph -> dict of int32 torch tensors on the GPU."""
+    import torch
+    t = lambda a: None if a is None else torch.from_numpy(np.ascontiguousarray(a, dtype=np.int32)).to(device)
+    return dict(offsets=t(g.offsets), pins=t(g.pins) if g.num_pins else torch.zeros(1, dtype=torch.int32, device=device),
+                src_counts=t(g.src_counts), weights=t(g.weights))
+
+
+def partition(g, omega: int, delta: int, seed: int = 0, trace: bool = False, dev=None, stream=0, **opts) -> Result:
+    """Partition numpy hypergraph ``g`` on the current CUDA device."""
+    import torch
+    d = dev if dev is not None else to_device(g)
+    part = torch.empty(max(g.num_nodes, 1), dtype=torch.int32, device=d["offsets"].device)
+    st = hp_stats()
+    cap = 4096 if trace else 0
+    tr = (hp_level_trace * cap)() if cap else None
+    ptr = lambda x: None if x is None else x.data_ptr()
+    rc = hp_partition_ex(ptr(d["pins"]), ptr(d["offsets"]), g.num_hedges, g.num_nodes, ptr(d["src_counts"]),
+                         ptr(d["weights"]), omega, delta, seed, ctypes.byref(options(**opts)), part.data_ptr(),
+                         ctypes.byref(st), tr, cap, stream)
+    torch.cuda.synchronize()
+    sd = _stats_dict(st)
+    levels = []
+    if rc == HP_OK and tr is not None:
+        for l in range(min(sd["levels"], cap)):
+            x = tr[l]
+            levels.append(dict(n=x.n, pins=x.pins, pairs=x.pairs, iso_pairs=x.iso_pairs, conn=x.conn,
+                               moves=x.moves, reps=x.reps))
+    return Result(rc, part[: g.num_nodes].cpu().numpy(), sd, levels)
+
+
+def partition_host(g, omega: int, delta: int, seed: int = 0, stream=0, **opts) -> Result:
+    """Host-memory entry point: one copy in, one copy out (hp_partition_host)."""
+    a = lambda x: None if x is None else np.ascontiguousarray(x, dtype=np.int32)
+    off, pins, src, w = a(g.offsets), a(g.pins), a(g.src_counts), a(g.weights)
+    part = np.zeros(max(g.num_nodes, 1), dtype=np.int32)
+    st = hp_stats()
+    p = lambda x: None if x is None else x.ctypes.data
+    rc = hp_partition_host(p(pins), p(off), g.num_hedges, g.num_nodes, p(src), p(w), omega, delta, seed,
+                           ctypes.byref(options(**opts)), p(part), ctypes.byref(st), stream)
+    return Result(rc, part[: g.num_nodes], _stats_dict(st), [])

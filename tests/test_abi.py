@@ -1,0 +1,54 @@
+"""The C-ABI library builds, loads and exports every symbol include/hp.h
+declares; host-only calls work without a GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2605_20497_gb300 import build, hp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    src = open(os.path.join(ROOT, "include", "hp.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(hp_[a-z_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return hp.load()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    syms = declared_symbols()
+    assert "hp_partition" in syms and "hp_partition_host" in syms
+    for s in syms:
+        assert hasattr(lib, s), s
+        assert s in hp.EXPORTS, s
+
+
+def test_only_declared_symbols_are_exported(lib):
+    import subprocess
+    out = subprocess.run(["nm", "-D", "--defined-only", hp.LIB_PATH], capture_output=True, text=True).stdout
+    exported = {l.split()[-1] for l in out.splitlines() if " T " in l}
+    ours = {s for s in exported if s.startswith("hp_")}
+    assert ours == set(declared_symbols())
+
+
+def test_host_only_calls(lib):
+    o = hp.hp_default_options()
+    assert (o.pi, o.theta, o.chain_window, o.chain_rounds, o.noise_permille, o.count_kind, o.max_levels,
+            o.debug_table_cap) == (4, 16, 256, 16, 100, 0, 256, 0)
+    assert hp.hp_status_string(hp.HP_OK) == "ok"
+    assert "CSR" in hp.hp_status_string(hp.HP_ERR_BAD_CSR)
+    assert hp.hp_last_error() == ""
+
+
+def test_struct_layout_matches_header(lib):
+    assert ctypes.sizeof(hp.hp_options) == 8 * 4
+    assert ctypes.sizeof(hp.hp_stats) == 8 + 8 + 6 * 4 + 8 + 8 + 3 * 8
+    assert ctypes.sizeof(hp.hp_level_trace) == 4 * 4 + 3 * 8

@@ -1,0 +1,154 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle.
+
+Integer work end to end, so the bar is bit-exact: the same status, the same
+part vector, the same statistics and the same per-level trace (nodes, pins,
+pairs, connectivity after refinement, moves, repetitions).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2605_20497_gb300 import hp, inputs
+
+pytestmark = pytest.mark.gpu
+
+TRACE_KEYS = ("n", "pins", "pairs", "iso_pairs", "conn", "moves", "reps")
+STAT_KEYS = ("connectivity", "cut_net", "num_parts", "max_part_size", "max_part_distinct", "violations",
+             "levels", "moves_applied")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2605_20497_gb300 import build
+    build.build()
+    oracle.build()
+    hp.load()
+    return torch
+
+
+def check_same(g, omega, delta, seed=0, trace=True, **opts):
+    r = hp.partition(g, omega, delta, seed=seed, trace=trace, **opts)
+    okeys = {k: v for k, v in opts.items() if k != "debug_table_cap"}
+    o = oracle.partition(g, omega, delta, seed=seed, trace=trace, **okeys)
+    assert r.status == o.status, (r.status, o.status, hp.hp_last_error())
+    if o.status != oracle.OK:
+        return r, o
+    if trace:
+        assert len(r.trace) == len(o.trace)
+        for l, (a, b) in enumerate(zip(r.trace, o.trace)):
+            for k in TRACE_KEYS:
+                assert a[k] == b[k], f"level {l} {k}: gpu {a[k]} oracle {b[k]}"
+    for k in STAT_KEYS:
+        assert r.stats[k] == o.stats[k], (k, r.stats[k], o.stats[k])
+    assert np.array_equal(r.part, o.part)
+    return r, o
+
+
+TINY = [
+    dict(n=12, e=10, max_size=5, seed=1),
+    dict(n=20, e=30, max_size=6, seed=2, multi_src=True),
+    dict(n=16, e=25, max_size=4, seed=3, weights=True),
+    dict(n=25, e=20, max_size=8, seed=4, multi_src=True, weights=True, isolated=3),
+    dict(n=70, e=90, max_size=9, seed=5),
+    dict(n=300, e=350, max_size=12, seed=6, multi_src=True),
+    dict(n=2000, e=1800, max_size=40, seed=7, weights=True),
+]
+
+
+@pytest.mark.parametrize("spec", TINY)
+@pytest.mark.parametrize("omega,delta", [(2, 100), (4, 8), (16, 40), (1000, 100000)])
+def test_tiny_parity(spec, omega, delta):
+    g = inputs.random_hypergraph(**spec)
+    check_same(g, omega, delta, seed=spec["seed"])
+
+
+@pytest.mark.parametrize("spec", TINY[3:])
+@pytest.mark.parametrize("kind", [0, 1])
+@pytest.mark.parametrize("pi", [1, 4, 7])
+def test_options_parity(spec, kind, pi):
+    g = inputs.random_hypergraph(**spec)
+    check_same(g, 8, 30, seed=11, count_kind=kind, pi=pi, theta=6, chain_window=3, chain_rounds=2,
+               noise_permille=0 if pi == 7 else 100)
+
+
+@pytest.mark.parametrize("cap", [64, 256])
+def test_overflow_paths_parity(cap):
+    """A tiny neighbour/gain table forces every overflow path (result-neutral)."""
+    g = inputs.random_hypergraph(3000, 2500, 60, seed=8, multi_src=True)
+    check_same(g, 12, 200, seed=2, debug_table_cap=cap)
+    g = inputs.random_snn(1024, 31, seed=4)
+    check_same(g, 64, 512, seed=1, debug_table_cap=cap)
+
+
+def test_planted_components():
+    rng = np.random.default_rng(3)
+    g = inputs.planted_components(rng.integers(2, 30, 300).tolist(), edges_per_comp=8, edge_size=5, seed=3)
+    r, o = check_same(g, 32, 10000)
+    assert r.stats["connectivity"] == 0
+
+
+def test_random_snn_4k_parity():
+    g = inputs.workload("random_snn_4k")
+    check_same(g, *inputs.CONSTRAINTS["random_snn_4k"])
+
+
+def test_random_snn_4k_incident_parity():
+    g = inputs.workload("random_snn_4k")
+    check_same(g, 256, 1024, count_kind=1)
+
+
+def test_layered_16k_parity():
+    g = inputs.workload("layered_snn_16k")
+    check_same(g, *inputs.CONSTRAINTS["layered_snn_16k"])
+
+
+def test_error_status_parity():
+    base = inputs.random_hypergraph(10, 5, 3, seed=1)
+    bad = inputs.Hypergraph(10, base.offsets, base.pins.copy())
+    bad.pins[0] = 10
+    dup = inputs.Hypergraph(3, np.array([0, 2], np.int32), np.array([1, 1], np.int32))
+    srcdst = inputs.Hypergraph(3, np.array([0, 2], np.int32), np.array([1, 1], np.int32), np.array([1], np.int32))
+    mono = inputs.Hypergraph(3, np.array([0, 2, 2], np.int32), np.array([0, 1], np.int32))
+    srcbad = inputs.Hypergraph(3, np.array([0, 2], np.int32), np.array([0, 1], np.int32), np.array([3], np.int32))
+    star = inputs.Hypergraph(4, np.array([0, 2, 4, 6], np.int32), np.array([0, 3, 1, 3, 2, 3], np.int32))
+    wbad = inputs.Hypergraph(4, star.offsets, star.pins, None, np.array([1, 0, 1], np.int32))
+    for g, om, de in [(bad, 4, 5), (dup, 4, 5), (srcdst, 4, 5), (mono, 4, 5), (srcbad, 4, 5), (star, 4, 2),
+                      (star, 4, 3), (wbad, 4, 3), (base, 0, 5)]:
+        r = hp.partition(g, om, de)
+        o = oracle.partition(g, om, de)
+        assert r.status == o.status, (g.name, r.status, o.status)
+
+
+def test_empty_and_edge_free():
+    empty = inputs.Hypergraph(0, np.array([0], np.int32), np.zeros(0, np.int32))
+    r = hp.partition(empty, 4, 3)
+    assert r.status == hp.HP_OK and r.stats["num_parts"] == 0
+    lone = inputs.Hypergraph(9, np.array([0], np.int32), np.zeros(0, np.int32))
+    check_same(lone, 2, 0)
+    single = inputs.Hypergraph(5, np.array([0, 1, 2], np.int32), np.array([3, 3 + 1], np.int32))
+    check_same(single, 3, 1)
+
+
+def test_determinism_and_host_api():
+    g = inputs.random_snn(2048, 31, seed=9)
+    a = hp.partition(g, 128, 700, seed=5)
+    b = hp.partition(g, 128, 700, seed=5)
+    c = hp.partition_host(g, 128, 700, seed=5)
+    assert a.status == b.status == c.status == hp.HP_OK
+    assert np.array_equal(a.part, b.part) and np.array_equal(a.part, c.part)
+    assert a.stats["connectivity"] == c.stats["connectivity"]
+
+
+def test_connectivity_entry_point(gpu):
+    torch = gpu
+    g = inputs.random_hypergraph(500, 600, 10, seed=3, weights=True)
+    rho = np.random.default_rng(0).integers(0, 7, 500).astype(np.int32)
+    d = hp.to_device(g)
+    part = torch.from_numpy(rho).cuda()
+    st, c, cn = hp.hp_connectivity(d["pins"].data_ptr(), d["offsets"].data_ptr(), g.num_hedges,
+                                   d["weights"].data_ptr(), part.data_ptr(), 500, 7)
+    assert st == hp.HP_OK
+    assert (c, cn) == oracle.objective(g, rho, 7)
