@@ -1,0 +1,312 @@
+#!/usr/bin/env python3
+"""Benchmark: pins partitioned per second by the GB300 partitioner.
+
+One step = one full constrained multilevel partition (coarsening + refinement,
+every step on the GPU) of the layered spiking-network hypergraph: 8 layers of
+32 x 32 x 32 neurons (262,144 nodes, 63,565,824 pins, Omega = 4096,
+Delta = 65536).  Inputs are device resident when the timed region starts; the
+inputs (254 MB) are larger than L2, so no separate flush is needed.
+
+Prints one JSON line on rank 0.  ``--impl reference`` times the CPU oracle
+(single thread) on a bounded sample of the same workload family instead.
+Multi-GPU runs (torchrun, one process per GPU) partition independent replicas
+(the single-instance path does not shard); value = all ranks' pins / the
+slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "layered_snn_262k"
+WORKLOAD_DESC = ("layered SNN hypergraph: 8 layers x 32x32 grid x 32 channels = 262,144 nodes; each neuron of "
+                 "layers 0-6 owns a hyperedge {itself} + all 32 channels of the 3x3 window (border-clipped) in the "
+                 "next layer; 229,376 hyperedges, 63,565,824 pins; Omega=4096, Delta=65536 (inbound); seed 0")
+# bounded CPU samples of the same generator family (same hyperedge structure, smaller grid)
+CPU_SAMPLE = ("layered_snn_65k", "layered SNN 8 layers x 16x16 grid x 32 channels (65,536 nodes, 15.2M pins), "
+              "Omega=4096, Delta=65536")
+REF_SAMPLE = ("layered 8x8x8x32", "layered SNN 8 layers x 8x8 grid x 32 channels (16,384 nodes), Omega=4096, "
+              "Delta=65536")
+METRIC = "pins partitioned/s on 1 GB300"
+CLOCK_QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+
+    def __init__(self, gpu_index: int):
+        self.path = tempfile.mktemp(prefix="clocks_", suffix=".csv")
+        self.proc = None
+        self.gpu = gpu_index
+
+    def __enter__(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={CLOCK_QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if not self.proc or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def proposal_bytes(stats: dict, num_pins: int, num_nodes: int, pi: int = 4) -> int:
+    """Algorithmic bytes of the level-0 candidate proposal: every pin of every
+    incident hyperedge once (4 B per visit), size and inbound count of every
+    distinct neighbour (8 B), per incidence entry the hyperedge id and q(e)
+    (12 B), per node the top-pi candidates (12 B each) and its neighbour
+    count (4 B)."""
+    return (4 * stats["l0_pin_visits"] + 8 * stats["l0_neighbours"] + 12 * num_pins
+            + num_nodes * (12 * pi + 4))
+
+
+def traffic_for_current_kernel():
+    """DRAM bytes per launch of the level-0 proposal from the committed ncu
+    summary, if it was taken on the current kernel source (else None)."""
+    p = os.path.join(ROOT, "profiles", "roofline_traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    src = os.path.join(ROOT, "paper_2605_20497_gb300", "csrc", "hp_coarsen.cu")
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    if d.get("source_sha256_16") != h or d.get("workload") != WORKLOAD:
+        return None
+    return d.get("dram_bytes_per_launch")
+
+
+def cpu_baseline(sample_name: str, sample_desc: str):
+    import oracle
+    from paper_2605_20497_gb300 import inputs
+    oracle.build()
+    g = inputs.workload(sample_name)
+    om, de = inputs.CONSTRAINTS[sample_name]
+    t = time.perf_counter()
+    r = oracle.partition(g, om, de, seed=0)
+    dt = time.perf_counter() - t
+    assert r.status == oracle.OK
+    return {"value": g.num_pins / dt, "unit": "pins/s", "cores": 1, "kind": "oracle",
+            "sample": f"{sample_desc}: one full single-threaded oracle partition, {dt:.1f} s",
+            "connectivity": r.stats["connectivity"]}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import numpy as np  # noqa: F401
+    import oracle
+    from paper_2605_20497_gb300 import inputs
+    oracle.build()
+    g = inputs.layered_snn(8, 8, 8, 32)
+    om, de = 4096, 65536
+    for _ in range(args.warmup):
+        oracle.partition(g, om, de, seed=0)
+    times = []
+    for _ in range(args.steps):
+        t = time.perf_counter()
+        r = oracle.partition(g, om, de, seed=0)
+        times.append(time.perf_counter() - t)
+        assert r.status == oracle.OK
+    dt = sum(times) / len(times)
+    val = g.num_pins / dt
+    out = {"impl": "reference", "metric": METRIC, "value": val, "unit": "pins/s", "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "sample": REF_SAMPLE[1], "pins_per_step": g.num_pins},
+           "cpu_baseline": {"value": val, "unit": "pins/s", "cores": 1, "kind": "oracle",
+                            "sample": f"{REF_SAMPLE[1]}: one single-threaded oracle partition per step"},
+           "e2e": {"value": val, "unit": "pins/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2605_20497_gb300 import hp, inputs
+
+    g = inputs.workload(WORKLOAD)
+    omega, delta = inputs.CONSTRAINTS[WORKLOAD]
+    d = hp.to_device(g)
+    n = g.num_nodes
+    part = torch.empty(n, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream()
+    sp = stream.cuda_stream
+    opt = hp.hp_default_options()
+    st = hp.hp_stats()
+
+    def step():
+        rc = hp.hp_partition(d["pins"].data_ptr(), d["offsets"].data_ptr(), g.num_hedges, n, None, None, omega,
+                             delta, 0, ctypes.byref(opt), part.data_ptr(), ctypes.byref(st), sp)
+        if rc != hp.HP_OK:
+            raise RuntimeError(f"hp_partition failed: {hp.hp_status_string(rc)}: {hp.hp_last_error()}")
+        return {k: getattr(st, k) for k, _ in hp.hp_stats._fields_}
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    for _ in range(args.warmup):
+        step()
+    per = []
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        barrier()
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            per.append(step())
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    clocks = clk.summary()
+    value = world * g.num_pins / (ms / 1e3)
+
+    # end to end through the host entry point: pinned host inputs, H2D + D2H inside
+    h_off = torch.from_numpy(g.offsets).pin_memory()
+    h_pins = torch.from_numpy(g.pins).pin_memory()
+    h_part = torch.empty(n, dtype=torch.int32).pin_memory()
+    st2 = hp.hp_stats()
+
+    def e2e_step():
+        rc = hp.hp_partition_host(h_pins.data_ptr(), h_off.data_ptr(), g.num_hedges, n, None, None, omega, delta, 0,
+                                  ctypes.byref(opt), h_part.data_ptr(), ctypes.byref(st2), sp)
+        if rc != hp.HP_OK:
+            raise RuntimeError(hp.hp_last_error())
+
+    e2e_step()
+    barrier()
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        e2e_step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ms_e2e = ev0.elapsed_time(ev1) / args.steps
+    if world > 1:
+        t = torch.tensor([ms_e2e], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_e2e = float(t.item())
+    import numpy as np
+    assert np.array_equal(h_part.numpy(), part.cpu().numpy()), "host and device entry points disagree"
+
+    last = per[-1]
+    prop_ms = statistics.mean(p["ms_propose_l0"] for p in per)
+    alg = proposal_bytes(last, g.num_pins, n, opt.pi)
+    peak, peak_kind = measured_peaks()
+    achieved = alg / (prop_ms / 1e3) / 1e9
+    launches = sum(p["kernel_launches"] for p in per)
+    out = {
+        "metric": METRIC, "value": value, "unit": "pins/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "description": WORKLOAD_DESC, "pins": g.num_pins, "nodes": n,
+                   "omega": omega, "delta": delta, "l2": "inputs (254 MB) exceed L2; no flush",
+                   "parallelism": "replicas" if world > 1 else "single",
+                   "connectivity": last["connectivity"], "num_parts": last["num_parts"],
+                   "violations": last["violations"], "levels": last["levels"],
+                   "moves_applied": last["moves_applied"], "ms_coarsen": last["ms_coarsen"],
+                   "ms_refine": last["ms_refine"]},
+        "e2e": {"value": world * g.num_pins / (ms_e2e / 1e3), "unit": "pins/s",
+                "h2d_bytes_per_step": int(g.offsets.nbytes + g.pins.nbytes), "d2h_bytes_per_step": int(4 * n)},
+        "roofline": {"bound": "hbm", "kernel": "level-0 candidate proposal (k_propose_smem)", "achieved": achieved,
+                     "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic_for_current_kernel(),
+                     "algorithmic_bytes": alg, "ms_per_launch": prop_ms,
+                     "peak_source": f"{peak_kind} hbm_gbs"},
+        "gpu_launches": launches,
+        "clocks": clocks,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(*CPU_SAMPLE)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

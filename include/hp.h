@@ -112,6 +112,10 @@ typedef struct {
     double ms_total;           /* device time of the call, input checks included */
     double ms_coarsen;
     double ms_refine;
+    int64_t kernel_launches;   /* CUDA kernels this call launched */
+    int64_t l0_pin_visits;     /* sum_e |e|^2 of level 0: pins read by the level-0 proposal */
+    int64_t l0_neighbours;     /* sum over nodes of |N(n)| at level 0 */
+    double ms_propose_l0;      /* CUDA-event time of the level-0 candidate proposal (Sec. V-C) */
 } hp_stats;
 
 /* Per-level trace record (optional output of hp_partition_ex). */
@@ -185,6 +189,41 @@ HP_API const char *hp_last_error(void);
 HP_API hp_status hp_connectivity(const int32_t *pins, const int32_t *offsets, int32_t num_hedges, const int32_t *weights,
                           const int32_t *part, int32_t num_nodes, int32_t num_parts, int64_t *conn_out,
                           int64_t *cutnet_out, void *stream);
+
+/*
+ * Step-level entry points (test hooks) on one level graph given in device
+ * memory: num_nodes, num_hedges, offsets, pins, src_counts (required, one
+ * count per hyperedge), weights (required) and node sizes.  They run one step
+ * of the method exactly as hp_partition runs it inside its level loop.
+ *
+ * hp_debug_coarsen_level -- one coarsening level (Sec. V-C, V-D): the top-pi
+ *   candidates of every node (cand_out[n*pi], -1 padded; score_out[n*pi] the
+ *   fixed-point eta plus noise of Eq. 5, noise keyed by seed and level), then
+ *   best-effort pairing and pi rounds of matching; mate_out[n] is the
+ *   partner or -1; *pairs_out (host) counts the pairs.
+ */
+HP_API hp_status hp_debug_coarsen_level(int32_t num_nodes, int32_t num_hedges, const int32_t *offsets,
+                                        const int32_t *pins, const int32_t *src_counts, const int32_t *weights,
+                                        const int32_t *size, int32_t omega, int32_t delta, uint64_t seed,
+                                        int32_t level, const hp_options *opt, int32_t *cand_out, uint64_t *score_out,
+                                        int32_t *mate_out, int64_t *pairs_out, void *stream);
+
+/*
+ * hp_debug_refine_rep -- one refinement repetition (Sec. VI) of part vector
+ *   rho (device int32[n], ids < num_parts, updated in place).  Device outputs
+ *   of n entries: the proposed moves sorted by (p_s asc, gain desc, node asc)
+ *   (move_node/src/dst/gain, Eq. 13), seq[k] = index of the k-th move of the
+ *   chained sequence (Sec. VI-C), gseq[k] its in-sequence gain (Eq. 14-15).
+ *   Host outputs: *num_moves, *applied (moves of the best valid prefix,
+ *   Sec. VI-D) and *best_gain (its cumulative gain; 0 when none is applied).
+ */
+HP_API hp_status hp_debug_refine_rep(int32_t num_nodes, int32_t num_hedges, const int32_t *offsets,
+                                     const int32_t *pins, const int32_t *src_counts, const int32_t *weights,
+                                     const int32_t *size, int32_t *rho, int32_t num_parts, int32_t second_half,
+                                     int32_t omega, int32_t delta, const hp_options *opt, int32_t *move_node,
+                                     int32_t *move_src, int32_t *move_dst, int64_t *move_gain, int32_t *seq,
+                                     int64_t *gseq, int32_t *num_moves, int32_t *applied, int64_t *best_gain,
+                                     void *stream);
 
 #ifdef __cplusplus
 }

@@ -22,8 +22,8 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 OK, ERR_INVALID_ARG, ERR_BAD_CSR, ERR_INFEASIBLE = 0, 1, 2, 3
 COUNT_INBOUND, COUNT_INCIDENT = 0, 1
 # layout of the option vector (see hp_oracle.c)
-OPT_KEYS = ("pi", "theta", "window", "rounds", "permille", "count_kind", "max_levels")
-DEFAULTS = dict(pi=4, theta=16, window=256, rounds=16, permille=100, count_kind=0, max_levels=256)
+OPT_KEYS = ("pi", "theta", "chain_window", "chain_rounds", "noise_permille", "count_kind", "max_levels")
+DEFAULTS = dict(pi=4, theta=16, chain_window=256, chain_rounds=16, noise_permille=100, count_kind=0, max_levels=256)
 STAT_KEYS = ("connectivity", "cut_net", "num_parts", "max_part_size", "max_part_distinct",
              "violations", "levels", "moves_applied")
 TRACE_KEYS = ("n", "pins", "pairs", "iso_pairs", "conn", "moves", "reps", "parts")
@@ -99,6 +99,9 @@ class Result:
 
 def partition(g, omega: int, delta: int, seed: int = 0, trace: bool = False, **opts) -> Result:
     """Full multilevel partition of hypergraph ``g`` (see paper Sec. III)."""
+    unknown = set(opts) - set(DEFAULTS)
+    if unknown:
+        raise TypeError(f"unknown oracle option(s): {sorted(unknown)}")
     o = dict(DEFAULTS)
     o.update(opts)
     optv = np.array([o[k] for k in OPT_KEYS] + [0], dtype=np.int32)

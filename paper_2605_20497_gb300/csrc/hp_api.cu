@@ -65,17 +65,21 @@ static bool options_ok(const hp_options &o) {
 }
 
 struct Timer {
-    cudaEvent_t a, b, c;
+    cudaEvent_t a, b, c, p[2];
     cudaStream_t s;
     explicit Timer(cudaStream_t st) : s(st) {
         HPC(cudaEventCreate(&a));
         HPC(cudaEventCreate(&b));
         HPC(cudaEventCreate(&c));
+        HPC(cudaEventCreate(&p[0]));
+        HPC(cudaEventCreate(&p[1]));
     }
     ~Timer() {
         cudaEventDestroy(a);
         cudaEventDestroy(b);
         cudaEventDestroy(c);
+        cudaEventDestroy(p[0]);
+        cudaEventDestroy(p[1]);
     }
 };
 
@@ -92,6 +96,7 @@ static hp_status run(const int32_t *pins, const int32_t *offsets, int32_t e, int
         (trace_cap > 0 && !trace))
         return HP_ERR_INVALID_ARG;
     Timer T(s);
+    const int64_t launches0 = t_launches;
     HPC(cudaEventRecord(T.a, s));
     Arena A(s);
     int32_t *w = A.get<int32_t>(e);
@@ -112,6 +117,7 @@ static hp_status run(const int32_t *pins, const int32_t *offsets, int32_t e, int
     // ---- coarsening (Sec. V)
     const int64_t target_n = ((int64_t)n + omega - 1) / omega;
     int32_t L = 0;
+    bool prop0_timed = false;
     for (;;) {
         hp_level_trace t;
         std::memset(&t, 0, sizeof t);
@@ -122,8 +128,13 @@ static hp_status run(const int32_t *pins, const int32_t *offsets, int32_t e, int
             break;
         }
         int32_t *mate = A.get<int32_t>(lv[L].n);
-        CoarsenOut co = coarsen_level(lv[L], L, w, P, mate, A, err_dev);
+        CoarsenOut co = coarsen_level(lv[L], L, w, P, mate, A, err_dev, nullptr, nullptr, L == 0 ? T.p : nullptr);
         st.pin_visits += co.pin_visits;
+        if (L == 0) {
+            prop0_timed = true;
+            st.l0_pin_visits = co.pin_visits;
+            st.l0_neighbours = co.neighbours;
+        }
         t.pairs = (int32_t)co.pairs;
         t.iso_pairs = (int32_t)co.iso_pairs;
         tr.push_back(t);
@@ -199,6 +210,12 @@ static hp_status run(const int32_t *pins, const int32_t *offsets, int32_t e, int
     HPC(cudaEventElapsedTime(&ms_all, T.a, T.c));
     HPC(cudaEventElapsedTime(&ms_c, T.a, T.b));
     HPC(cudaEventElapsedTime(&ms_r, T.b, T.c));
+    if (prop0_timed) {
+        float mp = 0;
+        HPC(cudaEventElapsedTime(&mp, T.p[0], T.p[1]));
+        st.ms_propose_l0 = mp;
+    }
+    st.kernel_launches = t_launches - launches0;
     st.connectivity = hs[0];
     st.cut_net = hs[1];
     st.num_parts = k;
@@ -342,6 +359,72 @@ hp_status hp_connectivity(const int32_t *pins, const int32_t *offsets, int32_t n
         hp::fetch_bytes(h, obj, sizeof h, s);
         if (conn_out) *conn_out = h[0];
         if (cutnet_out) *cutnet_out = h[1];
+        return HP_OK;
+    });
+}
+
+hp_status hp_debug_coarsen_level(int32_t num_nodes, int32_t num_hedges, const int32_t *offsets, const int32_t *pins,
+                                 const int32_t *src_counts, const int32_t *weights, const int32_t *size, int32_t omega,
+                                 int32_t delta, uint64_t seed, int32_t level, const hp_options *opt, int32_t *cand_out,
+                                 uint64_t *score_out, int32_t *mate_out, int64_t *pairs_out, void *stream) {
+    return hp::guarded([&]() -> hp_status {
+        hp::Params P;
+        P.omega = omega;
+        P.delta = delta;
+        P.seed = seed;
+        if (opt) P.o = *opt;
+        else hp_default_options(&P.o);
+        if (num_nodes < 1 || num_hedges < 0 || omega < 1 || delta < 0 || level < 0 || !offsets || !src_counts ||
+            !weights || !size || !cand_out || !score_out || !mate_out || !hp::options_ok(P.o))
+            return HP_ERR_INVALID_ARG;
+        cudaStream_t s = static_cast<cudaStream_t>(stream);
+        hp::Arena A(s);
+        hp::Level L;
+        hp::make_level(num_nodes, num_hedges, offsets, pins, src_counts, size, L, A);
+        uint32_t *err = A.get<uint32_t>(1);
+        HPC(cudaMemsetAsync(err, 0, sizeof(uint32_t), s));
+        hp::CoarsenOut co = hp::coarsen_level(L, level, weights, P, mate_out, A, err, cand_out, score_out);
+        uint32_t e = hp::fetch<uint32_t>(err, s);
+        if (e) return hp::status_of(e);
+        if (pairs_out) *pairs_out = co.pairs;
+        return HP_OK;
+    });
+}
+
+hp_status hp_debug_refine_rep(int32_t num_nodes, int32_t num_hedges, const int32_t *offsets, const int32_t *pins,
+                              const int32_t *src_counts, const int32_t *weights, const int32_t *size, int32_t *rho,
+                              int32_t num_parts, int32_t second_half, int32_t omega, int32_t delta,
+                              const hp_options *opt, int32_t *move_node, int32_t *move_src, int32_t *move_dst,
+                              int64_t *move_gain, int32_t *seq, int64_t *gseq, int32_t *num_moves, int32_t *applied,
+                              int64_t *best_gain, void *stream) {
+    return hp::guarded([&]() -> hp_status {
+        hp::Params P;
+        P.omega = omega;
+        P.delta = delta;
+        P.seed = 0;
+        if (opt) P.o = *opt;
+        else hp_default_options(&P.o);
+        if (num_nodes < 1 || num_hedges < 0 || num_parts < 1 || omega < 1 || delta < 0 || !offsets ||
+            !src_counts || !weights || !size || !rho || !move_node || !move_src || !move_dst || !move_gain ||
+            !seq || !gseq || !hp::options_ok(P.o))
+            return HP_ERR_INVALID_ARG;
+        cudaStream_t s = static_cast<cudaStream_t>(stream);
+        hp::Arena A(s);
+        hp::Level L;
+        hp::make_level(num_nodes, num_hedges, offsets, pins, src_counts, size, L, A);
+        uint32_t *err = A.get<uint32_t>(1);
+        long long *bg = A.get<long long>(1);
+        HPC(cudaMemsetAsync(err, 0, sizeof(uint32_t), s));
+        HPC(cudaMemsetAsync(bg, 0, sizeof(long long), s));
+        int32_t m = 0;
+        hp::RepDebug D{move_node, move_src, move_dst, reinterpret_cast<long long *>(move_gain), seq,
+                       reinterpret_cast<long long *>(gseq), bg, &m};
+        int32_t k = hp::refine_rep_debug(L, weights, num_parts, P, rho, second_half, A, err, D);
+        uint32_t e = hp::fetch<uint32_t>(err, s);
+        if (e) return hp::status_of(e);
+        if (num_moves) *num_moves = m;
+        if (applied) *applied = k;
+        if (best_gain) *best_gain = hp::fetch<long long>(bg, s);
         return HP_OK;
     });
 }

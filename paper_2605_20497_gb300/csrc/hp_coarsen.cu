@@ -619,13 +619,20 @@ __global__ void k_dp_down(DpCtx D, const int32_t *target, int32_t *mate, unsigne
     }
 }
 
+__global__ void k_sum_i32(const int32_t *x, int32_t n, unsigned long long *sum) {
+    unsigned long long loc = 0;
+    GRID_STRIDE(i, (int64_t)n) loc += (unsigned long long)x[i];
+    for (int o = 16; o > 0; o >>= 1) loc += __shfl_down_sync(0xffffffffu, loc, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(sum, loc);
+}
+
 CoarsenOut coarsen_level(Level &L, int32_t level, const int32_t *w, const Params &P, int32_t *mate, Arena &A,
-                         uint32_t *err_dev) {
+                         uint32_t *err_dev, int32_t *cand_out, uint64_t *score_out, cudaEvent_t *prop_events) {
     cudaStream_t s = A.stream();
     const int32_t n = L.n, pi = P.o.pi;
     CoarsenOut out;
     struct Box {
-        unsigned long long qsum, visits, pairs, iso;
+        unsigned long long qsum, visits, pairs, iso, nbrs;
         uint64_t cap;
     };
     Box *box = A.get<Box>(1);
@@ -668,10 +675,18 @@ CoarsenOut coarsen_level(Level &L, int32_t level, const int32_t *w, const Params
     C.cscore = cscore;
     C.nbcnt = L.nbnd;   // exact counts replace the bounds (used to size the next level)
     if (n > 0) {
+        if (prop_events) HPC(cudaEventRecord(prop_events[0], s));
         if (pi <= 4) run_proposal<4>(C, L, P, A, err_dev);
         else run_proposal<16>(C, L, P, A, err_dev);
+        if (prop_events) HPC(cudaEventRecord(prop_events[1], s));
+        k_sum_i32<<<grid_of(n, 256), 256, 0, s>>>(L.nbnd, n, &box->nbrs);
+        HP_LAUNCH_CHECK();
     }
     A.release(q);
+    if (cand_out && n > 0) {
+        HPC(cudaMemcpyAsync(cand_out, cand, sizeof(int32_t) * n * pi, cudaMemcpyDeviceToDevice, s));
+        HPC(cudaMemcpyAsync(score_out, cscore, sizeof(uint64_t) * n * pi, cudaMemcpyDeviceToDevice, s));
+    }
 
     // best-effort pairing of nodes with no valid neighbour (Sec. V-C)
     fill_i32(mate, n, -1, s);
@@ -753,6 +768,7 @@ CoarsenOut coarsen_level(Level &L, int32_t level, const int32_t *w, const Params
     out.pairs = (int64_t)(hb.pairs + hb.iso);
     out.iso_pairs = (int64_t)hb.iso;
     out.pin_visits = (int64_t)hb.visits;
+    out.neighbours = (int64_t)hb.nbrs;
     return out;
 }
 

@@ -169,6 +169,30 @@ uint32_t validate_and_build_level0(const int32_t *pins, const int32_t *offsets, 
     return hb.err;
 }
 
+void make_level(int32_t n, int32_t e, const int32_t *off, const int32_t *pins, const int32_t *nsrc,
+                const int32_t *size, Level &L, Arena &A) {
+    cudaStream_t s = A.stream();
+    L.n = n;
+    L.e = e;
+    L.off = A.get<int32_t>(e + 1);
+    HPC(cudaMemcpyAsync(L.off, off, sizeof(int32_t) * (e + 1), cudaMemcpyDeviceToDevice, s));
+    L.np = fetch<int32_t>(L.off + e, s);
+    L.pin = A.get<int32_t>(L.np);
+    if (L.np) HPC(cudaMemcpyAsync(L.pin, pins, sizeof(int32_t) * L.np, cudaMemcpyDeviceToDevice, s));
+    L.nsrc = A.get<int32_t>(e);
+    if (e) HPC(cudaMemcpyAsync(L.nsrc, nsrc, sizeof(int32_t) * e, cudaMemcpyDeviceToDevice, s));
+    L.size = A.get<int32_t>(n);
+    if (n) HPC(cudaMemcpyAsync(L.size, size, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s));
+    L.pedge = A.get<int32_t>(L.np);
+    if (e > 0) {
+        k_pin_edges<<<grid_of((int64_t)e * 32, 256), 256, 0, s>>>(L.off, e, L.pedge);
+        HP_LAUNCH_CHECK();
+    }
+    build_incidence(L, A);
+    L.nbnd = A.get<int32_t>(n);
+    fill_i32(L.nbnd, n, n > 0 ? n - 1 : 0, s);
+}
+
 // ---------------------------------------------------------------- contraction
 __global__ void k_rep_flags(const int32_t *mate, int32_t n, int32_t *isrep) {
     GRID_STRIDE(v, (int64_t)n) {

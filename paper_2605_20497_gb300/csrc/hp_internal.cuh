@@ -21,7 +21,10 @@ struct Error : std::runtime_error {
 
 void cuda_check(cudaError_t e, const char *what, const char *file, int line);
 #define HPC(x) ::hp::cuda_check((x), #x, __FILE__, __LINE__)
-#define HP_LAUNCH_CHECK() ::hp::cuda_check(cudaGetLastError(), "kernel launch", __FILE__, __LINE__)
+// every kernel launch is followed by this check, which also counts the launch
+extern thread_local int64_t t_launches;
+#define HP_LAUNCH_CHECK() \
+    (::hp::t_launches++, ::hp::cuda_check(cudaGetLastError(), "kernel launch", __FILE__, __LINE__))
 
 // bits of the device error word
 enum : uint32_t {
@@ -105,16 +108,33 @@ uint32_t validate_and_build_level0(const int32_t *pins, const int32_t *offsets, 
                                    const int32_t *src_counts, const int32_t *weights, const Params &P, Level &L,
                                    int32_t *w_out, Arena &A);
 void build_incidence(Level &L, Arena &A);
+// level graph from caller arrays (device): copies them and builds the incidence
+void make_level(int32_t n, int32_t e, const int32_t *off, const int32_t *pins, const int32_t *nsrc,
+                const int32_t *size, Level &L, Arena &A);
 void contract_level(const Level &L, const int32_t *mate, Level &C, Arena &A);
 
 // coarsening (hp_coarsen.cu)
 struct CoarsenOut {
-    int64_t pairs = 0, iso_pairs = 0, pin_visits = 0;
+    int64_t pairs = 0, iso_pairs = 0, pin_visits = 0, neighbours = 0;
 };
+// prop_events (optional): two events recorded around the proposal launches
 CoarsenOut coarsen_level(Level &L, int32_t level, const int32_t *w, const Params &P, int32_t *mate, Arena &A,
-                         uint32_t *err_dev);
+                         uint32_t *err_dev, int32_t *cand_out = nullptr, uint64_t *score_out = nullptr,
+                         cudaEvent_t *prop_events = nullptr);
 
 // refinement (hp_refine.cu)
+// optional copies of the intermediate results of one repetition (device
+// buffers of n entries; m and best_gain are host / device scalars)
+struct RepDebug {
+    int32_t *node, *src, *dst;   // proposed moves, sorted (p_s asc, gain desc, node asc)
+    long long *gain;
+    int32_t *seq;                // seq[k] = index (into the sorted moves) of the k-th move of the sequence
+    long long *gseq;             // in-sequence gain of the k-th move
+    long long *best_gain;        // device scalar
+    int32_t *m;                  // host: number of moves
+};
+int32_t refine_rep_debug(const Level &L, const int32_t *w, int32_t nparts, const Params &P, int32_t *rho,
+                         int second_half, Arena &A, uint32_t *err_dev, const RepDebug &dbg);
 struct RefineOut {
     int64_t moves = 0;
     int32_t reps = 0;

@@ -10,6 +10,8 @@
 
 namespace hp {
 
+thread_local int64_t t_launches = 0;
+
 // ================================================================ errors
 void cuda_check(cudaError_t e, const char *what, const char *file, int line) {
     if (e == cudaSuccess) return;

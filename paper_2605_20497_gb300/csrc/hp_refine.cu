@@ -920,7 +920,8 @@ __global__ void k_apply(const int32_t *seqmove, const int32_t *node, const int32
 
 // ---------------------------------------------------------------- one repetition
 static int32_t refine_rep(const Level &L, const int32_t *w, int32_t nparts, const Params &P, int32_t *rho,
-                          int second_half, int32_t max_e, const long long *wns, Arena &A, uint32_t *err_dev) {
+                          int second_half, int32_t max_e, const long long *wns, Arena &A, uint32_t *err_dev,
+                          const RepDebug *dbg = nullptr) {
     cudaStream_t s = A.stream();
     const int32_t n = L.n;
     // pins(p,e), D(p), saving(v)
@@ -980,6 +981,7 @@ static int32_t refine_rep(const Level &L, const int32_t *w, int32_t nparts, cons
         A.release(ovf);
     }
     const int32_t m = fetch<int32_t>(M.count, s);
+    if (dbg) *dbg->m = m;
     A.release(cl);
     A.release(saving);
     int32_t applied = 0;
@@ -1017,6 +1019,12 @@ static int32_t refine_rep(const Level &L, const int32_t *w, int32_t nparts, cons
         HP_LAUNCH_CHECK();
         A.release(keys);
         A.release(idx);
+        if (dbg) {
+            HPC(cudaMemcpyAsync(dbg->node, S.node, sizeof(int32_t) * m, cudaMemcpyDeviceToDevice, s));
+            HPC(cudaMemcpyAsync(dbg->src, S.src, sizeof(int32_t) * m, cudaMemcpyDeviceToDevice, s));
+            HPC(cudaMemcpyAsync(dbg->dst, S.dst, sizeof(int32_t) * m, cudaMemcpyDeviceToDevice, s));
+            HPC(cudaMemcpyAsync(dbg->gain, S.gain, sizeof(long long) * m, cudaMemcpyDeviceToDevice, s));
+        }
         A.release(gm);
 
         // chaining (Sec. VI-C)
@@ -1127,6 +1135,7 @@ static int32_t refine_rep(const Level &L, const int32_t *w, int32_t nparts, cons
         int32_t *seqmove = A.get<int32_t>(m);
         k_seq_pos<<<grid_of(m, 256), 256, 0, s>>>(Q.chain, Q.pos, cstart, m, seqpos, seqmove);
         HP_LAUNCH_CHECK();
+        if (dbg) HPC(cudaMemcpyAsync(dbg->seq, seqmove, sizeof(int32_t) * m, cudaMemcpyDeviceToDevice, s));
         A.release(lens);
         A.release(starts);
         A.release(cstart);
@@ -1200,6 +1209,10 @@ static int32_t refine_rep(const Level &L, const int32_t *w, int32_t nparts, cons
         k_apply<<<grid_of(m, 256), 256, 0, s>>>(seqmove, S.node, S.dst, cnts + 7, rho);
         HP_LAUNCH_CHECK();
         applied = fetch<int32_t>(cnts + 7, s);
+        if (dbg) {
+            HPC(cudaMemcpyAsync(dbg->gseq, gseq, sizeof(long long) * m, cudaMemcpyDeviceToDevice, s));
+            HPC(cudaMemcpyAsync(dbg->best_gain, bgain, sizeof(long long), cudaMemcpyDeviceToDevice, s));
+        }
         A.release(vk);
         A.release(vi);
         A.release(vds);
@@ -1228,6 +1241,28 @@ static int32_t refine_rep(const Level &L, const int32_t *w, int32_t nparts, cons
     A.release(D0);
     A.release(psize);
     return applied;
+}
+
+int32_t refine_rep_debug(const Level &L, const int32_t *w, int32_t nparts, const Params &P, int32_t *rho,
+                         int second_half, Arena &A, uint32_t *err_dev, const RepDebug &dbg) {
+    cudaStream_t s = A.stream();
+    int32_t *maxe = A.get<int32_t>(1);
+    HPC(cudaMemsetAsync(maxe, 0, sizeof(int32_t), s));
+    if (L.e > 0) {
+        k_max_edge<<<grid_of(L.e, 256), 256, 0, s>>>(L.off, L.e, maxe);
+        HP_LAUNCH_CHECK();
+    }
+    const int32_t max_e = fetch<int32_t>(maxe, s);
+    long long *wns = A.get<long long>(std::max(L.n, 1));
+    if (L.n > 0) {
+        k_wns<<<grid_of(L.n, 256), 256, 0, s>>>(L.off, L.ioff, L.inc, w, L.n, wns);
+        HP_LAUNCH_CHECK();
+    }
+    *dbg.m = 0;
+    int32_t k = L.n > 0 ? refine_rep(L, w, nparts, P, rho, second_half, max_e, wns, A, err_dev, &dbg) : 0;
+    A.release(wns);
+    A.release(maxe);
+    return k;
 }
 
 RefineOut refine_level(const Level &L, const int32_t *w, int32_t nparts, const Params &P, int32_t *rho, Arena &A,

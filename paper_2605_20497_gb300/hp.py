@@ -26,7 +26,8 @@ HP_ERR_OOM, HP_ERR_CUDA, HP_ERR_TIMEOUT, HP_ERR_INTERNAL = 4, 5, 6, 7
 HP_COUNT_INBOUND, HP_COUNT_INCIDENT = 0, 1
 
 EXPORTS = ("hp_default_options", "hp_partition", "hp_partition_ex", "hp_partition_host", "hp_set_allocator",
-           "hp_status_string", "hp_last_error", "hp_connectivity")
+           "hp_status_string", "hp_last_error", "hp_connectivity", "hp_debug_coarsen_level",
+           "hp_debug_refine_rep")
 
 
 class hp_options(ctypes.Structure):
@@ -39,7 +40,9 @@ class hp_stats(ctypes.Structure):
                 ("max_part_size", ctypes.c_int32), ("max_part_distinct", ctypes.c_int32),
                 ("violations", ctypes.c_int32), ("levels", ctypes.c_int32), ("reserved0", ctypes.c_int32),
                 ("moves_applied", ctypes.c_int64), ("pin_visits", ctypes.c_int64), ("ms_total", ctypes.c_double),
-                ("ms_coarsen", ctypes.c_double), ("ms_refine", ctypes.c_double)]
+                ("ms_coarsen", ctypes.c_double), ("ms_refine", ctypes.c_double),
+                ("kernel_launches", ctypes.c_int64), ("l0_pin_visits", ctypes.c_int64),
+                ("l0_neighbours", ctypes.c_int64), ("ms_propose_l0", ctypes.c_double)]
 
 
 class hp_level_trace(ctypes.Structure):
@@ -77,6 +80,14 @@ def load() -> ctypes.CDLL:
         L.hp_connectivity.argtypes = [P, P, I32, P, P, I32, I32, ctypes.POINTER(ctypes.c_int64),
                                       ctypes.POINTER(ctypes.c_int64), P]
         L.hp_connectivity.restype = ctypes.c_int
+        L.hp_debug_coarsen_level.argtypes = [I32, I32, P, P, P, P, P, I32, I32, U64, I32, ctypes.POINTER(hp_options),
+                                             P, P, P, ctypes.POINTER(ctypes.c_int64), P]
+        L.hp_debug_coarsen_level.restype = ctypes.c_int
+        L.hp_debug_refine_rep.argtypes = [I32, I32, P, P, P, P, P, P, I32, I32, I32, I32,
+                                          ctypes.POINTER(hp_options), P, P, P, P, P, P,
+                                          ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
+                                          ctypes.POINTER(ctypes.c_int64), P]
+        L.hp_debug_refine_rep.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -111,6 +122,26 @@ def hp_connectivity(pins, offsets, num_hedges, weights, part, num_nodes, num_par
     st = load().hp_connectivity(pins, offsets, num_hedges, weights, part, num_nodes, num_parts, ctypes.byref(c),
                                 ctypes.byref(cn), stream)
     return st, int(c.value), int(cn.value)
+
+
+def hp_debug_coarsen_level(num_nodes, num_hedges, offsets, pins, src_counts, weights, size, omega, delta, seed,
+                           level, opt, cand_out, score_out, mate_out, stream=0):
+    pairs = ctypes.c_int64(0)
+    st = load().hp_debug_coarsen_level(num_nodes, num_hedges, offsets, pins, src_counts, weights, size, omega,
+                                       delta, ctypes.c_uint64(seed), level, opt, cand_out, score_out, mate_out,
+                                       ctypes.byref(pairs), stream)
+    return st, int(pairs.value)
+
+
+def hp_debug_refine_rep(num_nodes, num_hedges, offsets, pins, src_counts, weights, size, rho, num_parts,
+                        second_half, omega, delta, opt, move_node, move_src, move_dst, move_gain, seq, gseq,
+                        stream=0):
+    m, k, bg = ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_int64(0)
+    st = load().hp_debug_refine_rep(num_nodes, num_hedges, offsets, pins, src_counts, weights, size, rho,
+                                    num_parts, second_half, omega, delta, opt, move_node, move_src, move_dst,
+                                    move_gain, seq, gseq, ctypes.byref(m), ctypes.byref(k), ctypes.byref(bg),
+                                    stream)
+    return st, int(m.value), int(k.value), int(bg.value)
 
 
 def hp_status_string(status: int) -> str:
