@@ -113,11 +113,14 @@ static hp_status run(const int32_t *pins, const int32_t *offsets, int32_t e, int
     }
     uint32_t *err_dev = A.get<uint32_t>(1);
     HPC(cudaMemsetAsync(err_dev, 0, sizeof(uint32_t), s));
+    const int32_t max_e0 = max_edge_size(lv[0], A);
 
     // ---- coarsening (Sec. V)
     const int64_t target_n = ((int64_t)n + omega - 1) / omega;
     int32_t L = 0;
     bool prop0_timed = false;
+    CoarsenWs *CW = coarsen_workspace(n, e, P, A);
+    int32_t *mate = A.get<int32_t>(n);
     for (;;) {
         hp_level_trace t;
         std::memset(&t, 0, sizeof t);
@@ -127,29 +130,30 @@ static hp_status run(const int32_t *pins, const int32_t *offsets, int32_t e, int
             tr.push_back(t);
             break;
         }
-        int32_t *mate = A.get<int32_t>(lv[L].n);
-        CoarsenOut co = coarsen_level(lv[L], L, w, P, mate, A, err_dev, nullptr, nullptr, L == 0 ? T.p : nullptr);
-        st.pin_visits += co.pin_visits;
+        coarsen_level(lv[L], L, w, P, mate, *CW, A, err_dev, nullptr, nullptr, L == 0 ? T.p : nullptr);
+        lv.emplace_back();
+        LevelBox hb;
+        const bool go = contract_level(lv[L], mate, coarsen_box(CW), &hb, lv[L + 1], A);
+        st.pin_visits += (int64_t)hb.visits;
         if (L == 0) {
             prop0_timed = true;
-            st.l0_pin_visits = co.pin_visits;
-            st.l0_neighbours = co.neighbours;
+            st.l0_pin_visits = (int64_t)hb.visits;
+            st.l0_neighbours = (int64_t)hb.nbrs;
         }
-        t.pairs = (int32_t)co.pairs;
-        t.iso_pairs = (int32_t)co.iso_pairs;
+        t.pairs = (int32_t)(hb.pairs + hb.iso);
+        t.iso_pairs = (int32_t)hb.iso;
         tr.push_back(t);
-        if (co.pairs == 0) {
-            A.release(mate);
+        if (!go) {
+            lv.pop_back();
             break;
         }
-        lv.emplace_back();
-        contract_level(lv[L], mate, lv[L + 1], A);
-        A.release(mate);
         A.release(lv[L].nbnd);
         A.release(lv[L].pedge);
         lv[L].nbnd = lv[L].pedge = nullptr;
         L++;
     }
+    coarsen_workspace_free(CW, A);
+    A.release(mate);
     HPC(cudaEventRecord(T.b, s));
 
     // ---- refinement (Sec. VI): coarsest clusters are the initial parts
@@ -157,6 +161,7 @@ static hp_status run(const int32_t *pins, const int32_t *offsets, int32_t e, int
     int32_t *rho = A.get<int32_t>(nparts);
     iota_i32(rho, nparts, s);
     int64_t *obj = A.get<int64_t>(2);
+    LevelWs *RW = refine_workspace(lv[0].n, lv[0].np, lv[0].e, nparts, max_e0, P, A);
     for (int32_t l = L; l >= 0; l--) {
         Level &g = lv[l];
         if (l < L) {
@@ -167,11 +172,11 @@ static hp_status run(const int32_t *pins, const int32_t *offsets, int32_t e, int
             rho = r;
             // the coarser level is no longer needed
             Level &c = lv[l + 1];
-            for (int32_t *p : {c.off, c.pin, c.pedge, c.nsrc, c.size, c.ioff, c.inc, c.nin, c.gamma, c.nbnd})
+            for (int32_t *p : {c.off, c.pin, c.pedge, c.nsrc, c.size, c.ioff, c.inc, c.inode, c.nin, c.gamma, c.nbnd})
                 A.release(p);
             c = Level();
         }
-        RefineOut ro = refine_level(g, w, nparts, P, rho, A, err_dev);
+        RefineOut ro = refine_level(g, w, P, rho, RW, A, err_dev);
         st.moves_applied += ro.moves;
         tr[l].reps = ro.reps;
         tr[l].moves = ro.moves;
@@ -180,6 +185,7 @@ static hp_status run(const int32_t *pins, const int32_t *offsets, int32_t e, int
             tr[l].conn = fetch<int64_t>(obj, s);
         }
     }
+    refine_workspace_free(RW, A);
     HPC(cudaEventRecord(T.c, s));
 
     // ---- compact part ids (ascending internal id) and statistics
@@ -383,10 +389,14 @@ hp_status hp_debug_coarsen_level(int32_t num_nodes, int32_t num_hedges, const in
         hp::make_level(num_nodes, num_hedges, offsets, pins, src_counts, size, L, A);
         uint32_t *err = A.get<uint32_t>(1);
         HPC(cudaMemsetAsync(err, 0, sizeof(uint32_t), s));
-        hp::CoarsenOut co = hp::coarsen_level(L, level, weights, P, mate_out, A, err, cand_out, score_out);
+        hp::CoarsenWs *CW = hp::coarsen_workspace(num_nodes, num_hedges, P, A);
+        hp::coarsen_level(L, level, weights, P, mate_out, *CW, A, err, cand_out, score_out);
+        hp::LevelBox hb;
+        hp::fetch_bytes(&hb, hp::coarsen_box(CW), sizeof hb, s);
+        hp::coarsen_workspace_free(CW, A);
         uint32_t e = hp::fetch<uint32_t>(err, s);
         if (e) return hp::status_of(e);
-        if (pairs_out) *pairs_out = co.pairs;
+        if (pairs_out) *pairs_out = (int64_t)(hb.pairs + hb.iso);
         return HP_OK;
     });
 }
@@ -412,6 +422,7 @@ hp_status hp_debug_refine_rep(int32_t num_nodes, int32_t num_hedges, const int32
         hp::Arena A(s);
         hp::Level L;
         hp::make_level(num_nodes, num_hedges, offsets, pins, src_counts, size, L, A);
+        P.wsum = (int64_t)num_hedges * 65536;
         uint32_t *err = A.get<uint32_t>(1);
         long long *bg = A.get<long long>(1);
         HPC(cudaMemsetAsync(err, 0, sizeof(uint32_t), s));

@@ -76,24 +76,44 @@ __global__ void k_level_cap(const unsigned long long *sum, int32_t e, int32_t pe
     *cap = e > 0 ? (uint64_t)((*sum / (unsigned long long)e) * (unsigned long long)permille / 1000ull) : 0ull;
 }
 
-// per node: bound on |N(v)| and the pin visits of its traversal
-__global__ void k_node_bounds(const int32_t *off, const int32_t *ioff, const int32_t *inc, int32_t n,
-                              int32_t *bound, unsigned long long *visits) {
+// per incidence entry (e, v): sums over I(v) of |e| - 1 (bound on |N(v)|)
+// and |e| (pins the traversal of v visits), reduced per run of equal v
+// inside a warp, so hub nodes with huge incidence lists spread over threads
+__global__ void k_node_sums(const int32_t *off, const int32_t *inc, const int32_t *inode, int64_t np,
+                            long long *nsum, long long *vis, unsigned long long *visits) {
+    const int lane = threadIdx.x & 31;
+    const int64_t wbase = ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5) << 5;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     unsigned long long loc = 0;
-    GRID_STRIDE(v, (int64_t)n) {
-        int64_t s = 0;
-        for (int32_t t = ioff[v]; t < ioff[v + 1]; t++) {
-            int32_t e = inc[t];
-            int32_t sz = off[e + 1] - off[e];
-            s += sz - 1;
+    for (int64_t base = wbase; base < np; base += stride) {
+        const int64_t t = base + lane;
+        const bool valid = t < np;
+        const int32_t v = valid ? inode[t] : -1 - lane;
+        long long sz = 0;
+        if (valid) {
+            const int32_t e = inc[t];
+            sz = off[e + 1] - off[e];
             loc += (unsigned long long)sz;
         }
-        int64_t b = bound[v];
-        if (s < b) b = s;
+        long long a = valid ? sz - 1 : 0, b = sz;
+        bool tail = warp_run_sum(v, a);
+        warp_run_sum(v, b);
+        if (valid && tail) {
+            atomicAdd((unsigned long long *)&nsum[v], (unsigned long long)a);
+            atomicAdd((unsigned long long *)&vis[v], (unsigned long long)b);
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) loc += __shfl_down_sync(0xffffffffu, loc, o);
+    if (lane == 0) atomicAdd(visits, loc);
+}
+
+__global__ void k_node_bounds(const long long *nsum, int32_t n, int32_t *bound) {
+    GRID_STRIDE(v, (int64_t)n) {
+        long long b = bound[v];
+        if (nsum[v] < b) b = nsum[v];
         if (n - 1 < b) b = n - 1;
         bound[v] = (int32_t)b;
     }
-    atomicAdd(visits, loc);
 }
 
 // ---------------------------------------------------------------- top-Pi selection
@@ -184,31 +204,57 @@ __device__ __forceinline__ int32_t block_sum_i32(int32_t x, int32_t *s_tmp) {
 }
 
 // ---------------------------------------------------------------- dense table
-// eta[m], inter[m] for every node of the level in shared memory.
-template <int PIMAX> __global__ void __launch_bounds__(PT) k_propose_dense(PropCtx C) {
+// eta[m], inter[m] for every node of the level in shared memory (levels of at
+// most DENSE_N nodes, nodes with large neighbourhoods).
+template <int PIMAX>
+__global__ void __launch_bounds__(PT) k_propose_dense(PropCtx C, const int32_t *list, const int32_t *count_p) {
     extern __shared__ __align__(16) unsigned char smem[];
     unsigned long long *eta = reinterpret_cast<unsigned long long *>(smem);
     uint32_t *inter = reinterpret_cast<uint32_t *>(eta + C.n);
     __shared__ Cand s_red[16 + 8];
     __shared__ int32_t s_tmp[32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = PT / 32;
+    const int32_t count = *count_p;
+    if (count == 0) return;
     for (int32_t i = threadIdx.x; i < C.n; i += PT) {
         eta[i] = 0;
         inter[i] = 0;
     }
     __syncthreads();
     const uint64_t cap = *C.cap;
-    for (int32_t v = blockIdx.x; v < C.n; v += gridDim.x) {
+    for (int32_t k = blockIdx.x; k < count; k += gridDim.x) {
+        const int32_t v = list[k];
         const int32_t i0 = C.ioff[v], deg = C.ioff[v + 1] - i0, nin_v = C.nin[v];
-        for (int32_t t = wid; t < deg; t += nw) {
-            int32_t e = C.inc[i0 + t];
-            int32_t a = C.off[e], b = C.off[e + 1];
-            if (b - a < 2) continue;
-            int32_t dst0 = a + C.nsrc[e];
-            unsigned long long qe = C.q[e];
-            bool vin = t < nin_v;
+        {   // hyperedges of 2..32 pins: one per thread, repeated neighbours combined in registers
+            RegCache<4> rc;
+            rc.init();
+            auto flush = [&](int32_t m, unsigned long long eq, uint32_t ic) {
+                atomicAdd(&eta[m], eq);
+                if (ic) atomicAdd(&inter[m], ic);
+            };
+            for (int32_t t = threadIdx.x; t < deg; t += PT) {
+                const int32_t e = C.inc[i0 + t];
+                const int32_t a = C.off[e], b = C.off[e + 1];
+                if (b - a < 2 || b - a > 32) continue;
+                const int32_t dst0 = a + C.nsrc[e];
+                const unsigned long long qe = C.q[e];
+                const bool vin = t < nin_v;
+                for (int32_t j = a; j < b; j++) {
+                    const int32_t m = C.pin[j];
+                    if (m != v) rc.add(m, qe, (vin && j >= dst0) ? 1u : 0u, flush);
+                }
+            }
+            rc.drain(flush);
+        }
+        for (int32_t t = wid; t < deg; t += nw) {   // larger hyperedges: lanes over pins
+            const int32_t e = C.inc[i0 + t];
+            const int32_t a = C.off[e], b = C.off[e + 1];
+            if (b - a <= 32) continue;
+            const int32_t dst0 = a + C.nsrc[e];
+            const unsigned long long qe = C.q[e];
+            const bool vin = t < nin_v;
             for (int32_t j = a + lane; j < b; j += 32) {
-                int32_t m = C.pin[j];
+                const int32_t m = C.pin[j];
                 if (m == v) continue;
                 atomicAdd(&eta[m], qe);
                 if (vin && j >= dst0) atomicAdd(&inter[m], 1u);
@@ -234,6 +280,127 @@ template <int PIMAX> __global__ void __launch_bounds__(PT) k_propose_dense(PropC
     }
 }
 
+// ---------------------------------------------------------------- warp per node
+// Nodes whose neighbourhood bound is at most half the per-warp table: one
+// warp per node, no block barriers.  Incident hyperedges of up to 32 pins are
+// spread over the lanes (one hyperedge per lane), larger ones lane per pin.
+constexpr int WP_T = 256;
+__device__ __forceinline__ uint32_t hslot_w(int32_t m, uint32_t mask) {
+    return ((uint32_t)m * 0x9E3779B1u) & mask;
+}
+__device__ __forceinline__ void warp_insert(int32_t *keys, unsigned long long *eta, uint32_t *inter, uint32_t mask,
+                                            uint32_t cap, int32_t m, unsigned long long qe, uint32_t ninter) {
+    uint32_t h = hslot_w(m, mask);
+    for (uint32_t probe = 0; probe < cap; probe++) {
+        int32_t k = ((volatile int32_t *)keys)[h];
+        if (k == -1) {
+            int32_t old = atomicCAS(&keys[h], -1, m);
+            k = old == -1 ? m : old;
+        }
+        if (k == m) {
+            atomicAdd(&eta[h], qe);
+            if (ninter) atomicAdd(&inter[h], ninter);
+            return;
+        }
+        h = (h + 1) & mask;
+    }
+}
+template <int PIMAX>
+__global__ void __launch_bounds__(WP_T) k_propose_warp(PropCtx C, const int32_t *list, const int32_t *count_p,
+                                                       uint32_t cap) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwb = WP_T / 32;
+    unsigned long long *eta = reinterpret_cast<unsigned long long *>(smem) + (size_t)wid * cap;
+    uint32_t *inter = reinterpret_cast<uint32_t *>(reinterpret_cast<unsigned long long *>(smem) + (size_t)nwb * cap) +
+                      (size_t)wid * cap;
+    int32_t *keys = reinterpret_cast<int32_t *>(reinterpret_cast<uint32_t *>(reinterpret_cast<unsigned long long *>(
+                                                    smem) + (size_t)nwb * cap) + (size_t)nwb * cap) +
+                    (size_t)wid * cap;
+    const int32_t count = *count_p;
+    if (count == 0) return;
+    const uint32_t mask = cap - 1;
+    for (uint32_t i = lane; i < cap; i += 32) {
+        keys[i] = -1;
+        eta[i] = 0;
+        inter[i] = 0;
+    }
+    __syncwarp();
+    const uint64_t capn = *C.cap;
+    const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t k = gw; k < count; k += nw) {
+        const int32_t v = list[k];
+        const int32_t i0 = C.ioff[v], deg = C.ioff[v + 1] - i0, nin_v = C.nin[v];
+        {   // hyperedges of 2..32 pins: one per lane, repeated neighbours combined in registers
+            RegCache<4> rc;
+            rc.init();
+            auto flush = [&](int32_t m, unsigned long long eq, uint32_t ic) {
+                warp_insert(keys, eta, inter, mask, cap, m, eq, ic);
+            };
+            for (int32_t t = lane; t < deg; t += 32) {
+                const int32_t e = C.inc[i0 + t];
+                const int32_t a = C.off[e], b = C.off[e + 1];
+                if (b - a < 2 || b - a > 32) continue;
+                const int32_t dst0 = a + C.nsrc[e];
+                const unsigned long long qe = C.q[e];
+                const bool vin = t < nin_v;
+                for (int32_t j = a; j < b; j++) {
+                    const int32_t m = C.pin[j];
+                    if (m != v) rc.add(m, qe, (vin && j >= dst0) ? 1u : 0u, flush);
+                }
+            }
+            rc.drain(flush);
+        }
+        // larger hyperedges: lanes over pins
+        for (int32_t t = 0; t < deg; t++) {
+            const int32_t e = C.inc[i0 + t];
+            const int32_t a = C.off[e], b = C.off[e + 1];
+            if (b - a <= 32) continue;
+            const int32_t dst0 = a + C.nsrc[e];
+            const unsigned long long qe = C.q[e];
+            const bool vin = t < nin_v;
+            for (int32_t j = a + lane; j < b; j += 32) {
+                const int32_t m = C.pin[j];
+                if (m != v) warp_insert(keys, eta, inter, mask, cap, m, qe, (vin && j >= dst0) ? 1u : 0u);
+            }
+        }
+        __syncwarp();
+        TopList<PIMAX> tl;
+        tl.init();
+        int32_t cnt = 0;
+        for (uint32_t h = lane; h < cap; h += 32) {
+            const int32_t m = keys[h];
+            if (m >= 0) {
+                cnt++;
+                if (pair_valid(C, v, m, (int32_t)inter[h])) tl.push(Cand{eta[h] + pair_noise(C.level_key, v, m, capn), m});
+                keys[h] = -1;
+                eta[h] = 0;
+                inter[h] = 0;
+            }
+        }
+        __syncwarp();
+        for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+        if (lane == 0) C.nbcnt[v] = cnt;
+        for (int r = 0; r < C.pi; r++) {
+            Cand best = tl.c[0];
+            int owner = lane;
+            for (int o = 16; o > 0; o >>= 1) {
+                Cand ob{__shfl_xor_sync(0xffffffffu, best.eta, o), __shfl_xor_sync(0xffffffffu, best.id, o)};
+                int oo = __shfl_xor_sync(0xffffffffu, owner, o);
+                if (cand_gt(ob, best)) {
+                    best = ob;
+                    owner = oo;
+                }
+            }
+            if (lane == 0) {
+                C.cand[(int64_t)v * C.pi + r] = best.id;
+                C.cscore[(int64_t)v * C.pi + r] = best.id >= 0 ? best.eta : 0;
+            }
+            if (best.id >= 0 && lane == owner) tl.pop();
+        }
+    }
+}
+
 // ---------------------------------------------------------------- hashed table
 __device__ __forceinline__ uint32_t hslot(int32_t m, uint32_t mask) {
     return ((uint32_t)m * 0x9E3779B1u) & mask;
@@ -249,36 +416,60 @@ __device__ void propose_hashed_node(const PropCtx &C, int32_t v, int32_t *keys, 
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const uint32_t mask = cap - 1;
     const int32_t i0 = C.ioff[v], deg = C.ioff[v + 1] - i0, nin_v = C.nin[v];
+    auto insert_n = [&](int32_t m, unsigned long long qe, uint32_t ninter) {
+        uint32_t h = hslot(m, mask);
+        for (uint32_t probe = 0; probe < cap; probe++) {
+            int32_t k = ((volatile int32_t *)keys)[h];
+            if (k == -1) {
+                int32_t old = atomicCAS(&keys[h], -1, m);
+                if (old == -1) {
+                    if ((uint32_t)atomicAdd(s_cnt, 1) + 1 > limit) *(volatile int *)s_flag = 1;
+                    k = m;
+                } else {
+                    k = old;
+                }
+            }
+            if (k == m) {
+                atomicAdd(&eta[h], qe);
+                if (ninter) atomicAdd(&inter[h], ninter);
+                return;
+            }
+            h = (h + 1) & mask;
+        }
+    };
+    auto insert = [&](int32_t m, unsigned long long qe, bool add_inter) { insert_n(m, qe, add_inter ? 1u : 0u); };
+    // hyperedges of 2..32 pins: one per thread, repeated neighbours combined in registers
+    {
+        RegCache<4> rc;
+        rc.init();
+        auto flush = [&](int32_t m, unsigned long long eq, uint32_t ic) { insert_n(m, eq, ic); };
+        for (int32_t t = threadIdx.x; t < deg; t += blockDim.x) {
+            if (*(volatile int *)s_flag) break;
+            const int32_t e = C.inc[i0 + t];
+            const int32_t a = C.off[e], b = C.off[e + 1];
+            if (b - a < 2 || b - a > 32) continue;
+            const int32_t dst0 = a + C.nsrc[e];
+            const unsigned long long qe = C.q[e];
+            const bool vin = t < nin_v;
+            for (int32_t j = a; j < b; j++) {
+                const int32_t m = C.pin[j];
+                if (m != v) rc.add(m, qe, (vin && j >= dst0) ? 1u : 0u, flush);
+            }
+        }
+        rc.drain(flush);
+    }
+    // larger hyperedges: a warp each, lanes over pins
     for (int32_t t = wid; t < deg; t += nw) {
         if (*(volatile int *)s_flag) break;
-        int32_t e = C.inc[i0 + t];
-        int32_t a = C.off[e], b = C.off[e + 1];
-        if (b - a < 2) continue;
-        int32_t dst0 = a + C.nsrc[e];
-        unsigned long long qe = C.q[e];
-        bool vin = t < nin_v;
+        const int32_t e = C.inc[i0 + t];
+        const int32_t a = C.off[e], b = C.off[e + 1];
+        if (b - a <= 32) continue;
+        const int32_t dst0 = a + C.nsrc[e];
+        const unsigned long long qe = C.q[e];
+        const bool vin = t < nin_v;
         for (int32_t j = a + lane; j < b; j += 32) {
-            int32_t m = C.pin[j];
-            if (m == v) continue;
-            uint32_t h = hslot(m, mask);
-            for (uint32_t probe = 0; probe < cap; probe++) {
-                int32_t k = ((volatile int32_t *)keys)[h];
-                if (k == -1) {
-                    int32_t old = atomicCAS(&keys[h], -1, m);
-                    if (old == -1) {
-                        if ((uint32_t)atomicAdd(s_cnt, 1) + 1 > limit) *(volatile int *)s_flag = 1;
-                        k = m;
-                    } else {
-                        k = old;
-                    }
-                }
-                if (k == m) {
-                    atomicAdd(&eta[h], qe);
-                    if (vin && j >= dst0) atomicAdd(&inter[h], 1u);
-                    break;
-                }
-                h = (h + 1) & mask;
-            }
+            const int32_t m = C.pin[j];
+            if (m != v) insert(m, qe, vin && j >= dst0);
         }
     }
     __syncthreads();
@@ -319,8 +510,8 @@ __device__ void propose_hashed_node(const PropCtx &C, int32_t v, int32_t *keys, 
 }
 
 template <int PIMAX>
-__global__ void __launch_bounds__(PT) k_propose_smem(PropCtx C, const int32_t *list, int32_t count, uint32_t cap,
-                                                     uint32_t limit, int32_t *ovf, int32_t *ovf_n) {
+__global__ void __launch_bounds__(PT) k_propose_smem(PropCtx C, const int32_t *list, const int32_t *count_p,
+                                                     uint32_t cap, uint32_t limit, int32_t *ovf, int32_t *ovf_n) {
     extern __shared__ __align__(16) unsigned char smem[];
     unsigned long long *eta = reinterpret_cast<unsigned long long *>(smem);
     uint32_t *inter = reinterpret_cast<uint32_t *>(eta + cap);
@@ -329,6 +520,8 @@ __global__ void __launch_bounds__(PT) k_propose_smem(PropCtx C, const int32_t *l
     __shared__ int32_t s_tmp[32];
     __shared__ int s_flag;
     __shared__ int32_t s_cnt;
+    const int32_t count = *count_p;
+    if (count == 0) return;
     for (uint32_t i = threadIdx.x; i < cap; i += PT) {
         keys[i] = -1;
         eta[i] = 0;
@@ -344,126 +537,100 @@ __global__ void __launch_bounds__(PT) k_propose_smem(PropCtx C, const int32_t *l
                                    s_tmp);
 }
 
-// one CTA per node, table of capacity gcap[k] at global offset goff[k]
+// one CTA region of gcap slots in global memory per CTA (clean on entry and
+// left clean); gcap >= 2 * (nodes of the level) so no node overflows it
 template <int PIMAX>
-__global__ void __launch_bounds__(PT) k_propose_global(PropCtx C, const int32_t *list, int32_t count,
-                                                       const int64_t *goff, const int32_t *gcap, int32_t *gkeys,
-                                                       unsigned long long *geta, uint32_t *ginter, int32_t *err_list,
-                                                       int32_t *err_n) {
+__global__ void __launch_bounds__(PT) k_propose_global(PropCtx C, const int32_t *list, const int32_t *count_p,
+                                                       uint32_t gcap, int32_t *gkeys, unsigned long long *geta,
+                                                       uint32_t *ginter, int32_t *err_list, int32_t *err_n) {
     __shared__ Cand s_red[16 + 8];
     __shared__ int32_t s_tmp[32];
     __shared__ int s_flag;
     __shared__ int32_t s_cnt;
-    for (int32_t k = blockIdx.x; k < count; k += gridDim.x) {
-        if (threadIdx.x == 0) {
-            s_flag = 0;
-            s_cnt = 0;
-        }
-        __syncthreads();
-        int64_t o = goff[k];
-        uint32_t cap = (uint32_t)gcap[k];
-        propose_hashed_node<PIMAX>(C, list[k], gkeys + o, geta + o, ginter + o, cap, cap - 1, err_list, err_n,
-                                   &s_flag, &s_cnt, s_red, s_tmp);
-        __syncthreads();
+    const int32_t count = *count_p;
+    if (count == 0) return;
+    const int64_t o = (int64_t)blockIdx.x * gcap;
+    if (threadIdx.x == 0) {
+        s_flag = 0;
+        s_cnt = 0;
     }
+    __syncthreads();
+    for (int32_t k = blockIdx.x; k < count; k += gridDim.x)
+        propose_hashed_node<PIMAX>(C, list[k], gkeys + o, geta + o, ginter + o, gcap, gcap - 1, err_list, err_n,
+                                   &s_flag, &s_cnt, s_red, s_tmp);
 }
 
 // ---------------------------------------------------------------- node tiers
-__global__ void k_tiers(const int32_t *bound, int32_t n, uint32_t small_limit, int32_t *lA, int32_t *nA, int32_t *lB,
-                        int32_t *nB) {
+// warp tier: small neighbourhood bound and little traversal work
+constexpr long long WARP_VISITS = 4096;
+__global__ void k_tiers(const int32_t *bound, const long long *vis, int32_t n, uint32_t warp_limit, int32_t *lW,
+                        int32_t *lB, int32_t *cnt) {
     GRID_STRIDE(v, (int64_t)n) {
-        if ((uint32_t)bound[v] <= small_limit) lA[atomicAdd(nA, 1)] = (int32_t)v;
-        else lB[atomicAdd(nB, 1)] = (int32_t)v;
+        if ((uint32_t)bound[v] <= warp_limit && vis[v] <= WARP_VISITS) lW[atomicAdd(&cnt[0], 1)] = (int32_t)v;
+        else lB[atomicAdd(&cnt[1], 1)] = (int32_t)v;
     }
 }
 
-__global__ void k_global_caps(const int32_t *list, int32_t count, const int32_t *bound, int32_t *gcap,
-                              int64_t *gsz) {
-    GRID_STRIDE(k, (int64_t)count) {
-        uint32_t b = (uint32_t)bound[list[k]];
-        uint32_t c = 64;
-        while (c < 2u * b + 2u && c < (1u << 30)) c <<= 1;
-        gcap[k] = (int32_t)c;
-        gsz[k] = c;
-    }
-}
-
-static size_t table_bytes(uint32_t cap) { return (size_t)cap * 16; }
+// Per-call coarsening workspace (sized for level 0, reused by every level).
+struct CoarsenWs {
+    int32_t cn, ce, pi;
+    uint64_t *q;
+    int32_t *cand;
+    uint64_t *cscore;
+    int32_t *lW, *lB, *lC, *lG, *cnt;   // cnt: 0 W, 1 B, 2 C, 3 G, 4 global errors
+    long long *nsum, *vis;             // per node: sum of (|e|-1), sum of |e| over I(v)
+    uint32_t gcap;
+    int gnb;
+    int32_t *gkeys;
+    unsigned long long *geta;
+    uint32_t *ginter;
+    // best-effort pairing and matching
+    int32_t *flag, *pos, *target, *ccount, *coff, *fillpos, *kids, *best;
+    uint32_t *ikeys, *iids;
+    uint64_t *score;
+    long long *ss0, *ss10, *sum0;
+    LevelBox *box;
+};
 
 template <int PIMAX>
-static void run_proposal(const PropCtx &C, Level &L, const Params &P, Arena &A, uint32_t *err_dev) {
+static void run_proposal(const PropCtx &C, Level &L, const Params &P, CoarsenWs &W, Arena &A) {
     cudaStream_t s = A.stream();
     const int sms = num_sms();
-    int32_t dbg = P.o.debug_table_cap;
+    const int32_t dbg = P.o.debug_table_cap;
+    const uint32_t wcap = dbg > 0 ? std::min<uint32_t>(512, (uint32_t)dbg) : 512;
+    HPC(cudaMemsetAsync(W.cnt, 0, 8 * sizeof(int32_t), s));
+    k_tiers<<<grid_of(C.n, 256), 256, 0, s>>>(L.nbnd, W.vis, C.n, wcap / 2, W.lW, W.lB, W.cnt);
+    HP_LAUNCH_CHECK();
+    {
+        size_t sm = (size_t)wcap * 16 * (WP_T / 32);
+        int occ = prepare_kernel((const void *)k_propose_warp<PIMAX>, WP_T, sm);
+        int grid = (int)std::min<int64_t>(cdiv(C.n, WP_T / 32), (int64_t)sms * occ);
+        k_propose_warp<PIMAX><<<std::max(grid, 1), WP_T, sm, s>>>(C, W.lW, W.cnt + 0, wcap);
+        HP_LAUNCH_CHECK();
+    }
     if (C.n <= DENSE_N && dbg == 0) {
         size_t sm = (size_t)C.n * 12;
-        HPC(cudaFuncSetAttribute(k_propose_dense<PIMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-        int occ = 0;
-        HPC(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_propose_dense<PIMAX>, PT, sm));
-        int grid = std::max(1, std::min<int>(C.n, sms * std::max(occ, 1)));
-        k_propose_dense<PIMAX><<<grid, PT, sm, s>>>(C);
+        int occ = prepare_kernel((const void *)k_propose_dense<PIMAX>, PT, sm);
+        int grid = std::max(1, std::min<int>(C.n, sms * occ));
+        k_propose_dense<PIMAX><<<grid, PT, sm, s>>>(C, W.lB, W.cnt + 1);
         HP_LAUNCH_CHECK();
         return;
     }
-    // tiered hashed tables
-    uint32_t capA = 512, capB = 4096, capC = 8192;
-    if (dbg > 0) capA = capB = capC = (uint32_t)dbg;
-    int32_t *cnts = A.get<int32_t>(8);
-    HPC(cudaMemsetAsync(cnts, 0, 8 * sizeof(int32_t), s));
-    int32_t *lA = A.get<int32_t>(C.n), *lB = A.get<int32_t>(C.n), *lC = A.get<int32_t>(C.n), *lG = A.get<int32_t>(C.n);
-    k_tiers<<<grid_of(C.n, 256), 256, 0, s>>>(L.nbnd, C.n, capA / 2, lA, cnts + 0, lB, cnts + 1);
-    HP_LAUNCH_CHECK();
-    int32_t hc[8];
-    fetch_bytes(hc, cnts, sizeof hc, s);
-    auto launch_smem = [&](const int32_t *list, int32_t count, uint32_t cap, int32_t *ovf, int32_t *ovf_n) {
-        if (count <= 0) return;
-        size_t sm = table_bytes(cap);
-        HPC(cudaFuncSetAttribute(k_propose_smem<PIMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-        int occ = 0;
-        HPC(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_propose_smem<PIMAX>, PT, sm));
-        int grid = std::max(1, std::min<int>(count, sms * std::max(occ, 1)));
-        k_propose_smem<PIMAX><<<grid, PT, sm, s>>>(C, list, count, cap, cap * 3 / 4, ovf, ovf_n);
+    uint32_t capB = 4096, capC = 8192;
+    if (dbg > 0) capB = capC = (uint32_t)dbg;
+    auto launch_smem = [&](const int32_t *list, const int32_t *count_p, uint32_t cap, int32_t *ovf, int32_t *ovf_n) {
+        size_t sm = (size_t)cap * 16;
+        int occ = prepare_kernel((const void *)k_propose_smem<PIMAX>, PT, sm);
+        int grid = std::max(1, std::min<int>(C.n, sms * occ));
+        k_propose_smem<PIMAX><<<grid, PT, sm, s>>>(C, list, count_p, cap, cap * 3 / 4, ovf, ovf_n);
         HP_LAUNCH_CHECK();
     };
-    // tier A nodes cannot overflow (bound <= capA/2); tier B may (optimistic)
-    launch_smem(lA, hc[0], capA, lC, cnts + 2);
-    launch_smem(lB, hc[1], capB, lC, cnts + 2);
-    fetch_bytes(hc, cnts, sizeof hc, s);
-    launch_smem(lC, hc[2], capC, lG, cnts + 3);
-    fetch_bytes(hc, cnts, sizeof hc, s);
-    int32_t ng = hc[3];
-    if (ng > 0) {
-        int32_t *gcap = A.get<int32_t>(ng);
-        int64_t *gsz = A.get<int64_t>(ng + 1);
-        int64_t *goff = A.get<int64_t>(ng + 1);
-        k_global_caps<<<grid_of(ng, 256), 256, 0, s>>>(lG, ng, L.nbnd, gcap, gsz);
-        HP_LAUNCH_CHECK();
-        scan_excl(gsz, goff, ng, goff + ng, A);
-        int64_t total = fetch<int64_t>(goff + ng, s);
-        int32_t *gkeys = A.get<int32_t>(total);
-        unsigned long long *geta = A.get<unsigned long long>(total);
-        uint32_t *ginter = A.get<uint32_t>(total);
-        HPC(cudaMemsetAsync(gkeys, 0xff, sizeof(int32_t) * total, s));
-        HPC(cudaMemsetAsync(geta, 0, sizeof(unsigned long long) * total, s));
-        HPC(cudaMemsetAsync(ginter, 0, sizeof(uint32_t) * total, s));
-        k_propose_global<PIMAX><<<std::min<int>(ng, sms * 4), PT, 0, s>>>(C, lG, ng, goff, gcap, gkeys, geta, ginter,
-                                                                         lA, cnts + 4);
-        HP_LAUNCH_CHECK();
-        int32_t bad = fetch<int32_t>(cnts + 4, s);
-        if (bad) throw Error(HP_ERR_INTERNAL, "neighbour table in global memory overflowed");
-        A.release(gkeys);
-        A.release(geta);
-        A.release(ginter);
-        A.release(gcap);
-        A.release(gsz);
-        A.release(goff);
-    }
-    A.release(lA);
-    A.release(lB);
-    A.release(lC);
-    A.release(lG);
-    A.release(cnts);
-    (void)err_dev;
+    // tier B may overflow (the bound can be far above the true neighbourhood)
+    launch_smem(W.lB, W.cnt + 1, capB, W.lC, W.cnt + 2);
+    launch_smem(W.lC, W.cnt + 2, capC, W.lG, W.cnt + 3);
+    k_propose_global<PIMAX><<<W.gnb, PT, 0, s>>>(C, W.lG, W.cnt + 3, W.gcap, W.gkeys, W.geta, W.ginter, W.lW,
+                                                  W.cnt + 4);
+    HP_LAUNCH_CHECK();
 }
 
 // ---------------------------------------------------------------- best-effort pairing
@@ -625,31 +792,92 @@ __global__ void k_sum_i32(const int32_t *x, int32_t n, unsigned long long *sum) 
     for (int o = 16; o > 0; o >>= 1) loc += __shfl_down_sync(0xffffffffu, loc, o);
     if ((threadIdx.x & 31) == 0) atomicAdd(sum, loc);
 }
+__global__ void k_flag_if_nonzero(const int32_t *x, uint32_t *err) {
+    if (*x) atomicOr(err, E_INTERNAL);
+}
 
-CoarsenOut coarsen_level(Level &L, int32_t level, const int32_t *w, const Params &P, int32_t *mate, Arena &A,
-                         uint32_t *err_dev, int32_t *cand_out, uint64_t *score_out, cudaEvent_t *prop_events) {
+CoarsenWs *coarsen_workspace(int32_t n, int32_t e, const Params &P, Arena &A) {
+    cudaStream_t s = A.stream();
+    CoarsenWs *W = new CoarsenWs();
+    const int32_t pi = P.o.pi;
+    W->cn = n;
+    W->ce = e;
+    W->pi = pi;
+    W->q = A.get<uint64_t>(e);
+    W->cand = A.get<int32_t>((int64_t)n * pi);
+    W->cscore = A.get<uint64_t>((int64_t)n * pi);
+    W->lW = A.get<int32_t>(n);
+    W->lB = A.get<int32_t>(n);
+    W->lC = A.get<int32_t>(n);
+    W->lG = A.get<int32_t>(n);
+    W->cnt = A.get<int32_t>(8);
+    W->nsum = A.get<long long>(n);
+    W->vis = A.get<long long>(n);
+    // global neighbour tables: one region of gcap >= 2n slots per CTA
+    W->gcap = 64;
+    while (W->gcap < 2u * (uint32_t)std::max(n, 1) + 2u && W->gcap < (1u << 30)) W->gcap <<= 1;
+    W->gnb = (int)std::max<int64_t>(1, std::min<int64_t>(2 * num_sms(), ((int64_t)1 << 28) / ((int64_t)W->gcap * 16)));
+    W->gkeys = A.get<int32_t>((int64_t)W->gnb * W->gcap);
+    W->geta = A.get<unsigned long long>((int64_t)W->gnb * W->gcap);
+    W->ginter = A.get<uint32_t>((int64_t)W->gnb * W->gcap);
+    HPC(cudaMemsetAsync(W->gkeys, 0xff, sizeof(int32_t) * W->gnb * W->gcap, s));
+    HPC(cudaMemsetAsync(W->geta, 0, sizeof(unsigned long long) * W->gnb * W->gcap, s));
+    HPC(cudaMemsetAsync(W->ginter, 0, sizeof(uint32_t) * W->gnb * W->gcap, s));
+    W->flag = A.get<int32_t>(n);
+    W->pos = A.get<int32_t>(n + 1);
+    W->ikeys = A.get<uint32_t>(n);
+    W->iids = A.get<uint32_t>(n);
+    W->target = A.get<int32_t>(n);
+    W->score = A.get<uint64_t>(n);
+    W->ccount = A.get<int32_t>(n + 1);
+    W->coff = A.get<int32_t>(n + 1);
+    W->fillpos = A.get<int32_t>(n);
+    W->kids = A.get<int32_t>(n);
+    W->best = A.get<int32_t>(n);
+    W->ss0 = A.get<long long>(n);
+    W->ss10 = A.get<long long>(n);
+    W->sum0 = A.get<long long>(n);
+    W->box = A.get<LevelBox>(1);
+    return W;
+}
+
+void coarsen_workspace_free(CoarsenWs *W, Arena &A) {
+    if (!W) return;
+    for (void *p : {(void *)W->nsum, (void *)W->vis, (void *)W->q, (void *)W->cand, (void *)W->cscore, (void *)W->lW, (void *)W->lB, (void *)W->lC,
+                    (void *)W->lG, (void *)W->cnt, (void *)W->gkeys, (void *)W->geta, (void *)W->ginter,
+                    (void *)W->flag, (void *)W->pos, (void *)W->ikeys, (void *)W->iids, (void *)W->target,
+                    (void *)W->score, (void *)W->ccount, (void *)W->coff, (void *)W->fillpos, (void *)W->kids,
+                    (void *)W->best, (void *)W->ss0, (void *)W->ss10, (void *)W->sum0, (void *)W->box})
+        A.release(p);
+    delete W;
+}
+
+LevelBox *coarsen_box(CoarsenWs *W) { return W->box; }
+
+// One coarsening level, entirely on the device (no host synchronisation);
+// the counters end up in the workspace box.
+void coarsen_level(Level &L, int32_t level, const int32_t *w, const Params &P, int32_t *mate, CoarsenWs &W, Arena &A,
+                   uint32_t *err_dev, int32_t *cand_out, uint64_t *score_out, cudaEvent_t *prop_events) {
     cudaStream_t s = A.stream();
     const int32_t n = L.n, pi = P.o.pi;
-    CoarsenOut out;
-    struct Box {
-        unsigned long long qsum, visits, pairs, iso, nbrs;
-        uint64_t cap;
-    };
-    Box *box = A.get<Box>(1);
-    HPC(cudaMemsetAsync(box, 0, sizeof(Box), s));
-    uint64_t *q = A.get<uint64_t>(L.e);
+    LevelBox *box = W.box;
+    HPC(cudaMemsetAsync(box, 0, sizeof(LevelBox), s));
     if (L.e > 0) {
-        k_level_q<<<grid_of(L.e, 256), 256, 0, s>>>(L.off, w, L.e, q, &box->qsum);
+        k_level_q<<<grid_of(L.e, 256), 256, 0, s>>>(L.off, w, L.e, W.q, &box->qsum);
         HP_LAUNCH_CHECK();
     }
     k_level_cap<<<1, 1, 0, s>>>(&box->qsum, L.e, P.o.noise_permille, &box->cap);
     HP_LAUNCH_CHECK();
-    if (n > 0) {
-        k_node_bounds<<<grid_of(n, 256), 256, 0, s>>>(L.off, L.ioff, L.inc, n, L.nbnd, &box->visits);
+    fill_i32(mate, n, -1, s);
+    if (n == 0) return;
+    HPC(cudaMemsetAsync(W.nsum, 0, sizeof(long long) * n, s));
+    HPC(cudaMemsetAsync(W.vis, 0, sizeof(long long) * n, s));
+    if (L.np > 0) {
+        k_node_sums<<<grid_of(L.np, 256), 256, 0, s>>>(L.off, L.inc, L.inode, L.np, W.nsum, W.vis, &box->visits);
         HP_LAUNCH_CHECK();
     }
-    int32_t *cand = A.get<int32_t>((int64_t)n * pi);
-    uint64_t *cscore = A.get<uint64_t>((int64_t)n * pi);
+    k_node_bounds<<<grid_of(n, 256), 256, 0, s>>>(W.nsum, n, L.nbnd);
+    HP_LAUNCH_CHECK();
     PropCtx C;
     C.n = n;
     C.pi = pi;
@@ -660,7 +888,7 @@ CoarsenOut coarsen_level(Level &L, int32_t level, const int32_t *w, const Params
     C.ioff = L.ioff;
     C.inc = L.inc;
     C.nin = L.nin;
-    C.q = q;
+    C.q = W.q;
     C.cap = &box->cap;
     {
         // the level key folds seed and level exactly as the oracle's noise
@@ -671,105 +899,62 @@ CoarsenOut coarsen_level(Level &L, int32_t level, const int32_t *w, const Params
     }
     C.omega = P.omega;
     C.delta = P.delta;
-    C.cand = cand;
-    C.cscore = cscore;
+    C.cand = W.cand;
+    C.cscore = W.cscore;
     C.nbcnt = L.nbnd;   // exact counts replace the bounds (used to size the next level)
-    if (n > 0) {
-        if (prop_events) HPC(cudaEventRecord(prop_events[0], s));
-        if (pi <= 4) run_proposal<4>(C, L, P, A, err_dev);
-        else run_proposal<16>(C, L, P, A, err_dev);
-        if (prop_events) HPC(cudaEventRecord(prop_events[1], s));
-        k_sum_i32<<<grid_of(n, 256), 256, 0, s>>>(L.nbnd, n, &box->nbrs);
-        HP_LAUNCH_CHECK();
-    }
-    A.release(q);
-    if (cand_out && n > 0) {
-        HPC(cudaMemcpyAsync(cand_out, cand, sizeof(int32_t) * n * pi, cudaMemcpyDeviceToDevice, s));
-        HPC(cudaMemcpyAsync(score_out, cscore, sizeof(uint64_t) * n * pi, cudaMemcpyDeviceToDevice, s));
+    if (prop_events) HPC(cudaEventRecord(prop_events[0], s));
+    if (pi <= 4) run_proposal<4>(C, L, P, W, A);
+    else run_proposal<16>(C, L, P, W, A);
+    if (prop_events) HPC(cudaEventRecord(prop_events[1], s));
+    k_flag_if_nonzero<<<1, 1, 0, s>>>(W.cnt + 4, err_dev);
+    HP_LAUNCH_CHECK();
+    k_sum_i32<<<grid_of(n, 256), 256, 0, s>>>(L.nbnd, n, &box->nbrs);
+    HP_LAUNCH_CHECK();
+    if (cand_out) {
+        HPC(cudaMemcpyAsync(cand_out, W.cand, sizeof(int32_t) * n * pi, cudaMemcpyDeviceToDevice, s));
+        HPC(cudaMemcpyAsync(score_out, W.cscore, sizeof(uint64_t) * n * pi, cudaMemcpyDeviceToDevice, s));
     }
 
     // best-effort pairing of nodes with no valid neighbour (Sec. V-C)
-    fill_i32(mate, n, -1, s);
-    if (n > 0) {
-        int32_t *flag = A.get<int32_t>(n);
-        int32_t *pos = A.get<int32_t>(n + 1);
-        k_iso_flags<<<grid_of(n, 256), 256, 0, s>>>(cand, pi, n, flag);
-        HP_LAUNCH_CHECK();
-        scan_excl(flag, pos, n, pos + n, A);
-        int32_t niso = fetch<int32_t>(pos + n, s);
-        if (niso > 1) {
-            uint32_t *keys = A.get<uint32_t>(niso);
-            uint32_t *ids = A.get<uint32_t>(niso);
-            k_iso_compact<<<grid_of(n, 256), 256, 0, s>>>(flag, pos, L.size, n, keys, ids);
-            HP_LAUNCH_CHECK();
-            radix_sort(keys, ids, niso, bits_for((uint64_t)P.omega), A);
-            k_iso_pair<<<grid_of(niso / 2 + 1, 256), 256, 0, s>>>(ids, pos + n, L.size, L.nin, P.omega, P.delta, mate,
-                                                                  &box->iso);
-            HP_LAUNCH_CHECK();
-            A.release(keys);
-            A.release(ids);
-        }
-        A.release(flag);
-        A.release(pos);
+    k_iso_flags<<<grid_of(n, 256), 256, 0, s>>>(W.cand, pi, n, W.flag);
+    HP_LAUNCH_CHECK();
+    scan_excl(W.flag, W.pos, n, W.pos + n, A);
+    k_iso_compact<<<grid_of(n, 256), 256, 0, s>>>(W.flag, W.pos, L.size, n, W.ikeys, W.iids);
+    HP_LAUNCH_CHECK();
+    radix_sort_dev(W.ikeys, W.iids, W.pos + n, n, bits_for((uint64_t)P.omega), A);
+    k_iso_pair<<<grid_of(n / 2 + 1, 256), 256, 0, s>>>(W.iids, W.pos + n, L.size, L.nin, P.omega, P.delta, mate,
+                                                         &box->iso);
+    HP_LAUNCH_CHECK();
 
-        // Pi rounds of maximum-weight matching (Sec. V-D)
-        int32_t *target = A.get<int32_t>(n);
-        uint64_t *score = A.get<uint64_t>(n);
-        int32_t *ccount = A.get<int32_t>(n + 1);
-        int32_t *coff = A.get<int32_t>(n + 1);
-        int32_t *fillpos = A.get<int32_t>(n);
-        int32_t *kids = A.get<int32_t>(n);
-        long long *ss0 = A.get<long long>(n), *ss10 = A.get<long long>(n), *sum0 = A.get<long long>(n);
-        int32_t *best = A.get<int32_t>(n);
-        DpCtx D;
-        D.n = n;
-        D.target = target;
-        D.coff = coff;
-        D.kids = kids;
-        D.score = score;
-        D.pending = fillpos;
-        D.ss0 = ss0;
-        D.ss10 = ss10;
-        D.sum0 = sum0;
-        D.best = best;
-        D.err = err_dev;
-        for (int32_t r = 0; r < pi; r++) {
-            k_targets<<<grid_of(n, 256), 256, 0, s>>>(cand, cscore, pi, mate, n, target, score);
-            HP_LAUNCH_CHECK();
-            HPC(cudaMemsetAsync(ccount, 0, sizeof(int32_t) * (n + 1), s));
-            k_child_count<<<grid_of(n, 256), 256, 0, s>>>(target, n, ccount);
-            HP_LAUNCH_CHECK();
-            scan_excl(ccount, coff, n + 1, nullptr, A);
-            HPC(cudaMemsetAsync(fillpos, 0, sizeof(int32_t) * n, s));
-            k_child_fill<<<grid_of(n, 256), 256, 0, s>>>(target, n, coff, fillpos, kids);
-            HP_LAUNCH_CHECK();
-            HPC(cudaMemcpyAsync(fillpos, ccount, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s));
-            k_dp_up<<<grid_of(n, 256), 256, 0, s>>>(D);
-            HP_LAUNCH_CHECK();
-            k_dp_down<<<grid_of(n, 256), 256, 0, s>>>(D, target, mate, &box->pairs);
-            HP_LAUNCH_CHECK();
-        }
-        A.release(target);
-        A.release(score);
-        A.release(ccount);
-        A.release(coff);
-        A.release(fillpos);
-        A.release(kids);
-        A.release(ss0);
-        A.release(ss10);
-        A.release(sum0);
-        A.release(best);
+    // Pi rounds of maximum-weight matching (Sec. V-D)
+    DpCtx D;
+    D.n = n;
+    D.target = W.target;
+    D.coff = W.coff;
+    D.kids = W.kids;
+    D.score = W.score;
+    D.pending = W.fillpos;
+    D.ss0 = W.ss0;
+    D.ss10 = W.ss10;
+    D.sum0 = W.sum0;
+    D.best = W.best;
+    D.err = err_dev;
+    for (int32_t r = 0; r < pi; r++) {
+        k_targets<<<grid_of(n, 256), 256, 0, s>>>(W.cand, W.cscore, pi, mate, n, W.target, W.score);
+        HP_LAUNCH_CHECK();
+        HPC(cudaMemsetAsync(W.ccount, 0, sizeof(int32_t) * (n + 1), s));
+        k_child_count<<<grid_of(n, 256), 256, 0, s>>>(W.target, n, W.ccount);
+        HP_LAUNCH_CHECK();
+        scan_excl(W.ccount, W.coff, n + 1, nullptr, A);
+        HPC(cudaMemsetAsync(W.fillpos, 0, sizeof(int32_t) * n, s));
+        k_child_fill<<<grid_of(n, 256), 256, 0, s>>>(W.target, n, W.coff, W.fillpos, W.kids);
+        HP_LAUNCH_CHECK();
+        HPC(cudaMemcpyAsync(W.fillpos, W.ccount, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s));
+        k_dp_up<<<grid_of(n, 256), 256, 0, s>>>(D);
+        HP_LAUNCH_CHECK();
+        k_dp_down<<<grid_of(n, 256), 256, 0, s>>>(D, W.target, mate, &box->pairs);
+        HP_LAUNCH_CHECK();
     }
-    A.release(cand);
-    A.release(cscore);
-    Box hb;
-    fetch_bytes(&hb, box, sizeof hb, s);
-    A.release(box);
-    out.pairs = (int64_t)(hb.pairs + hb.iso);
-    out.iso_pairs = (int64_t)hb.iso;
-    out.pin_visits = (int64_t)hb.visits;
-    out.neighbours = (int64_t)hb.nbrs;
-    return out;
 }
 
 }  // namespace hp

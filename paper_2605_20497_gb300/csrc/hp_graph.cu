@@ -88,6 +88,10 @@ __global__ void k_inc_keys(const int32_t *pin, const int32_t *pedge, const int32
     }
 }
 
+__global__ void k_inc_nodes(const uint32_t *keys, int64_t np, int32_t *inode) {
+    GRID_STRIDE(j, np) inode[j] = (int32_t)(keys[j] >> 1);
+}
+
 void build_incidence(Level &L, Arena &A) {
     cudaStream_t s = A.stream();
     L.ioff = A.get<int32_t>(L.n + 1);
@@ -104,12 +108,17 @@ void build_incidence(Level &L, Arena &A) {
         radix_sort(keys, reinterpret_cast<uint32_t *>(L.inc), L.np, bits_for(2ull * (uint64_t)L.n - 1), A);
     }
     scan_excl(cnt, L.ioff, L.n + 1, nullptr, A);
+    L.inode = A.get<int32_t>(L.np);
+    if (L.np > 0) {
+        k_inc_nodes<<<grid_of(L.np, 256), 256, 0, s>>>(keys, L.np, L.inode);
+        HP_LAUNCH_CHECK();
+    }
     A.release(keys);
     A.release(cnt);
 }
 
 uint32_t validate_and_build_level0(const int32_t *pins, const int32_t *offsets, int32_t e, int32_t n,
-                                   const int32_t *src_counts, const int32_t *weights, const Params &P, Level &L,
+                                   const int32_t *src_counts, const int32_t *weights, Params &P, Level &L,
                                    int32_t *w, Arena &A) {
     cudaStream_t s = A.stream();
     struct Box {
@@ -165,6 +174,7 @@ uint32_t validate_and_build_level0(const int32_t *pins, const int32_t *offsets, 
     fill_i32(L.nbnd, n, n > 0 ? n - 1 : 0, s);
     fetch_bytes(&hb, box, sizeof(Box), s);
     if (hb.wsum > (1ull << 37)) hb.err |= E_WSUM;
+    P.wsum = weights ? (int64_t)hb.wsum : (int64_t)e;
     A.release(box);
     return hb.err;
 }
@@ -273,22 +283,13 @@ __global__ void k_coarse_pins(const int32_t *pin, const int32_t *pedge, const in
     }
 }
 
-void contract_level(const Level &L, const int32_t *mate, Level &C, Arena &A) {
+bool contract_level(const Level &L, const int32_t *mate, LevelBox *box, LevelBox *hb, Level &C, Arena &A) {
     cudaStream_t s = A.stream();
     int32_t *isrep = A.get<int32_t>(L.n);
     int32_t *cid = A.get<int32_t>(L.n + 1);
     k_rep_flags<<<grid_of(L.n, 256), 256, 0, s>>>(mate, L.n, isrep);
     HP_LAUNCH_CHECK();
-    scan_excl(isrep, cid, L.n, cid + L.n, A);
-    C.n = fetch<int32_t>(cid + L.n, s);
-    C.e = L.e;
-    C.size = A.get<int32_t>(C.n);
-    C.nbnd = A.get<int32_t>(C.n);
-    const_cast<Level &>(L).gamma = A.get<int32_t>(L.n);
-    k_gamma<<<grid_of(L.n, 256), 256, 0, s>>>(mate, cid, L.size, L.nbnd, L.n, L.gamma, C.size, C.nbnd);
-    HP_LAUNCH_CHECK();
-    A.release(isrep);
-    A.release(cid);
+    scan_excl(isrep, cid, L.n, &box->cn, A);
     int32_t *keep = A.get<int32_t>(L.np);
     int32_t *newpos = A.get<int32_t>(L.np + 1);
     if (L.np) {
@@ -296,8 +297,23 @@ void contract_level(const Level &L, const int32_t *mate, Level &C, Arena &A) {
                                                    keep);
         HP_LAUNCH_CHECK();
     }
-    scan_excl(keep, newpos, L.np, newpos + L.np, A);
-    C.np = fetch<int32_t>(newpos + L.np, s);
+    scan_excl(keep, newpos, L.np, &box->cnp, A);
+    HPC(cudaMemcpyAsync(newpos + L.np, &box->cnp, sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+    fetch_bytes(hb, box, sizeof(LevelBox), s);
+    if (hb->pairs + hb->iso == 0) {
+        for (void *p : {(void *)isrep, (void *)cid, (void *)keep, (void *)newpos}) A.release(p);
+        return false;
+    }
+    C.n = hb->cn;
+    C.e = L.e;
+    C.np = hb->cnp;
+    C.size = A.get<int32_t>(C.n);
+    C.nbnd = A.get<int32_t>(C.n);
+    const_cast<Level &>(L).gamma = A.get<int32_t>(L.n);
+    k_gamma<<<grid_of(L.n, 256), 256, 0, s>>>(mate, cid, L.size, L.nbnd, L.n, L.gamma, C.size, C.nbnd);
+    HP_LAUNCH_CHECK();
+    A.release(isrep);
+    A.release(cid);
     C.off = A.get<int32_t>(C.e + 1);
     C.nsrc = A.get<int32_t>(C.e);
     C.pin = A.get<int32_t>(C.np);
@@ -314,6 +330,7 @@ void contract_level(const Level &L, const int32_t *mate, Level &C, Arena &A) {
     A.release(keep);
     A.release(newpos);
     build_incidence(C, A);
+    return true;
 }
 
 }  // namespace hp

@@ -77,8 +77,152 @@ void scan_excl(const int64_t *in, int64_t *out, int64_t n, int64_t *total_dev, A
 // stable LSD radix sort of (key, value) pairs on the low `bits` bits of key.
 void radix_sort(uint32_t *keys, uint32_t *vals, int64_t n, int bits, Arena &A);
 void radix_sort(uint64_t *keys, uint32_t *vals, int64_t n, int bits, Arena &A);
+// the same with the element count in device memory (*n_dev <= cap); stable
+void radix_sort_dev(uint32_t *keys, uint32_t *vals, const int32_t *n_dev, int64_t cap, int bits, Arena &A);
+void radix_sort_dev(uint64_t *keys, uint32_t *vals, const int32_t *n_dev, int64_t cap, int bits, Arena &A);
 void fill_i32(int32_t *p, int64_t n, int32_t v, cudaStream_t s);
 void iota_i32(int32_t *p, int64_t n, cudaStream_t s);
+
+// Stable LSD radix sort of (keys[i], vals[i]), i < n <= cap, by one CTA of
+// any multiple of 32 threads (up to 1024), on the low 8*passes bits.
+// smem: 2*cap*(sizeof(K)+4) bytes; s_wc: 32*256 words; s_hist: 256 words.
+// Per pass: digit histogram, its exclusive scan, then rounds of blockDim
+// items in index order ranked within a warp by match and across warps by
+// per-warp digit counts.  Ends with the sorted data back in keys/vals and a
+// __syncthreads.
+template <class K>
+__device__ void block_radix_sort(K *keys, uint32_t *vals, int n, int passes, int cap, unsigned char *smem,
+                                 uint32_t *s_wc, uint32_t *s_hist) {
+    K *ka = reinterpret_cast<K *>(smem);
+    K *kb = ka + cap;
+    uint32_t *va = reinterpret_cast<uint32_t *>(kb + cap);
+    uint32_t *vb = va + cap;
+    const int t = threadIdx.x, T = blockDim.x, lane = t & 31, w = t >> 5;
+    const uint32_t lt = (1u << lane) - 1u;
+    __syncthreads();
+    if (n <= 1) return;
+    for (int i = t; i < n; i += T) {
+        ka[i] = keys[i];
+        va[i] = vals[i];
+    }
+    __syncthreads();
+    for (int p = 0; p < passes; p++) {
+        const int shift = 8 * p;
+        for (int d = t; d < 256; d += T) s_hist[d] = 0;
+        __syncthreads();
+        for (int i = t; i < n; i += T) atomicAdd(&s_hist[(uint32_t)(ka[i] >> shift) & 255u], 1u);
+        __syncthreads();
+        if (t == 0) {
+            uint32_t run = 0;
+            for (int d = 0; d < 256; d++) {
+                uint32_t c = s_hist[d];
+                s_hist[d] = run;
+                run += c;
+            }
+        }
+        __syncthreads();
+        for (int r0 = 0; r0 < n; r0 += T) {
+            const int i = r0 + t;
+            const bool valid = i < n;
+            const uint32_t d = valid ? ((uint32_t)(ka[i] >> shift) & 255u) : 256u;
+            const uint32_t peers = __match_any_sync(0xffffffffu, d);
+            const uint32_t rank = __popc(peers & lt);
+            for (int k = t; k < 32 * 256; k += T) s_wc[k] = 0;
+            __syncthreads();
+            if (valid && rank == 0) s_wc[w * 256 + d] = __popc(peers);
+            __syncthreads();
+            for (int d2 = t; d2 < 256; d2 += T) {
+                uint32_t run = 0, base = s_hist[d2];
+                for (int k = 0; k < 32; k++) {
+                    uint32_t c = s_wc[k * 256 + d2];
+                    s_wc[k * 256 + d2] = base + run;
+                    run += c;
+                }
+                s_hist[d2] = base + run;
+            }
+            __syncthreads();
+            if (valid) {
+                uint32_t pos = s_wc[w * 256 + d] + rank;
+                kb[pos] = ka[i];
+                vb[pos] = va[i];
+            }
+            __syncthreads();
+        }
+        K *tk = ka;
+        ka = kb;
+        kb = tk;
+        uint32_t *tv = va;
+        va = vb;
+        vb = tv;
+    }
+    for (int i = t; i < n; i += T) {
+        keys[i] = ka[i];
+        vals[i] = va[i];
+    }
+    __syncthreads();
+}
+
+// Segmented sum over runs of equal, non-decreasing keys within a warp: every
+// lane passes its key and value; returns true on the last lane of its run
+// (whose *acc then holds the run's total within the warp).  All 32 lanes
+// must take part.
+template <class T> __device__ __forceinline__ bool warp_run_sum(int32_t key, T &acc) {
+    const int lane = threadIdx.x & 31;
+    for (int o = 1; o < 32; o <<= 1) {
+        T y = __shfl_up_sync(0xffffffffu, acc, o);
+        int32_t k = __shfl_up_sync(0xffffffffu, key, o);
+        if (lane >= o && k == key) acc += y;
+    }
+    int32_t nk = __shfl_down_sync(0xffffffffu, key, 1);
+    return lane == 31 || nk != key;
+}
+
+// Per-thread write combining for hub nodes: a few (key, sum, count) entries
+// in registers absorb repeated updates of the same key; an evicted or final
+// entry is flushed by the caller-supplied functor (one atomic per flush).
+// Sums are integers, so the result does not depend on the flush order.
+template <int K> struct RegCache {
+    int32_t key[K];
+    unsigned long long sum[K];
+    uint32_t cnt[K];
+    int next;
+    __device__ void init() {
+#pragma unroll
+        for (int i = 0; i < K; i++) key[i] = -1;
+        next = 0;
+    }
+    template <class F> __device__ void add(int32_t k, unsigned long long v, uint32_t c, F &&flush) {
+#pragma unroll
+        for (int i = 0; i < K; i++)
+            if (key[i] == k) {
+                sum[i] += v;
+                cnt[i] += c;
+                return;
+            }
+        int slot = next;
+        next = (next + 1) % K;
+#pragma unroll
+        for (int i = 0; i < K; i++)
+            if (i == slot) {
+                if (key[i] >= 0) flush(key[i], sum[i], cnt[i]);
+                key[i] = k;
+                sum[i] = v;
+                cnt[i] = c;
+            }
+    }
+    template <class F> __device__ void drain(F &&flush) {
+#pragma unroll
+        for (int i = 0; i < K; i++)
+            if (key[i] >= 0) {
+                flush(key[i], sum[i], cnt[i]);
+                key[i] = -1;
+            }
+    }
+};
+
+// kernel attributes: raises the dynamic shared memory limit of `func` to
+// `smem` once and returns its resident CTAs per SM (cached per pair)
+int prepare_kernel(const void *func, int block, size_t smem);
 
 // ---------------------------------------------------------------- levels
 // One hypergraph of the hierarchy, device resident.
@@ -92,6 +236,7 @@ struct Level {
     int32_t *size = nullptr;   // [n] node sizes
     int32_t *ioff = nullptr;   // [n+1] incidence segments
     int32_t *inc = nullptr;    // [np] in(v) ascending, then out(v) ascending
+    int32_t *inode = nullptr;  // [np] node of every incidence entry
     int32_t *nin = nullptr;    // [n] |in(v)|
     int32_t *gamma = nullptr;  // [n] node -> node of the next level
     int32_t *nbnd = nullptr;   // [n] upper bound on |N(v)| (neighbour table sizing)
@@ -101,26 +246,38 @@ struct Params {
     int32_t omega, delta;
     uint64_t seed;
     hp_options o;
+    int64_t wsum = 0;   // sum of hyperedge weights (bounds any gain)
 };
 
 // graph construction (hp_graph.cu)
 uint32_t validate_and_build_level0(const int32_t *pins, const int32_t *offsets, int32_t e, int32_t n,
-                                   const int32_t *src_counts, const int32_t *weights, const Params &P, Level &L,
+                                   const int32_t *src_counts, const int32_t *weights, Params &P, Level &L,
                                    int32_t *w_out, Arena &A);
 void build_incidence(Level &L, Arena &A);
 // level graph from caller arrays (device): copies them and builds the incidence
 void make_level(int32_t n, int32_t e, const int32_t *off, const int32_t *pins, const int32_t *nsrc,
                 const int32_t *size, Level &L, Arena &A);
-void contract_level(const Level &L, const int32_t *mate, Level &C, Arena &A);
+// device counters of one coarsening level (read by the host once per level)
+struct LevelBox {
+    unsigned long long qsum, visits, pairs, iso, nbrs;
+    uint64_t cap;      // noise cap of the level
+    int32_t cn, cnp;   // nodes and pins of the coarse level
+};
+// Contraction (Sec. V-E): computes the coarse sizes into box_dev, reads the
+// box once into box_host; returns false and builds nothing when the level
+// formed no pair.
+bool contract_level(const Level &L, const int32_t *mate, LevelBox *box_dev, LevelBox *box_host, Level &C, Arena &A);
 
 // coarsening (hp_coarsen.cu)
-struct CoarsenOut {
-    int64_t pairs = 0, iso_pairs = 0, pin_visits = 0, neighbours = 0;
-};
+struct CoarsenWs;
+CoarsenWs *coarsen_workspace(int32_t n, int32_t e, const Params &P, Arena &A);
+void coarsen_workspace_free(CoarsenWs *W, Arena &A);
+LevelBox *coarsen_box(CoarsenWs *W);
+// One level on the device, no host synchronisation; counters in the box.
 // prop_events (optional): two events recorded around the proposal launches
-CoarsenOut coarsen_level(Level &L, int32_t level, const int32_t *w, const Params &P, int32_t *mate, Arena &A,
-                         uint32_t *err_dev, int32_t *cand_out = nullptr, uint64_t *score_out = nullptr,
-                         cudaEvent_t *prop_events = nullptr);
+void coarsen_level(Level &L, int32_t level, const int32_t *w, const Params &P, int32_t *mate, CoarsenWs &W, Arena &A,
+                   uint32_t *err_dev, int32_t *cand_out = nullptr, uint64_t *score_out = nullptr,
+                   cudaEvent_t *prop_events = nullptr);
 
 // refinement (hp_refine.cu)
 // optional copies of the intermediate results of one repetition (device
@@ -139,7 +296,14 @@ struct RefineOut {
     int64_t moves = 0;
     int32_t reps = 0;
 };
-RefineOut refine_level(const Level &L, const int32_t *w, int32_t nparts, const Params &P, int32_t *rho, Arena &A,
+struct LevelWs;
+// refinement workspace for levels of at most n nodes, np pins, e hyperedges
+// and max_e pins per hyperedge (the level-0 sizes)
+LevelWs *refine_workspace(int32_t n, int64_t np, int32_t e, int32_t nparts, int32_t max_e, const Params &P,
+                          Arena &A);
+void refine_workspace_free(LevelWs *W, Arena &A);
+int32_t max_edge_size(const Level &L, Arena &A);
+RefineOut refine_level(const Level &L, const int32_t *w, const Params &P, int32_t *rho, LevelWs *W, Arena &A,
                        uint32_t *err_dev);
 void objective(const Level &L, const int32_t *w, const int32_t *rho, int32_t nparts, int64_t *conn_dev,
                int64_t *cutnet_dev, Arena &A);

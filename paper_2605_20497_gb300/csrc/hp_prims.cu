@@ -117,6 +117,41 @@ template uint64_t fetch<uint64_t>(const uint64_t *, cudaStream_t);
 template unsigned long long fetch<unsigned long long>(const unsigned long long *, cudaStream_t);
 template long long fetch<long long>(const long long *, cudaStream_t);
 
+int prepare_kernel(const void *func, int block, size_t smem) {
+    // per (kernel, device): the dynamic shared memory limit only ever grows,
+    // so a size admitted once stays admitted; occupancy cached per size
+    struct Entry {
+        const void *f;
+        int dev, block;
+        size_t smem;
+        int occ;
+    };
+    static std::mutex mu;
+    static std::vector<Entry> occ_cache;
+    static std::vector<std::pair<std::pair<const void *, int>, size_t>> limit;
+    int dev = 0;
+    HPC(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(mu);
+    size_t *lim = nullptr;
+    for (auto &l : limit)
+        if (l.first.first == func && l.first.second == dev) lim = &l.second;
+    if (!lim) {
+        limit.push_back({{func, dev}, (size_t)48 * 1024});
+        lim = &limit.back().second;
+    }
+    if (smem > *lim) {
+        HPC(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        *lim = smem;
+    }
+    for (auto &c : occ_cache)
+        if (c.f == func && c.dev == dev && c.block == block && c.smem == smem) return c.occ;
+    int occ = 0;
+    HPC(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, func, block, smem));
+    occ = std::max(occ, 1);
+    occ_cache.push_back({func, dev, block, smem, occ});
+    return occ;
+}
+
 int num_sms() {
     static int sms[64] = {0};
     int dev = 0;
@@ -348,6 +383,122 @@ template <class K> static void radix_impl(K *keys, uint32_t *vals, int64_t n, in
     A.release(k2);
     A.release(v2);
     A.release(hist);
+}
+
+// ---- variants with the element count in device memory ------------------
+// Grids are sized for `cap` elements; tiles past *n_dev contribute nothing.
+template <class K>
+__global__ void __launch_bounds__(RS_T) k_radix_hist_dev(const K *keys, const int32_t *n_dev, int shift, uint32_t *hist,
+                                                         int tiles) {
+    __shared__ uint32_t cnt[256];
+    cnt[threadIdx.x] = 0;
+    __syncthreads();
+    const int64_t n = *n_dev;
+    int64_t base = (int64_t)blockIdx.x * RS_TILE;
+    for (int r = 0; r < RS_R; r++) {
+        int64_t i = base + (int64_t)r * RS_T + threadIdx.x;
+        if (i < n) atomicAdd(&cnt[(uint32_t)(keys[i] >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    hist[(int64_t)threadIdx.x * tiles + blockIdx.x] = cnt[threadIdx.x];
+}
+
+template <class K>
+__global__ void __launch_bounds__(RS_T) k_radix_scatter_dev(const K *kin, const uint32_t *vin, K *kout,
+                                                            uint32_t *vout, const int32_t *n_dev, int shift,
+                                                            const uint32_t *offs, int tiles) {
+    __shared__ uint32_t s_off[256];
+    __shared__ uint32_t s_wc[8][256];
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    const uint32_t lt = (1u << lane) - 1u;
+    const int64_t n = *n_dev;
+    s_off[t] = offs[(int64_t)t * tiles + blockIdx.x];
+    int64_t base = (int64_t)blockIdx.x * RS_TILE;
+    for (int r = 0; r < RS_R; r++) {
+        int64_t i0 = base + (int64_t)r * RS_T;
+        if (i0 >= n) break;
+        int64_t i = i0 + t;
+        bool valid = i < n;
+        K key = valid ? kin[i] : K(0);
+        uint32_t val = valid ? vin[i] : 0u;
+        uint32_t d = valid ? ((uint32_t)(key >> shift) & 255u) : 256u;
+        for (int k = 0; k < 8; k++) s_wc[k][t] = 0;
+        __syncthreads();
+        uint32_t peers = __match_any_sync(0xffffffffu, d);
+        uint32_t rank = __popc(peers & lt);
+        if (valid && rank == 0) s_wc[w][d] = __popc(peers);
+        __syncthreads();
+        uint32_t run = 0;
+        for (int k = 0; k < 8; k++) {
+            uint32_t c = s_wc[k][t];
+            s_wc[k][t] = run;
+            run += c;
+        }
+        __syncthreads();
+        if (valid) {
+            uint32_t pos = s_off[d] + s_wc[w][d] + rank;
+            kout[pos] = key;
+            vout[pos] = val;
+        }
+        __syncthreads();
+        s_off[t] += run;
+    }
+}
+
+// Single-CTA LSD radix sort in shared memory for n <= SMALL_SORT elements
+// (block_radix_sort, hp_internal.cuh); this kernel wraps it for the
+// device-count sort entry points.
+constexpr int SS_T = 1024, SMALL_SORT = 4096;
+template <class K>
+__global__ void __launch_bounds__(SS_T) k_small_sort(K *keys, uint32_t *vals, const int32_t *n_dev, int passes) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ uint32_t s_wc[32][256];
+    __shared__ uint32_t s_hist[256];
+    block_radix_sort<K>(keys, vals, *n_dev, passes, SMALL_SORT, smem, &s_wc[0][0], s_hist);
+}
+
+template <class K>
+static void radix_dev_impl(K *keys, uint32_t *vals, const int32_t *n_dev, int64_t cap, int bits, Arena &A) {
+    if (cap <= 1 || bits <= 0) return;
+    cudaStream_t s = A.stream();
+    const int passes = (bits + 7) / 8;
+    if (cap <= SMALL_SORT) {
+        size_t sm = (size_t)SMALL_SORT * 2 * (sizeof(K) + sizeof(uint32_t));
+        prepare_kernel((const void *)k_small_sort<K>, SS_T, sm);
+        k_small_sort<K><<<1, SS_T, sm, s>>>(keys, vals, n_dev, passes);
+        HP_LAUNCH_CHECK();
+        return;
+    }
+    const int tiles = (int)cdiv(cap, RS_TILE);
+    K *k2 = A.get<K>(cap);
+    uint32_t *v2 = A.get<uint32_t>(cap);
+    uint32_t *hist = A.get<uint32_t>((int64_t)256 * tiles);
+    K *ka = keys, *kb = k2;
+    uint32_t *va = vals, *vb = v2;
+    for (int p = 0; p < passes; p++) {
+        k_radix_hist_dev<K><<<tiles, RS_T, 0, s>>>(ka, n_dev, 8 * p, hist, tiles);
+        HP_LAUNCH_CHECK();
+        scan_excl(reinterpret_cast<int32_t *>(hist), reinterpret_cast<int32_t *>(hist), (int64_t)256 * tiles,
+                  nullptr, A);
+        k_radix_scatter_dev<K><<<tiles, RS_T, 0, s>>>(ka, va, kb, vb, n_dev, 8 * p, hist, tiles);
+        HP_LAUNCH_CHECK();
+        std::swap(ka, kb);
+        std::swap(va, vb);
+    }
+    if (ka != keys) {
+        HPC(cudaMemcpyAsync(keys, ka, cap * sizeof(K), cudaMemcpyDeviceToDevice, s));
+        HPC(cudaMemcpyAsync(vals, va, cap * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
+    }
+    A.release(k2);
+    A.release(v2);
+    A.release(hist);
+}
+
+void radix_sort_dev(uint32_t *keys, uint32_t *vals, const int32_t *n_dev, int64_t cap, int bits, Arena &A) {
+    radix_dev_impl<uint32_t>(keys, vals, n_dev, cap, bits > 32 ? 32 : bits, A);
+}
+void radix_sort_dev(uint64_t *keys, uint32_t *vals, const int32_t *n_dev, int64_t cap, int bits, Arena &A) {
+    radix_dev_impl<uint64_t>(keys, vals, n_dev, cap, bits > 64 ? 64 : bits, A);
 }
 
 void radix_sort(uint32_t *keys, uint32_t *vals, int64_t n, int bits, Arena &A) {

@@ -9,6 +9,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <initializer_list>
 
 #include "hp_internal.cuh"
 
@@ -112,8 +113,8 @@ constexpr int PLW_T = 128;  // warp-per-edge kernel: 4 warps
 // edges with |e| <= small_max, one warp each, tables in shared memory
 __global__ void __launch_bounds__(PLW_T) k_plist_small(const int32_t *off, const int32_t *pin, const int32_t *nsrc,
                                                        const int32_t *w, const int32_t *rho, int32_t e,
-                                                       int32_t small_max, uint32_t cap, Plist PL, int32_t *D,
-                                                       long long *saving) {
+                                                       const int32_t *list, int32_t small_max, uint32_t cap, Plist PL,
+                                                       int32_t *D, long long *saving) {
     extern __shared__ __align__(16) int32_t sm[];
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int per = 3 * (int)cap + 4 * small_max + 1;
@@ -129,10 +130,11 @@ __global__ void __launch_bounds__(PLW_T) k_plist_small(const int32_t *off, const
     __syncwarp();
     int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    // all hyperedges up to small_max pins, or the given list (count e)
     for (int64_t i = warp; i < e; i += nw) {
-        if (off[i + 1] - off[i] > small_max) continue;
-        plist_edge<32>((int32_t)i, lane, off, pin, nsrc, w, rho, keys, tc, tci, cap, es, ep, ec, eci, gcnt, PL, D,
-                       saving);
+        const int32_t ed = list ? list[i] : (int32_t)i;
+        if (!list && off[ed + 1] - off[ed] > small_max) continue;
+        plist_edge<32>(ed, lane, off, pin, nsrc, w, rho, keys, tc, tci, cap, es, ep, ec, eci, gcnt, PL, D, saving);
     }
 }
 
@@ -188,12 +190,10 @@ static void build_plist(const Level &L, const int32_t *w, const int32_t *rho, in
     const uint32_t cap = pow2_at_least(2 * (int64_t)small_max);
     const int per = 3 * (int)cap + 4 * small_max + 1;
     size_t sm = (size_t)per * 4 * (PLW_T / 32);
-    HPC(cudaFuncSetAttribute(k_plist_small, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    int occ = 0;
-    HPC(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_plist_small, PLW_T, sm));
+    int occ = prepare_kernel((const void *)k_plist_small, PLW_T, sm);
     int grid = (int)std::min<int64_t>(cdiv(L.e, PLW_T / 32), (int64_t)num_sms() * std::max(occ, 1));
-    k_plist_small<<<std::max(grid, 1), PLW_T, sm, s>>>(L.off, L.pin, L.nsrc, w, rho, L.e, small_max, cap, PL, D,
-                                                       saving);
+    k_plist_small<<<std::max(grid, 1), PLW_T, sm, s>>>(L.off, L.pin, L.nsrc, w, rho, L.e, nullptr, small_max, cap,
+                                                       PL, D, saving);
     HP_LAUNCH_CHECK();
     if (max_e > small_max) {
         int32_t *list = A.get<int32_t>(L.e);
@@ -264,30 +264,6 @@ void objective(const Level &L, const int32_t *w, const int32_t *rho, int32_t npa
     A.release(maxe);
 }
 
-// ---------------------------------------------------------------- per level constants
-// Wns(v) = sum of w(e) over incident hyperedges with |e| >= 2
-__global__ void k_wns(const int32_t *off, const int32_t *ioff, const int32_t *inc, const int32_t *w, int32_t n,
-                      long long *wns) {
-    GRID_STRIDE(v, (int64_t)n) {
-        long long s = 0;
-        for (int32_t t = ioff[v]; t < ioff[v + 1]; t++) {
-            int32_t e = inc[t];
-            if (off[e + 1] - off[e] >= 2) s += w[e];
-        }
-        wns[v] = s;
-    }
-}
-
-__global__ void k_psize(const int32_t *rho, const int32_t *size, int32_t n, long long *psize) {
-    GRID_STRIDE(v, (int64_t)n) atomicAdd((unsigned long long *)&psize[rho[v]], (unsigned long long)size[v]);
-}
-
-__global__ void k_candidates(const long long *saving, int32_t n, int32_t *list, int32_t *cnt) {
-    GRID_STRIDE(v, (int64_t)n) {
-        if (saving[v] > 0) list[atomicAdd(cnt, 1)] = (int32_t)v;
-    }
-}
-
 // ---------------------------------------------------------------- Eq. 13 gains
 struct Moves {
     int32_t *node, *src, *dst;
@@ -307,34 +283,58 @@ __device__ void gains_node(int32_t v, const int32_t *off, const int32_t *ioff, c
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const uint32_t mask = cap - 1;
     const int32_t s = rho[v];
+    auto add = [&](int32_t p, long long we) {
+        uint32_t h = hslot(p, mask);
+        for (uint32_t probe = 0; probe < cap; probe++) {
+            int32_t kk = ((volatile int32_t *)keys)[h];
+            if (kk == -1) {
+                int32_t old = atomicCAS(&keys[h], -1, p);
+                if (old == -1) {
+                    if ((uint32_t)atomicAdd(s_cnt, 1) + 1 > limit) *(volatile int *)s_flag = 1;
+                    kk = p;
+                } else {
+                    kk = old;
+                }
+            }
+            if (kk == p) {
+                atomicAdd((unsigned long long *)&conn[h], (unsigned long long)we);
+                return;
+            }
+            h = (h + 1) & mask;
+        }
+    };
+    // hyperedges with at most 8 parts: one per thread, repeated parts combined
+    // in registers; longer lists: a warp each
+    {
+        RegCache<4> rc;
+        rc.init();
+        auto flush = [&](int32_t p, unsigned long long sw, uint32_t) { add(p, (long long)sw); };
+        for (int32_t t = ioff[v] + threadIdx.x; t < ioff[v + 1]; t += blockDim.x) {
+            if (*(volatile int *)s_flag) break;
+            const int32_t e = inc[t];
+            const int32_t a = off[e];
+            if (off[e + 1] - a < 2) continue;
+            const int32_t lam = PL.lam[e];
+            if (lam > 8) continue;
+            const unsigned long long we = (unsigned long long)w[e];
+            for (int32_t k = 0; k < lam; k++) {
+                const int32_t p = PL.p[a + k];
+                if (p != s) rc.add(p, we, 0u, flush);
+            }
+        }
+        rc.drain(flush);
+    }
     for (int32_t t = ioff[v] + wid; t < ioff[v + 1]; t += nw) {
         if (*(volatile int *)s_flag) break;
-        int32_t e = inc[t];
-        int32_t a = off[e];
+        const int32_t e = inc[t];
+        const int32_t a = off[e];
         if (off[e + 1] - a < 2) continue;
-        const long long we = w[e];
         const int32_t lam = PL.lam[e];
+        if (lam <= 8) continue;
+        const long long we = w[e];
         for (int32_t k = lane; k < lam; k += 32) {
-            int32_t p = PL.p[a + k];
-            if (p == s) continue;
-            uint32_t h = hslot(p, mask);
-            for (uint32_t probe = 0; probe < cap; probe++) {
-                int32_t kk = ((volatile int32_t *)keys)[h];
-                if (kk == -1) {
-                    int32_t old = atomicCAS(&keys[h], -1, p);
-                    if (old == -1) {
-                        if ((uint32_t)atomicAdd(s_cnt, 1) + 1 > limit) *(volatile int *)s_flag = 1;
-                        kk = p;
-                    } else {
-                        kk = old;
-                    }
-                }
-                if (kk == p) {
-                    atomicAdd((unsigned long long *)&conn[h], (unsigned long long)we);
-                    break;
-                }
-                h = (h + 1) & mask;
-            }
+            const int32_t p = PL.p[a + k];
+            if (p != s) add(p, we);
         }
     }
     __syncthreads();
@@ -407,8 +407,9 @@ struct GainArgs {
     Moves M;
 };
 
-__global__ void __launch_bounds__(GN_T) k_gains_smem(GainArgs G, const int32_t *list, int32_t count, uint32_t cap,
-                                                     int32_t *ovf, int32_t *ovf_n) {
+__global__ void __launch_bounds__(GN_T) k_gains_smem(GainArgs G, const int32_t *list, const int32_t *count_p,
+                                                     uint32_t cap, int32_t *ovf, int32_t *ovf_n) {
+    const int32_t count = *count_p;
     extern __shared__ __align__(16) unsigned char smem[];
     long long *conn = reinterpret_cast<long long *>(smem);
     int32_t *keys = reinterpret_cast<int32_t *>(conn + cap);
@@ -430,9 +431,11 @@ __global__ void __launch_bounds__(GN_T) k_gains_smem(GainArgs G, const int32_t *
                    G.second_half, keys, conn, cap, cap * 3 / 4, &s_cnt, &s_flag, G.M, ovf, ovf_n, s_rg, s_rp);
 }
 
-__global__ void __launch_bounds__(GN_T) k_gains_global(GainArgs G, const int32_t *list, int32_t count, uint32_t cap,
-                                                       int32_t *gkeys, long long *gconn, int32_t *bad,
+__global__ void __launch_bounds__(GN_T) k_gains_global(GainArgs G, const int32_t *list, const int32_t *count_p,
+                                                       uint32_t cap, int32_t *gkeys, long long *gconn, int32_t *bad,
                                                        int32_t *bad_n) {
+    const int32_t count = *count_p;
+    if (count == 0) return;
     __shared__ int32_t s_cnt;
     __shared__ int s_flag;
     __shared__ long long s_rg[8];
@@ -453,62 +456,165 @@ __global__ void __launch_bounds__(GN_T) k_gains_global(GainArgs G, const int32_t
                    G.second_half, keys, conn, cap, cap - 1, &s_cnt, &s_flag, G.M, bad, bad_n, s_rg, s_rp);
 }
 
-// ---------------------------------------------------------------- sort of moves
-__global__ void k_move_keys(const Moves M, const int32_t *cntp, long long gmax, int gb, int nb, uint64_t *keys,
-                            uint32_t *idx) {
-    int32_t m = *cntp;
-    GRID_STRIDE(i, (int64_t)m) {
-        uint64_t k = ((uint64_t)M.src[i] << (gb + nb)) | ((uint64_t)(gmax - M.gain[i]) << nb) | (uint64_t)M.node[i];
-        keys[i] = k;
-        idx[i] = (uint32_t)i;
+// ---------------------------------------------------------------- per level constants
+// Per node: Wns(v) = sum of w(e) over incident hyperedges with |e| >= 2, and
+// the number of singleton hyperedges {v} that hold v as a destination.
+// Singleton hyperedges cancel in every gain (they are spared and re-created
+// by any move) and change only the distinct-inbound count, by one per
+// singleton at p_s (-) and at p_d (+): they are handled per node.
+__global__ void k_level_nodes(const int32_t *off, const int32_t *ioff, const int32_t *inc, const int32_t *inode,
+                              const int32_t *nin, const int32_t *w, int64_t np, long long *wns, int32_t *singin) {
+    const int lane = threadIdx.x & 31;
+    const int64_t wbase = ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5) << 5;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = wbase; base < np; base += stride) {
+        const int64_t t = base + lane;
+        const bool valid = t < np;
+        const int32_t v = valid ? inode[t] : -1 - lane;
+        long long a = 0;
+        int32_t c = 0;
+        if (valid) {
+            const int32_t e = inc[t];
+            const int32_t sz = off[e + 1] - off[e];
+            if (sz >= 2) a = w[e];
+            else if (t < ioff[v] + nin[v]) c = 1;
+        }
+        bool tail = warp_run_sum(v, a);
+        warp_run_sum(v, c);
+        if (valid && tail) {
+            if (a) atomicAdd((unsigned long long *)&wns[v], (unsigned long long)a);
+            if (c) atomicAdd(&singin[v], c);
+        }
     }
 }
-__global__ void k_gather_moves(const Moves M, const uint32_t *idx, int32_t m, Moves S) {
-    GRID_STRIDE(i, (int64_t)m) {
+
+// hyperedges with >= 2 pins, split at small_max pins
+__global__ void k_level_edges(const int32_t *off, int32_t e, int32_t small_max, int32_t *act, int32_t *big,
+                              int32_t *cnt) {
+    GRID_STRIDE(i, (int64_t)e) {
+        int32_t sz = off[i + 1] - off[i];
+        if (sz >= 2 && sz <= small_max) act[atomicAdd(&cnt[0], 1)] = (int32_t)i;
+        else if (sz > small_max) big[atomicAdd(&cnt[1], 1)] = (int32_t)i;
+    }
+}
+
+// counters of one repetition (device)
+enum { C_CAND, C_MOVES, C_OVF, C_BAD, C_NH, C_BAD0, C_APPLIED, C_NV, C_N };
+
+// moves of at most SMALLM are sequenced and validated by one CTA each
+constexpr int SMALLM = 4096, SEQ_T = 1024;
+
+#define STRIDE(i, n, t0, nt) for (int64_t i = (t0); i < (int64_t)(n); i += (nt))
+#define G_T0 (blockIdx.x * (int64_t)blockDim.x + threadIdx.x)
+#define G_NT ((int64_t)gridDim.x * blockDim.x)
+
+struct RepArrays {
+    int32_t n, e, nparts, rounds;
+    int32_t *cnt, *linked;
+    int32_t *D0;
+    long long *psize, *saving;
+    int32_t *pc;
+    int32_t *pred, *succ, *chain, *mvpos;
+    long long *cgain;
+    unsigned long long *gseq, *acc0;
+    int32_t *dDs, *dDd, *viol;
+};
+
+__device__ __forceinline__ int64_t rep_zero_span(const RepArrays &R) {
+    return max(max((int64_t)R.n, (int64_t)R.nparts + 1), max((int64_t)C_N, (int64_t)R.rounds + 1));
+}
+__global__ void k_rep_zero(RepArrays R) {
+    GRID_STRIDE(i, rep_zero_span(R)) {
+        if (i < R.nparts) {
+            R.D0[i] = 0;
+            R.psize[i] = 0;
+        }
+        if (i <= R.nparts) R.pc[i] = 0;
+        if (i < R.n) {
+            R.saving[i] = 0;
+            R.pred[i] = -1;
+            R.succ[i] = -1;
+            R.chain[i] = -1;
+            R.mvpos[i] = -1;
+            R.cgain[i] = 0;
+            R.gseq[i] = 0;
+            R.acc0[i] = 0;
+            R.dDs[i] = 0;
+            R.dDd[i] = 0;
+            R.viol[i] = 0;
+        }
+        if (i < C_N) R.cnt[i] = 0;
+        if (i <= R.rounds) R.linked[i] = 0;
+    }
+}
+
+__global__ void k_rep_nodes(const int32_t *rho, const int32_t *size, const int32_t *singin, int32_t n,
+                            long long *psize, int32_t *D0) {
+    GRID_STRIDE(v, (int64_t)n) {
+        int32_t p = rho[v];
+        atomicAdd((unsigned long long *)&psize[p], (unsigned long long)size[v]);
+        if (singin[v]) atomicAdd(&D0[p], singin[v]);
+    }
+}
+
+__global__ void k_candidates(const long long *saving, int32_t n, int32_t *list, int32_t *cnt) {
+    GRID_STRIDE(v, (int64_t)n) {
+        if (saving[v] > 0) list[atomicAdd(cnt, 1)] = (int32_t)v;
+    }
+}
+
+// ---------------------------------------------------------------- phases
+// Each phase is a strided loop (t0, nt): a kernel runs it over its grid, the
+// single-CTA sequence kernels over their block, with a barrier in between.
+
+// sort keys (p_s, gbound - gain, node): ascending = (p_s asc, gain desc, node asc)
+__device__ void ph_move_keys(const Moves &M, int32_t m, long long gbound, int gb, int nb, int field, uint64_t *keys,
+                             uint32_t *idx, int init_idx, int64_t t0, int64_t nt) {
+    STRIDE(i, m, t0, nt) {
+        if (init_idx) idx[i] = (uint32_t)i;
+        uint32_t k = idx[i];
+        uint64_t g = (uint64_t)(gbound - M.gain[k]);
+        if (field < 0) keys[i] = ((uint64_t)M.src[k] << (gb + nb)) | (g << nb) | (uint64_t)M.node[k];
+        else keys[i] = field == 0 ? (uint64_t)M.node[k] : field == 1 ? g : (uint64_t)M.src[k];
+    }
+}
+__device__ void ph_gather(const Moves &M, const uint32_t *idx, int32_t m, const Moves &S, int32_t *pc, int64_t t0,
+                          int64_t nt) {
+    STRIDE(i, m, t0, nt) {
         uint32_t k = idx[i];
         S.node[i] = M.node[k];
         S.src[i] = M.src[k];
         S.dst[i] = M.dst[k];
         S.gain[i] = M.gain[k];
+        atomicAdd(&pc[M.src[k]], 1);
     }
-}
-__global__ void k_max_gain(const long long *gain, int32_t m, unsigned long long *gmax) {
-    unsigned long long g = 0;
-    GRID_STRIDE(i, (int64_t)m) g = max(g, (unsigned long long)gain[i]);
-    for (int o = 16; o > 0; o >>= 1) g = max(g, __shfl_down_sync(0xffffffffu, g, o));
-    if ((threadIdx.x & 31) == 0) atomicMax(gmax, g);
-}
-// generic path: keys of one field at a time (stable LSD over three sorts)
-__global__ void k_field_keys(const Moves M, int32_t m, int field, long long gmax, uint64_t *keys, const uint32_t *idx) {
-    GRID_STRIDE(i, (int64_t)m) {
-        uint32_t k = idx[i];
-        keys[i] = field == 0 ? (uint64_t)M.node[k] : field == 1 ? (uint64_t)(gmax - M.gain[k]) : (uint64_t)M.src[k];
-    }
-}
-
-// ---------------------------------------------------------------- chaining
-__global__ void k_part_count(const int32_t *src, int32_t m, int32_t *cnt) {
-    GRID_STRIDE(i, (int64_t)m) atomicAdd(&cnt[src[i]], 1);
 }
 
 struct ChainCtx {
-    int32_t m, window;
+    int32_t window;
     const int32_t *node, *src, *dst, *size, *nin;
     const long long *gain;
-    const int32_t *first;   // [nparts+1]
+    const int32_t *first;   // [nparts+1]: moves leaving p are [first[p], first[p+1])
     int32_t *pred, *succ, *choice;
-    unsigned long long *pen, *minpen;
+    unsigned long long *pen, *minpen;     // general acceptance
     int32_t *accnode;
-    int32_t *linked;
+    unsigned long long *acc[2];           // packed acceptance (penalty < 2^32)
+    int32_t *linked;                      // linked[r]: round r linked something
 };
 
-// every free chain end picks, among the first `window` moves leaving its
-// destination that have no predecessor, the one of maximum grade
-// G = gain(m)*10^7 - 10|size(n)-size(m)| - |nin(n)-nin(m)|, earliest on ties.
-__global__ void k_choose(ChainCtx C) {
-    GRID_STRIDE(i0, (int64_t)C.m) {
+// Sec. VI-C: every free chain end picks, among the first `window` moves
+// leaving its destination that have no predecessor, the one of maximum
+// grade G = gain(m)*10^7 - 10|size(n)-size(m)| - |nin(n)-nin(m)|, earliest on
+// ties.  For a chosen move all choosers share gain(m), so the acceptor of
+// maximum (G, node id) is the chooser of minimum penalty, then maximum id.
+__device__ void ph_choose(const ChainCtx &C, int r, int packed, int32_t m, int64_t t0, int64_t nt) {
+    STRIDE(i0, m, t0, nt) {
         int32_t i = (int32_t)i0;
         C.choice[i] = -1;
+        if (!packed) {
+            C.minpen[i] = ~0ull;
+            C.accnode[i] = -1;
+        }
         if (C.succ[i] >= 0) continue;
         int32_t d = C.dst[i];
         int32_t seen = 0, best = -1;
@@ -521,7 +627,8 @@ __global__ void k_choose(ChainCtx C) {
             int32_t vj = C.node[j];
             long long ds = (long long)C.size[vi] - C.size[vj];
             long long di = (long long)C.nin[vi] - C.nin[vj];
-            unsigned long long pen = 10ull * (unsigned long long)(ds < 0 ? -ds : ds) + (unsigned long long)(di < 0 ? -di : di);
+            unsigned long long pen =
+                10ull * (unsigned long long)(ds < 0 ? -ds : ds) + (unsigned long long)(di < 0 ? -di : di);
             __int128 G = (__int128)C.gain[j] * 10000000 - (__int128)pen;
             if (best < 0 || G > bG) {
                 best = j;
@@ -531,49 +638,58 @@ __global__ void k_choose(ChainCtx C) {
         }
         C.choice[i] = best;
         C.pen[i] = bpen;
+        if (best >= 0 && packed)
+            atomicMax(&C.acc[r & 1][best], ((0xffffffffull - bpen) << 32) | (unsigned long long)(uint32_t)vi);
     }
 }
-// for a chosen move, choosers compare by G; G differs only by the penalty
-__global__ void k_accept_min(ChainCtx C) {
-    GRID_STRIDE(i, (int64_t)C.m) {
+__device__ void ph_accept_min(const ChainCtx &C, int32_t m, int64_t t0, int64_t nt) {
+    STRIDE(i, m, t0, nt) {
         int32_t j = C.choice[i];
         if (j >= 0) atomicMin(&C.minpen[j], C.pen[i]);
     }
 }
-__global__ void k_accept_id(ChainCtx C) {
-    GRID_STRIDE(i, (int64_t)C.m) {
+__device__ void ph_accept_id(const ChainCtx &C, int32_t m, int64_t t0, int64_t nt) {
+    STRIDE(i, m, t0, nt) {
         int32_t j = C.choice[i];
         if (j >= 0 && C.pen[i] == C.minpen[j]) atomicMax(&C.accnode[j], C.node[i]);
     }
 }
-__global__ void k_link(ChainCtx C) {
-    GRID_STRIDE(i, (int64_t)C.m) {
+// link the winners; clear the packed slots of the next round
+__device__ void ph_link(const ChainCtx &C, int r, int packed, int32_t m, int64_t t0, int64_t nt) {
+    STRIDE(i, m, t0, nt) {
         int32_t j = C.choice[i];
-        if (j >= 0 && C.pen[i] == C.minpen[j] && C.accnode[j] == C.node[i]) {
+        bool won = false;
+        if (j >= 0) {
+            if (packed)
+                won = C.acc[r & 1][j] ==
+                      (((0xffffffffull - C.pen[i]) << 32) | (unsigned long long)(uint32_t)C.node[i]);
+            else
+                won = C.pen[i] == C.minpen[j] && C.accnode[j] == C.node[i];
+        }
+        if (won) {
             C.pred[j] = (int32_t)i;
             C.succ[i] = j;
-            *C.linked = 1;
+            C.linked[r] = 1;
         }
+        if (packed) C.acc[(r + 1) & 1][i] = 0;
     }
 }
 
-// ---------------------------------------------------------------- chain order
 struct SeqCtx {
-    int32_t m;
     const int32_t *node, *pred, *succ;
     const long long *gain;
     int32_t *chain, *pos, *clen;
     long long *cgain;
     uint32_t *err;
 };
-__global__ void k_path_heads(SeqCtx S) {
-    GRID_STRIDE(i0, (int64_t)S.m) {
+__device__ void ph_path_heads(const SeqCtx &S, int32_t m, int64_t t0, int64_t nt) {
+    STRIDE(i0, m, t0, nt) {
         int32_t i = (int32_t)i0;
         if (S.pred[i] >= 0) continue;
         long long g = 0;
         int32_t k = 0;
         for (int32_t j = i; j >= 0; j = S.succ[j]) {
-            if (k > S.m) {
+            if (k > m) {
                 atomicOr(S.err, E_TIMEOUT);
                 break;
             }
@@ -586,13 +702,13 @@ __global__ void k_path_heads(SeqCtx S) {
     }
 }
 // moves left unassigned lie on cycles; the member of smallest node id heads it
-__global__ void k_cycle_heads(SeqCtx S) {
-    GRID_STRIDE(i0, (int64_t)S.m) {
+__device__ void ph_cycle_heads(const SeqCtx &S, int32_t m, int64_t t0, int64_t nt) {
+    STRIDE(i0, m, t0, nt) {
         int32_t i = (int32_t)i0;
         if (S.chain[i] >= 0) continue;
         int32_t mn = S.node[i], k = 0;
         for (int32_t j = S.succ[i]; j != i; j = S.succ[j]) {
-            if (j < 0 || ++k > S.m) {
+            if (j < 0 || ++k > m) {
                 atomicOr(S.err, E_INTERNAL);
                 mn = -1;
                 break;
@@ -607,228 +723,158 @@ __global__ void k_cycle_heads(SeqCtx S) {
             S.pos[j] = c++;
             g += S.gain[j];
             j = S.succ[j];
-        } while (j != i && c <= S.m);
+        } while (j != i && c <= m);
         S.clen[i] = c;
         S.cgain[i] = g;
     }
 }
-__global__ void k_head_flags(const int32_t *chain, int32_t m, int32_t *flag) {
-    GRID_STRIDE(i, (int64_t)m) flag[i] = chain[i] == (int32_t)i ? 1 : 0;
-}
-__global__ void k_head_compact(const int32_t *flag, const int32_t *pos, int32_t m, uint32_t *heads) {
-    GRID_STRIDE(i, (int64_t)m) {
-        if (flag[i]) heads[pos[i]] = (uint32_t)i;
+__device__ void ph_head_collect(const SeqCtx &S, int32_t m, uint32_t *heads, int32_t *nh, int64_t t0, int64_t nt) {
+    STRIDE(i, m, t0, nt) {
+        if (S.chain[i] == (int32_t)i) heads[atomicAdd(nh, 1)] = (uint32_t)i;
     }
 }
-__global__ void k_head_keys(const uint32_t *heads, int32_t nh, const long long *cgain, const int32_t *node,
-                            long long gmax, int nb, int field, uint64_t *keys) {
-    GRID_STRIDE(k, (int64_t)nh) {
+// key (cgbound - chain gain, head node): ascending = (total gain desc, head node asc)
+__device__ void ph_head_keys(const uint32_t *heads, int32_t nh, const long long *cgain, const int32_t *node,
+                             long long cgbound, int nb, int field, uint64_t *keys, int64_t t0, int64_t nt) {
+    STRIDE(k, nh, t0, nt) {
         uint32_t h = heads[k];
-        uint64_t gk = (uint64_t)(gmax - cgain[h]);
+        uint64_t gk = (uint64_t)(cgbound - cgain[h]);
         if (field < 0) keys[k] = (gk << nb) | (uint64_t)node[h];
         else keys[k] = field == 0 ? (uint64_t)node[h] : gk;
     }
 }
-__global__ void k_chain_lens(const uint32_t *heads, int32_t nh, const int32_t *clen, int32_t *lens) {
-    GRID_STRIDE(k, (int64_t)nh) lens[k] = clen[heads[k]];
+__device__ void ph_chain_lens(const uint32_t *heads, int32_t nh, const int32_t *clen, int64_t cap, int32_t *lens,
+                              int64_t t0, int64_t nt) {
+    STRIDE(k, cap, t0, nt) lens[k] = k < nh ? clen[heads[k]] : 0;
 }
-__global__ void k_chain_start(const uint32_t *heads, int32_t nh, const int32_t *starts, int32_t *cstart) {
-    GRID_STRIDE(k, (int64_t)nh) cstart[heads[k]] = starts[k];
+__device__ void ph_chain_start(const uint32_t *heads, int32_t nh, const int32_t *starts, int32_t *cstart, int64_t t0,
+                               int64_t nt) {
+    STRIDE(k, nh, t0, nt) cstart[heads[k]] = starts[k];
 }
-__global__ void k_seq_pos(const int32_t *chain, const int32_t *pos, const int32_t *cstart, int32_t m, int32_t *seqpos,
-                          int32_t *seqmove) {
-    GRID_STRIDE(i, (int64_t)m) {
+__device__ void ph_seq_pos(const int32_t *chain, const int32_t *pos, const int32_t *cstart, int32_t m,
+                           const int32_t *node, int32_t *seqmove, int32_t *mvpos, int64_t t0, int64_t nt) {
+    STRIDE(i, m, t0, nt) {
         int32_t k = cstart[chain[i]] + pos[i];
-        seqpos[i] = k;
         seqmove[k] = (int32_t)i;
+        mvpos[node[i]] = k;
     }
 }
 
-// ---------------------------------------------------------------- in-sequence gains
-// Events of move k (node v: s -> d) on every e in I(v): (e, s, k, -1) and
-// (e, d, k, +1).  Sorted by (e, p, k), each (e, p) run is walked with the
-// running pins(p,e) and pins_in(p,e): a -1 event that empties e in p spares
-// w(e), a +1 event that enters an empty p costs w(e) (Eq. 14-15 read as the
-// exact change of connectivity); inbound 1->0 and 0->1 transitions give the
-// distinct-inbound events of Sec. VI-D.
-__global__ void k_ev_count(const int32_t *seqmove, const int32_t *node, const int32_t *ioff, int32_t m,
-                           int32_t *cnt) {
-    GRID_STRIDE(k, (int64_t)m) {
-        int32_t v = node[seqmove[k]];
-        cnt[k] = 2 * (ioff[v + 1] - ioff[v]);
-    }
-}
-struct EvCtx {
-    int32_t m, e_bits, p_bits, k_bits;
-    const int32_t *seqmove, *node, *src, *dst, *ioff, *inc, *nin;
-    const int32_t *evoff;
-    uint64_t *keys;
-    uint32_t *vals;   // bit 0: +1 event, bit 1: inbound (v is a destination of e)
-};
-__global__ void k_ev_gen(EvCtx E) {
-    GRID_STRIDE(k, (int64_t)E.m) {
-        int32_t i = E.seqmove[k];
-        int32_t v = E.node[i], s = E.src[i], d = E.dst[i];
-        int32_t o = E.evoff[k];
-        int32_t a = E.ioff[v], b = E.ioff[v + 1], mi = a + E.nin[v];
-        for (int32_t t = a; t < b; t++) {
-            uint64_t e = (uint64_t)E.inc[t];
-            uint32_t inb = t < mi ? 2u : 0u;
-            E.keys[o] = (((e << E.p_bits) | (uint64_t)s) << E.k_bits) | (uint64_t)k;
-            E.vals[o] = inb;
-            o++;
-            E.keys[o] = (((e << E.p_bits) | (uint64_t)d) << E.k_bits) | (uint64_t)k;
-            E.vals[o] = inb | 1u;
-            o++;
-        }
-    }
-}
-
-__device__ __forceinline__ int32_t plist_find(const Plist &PL, int32_t a, int32_t lam, int32_t p) {
-    int32_t lo = 0, hi = lam;
-    while (lo < hi) {
-        int32_t mid = (lo + hi) >> 1;
-        if (PL.p[a + mid] < p) lo = mid + 1;
-        else hi = mid;
-    }
-    return (lo < lam && PL.p[a + lo] == p) ? a + lo : -1;
-}
-
-struct WalkCtx {
-    int64_t nev;
-    int32_t p_bits, k_bits;
-    const uint64_t *keys;
-    const uint32_t *vals;
-    const int32_t *off, *w;
-    Plist PL;
-    unsigned long long *gseq;   // [m] (two's complement sums)
-    uint64_t *dkeys;            // distinct-inbound events: key (p, k)
-    int32_t *dvals;             // +1 / -1
-    int32_t *dcount;
-};
-__global__ void k_ev_walk(WalkCtx W) {
-    const uint64_t kmask = (1ull << W.k_bits) - 1, pmask = (1ull << W.p_bits) - 1;
-    GRID_STRIDE(i, W.nev) {
-        uint64_t key = W.keys[i];
-        uint64_t ep = key >> W.k_bits;
-        if (i > 0 && (W.keys[i - 1] >> W.k_bits) == ep) continue;   // not the head of its (e, p) run
-        int32_t e = (int32_t)(ep >> W.p_bits), p = (int32_t)(ep & pmask);
-        int32_t a = W.off[e];
-        int32_t f = plist_find(W.PL, a, W.PL.lam[e], p);
-        int32_t c = f >= 0 ? W.PL.cnt[f] : 0, ci = f >= 0 ? W.PL.cin[f] : 0;
-        const long long we = W.w[e];
-        for (int64_t j = i; j < W.nev && (W.keys[j] >> W.k_bits) == ep; j++) {
-            int32_t k = (int32_t)(W.keys[j] & kmask);
-            uint32_t val = W.vals[j];
-            bool plus = val & 1u, inb = val & 2u;
-            if (plus) {
-                if (c == 0) atomicAdd(&W.gseq[k], (unsigned long long)(-we));
-                c++;
-                if (inb) {
-                    if (ci == 0) {
-                        int32_t o = atomicAdd(W.dcount, 1);
-                        W.dkeys[o] = ((uint64_t)p << W.k_bits) | (uint64_t)k;
-                        W.dvals[o] = 1;
-                    }
-                    ci++;
-                }
-            } else {
-                if (c == 1) atomicAdd(&W.gseq[k], (unsigned long long)we);
-                c--;
-                if (inb) {
-                    ci--;
-                    if (ci == 0) {
-                        int32_t o = atomicAdd(W.dcount, 1);
-                        W.dkeys[o] = ((uint64_t)p << W.k_bits) | (uint64_t)k;
-                        W.dvals[o] = -1;
-                    }
-                }
-            }
-        }
-    }
-}
-
-// ---------------------------------------------------------------- validity
-// All capacity events of the sequence, keyed (p, k): size events (-size at
-// p_s, +size at p_d) and distinct-inbound events.  Per part, walk them in
-// sequence order and record every change of the part's validity at k.
+// Sec. VI-D: two capacity entries per move k, in sequence order: at p_s
+// (-size, dD_s) and at p_d (+size, dD_d); sorted stably by part, each part's
+// entries are walked in sequence order and each change of its validity is
+// recorded at the move that caused it.
 struct ValCtx {
-    int64_t nev;
-    int32_t k_bits;
-    const uint64_t *keys;
-    const uint32_t *idx;       // index into the payload arrays
-    const long long *dsize;
-    const int32_t *dd;
+    const int32_t *seqmove, *size, *singin, *dDs, *dDd, *D0;
+    const unsigned long long *gseq;
+    Moves S;
     const long long *psize;
-    const int32_t *D0;
+    uint32_t *vkey, *vidx;
+    long long *vsz;
+    int32_t *vdd, *viol;
     int32_t omega, delta;
-    int32_t *viol;             // [m] change of the number of invalid parts at k
 };
-__global__ void k_size_events(const int32_t *seqmove, const int32_t *node, const int32_t *src, const int32_t *dst,
-                              const int32_t *size, int32_t m, int32_t k_bits, uint64_t *keys, long long *dsize,
-                              int32_t *dd, int64_t base) {
-    GRID_STRIDE(k, (int64_t)m) {
-        int32_t i = seqmove[k];
-        long long sz = size[node[i]];
-        keys[base + 2 * k] = ((uint64_t)src[i] << k_bits) | (uint64_t)k;
-        dsize[base + 2 * k] = -sz;
-        dd[base + 2 * k] = 0;
-        keys[base + 2 * k + 1] = ((uint64_t)dst[i] << k_bits) | (uint64_t)k;
-        dsize[base + 2 * k + 1] = sz;
-        dd[base + 2 * k + 1] = 0;
+__device__ void ph_val_entries(const ValCtx &V, int32_t m, int64_t t0, int64_t nt) {
+    STRIDE(k, m, t0, nt) {
+        int32_t i = V.seqmove[k];
+        int32_t v = V.S.node[i];
+        long long sz = V.size[v];
+        V.vkey[2 * k] = (uint32_t)V.S.src[i];
+        V.vidx[2 * k] = (uint32_t)(2 * k);
+        V.vsz[2 * k] = -sz;
+        V.vdd[2 * k] = V.dDs[k] - V.singin[v];
+        V.vkey[2 * k + 1] = (uint32_t)V.S.dst[i];
+        V.vidx[2 * k + 1] = (uint32_t)(2 * k + 1);
+        V.vsz[2 * k + 1] = sz;
+        V.vdd[2 * k + 1] = V.dDd[k] + V.singin[v];
     }
 }
-__global__ void k_d_events(const uint64_t *dkeys, const int32_t *dvals, int32_t nd, uint64_t *keys, long long *dsize,
-                           int32_t *dd) {
-    GRID_STRIDE(i, (int64_t)nd) {
-        keys[i] = dkeys[i];
-        dsize[i] = 0;
-        dd[i] = dvals[i];
-    }
-}
-__global__ void k_val_walk(ValCtx V) {
-    const uint64_t kmask = (1ull << V.k_bits) - 1;
-    GRID_STRIDE(i, V.nev) {
-        uint64_t key = V.keys[i];
-        uint64_t p64 = key >> V.k_bits;
-        if (i > 0 && (V.keys[i - 1] >> V.k_bits) == p64) continue;
-        int32_t p = (int32_t)p64;
-        long long sz = V.psize[p];
-        long long dcnt = V.D0[p];
-        bool valid = sz <= V.omega && dcnt <= V.delta;
-        int64_t j = i;
-        while (j < V.nev && (V.keys[j] >> V.k_bits) == p64) {
-            uint64_t kk = V.keys[j] & kmask;
-            while (j < V.nev && V.keys[j] == ((p64 << V.k_bits) | kk)) {
-                uint32_t x = V.idx[j];
-                sz += V.dsize[x];
-                dcnt += V.dd[x];
-                j++;
-            }
-            bool nv = sz <= V.omega && dcnt <= V.delta;
-            if (nv != valid) atomicAdd(&V.viol[kk], nv ? -1 : 1);
-            valid = nv;
+__device__ void ph_val_walk(const ValCtx &V, int32_t c, int64_t t0, int64_t nt) {
+    STRIDE(i, c, t0, nt) {
+        uint32_t p = V.vkey[i];
+        if (i > 0 && V.vkey[i - 1] == p) continue;
+        long long sz = V.psize[p], dc = V.D0[p];
+        bool valid = sz <= V.omega && dc <= V.delta;
+        for (int64_t j = i; j < c && V.vkey[j] == p; j++) {
+            uint32_t x = V.vidx[j];
+            sz += V.vsz[x];
+            dc += V.vdd[x];
+            bool nv2 = sz <= V.omega && dc <= V.delta;
+            if (nv2 != valid) atomicAdd(&V.viol[x >> 1], nv2 ? -1 : 1);
+            valid = nv2;
         }
     }
 }
-__global__ void k_initial_bad(const long long *psize, const int32_t *D0, int32_t nparts, int32_t omega, int32_t delta,
-                              int32_t *bad) {
+__device__ int32_t ph_initial_bad(const long long *psize, const int32_t *D0, int32_t nparts, int32_t omega,
+                                  int32_t delta, int64_t t0, int64_t nt) {
     int32_t c = 0;
-    GRID_STRIDE(p, (int64_t)nparts) c += (psize[p] > omega || D0[p] > delta) ? 1 : 0;
-    for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
-    if ((threadIdx.x & 31) == 0) atomicAdd(bad, c);
+    STRIDE(p, nparts, t0, nt) c += (psize[p] > omega || D0[p] > delta) ? 1 : 0;
+    return c;
+}
+__device__ void ph_apply(const int32_t *seqmove, const int32_t *node, const int32_t *dst, int32_t L, int32_t *rho,
+                         int64_t t0, int64_t nt) {
+    STRIDE(k, L, t0, nt) {
+        int32_t i = seqmove[k];
+        rho[node[i]] = dst[i];
+    }
 }
 
-// best prefix: max cumulative gain with zero invalid parts, longest on ties
-__global__ void __launch_bounds__(1024) k_best_prefix(const unsigned long long *gseq, const int32_t *violc, int32_t m,
-                                                      const int32_t *bad0, int32_t *best_len, long long *best_gain) {
+// ---- block-level helpers of the single-CTA kernels (blockDim = SEQ_T)
+__device__ int32_t block_sum(int32_t x, int32_t *s_tmp) {
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    if ((threadIdx.x & 31) == 0) s_tmp[threadIdx.x >> 5] = x;
+    __syncthreads();
+    int32_t t = 0;
+    if (threadIdx.x < 32) {
+        t = threadIdx.x < (blockDim.x >> 5) ? s_tmp[threadIdx.x] : 0;
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+        if (threadIdx.x == 0) s_tmp[32] = t;
+    }
+    __syncthreads();
+    t = s_tmp[32];
+    __syncthreads();
+    return t;
+}
+// exclusive prefix sum of in[0..n) into out, by one CTA
+__device__ void block_scan_excl(const int32_t *in, int32_t *out, int64_t n, int32_t *s_tmp) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    int32_t carry = 0;
+    for (int64_t base = 0; base < n; base += blockDim.x) {
+        int64_t i = base + threadIdx.x;
+        int32_t x = i < n ? in[i] : 0, inc = x;
+        for (int o = 1; o < 32; o <<= 1) {
+            int32_t u = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += u;
+        }
+        if (lane == 31) s_tmp[wid] = inc;
+        __syncthreads();
+        if (wid == 0) {
+            int32_t y = lane < nw ? s_tmp[lane] : 0, yi = y;
+            for (int o = 1; o < 32; o <<= 1) {
+                int32_t u = __shfl_up_sync(0xffffffffu, yi, o);
+                if (lane >= o) yi += u;
+            }
+            if (lane < nw) s_tmp[lane] = yi - y;
+            if (lane == nw - 1) s_tmp[32] = yi;
+        }
+        __syncthreads();
+        if (i < n) out[i] = carry + s_tmp[wid] + inc - x;
+        carry += s_tmp[32];
+        __syncthreads();
+    }
+}
+
+// best prefix (Sec. VI-D): max cumulative gain over prefixes with zero
+// invalid parts, longest on ties; one CTA of 1024 threads
+__device__ void best_prefix_block(const unsigned long long *gseq, const int32_t *violc, int32_t m, int32_t bad0,
+                                  int32_t *best_len, long long *best_gain) {
     __shared__ long long s_g[32];
     __shared__ int32_t s_k[32];
     __shared__ long long s_carry_g;
     __shared__ int32_t s_carry_v;
     if (threadIdx.x == 0) {
         s_carry_g = 0;
-        s_carry_v = *bad0;
+        s_carry_v = bad0;
     }
     __syncthreads();
     long long bestg = 0;
@@ -838,7 +884,6 @@ __global__ void __launch_bounds__(1024) k_best_prefix(const unsigned long long *
         int32_t k = base + threadIdx.x;
         long long g = k < m ? (long long)gseq[k] : 0;
         int32_t dv = k < m ? violc[k] : 0;
-        // block inclusive scans of g and dv
         long long gi = g;
         int32_t vi = dv;
         for (int o = 1; o < 32; o <<= 1) {
@@ -884,7 +929,6 @@ __global__ void __launch_bounds__(1024) k_best_prefix(const unsigned long long *
         }
         __syncthreads();
     }
-    // reduce (bestg, bestk): larger gain, then larger k
     for (int o = 16; o > 0; o >>= 1) {
         long long og = __shfl_down_sync(0xffffffffu, bestg, o);
         int32_t ok = __shfl_down_sync(0xffffffffu, bestk, o);
@@ -907,383 +951,685 @@ __global__ void __launch_bounds__(1024) k_best_prefix(const unsigned long long *
         *best_gain = bestg;
         *best_len = bestg > 0 ? bestk : 0;
     }
+    __syncthreads();
 }
 
+// ---------------------------------------------------------------- multi-kernel path
+__global__ void k_move_keys(const Moves M, const int32_t *cntp, long long gbound, int gb, int nb, int field,
+                            uint64_t *keys, uint32_t *idx, int init_idx) {
+    ph_move_keys(M, *cntp, gbound, gb, nb, field, keys, idx, init_idx, G_T0, G_NT);
+}
+__global__ void k_gather_moves(const Moves M, const uint32_t *idx, const int32_t *cntp, Moves S, int32_t *pc) {
+    ph_gather(M, idx, *cntp, S, pc, G_T0, G_NT);
+}
+__global__ void k_choose(ChainCtx C, const int32_t *mcount, int r, int packed) {
+    if (r > 0 && !C.linked[r - 1]) return;
+    ph_choose(C, r, packed, *mcount, G_T0, G_NT);
+}
+__global__ void k_accept_min(ChainCtx C, const int32_t *mcount, int r) {
+    if (r > 0 && !C.linked[r - 1]) return;
+    ph_accept_min(C, *mcount, G_T0, G_NT);
+}
+__global__ void k_accept_id(ChainCtx C, const int32_t *mcount, int r) {
+    if (r > 0 && !C.linked[r - 1]) return;
+    ph_accept_id(C, *mcount, G_T0, G_NT);
+}
+__global__ void k_link(ChainCtx C, const int32_t *mcount, int r, int packed) {
+    if (r > 0 && !C.linked[r - 1]) return;
+    ph_link(C, r, packed, *mcount, G_T0, G_NT);
+}
+__global__ void k_path_heads(SeqCtx S, const int32_t *mcount) { ph_path_heads(S, *mcount, G_T0, G_NT); }
+__global__ void k_cycle_heads(SeqCtx S, const int32_t *mcount) { ph_cycle_heads(S, *mcount, G_T0, G_NT); }
+__global__ void k_head_collect(SeqCtx S, const int32_t *mcount, uint32_t *heads, int32_t *nh) {
+    ph_head_collect(S, *mcount, heads, nh, G_T0, G_NT);
+}
+__global__ void k_head_keys(const uint32_t *heads, const int32_t *nh, const long long *cgain, const int32_t *node,
+                            long long cgbound, int nb, int field, uint64_t *keys) {
+    ph_head_keys(heads, *nh, cgain, node, cgbound, nb, field, keys, G_T0, G_NT);
+}
+__global__ void k_chain_lens(const uint32_t *heads, const int32_t *nh, const int32_t *clen, int32_t cap,
+                             int32_t *lens) {
+    ph_chain_lens(heads, *nh, clen, cap, lens, G_T0, G_NT);
+}
+__global__ void k_chain_start(const uint32_t *heads, const int32_t *nh, const int32_t *starts, int32_t *cstart) {
+    ph_chain_start(heads, *nh, starts, cstart, G_T0, G_NT);
+}
+__global__ void k_seq_pos(const int32_t *chain, const int32_t *pos, const int32_t *cstart, const int32_t *mcount,
+                          const int32_t *node, int32_t *seqmove, int32_t *mvpos) {
+    ph_seq_pos(chain, pos, cstart, *mcount, node, seqmove, mvpos, G_T0, G_NT);
+}
+__global__ void k_val_entries(ValCtx V, const int32_t *mcount, int32_t *nv) {
+    const int32_t m = *mcount;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *nv = 2 * m;
+    ph_val_entries(V, m, G_T0, G_NT);
+}
+__global__ void k_val_walk(ValCtx V, const int32_t *nv) { ph_val_walk(V, *nv, G_T0, G_NT); }
+__global__ void k_initial_bad(const long long *psize, const int32_t *D0, int32_t nparts, int32_t omega, int32_t delta,
+                              int32_t *bad) {
+    int32_t c = ph_initial_bad(psize, D0, nparts, omega, delta, G_T0, G_NT);
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(bad, c);
+}
+__global__ void __launch_bounds__(1024) k_best_prefix(const unsigned long long *gseq, const int32_t *violc,
+                                                      const int32_t *mcount, const int32_t *bad0, int32_t *best_len,
+                                                      long long *best_gain) {
+    best_prefix_block(gseq, violc, *mcount, *bad0, best_len, best_gain);
+}
 __global__ void k_apply(const int32_t *seqmove, const int32_t *node, const int32_t *dst, const int32_t *lenp,
                         int32_t *rho) {
-    int32_t L = *lenp;
-    GRID_STRIDE(k, (int64_t)L) {
-        int32_t i = seqmove[k];
-        rho[node[i]] = dst[i];
-    }
+    ph_apply(seqmove, node, dst, *lenp, rho, G_T0, G_NT);
 }
 
-// ---------------------------------------------------------------- one repetition
-static int32_t refine_rep(const Level &L, const int32_t *w, int32_t nparts, const Params &P, int32_t *rho,
-                          int second_half, int32_t max_e, const long long *wns, Arena &A, uint32_t *err_dev,
-                          const RepDebug *dbg = nullptr) {
-    cudaStream_t s = A.stream();
-    const int32_t n = L.n;
-    // pins(p,e), D(p), saving(v)
-    Plist PL;
-    PL.p = A.get<int32_t>(L.np);
-    PL.cnt = A.get<int32_t>(L.np);
-    PL.cin = A.get<int32_t>(L.np);
-    PL.lam = A.get<int32_t>(L.e);
-    int32_t *D0 = A.get<int32_t>(nparts);
-    long long *saving = A.get<long long>(n);
-    long long *psize = A.get<long long>(nparts);
-    HPC(cudaMemsetAsync(D0, 0, sizeof(int32_t) * nparts, s));
-    HPC(cudaMemsetAsync(saving, 0, sizeof(long long) * n, s));
-    HPC(cudaMemsetAsync(psize, 0, sizeof(long long) * nparts, s));
-    build_plist(L, w, rho, max_e, PL, D0, saving, A);
-    k_psize<<<grid_of(n, 256), 256, 0, s>>>(rho, L.size, n, psize);
-    HP_LAUNCH_CHECK();
+// ---------------------------------------------------------------- single-CTA path (M <= SMALLM)
+struct SmallSeqArgs {
+    Moves M, S;
+    uint64_t *keys, *hkeys;
+    uint32_t *idx, *heads;
+    int32_t *pc, *first, *lens, *starts, *cstart, *seqmove, *mvpos, *cnt;
+    ChainCtx C;
+    SeqCtx Q;
+    int32_t nparts, rounds, packed, gb, nb, sb, cgb;
+    long long gbound, cgbound;
+};
+// sort of the moves, chaining rounds, chain order, sequence positions
+__global__ void __launch_bounds__(SEQ_T) k_seq_small(SmallSeqArgs A) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ uint32_t s_wc[32 * 256];
+    __shared__ uint32_t s_hist[256];
+    __shared__ int32_t s_tmp[40];
+    const int32_t m = A.cnt[C_MOVES];
+    if (m == 0 || m > SMALLM) return;
+    const int64_t t0 = threadIdx.x, nt = blockDim.x;
+    if (A.sb + A.gb + A.nb <= 64) {
+        ph_move_keys(A.M, m, A.gbound, A.gb, A.nb, -1, A.keys, A.idx, 1, t0, nt);
+        block_radix_sort<uint64_t>(A.keys, A.idx, m, (A.sb + A.gb + A.nb + 7) / 8, SMALLM, smem, s_wc, s_hist);
+    } else {
+        const int fb[3] = {A.nb, A.gb, A.sb};
+        for (int f = 0; f < 3; f++) {
+            __syncthreads();
+            ph_move_keys(A.M, m, A.gbound, A.gb, A.nb, f, A.keys, A.idx, f == 0, t0, nt);
+            block_radix_sort<uint64_t>(A.keys, A.idx, m, (fb[f] + 7) / 8, SMALLM, smem, s_wc, s_hist);
+        }
+    }
+    ph_gather(A.M, A.idx, m, A.S, A.pc, t0, nt);
+    __syncthreads();
+    block_scan_excl(A.pc, A.first, (int64_t)A.nparts + 1, s_tmp);
+    __syncthreads();
+    for (int r = 0; r < A.rounds; r++) {
+        if (r > 0 && !*(volatile int32_t *)&A.C.linked[r - 1]) break;
+        ph_choose(A.C, r, A.packed, m, t0, nt);
+        __syncthreads();
+        if (!A.packed) {
+            ph_accept_min(A.C, m, t0, nt);
+            __syncthreads();
+            ph_accept_id(A.C, m, t0, nt);
+            __syncthreads();
+        }
+        ph_link(A.C, r, A.packed, m, t0, nt);
+        __syncthreads();
+    }
+    ph_path_heads(A.Q, m, t0, nt);
+    __syncthreads();
+    ph_cycle_heads(A.Q, m, t0, nt);
+    __syncthreads();
+    ph_head_collect(A.Q, m, A.heads, &A.cnt[C_NH], t0, nt);
+    __syncthreads();
+    const int32_t nh = *(volatile int32_t *)&A.cnt[C_NH];
+    if (A.cgb + A.nb <= 64) {
+        ph_head_keys(A.heads, nh, A.Q.cgain, A.S.node, A.cgbound, A.nb, -1, A.hkeys, t0, nt);
+        block_radix_sort<uint64_t>(A.hkeys, A.heads, nh, (A.cgb + A.nb + 7) / 8, SMALLM, smem, s_wc, s_hist);
+    } else {
+        for (int f = 0; f < 2; f++) {
+            __syncthreads();
+            ph_head_keys(A.heads, nh, A.Q.cgain, A.S.node, A.cgbound, A.nb, f, A.hkeys, t0, nt);
+            block_radix_sort<uint64_t>(A.hkeys, A.heads, nh, ((f == 0 ? A.nb : A.cgb) + 7) / 8, SMALLM, smem, s_wc,
+                                       s_hist);
+        }
+    }
+    ph_chain_lens(A.heads, nh, A.Q.clen, nh, A.lens, t0, nt);
+    __syncthreads();
+    block_scan_excl(A.lens, A.starts, nh, s_tmp);
+    __syncthreads();
+    ph_chain_start(A.heads, nh, A.starts, A.cstart, t0, nt);
+    __syncthreads();
+    ph_seq_pos(A.Q.chain, A.Q.pos, A.cstart, m, A.S.node, A.seqmove, A.mvpos, t0, nt);
+}
 
-    // moves in isolation (Eq. 13) for nodes that can spare a cut
-    int32_t *cnts = A.get<int32_t>(8);
-    HPC(cudaMemsetAsync(cnts, 0, 8 * sizeof(int32_t), s));
-    int32_t *cl = A.get<int32_t>(n);
-    k_candidates<<<grid_of(n, 256), 256, 0, s>>>(saving, n, cl, cnts + 0);
+// validity of every prefix, best prefix, apply
+__global__ void __launch_bounds__(SEQ_T) k_val_small(ValCtx V, int32_t *cnt, int32_t nparts, int sb, long long *bgain,
+                                                     int32_t *rho) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ uint32_t s_wc[32 * 256];
+    __shared__ uint32_t s_hist[256];
+    __shared__ int32_t s_tmp[40];
+    const int32_t m = cnt[C_MOVES];
+    if (m == 0 || m > SMALLM) return;
+    const int64_t t0 = threadIdx.x, nt = blockDim.x;
+    ph_val_entries(V, m, t0, nt);
+    block_radix_sort<uint32_t>(V.vkey, V.vidx, 2 * m, (sb + 7) / 8, 2 * SMALLM, smem, s_wc, s_hist);
+    ph_val_walk(V, 2 * m, t0, nt);
+    int32_t bad = block_sum(ph_initial_bad(V.psize, V.D0, nparts, V.omega, V.delta, t0, nt), s_tmp);
+    __syncthreads();
+    best_prefix_block(V.gseq, V.viol, m, bad, &cnt[C_APPLIED], bgain);
+    const int32_t L = *(volatile int32_t *)&cnt[C_APPLIED];
+    ph_apply(V.seqmove, V.S.node, V.S.dst, L, rho, t0, nt);
+}
+
+// ---------------------------------------------------------------- in-sequence gains
+// Per hyperedge e with moved pins: its moved pins in sequence order; the
+// running pins(p,e) / pins_in(p,e) of the parts they touch start from the
+// pins list.  A move that empties e in p_s spares w(e), one that enters an
+// empty p_d costs w(e) (Eq. 14-15 read as the exact change of connectivity);
+// an inbound count crossing 1 -> 0 at p_s or 0 -> 1 at p_d changes the
+// distinct-inbound count of that part at that move (Sec. VI-D).
+struct SeqSim {
+    const int32_t *off, *pin, *nsrc, *w, *mvpos, *seqmove, *src, *dst;
+    Plist PL;
+    unsigned long long *gseq;
+    int32_t *dDs, *dDd;
+};
+
+__device__ __forceinline__ int32_t plist_find(const Plist &PL, int32_t a, int32_t lam, int32_t p) {
+    int32_t lo = 0, hi = lam;
+    while (lo < hi) {
+        int32_t mid = (lo + hi) >> 1;
+        if (PL.p[a + mid] < p) lo = mid + 1;
+        else hi = mid;
+    }
+    return (lo < lam && PL.p[a + lo] == p) ? a + lo : -1;
+}
+
+// group of G threads; buffers: bk/bd/ord >= |e|, table tp/tc/tci >= 2|e|
+template <int G>
+__device__ void inseq_edge(const SeqSim &Q, int32_t e, int gt, int32_t *bk, int32_t *bd, int32_t *ord, int32_t *tp,
+                           int32_t *tc, int32_t *tci, int32_t *g_cnt) {
+    const int32_t a = Q.off[e], b = Q.off[e + 1], dst0 = a + Q.nsrc[e];
+    if (gt == 0) *g_cnt = 0;
+    gsync<G>();
+    for (int32_t j = a + gt; j < b; j += G) {
+        int32_t k = Q.mvpos[Q.pin[j]];
+        if (k >= 0) {
+            int32_t s = atomicAdd(g_cnt, 1);
+            bk[s] = k;
+            bd[s] = j >= dst0;
+        }
+    }
+    gsync<G>();
+    const int32_t c = *(volatile int32_t *)g_cnt;
+    if (c == 0) {
+        gsync<G>();
+        return;
+    }
+    for (int32_t i = gt; i < c; i += G) {
+        int32_t k = bk[i], r = 0;
+        for (int32_t t = 0; t < c; t++) r += bk[t] < k;
+        ord[r] = i;
+    }
+    gsync<G>();
+    if (gt == 0) {
+        const long long we = Q.w[e];
+        const int32_t lam = Q.PL.lam[e];
+        int32_t nt = 0;
+        for (int32_t r = 0; r < c; r++) {
+            const int32_t i = ord[r], k = bk[i];
+            const int32_t mi = Q.seqmove[k];
+            const int32_t ps[2] = {Q.src[mi], Q.dst[mi]};
+            int32_t slot[2];
+            for (int h = 0; h < 2; h++) {
+                int32_t x = 0;
+                while (x < nt && tp[x] != ps[h]) x++;
+                if (x == nt) {
+                    int32_t f = plist_find(Q.PL, a, lam, ps[h]);
+                    tp[x] = ps[h];
+                    tc[x] = f >= 0 ? Q.PL.cnt[f] : 0;
+                    tci[x] = f >= 0 ? Q.PL.cin[f] : 0;
+                    nt++;
+                }
+                slot[h] = x;
+            }
+            long long g = 0;
+            if (tc[slot[0]] == 1) g += we;
+            if (tc[slot[1]] == 0) g -= we;
+            if (g) atomicAdd(&Q.gseq[k], (unsigned long long)g);
+            tc[slot[0]]--;
+            tc[slot[1]]++;
+            if (bd[i]) {
+                if (--tci[slot[0]] == 0) atomicAdd(&Q.dDs[k], -1);
+                if (++tci[slot[1]] == 1) atomicAdd(&Q.dDd[k], 1);
+            }
+        }
+    }
+    gsync<G>();
+}
+
+constexpr int IS_T = 128;
+__global__ void __launch_bounds__(IS_T) k_inseq_small(SeqSim Q, const int32_t *list, int32_t count, int32_t emax,
+                                                      const int32_t *mcount) {
+    if (*mcount == 0) return;
+    extern __shared__ __align__(16) int32_t sm[];
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int32_t *base = sm + wid * (9 * emax + 1);
+    int32_t *bk = base, *bd = bk + emax, *ord = bd + emax, *tp = ord + emax, *tc = tp + 2 * emax,
+            *tci = tc + 2 * emax, *gc = tci + 2 * emax;
+    int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t i = warp; i < count; i += nw) inseq_edge<32>(Q, list[i], lane, bk, bd, ord, tp, tc, tci, gc);
+}
+__global__ void __launch_bounds__(256) k_inseq_big(SeqSim Q, const int32_t *list, int32_t count, int32_t emax,
+                                                   int32_t *gbuf, const int32_t *mcount) {
+    if (*mcount == 0) return;
+    __shared__ int32_t gc;
+    int32_t *base = gbuf + (int64_t)blockIdx.x * 9 * (int64_t)emax;
+    int32_t *bk = base, *bd = bk + emax, *ord = bd + emax, *tp = ord + emax, *tc = tp + 2 * emax,
+            *tci = tc + 2 * emax;
+    for (int32_t k = blockIdx.x; k < count; k += gridDim.x)
+        inseq_edge<256>(Q, list[k], threadIdx.x, bk, bd, ord, tp, tc, tci, &gc);
+}
+
+
+// ---------------------------------------------------------------- workspace
+// Allocated once per call for the largest level and reused by every level
+// and repetition.
+struct LevelWs {
+    // capacities
+    int32_t cn, ce, nparts, cmax_e;
+    int64_t cnp;
+    // per level
+    int32_t n, max_e, small_max, n_act, n_big;
+    uint32_t pcap;
+    int32_t *act, *big;
+    long long *wns;
+    int32_t *singin;
+    Plist PL;
+    RepArrays R;
+    int32_t *cl;
+    Moves M, S;
+    uint64_t *keys;
+    uint32_t *idx;
+    int32_t *first, *choice, *accnode, *pos, *clen, *lens, *starts, *cstart, *seqmove;
+    unsigned long long *pen, *minpen, *acc1;
+    uint32_t *heads;
+    uint64_t *hkeys;
+    uint32_t *vkey, *vidx;
+    long long *vsz;
+    int32_t *vdd;
+    int32_t *ovf, *gk;
+    long long *gc;
+    uint32_t gcap;
+    int gnb;
+    int32_t *ptab, *ibuf;
+    uint32_t bcap;
+    int pnb;
+    long long *bgain;
+    int32_t *lvl;   // per-level counters
+};
+
+LevelWs *refine_workspace(int32_t n, int64_t np, int32_t e, int32_t nparts, int32_t max_e, const Params &P,
+                          Arena &A) {
+    cudaStream_t s = A.stream();
+    LevelWs *W = new LevelWs();
+    W->cn = n;
+    W->cnp = np;
+    W->ce = e;
+    W->nparts = nparts;
+    W->cmax_e = max_e;
+    W->act = A.get<int32_t>(e);
+    W->big = A.get<int32_t>(e);
+    W->wns = A.get<long long>(n);
+    W->singin = A.get<int32_t>(n);
+    W->PL.p = A.get<int32_t>(np);
+    W->PL.cnt = A.get<int32_t>(np);
+    W->PL.cin = A.get<int32_t>(np);
+    W->PL.lam = A.get<int32_t>(e);
+    RepArrays &R = W->R;
+    R.nparts = nparts;
+    R.rounds = P.o.chain_rounds;
+    R.cnt = A.get<int32_t>(C_N);
+    R.linked = A.get<int32_t>(P.o.chain_rounds + 1);
+    R.D0 = A.get<int32_t>(nparts);
+    R.psize = A.get<long long>(nparts);
+    R.saving = A.get<long long>(n);
+    R.pc = A.get<int32_t>(nparts + 1);
+    R.pred = A.get<int32_t>(n);
+    R.succ = A.get<int32_t>(n);
+    R.chain = A.get<int32_t>(n);
+    R.mvpos = A.get<int32_t>(n);
+    R.cgain = A.get<long long>(n);
+    R.gseq = A.get<unsigned long long>(n);
+    R.acc0 = A.get<unsigned long long>(n);
+    R.dDs = A.get<int32_t>(n);
+    R.dDd = A.get<int32_t>(n);
+    R.viol = A.get<int32_t>(n);
+    W->cl = A.get<int32_t>(n);
+    for (Moves *m : {&W->M, &W->S}) {
+        m->node = A.get<int32_t>(n);
+        m->src = A.get<int32_t>(n);
+        m->dst = A.get<int32_t>(n);
+        m->gain = A.get<long long>(n);
+        m->count = R.cnt + C_MOVES;
+    }
+    W->keys = A.get<uint64_t>(n);
+    W->idx = A.get<uint32_t>(n);
+    W->first = A.get<int32_t>(nparts + 1);
+    W->choice = A.get<int32_t>(n);
+    W->accnode = A.get<int32_t>(n);
+    W->pen = A.get<unsigned long long>(n);
+    W->minpen = A.get<unsigned long long>(n);
+    W->acc1 = A.get<unsigned long long>(n);
+    W->pos = A.get<int32_t>(n);
+    W->clen = A.get<int32_t>(n);
+    W->lens = A.get<int32_t>(n);
+    W->starts = A.get<int32_t>(n);
+    W->cstart = A.get<int32_t>(n);
+    W->seqmove = A.get<int32_t>(n);
+    W->heads = A.get<uint32_t>(n);
+    W->hkeys = A.get<uint64_t>(n);
+    W->vkey = A.get<uint32_t>(2 * (int64_t)n);
+    W->vidx = A.get<uint32_t>(2 * (int64_t)n);
+    W->vsz = A.get<long long>(2 * (int64_t)n);
+    W->vdd = A.get<int32_t>(2 * (int64_t)n);
+    W->bgain = A.get<long long>(1);
+    W->lvl = A.get<int32_t>(4);
+    // overflow tables of the gain kernel, one per CTA of its fallback grid
+    W->gcap = pow2_at_least(2 * (int64_t)nparts + 2);
+    W->gnb = (int)std::min<int64_t>(num_sms(), std::max<int64_t>(1, ((int64_t)1 << 27) / ((int64_t)W->gcap * 12)));
+    W->ovf = A.get<int32_t>(n);
+    W->gk = A.get<int32_t>((int64_t)W->gnb * W->gcap);
+    W->gc = A.get<long long>((int64_t)W->gnb * W->gcap);
+    fill_i32(W->gk, (int64_t)W->gnb * W->gcap, -1, s);
+    HPC(cudaMemsetAsync(W->gc, 0, sizeof(long long) * W->gnb * W->gcap, s));
+    // hyperedges above 512 pins: tables and buffers in global memory
+    W->ptab = W->ibuf = nullptr;
+    W->pnb = 0;
+    if (max_e > 512) {
+        W->bcap = pow2_at_least(2 * (int64_t)max_e);
+        W->pnb = num_sms() * 2;
+        W->ptab = A.get<int32_t>((int64_t)W->pnb * (3 * (int64_t)W->bcap + 4 * (int64_t)max_e));
+        W->ibuf = A.get<int32_t>((int64_t)W->pnb * 9 * (int64_t)max_e);
+    }
+    return W;
+}
+
+void refine_workspace_free(LevelWs *W, Arena &A) {
+    if (!W) return;
+    for (void *p : std::initializer_list<void *>{
+             W->act, W->big, W->wns, W->singin, W->PL.p, W->PL.cnt, W->PL.cin, W->PL.lam, W->R.cnt, W->R.linked,
+             W->R.D0, W->R.psize, W->R.saving, W->R.pc, W->R.pred, W->R.succ, W->R.chain, W->R.mvpos, W->R.cgain,
+             W->R.gseq, W->R.acc0, W->R.dDs, W->R.dDd, W->R.viol, W->cl, W->M.node, W->M.src, W->M.dst, W->M.gain,
+             W->S.node, W->S.src, W->S.dst, W->S.gain, W->keys, W->idx, W->first, W->choice, W->accnode, W->pen,
+             W->minpen, W->acc1, W->pos, W->clen, W->lens, W->starts, W->cstart, W->seqmove, W->heads, W->hkeys,
+             W->vkey, W->vidx, W->vsz, W->vdd, W->bgain, W->lvl, W->ovf, W->gk, W->gc, W->ptab, W->ibuf})
+        A.release(p);
+    delete W;
+}
+
+// per level: hyperedge classes and per-node constants
+static void level_prepare(const Level &L, const int32_t *w, LevelWs &W, Arena &A) {
+    cudaStream_t s = A.stream();
+    const int32_t n = L.n, e = L.e;
+    W.n = n;
+    W.R.n = n;
+    W.R.e = e;
+    HPC(cudaMemsetAsync(W.lvl, 0, 4 * sizeof(int32_t), s));
+    if (e > 0) {
+        k_max_edge<<<grid_of(e, 256), 256, 0, s>>>(L.off, e, W.lvl + 2);
+        HP_LAUNCH_CHECK();
+    }
+    W.max_e = fetch<int32_t>(W.lvl + 2, s);
+    W.small_max = std::min<int32_t>(std::max<int32_t>(W.max_e, 2), 512);
+    W.pcap = pow2_at_least(2 * (int64_t)W.small_max);
+    if (e > 0) {
+        k_level_edges<<<grid_of(e, 256), 256, 0, s>>>(L.off, e, W.small_max, W.act, W.big, W.lvl);
+        HP_LAUNCH_CHECK();
+    }
+    HPC(cudaMemsetAsync(W.wns, 0, sizeof(long long) * n, s));
+    HPC(cudaMemsetAsync(W.singin, 0, sizeof(int32_t) * n, s));
+    if (L.np > 0) {
+        k_level_nodes<<<grid_of(L.np, 256), 256, 0, s>>>(L.off, L.ioff, L.inc, L.inode, L.nin, w, L.np, W.wns,
+                                                          W.singin);
+        HP_LAUNCH_CHECK();
+    }
+    int32_t hc[2];
+    fetch_bytes(hc, W.lvl, sizeof hc, s);
+    W.n_act = hc[0];
+    W.n_big = hc[1];
+    if (W.n_big > 0 && !W.ptab) throw Error(HP_ERR_INTERNAL, "large hyperedge buffers missing");
+}
+
+// One repetition; returns the number of moves applied.
+static int32_t rep_run(const Level &L, const int32_t *w, const Params &P, int32_t *rho, int second_half, LevelWs &W,
+                       Arena &A, uint32_t *err_dev, const RepDebug *dbg) {
+    cudaStream_t s = A.stream();
+    const int32_t n = L.n, nparts = W.nparts;
+    RepArrays &R = W.R;
+    int32_t *cnt = R.cnt;
+    const int64_t zspan = std::max<int64_t>(std::max<int64_t>(n, (int64_t)nparts + 1),
+                                            std::max<int64_t>((int64_t)C_N, (int64_t)P.o.chain_rounds + 1));
+    k_rep_zero<<<grid_of(zspan, 256), 256, 0, s>>>(R);
     HP_LAUNCH_CHECK();
-    Moves M;
-    M.node = A.get<int32_t>(n);
-    M.src = A.get<int32_t>(n);
-    M.dst = A.get<int32_t>(n);
-    M.gain = A.get<long long>(n);
-    M.count = cnts + 1;
-    int32_t hc[8];
-    fetch_bytes(hc, cnts, sizeof hc, s);
-    GainArgs G{L.off, L.ioff, L.inc, w, rho, L.size, psize, saving, wns, PL, P.omega, second_half, M};
-    if (hc[0] > 0) {
+    k_rep_nodes<<<grid_of(n, 256), 256, 0, s>>>(rho, L.size, W.singin, n, R.psize, R.D0);
+    HP_LAUNCH_CHECK();
+    // pins(p,e), pins_in(p,e), D(p), saving(v)
+    if (W.n_act > 0) {
+        const int per = 3 * (int)W.pcap + 4 * W.small_max + 1;
+        size_t sm = (size_t)per * 4 * (PLW_T / 32);
+        int occ = prepare_kernel((const void *)k_plist_small, PLW_T, sm);
+        int grid = (int)std::min<int64_t>(cdiv(W.n_act, PLW_T / 32), (int64_t)num_sms() * occ);
+        k_plist_small<<<std::max(grid, 1), PLW_T, sm, s>>>(L.off, L.pin, L.nsrc, w, rho, W.n_act, W.act, W.small_max,
+                                                           W.pcap, W.PL, R.D0, R.saving);
+        HP_LAUNCH_CHECK();
+    }
+    if (W.n_big > 0) {
+        k_plist_big<<<W.pnb, 256, 0, s>>>(L.off, L.pin, L.nsrc, w, rho, W.big, W.n_big, W.bcap, W.ptab, W.cmax_e,
+                                           W.PL, R.D0, R.saving);
+        HP_LAUNCH_CHECK();
+    }
+    // moves in isolation (Eq. 13)
+    k_candidates<<<grid_of(n, 256), 256, 0, s>>>(R.saving, n, W.cl, cnt + C_CAND);
+    HP_LAUNCH_CHECK();
+    GainArgs G{L.off, L.ioff, L.inc, w, rho, L.size, R.psize, R.saving, W.wns, W.PL, P.omega, second_half, W.M};
+    {
         uint32_t cap = 2048;
         if (P.o.debug_table_cap > 0) cap = (uint32_t)P.o.debug_table_cap;
         size_t sm = (size_t)cap * 12;
-        HPC(cudaFuncSetAttribute(k_gains_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-        int occ = 0;
-        HPC(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_gains_smem, GN_T, sm));
-        int32_t *ovf = A.get<int32_t>(hc[0]);
-        int grid = std::max(1, std::min<int>(hc[0], num_sms() * std::max(occ, 1)));
-        k_gains_smem<<<grid, GN_T, sm, s>>>(G, cl, hc[0], cap, ovf, cnts + 2);
+        int occ = prepare_kernel((const void *)k_gains_smem, GN_T, sm);
+        int grid = std::max(1, std::min<int>(n, num_sms() * occ));
+        k_gains_smem<<<grid, GN_T, sm, s>>>(G, W.cl, cnt + C_CAND, cap, W.ovf, cnt + C_OVF);
         HP_LAUNCH_CHECK();
-        int32_t novf = fetch<int32_t>(cnts + 2, s);
-        if (novf > 0) {
-            uint32_t gcap = pow2_at_least(2 * (int64_t)nparts + 2);
-            int nb = std::min<int>(novf, num_sms() * 2);
-            int32_t *gk = A.get<int32_t>((int64_t)nb * gcap);
-            long long *gc = A.get<long long>((int64_t)nb * gcap);
-            k_gains_global<<<nb, GN_T, 0, s>>>(G, ovf, novf, gcap, gk, gc, cl, cnts + 3);
-            HP_LAUNCH_CHECK();
-            if (fetch<int32_t>(cnts + 3, s)) throw Error(HP_ERR_INTERNAL, "gain table overflow");
-            A.release(gk);
-            A.release(gc);
-        }
-        A.release(ovf);
+        k_gains_global<<<W.gnb, GN_T, 0, s>>>(G, W.ovf, cnt + C_OVF, W.gcap, W.gk, W.gc, W.cl, cnt + C_BAD);
+        HP_LAUNCH_CHECK();
     }
-    const int32_t m = fetch<int32_t>(M.count, s);
+    int32_t hc[C_N];
+    fetch_bytes(hc, cnt, sizeof hc, s);
+    if (hc[C_BAD]) throw Error(HP_ERR_INTERNAL, "gain table overflow");
+    const int32_t m = hc[C_MOVES];
     if (dbg) *dbg->m = m;
-    A.release(cl);
-    A.release(saving);
-    int32_t applied = 0;
-    if (m > 0) {
-        // sort (p_s asc, gain desc, node asc)
-        unsigned long long *gm = (unsigned long long *)A.get<long long>(1);
-        HPC(cudaMemsetAsync(gm, 0, sizeof(long long), s));
-        k_max_gain<<<grid_of(m, 256), 256, 0, s>>>(M.gain, m, gm);
+    if (m == 0) return 0;
+
+    const long long gbound = std::max<long long>(P.wsum, 1);
+    const int nb = bits_for((uint64_t)std::max(n - 1, 1)), gb = bits_for((uint64_t)gbound),
+              sb = bits_for((uint64_t)std::max(nparts - 1, 1));
+    const long long cgbound = (long long)std::min<double>((double)gbound * (double)std::max(n, 1), 9.0e18);
+    const int cgb = bits_for((uint64_t)cgbound);
+    const int packed = (10ll * P.omega + (long long)P.delta) < 0xffffffffll;
+    ChainCtx C;
+    C.window = P.o.chain_window;
+    C.node = W.S.node;
+    C.src = W.S.src;
+    C.dst = W.S.dst;
+    C.size = L.size;
+    C.nin = L.nin;
+    C.gain = W.S.gain;
+    C.first = W.first;
+    C.pred = R.pred;
+    C.succ = R.succ;
+    C.choice = W.choice;
+    C.pen = W.pen;
+    C.minpen = W.minpen;
+    C.accnode = W.accnode;
+    C.acc[0] = R.acc0;
+    C.acc[1] = W.acc1;
+    C.linked = R.linked;
+    SeqCtx Q{W.S.node, R.pred, R.succ, W.S.gain, R.chain, W.pos, W.clen, R.cgain, err_dev};
+    ValCtx V{W.seqmove, L.size, W.singin, R.dDs, R.dDd, R.D0, R.gseq, W.S, R.psize, W.vkey, W.vidx, W.vsz, W.vdd,
+             R.viol, P.omega, P.delta};
+    const bool small = m <= SMALLM;
+    if (small) {
+        SmallSeqArgs SA{W.M, W.S, W.keys, W.hkeys, W.idx, W.heads, R.pc, W.first, W.lens, W.starts, W.cstart,
+                        W.seqmove, R.mvpos, cnt, C, Q, nparts, P.o.chain_rounds, packed, gb, nb, sb, cgb, gbound,
+                        cgbound};
+        size_t sm = (size_t)SMALLM * 2 * (8 + 4);
+        prepare_kernel((const void *)k_seq_small, SEQ_T, sm);
+        k_seq_small<<<1, SEQ_T, sm, s>>>(SA);
         HP_LAUNCH_CHECK();
-        const long long gmax = (long long)fetch<unsigned long long>(gm, s);
-        const int nb = bits_for((uint64_t)std::max(n - 1, 1)), gb = bits_for((uint64_t)gmax),
-                  sb = bits_for((uint64_t)std::max(nparts - 1, 1));
-        uint64_t *keys = A.get<uint64_t>(m);
-        uint32_t *idx = A.get<uint32_t>(m);
+    } else {
+        // sort (p_s asc, gain desc, node asc)
         if (sb + gb + nb <= 64) {
-            k_move_keys<<<grid_of(m, 256), 256, 0, s>>>(M, M.count, gmax, gb, nb, keys, idx);
+            k_move_keys<<<grid_of(m, 256), 256, 0, s>>>(W.M, cnt + C_MOVES, gbound, gb, nb, -1, W.keys, W.idx, 1);
             HP_LAUNCH_CHECK();
-            radix_sort(keys, idx, m, sb + gb + nb, A);
+            radix_sort_dev(W.keys, W.idx, cnt + C_MOVES, m, sb + gb + nb, A);
         } else {
-            iota_i32(reinterpret_cast<int32_t *>(idx), m, s);
             const int fb[3] = {nb, gb, sb};
             for (int f = 0; f < 3; f++) {
-                k_field_keys<<<grid_of(m, 256), 256, 0, s>>>(M, m, f, gmax, keys, idx);
+                k_move_keys<<<grid_of(m, 256), 256, 0, s>>>(W.M, cnt + C_MOVES, gbound, gb, nb, f, W.keys, W.idx,
+                                                            f == 0);
                 HP_LAUNCH_CHECK();
-                radix_sort(keys, idx, m, fb[f], A);
+                radix_sort_dev(W.keys, W.idx, cnt + C_MOVES, m, fb[f], A);
             }
         }
-        Moves S;
-        S.node = A.get<int32_t>(m);
-        S.src = A.get<int32_t>(m);
-        S.dst = A.get<int32_t>(m);
-        S.gain = A.get<long long>(m);
-        S.count = M.count;
-        k_gather_moves<<<grid_of(m, 256), 256, 0, s>>>(M, idx, m, S);
+        k_gather_moves<<<grid_of(m, 256), 256, 0, s>>>(W.M, W.idx, cnt + C_MOVES, W.S, R.pc);
         HP_LAUNCH_CHECK();
-        A.release(keys);
-        A.release(idx);
-        if (dbg) {
-            HPC(cudaMemcpyAsync(dbg->node, S.node, sizeof(int32_t) * m, cudaMemcpyDeviceToDevice, s));
-            HPC(cudaMemcpyAsync(dbg->src, S.src, sizeof(int32_t) * m, cudaMemcpyDeviceToDevice, s));
-            HPC(cudaMemcpyAsync(dbg->dst, S.dst, sizeof(int32_t) * m, cudaMemcpyDeviceToDevice, s));
-            HPC(cudaMemcpyAsync(dbg->gain, S.gain, sizeof(long long) * m, cudaMemcpyDeviceToDevice, s));
-        }
-        A.release(gm);
-
+        scan_excl(R.pc, W.first, nparts + 1, nullptr, A);
         // chaining (Sec. VI-C)
-        int32_t *pc = A.get<int32_t>(nparts + 1);
-        int32_t *first = A.get<int32_t>(nparts + 1);
-        HPC(cudaMemsetAsync(pc, 0, sizeof(int32_t) * (nparts + 1), s));
-        k_part_count<<<grid_of(m, 256), 256, 0, s>>>(S.src, m, pc);
-        HP_LAUNCH_CHECK();
-        scan_excl(pc, first, nparts + 1, nullptr, A);
-        ChainCtx C;
-        C.m = m;
-        C.window = P.o.chain_window;
-        C.node = S.node;
-        C.src = S.src;
-        C.dst = S.dst;
-        C.size = L.size;
-        C.nin = L.nin;
-        C.gain = S.gain;
-        C.first = first;
-        C.pred = A.get<int32_t>(m);
-        C.succ = A.get<int32_t>(m);
-        C.choice = A.get<int32_t>(m);
-        C.pen = A.get<unsigned long long>(m);
-        C.minpen = A.get<unsigned long long>(m);
-        C.accnode = A.get<int32_t>(m);
-        C.linked = cnts + 4;
-        fill_i32(C.pred, m, -1, s);
-        fill_i32(C.succ, m, -1, s);
         for (int32_t r = 0; r < P.o.chain_rounds; r++) {
-            HPC(cudaMemsetAsync(C.minpen, 0xff, sizeof(unsigned long long) * m, s));
-            fill_i32(C.accnode, m, -1, s);
-            HPC(cudaMemsetAsync(C.linked, 0, sizeof(int32_t), s));
-            k_choose<<<grid_of(m, 128), 128, 0, s>>>(C);
+            k_choose<<<grid_of(m, 128), 128, 0, s>>>(C, cnt + C_MOVES, r, packed);
             HP_LAUNCH_CHECK();
-            k_accept_min<<<grid_of(m, 256), 256, 0, s>>>(C);
-            HP_LAUNCH_CHECK();
-            k_accept_id<<<grid_of(m, 256), 256, 0, s>>>(C);
-            HP_LAUNCH_CHECK();
-            k_link<<<grid_of(m, 256), 256, 0, s>>>(C);
-            HP_LAUNCH_CHECK();
-            if (!fetch<int32_t>(C.linked, s)) break;
-        }
-        A.release(C.choice);
-        A.release(C.pen);
-        A.release(C.minpen);
-        A.release(C.accnode);
-        A.release(pc);
-        A.release(first);
-
-        // chains in order of (total gain desc, head node asc)
-        SeqCtx Q;
-        Q.m = m;
-        Q.node = S.node;
-        Q.pred = C.pred;
-        Q.succ = C.succ;
-        Q.gain = S.gain;
-        Q.chain = A.get<int32_t>(m);
-        Q.pos = A.get<int32_t>(m);
-        Q.clen = A.get<int32_t>(m);
-        Q.cgain = A.get<long long>(m);
-        Q.err = err_dev;
-        HPC(cudaMemsetAsync(Q.cgain, 0, sizeof(long long) * m, s));
-        fill_i32(Q.chain, m, -1, s);
-        k_path_heads<<<grid_of(m, 256), 256, 0, s>>>(Q);
-        HP_LAUNCH_CHECK();
-        k_cycle_heads<<<grid_of(m, 256), 256, 0, s>>>(Q);
-        HP_LAUNCH_CHECK();
-        int32_t *hflag = A.get<int32_t>(m);
-        int32_t *hpos = A.get<int32_t>(m + 1);
-        k_head_flags<<<grid_of(m, 256), 256, 0, s>>>(Q.chain, m, hflag);
-        HP_LAUNCH_CHECK();
-        scan_excl(hflag, hpos, m, hpos + m, A);
-        const int32_t nh = fetch<int32_t>(hpos + m, s);
-        uint32_t *heads = A.get<uint32_t>(nh);
-        k_head_compact<<<grid_of(m, 256), 256, 0, s>>>(hflag, hpos, m, heads);
-        HP_LAUNCH_CHECK();
-        {
-            unsigned long long *cg = (unsigned long long *)A.get<long long>(1);
-            HPC(cudaMemsetAsync(cg, 0, sizeof(long long), s));
-            k_max_gain<<<grid_of(m, 256), 256, 0, s>>>(Q.cgain, m, cg);  // chain gains are >= 0 at heads, 0 elsewhere
-            HP_LAUNCH_CHECK();
-            const long long cgmax = (long long)fetch<unsigned long long>(cg, s);
-            const int cgb = bits_for((uint64_t)cgmax);
-            uint64_t *hk = A.get<uint64_t>(nh);
-            if (cgb + nb <= 64) {
-                k_head_keys<<<grid_of(nh, 256), 256, 0, s>>>(heads, nh, Q.cgain, S.node, cgmax, nb, -1, hk);
+            if (!packed) {
+                k_accept_min<<<grid_of(m, 256), 256, 0, s>>>(C, cnt + C_MOVES, r);
                 HP_LAUNCH_CHECK();
-                radix_sort(hk, heads, nh, cgb + nb, A);
-            } else {
-                for (int f = 0; f < 2; f++) {
-                    k_head_keys<<<grid_of(nh, 256), 256, 0, s>>>(heads, nh, Q.cgain, S.node, cgmax, nb, f, hk);
-                    HP_LAUNCH_CHECK();
-                    radix_sort(hk, heads, nh, f == 0 ? nb : cgb, A);
-                }
+                k_accept_id<<<grid_of(m, 256), 256, 0, s>>>(C, cnt + C_MOVES, r);
+                HP_LAUNCH_CHECK();
             }
-            A.release(hk);
-            A.release(cg);
-        }
-        int32_t *lens = A.get<int32_t>(nh + 1);
-        int32_t *starts = A.get<int32_t>(nh + 1);
-        k_chain_lens<<<grid_of(nh, 256), 256, 0, s>>>(heads, nh, Q.clen, lens);
-        HP_LAUNCH_CHECK();
-        scan_excl(lens, starts, nh, nullptr, A);
-        int32_t *cstart = A.get<int32_t>(m);
-        k_chain_start<<<grid_of(nh, 256), 256, 0, s>>>(heads, nh, starts, cstart);
-        HP_LAUNCH_CHECK();
-        int32_t *seqpos = A.get<int32_t>(m);
-        int32_t *seqmove = A.get<int32_t>(m);
-        k_seq_pos<<<grid_of(m, 256), 256, 0, s>>>(Q.chain, Q.pos, cstart, m, seqpos, seqmove);
-        HP_LAUNCH_CHECK();
-        if (dbg) HPC(cudaMemcpyAsync(dbg->seq, seqmove, sizeof(int32_t) * m, cudaMemcpyDeviceToDevice, s));
-        A.release(lens);
-        A.release(starts);
-        A.release(cstart);
-        A.release(heads);
-        A.release(hflag);
-        A.release(hpos);
-        A.release(Q.chain);
-        A.release(Q.pos);
-        A.release(Q.clen);
-        A.release(Q.cgain);
-        A.release(C.pred);
-        A.release(C.succ);
-
-        // in-sequence gains and distinct-inbound events
-        int32_t *evc = A.get<int32_t>(m);
-        int32_t *evoff = A.get<int32_t>(m + 1);
-        k_ev_count<<<grid_of(m, 256), 256, 0, s>>>(seqmove, S.node, L.ioff, m, evc);
-        HP_LAUNCH_CHECK();
-        scan_excl(evc, evoff, m, evoff + m, A);
-        const int32_t nev = fetch<int32_t>(evoff + m, s);
-        const int e_bits = bits_for((uint64_t)std::max(L.e - 1, 1));
-        const int p_bits = bits_for((uint64_t)std::max(nparts - 1, 1));
-        const int k_bits = bits_for((uint64_t)std::max(m - 1, 1));
-        if (e_bits + p_bits + k_bits > 64) throw Error(HP_ERR_INTERNAL, "event key wider than 64 bits");
-        unsigned long long *gseq = (unsigned long long *)A.get<long long>(m);
-        HPC(cudaMemsetAsync(gseq, 0, sizeof(long long) * m, s));
-        uint64_t *dkeys = A.get<uint64_t>(nev);
-        int32_t *dvals = A.get<int32_t>(nev);
-        if (nev > 0) {
-            uint64_t *ek = A.get<uint64_t>(nev);
-            uint32_t *ev = A.get<uint32_t>(nev);
-            EvCtx E{m, e_bits, p_bits, k_bits, seqmove, S.node, S.src, S.dst, L.ioff, L.inc, L.nin, evoff, ek, ev};
-            k_ev_gen<<<grid_of(m, 128), 128, 0, s>>>(E);
-            HP_LAUNCH_CHECK();
-            radix_sort(ek, ev, nev, e_bits + p_bits + k_bits, A);
-            WalkCtx W{nev, p_bits, k_bits, ek, ev, L.off, w, PL, gseq, dkeys, dvals, cnts + 5};
-            k_ev_walk<<<grid_of(nev, 256), 256, 0, s>>>(W);
-            HP_LAUNCH_CHECK();
-            A.release(ek);
-            A.release(ev);
-        }
-        A.release(evc);
-        A.release(evoff);
-        const int32_t nd = fetch<int32_t>(cnts + 5, s);
-
-        // validity of every prefix (Sec. VI-D)
-        const int64_t nv = (int64_t)nd + 2 * (int64_t)m;
-        uint64_t *vk = A.get<uint64_t>(nv);
-        uint32_t *vi = A.get<uint32_t>(nv);
-        long long *vds = A.get<long long>(nv);
-        int32_t *vdd = A.get<int32_t>(nv);
-        if (nd > 0) {
-            k_d_events<<<grid_of(nd, 256), 256, 0, s>>>(dkeys, dvals, nd, vk, vds, vdd);
+            k_link<<<grid_of(m, 256), 256, 0, s>>>(C, cnt + C_MOVES, r, packed);
             HP_LAUNCH_CHECK();
         }
-        k_size_events<<<grid_of(m, 256), 256, 0, s>>>(seqmove, S.node, S.src, S.dst, L.size, m, k_bits, vk, vds, vdd,
-                                                      nd);
+        // chains in order of (total gain desc, head node asc)
+        k_path_heads<<<grid_of(m, 256), 256, 0, s>>>(Q, cnt + C_MOVES);
         HP_LAUNCH_CHECK();
-        iota_i32(reinterpret_cast<int32_t *>(vi), nv, s);
-        radix_sort(vk, vi, nv, p_bits + k_bits, A);
-        int32_t *viol = A.get<int32_t>(m);
-        HPC(cudaMemsetAsync(viol, 0, sizeof(int32_t) * m, s));
-        ValCtx V{nv, k_bits, vk, vi, vds, vdd, psize, D0, P.omega, P.delta, viol};
-        k_val_walk<<<grid_of(nv, 256), 256, 0, s>>>(V);
+        k_cycle_heads<<<grid_of(m, 256), 256, 0, s>>>(Q, cnt + C_MOVES);
         HP_LAUNCH_CHECK();
-        k_initial_bad<<<grid_of(nparts, 256), 256, 0, s>>>(psize, D0, nparts, P.omega, P.delta, cnts + 6);
+        k_head_collect<<<grid_of(m, 256), 256, 0, s>>>(Q, cnt + C_MOVES, W.heads, cnt + C_NH);
         HP_LAUNCH_CHECK();
-        long long *bgain = A.get<long long>(1);
-        k_best_prefix<<<1, 1024, 0, s>>>(gseq, viol, m, cnts + 6, cnts + 7, bgain);
-        HP_LAUNCH_CHECK();
-        k_apply<<<grid_of(m, 256), 256, 0, s>>>(seqmove, S.node, S.dst, cnts + 7, rho);
-        HP_LAUNCH_CHECK();
-        applied = fetch<int32_t>(cnts + 7, s);
-        if (dbg) {
-            HPC(cudaMemcpyAsync(dbg->gseq, gseq, sizeof(long long) * m, cudaMemcpyDeviceToDevice, s));
-            HPC(cudaMemcpyAsync(dbg->best_gain, bgain, sizeof(long long), cudaMemcpyDeviceToDevice, s));
+        if (cgb + nb <= 64) {
+            k_head_keys<<<grid_of(m, 256), 256, 0, s>>>(W.heads, cnt + C_NH, R.cgain, W.S.node, cgbound, nb, -1,
+                                                         W.hkeys);
+            HP_LAUNCH_CHECK();
+            radix_sort_dev(W.hkeys, W.heads, cnt + C_NH, m, cgb + nb, A);
+        } else {
+            for (int f = 0; f < 2; f++) {
+                k_head_keys<<<grid_of(m, 256), 256, 0, s>>>(W.heads, cnt + C_NH, R.cgain, W.S.node, cgbound, nb, f,
+                                                             W.hkeys);
+                HP_LAUNCH_CHECK();
+                radix_sort_dev(W.hkeys, W.heads, cnt + C_NH, m, f == 0 ? nb : cgb, A);
+            }
         }
-        A.release(vk);
-        A.release(vi);
-        A.release(vds);
-        A.release(vdd);
-        A.release(viol);
-        A.release(bgain);
-        A.release(dkeys);
-        A.release(dvals);
-        A.release(gseq);
-        A.release(seqpos);
-        A.release(seqmove);
-        A.release(S.node);
-        A.release(S.src);
-        A.release(S.dst);
-        A.release(S.gain);
+        k_chain_lens<<<grid_of(m, 256), 256, 0, s>>>(W.heads, cnt + C_NH, W.clen, m, W.lens);
+        HP_LAUNCH_CHECK();
+        scan_excl(W.lens, W.starts, m, nullptr, A);
+        k_chain_start<<<grid_of(m, 256), 256, 0, s>>>(W.heads, cnt + C_NH, W.starts, W.cstart);
+        HP_LAUNCH_CHECK();
+        k_seq_pos<<<grid_of(m, 256), 256, 0, s>>>(R.chain, W.pos, W.cstart, cnt + C_MOVES, W.S.node, W.seqmove,
+                                                  R.mvpos);
+        HP_LAUNCH_CHECK();
     }
-    A.release(M.node);
-    A.release(M.src);
-    A.release(M.dst);
-    A.release(M.gain);
-    A.release(cnts);
-    A.release(PL.p);
-    A.release(PL.cnt);
-    A.release(PL.cin);
-    A.release(PL.lam);
-    A.release(D0);
-    A.release(psize);
-    return applied;
+    if (dbg) {
+        HPC(cudaMemcpyAsync(dbg->node, W.S.node, sizeof(int32_t) * m, cudaMemcpyDeviceToDevice, s));
+        HPC(cudaMemcpyAsync(dbg->src, W.S.src, sizeof(int32_t) * m, cudaMemcpyDeviceToDevice, s));
+        HPC(cudaMemcpyAsync(dbg->dst, W.S.dst, sizeof(int32_t) * m, cudaMemcpyDeviceToDevice, s));
+        HPC(cudaMemcpyAsync(dbg->gain, W.S.gain, sizeof(long long) * m, cudaMemcpyDeviceToDevice, s));
+        HPC(cudaMemcpyAsync(dbg->seq, W.seqmove, sizeof(int32_t) * m, cudaMemcpyDeviceToDevice, s));
+    }
+
+    // in-sequence gains and distinct-inbound changes per move
+    SeqSim Z{L.off, L.pin, L.nsrc, w, R.mvpos, W.seqmove, W.S.src, W.S.dst, W.PL, R.gseq, R.dDs, R.dDd};
+    if (W.n_act > 0) {
+        size_t sm = (size_t)(9 * W.small_max + 1) * 4 * (IS_T / 32);
+        int occ = prepare_kernel((const void *)k_inseq_small, IS_T, sm);
+        int grid = (int)std::min<int64_t>(cdiv(W.n_act, IS_T / 32), (int64_t)num_sms() * occ);
+        k_inseq_small<<<std::max(grid, 1), IS_T, sm, s>>>(Z, W.act, W.n_act, W.small_max, cnt + C_MOVES);
+        HP_LAUNCH_CHECK();
+    }
+    if (W.n_big > 0) {
+        k_inseq_big<<<W.pnb, 256, 0, s>>>(Z, W.big, W.n_big, W.cmax_e, W.ibuf, cnt + C_MOVES);
+        HP_LAUNCH_CHECK();
+    }
+
+    // validity of every prefix (Sec. VI-D), best valid prefix, apply
+    if (small) {
+        size_t sm = (size_t)2 * SMALLM * 2 * (4 + 4);
+        prepare_kernel((const void *)k_val_small, SEQ_T, sm);
+        k_val_small<<<1, SEQ_T, sm, s>>>(V, cnt, nparts, sb, W.bgain, rho);
+        HP_LAUNCH_CHECK();
+    } else {
+        k_val_entries<<<grid_of(m, 256), 256, 0, s>>>(V, cnt + C_MOVES, cnt + C_NV);
+        HP_LAUNCH_CHECK();
+        radix_sort_dev(W.vkey, W.vidx, cnt + C_NV, 2 * (int64_t)m, sb, A);
+        k_val_walk<<<grid_of(2 * (int64_t)m, 256), 256, 0, s>>>(V, cnt + C_NV);
+        HP_LAUNCH_CHECK();
+        k_initial_bad<<<grid_of(nparts, 256), 256, 0, s>>>(R.psize, R.D0, nparts, P.omega, P.delta, cnt + C_BAD0);
+        HP_LAUNCH_CHECK();
+        k_best_prefix<<<1, 1024, 0, s>>>(R.gseq, R.viol, cnt + C_MOVES, cnt + C_BAD0, cnt + C_APPLIED, W.bgain);
+        HP_LAUNCH_CHECK();
+        k_apply<<<grid_of(m, 256), 256, 0, s>>>(W.seqmove, W.S.node, W.S.dst, cnt + C_APPLIED, rho);
+        HP_LAUNCH_CHECK();
+    }
+    if (dbg) {
+        HPC(cudaMemcpyAsync(dbg->gseq, R.gseq, sizeof(long long) * m, cudaMemcpyDeviceToDevice, s));
+        HPC(cudaMemcpyAsync(dbg->best_gain, W.bgain, sizeof(long long), cudaMemcpyDeviceToDevice, s));
+    }
+    return fetch<int32_t>(cnt + C_APPLIED, s);
+}
+
+__global__ void k_max_edge_i(const int32_t *off, int32_t e, int32_t *maxe) {
+    int32_t m = 0;
+    GRID_STRIDE(i, (int64_t)e) m = max(m, off[i + 1] - off[i]);
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_down_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(maxe, m);
+}
+
+int32_t max_edge_size(const Level &L, Arena &A) {
+    cudaStream_t s = A.stream();
+    int32_t *mx = A.get<int32_t>(1);
+    HPC(cudaMemsetAsync(mx, 0, sizeof(int32_t), s));
+    if (L.e > 0) {
+        k_max_edge_i<<<grid_of(L.e, 256), 256, 0, s>>>(L.off, L.e, mx);
+        HP_LAUNCH_CHECK();
+    }
+    const int32_t r = fetch<int32_t>(mx, s);
+    A.release(mx);
+    return r;
 }
 
 int32_t refine_rep_debug(const Level &L, const int32_t *w, int32_t nparts, const Params &P, int32_t *rho,
                          int second_half, Arena &A, uint32_t *err_dev, const RepDebug &dbg) {
-    cudaStream_t s = A.stream();
-    int32_t *maxe = A.get<int32_t>(1);
-    HPC(cudaMemsetAsync(maxe, 0, sizeof(int32_t), s));
-    if (L.e > 0) {
-        k_max_edge<<<grid_of(L.e, 256), 256, 0, s>>>(L.off, L.e, maxe);
-        HP_LAUNCH_CHECK();
-    }
-    const int32_t max_e = fetch<int32_t>(maxe, s);
-    long long *wns = A.get<long long>(std::max(L.n, 1));
-    if (L.n > 0) {
-        k_wns<<<grid_of(L.n, 256), 256, 0, s>>>(L.off, L.ioff, L.inc, w, L.n, wns);
-        HP_LAUNCH_CHECK();
-    }
     *dbg.m = 0;
-    int32_t k = L.n > 0 ? refine_rep(L, w, nparts, P, rho, second_half, max_e, wns, A, err_dev, &dbg) : 0;
-    A.release(wns);
-    A.release(maxe);
+    if (L.n == 0) return 0;
+    const int32_t max_e = max_edge_size(L, A);
+    LevelWs *W = refine_workspace(L.n, L.np, L.e, nparts, max_e, P, A);
+    level_prepare(L, w, *W, A);
+    int32_t k = rep_run(L, w, P, rho, second_half, *W, A, err_dev, &dbg);
+    refine_workspace_free(W, A);
     return k;
 }
 
-RefineOut refine_level(const Level &L, const int32_t *w, int32_t nparts, const Params &P, int32_t *rho, Arena &A,
+RefineOut refine_level(const Level &L, const int32_t *w, const Params &P, int32_t *rho, LevelWs *W, Arena &A,
                        uint32_t *err_dev) {
-    cudaStream_t s = A.stream();
     RefineOut out;
     if (L.n == 0 || P.o.theta == 0) return out;
-    int32_t *maxe = A.get<int32_t>(1);
-    HPC(cudaMemsetAsync(maxe, 0, sizeof(int32_t), s));
-    if (L.e > 0) {
-        k_max_edge<<<grid_of(L.e, 256), 256, 0, s>>>(L.off, L.e, maxe);
-        HP_LAUNCH_CHECK();
-    }
-    const int32_t max_e = fetch<int32_t>(maxe, s);
-    A.release(maxe);
-    long long *wns = A.get<long long>(L.n);
-    k_wns<<<grid_of(L.n, 256), 256, 0, s>>>(L.off, L.ioff, L.inc, w, L.n, wns);
-    HP_LAUNCH_CHECK();
+    level_prepare(L, w, *W, A);
     const int32_t half = P.o.theta / 2;
     for (int32_t rep = 0; rep < P.o.theta; rep++) {
-        int32_t k = refine_rep(L, w, nparts, P, rho, rep >= half, max_e, wns, A, err_dev);
+        const int32_t k = rep_run(L, w, P, rho, rep >= half, *W, A, err_dev, nullptr);
         out.reps++;
         out.moves += k;
         if (k == 0) {
@@ -1291,13 +1637,8 @@ RefineOut refine_level(const Level &L, const int32_t *w, int32_t nparts, const P
             else break;
         }
     }
-    A.release(wns);
     return out;
 }
-
-}  // namespace hp
-
-namespace hp {
 
 // ---------------------------------------------------------------- final statistics
 __global__ void k_part_sizes(const int32_t *part, int32_t n, long long *psize) {
