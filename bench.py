@@ -108,6 +108,23 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def max_over_ranks(x: float, world: int, device) -> float:
+    """The largest of every rank's x (the slowest replica's time)."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_value(pins_per_replica: int, world: int, ms_slowest: float) -> float:
+    """Whole-job pins/s: every replica partitions its own copy of the
+    workload; the job ends with the slowest one."""
+    return world * pins_per_replica / (ms_slowest / 1e3)
+
+
 def proposal_bytes(stats: dict, num_pins: int, num_nodes: int, pi: int = 4) -> int:
     """Algorithmic bytes of the level-0 candidate proposal: every pin of every
     incident hyperedge once (4 B per visit), size and inbound count of every
@@ -236,13 +253,9 @@ def main():
         ev1.record(stream)
         torch.cuda.synchronize()
         barrier()
-    ms = ev0.elapsed_time(ev1) / args.steps
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ev0.elapsed_time(ev1) / args.steps, world, "cuda")
     clocks = clk.summary()
-    value = world * g.num_pins / (ms / 1e3)
+    value = replica_value(g.num_pins, world, ms)
 
     # end to end through the host entry point: pinned host inputs, H2D + D2H inside
     h_off = torch.from_numpy(g.offsets).pin_memory()
@@ -265,11 +278,7 @@ def main():
     ev1.record(stream)
     torch.cuda.synchronize()
     barrier()
-    ms_e2e = ev0.elapsed_time(ev1) / args.steps
-    if world > 1:
-        t = torch.tensor([ms_e2e], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_e2e = float(t.item())
+    ms_e2e = max_over_ranks(ev0.elapsed_time(ev1) / args.steps, world, "cuda")
     import numpy as np
     assert np.array_equal(h_part.numpy(), part.cpu().numpy()), "host and device entry points disagree"
 
@@ -290,7 +299,7 @@ def main():
                    "violations": last["violations"], "levels": last["levels"],
                    "moves_applied": last["moves_applied"], "ms_coarsen": last["ms_coarsen"],
                    "ms_refine": last["ms_refine"]},
-        "e2e": {"value": world * g.num_pins / (ms_e2e / 1e3), "unit": "pins/s",
+        "e2e": {"value": replica_value(g.num_pins, world, ms_e2e), "unit": "pins/s",
                 "h2d_bytes_per_step": int(g.offsets.nbytes + g.pins.nbytes), "d2h_bytes_per_step": int(4 * n)},
         "roofline": {"bound": "hbm", "kernel": "level-0 candidate proposal (k_propose_smem)", "achieved": achieved,
                      "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic_for_current_kernel(),

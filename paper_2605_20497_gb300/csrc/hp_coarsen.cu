@@ -149,9 +149,10 @@ template <int PIMAX> struct TopList {
 };
 
 // block-wide: write the pi best of the per-thread lists to cand/cscore of v
+// (s_red: 32 entries, s_own: 33 entries; at most 32 warps)
 template <int PIMAX>
-__device__ void block_emit_top(TopList<PIMAX> &tl, const PropCtx &C, int32_t v, Cand *s_red) {
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+__device__ void block_emit_top(TopList<PIMAX> &tl, const PropCtx &C, int32_t v, Cand *s_red, int *s_own) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int r = 0; r < C.pi; r++) {
         Cand best = tl.c[0];
         int owner = threadIdx.x;
@@ -165,24 +166,24 @@ __device__ void block_emit_top(TopList<PIMAX> &tl, const PropCtx &C, int32_t v, 
         }
         if (lane == 0) {
             s_red[wid] = best;
-            reinterpret_cast<int *>(s_red + 16)[wid] = owner;
+            s_own[wid] = owner;
         }
         __syncthreads();
         if (threadIdx.x == 0) {
             Cand b = s_red[0];
-            int ow = reinterpret_cast<int *>(s_red + 16)[0];
-            for (int k = 1; k < (int)(blockDim.x >> 5); k++) {
+            int ow = s_own[0];
+            for (int k = 1; k < nw; k++) {
                 if (cand_gt(s_red[k], b)) {
                     b = s_red[k];
-                    ow = reinterpret_cast<int *>(s_red + 16)[k];
+                    ow = s_own[k];
                 }
             }
             C.cand[(int64_t)v * C.pi + r] = b.id;
             C.cscore[(int64_t)v * C.pi + r] = b.id >= 0 ? b.eta : 0;
-            reinterpret_cast<int *>(s_red + 16)[15] = b.id >= 0 ? ow : -1;
+            s_own[32] = b.id >= 0 ? ow : -1;
         }
         __syncthreads();
-        if (threadIdx.x == reinterpret_cast<int *>(s_red + 16)[15]) tl.pop();
+        if ((int)threadIdx.x == s_own[32]) tl.pop();
         __syncthreads();
     }
 }
@@ -203,20 +204,64 @@ __device__ __forceinline__ int32_t block_sum_i32(int32_t x, int32_t *s_tmp) {
     return t;
 }
 
+// The group's hyperedges of 2..32 pins, one per thread (t = base + tid,
+// base stepping by `step` over v's incidence, uniform across each warp): the
+// j-th pins of a warp's 32 hyperedges are combined by neighbour (match_any)
+// and one table update per distinct neighbour carries the warp's sums of q(e)
+// and of the inbound-overlap counts.  q(e) <= 2^40 is summed as two 21-bit
+// halves so that 32-bit warp reductions cannot overflow.
+template <class Ins>
+__device__ __forceinline__ void small_edges_aggregated(const PropCtx &C, int32_t v, int32_t i0, int32_t deg,
+                                                       int32_t nin_v, int tid, int step, const int *stop, Ins ins) {
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    for (int32_t base = 0; base < deg; base += step) {
+        if (stop && __any_sync(FULL, *(volatile const int *)stop)) break;
+        const int32_t t = base + tid;
+        int32_t a = 0, sz = 0, dst0 = 0;
+        unsigned long long qe = 0;
+        bool vin = false;
+        if (t < deg) {
+            const int32_t e = C.inc[i0 + t];
+            a = C.off[e];
+            sz = C.off[e + 1] - a;
+            if (sz < 2 || sz > 32) {
+                sz = 0;
+            } else {
+                dst0 = a + C.nsrc[e];
+                qe = C.q[e];
+                vin = t < nin_v;
+            }
+        }
+        const int jmax = (int)__reduce_max_sync(FULL, (unsigned)sz);
+        for (int j = 0; j < jmax; j++) {
+            int32_t m = j < sz ? C.pin[a + j] : -1;
+            if (m == v) m = -1;
+            const unsigned g = __match_any_sync(FULL, m);
+            const bool on = m >= 0;
+            const unsigned lo = __reduce_add_sync(g, on ? (unsigned)(qe & 0x1FFFFFull) : 0u);
+            const unsigned hi = __reduce_add_sync(g, on ? (unsigned)(qe >> 21) : 0u);
+            const unsigned ic = __reduce_add_sync(g, (on && vin && a + j >= dst0) ? 1u : 0u);
+            if (on && lane == __ffs(g) - 1) ins(m, (unsigned long long)lo + ((unsigned long long)hi << 21), ic);
+        }
+    }
+}
+
 // ---------------------------------------------------------------- dense table
 // eta[m], inter[m] for every node of the level in shared memory (levels of at
 // most DENSE_N nodes, nodes with large neighbourhoods).
-template <int PIMAX>
-__global__ void __launch_bounds__(PT) k_propose_dense(PropCtx C, const int32_t *list, const int32_t *count_p) {
+template <int PIMAX, int BT>
+__global__ void __launch_bounds__(BT) k_propose_dense(PropCtx C, const int32_t *list, const int32_t *count_p) {
     extern __shared__ __align__(16) unsigned char smem[];
     unsigned long long *eta = reinterpret_cast<unsigned long long *>(smem);
     uint32_t *inter = reinterpret_cast<uint32_t *>(eta + C.n);
-    __shared__ Cand s_red[16 + 8];
+    __shared__ Cand s_red[32];
+    __shared__ int s_own[33];
     __shared__ int32_t s_tmp[32];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = PT / 32;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = BT / 32;
     const int32_t count = *count_p;
     if (count == 0) return;
-    for (int32_t i = threadIdx.x; i < C.n; i += PT) {
+    for (int32_t i = threadIdx.x; i < C.n; i += BT) {
         eta[i] = 0;
         inter[i] = 0;
     }
@@ -225,27 +270,12 @@ __global__ void __launch_bounds__(PT) k_propose_dense(PropCtx C, const int32_t *
     for (int32_t k = blockIdx.x; k < count; k += gridDim.x) {
         const int32_t v = list[k];
         const int32_t i0 = C.ioff[v], deg = C.ioff[v + 1] - i0, nin_v = C.nin[v];
-        {   // hyperedges of 2..32 pins: one per thread, repeated neighbours combined in registers
-            RegCache<4> rc;
-            rc.init();
-            auto flush = [&](int32_t m, unsigned long long eq, uint32_t ic) {
-                atomicAdd(&eta[m], eq);
-                if (ic) atomicAdd(&inter[m], ic);
-            };
-            for (int32_t t = threadIdx.x; t < deg; t += PT) {
-                const int32_t e = C.inc[i0 + t];
-                const int32_t a = C.off[e], b = C.off[e + 1];
-                if (b - a < 2 || b - a > 32) continue;
-                const int32_t dst0 = a + C.nsrc[e];
-                const unsigned long long qe = C.q[e];
-                const bool vin = t < nin_v;
-                for (int32_t j = a; j < b; j++) {
-                    const int32_t m = C.pin[j];
-                    if (m != v) rc.add(m, qe, (vin && j >= dst0) ? 1u : 0u, flush);
-                }
-            }
-            rc.drain(flush);
-        }
+        // hyperedges of 2..32 pins: one per thread, combined across each warp
+        small_edges_aggregated(C, v, i0, deg, nin_v, (int)threadIdx.x, BT, nullptr,
+                               [&](int32_t m, unsigned long long eq, uint32_t ic) {
+                                   atomicAdd(&eta[m], eq);
+                                   if (ic) atomicAdd(&inter[m], ic);
+                               });
         for (int32_t t = wid; t < deg; t += nw) {   // larger hyperedges: lanes over pins
             const int32_t e = C.inc[i0 + t];
             const int32_t a = C.off[e], b = C.off[e + 1];
@@ -264,7 +294,7 @@ __global__ void __launch_bounds__(PT) k_propose_dense(PropCtx C, const int32_t *
         TopList<PIMAX> tl;
         tl.init();
         int32_t cnt = 0;
-        for (int32_t m = threadIdx.x; m < C.n; m += PT) {
+        for (int32_t m = threadIdx.x; m < C.n; m += BT) {
             unsigned long long em = eta[m];
             if (em) {
                 cnt++;
@@ -276,7 +306,7 @@ __global__ void __launch_bounds__(PT) k_propose_dense(PropCtx C, const int32_t *
         }
         int32_t tot = block_sum_i32(cnt, s_tmp);
         if (threadIdx.x == 0) C.nbcnt[v] = tot;
-        block_emit_top<PIMAX>(tl, C, v, s_red);
+        block_emit_top<PIMAX>(tl, C, v, s_red, s_own);
     }
 }
 
@@ -331,26 +361,11 @@ __global__ void __launch_bounds__(WP_T) k_propose_warp(PropCtx C, const int32_t 
     for (int64_t k = gw; k < count; k += nw) {
         const int32_t v = list[k];
         const int32_t i0 = C.ioff[v], deg = C.ioff[v + 1] - i0, nin_v = C.nin[v];
-        {   // hyperedges of 2..32 pins: one per lane, repeated neighbours combined in registers
-            RegCache<4> rc;
-            rc.init();
-            auto flush = [&](int32_t m, unsigned long long eq, uint32_t ic) {
-                warp_insert(keys, eta, inter, mask, cap, m, eq, ic);
-            };
-            for (int32_t t = lane; t < deg; t += 32) {
-                const int32_t e = C.inc[i0 + t];
-                const int32_t a = C.off[e], b = C.off[e + 1];
-                if (b - a < 2 || b - a > 32) continue;
-                const int32_t dst0 = a + C.nsrc[e];
-                const unsigned long long qe = C.q[e];
-                const bool vin = t < nin_v;
-                for (int32_t j = a; j < b; j++) {
-                    const int32_t m = C.pin[j];
-                    if (m != v) rc.add(m, qe, (vin && j >= dst0) ? 1u : 0u, flush);
-                }
-            }
-            rc.drain(flush);
-        }
+        // hyperedges of 2..32 pins: one per lane, combined across the warp
+        small_edges_aggregated(C, v, i0, deg, nin_v, lane, 32, nullptr,
+                               [&](int32_t m, unsigned long long eq, uint32_t ic) {
+                                   warp_insert(keys, eta, inter, mask, cap, m, eq, ic);
+                               });
         // larger hyperedges: lanes over pins
         for (int32_t t = 0; t < deg; t++) {
             const int32_t e = C.inc[i0 + t];
@@ -411,8 +426,9 @@ __device__ __forceinline__ uint32_t hslot(int32_t m, uint32_t mask) {
 // limit is appended to ovf (and its table cleared).
 template <int PIMAX>
 __device__ void propose_hashed_node(const PropCtx &C, int32_t v, int32_t *keys, unsigned long long *eta,
-                                    uint32_t *inter, uint32_t cap, uint32_t limit, int32_t *ovf, int32_t *ovf_n,
-                                    int *s_flag, int32_t *s_cnt, Cand *s_red, int32_t *s_tmp) {
+                                    uint32_t *inter, uint32_t cap, uint32_t limit, int32_t *slots, int32_t *ovf,
+                                    int32_t *ovf_n, int *s_flag, int32_t *s_cnt, Cand *s_red, int *s_own,
+                                    int32_t *s_tmp) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const uint32_t mask = cap - 1;
     const int32_t i0 = C.ioff[v], deg = C.ioff[v + 1] - i0, nin_v = C.nin[v];
@@ -423,7 +439,9 @@ __device__ void propose_hashed_node(const PropCtx &C, int32_t v, int32_t *keys, 
             if (k == -1) {
                 int32_t old = atomicCAS(&keys[h], -1, m);
                 if (old == -1) {
-                    if ((uint32_t)atomicAdd(s_cnt, 1) + 1 > limit) *(volatile int *)s_flag = 1;
+                    const uint32_t slot = (uint32_t)atomicAdd(s_cnt, 1);
+                    if (slot < limit) slots[slot] = (int32_t)h;
+                    else *(volatile int *)s_flag = 1;
                     k = m;
                 } else {
                     k = old;
@@ -438,26 +456,9 @@ __device__ void propose_hashed_node(const PropCtx &C, int32_t v, int32_t *keys, 
         }
     };
     auto insert = [&](int32_t m, unsigned long long qe, bool add_inter) { insert_n(m, qe, add_inter ? 1u : 0u); };
-    // hyperedges of 2..32 pins: one per thread, repeated neighbours combined in registers
-    {
-        RegCache<4> rc;
-        rc.init();
-        auto flush = [&](int32_t m, unsigned long long eq, uint32_t ic) { insert_n(m, eq, ic); };
-        for (int32_t t = threadIdx.x; t < deg; t += blockDim.x) {
-            if (*(volatile int *)s_flag) break;
-            const int32_t e = C.inc[i0 + t];
-            const int32_t a = C.off[e], b = C.off[e + 1];
-            if (b - a < 2 || b - a > 32) continue;
-            const int32_t dst0 = a + C.nsrc[e];
-            const unsigned long long qe = C.q[e];
-            const bool vin = t < nin_v;
-            for (int32_t j = a; j < b; j++) {
-                const int32_t m = C.pin[j];
-                if (m != v) rc.add(m, qe, (vin && j >= dst0) ? 1u : 0u, flush);
-            }
-        }
-        rc.drain(flush);
-    }
+    // hyperedges of 2..32 pins: one per thread, combined across each warp
+    small_edges_aggregated(C, v, i0, deg, nin_v, (int)threadIdx.x, (int)blockDim.x, s_flag,
+                           [&](int32_t m, unsigned long long eq, uint32_t ic) { insert_n(m, eq, ic); });
     // larger hyperedges: a warp each, lanes over pins
     for (int32_t t = wid; t < deg; t += nw) {
         if (*(volatile int *)s_flag) break;
@@ -477,21 +478,13 @@ __device__ void propose_hashed_node(const PropCtx &C, int32_t v, int32_t *keys, 
     const uint64_t capn = *C.cap;
     TopList<PIMAX> tl;
     tl.init();
-    int32_t cnt = 0;
-    for (uint32_t h = threadIdx.x; h < cap; h += blockDim.x) {
-        int32_t m = keys[h];
-        if (m >= 0) {
-            if (!overflow) {
-                cnt++;
-                int32_t it = (int32_t)inter[h];
-                if (pair_valid(C, v, m, it)) tl.push(Cand{eta[h] + pair_noise(C.level_key, v, m, capn), m});
-            }
+    if (overflow) {
+        // the slot list is incomplete: clear the whole table, redo the node in a larger one
+        for (uint32_t h = threadIdx.x; h < cap; h += blockDim.x) {
             keys[h] = -1;
             eta[h] = 0;
             inter[h] = 0;
         }
-    }
-    if (overflow) {
         __syncthreads();
         if (threadIdx.x == 0) {
             ovf[atomicAdd(ovf_n, 1)] = v;
@@ -501,28 +494,41 @@ __device__ void propose_hashed_node(const PropCtx &C, int32_t v, int32_t *keys, 
         __syncthreads();
         return;
     }
-    int32_t tot = block_sum_i32(cnt, s_tmp);
+    // only the occupied slots, from the slot list
+    const int32_t used = *(volatile int32_t *)s_cnt;
+    for (int32_t i = threadIdx.x; i < used; i += blockDim.x) {
+        const int32_t h = slots[i];
+        const int32_t m = keys[h];
+        if (pair_valid(C, v, m, (int32_t)inter[h])) tl.push(Cand{eta[h] + pair_noise(C.level_key, v, m, capn), m});
+        keys[h] = -1;
+        eta[h] = 0;
+        inter[h] = 0;
+    }
+    int32_t tot = used;
+    __syncthreads();
     if (threadIdx.x == 0) {
         C.nbcnt[v] = tot;
         *s_cnt = 0;
     }
-    block_emit_top<PIMAX>(tl, C, v, s_red);
+    block_emit_top<PIMAX>(tl, C, v, s_red, s_own);
 }
 
-template <int PIMAX>
-__global__ void __launch_bounds__(PT) k_propose_smem(PropCtx C, const int32_t *list, const int32_t *count_p,
+template <int PIMAX, int BT>
+__global__ void __launch_bounds__(BT) k_propose_smem(PropCtx C, const int32_t *list, const int32_t *count_p,
                                                      uint32_t cap, uint32_t limit, int32_t *ovf, int32_t *ovf_n) {
     extern __shared__ __align__(16) unsigned char smem[];
     unsigned long long *eta = reinterpret_cast<unsigned long long *>(smem);
     uint32_t *inter = reinterpret_cast<uint32_t *>(eta + cap);
     int32_t *keys = reinterpret_cast<int32_t *>(inter + cap);
-    __shared__ Cand s_red[16 + 8];
+    int32_t *slots = keys + cap;
+    __shared__ Cand s_red[32];
+    __shared__ int s_own[33];
     __shared__ int32_t s_tmp[32];
     __shared__ int s_flag;
     __shared__ int32_t s_cnt;
     const int32_t count = *count_p;
     if (count == 0) return;
-    for (uint32_t i = threadIdx.x; i < cap; i += PT) {
+    for (uint32_t i = threadIdx.x; i < cap; i += BT) {
         keys[i] = -1;
         eta[i] = 0;
         inter[i] = 0;
@@ -533,8 +539,8 @@ __global__ void __launch_bounds__(PT) k_propose_smem(PropCtx C, const int32_t *l
     }
     __syncthreads();
     for (int32_t k = blockIdx.x; k < count; k += gridDim.x)
-        propose_hashed_node<PIMAX>(C, list[k], keys, eta, inter, cap, limit, ovf, ovf_n, &s_flag, &s_cnt, s_red,
-                                   s_tmp);
+        propose_hashed_node<PIMAX>(C, list[k], keys, eta, inter, cap, limit, slots, ovf, ovf_n, &s_flag, &s_cnt,
+                                   s_red, s_own, s_tmp);
 }
 
 // one CTA region of gcap slots in global memory per CTA (clean on entry and
@@ -542,8 +548,10 @@ __global__ void __launch_bounds__(PT) k_propose_smem(PropCtx C, const int32_t *l
 template <int PIMAX>
 __global__ void __launch_bounds__(PT) k_propose_global(PropCtx C, const int32_t *list, const int32_t *count_p,
                                                        uint32_t gcap, int32_t *gkeys, unsigned long long *geta,
-                                                       uint32_t *ginter, int32_t *err_list, int32_t *err_n) {
-    __shared__ Cand s_red[16 + 8];
+                                                       uint32_t *ginter, int32_t *gslots, int32_t *err_list,
+                                                       int32_t *err_n) {
+    __shared__ Cand s_red[32];
+    __shared__ int s_own[33];
     __shared__ int32_t s_tmp[32];
     __shared__ int s_flag;
     __shared__ int32_t s_cnt;
@@ -556,17 +564,26 @@ __global__ void __launch_bounds__(PT) k_propose_global(PropCtx C, const int32_t 
     }
     __syncthreads();
     for (int32_t k = blockIdx.x; k < count; k += gridDim.x)
-        propose_hashed_node<PIMAX>(C, list[k], gkeys + o, geta + o, ginter + o, gcap, gcap - 1, err_list, err_n,
-                                   &s_flag, &s_cnt, s_red, s_tmp);
+        propose_hashed_node<PIMAX>(C, list[k], gkeys + o, geta + o, ginter + o, gcap, gcap - 1, gslots + o, err_list,
+                                   err_n, &s_flag, &s_cnt, s_red, s_own, s_tmp);
 }
 
 // ---------------------------------------------------------------- node tiers
-// warp tier: small neighbourhood bound and little traversal work
-constexpr long long WARP_VISITS = 4096;
-__global__ void k_tiers(const int32_t *bound, const long long *vis, int32_t n, uint32_t warp_limit, int32_t *lW,
-                        int32_t *lB, int32_t *cnt) {
+// warp tier: small neighbourhood bound and little traversal work; hub
+// tier: traversals large enough to keep a 1024-thread CTA busy
+// dense tier (level of at most DENSE_N nodes): neighbourhood bound above
+// dense_bound; the others use hashed tables
+constexpr long long WARP_VISITS = 4096, HUB_VISITS = 65536;
+__global__ void k_tiers(const int32_t *bound, const long long *vis, int32_t n, uint32_t warp_limit,
+                        int32_t dense_bound, int32_t *lW, int32_t *lB, int32_t *lH, int32_t *lD, int32_t *lDH,
+                        int32_t *cnt) {
     GRID_STRIDE(v, (int64_t)n) {
+        const bool hub = vis[v] > HUB_VISITS;
         if ((uint32_t)bound[v] <= warp_limit && vis[v] <= WARP_VISITS) lW[atomicAdd(&cnt[0], 1)] = (int32_t)v;
+        else if (bound[v] > dense_bound) {
+            if (hub) lDH[atomicAdd(&cnt[7], 1)] = (int32_t)v;
+            else lD[atomicAdd(&cnt[6], 1)] = (int32_t)v;
+        } else if (hub) lH[atomicAdd(&cnt[5], 1)] = (int32_t)v;
         else lB[atomicAdd(&cnt[1], 1)] = (int32_t)v;
     }
 }
@@ -577,13 +594,14 @@ struct CoarsenWs {
     uint64_t *q;
     int32_t *cand;
     uint64_t *cscore;
-    int32_t *lW, *lB, *lC, *lG, *cnt;   // cnt: 0 W, 1 B, 2 C, 3 G, 4 global errors
+    int32_t *lW, *lB, *lC, *lG, *lH, *lD, *lDH, *cnt;   // cnt: 0 W 1 B 2 C 3 G 4 errors 5 H 6 D 7 DH
     long long *nsum, *vis;             // per node: sum of (|e|-1), sum of |e| over I(v)
     uint32_t gcap;
     int gnb;
     int32_t *gkeys;
     unsigned long long *geta;
     uint32_t *ginter;
+    int32_t *gslots;
     // best-effort pairing and matching
     int32_t *flag, *pos, *target, *ccount, *coff, *fillpos, *kids, *best;
     uint32_t *ikeys, *iids;
@@ -598,8 +616,13 @@ static void run_proposal(const PropCtx &C, Level &L, const Params &P, CoarsenWs 
     const int sms = num_sms();
     const int32_t dbg = P.o.debug_table_cap;
     const uint32_t wcap = dbg > 0 ? std::min<uint32_t>(512, (uint32_t)dbg) : 512;
+    uint32_t capB = 4096, capC = 8192;
+    if (dbg > 0) capB = capC = (uint32_t)dbg;
+    // dense tables only on small levels, for neighbourhoods too large for the first hashed table
+    const int32_t dense_bound = (C.n <= DENSE_N && dbg == 0) ? (int32_t)(capB / 2) : 0x7fffffff;
     HPC(cudaMemsetAsync(W.cnt, 0, 8 * sizeof(int32_t), s));
-    k_tiers<<<grid_of(C.n, 256), 256, 0, s>>>(L.nbnd, W.vis, C.n, wcap / 2, W.lW, W.lB, W.cnt);
+    k_tiers<<<grid_of(C.n, 256), 256, 0, s>>>(L.nbnd, W.vis, C.n, wcap / 2, dense_bound, W.lW, W.lB, W.lH, W.lD,
+                                              W.lDH, W.cnt);
     HP_LAUNCH_CHECK();
     {
         size_t sm = (size_t)wcap * 16 * (WP_T / 32);
@@ -608,28 +631,36 @@ static void run_proposal(const PropCtx &C, Level &L, const Params &P, CoarsenWs 
         k_propose_warp<PIMAX><<<std::max(grid, 1), WP_T, sm, s>>>(C, W.lW, W.cnt + 0, wcap);
         HP_LAUNCH_CHECK();
     }
-    if (C.n <= DENSE_N && dbg == 0) {
+    if (dense_bound != 0x7fffffff) {
         size_t sm = (size_t)C.n * 12;
-        int occ = prepare_kernel((const void *)k_propose_dense<PIMAX>, PT, sm);
-        int grid = std::max(1, std::min<int>(C.n, sms * occ));
-        k_propose_dense<PIMAX><<<grid, PT, sm, s>>>(C, W.lB, W.cnt + 1);
+        int occ = prepare_kernel((const void *)k_propose_dense<PIMAX, PT>, PT, sm);
+        k_propose_dense<PIMAX, PT><<<std::max(1, std::min<int>(C.n, sms * occ)), PT, sm, s>>>(C, W.lD, W.cnt + 6);
         HP_LAUNCH_CHECK();
-        return;
+        prepare_kernel((const void *)k_propose_dense<PIMAX, 1024>, 1024, sm);
+        k_propose_dense<PIMAX, 1024><<<sms, 1024, sm, s>>>(C, W.lDH, W.cnt + 7);
+        HP_LAUNCH_CHECK();
     }
-    uint32_t capB = 4096, capC = 8192;
-    if (dbg > 0) capB = capC = (uint32_t)dbg;
-    auto launch_smem = [&](const int32_t *list, const int32_t *count_p, uint32_t cap, int32_t *ovf, int32_t *ovf_n) {
-        size_t sm = (size_t)cap * 16;
-        int occ = prepare_kernel((const void *)k_propose_smem<PIMAX>, PT, sm);
-        int grid = std::max(1, std::min<int>(C.n, sms * occ));
-        k_propose_smem<PIMAX><<<grid, PT, sm, s>>>(C, list, count_p, cap, cap * 3 / 4, ovf, ovf_n);
+    auto smem_of = [](uint32_t cap) { return (size_t)cap * 16 + (size_t)(cap * 3 / 4) * 4; };
+    {
+        size_t sm = smem_of(capB);
+        int occ = prepare_kernel((const void *)k_propose_smem<PIMAX, 512>, 512, sm);
+        k_propose_smem<PIMAX, 512><<<std::max(1, std::min<int>(C.n, sms * occ)), 512, sm, s>>>(
+            C, W.lB, W.cnt + 1, capB, capB * 3 / 4, W.lC, W.cnt + 2);
         HP_LAUNCH_CHECK();
-    };
-    // tier B may overflow (the bound can be far above the true neighbourhood)
-    launch_smem(W.lB, W.cnt + 1, capB, W.lC, W.cnt + 2);
-    launch_smem(W.lC, W.cnt + 2, capC, W.lG, W.cnt + 3);
-    k_propose_global<PIMAX><<<W.gnb, PT, 0, s>>>(C, W.lG, W.cnt + 3, W.gcap, W.gkeys, W.geta, W.ginter, W.lW,
-                                                  W.cnt + 4);
+        prepare_kernel((const void *)k_propose_smem<PIMAX, 1024>, 1024, sm);
+        k_propose_smem<PIMAX, 1024><<<sms, 1024, sm, s>>>(C, W.lH, W.cnt + 5, capB, capB * 3 / 4, W.lC, W.cnt + 2);
+        HP_LAUNCH_CHECK();
+    }
+    {
+        // nodes whose neighbourhood outgrew the first table (the bound can be far above the truth)
+        size_t sm = smem_of(capC);
+        int occ = prepare_kernel((const void *)k_propose_smem<PIMAX, PT>, PT, sm);
+        k_propose_smem<PIMAX, PT><<<std::max(1, std::min<int>(C.n, sms * occ)), PT, sm, s>>>(
+            C, W.lC, W.cnt + 2, capC, capC * 3 / 4, W.lG, W.cnt + 3);
+        HP_LAUNCH_CHECK();
+    }
+    k_propose_global<PIMAX><<<W.gnb, PT, 0, s>>>(C, W.lG, W.cnt + 3, W.gcap, W.gkeys, W.geta, W.ginter, W.gslots,
+                                                  W.lW, W.cnt + 4);
     HP_LAUNCH_CHECK();
 }
 
@@ -707,27 +738,39 @@ struct DpCtx {
 
 // Bottom-up (Eq. 7, 8, 10): a thread starts at every leaf and climbs; the
 // thread completing the last child of a node continues with that node, so a
-// node is evaluated once, after all of its children.
+// node is evaluated once, after all of its children.  A parent with a single
+// child is reached only by that child's thread: it takes the child's values
+// from registers and needs neither the fence nor the arrival counter, so a
+// long chain costs one dependent load of target per step.
 __global__ void k_dp_up(DpCtx D) {
     GRID_STRIDE(v0, (int64_t)D.n) {
         int32_t v = (int32_t)v0;
         if (D.coff[v + 1] != D.coff[v]) continue;   // not a leaf
         if (D.target[v] < 0) continue;              // isolated, no proposal edge
         int32_t cur = v;
+        int32_t hc = -1;                            // child we climbed from (its values below)
+        long long hc0 = 0, hc10 = 0;
         for (int32_t steps = 0;; steps++) {
             if (steps > D.n) {
                 atomicOr(D.err, E_TIMEOUT);
                 break;
             }
+            const int32_t k0 = D.coff[cur], k1 = D.coff[cur + 1];
             long long s0 = 0, bss = 0;
             int32_t b = -1;
-            for (int32_t k = D.coff[cur]; k < D.coff[cur + 1]; k++) {
-                int32_t c = D.kids[k];
-                long long c0 = __ldcg(&D.ss0[c]), c10 = __ldcg(&D.ss10[c]);
-                s0 += c0;
-                if (b < 0 || c10 > bss || (c10 == bss && c > b)) {
-                    b = c;
-                    bss = c10;
+            if (hc >= 0 && k1 - k0 == 1) {
+                s0 = hc0;
+                b = hc;
+                bss = hc10;
+            } else {
+                for (int32_t k = k0; k < k1; k++) {
+                    int32_t c = D.kids[k];
+                    long long c0 = __ldcg(&D.ss0[c]), c10 = __ldcg(&D.ss10[c]);
+                    s0 += c0;
+                    if (b < 0 || c10 > bss || (c10 == bss && c > b)) {
+                        b = c;
+                        bss = c10;
+                    }
                 }
             }
             long long my0 = s0 + ((b >= 0 && bss > 0) ? bss : 0);
@@ -736,10 +779,16 @@ __global__ void k_dp_up(DpCtx D) {
             D.best[cur] = b;
             int32_t t = D.target[cur];
             if (t < 0 || D.target[t] == cur) break;   // a root
-            __stcg(&D.ss10[cur], (long long)D.score[cur] + s0 - my0);
-            __threadfence();
-            if (atomicSub(&D.pending[t], 1) != 1) break;
-            __threadfence();
+            const long long my10 = (long long)D.score[cur] + s0 - my0;
+            __stcg(&D.ss10[cur], my10);
+            if (D.coff[t + 1] - D.coff[t] > 1) {
+                __threadfence();
+                if (atomicSub(&D.pending[t], 1) != 1) break;
+                __threadfence();
+            }
+            hc = cur;
+            hc0 = my0;
+            hc10 = my10;
             cur = t;
         }
     }
@@ -810,6 +859,9 @@ CoarsenWs *coarsen_workspace(int32_t n, int32_t e, const Params &P, Arena &A) {
     W->lB = A.get<int32_t>(n);
     W->lC = A.get<int32_t>(n);
     W->lG = A.get<int32_t>(n);
+    W->lH = A.get<int32_t>(n);
+    W->lD = A.get<int32_t>(n);
+    W->lDH = A.get<int32_t>(n);
     W->cnt = A.get<int32_t>(8);
     W->nsum = A.get<long long>(n);
     W->vis = A.get<long long>(n);
@@ -820,6 +872,7 @@ CoarsenWs *coarsen_workspace(int32_t n, int32_t e, const Params &P, Arena &A) {
     W->gkeys = A.get<int32_t>((int64_t)W->gnb * W->gcap);
     W->geta = A.get<unsigned long long>((int64_t)W->gnb * W->gcap);
     W->ginter = A.get<uint32_t>((int64_t)W->gnb * W->gcap);
+    W->gslots = A.get<int32_t>((int64_t)W->gnb * W->gcap);
     HPC(cudaMemsetAsync(W->gkeys, 0xff, sizeof(int32_t) * W->gnb * W->gcap, s));
     HPC(cudaMemsetAsync(W->geta, 0, sizeof(unsigned long long) * W->gnb * W->gcap, s));
     HPC(cudaMemsetAsync(W->ginter, 0, sizeof(uint32_t) * W->gnb * W->gcap, s));
@@ -844,7 +897,7 @@ CoarsenWs *coarsen_workspace(int32_t n, int32_t e, const Params &P, Arena &A) {
 void coarsen_workspace_free(CoarsenWs *W, Arena &A) {
     if (!W) return;
     for (void *p : {(void *)W->nsum, (void *)W->vis, (void *)W->q, (void *)W->cand, (void *)W->cscore, (void *)W->lW, (void *)W->lB, (void *)W->lC,
-                    (void *)W->lG, (void *)W->cnt, (void *)W->gkeys, (void *)W->geta, (void *)W->ginter,
+                    (void *)W->lG, (void *)W->lH, (void *)W->lD, (void *)W->lDH, (void *)W->cnt, (void *)W->gkeys, (void *)W->geta, (void *)W->ginter, (void *)W->gslots,
                     (void *)W->flag, (void *)W->pos, (void *)W->ikeys, (void *)W->iids, (void *)W->target,
                     (void *)W->score, (void *)W->ccount, (void *)W->coff, (void *)W->fillpos, (void *)W->kids,
                     (void *)W->best, (void *)W->ss0, (void *)W->ss10, (void *)W->sum0, (void *)W->box})

@@ -76,15 +76,31 @@ __global__ void k_check_dups(const int32_t *ioff, const int32_t *inc, const int3
 }
 
 // ---------------------------------------------------------------- incidence
+// counts per node are combined across the lanes holding the same node
+// before the atomics (hub nodes appear in many hyperedges of a warp)
 __global__ void k_inc_keys(const int32_t *pin, const int32_t *pedge, const int32_t *off, const int32_t *nsrc,
                            int64_t np, uint32_t *keys, uint32_t *vals, int32_t *cnt, int32_t *nin) {
-    GRID_STRIDE(j, np) {
-        int32_t e = pedge[j], v = pin[j];
-        bool src = (int32_t)j - off[e] < nsrc[e];
-        keys[j] = (uint32_t)v * 2u + (src ? 1u : 0u);
-        vals[j] = (uint32_t)e;
-        atomicAdd(&cnt[v], 1);
-        if (!src) atomicAdd(&nin[v], 1);
+    const int lane = threadIdx.x & 31;
+    const int64_t wbase = ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5) << 5;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = wbase; base < np; base += stride) {
+        const int64_t j = base + lane;
+        const bool valid = j < np;
+        int32_t v = -1 - lane;
+        bool src = false;
+        if (valid) {
+            const int32_t e = pedge[j];
+            v = pin[j];
+            src = (int32_t)j - off[e] < nsrc[e];
+            keys[j] = (uint32_t)v * 2u + (src ? 1u : 0u);
+            vals[j] = (uint32_t)e;
+        }
+        const uint32_t peers = __match_any_sync(0xffffffffu, v);
+        const uint32_t dstpeers = __ballot_sync(0xffffffffu, valid && !src) & peers;
+        if (valid && lane == __ffs(peers) - 1) {
+            atomicAdd(&cnt[v], __popc(peers));
+            if (dstpeers) atomicAdd(&nin[v], __popc(dstpeers));
+        }
     }
 }
 

@@ -114,7 +114,7 @@ constexpr int PLW_T = 128;  // warp-per-edge kernel: 4 warps
 __global__ void __launch_bounds__(PLW_T) k_plist_small(const int32_t *off, const int32_t *pin, const int32_t *nsrc,
                                                        const int32_t *w, const int32_t *rho, int32_t e,
                                                        const int32_t *list, int32_t small_max, uint32_t cap, Plist PL,
-                                                       int32_t *D, long long *saving) {
+                                                       int32_t *D, long long *saving, int32_t skip_below) {
     extern __shared__ __align__(16) int32_t sm[];
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int per = 3 * (int)cap + 4 * small_max + 1;
@@ -130,10 +130,12 @@ __global__ void __launch_bounds__(PLW_T) k_plist_small(const int32_t *off, const
     __syncwarp();
     int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    // all hyperedges up to small_max pins, or the given list (count e)
+    // all hyperedges up to small_max pins, or the given list (count e) skipping
+    // the ones of at most skip_below pins
     for (int64_t i = warp; i < e; i += nw) {
         const int32_t ed = list ? list[i] : (int32_t)i;
-        if (!list && off[ed + 1] - off[ed] > small_max) continue;
+        const int32_t sz = off[ed + 1] - off[ed];
+        if ((!list && sz > small_max) || sz <= skip_below) continue;
         plist_edge<32>(ed, lane, off, pin, nsrc, w, rho, keys, tc, tci, cap, es, ep, ec, eci, gcnt, PL, D, saving);
     }
 }
@@ -193,7 +195,7 @@ static void build_plist(const Level &L, const int32_t *w, const int32_t *rho, in
     int occ = prepare_kernel((const void *)k_plist_small, PLW_T, sm);
     int grid = (int)std::min<int64_t>(cdiv(L.e, PLW_T / 32), (int64_t)num_sms() * std::max(occ, 1));
     k_plist_small<<<std::max(grid, 1), PLW_T, sm, s>>>(L.off, L.pin, L.nsrc, w, rho, L.e, nullptr, small_max, cap,
-                                                       PL, D, saving);
+                                                       PL, D, saving, 0);
     HP_LAUNCH_CHECK();
     if (max_e > small_max) {
         int32_t *list = A.get<int32_t>(L.e);
@@ -278,7 +280,8 @@ constexpr int GN_T = 128;
 __device__ void gains_node(int32_t v, const int32_t *off, const int32_t *ioff, const int32_t *inc, const int32_t *w,
                            const int32_t *rho, const int32_t *size, const long long *psize, const long long *saving,
                            const long long *wns, Plist PL, int32_t omega, int second_half, int32_t *keys,
-                           long long *conn, uint32_t cap, uint32_t limit, int32_t *s_cnt, int *s_flag, Moves M,
+                           long long *conn, int32_t *slots, uint32_t cap, uint32_t limit, int32_t *s_cnt, int *s_flag,
+                           Moves M,
                            int32_t *ovf, int32_t *ovf_n, long long *s_rg, int32_t *s_rp) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const uint32_t mask = cap - 1;
@@ -290,7 +293,9 @@ __device__ void gains_node(int32_t v, const int32_t *off, const int32_t *ioff, c
             if (kk == -1) {
                 int32_t old = atomicCAS(&keys[h], -1, p);
                 if (old == -1) {
-                    if ((uint32_t)atomicAdd(s_cnt, 1) + 1 > limit) *(volatile int *)s_flag = 1;
+                    const uint32_t slot = (uint32_t)atomicAdd(s_cnt, 1);
+                    if (slot < limit) slots[slot] = (int32_t)h;
+                    else *(volatile int *)s_flag = 1;
                     kk = p;
                 } else {
                     kk = old;
@@ -303,26 +308,36 @@ __device__ void gains_node(int32_t v, const int32_t *off, const int32_t *ioff, c
             h = (h + 1) & mask;
         }
     };
-    // hyperedges with at most 8 parts: one per thread, repeated parts combined
-    // in registers; longer lists: a warp each
+    // hyperedges with at most 8 parts: one per thread.  The k-th entries of a
+    // warp's 32 hyperedges are combined by part across the warp (match_any)
+    // before one table update per distinct part, so that the few parts a
+    // node touches are not hammered by every lane.
     {
-        RegCache<4> rc;
-        rc.init();
-        auto flush = [&](int32_t p, unsigned long long sw, uint32_t) { add(p, (long long)sw); };
-        for (int32_t t = ioff[v] + threadIdx.x; t < ioff[v + 1]; t += blockDim.x) {
-            if (*(volatile int *)s_flag) break;
-            const int32_t e = inc[t];
-            const int32_t a = off[e];
-            if (off[e + 1] - a < 2) continue;
-            const int32_t lam = PL.lam[e];
-            if (lam > 8) continue;
-            const unsigned long long we = (unsigned long long)w[e];
-            for (int32_t k = 0; k < lam; k++) {
-                const int32_t p = PL.p[a + k];
-                if (p != s) rc.add(p, we, 0u, flush);
+        const int32_t c0 = ioff[v], c1 = ioff[v + 1];
+        for (int32_t base = c0; base < c1; base += blockDim.x) {
+            if (__any_sync(0xffffffffu, *(volatile int *)s_flag)) break;
+            const int32_t t = base + (int32_t)threadIdx.x;
+            int32_t a = 0, lam = 0;
+            uint32_t we = 0;
+            if (t < c1) {
+                const int32_t e = inc[t];
+                lam = PL.lam[e];
+                if (lam <= 8) {
+                    a = off[e];
+                    we = (uint32_t)w[e];
+                } else {
+                    lam = 0;
+                }
+            }
+            const int kmax = __reduce_max_sync(0xffffffffu, (unsigned)lam);
+            for (int k = 0; k < kmax; k++) {
+                int32_t p = k < lam ? PL.p[a + k] : -1;
+                if (p == s) p = -1;
+                const unsigned m = __match_any_sync(0xffffffffu, p);
+                const unsigned sw = __reduce_add_sync(m, p >= 0 ? we : 0u);
+                if (p >= 0 && lane == __ffs(m) - 1) add(p, (long long)sw);
             }
         }
-        rc.drain(flush);
     }
     for (int32_t t = ioff[v] + wid; t < ioff[v + 1]; t += nw) {
         if (*(volatile int *)s_flag) break;
@@ -342,21 +357,12 @@ __device__ void gains_node(int32_t v, const int32_t *off, const int32_t *ioff, c
     long long bg = 0;
     int32_t bp = -1;
     const long long base = saving[v] - wns[v];
-    for (uint32_t h = threadIdx.x; h < cap; h += blockDim.x) {
-        int32_t p = keys[h];
-        if (p >= 0) {
-            if (!overflow && (!second_half || (long long)size[v] + psize[p] <= omega)) {
-                long long g = base + conn[h];
-                if (bp < 0 || g > bg || (g == bg && p > bp)) {
-                    bg = g;
-                    bp = p;
-                }
-            }
+    if (overflow) {
+        // the slot list is incomplete: clear the whole table, redo the node in a larger one
+        for (uint32_t h = threadIdx.x; h < cap; h += blockDim.x) {
             keys[h] = -1;
             conn[h] = 0;
         }
-    }
-    if (overflow) {
         __syncthreads();
         if (threadIdx.x == 0) {
             ovf[atomicAdd(ovf_n, 1)] = v;
@@ -365,6 +371,20 @@ __device__ void gains_node(int32_t v, const int32_t *off, const int32_t *ioff, c
         }
         __syncthreads();
         return;
+    }
+    const int32_t used = *(volatile int32_t *)s_cnt;
+    for (int32_t i = threadIdx.x; i < used; i += blockDim.x) {
+        const int32_t h = slots[i];
+        const int32_t p = keys[h];
+        if (!second_half || (long long)size[v] + psize[p] <= omega) {
+            long long g = base + conn[h];
+            if (bp < 0 || g > bg || (g == bg && p > bp)) {
+                bg = g;
+                bp = p;
+            }
+        }
+        keys[h] = -1;
+        conn[h] = 0;
     }
     for (int o = 16; o > 0; o >>= 1) {
         long long og = __shfl_down_sync(0xffffffffu, bg, o);
@@ -407,17 +427,19 @@ struct GainArgs {
     Moves M;
 };
 
-__global__ void __launch_bounds__(GN_T) k_gains_smem(GainArgs G, const int32_t *list, const int32_t *count_p,
+template <int BT>
+__global__ void __launch_bounds__(BT) k_gains_smem(GainArgs G, const int32_t *list, const int32_t *count_p,
                                                      uint32_t cap, int32_t *ovf, int32_t *ovf_n) {
     const int32_t count = *count_p;
     extern __shared__ __align__(16) unsigned char smem[];
     long long *conn = reinterpret_cast<long long *>(smem);
     int32_t *keys = reinterpret_cast<int32_t *>(conn + cap);
+    int32_t *slots = keys + cap;
     __shared__ int32_t s_cnt;
     __shared__ int s_flag;
-    __shared__ long long s_rg[8];
-    __shared__ int32_t s_rp[8];
-    for (uint32_t i = threadIdx.x; i < cap; i += GN_T) {
+    __shared__ long long s_rg[32];
+    __shared__ int32_t s_rp[32];
+    for (uint32_t i = threadIdx.x; i < cap; i += BT) {
         keys[i] = -1;
         conn[i] = 0;
     }
@@ -428,7 +450,7 @@ __global__ void __launch_bounds__(GN_T) k_gains_smem(GainArgs G, const int32_t *
     __syncthreads();
     for (int32_t k = blockIdx.x; k < count; k += gridDim.x)
         gains_node(list[k], G.off, G.ioff, G.inc, G.w, G.rho, G.size, G.psize, G.saving, G.wns, G.PL, G.omega,
-                   G.second_half, keys, conn, cap, cap * 3 / 4, &s_cnt, &s_flag, G.M, ovf, ovf_n, s_rg, s_rp);
+                   G.second_half, keys, conn, slots, cap, cap * 3 / 4, &s_cnt, &s_flag, G.M, ovf, ovf_n, s_rg, s_rp);
 }
 
 __global__ void __launch_bounds__(GN_T) k_gains_global(GainArgs G, const int32_t *list, const int32_t *count_p,
@@ -440,7 +462,8 @@ __global__ void __launch_bounds__(GN_T) k_gains_global(GainArgs G, const int32_t
     __shared__ int s_flag;
     __shared__ long long s_rg[8];
     __shared__ int32_t s_rp[8];
-    int32_t *keys = gkeys + (int64_t)blockIdx.x * cap;
+    int32_t *keys = gkeys + (int64_t)blockIdx.x * 2 * cap;
+    int32_t *slots = keys + cap;
     long long *conn = gconn + (int64_t)blockIdx.x * cap;
     for (uint32_t i = threadIdx.x; i < cap; i += GN_T) {
         keys[i] = -1;
@@ -453,7 +476,115 @@ __global__ void __launch_bounds__(GN_T) k_gains_global(GainArgs G, const int32_t
     __syncthreads();
     for (int32_t k = blockIdx.x; k < count; k += gridDim.x)
         gains_node(list[k], G.off, G.ioff, G.inc, G.w, G.rho, G.size, G.psize, G.saving, G.wns, G.PL, G.omega,
-                   G.second_half, keys, conn, cap, cap - 1, &s_cnt, &s_flag, G.M, bad, bad_n, s_rg, s_rp);
+                   G.second_half, keys, conn, slots, cap, cap - 1, &s_cnt, &s_flag, G.M, bad, bad_n, s_rg, s_rp);
+}
+
+// Nodes with at most GW_DEG cut hyperedges: one warp each, with a warp-private
+// table of GW_SLOTS parts in shared memory.  Entries of the lanes' hyperedges
+// are combined by part across the warp before each table update.  A node
+// whose neighbouring parts outgrow `limit` is handed to the CTA kernel's list.
+constexpr int GW_T = 256, GW_SLOTS = 256;
+__global__ void __launch_bounds__(GW_T) k_gains_warp(GainArgs G, const int32_t *list, const int32_t *count_p,
+                                                     uint32_t limit, int32_t *spill, int32_t *spill_n) {
+    __shared__ int32_t s_keys[GW_T / 32][GW_SLOTS];
+    __shared__ long long s_conn[GW_T / 32][GW_SLOTS];
+    __shared__ int32_t s_used[GW_T / 32];
+    const unsigned FULL = 0xffffffffu;
+    const int32_t count = *count_p;
+    if (count == 0) return;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int32_t *keys = s_keys[wid];
+    long long *conn = s_conn[wid];
+    for (int h = lane; h < GW_SLOTS; h += 32) {
+        keys[h] = -1;
+        conn[h] = 0;
+    }
+    if (lane == 0) s_used[wid] = 0;
+    __syncwarp();
+    const int64_t gw = (int64_t)blockIdx.x * (GW_T / 32) + wid, nw = (int64_t)gridDim.x * (GW_T / 32);
+    for (int64_t k = gw; k < count; k += nw) {
+        const int32_t v = list[k];
+        const int32_t s = G.rho[v];
+        const int32_t c0 = G.ioff[v], c1 = G.ioff[v + 1];
+        for (int32_t base = c0; base < c1; base += 32) {
+            if (*(volatile int32_t *)&s_used[wid] > (int32_t)limit) break;   // same value for the whole warp
+            const int32_t t = base + lane;
+            int32_t a = 0, lam = 0;
+            uint32_t we = 0;
+            if (t < c1) {
+                const int32_t e = G.inc[t];
+                lam = G.PL.lam[e];
+                a = G.off[e];
+                we = (uint32_t)G.w[e];
+            }
+            const int kmax = (int)__reduce_max_sync(FULL, (unsigned)lam);
+            for (int k2 = 0; k2 < kmax; k2++) {
+                int32_t p = k2 < lam ? G.PL.p[a + k2] : -1;
+                if (p == s) p = -1;
+                const unsigned m = __match_any_sync(FULL, p);
+                const unsigned sw = __reduce_add_sync(m, p >= 0 ? we : 0u);
+                if (p >= 0 && lane == __ffs(m) - 1) {
+                    uint32_t h = hslot(p, GW_SLOTS - 1);
+                    for (int probe = 0; probe < GW_SLOTS; probe++) {
+                        int32_t kk = ((volatile int32_t *)keys)[h];
+                        if (kk == -1) {
+                            const int32_t old = atomicCAS(&keys[h], -1, p);
+                            if (old == -1) {
+                                atomicAdd(&s_used[wid], 1);
+                                kk = p;
+                            } else {
+                                kk = old;
+                            }
+                        }
+                        if (kk == p) {
+                            atomicAdd((unsigned long long *)&conn[h], (unsigned long long)sw);
+                            break;
+                        }
+                        h = (h + 1) & (GW_SLOTS - 1);
+                    }
+                }
+            }
+            __syncwarp();
+        }
+        __syncwarp();
+        const bool spilled = *(volatile int32_t *)&s_used[wid] > (int32_t)limit;
+        const long long basev = G.saving[v] - G.wns[v];
+        long long bg = 0;
+        int32_t bp = -1;
+        for (int h = lane; h < GW_SLOTS; h += 32) {
+            const int32_t p = keys[h];
+            if (p >= 0 && !spilled && (!G.second_half || (long long)G.size[v] + G.psize[p] <= G.omega)) {
+                const long long g = basev + conn[h];
+                if (bp < 0 || g > bg || (g == bg && p > bp)) {
+                    bg = g;
+                    bp = p;
+                }
+            }
+            keys[h] = -1;
+            conn[h] = 0;
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            const long long og = __shfl_down_sync(FULL, bg, o);
+            const int32_t op = __shfl_down_sync(FULL, bp, o);
+            if (op >= 0 && (bp < 0 || og > bg || (og == bg && op > bp))) {
+                bg = og;
+                bp = op;
+            }
+        }
+        if (lane == 0) {
+            if (spilled) {
+                spill[atomicAdd(spill_n, 1)] = v;
+            } else if (bp >= 0 && bg > 0) {
+                const int32_t i = atomicAdd(G.M.count, 1);
+                G.M.node[i] = v;
+                G.M.src[i] = s;
+                G.M.dst[i] = bp;
+                G.M.gain[i] = bg;
+            }
+            s_used[wid] = 0;
+        }
+        __syncwarp();
+    }
 }
 
 // ---------------------------------------------------------------- per level constants
@@ -488,18 +619,117 @@ __global__ void k_level_nodes(const int32_t *off, const int32_t *ioff, const int
     }
 }
 
-// hyperedges with >= 2 pins, split at small_max pins
+// hyperedges with >= 2 pins: up to TINY_E pins (one thread each), up to
+// small_max (a warp each), larger (a CTA each).  All of them form `act`
+// (the in-sequence pass); tiny ones are also listed apart.
+constexpr int TINY_E = 8;
 __global__ void k_level_edges(const int32_t *off, int32_t e, int32_t small_max, int32_t *act, int32_t *big,
-                              int32_t *cnt) {
+                              int32_t *tiny, int32_t *cnt) {
     GRID_STRIDE(i, (int64_t)e) {
         int32_t sz = off[i + 1] - off[i];
-        if (sz >= 2 && sz <= small_max) act[atomicAdd(&cnt[0], 1)] = (int32_t)i;
-        else if (sz > small_max) big[atomicAdd(&cnt[1], 1)] = (int32_t)i;
+        if (sz >= 2 && sz <= small_max) {
+            act[atomicAdd(&cnt[0], 1)] = (int32_t)i;
+            if (sz <= TINY_E) tiny[atomicAdd(&cnt[3], 1)] = (int32_t)i;
+        } else if (sz > small_max) big[atomicAdd(&cnt[1], 1)] = (int32_t)i;
+    }
+}
+
+// pins(p, e) list of a hyperedge of 2..TINY_E pins by one thread.  D(p) and
+// saving(v) updates are combined across the warp by key (match_any) first:
+// a coarse node or a part shared by many neighbouring hyperedges would
+// otherwise take one global atomic per hyperedge.
+__global__ void k_plist_tiny(const int32_t *off, const int32_t *pin, const int32_t *nsrc, const int32_t *w,
+                             const int32_t *rho, const int32_t *list, int32_t count, Plist PL, int32_t *D,
+                             long long *saving) {
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < count; base += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t k = base + threadIdx.x;
+        const bool live = k < count;
+        int32_t a = 0, sz = 0, dst0 = 0;
+        uint32_t we = 0;
+        if (live) {
+            const int32_t e = list[k];
+            a = off[e];
+            sz = off[e + 1] - a;
+            dst0 = nsrc[e];
+            we = (uint32_t)w[e];
+        }
+        int32_t vv[TINY_E], pp[TINY_E], up[TINY_E], uc[TINY_E], uci[TINY_E];
+        int32_t nu = 0;
+#pragma unroll
+        for (int j = 0; j < TINY_E; j++) {
+            vv[j] = -1;
+            pp[j] = -1;
+            up[j] = 0x7fffffff;
+            uc[j] = 0;
+            uci[j] = 0;
+        }
+#pragma unroll
+        for (int j = 0; j < TINY_E; j++) {
+            if (j < sz) {
+                vv[j] = pin[a + j];
+                pp[j] = rho[vv[j]];
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < TINY_E; j++) {
+            if (j >= sz) break;
+            const int32_t p = pp[j];
+            int32_t f = -1;
+#pragma unroll
+            for (int u = 0; u < TINY_E; u++)
+                if (u < nu && up[u] == p) f = u;
+            if (f < 0) f = nu++;
+#pragma unroll
+            for (int u = 0; u < TINY_E; u++)
+                if (u == f) {
+                    up[u] = p;
+                    uc[u]++;
+                    uci[u] += j >= dst0;
+                }
+        }
+        // sorted by part id: rank of each distinct entry
+#pragma unroll
+        for (int u = 0; u < TINY_E; u++) {
+            if (u < nu) {
+                int32_t r = 0;
+#pragma unroll
+                for (int x = 0; x < TINY_E; x++)
+                    if (x < nu && up[x] < up[u]) r++;
+                PL.p[a + r] = up[u];
+                PL.cnt[a + r] = uc[u];
+                PL.cin[a + r] = uci[u];
+            }
+        }
+        if (live) PL.lam[list[k]] = nu;
+        if (D) {
+#pragma unroll
+            for (int u = 0; u < TINY_E; u++) {
+                const int32_t key = (u < nu && uci[u] > 0) ? up[u] : -1;
+                const unsigned m = __match_any_sync(FULL, key);
+                if (key >= 0 && lane == __ffs(m) - 1) atomicAdd(&D[key], __popc(m));
+            }
+        }
+        if (saving) {
+#pragma unroll
+            for (int j = 0; j < TINY_E; j++) {
+                int32_t c = 0;
+#pragma unroll
+                for (int u = 0; u < TINY_E; u++)
+                    if (u < nu && up[u] == pp[j]) c = uc[u];
+                const int32_t key = (j < sz && c == 1) ? vv[j] : -1;
+                const unsigned m = __match_any_sync(FULL, key);
+                const unsigned sw = __reduce_add_sync(m, key >= 0 ? we : 0u);
+                if (key >= 0 && lane == __ffs(m) - 1)
+                    atomicAdd((unsigned long long *)&saving[key], (unsigned long long)sw);
+            }
+        }
     }
 }
 
 // counters of one repetition (device)
-enum { C_CAND, C_MOVES, C_OVF, C_BAD, C_NH, C_BAD0, C_APPLIED, C_NV, C_N };
+enum { C_CAND, C_MOVES, C_OVF, C_BAD, C_NH, C_BAD0, C_APPLIED, C_NV, C_HUB, C_CW, C_N };
 
 // moves of at most SMALLM are sequenced and validated by one CTA each
 constexpr int SMALLM = 4096, SEQ_T = 1024;
@@ -557,9 +787,35 @@ __global__ void k_rep_nodes(const int32_t *rho, const int32_t *size, const int32
     }
 }
 
-__global__ void k_candidates(const long long *saving, int32_t n, int32_t *list, int32_t *cnt) {
+// Cut incident hyperedges (|e| >= 2 and more than one part): the only ones
+// that add to conn(v, p) for p != rho(v).  Compacted per node, in incidence
+// order, for the gain kernels.
+__global__ void k_cut_flags(const int32_t *off, const int32_t *inc, const int32_t *lam, int64_t np, int32_t *flag) {
+    GRID_STRIDE(t, np) {
+        const int32_t e = inc[t];
+        flag[t] = (off[e + 1] - off[e] >= 2 && lam[e] >= 2) ? 1 : 0;
+    }
+}
+__global__ void k_cut_fill(const int32_t *inc, const int32_t *flag, const int32_t *cpos, const int32_t *ioff,
+                           int64_t np, int32_t n, int32_t *cut, int32_t *cut_off) {
+    GRID_STRIDE(t, np) {
+        if (flag[t]) cut[cpos[t]] = inc[t];
+    }
+    GRID_STRIDE(v, (int64_t)n + 1) cut_off[v] = cpos[ioff[v]];
+}
+
+// candidates: nodes that can spare a cut, by number of cut hyperedges:
+// up to GW_DEG a warp each, up to HUB_DEG a CTA each, more a large CTA each
+constexpr int32_t HUB_DEG = 4096, GW_DEG = 256;
+__global__ void k_candidates(const long long *saving, const int32_t *cut_off, int32_t n, int32_t *list, int32_t *cnt,
+                             int32_t *hubs, int32_t *hcnt, int32_t *wlist, int32_t *wcnt) {
     GRID_STRIDE(v, (int64_t)n) {
-        if (saving[v] > 0) list[atomicAdd(cnt, 1)] = (int32_t)v;
+        if (saving[v] > 0) {
+            const int32_t d = cut_off[v + 1] - cut_off[v];
+            if (d > HUB_DEG) hubs[atomicAdd(hcnt, 1)] = (int32_t)v;
+            else if (d <= GW_DEG) wlist[atomicAdd(wcnt, 1)] = (int32_t)v;
+            else list[atomicAdd(cnt, 1)] = (int32_t)v;
+        }
     }
 }
 
@@ -773,6 +1029,8 @@ struct ValCtx {
     long long *vsz;
     int32_t *vdd, *viol;
     int32_t omega, delta;
+    long long *gsz, *gdd, *esz, *edd;  // [2m] events in part order; their exclusive prefix sums
+    int32_t *vhead;                    // [nparts] first event of each part
 };
 __device__ void ph_val_entries(const ValCtx &V, int32_t m, int64_t t0, int64_t nt) {
     STRIDE(k, m, t0, nt) {
@@ -789,20 +1047,29 @@ __device__ void ph_val_entries(const ValCtx &V, int32_t m, int64_t t0, int64_t n
         V.vdd[2 * k + 1] = V.dDd[k] + V.singin[v];
     }
 }
-__device__ void ph_val_walk(const ValCtx &V, int32_t c, int64_t t0, int64_t nt) {
-    STRIDE(i, c, t0, nt) {
-        uint32_t p = V.vkey[i];
-        if (i > 0 && V.vkey[i - 1] == p) continue;
-        long long sz = V.psize[p], dc = V.D0[p];
-        bool valid = sz <= V.omega && dc <= V.delta;
-        for (int64_t j = i; j < c && V.vkey[j] == p; j++) {
-            uint32_t x = V.vidx[j];
-            sz += V.vsz[x];
-            dc += V.vdd[x];
-            bool nv2 = sz <= V.omega && dc <= V.delta;
-            if (nv2 != valid) atomicAdd(&V.viol[x >> 1], nv2 ? -1 : 1);
-            valid = nv2;
-        }
+// Validity of every prefix (Sec. VI-D) from the c = 2m capacity events
+// sorted by part (stably, so in sequence order within a part).  A part's
+// running size and distinct-inbound count after each of its events are
+// global prefix sums minus the prefix at the part's first event; every event
+// at which the part turns valid or invalid adds -1 / +1 to the violation
+// count of its move.
+__device__ void ph_val_gather(const ValCtx &V, int32_t c, int64_t t0, int64_t nt) {
+    STRIDE(j, c, t0, nt) {
+        const uint32_t x = V.vidx[j];
+        V.gsz[j] = V.vsz[x];
+        V.gdd[j] = V.vdd[x];
+        const uint32_t p = V.vkey[j];
+        if (j == 0 || V.vkey[j - 1] != p) V.vhead[p] = (int32_t)j;
+    }
+}
+__device__ void ph_val_trans(const ValCtx &V, int32_t c, int64_t t0, int64_t nt) {
+    STRIDE(j, c, t0, nt) {
+        const uint32_t p = V.vkey[j];
+        const int32_t h = V.vhead[p];
+        const long long bs = V.psize[p] + (V.esz[j] - V.esz[h]), bd = (long long)V.D0[p] + (V.edd[j] - V.edd[h]);
+        const long long as = bs + V.gsz[j], ad = bd + V.gdd[j];
+        const bool vb = bs <= V.omega && bd <= V.delta, va = as <= V.omega && ad <= V.delta;
+        if (vb != va) atomicAdd(&V.viol[V.vidx[j] >> 1], va ? -1 : 1);
     }
 }
 __device__ int32_t ph_initial_bad(const long long *psize, const int32_t *D0, int32_t nparts, int32_t omega,
@@ -852,6 +1119,35 @@ __device__ void block_scan_excl(const int32_t *in, int32_t *out, int64_t n, int3
             int32_t y = lane < nw ? s_tmp[lane] : 0, yi = y;
             for (int o = 1; o < 32; o <<= 1) {
                 int32_t u = __shfl_up_sync(0xffffffffu, yi, o);
+                if (lane >= o) yi += u;
+            }
+            if (lane < nw) s_tmp[lane] = yi - y;
+            if (lane == nw - 1) s_tmp[32] = yi;
+        }
+        __syncthreads();
+        if (i < n) out[i] = carry + s_tmp[wid] + inc - x;
+        carry += s_tmp[32];
+        __syncthreads();
+    }
+}
+
+// the same for int64 values, in place allowed (in == out)
+__device__ void block_scan_excl_ll(const long long *in, long long *out, int64_t n, long long *s_tmp) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    long long carry = 0;
+    for (int64_t base = 0; base < n; base += blockDim.x) {
+        int64_t i = base + threadIdx.x;
+        long long x = i < n ? in[i] : 0, inc = x;
+        for (int o = 1; o < 32; o <<= 1) {
+            long long u = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += u;
+        }
+        if (lane == 31) s_tmp[wid] = inc;
+        __syncthreads();
+        if (wid == 0) {
+            long long y = lane < nw ? s_tmp[lane] : 0, yi = y;
+            for (int o = 1; o < 32; o <<= 1) {
+                long long u = __shfl_up_sync(0xffffffffu, yi, o);
                 if (lane >= o) yi += u;
             }
             if (lane < nw) s_tmp[lane] = yi - y;
@@ -1003,7 +1299,8 @@ __global__ void k_val_entries(ValCtx V, const int32_t *mcount, int32_t *nv) {
     if (blockIdx.x == 0 && threadIdx.x == 0) *nv = 2 * m;
     ph_val_entries(V, m, G_T0, G_NT);
 }
-__global__ void k_val_walk(ValCtx V, const int32_t *nv) { ph_val_walk(V, *nv, G_T0, G_NT); }
+__global__ void k_val_gather(ValCtx V, const int32_t *nv) { ph_val_gather(V, *nv, G_T0, G_NT); }
+__global__ void k_val_trans(ValCtx V, const int32_t *nv) { ph_val_trans(V, *nv, G_T0, G_NT); }
 __global__ void k_initial_bad(const long long *psize, const int32_t *D0, int32_t nparts, int32_t omega, int32_t delta,
                               int32_t *bad) {
     int32_t c = ph_initial_bad(psize, D0, nparts, omega, delta, G_T0, G_NT);
@@ -1102,12 +1399,18 @@ __global__ void __launch_bounds__(SEQ_T) k_val_small(ValCtx V, int32_t *cnt, int
     __shared__ uint32_t s_wc[32 * 256];
     __shared__ uint32_t s_hist[256];
     __shared__ int32_t s_tmp[40];
+    __shared__ long long s_ll[40];
     const int32_t m = cnt[C_MOVES];
     if (m == 0 || m > SMALLM) return;
     const int64_t t0 = threadIdx.x, nt = blockDim.x;
     ph_val_entries(V, m, t0, nt);
     block_radix_sort<uint32_t>(V.vkey, V.vidx, 2 * m, (sb + 7) / 8, 2 * SMALLM, smem, s_wc, s_hist);
-    ph_val_walk(V, 2 * m, t0, nt);
+    __syncthreads();
+    ph_val_gather(V, 2 * m, t0, nt);
+    __syncthreads();
+    block_scan_excl_ll(V.gsz, V.esz, 2 * m, s_ll);
+    block_scan_excl_ll(V.gdd, V.edd, 2 * m, s_ll);
+    ph_val_trans(V, 2 * m, t0, nt);
     int32_t bad = block_sum(ph_initial_bad(V.psize, V.D0, nparts, V.omega, V.delta, t0, nt), s_tmp);
     __syncthreads();
     best_prefix_block(V.gseq, V.viol, m, bad, &cnt[C_APPLIED], bgain);
@@ -1242,7 +1545,9 @@ struct LevelWs {
     int32_t *singin;
     Plist PL;
     RepArrays R;
-    int32_t *cl;
+    int32_t *cl, *hubs, *cw;
+    int32_t *cflag, *cpos, *cut, *cut_off;   // cut incident hyperedges per node
+    int32_t *tiny, n_tiny;                   // hyperedges of 2..8 pins
     Moves M, S;
     uint64_t *keys;
     uint32_t *idx;
@@ -1253,6 +1558,8 @@ struct LevelWs {
     uint32_t *vkey, *vidx;
     long long *vsz;
     int32_t *vdd;
+    long long *gsz, *gdd, *esz, *edd;
+    int32_t *vhead;
     int32_t *ovf, *gk;
     long long *gc;
     uint32_t gcap;
@@ -1301,6 +1608,13 @@ LevelWs *refine_workspace(int32_t n, int64_t np, int32_t e, int32_t nparts, int3
     R.dDd = A.get<int32_t>(n);
     R.viol = A.get<int32_t>(n);
     W->cl = A.get<int32_t>(n);
+    W->hubs = A.get<int32_t>(n);
+    W->cw = A.get<int32_t>(n);
+    W->cflag = A.get<int32_t>(np);
+    W->cpos = A.get<int32_t>(np + 1);
+    W->cut = A.get<int32_t>(np);
+    W->cut_off = A.get<int32_t>(n + 1);
+    W->tiny = A.get<int32_t>(e);
     for (Moves *m : {&W->M, &W->S}) {
         m->node = A.get<int32_t>(n);
         m->src = A.get<int32_t>(n);
@@ -1328,15 +1642,20 @@ LevelWs *refine_workspace(int32_t n, int64_t np, int32_t e, int32_t nparts, int3
     W->vidx = A.get<uint32_t>(2 * (int64_t)n);
     W->vsz = A.get<long long>(2 * (int64_t)n);
     W->vdd = A.get<int32_t>(2 * (int64_t)n);
+    W->gsz = A.get<long long>(2 * (int64_t)n);
+    W->gdd = A.get<long long>(2 * (int64_t)n);
+    W->esz = A.get<long long>(2 * (int64_t)n);
+    W->edd = A.get<long long>(2 * (int64_t)n);
+    W->vhead = A.get<int32_t>(std::max<int64_t>(nparts, 1));
     W->bgain = A.get<long long>(1);
     W->lvl = A.get<int32_t>(4);
     // overflow tables of the gain kernel, one per CTA of its fallback grid
     W->gcap = pow2_at_least(2 * (int64_t)nparts + 2);
     W->gnb = (int)std::min<int64_t>(num_sms(), std::max<int64_t>(1, ((int64_t)1 << 27) / ((int64_t)W->gcap * 12)));
     W->ovf = A.get<int32_t>(n);
-    W->gk = A.get<int32_t>((int64_t)W->gnb * W->gcap);
+    W->gk = A.get<int32_t>((int64_t)W->gnb * 2 * W->gcap);
     W->gc = A.get<long long>((int64_t)W->gnb * W->gcap);
-    fill_i32(W->gk, (int64_t)W->gnb * W->gcap, -1, s);
+    fill_i32(W->gk, (int64_t)W->gnb * 2 * W->gcap, -1, s);
     HPC(cudaMemsetAsync(W->gc, 0, sizeof(long long) * W->gnb * W->gcap, s));
     // hyperedges above 512 pins: tables and buffers in global memory
     W->ptab = W->ibuf = nullptr;
@@ -1355,10 +1674,10 @@ void refine_workspace_free(LevelWs *W, Arena &A) {
     for (void *p : std::initializer_list<void *>{
              W->act, W->big, W->wns, W->singin, W->PL.p, W->PL.cnt, W->PL.cin, W->PL.lam, W->R.cnt, W->R.linked,
              W->R.D0, W->R.psize, W->R.saving, W->R.pc, W->R.pred, W->R.succ, W->R.chain, W->R.mvpos, W->R.cgain,
-             W->R.gseq, W->R.acc0, W->R.dDs, W->R.dDd, W->R.viol, W->cl, W->M.node, W->M.src, W->M.dst, W->M.gain,
+             W->R.gseq, W->R.acc0, W->R.dDs, W->R.dDd, W->R.viol, W->cl, W->hubs, W->cw, W->cflag, W->cpos, W->cut, W->cut_off, W->tiny, W->M.node, W->M.src, W->M.dst, W->M.gain,
              W->S.node, W->S.src, W->S.dst, W->S.gain, W->keys, W->idx, W->first, W->choice, W->accnode, W->pen,
              W->minpen, W->acc1, W->pos, W->clen, W->lens, W->starts, W->cstart, W->seqmove, W->heads, W->hkeys,
-             W->vkey, W->vidx, W->vsz, W->vdd, W->bgain, W->lvl, W->ovf, W->gk, W->gc, W->ptab, W->ibuf})
+             W->vkey, W->vidx, W->vsz, W->vdd, W->gsz, W->gdd, W->esz, W->edd, W->vhead, W->bgain, W->lvl, W->ovf, W->gk, W->gc, W->ptab, W->ibuf})
         A.release(p);
     delete W;
 }
@@ -1379,7 +1698,7 @@ static void level_prepare(const Level &L, const int32_t *w, LevelWs &W, Arena &A
     W.small_max = std::min<int32_t>(std::max<int32_t>(W.max_e, 2), 512);
     W.pcap = pow2_at_least(2 * (int64_t)W.small_max);
     if (e > 0) {
-        k_level_edges<<<grid_of(e, 256), 256, 0, s>>>(L.off, e, W.small_max, W.act, W.big, W.lvl);
+        k_level_edges<<<grid_of(e, 256), 256, 0, s>>>(L.off, e, W.small_max, W.act, W.big, W.tiny, W.lvl);
         HP_LAUNCH_CHECK();
     }
     HPC(cudaMemsetAsync(W.wns, 0, sizeof(long long) * n, s));
@@ -1389,10 +1708,11 @@ static void level_prepare(const Level &L, const int32_t *w, LevelWs &W, Arena &A
                                                           W.singin);
         HP_LAUNCH_CHECK();
     }
-    int32_t hc[2];
+    int32_t hc[4];
     fetch_bytes(hc, W.lvl, sizeof hc, s);
     W.n_act = hc[0];
     W.n_big = hc[1];
+    W.n_tiny = hc[3];
     if (W.n_big > 0 && !W.ptab) throw Error(HP_ERR_INTERNAL, "large hyperedge buffers missing");
 }
 
@@ -1416,7 +1736,12 @@ static int32_t rep_run(const Level &L, const int32_t *w, const Params &P, int32_
         int occ = prepare_kernel((const void *)k_plist_small, PLW_T, sm);
         int grid = (int)std::min<int64_t>(cdiv(W.n_act, PLW_T / 32), (int64_t)num_sms() * occ);
         k_plist_small<<<std::max(grid, 1), PLW_T, sm, s>>>(L.off, L.pin, L.nsrc, w, rho, W.n_act, W.act, W.small_max,
-                                                           W.pcap, W.PL, R.D0, R.saving);
+                                                           W.pcap, W.PL, R.D0, R.saving, TINY_E);
+        HP_LAUNCH_CHECK();
+    }
+    if (W.n_tiny > 0) {
+        k_plist_tiny<<<grid_of(W.n_tiny, 128), 128, 0, s>>>(L.off, L.pin, L.nsrc, w, rho, W.tiny, W.n_tiny, W.PL, R.D0,
+                                                            R.saving);
         HP_LAUNCH_CHECK();
     }
     if (W.n_big > 0) {
@@ -1425,16 +1750,36 @@ static int32_t rep_run(const Level &L, const int32_t *w, const Params &P, int32_
         HP_LAUNCH_CHECK();
     }
     // moves in isolation (Eq. 13)
-    k_candidates<<<grid_of(n, 256), 256, 0, s>>>(R.saving, n, W.cl, cnt + C_CAND);
+    if (L.np > 0) {
+        k_cut_flags<<<grid_of(L.np, 256), 256, 0, s>>>(L.off, L.inc, W.PL.lam, L.np, W.cflag);
+        HP_LAUNCH_CHECK();
+    }
+    scan_excl(W.cflag, W.cpos, L.np, W.cpos + L.np, A);
+    k_cut_fill<<<grid_of(std::max<int64_t>(L.np, (int64_t)n + 1), 256), 256, 0, s>>>(L.inc, W.cflag, W.cpos, L.ioff,
+                                                                                       L.np, n, W.cut, W.cut_off);
     HP_LAUNCH_CHECK();
-    GainArgs G{L.off, L.ioff, L.inc, w, rho, L.size, R.psize, R.saving, W.wns, W.PL, P.omega, second_half, W.M};
+    k_candidates<<<grid_of(n, 256), 256, 0, s>>>(R.saving, W.cut_off, n, W.cl, cnt + C_CAND, W.hubs, cnt + C_HUB,
+                                                 W.cw, cnt + C_CW);
+    HP_LAUNCH_CHECK();
+    GainArgs G{L.off, W.cut_off, W.cut, w, rho, L.size, R.psize, R.saving, W.wns, W.PL, P.omega, second_half, W.M};
+    {
+        const uint32_t wlimit = P.o.debug_table_cap > 0 ? std::min<uint32_t>(GW_SLOTS * 3 / 4, P.o.debug_table_cap / 2)
+                                                        : GW_SLOTS * 3 / 4;
+        int occ = prepare_kernel((const void *)k_gains_warp, GW_T, 0);
+        int grid = (int)std::max<int64_t>(1, std::min<int64_t>(cdiv(n, GW_T / 32), (int64_t)num_sms() * occ));
+        k_gains_warp<<<grid, GW_T, 0, s>>>(G, W.cw, cnt + C_CW, wlimit, W.cl, cnt + C_CAND);
+        HP_LAUNCH_CHECK();
+    }
     {
         uint32_t cap = 2048;
         if (P.o.debug_table_cap > 0) cap = (uint32_t)P.o.debug_table_cap;
-        size_t sm = (size_t)cap * 12;
-        int occ = prepare_kernel((const void *)k_gains_smem, GN_T, sm);
+        size_t sm = (size_t)cap * 12 + (size_t)(cap * 3 / 4) * 4;
+        int occ = prepare_kernel((const void *)k_gains_smem<GN_T>, GN_T, sm);
         int grid = std::max(1, std::min<int>(n, num_sms() * occ));
-        k_gains_smem<<<grid, GN_T, sm, s>>>(G, W.cl, cnt + C_CAND, cap, W.ovf, cnt + C_OVF);
+        k_gains_smem<GN_T><<<grid, GN_T, sm, s>>>(G, W.cl, cnt + C_CAND, cap, W.ovf, cnt + C_OVF);
+        HP_LAUNCH_CHECK();
+        prepare_kernel((const void *)k_gains_smem<1024>, 1024, sm);
+        k_gains_smem<1024><<<num_sms(), 1024, sm, s>>>(G, W.hubs, cnt + C_HUB, cap, W.ovf, cnt + C_OVF);
         HP_LAUNCH_CHECK();
         k_gains_global<<<W.gnb, GN_T, 0, s>>>(G, W.ovf, cnt + C_OVF, W.gcap, W.gk, W.gc, W.cl, cnt + C_BAD);
         HP_LAUNCH_CHECK();
@@ -1472,7 +1817,7 @@ static int32_t rep_run(const Level &L, const int32_t *w, const Params &P, int32_
     C.linked = R.linked;
     SeqCtx Q{W.S.node, R.pred, R.succ, W.S.gain, R.chain, W.pos, W.clen, R.cgain, err_dev};
     ValCtx V{W.seqmove, L.size, W.singin, R.dDs, R.dDd, R.D0, R.gseq, W.S, R.psize, W.vkey, W.vidx, W.vsz, W.vdd,
-             R.viol, P.omega, P.delta};
+             R.viol, P.omega, P.delta, W.gsz, W.gdd, W.esz, W.edd, W.vhead};
     const bool small = m <= SMALLM;
     if (small) {
         SmallSeqArgs SA{W.M, W.S, W.keys, W.hkeys, W.idx, W.heads, R.pc, W.first, W.lens, W.starts, W.cstart,
@@ -1574,7 +1919,11 @@ static int32_t rep_run(const Level &L, const int32_t *w, const Params &P, int32_
         k_val_entries<<<grid_of(m, 256), 256, 0, s>>>(V, cnt + C_MOVES, cnt + C_NV);
         HP_LAUNCH_CHECK();
         radix_sort_dev(W.vkey, W.vidx, cnt + C_NV, 2 * (int64_t)m, sb, A);
-        k_val_walk<<<grid_of(2 * (int64_t)m, 256), 256, 0, s>>>(V, cnt + C_NV);
+        k_val_gather<<<grid_of(2 * (int64_t)m, 256), 256, 0, s>>>(V, cnt + C_NV);
+        HP_LAUNCH_CHECK();
+        scan_excl((const int64_t *)W.gsz, (int64_t *)W.esz, 2 * (int64_t)m, nullptr, A);
+        scan_excl((const int64_t *)W.gdd, (int64_t *)W.edd, 2 * (int64_t)m, nullptr, A);
+        k_val_trans<<<grid_of(2 * (int64_t)m, 256), 256, 0, s>>>(V, cnt + C_NV);
         HP_LAUNCH_CHECK();
         k_initial_bad<<<grid_of(nparts, 256), 256, 0, s>>>(R.psize, R.D0, nparts, P.omega, P.delta, cnt + C_BAD0);
         HP_LAUNCH_CHECK();
