@@ -191,6 +191,34 @@ HP_API hp_status hp_connectivity(const int32_t *pins, const int32_t *offsets, in
                           int64_t *cutnet_out, void *stream);
 
 /*
+ * hp_connectivity_noalloc -- the same two numbers as hp_connectivity,
+ *   computed without allocating any device memory.  The paper has no
+ *   counterpart: this is a service call for callers that cannot let the
+ *   library allocate at the moment they need the number (an allocator hook
+ *   that refuses requests while the caller's own step runs, a process whose
+ *   free device memory belongs to another pool, a monitoring thread that must
+ *   not take or wait on an allocator lock).
+ *   Arguments, layouts and ownership as for hp_connectivity.
+ *   Scratch: a fixed area inside the loaded library, one per device (256 B of
+ *   result words, zeroed by each call on `stream` before use, and an 8 MiB
+ *   hash table that is zero at load and that every call returns to zero).
+ *   The first call on a device looks up the area's device address with the
+ *   device current; make that first call before capturing `stream` into a
+ *   graph.  Calls that can overlap on one device (two streams, two host
+ *   threads) share the area and race: serialise them.
+ *   Limit: a hyperedge of more than 262,144 pins returns HP_ERR_INVALID_ARG
+ *   (hp_last_error names the size), with nothing written.
+ *   Errors: HP_ERR_BAD_CSR for offsets that are not strictly increasing from
+ *   0 or a pin out of range (duplicate pins are not detected: they leave
+ *   lambda(e) unchanged); HP_ERR_INVALID_ARG for a part id outside
+ *   [0, num_parts), a weight outside 1..65536, or a bad scalar/pointer.
+ *   Synchronises `stream` before returning.
+ */
+HP_API hp_status hp_connectivity_noalloc(const int32_t *pins, const int32_t *offsets, int32_t num_hedges,
+                                         const int32_t *weights, const int32_t *part, int32_t num_nodes,
+                                         int32_t num_parts, int64_t *conn_out, int64_t *cutnet_out, void *stream);
+
+/*
  * Step-level entry points (test hooks) on one level graph given in device
  * memory: num_nodes, num_hedges, offsets, pins, src_counts (required, one
  * count per hyperedge), weights (required) and node sizes.  They run one step

@@ -237,6 +237,8 @@ static hp_status run(const int32_t *pins, const int32_t *offsets, int32_t e, int
     return HP_OK;
 }
 
+void set_last_error(const std::string &msg) { t_last_error = msg; }
+
 template <class F> static hp_status guarded(F &&f) {
     try {
         t_last_error.clear();

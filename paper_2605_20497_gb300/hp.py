@@ -26,7 +26,7 @@ HP_ERR_OOM, HP_ERR_CUDA, HP_ERR_TIMEOUT, HP_ERR_INTERNAL = 4, 5, 6, 7
 HP_COUNT_INBOUND, HP_COUNT_INCIDENT = 0, 1
 
 EXPORTS = ("hp_default_options", "hp_partition", "hp_partition_ex", "hp_partition_host", "hp_set_allocator",
-           "hp_status_string", "hp_last_error", "hp_connectivity", "hp_debug_coarsen_level",
+           "hp_status_string", "hp_last_error", "hp_connectivity", "hp_connectivity_noalloc", "hp_debug_coarsen_level",
            "hp_debug_refine_rep")
 
 
@@ -80,6 +80,8 @@ def load() -> ctypes.CDLL:
         L.hp_connectivity.argtypes = [P, P, I32, P, P, I32, I32, ctypes.POINTER(ctypes.c_int64),
                                       ctypes.POINTER(ctypes.c_int64), P]
         L.hp_connectivity.restype = ctypes.c_int
+        L.hp_connectivity_noalloc.argtypes = L.hp_connectivity.argtypes
+        L.hp_connectivity_noalloc.restype = ctypes.c_int
         L.hp_debug_coarsen_level.argtypes = [I32, I32, P, P, P, P, P, I32, I32, U64, I32, ctypes.POINTER(hp_options),
                                              P, P, P, ctypes.POINTER(ctypes.c_int64), P]
         L.hp_debug_coarsen_level.restype = ctypes.c_int
@@ -121,6 +123,13 @@ def hp_connectivity(pins, offsets, num_hedges, weights, part, num_nodes, num_par
     c, cn = ctypes.c_int64(0), ctypes.c_int64(0)
     st = load().hp_connectivity(pins, offsets, num_hedges, weights, part, num_nodes, num_parts, ctypes.byref(c),
                                 ctypes.byref(cn), stream)
+    return st, int(c.value), int(cn.value)
+
+
+def hp_connectivity_noalloc(pins, offsets, num_hedges, weights, part, num_nodes, num_parts, stream=0):
+    c, cn = ctypes.c_int64(0), ctypes.c_int64(0)
+    st = load().hp_connectivity_noalloc(pins, offsets, num_hedges, weights, part, num_nodes, num_parts,
+                                        ctypes.byref(c), ctypes.byref(cn), stream)
     return st, int(c.value), int(cn.value)
 
 
