@@ -13,6 +13,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <climits>
 
 #include "hp_internal.cuh"
 
@@ -63,11 +64,16 @@ __global__ void k_level_q(const int32_t *off, const int32_t *w, int32_t e, uint6
     __syncthreads();
     unsigned long long loc = 0;
     GRID_STRIDE(i, (int64_t)e) {
-        uint64_t qi = ((uint64_t)w[i] << 24) / (uint64_t)(off[i + 1] - off[i]);
+        // floor(w 2^24 / |e|): the numerator is below 2^41 and the divisor
+        // below 2^31, so the correctly rounded double quotient of a
+        // non-integer ratio is never rounded across an integer
+        const double num = (double)((uint64_t)w[i] << 24), den = (double)(off[i + 1] - off[i]);
+        const uint64_t qi = (uint64_t)floor(num / den);
         q[i] = qi;
         loc += qi;
     }
-    atomicAdd(&s, loc);
+    for (int o = 16; o > 0; o >>= 1) loc += __shfl_down_sync(0xffffffffu, loc, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(&s, loc);
     __syncthreads();
     if (threadIdx.x == 0) atomicAdd(sum, s);
 }
@@ -125,6 +131,17 @@ __device__ __forceinline__ bool cand_gt(const Cand &a, const Cand &b) {
     return a.eta > b.eta || (a.eta == b.eta && a.id > b.id);
 }
 
+// x added to the 64-bit counter at p with two 32-bit atomics: the low word's
+// carry goes to the high word, so the counter ends equal to the exact sum
+// (all updates of p use this form).
+__device__ __forceinline__ void add_u64_split(unsigned long long *p, unsigned long long x) {
+    uint32_t *w = reinterpret_cast<uint32_t *>(p);
+    const uint32_t xl = (uint32_t)x, xh = (uint32_t)(x >> 32);
+    const uint32_t old = atomicAdd(&w[0], xl);
+    const uint32_t hi = xh + (uint32_t)((uint32_t)(old + xl) < old);
+    if (hi) atomicAdd(&w[1], hi);
+}
+
 template <int PIMAX> struct TopList {
     Cand c[PIMAX];
     __device__ void init() {
@@ -148,44 +165,45 @@ template <int PIMAX> struct TopList {
     }
 };
 
-// block-wide: write the pi best of the per-thread lists to cand/cscore of v
-// (s_red: 32 entries, s_own: 33 entries; at most 32 warps)
+// block-wide: write the pi best of the per-thread lists to cand/cscore of v.
+// Each warp first extracts its own pi best by shuffles (no barrier); warp 0
+// then merges the warps' lists from s_top (32 * PIMAX entries).
 template <int PIMAX>
-__device__ void block_emit_top(TopList<PIMAX> &tl, const PropCtx &C, int32_t v, Cand *s_red, int *s_own) {
+__device__ __forceinline__ Cand warp_pop_best(TopList<PIMAX> &tl) {
+    Cand best = tl.c[0];
+    int owner = threadIdx.x & 31;
+    for (int o = 16; o > 0; o >>= 1) {
+        Cand ob{__shfl_xor_sync(0xffffffffu, best.eta, o), __shfl_xor_sync(0xffffffffu, best.id, o)};
+        const int oo = __shfl_xor_sync(0xffffffffu, owner, o);
+        if (cand_gt(ob, best) || (ob.id == best.id && oo < owner)) {
+            best = ob;
+            owner = oo;
+        }
+    }
+    if (best.id >= 0 && (int)(threadIdx.x & 31) == owner) tl.pop();
+    return best;
+}
+template <int PIMAX>
+__device__ void block_emit_top(TopList<PIMAX> &tl, const PropCtx &C, int32_t v, Cand *s_top) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int r = 0; r < C.pi; r++) {
-        Cand best = tl.c[0];
-        int owner = threadIdx.x;
-        for (int o = 16; o > 0; o >>= 1) {
-            Cand ob{__shfl_down_sync(0xffffffffu, best.eta, o), __shfl_down_sync(0xffffffffu, best.id, o)};
-            int oo = __shfl_down_sync(0xffffffffu, owner, o);
-            if (cand_gt(ob, best)) {
-                best = ob;
-                owner = oo;
-            }
-        }
-        if (lane == 0) {
-            s_red[wid] = best;
-            s_own[wid] = owner;
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            Cand b = s_red[0];
-            int ow = s_own[0];
-            for (int k = 1; k < nw; k++) {
-                if (cand_gt(s_red[k], b)) {
-                    b = s_red[k];
-                    ow = s_own[k];
-                }
-            }
-            C.cand[(int64_t)v * C.pi + r] = b.id;
-            C.cscore[(int64_t)v * C.pi + r] = b.id >= 0 ? b.eta : 0;
-            s_own[32] = b.id >= 0 ? ow : -1;
-        }
-        __syncthreads();
-        if ((int)threadIdx.x == s_own[32]) tl.pop();
-        __syncthreads();
+        const Cand b = warp_pop_best(tl);
+        if (lane == 0) s_top[wid * PIMAX + r] = b;
     }
+    __syncthreads();
+    if (wid == 0) {
+        TopList<PIMAX> m;
+        m.init();
+        for (int i = lane; i < nw * C.pi; i += 32) m.push(s_top[(i / C.pi) * PIMAX + (i % C.pi)]);
+        for (int r = 0; r < C.pi; r++) {
+            const Cand b = warp_pop_best(m);
+            if (lane == 0) {
+                C.cand[(int64_t)v * C.pi + r] = b.id;
+                C.cscore[(int64_t)v * C.pi + r] = b.id >= 0 ? b.eta : 0;
+            }
+        }
+    }
+    __syncthreads();
 }
 
 __device__ __forceinline__ bool pair_valid(const PropCtx &C, int32_t v, int32_t m, int32_t inter) {
@@ -204,47 +222,117 @@ __device__ __forceinline__ int32_t block_sum_i32(int32_t x, int32_t *s_tmp) {
     return t;
 }
 
-// The group's hyperedges of 2..32 pins, one per thread (t = base + tid,
-// base stepping by `step` over v's incidence, uniform across each warp): the
-// j-th pins of a warp's 32 hyperedges are combined by neighbour (match_any)
-// and one table update per distinct neighbour carries the warp's sums of q(e)
-// and of the inbound-overlap counts.  q(e) <= 2^40 is summed as two 21-bit
-// halves so that 32-bit warp reductions cannot overflow.
-template <class Ins>
-__device__ __forceinline__ void small_edges_aggregated(const PropCtx &C, int32_t v, int32_t i0, int32_t deg,
-                                                       int32_t nin_v, int tid, int step, const int *stop, Ins ins) {
+// One chunk of v's incidence for the calling warp: lane l takes the
+// hyperedge at incidence index t = base + l (none when t >= deg).  Hyperedges
+// of 2..32 pins: the j-th pins of the warp's hyperedges are combined by
+// neighbour (match_any) and one table update per distinct neighbour carries
+// the warp's sums of q(e) and of the inbound-overlap counts; q(e) <= 2^40 is
+// summed as two 21-bit halves so that 32-bit warp reductions cannot
+// overflow.  Larger hyperedges go to big(e, t) when it is given, else the
+// warp takes them one at a time, lanes over pins.
+template <class Ins, class Big>
+__device__ __forceinline__ void warp_chunk(const PropCtx &C, int32_t v, int32_t i0, int32_t deg, int32_t nin_v,
+                                           int32_t t, Ins &ins, Big *big) {
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
-    for (int32_t base = 0; base < deg; base += step) {
-        if (stop && __any_sync(FULL, *(volatile const int *)stop)) break;
-        const int32_t t = base + tid;
-        int32_t a = 0, sz = 0, dst0 = 0;
-        unsigned long long qe = 0;
-        bool vin = false;
-        if (t < deg) {
-            const int32_t e = C.inc[i0 + t];
-            a = C.off[e];
-            sz = C.off[e + 1] - a;
-            if (sz < 2 || sz > 32) {
-                sz = 0;
-            } else {
-                dst0 = a + C.nsrc[e];
-                qe = C.q[e];
-                vin = t < nin_v;
-            }
-        }
-        const int jmax = (int)__reduce_max_sync(FULL, (unsigned)sz);
-        for (int j = 0; j < jmax; j++) {
-            int32_t m = j < sz ? C.pin[a + j] : -1;
-            if (m == v) m = -1;
-            const unsigned g = __match_any_sync(FULL, m);
-            const bool on = m >= 0;
-            const unsigned lo = __reduce_add_sync(g, on ? (unsigned)(qe & 0x1FFFFFull) : 0u);
-            const unsigned hi = __reduce_add_sync(g, on ? (unsigned)(qe >> 21) : 0u);
-            const unsigned ic = __reduce_add_sync(g, (on && vin && a + j >= dst0) ? 1u : 0u);
-            if (on && lane == __ffs(g) - 1) ins(m, (unsigned long long)lo + ((unsigned long long)hi << 21), ic);
+    const uint32_t lt = (1u << lane) - 1u;
+    int32_t e = -1, a = 0, sz = 0, dst0 = 0;
+    unsigned long long qe = 0;
+    bool vin = false;
+    if (t < deg) {
+        e = C.inc[i0 + t];
+        a = C.off[e];
+        sz = C.off[e + 1] - a;
+        if (sz < 2) {
+            sz = 0;
+        } else {
+            dst0 = a + C.nsrc[e];
+            qe = C.q[e];
+            vin = t < nin_v;
         }
     }
+    const bool large = sz > 32;
+    if (large && big) (*big)(e, t);
+    const int32_t len = large ? 0 : sz;
+    const int jmax = (int)__reduce_max_sync(FULL, (unsigned)len);
+    for (int j = 0; j < jmax; j++) {
+        int32_t m = j < len ? C.pin[a + j] : -1;
+        if (m == v) m = -1;
+        const unsigned g = __match_any_sync(FULL, m);
+        const bool on = m >= 0;
+        const unsigned lo = __reduce_add_sync(g, on ? (unsigned)(qe & 0x1FFFFFull) : 0u);
+        const unsigned hi = __reduce_add_sync(g, on ? (unsigned)(qe >> 21) : 0u);
+        const unsigned ic = __reduce_add_sync(g, (on && vin && a + j >= dst0) ? 1u : 0u);
+        if (on && (g & lt) == 0u) ins(m, (unsigned long long)lo + ((unsigned long long)hi << 21), ic);
+    }
+    if (!big) {
+        unsigned bm = __ballot_sync(FULL, large);
+        while (bm) {
+            const int l = __ffs(bm) - 1;
+            bm &= bm - 1;
+            const int32_t la = __shfl_sync(FULL, a, l), lb = la + __shfl_sync(FULL, sz, l);
+            const int32_t ld0 = __shfl_sync(FULL, dst0, l);
+            const unsigned long long lq = __shfl_sync(FULL, qe, l);
+            const bool lvin = __shfl_sync(FULL, vin, l);
+            for (int32_t j = la + lane; j < lb; j += 32) {
+                const int32_t m = C.pin[j];
+                if (m != v) ins(m, lq, (lvin && j >= ld0) ? 1u : 0u);
+            }
+        }
+    }
+}
+
+struct NoBig {
+    __device__ void operator()(int32_t, int32_t) const {}
+};
+
+// A warp's walk over all of v's hyperedges.
+template <class Ins>
+__device__ __forceinline__ void warp_walk(const PropCtx &C, int32_t v, int32_t i0, int32_t deg, int32_t nin_v,
+                                          Ins ins) {
+    for (int32_t base = 0; base < deg; base += 32)
+        warp_chunk(C, v, i0, deg, nin_v, base + (int32_t)(threadIdx.x & 31), ins, (NoBig *)nullptr);
+}
+
+// A CTA's walk over all of v's hyperedges in chunks of blockDim.x: small
+// ones as above, larger ones queued in shared memory (s_big, blockDim.x
+// pairs (e, t); *s_nbig == 0 on entry and on exit) and then taken a warp
+// each, lanes over pins, so that every warp gets a share of them.  Stops
+// early (for every thread) once *stop is set.
+template <class Ins>
+__device__ void cta_walk(const PropCtx &C, int32_t v, int32_t i0, int32_t deg, int32_t nin_v, const int *stop,
+                         int32_t *s_big, int32_t *s_nbig, Ins ins) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    auto push = [&](int32_t e, int32_t t) {
+        const int32_t i = atomicAdd(s_nbig, 1);
+        s_big[2 * i] = e;
+        s_big[2 * i + 1] = t;
+    };
+    for (int32_t base = 0; base < deg; base += blockDim.x) {
+        if (__syncthreads_or(stop ? *(volatile const int *)stop : 0)) break;
+        warp_chunk(C, v, i0, deg, nin_v, base + (int32_t)threadIdx.x, ins, &push);
+        __syncthreads();
+        const int32_t nb = *(volatile int32_t *)s_nbig;
+        for (int32_t i = wid; i < nb; i += nw) {
+            const int32_t e = s_big[2 * i], t = s_big[2 * i + 1];
+            const int32_t a = C.off[e], b = C.off[e + 1];
+            const int32_t dst0 = a + C.nsrc[e];
+            const unsigned long long qe = C.q[e];
+            const bool vin = t < nin_v;
+            // the next pin is loaded before the current one is inserted
+            int32_t j = a + lane;
+            int32_t mn = j < b ? __ldg(&C.pin[j]) : -1;
+            while (j < b) {
+                const int32_t m = mn, jn = j + 32;
+                mn = jn < b ? __ldg(&C.pin[jn]) : -1;
+                if (m != v) ins(m, qe, (vin && j >= dst0) ? 1u : 0u);
+                j = jn;
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) *s_nbig = 0;
+    }
+    __syncthreads();
 }
 
 // ---------------------------------------------------------------- dense table
@@ -255,41 +343,26 @@ __global__ void __launch_bounds__(BT) k_propose_dense(PropCtx C, const int32_t *
     extern __shared__ __align__(16) unsigned char smem[];
     unsigned long long *eta = reinterpret_cast<unsigned long long *>(smem);
     uint32_t *inter = reinterpret_cast<uint32_t *>(eta + C.n);
-    __shared__ Cand s_red[32];
-    __shared__ int s_own[33];
+    __shared__ Cand s_top[32 * PIMAX];
+    __shared__ int32_t s_big[2 * BT];
+    __shared__ int32_t s_nbig;
     __shared__ int32_t s_tmp[32];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = BT / 32;
     const int32_t count = *count_p;
     if (count == 0) return;
     for (int32_t i = threadIdx.x; i < C.n; i += BT) {
         eta[i] = 0;
         inter[i] = 0;
     }
+    if (threadIdx.x == 0) s_nbig = 0;
     __syncthreads();
     const uint64_t cap = *C.cap;
     for (int32_t k = blockIdx.x; k < count; k += gridDim.x) {
         const int32_t v = list[k];
         const int32_t i0 = C.ioff[v], deg = C.ioff[v + 1] - i0, nin_v = C.nin[v];
-        // hyperedges of 2..32 pins: one per thread, combined across each warp
-        small_edges_aggregated(C, v, i0, deg, nin_v, (int)threadIdx.x, BT, nullptr,
-                               [&](int32_t m, unsigned long long eq, uint32_t ic) {
-                                   atomicAdd(&eta[m], eq);
-                                   if (ic) atomicAdd(&inter[m], ic);
-                               });
-        for (int32_t t = wid; t < deg; t += nw) {   // larger hyperedges: lanes over pins
-            const int32_t e = C.inc[i0 + t];
-            const int32_t a = C.off[e], b = C.off[e + 1];
-            if (b - a <= 32) continue;
-            const int32_t dst0 = a + C.nsrc[e];
-            const unsigned long long qe = C.q[e];
-            const bool vin = t < nin_v;
-            for (int32_t j = a + lane; j < b; j += 32) {
-                const int32_t m = C.pin[j];
-                if (m == v) continue;
-                atomicAdd(&eta[m], qe);
-                if (vin && j >= dst0) atomicAdd(&inter[m], 1u);
-            }
-        }
+        cta_walk(C, v, i0, deg, nin_v, nullptr, s_big, &s_nbig, [&](int32_t m, unsigned long long eq, uint32_t ic) {
+            add_u64_split(&eta[m], eq);
+            if (ic) atomicAdd(&inter[m], ic);
+        });
         __syncthreads();
         TopList<PIMAX> tl;
         tl.init();
@@ -306,7 +379,7 @@ __global__ void __launch_bounds__(BT) k_propose_dense(PropCtx C, const int32_t *
         }
         int32_t tot = block_sum_i32(cnt, s_tmp);
         if (threadIdx.x == 0) C.nbcnt[v] = tot;
-        block_emit_top<PIMAX>(tl, C, v, s_red, s_own);
+        block_emit_top<PIMAX>(tl, C, v, s_top);
     }
 }
 
@@ -316,7 +389,7 @@ __global__ void __launch_bounds__(BT) k_propose_dense(PropCtx C, const int32_t *
 // spread over the lanes (one hyperedge per lane), larger ones lane per pin.
 constexpr int WP_T = 256;
 __device__ __forceinline__ uint32_t hslot_w(int32_t m, uint32_t mask) {
-    return ((uint32_t)m * 0x9E3779B1u) & mask;
+    return mask ? ((uint32_t)m * 0x9E3779B1u) >> __clz(mask) : 0u;   // top bits (Fibonacci hashing)
 }
 __device__ __forceinline__ void warp_insert(int32_t *keys, unsigned long long *eta, uint32_t *inter, uint32_t mask,
                                             uint32_t cap, int32_t m, unsigned long long qe, uint32_t ninter) {
@@ -328,7 +401,7 @@ __device__ __forceinline__ void warp_insert(int32_t *keys, unsigned long long *e
             k = old == -1 ? m : old;
         }
         if (k == m) {
-            atomicAdd(&eta[h], qe);
+            add_u64_split(&eta[h], qe);
             if (ninter) atomicAdd(&inter[h], ninter);
             return;
         }
@@ -361,24 +434,10 @@ __global__ void __launch_bounds__(WP_T) k_propose_warp(PropCtx C, const int32_t 
     for (int64_t k = gw; k < count; k += nw) {
         const int32_t v = list[k];
         const int32_t i0 = C.ioff[v], deg = C.ioff[v + 1] - i0, nin_v = C.nin[v];
-        // hyperedges of 2..32 pins: one per lane, combined across the warp
-        small_edges_aggregated(C, v, i0, deg, nin_v, lane, 32, nullptr,
-                               [&](int32_t m, unsigned long long eq, uint32_t ic) {
-                                   warp_insert(keys, eta, inter, mask, cap, m, eq, ic);
-                               });
-        // larger hyperedges: lanes over pins
-        for (int32_t t = 0; t < deg; t++) {
-            const int32_t e = C.inc[i0 + t];
-            const int32_t a = C.off[e], b = C.off[e + 1];
-            if (b - a <= 32) continue;
-            const int32_t dst0 = a + C.nsrc[e];
-            const unsigned long long qe = C.q[e];
-            const bool vin = t < nin_v;
-            for (int32_t j = a + lane; j < b; j += 32) {
-                const int32_t m = C.pin[j];
-                if (m != v) warp_insert(keys, eta, inter, mask, cap, m, qe, (vin && j >= dst0) ? 1u : 0u);
-            }
-        }
+        // all incident hyperedges, one per lane, combined across the warp
+        warp_walk(C, v, i0, deg, nin_v, [&](int32_t m, unsigned long long eq, uint32_t ic) {
+            warp_insert(keys, eta, inter, mask, cap, m, eq, ic);
+        });
         __syncwarp();
         TopList<PIMAX> tl;
         tl.init();
@@ -418,7 +477,7 @@ __global__ void __launch_bounds__(WP_T) k_propose_warp(PropCtx C, const int32_t 
 
 // ---------------------------------------------------------------- hashed table
 __device__ __forceinline__ uint32_t hslot(int32_t m, uint32_t mask) {
-    return ((uint32_t)m * 0x9E3779B1u) & mask;
+    return mask ? ((uint32_t)m * 0x9E3779B1u) >> __clz(mask) : 0u;   // top bits (Fibonacci hashing)
 }
 
 // Table of `cap` slots at keys/eta/inter (shared or global).  Nodes from
@@ -427,9 +486,8 @@ __device__ __forceinline__ uint32_t hslot(int32_t m, uint32_t mask) {
 template <int PIMAX>
 __device__ void propose_hashed_node(const PropCtx &C, int32_t v, int32_t *keys, unsigned long long *eta,
                                     uint32_t *inter, uint32_t cap, uint32_t limit, int32_t *slots, int32_t *ovf,
-                                    int32_t *ovf_n, int *s_flag, int32_t *s_cnt, Cand *s_red, int *s_own,
-                                    int32_t *s_tmp) {
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+                                    int32_t *ovf_n, int *s_flag, int32_t *s_cnt, Cand *s_top,
+                                    int32_t *s_tmp, int32_t *s_big, int32_t *s_nbig) {
     const uint32_t mask = cap - 1;
     const int32_t i0 = C.ioff[v], deg = C.ioff[v + 1] - i0, nin_v = C.nin[v];
     auto insert_n = [&](int32_t m, unsigned long long qe, uint32_t ninter) {
@@ -448,31 +506,14 @@ __device__ void propose_hashed_node(const PropCtx &C, int32_t v, int32_t *keys, 
                 }
             }
             if (k == m) {
-                atomicAdd(&eta[h], qe);
+                add_u64_split(&eta[h], qe);
                 if (ninter) atomicAdd(&inter[h], ninter);
                 return;
             }
             h = (h + 1) & mask;
         }
     };
-    auto insert = [&](int32_t m, unsigned long long qe, bool add_inter) { insert_n(m, qe, add_inter ? 1u : 0u); };
-    // hyperedges of 2..32 pins: one per thread, combined across each warp
-    small_edges_aggregated(C, v, i0, deg, nin_v, (int)threadIdx.x, (int)blockDim.x, s_flag,
-                           [&](int32_t m, unsigned long long eq, uint32_t ic) { insert_n(m, eq, ic); });
-    // larger hyperedges: a warp each, lanes over pins
-    for (int32_t t = wid; t < deg; t += nw) {
-        if (*(volatile int *)s_flag) break;
-        const int32_t e = C.inc[i0 + t];
-        const int32_t a = C.off[e], b = C.off[e + 1];
-        if (b - a <= 32) continue;
-        const int32_t dst0 = a + C.nsrc[e];
-        const unsigned long long qe = C.q[e];
-        const bool vin = t < nin_v;
-        for (int32_t j = a + lane; j < b; j += 32) {
-            const int32_t m = C.pin[j];
-            if (m != v) insert(m, qe, vin && j >= dst0);
-        }
-    }
+    cta_walk(C, v, i0, deg, nin_v, s_flag, s_big, s_nbig, insert_n);
     __syncthreads();
     const int overflow = *s_flag;
     const uint64_t capn = *C.cap;
@@ -510,7 +551,7 @@ __device__ void propose_hashed_node(const PropCtx &C, int32_t v, int32_t *keys, 
         C.nbcnt[v] = tot;
         *s_cnt = 0;
     }
-    block_emit_top<PIMAX>(tl, C, v, s_red, s_own);
+    block_emit_top<PIMAX>(tl, C, v, s_top);
 }
 
 template <int PIMAX, int BT>
@@ -521,8 +562,9 @@ __global__ void __launch_bounds__(BT) k_propose_smem(PropCtx C, const int32_t *l
     uint32_t *inter = reinterpret_cast<uint32_t *>(eta + cap);
     int32_t *keys = reinterpret_cast<int32_t *>(inter + cap);
     int32_t *slots = keys + cap;
-    __shared__ Cand s_red[32];
-    __shared__ int s_own[33];
+    __shared__ Cand s_top[32 * PIMAX];
+    __shared__ int32_t s_big[2 * BT];
+    __shared__ int32_t s_nbig;
     __shared__ int32_t s_tmp[32];
     __shared__ int s_flag;
     __shared__ int32_t s_cnt;
@@ -536,11 +578,12 @@ __global__ void __launch_bounds__(BT) k_propose_smem(PropCtx C, const int32_t *l
     if (threadIdx.x == 0) {
         s_flag = 0;
         s_cnt = 0;
+        s_nbig = 0;
     }
     __syncthreads();
     for (int32_t k = blockIdx.x; k < count; k += gridDim.x)
         propose_hashed_node<PIMAX>(C, list[k], keys, eta, inter, cap, limit, slots, ovf, ovf_n, &s_flag, &s_cnt,
-                                   s_red, s_own, s_tmp);
+                                   s_top, s_tmp, s_big, &s_nbig);
 }
 
 // one CTA region of gcap slots in global memory per CTA (clean on entry and
@@ -550,8 +593,9 @@ __global__ void __launch_bounds__(PT) k_propose_global(PropCtx C, const int32_t 
                                                        uint32_t gcap, int32_t *gkeys, unsigned long long *geta,
                                                        uint32_t *ginter, int32_t *gslots, int32_t *err_list,
                                                        int32_t *err_n) {
-    __shared__ Cand s_red[32];
-    __shared__ int s_own[33];
+    __shared__ Cand s_top[32 * PIMAX];
+    __shared__ int32_t s_big[2 * PT];
+    __shared__ int32_t s_nbig;
     __shared__ int32_t s_tmp[32];
     __shared__ int s_flag;
     __shared__ int32_t s_cnt;
@@ -561,11 +605,12 @@ __global__ void __launch_bounds__(PT) k_propose_global(PropCtx C, const int32_t 
     if (threadIdx.x == 0) {
         s_flag = 0;
         s_cnt = 0;
+        s_nbig = 0;
     }
     __syncthreads();
     for (int32_t k = blockIdx.x; k < count; k += gridDim.x)
         propose_hashed_node<PIMAX>(C, list[k], gkeys + o, geta + o, ginter + o, gcap, gcap - 1, gslots + o, err_list,
-                                   err_n, &s_flag, &s_cnt, s_red, s_own, s_tmp);
+                                   err_n, &s_flag, &s_cnt, s_top, s_tmp, s_big, &s_nbig);
 }
 
 // ---------------------------------------------------------------- node tiers
@@ -573,7 +618,7 @@ __global__ void __launch_bounds__(PT) k_propose_global(PropCtx C, const int32_t 
 // tier: traversals large enough to keep a 1024-thread CTA busy
 // dense tier (level of at most DENSE_N nodes): neighbourhood bound above
 // dense_bound; the others use hashed tables
-constexpr long long WARP_VISITS = 4096, HUB_VISITS = 65536;
+constexpr long long WARP_VISITS = 4096, HUB_VISITS = 262144;
 __global__ void k_tiers(const int32_t *bound, const long long *vis, int32_t n, uint32_t warp_limit,
                         int32_t dense_bound, int32_t *lW, int32_t *lB, int32_t *lH, int32_t *lD, int32_t *lDH,
                         int32_t *cnt) {
@@ -603,10 +648,10 @@ struct CoarsenWs {
     uint32_t *ginter;
     int32_t *gslots;
     // best-effort pairing and matching
-    int32_t *flag, *pos, *target, *ccount, *coff, *fillpos, *kids, *best;
+    int32_t *flag, *pos, *target, *ccount, *fillpos, *best;
     uint32_t *ikeys, *iids;
     uint64_t *score;
-    long long *ss0, *ss10, *sum0;
+    long long *ss0, *ss10, *sum0, *kmax;
     LevelBox *box;
 };
 
@@ -692,8 +737,14 @@ __global__ void k_iso_pair(const uint32_t *ids, const int32_t *cntp, const int32
 
 // ---------------------------------------------------------------- matching
 __global__ void k_targets(const int32_t *cand, const uint64_t *cscore, int32_t pi, const int32_t *mate, int32_t n,
-                          int32_t *target, uint64_t *score) {
+                          int32_t *target, uint64_t *score, long long *sum0, long long *kmax, int32_t *best,
+                          int32_t *ccount, int32_t *pending) {
     GRID_STRIDE(v, (int64_t)n) {
+        sum0[v] = 0;
+        kmax[v] = LLONG_MIN;
+        best[v] = -1;
+        ccount[v] = 0;
+        pending[v] = 0;
         int32_t t = -1;
         uint64_t sc = 0;
         if (mate[v] < 0) {
@@ -712,85 +763,90 @@ __global__ void k_targets(const int32_t *cand, const uint64_t *cscore, int32_t p
     }
 }
 
-// child(n) \ R: count, then fill
-__global__ void k_child_count(const int32_t *target, int32_t n, int32_t *ccount) {
+// |child(n) \ R| per node, twice: the count and the counter of children still to finish
+__global__ void k_child_count(const int32_t *target, int32_t n, int32_t *ccount, int32_t *pending) {
     GRID_STRIDE(v, (int64_t)n) {
         int32_t t = target[v];
-        if (t >= 0 && target[t] != v) atomicAdd(&ccount[t], 1);
-    }
-}
-__global__ void k_child_fill(const int32_t *target, int32_t n, const int32_t *coff, int32_t *fillpos, int32_t *kids) {
-    GRID_STRIDE(v, (int64_t)n) {
-        int32_t t = target[v];
-        if (t >= 0 && target[t] != v) kids[coff[t] + atomicAdd(&fillpos[t], 1)] = (int32_t)v;
+        if (t >= 0 && target[t] != v) {
+            atomicAdd(&ccount[t], 1);
+            atomicAdd(&pending[t], 1);
+        }
     }
 }
 
 struct DpCtx {
     int32_t n;
-    const int32_t *target, *coff, *kids;
+    const int32_t *target, *ccount;   // ccount: |child(n) \ R|
     const uint64_t *score;
-    int32_t *pending;
-    long long *ss0, *ss10, *sum0;
+    int32_t *pending;                 // children still to finish
+    long long *ss0, *ss10;
+    long long *sum0;                  // sum of the children's ss0 (accumulated by them)
+    long long *kmax;                  // max of the children's ss1-0 (accumulated by them)
     int32_t *best;
     uint32_t *err;
 };
 
-// Bottom-up (Eq. 7, 8, 10): a thread starts at every leaf and climbs; the
-// thread completing the last child of a node continues with that node, so a
-// node is evaluated once, after all of its children.  A parent with a single
-// child is reached only by that child's thread: it takes the child's values
-// from registers and needs neither the fence nor the arrival counter, so a
-// long chain costs one dependent load of target per step.
+// Bottom-up (Eq. 7, 8, 10): a thread starts at every leaf and climbs.  A
+// finished child adds its ss0 to the parent's sum0 and raises the parent's
+// kmax to its ss1-0, then counts itself off; the thread finishing the last
+// child continues with the parent, whose children are then all accounted
+// for, so no node's children are ever walked one by one.  A parent with a
+// single child takes the child's values from registers (plain stores, no
+// fence, no counter).  The best child itself (largest ss1-0, ties to the
+// larger id) is found afterwards by k_best_child.
 __global__ void k_dp_up(DpCtx D) {
     GRID_STRIDE(v0, (int64_t)D.n) {
         int32_t v = (int32_t)v0;
-        if (D.coff[v + 1] != D.coff[v]) continue;   // not a leaf
+        if (D.ccount[v] != 0) continue;             // not a leaf
         if (D.target[v] < 0) continue;              // isolated, no proposal edge
         int32_t cur = v;
-        int32_t hc = -1;                            // child we climbed from (its values below)
-        long long hc0 = 0, hc10 = 0;
+        bool carried = false;                       // cur's single child's values in registers
+        long long cs0 = 0, cmax = 0;
         for (int32_t steps = 0;; steps++) {
             if (steps > D.n) {
                 atomicOr(D.err, E_TIMEOUT);
                 break;
             }
-            const int32_t k0 = D.coff[cur], k1 = D.coff[cur + 1];
-            long long s0 = 0, bss = 0;
-            int32_t b = -1;
-            if (hc >= 0 && k1 - k0 == 1) {
-                s0 = hc0;
-                b = hc;
-                bss = hc10;
-            } else {
-                for (int32_t k = k0; k < k1; k++) {
-                    int32_t c = D.kids[k];
-                    long long c0 = __ldcg(&D.ss0[c]), c10 = __ldcg(&D.ss10[c]);
-                    s0 += c0;
-                    if (b < 0 || c10 > bss || (c10 == bss && c > b)) {
-                        b = c;
-                        bss = c10;
-                    }
-                }
+            const int32_t nk = D.ccount[cur];
+            long long s0 = 0, mx = 0;
+            if (carried) {
+                s0 = cs0;
+                mx = cmax;
+            } else if (nk > 0) {
+                s0 = __ldcg(&D.sum0[cur]);
+                mx = __ldcg(&D.kmax[cur]);
             }
-            long long my0 = s0 + ((b >= 0 && bss > 0) ? bss : 0);
-            __stcg(&D.sum0[cur], s0);
+            const long long my0 = s0 + ((nk > 0 && mx > 0) ? mx : 0);
             __stcg(&D.ss0[cur], my0);
-            D.best[cur] = b;
-            int32_t t = D.target[cur];
+            const int32_t t = D.target[cur];
             if (t < 0 || D.target[t] == cur) break;   // a root
             const long long my10 = (long long)D.score[cur] + s0 - my0;
             __stcg(&D.ss10[cur], my10);
-            if (D.coff[t + 1] - D.coff[t] > 1) {
+            if (D.ccount[t] == 1) {
+                __stcg(&D.sum0[t], my0);
+                __stcg(&D.kmax[t], my10);
+                carried = true;
+                cs0 = my0;
+                cmax = my10;
+            } else {
+                atomicAdd((unsigned long long *)&D.sum0[t], (unsigned long long)my0);
+                atomicMax(&D.kmax[t], my10);
                 __threadfence();
                 if (atomicSub(&D.pending[t], 1) != 1) break;
                 __threadfence();
+                carried = false;
             }
-            hc = cur;
-            hc0 = my0;
-            hc10 = my10;
             cur = t;
         }
+    }
+}
+
+// best(t) = the child of t (partner root excluded) with the largest ss1-0,
+// ties to the larger id
+__global__ void k_best_child(DpCtx D) {
+    GRID_STRIDE(v0, (int64_t)D.n) {
+        const int32_t v = (int32_t)v0, t = D.target[v];
+        if (t >= 0 && D.target[t] != v && __ldcg(&D.ss10[v]) == __ldcg(&D.kmax[t])) atomicMax(&D.best[t], v);
     }
 }
 
@@ -883,13 +939,12 @@ CoarsenWs *coarsen_workspace(int32_t n, int32_t e, const Params &P, Arena &A) {
     W->target = A.get<int32_t>(n);
     W->score = A.get<uint64_t>(n);
     W->ccount = A.get<int32_t>(n + 1);
-    W->coff = A.get<int32_t>(n + 1);
     W->fillpos = A.get<int32_t>(n);
-    W->kids = A.get<int32_t>(n);
     W->best = A.get<int32_t>(n);
     W->ss0 = A.get<long long>(n);
     W->ss10 = A.get<long long>(n);
     W->sum0 = A.get<long long>(n);
+    W->kmax = A.get<long long>(n);
     W->box = A.get<LevelBox>(1);
     return W;
 }
@@ -899,8 +954,8 @@ void coarsen_workspace_free(CoarsenWs *W, Arena &A) {
     for (void *p : {(void *)W->nsum, (void *)W->vis, (void *)W->q, (void *)W->cand, (void *)W->cscore, (void *)W->lW, (void *)W->lB, (void *)W->lC,
                     (void *)W->lG, (void *)W->lH, (void *)W->lD, (void *)W->lDH, (void *)W->cnt, (void *)W->gkeys, (void *)W->geta, (void *)W->ginter, (void *)W->gslots,
                     (void *)W->flag, (void *)W->pos, (void *)W->ikeys, (void *)W->iids, (void *)W->target,
-                    (void *)W->score, (void *)W->ccount, (void *)W->coff, (void *)W->fillpos, (void *)W->kids,
-                    (void *)W->best, (void *)W->ss0, (void *)W->ss10, (void *)W->sum0, (void *)W->box})
+                    (void *)W->score, (void *)W->ccount, (void *)W->fillpos,
+                    (void *)W->best, (void *)W->ss0, (void *)W->ss10, (void *)W->sum0, (void *)W->kmax, (void *)W->box})
         A.release(p);
     delete W;
 }
@@ -983,27 +1038,24 @@ void coarsen_level(Level &L, int32_t level, const int32_t *w, const Params &P, i
     DpCtx D;
     D.n = n;
     D.target = W.target;
-    D.coff = W.coff;
-    D.kids = W.kids;
+    D.ccount = W.ccount;
     D.score = W.score;
     D.pending = W.fillpos;
     D.ss0 = W.ss0;
     D.ss10 = W.ss10;
     D.sum0 = W.sum0;
+    D.kmax = W.kmax;
     D.best = W.best;
     D.err = err_dev;
     for (int32_t r = 0; r < pi; r++) {
-        k_targets<<<grid_of(n, 256), 256, 0, s>>>(W.cand, W.cscore, pi, mate, n, W.target, W.score);
+        k_targets<<<grid_of(n, 256), 256, 0, s>>>(W.cand, W.cscore, pi, mate, n, W.target, W.score, W.sum0, W.kmax,
+                                                  W.best, W.ccount, W.fillpos);
         HP_LAUNCH_CHECK();
-        HPC(cudaMemsetAsync(W.ccount, 0, sizeof(int32_t) * (n + 1), s));
-        k_child_count<<<grid_of(n, 256), 256, 0, s>>>(W.target, n, W.ccount);
+        k_child_count<<<grid_of(n, 256), 256, 0, s>>>(W.target, n, W.ccount, W.fillpos);
         HP_LAUNCH_CHECK();
-        scan_excl(W.ccount, W.coff, n + 1, nullptr, A);
-        HPC(cudaMemsetAsync(W.fillpos, 0, sizeof(int32_t) * n, s));
-        k_child_fill<<<grid_of(n, 256), 256, 0, s>>>(W.target, n, W.coff, W.fillpos, W.kids);
-        HP_LAUNCH_CHECK();
-        HPC(cudaMemcpyAsync(W.fillpos, W.ccount, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s));
         k_dp_up<<<grid_of(n, 256), 256, 0, s>>>(D);
+        HP_LAUNCH_CHECK();
+        k_best_child<<<grid_of(n, 256), 256, 0, s>>>(D);
         HP_LAUNCH_CHECK();
         k_dp_down<<<grid_of(n, 256), 256, 0, s>>>(D, W.target, mate, &box->pairs);
         HP_LAUNCH_CHECK();

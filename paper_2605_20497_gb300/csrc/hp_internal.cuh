@@ -90,6 +90,14 @@ void iota_i32(int32_t *p, int64_t n, cudaStream_t s);
 // items in index order ranked within a warp by match and across warps by
 // per-warp digit counts.  Ends with the sorted data back in keys/vals and a
 // __syncthreads.
+// Stable LSD radix sort (8-bit digits) of n (key, value) pairs by one CTA of
+// up to 1024 threads, n <= 8 * blockDim.x.  keys/vals (global) are staged in
+// smem (two buffers of `cap` >= n keys and values); s_wc holds 32 * 256
+// counters, s_hist 256 + 33 words.  Warp w owns items [w * 32S, (w + 1) * 32S)
+// with S = ceil(n / blockDim.x), slot k of lane l being item w * 32S + 32k + l,
+// so one round per pass ranks every item: within a warp slot by slot
+// (match_any), then across warps by an exclusive scan over (digit, warp).
+constexpr int BRS_SLOTS = 8;
 template <class K>
 __device__ void block_radix_sort(K *keys, uint32_t *vals, int n, int passes, int cap, unsigned char *smem,
                                  uint32_t *s_wc, uint32_t *s_hist) {
@@ -97,10 +105,11 @@ __device__ void block_radix_sort(K *keys, uint32_t *vals, int n, int passes, int
     K *kb = ka + cap;
     uint32_t *va = reinterpret_cast<uint32_t *>(kb + cap);
     uint32_t *vb = va + cap;
-    const int t = threadIdx.x, T = blockDim.x, lane = t & 31, w = t >> 5;
+    const int t = threadIdx.x, T = blockDim.x, lane = t & 31, w = t >> 5, nwarp = T >> 5;
     const uint32_t lt = (1u << lane) - 1u;
     __syncthreads();
     if (n <= 1) return;
+    const int S = (n + T - 1) / T;
     for (int i = t; i < n; i += T) {
         ka[i] = keys[i];
         va[i] = vals[i];
@@ -108,46 +117,73 @@ __device__ void block_radix_sort(K *keys, uint32_t *vals, int n, int passes, int
     __syncthreads();
     for (int p = 0; p < passes; p++) {
         const int shift = 8 * p;
-        for (int d = t; d < 256; d += T) s_hist[d] = 0;
-        __syncthreads();
-        for (int i = t; i < n; i += T) atomicAdd(&s_hist[(uint32_t)(ka[i] >> shift) & 255u], 1u);
-        __syncthreads();
-        if (t == 0) {
-            uint32_t run = 0;
-            for (int d = 0; d < 256; d++) {
-                uint32_t c = s_hist[d];
-                s_hist[d] = run;
-                run += c;
+        uint32_t *run = s_wc + w * 256;
+        for (int d = lane; d < 256; d += 32) run[d] = 0;
+        __syncwarp();
+        uint32_t myrank[BRS_SLOTS], mydig[BRS_SLOTS];
+#pragma unroll
+        for (int k = 0; k < BRS_SLOTS; k++) {
+            if (k < S) {
+                const int i = w * 32 * S + 32 * k + lane;
+                const uint32_t d = i < n ? ((uint32_t)(ka[i] >> shift) & 255u) : 256u;
+                const uint32_t peers = __match_any_sync(0xffffffffu, d);
+                uint32_t base = 0;
+                if (d < 256u) base = run[d];
+                __syncwarp();
+                myrank[k] = base + __popc(peers & lt);
+                mydig[k] = d;
+                if (d < 256u && (peers & lt) == 0) run[d] = base + __popc(peers);
+                __syncwarp();
             }
         }
         __syncthreads();
-        for (int r0 = 0; r0 < n; r0 += T) {
-            const int i = r0 + t;
-            const bool valid = i < n;
-            const uint32_t d = valid ? ((uint32_t)(ka[i] >> shift) & 255u) : 256u;
-            const uint32_t peers = __match_any_sync(0xffffffffu, d);
-            const uint32_t rank = __popc(peers & lt);
-            for (int k = t; k < 32 * 256; k += T) s_wc[k] = 0;
-            __syncthreads();
-            if (valid && rank == 0) s_wc[w * 256 + d] = __popc(peers);
-            __syncthreads();
-            for (int d2 = t; d2 < 256; d2 += T) {
-                uint32_t run = 0, base = s_hist[d2];
-                for (int k = 0; k < 32; k++) {
-                    uint32_t c = s_wc[k * 256 + d2];
-                    s_wc[k * 256 + d2] = base + run;
-                    run += c;
-                }
-                s_hist[d2] = base + run;
+        // exclusive scan over the (digit, warp) counters, digit-major: thread
+        // t takes the counters of digits [8t / nwarp ...) in groups of 8
+        const int total = 256 * nwarp;
+        const int per = (total + T - 1) / T;
+        uint32_t loc = 0;
+        for (int q = 0; q < per; q++) {
+            const int e = t * per + q;
+            if (e < total) loc += s_wc[(e % nwarp) * 256 + e / nwarp];
+        }
+        uint32_t inc = loc;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t u = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += u;
+        }
+        if (lane == 31) s_hist[w] = inc;
+        __syncthreads();
+        if (w == 0) {
+            const uint32_t y = lane < nwarp ? s_hist[lane] : 0u;
+            uint32_t yi = y;
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t u = __shfl_up_sync(0xffffffffu, yi, o);
+                if (lane >= o) yi += u;
             }
-            __syncthreads();
-            if (valid) {
-                uint32_t pos = s_wc[w * 256 + d] + rank;
+            if (lane < nwarp) s_hist[256 + lane] = yi - y;
+        }
+        __syncthreads();
+        uint32_t off = s_hist[256 + w] + inc - loc;
+        for (int q = 0; q < per; q++) {
+            const int e = t * per + q;
+            if (e < total) {
+                uint32_t *c = &s_wc[(e % nwarp) * 256 + e / nwarp];
+                const uint32_t x = *c;
+                *c = off;
+                off += x;
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < BRS_SLOTS; k++) {
+            if (k < S && mydig[k] < 256u) {
+                const int i = w * 32 * S + 32 * k + lane;
+                const uint32_t pos = s_wc[w * 256 + mydig[k]] + myrank[k];
                 kb[pos] = ka[i];
                 vb[pos] = va[i];
             }
-            __syncthreads();
         }
+        __syncthreads();
         K *tk = ka;
         ka = kb;
         kb = tk;

@@ -453,7 +453,7 @@ template <class K>
 __global__ void __launch_bounds__(SS_T) k_small_sort(K *keys, uint32_t *vals, const int32_t *n_dev, int passes) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ uint32_t s_wc[32][256];
-    __shared__ uint32_t s_hist[256];
+    __shared__ uint32_t s_hist[256 + 33];
     block_radix_sort<K>(keys, vals, *n_dev, passes, SMALL_SORT, smem, &s_wc[0][0], s_hist);
 }
 

@@ -29,7 +29,11 @@ struct Plist {
     int32_t *lam = nullptr;                                // [e] entries per hyperedge
 };
 
-__device__ __forceinline__ uint32_t hslot(int32_t x, uint32_t mask) { return ((uint32_t)x * 0x9E3779B1u) & mask; }
+// slot of key x in a table of mask + 1 (a power of two, >= 2) slots: the top
+// bits of a Fibonacci product, so that keys with equal low bits spread out
+__device__ __forceinline__ uint32_t hslot(int32_t x, uint32_t mask) {
+    return mask ? ((uint32_t)x * 0x9E3779B1u) >> __clz(mask) : 0u;
+}
 
 template <int G> __device__ __forceinline__ void gsync() {
     if (G == 32) __syncwarp();
@@ -308,7 +312,7 @@ __device__ void gains_node(int32_t v, const int32_t *off, const int32_t *ioff, c
             h = (h + 1) & mask;
         }
     };
-    // hyperedges with at most 8 parts: one per thread.  The k-th entries of a
+    // one cut hyperedge per thread.  The k-th entries of the pins lists of a
     // warp's 32 hyperedges are combined by part across the warp (match_any)
     // before one table update per distinct part, so that the few parts a
     // node touches are not hammered by every lane.
@@ -322,12 +326,8 @@ __device__ void gains_node(int32_t v, const int32_t *off, const int32_t *ioff, c
             if (t < c1) {
                 const int32_t e = inc[t];
                 lam = PL.lam[e];
-                if (lam <= 8) {
-                    a = off[e];
-                    we = (uint32_t)w[e];
-                } else {
-                    lam = 0;
-                }
+                a = off[e];
+                we = (uint32_t)w[e];
             }
             const int kmax = __reduce_max_sync(0xffffffffu, (unsigned)lam);
             for (int k = 0; k < kmax; k++) {
@@ -337,19 +337,6 @@ __device__ void gains_node(int32_t v, const int32_t *off, const int32_t *ioff, c
                 const unsigned sw = __reduce_add_sync(m, p >= 0 ? we : 0u);
                 if (p >= 0 && lane == __ffs(m) - 1) add(p, (long long)sw);
             }
-        }
-    }
-    for (int32_t t = ioff[v] + wid; t < ioff[v + 1]; t += nw) {
-        if (*(volatile int *)s_flag) break;
-        const int32_t e = inc[t];
-        const int32_t a = off[e];
-        if (off[e + 1] - a < 2) continue;
-        const int32_t lam = PL.lam[e];
-        if (lam <= 8) continue;
-        const long long we = w[e];
-        for (int32_t k = lane; k < lam; k += 32) {
-            const int32_t p = PL.p[a + k];
-            if (p != s) add(p, we);
         }
     }
     __syncthreads();
@@ -729,7 +716,7 @@ __global__ void k_plist_tiny(const int32_t *off, const int32_t *pin, const int32
 }
 
 // counters of one repetition (device)
-enum { C_CAND, C_MOVES, C_OVF, C_BAD, C_NH, C_BAD0, C_APPLIED, C_NV, C_HUB, C_CW, C_N };
+enum { C_CAND, C_MOVES, C_OVF, C_BAD, C_NH, C_BAD0, C_APPLIED, C_NV, C_HUB, C_CW, C_TOUCH, C_TTOUCH, C_N };
 
 // moves of at most SMALLM are sequenced and validated by one CTA each
 constexpr int SMALLM = 4096, SEQ_T = 1024;
@@ -1332,7 +1319,7 @@ struct SmallSeqArgs {
 __global__ void __launch_bounds__(SEQ_T) k_seq_small(SmallSeqArgs A) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ uint32_t s_wc[32 * 256];
-    __shared__ uint32_t s_hist[256];
+    __shared__ uint32_t s_hist[256 + 33];
     __shared__ int32_t s_tmp[40];
     const int32_t m = A.cnt[C_MOVES];
     if (m == 0 || m > SMALLM) return;
@@ -1397,7 +1384,7 @@ __global__ void __launch_bounds__(SEQ_T) k_val_small(ValCtx V, int32_t *cnt, int
                                                      int32_t *rho) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ uint32_t s_wc[32 * 256];
-    __shared__ uint32_t s_hist[256];
+    __shared__ uint32_t s_hist[256 + 33];
     __shared__ int32_t s_tmp[40];
     __shared__ long long s_ll[40];
     const int32_t m = cnt[C_MOVES];
@@ -1505,10 +1492,53 @@ __device__ void inseq_edge(const SeqSim &Q, int32_t e, int gt, int32_t *bk, int3
     gsync<G>();
 }
 
-constexpr int IS_T = 128;
-__global__ void __launch_bounds__(IS_T) k_inseq_small(SeqSim Q, const int32_t *list, int32_t count, int32_t emax,
-                                                      const int32_t *mcount) {
+// The hyperedges of `list` that hold a moved pin (lanes take one hyperedge
+// each; those of more than 32 pins are scanned by the whole warp).
+__global__ void k_touched(const int32_t *off, const int32_t *pin, const int32_t *mvpos, const int32_t *list,
+                          int32_t count, int32_t *out, int32_t *out_n, int32_t *tout, int32_t *tout_n,
+                          const int32_t *mcount) {
     if (*mcount == 0) return;
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int64_t step = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < count; base += step) {
+        const int64_t i = base + lane;
+        int32_t e = -1, a = 0, b = 0;
+        if (i < count) {
+            e = list[i];
+            a = off[e];
+            b = off[e + 1];
+        }
+        bool hit = false;
+        if (e >= 0 && b - a <= 32)
+            for (int32_t j = a; j < b && !hit; j++) hit = mvpos[pin[j]] >= 0;
+        unsigned big = __ballot_sync(FULL, e >= 0 && b - a > 32);
+        while (big) {
+            const int l = __ffs(big) - 1;
+            big &= big - 1;
+            const int32_t ea = __shfl_sync(FULL, a, l), eb = __shfl_sync(FULL, b, l);
+            bool found = false;
+            for (int32_t j0 = ea; j0 < eb; j0 += 32) {
+                const bool h = j0 + lane < eb && mvpos[pin[j0 + lane]] >= 0;
+                if (__any_sync(FULL, h)) {
+                    found = true;
+                    break;
+                }
+            }
+            if (lane == l) hit = found;
+        }
+        if (hit) {
+            if (b - a <= TINY_E) tout[atomicAdd(tout_n, 1)] = e;
+            else out[atomicAdd(out_n, 1)] = e;
+        }
+    }
+}
+
+constexpr int IS_T = 128;
+__global__ void __launch_bounds__(IS_T) k_inseq_small(SeqSim Q, const int32_t *list, const int32_t *count_p,
+                                                      int32_t emax, const int32_t *mcount) {
+    if (*mcount == 0) return;
+    const int32_t count = *count_p;
     extern __shared__ __align__(16) int32_t sm[];
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int32_t *base = sm + wid * (9 * emax + 1);
@@ -1530,6 +1560,79 @@ __global__ void __launch_bounds__(256) k_inseq_big(SeqSim Q, const int32_t *list
 }
 
 
+// In-sequence gains of hyperedges of at most TINY_E pins, one thread each:
+// the moved pins are taken in sequence order (ranks among at most TINY_E
+// distinct positions) and the parts they leave or enter are tracked in a
+// per-thread table of 2 TINY_E entries in shared memory.
+constexpr int IST_T = 128;
+__global__ void __launch_bounds__(IST_T) k_inseq_tiny(SeqSim Q, const int32_t *list, const int32_t *count_p,
+                                                       const int32_t *mcount) {
+    __shared__ int32_t s_tab[IST_T * 6 * TINY_E];
+    if (*mcount == 0) return;
+    const int32_t count = *count_p;
+    int32_t *tp = s_tab + threadIdx.x * 6 * TINY_E, *tc = tp + 2 * TINY_E, *tci = tc + 2 * TINY_E;
+    for (int64_t i = blockIdx.x * (int64_t)IST_T + threadIdx.x; i < count; i += (int64_t)gridDim.x * IST_T) {
+        const int32_t e = list[i];
+        const int32_t a = Q.off[e], sz = Q.off[e + 1] - a, d0 = Q.nsrc[e];
+        const long long we = Q.w[e];
+        const int32_t lam = Q.PL.lam[e];
+        int32_t kk[TINY_E];
+        int nm = 0;
+#pragma unroll
+        for (int j = 0; j < TINY_E; j++) {
+            kk[j] = 0x7fffffff;
+            if (j < sz) {
+                const int32_t k = Q.mvpos[Q.pin[a + j]];
+                if (k >= 0) {
+                    kk[j] = k;
+                    nm++;
+                }
+            }
+        }
+        int nt = 0;
+        for (int r = 0; r < nm; r++) {
+            // the moved pin of rank r (positions are distinct)
+            int32_t k = 0x7fffffff;
+            bool isdst = false;
+#pragma unroll
+            for (int j = 0; j < TINY_E; j++) {
+                int32_t rk = 0;
+#pragma unroll
+                for (int x = 0; x < TINY_E; x++) rk += kk[x] < kk[j];
+                if (kk[j] != 0x7fffffff && rk == r) {
+                    k = kk[j];
+                    isdst = j >= d0;
+                }
+            }
+            const int32_t mi = Q.seqmove[k];
+            const int32_t ps[2] = {Q.src[mi], Q.dst[mi]};
+            int32_t sl[2];
+            for (int h = 0; h < 2; h++) {
+                int32_t x = 0;
+                while (x < nt && tp[x] != ps[h]) x++;
+                if (x == nt) {
+                    const int32_t f = plist_find(Q.PL, a, lam, ps[h]);
+                    tp[x] = ps[h];
+                    tc[x] = f >= 0 ? Q.PL.cnt[f] : 0;
+                    tci[x] = f >= 0 ? Q.PL.cin[f] : 0;
+                    nt++;
+                }
+                sl[h] = x;
+            }
+            long long g = 0;
+            if (tc[sl[0]] == 1) g += we;
+            if (tc[sl[1]] == 0) g -= we;
+            if (g) atomicAdd(&Q.gseq[k], (unsigned long long)g);
+            tc[sl[0]]--;
+            tc[sl[1]]++;
+            if (isdst) {
+                if (--tci[sl[0]] == 0) atomicAdd(&Q.dDs[k], -1);
+                if (++tci[sl[1]] == 1) atomicAdd(&Q.dDd[k], 1);
+            }
+        }
+    }
+}
+
 // ---------------------------------------------------------------- workspace
 // Allocated once per call for the largest level and reused by every level
 // and repetition.
@@ -1548,6 +1651,7 @@ struct LevelWs {
     int32_t *cl, *hubs, *cw;
     int32_t *cflag, *cpos, *cut, *cut_off;   // cut incident hyperedges per node
     int32_t *tiny, n_tiny;                   // hyperedges of 2..8 pins
+    int32_t *touched, *ttouched;             // hyperedges with a moved pin (more than / at most 8 pins)
     Moves M, S;
     uint64_t *keys;
     uint32_t *idx;
@@ -1615,6 +1719,8 @@ LevelWs *refine_workspace(int32_t n, int64_t np, int32_t e, int32_t nparts, int3
     W->cut = A.get<int32_t>(np);
     W->cut_off = A.get<int32_t>(n + 1);
     W->tiny = A.get<int32_t>(e);
+    W->touched = A.get<int32_t>(e);
+    W->ttouched = A.get<int32_t>(e);
     for (Moves *m : {&W->M, &W->S}) {
         m->node = A.get<int32_t>(n);
         m->src = A.get<int32_t>(n);
@@ -1674,7 +1780,7 @@ void refine_workspace_free(LevelWs *W, Arena &A) {
     for (void *p : std::initializer_list<void *>{
              W->act, W->big, W->wns, W->singin, W->PL.p, W->PL.cnt, W->PL.cin, W->PL.lam, W->R.cnt, W->R.linked,
              W->R.D0, W->R.psize, W->R.saving, W->R.pc, W->R.pred, W->R.succ, W->R.chain, W->R.mvpos, W->R.cgain,
-             W->R.gseq, W->R.acc0, W->R.dDs, W->R.dDd, W->R.viol, W->cl, W->hubs, W->cw, W->cflag, W->cpos, W->cut, W->cut_off, W->tiny, W->M.node, W->M.src, W->M.dst, W->M.gain,
+             W->R.gseq, W->R.acc0, W->R.dDs, W->R.dDd, W->R.viol, W->cl, W->hubs, W->cw, W->cflag, W->cpos, W->cut, W->cut_off, W->tiny, W->touched, W->ttouched, W->M.node, W->M.src, W->M.dst, W->M.gain,
              W->S.node, W->S.src, W->S.dst, W->S.gain, W->keys, W->idx, W->first, W->choice, W->accnode, W->pen,
              W->minpen, W->acc1, W->pos, W->clen, W->lens, W->starts, W->cstart, W->seqmove, W->heads, W->hkeys,
              W->vkey, W->vidx, W->vsz, W->vdd, W->gsz, W->gdd, W->esz, W->edd, W->vhead, W->bgain, W->lvl, W->ovf, W->gk, W->gc, W->ptab, W->ibuf})
@@ -1899,9 +2005,14 @@ static int32_t rep_run(const Level &L, const int32_t *w, const Params &P, int32_
     SeqSim Z{L.off, L.pin, L.nsrc, w, R.mvpos, W.seqmove, W.S.src, W.S.dst, W.PL, R.gseq, R.dDs, R.dDd};
     if (W.n_act > 0) {
         size_t sm = (size_t)(9 * W.small_max + 1) * 4 * (IS_T / 32);
+        k_touched<<<grid_of(W.n_act, 256), 256, 0, s>>>(L.off, L.pin, R.mvpos, W.act, W.n_act, W.touched,
+                                                         cnt + C_TOUCH, W.ttouched, cnt + C_TTOUCH, cnt + C_MOVES);
+        HP_LAUNCH_CHECK();
+        k_inseq_tiny<<<grid_of(W.n_act, IST_T), IST_T, 0, s>>>(Z, W.ttouched, cnt + C_TTOUCH, cnt + C_MOVES);
+        HP_LAUNCH_CHECK();
         int occ = prepare_kernel((const void *)k_inseq_small, IS_T, sm);
         int grid = (int)std::min<int64_t>(cdiv(W.n_act, IS_T / 32), (int64_t)num_sms() * occ);
-        k_inseq_small<<<std::max(grid, 1), IS_T, sm, s>>>(Z, W.act, W.n_act, W.small_max, cnt + C_MOVES);
+        k_inseq_small<<<std::max(grid, 1), IS_T, sm, s>>>(Z, W.touched, cnt + C_TOUCH, W.small_max, cnt + C_MOVES);
         HP_LAUNCH_CHECK();
     }
     if (W.n_big > 0) {
