@@ -91,20 +91,16 @@ void iota_i32(int32_t *p, int64_t n, cudaStream_t s);
 // per-warp digit counts.  Ends with the sorted data back in keys/vals and a
 // __syncthreads.
 // Stable LSD radix sort (8-bit digits) of n (key, value) pairs by one CTA of
-// up to 1024 threads, n <= 8 * blockDim.x.  keys/vals (global) are staged in
-// smem (two buffers of `cap` >= n keys and values); s_wc holds 32 * 256
-// counters, s_hist 256 + 33 words.  Warp w owns items [w * 32S, (w + 1) * 32S)
+// up to 1024 threads, n <= 16 * blockDim.x.  keys/vals are staged in two
+// pairs of buffers ka/kb, va/vb of >= n entries (shared or global memory);
+// s_wc holds 32 * 256 counters, s_hist 256 + 33 words.  Warp w owns items [w * 32S, (w + 1) * 32S)
 // with S = ceil(n / blockDim.x), slot k of lane l being item w * 32S + 32k + l,
 // so one round per pass ranks every item: within a warp slot by slot
 // (match_any), then across warps by an exclusive scan over (digit, warp).
-constexpr int BRS_SLOTS = 8;
+constexpr int BRS_SLOTS = 16;
 template <class K>
-__device__ void block_radix_sort(K *keys, uint32_t *vals, int n, int passes, int cap, unsigned char *smem,
-                                 uint32_t *s_wc, uint32_t *s_hist) {
-    K *ka = reinterpret_cast<K *>(smem);
-    K *kb = ka + cap;
-    uint32_t *va = reinterpret_cast<uint32_t *>(kb + cap);
-    uint32_t *vb = va + cap;
+__device__ void block_radix_sort_buf(K *keys, uint32_t *vals, int n, int passes, K *ka, K *kb, uint32_t *va,
+                                     uint32_t *vb, uint32_t *s_wc, uint32_t *s_hist) {
     const int t = threadIdx.x, T = blockDim.x, lane = t & 31, w = t >> 5, nwarp = T >> 5;
     const uint32_t lt = (1u << lane) - 1u;
     __syncthreads();
@@ -120,7 +116,7 @@ __device__ void block_radix_sort(K *keys, uint32_t *vals, int n, int passes, int
         uint32_t *run = s_wc + w * 256;
         for (int d = lane; d < 256; d += 32) run[d] = 0;
         __syncwarp();
-        uint32_t myrank[BRS_SLOTS], mydig[BRS_SLOTS];
+        uint32_t mine[BRS_SLOTS];   // rank << 9 | digit (256 = no item)
 #pragma unroll
         for (int k = 0; k < BRS_SLOTS; k++) {
             if (k < S) {
@@ -130,8 +126,7 @@ __device__ void block_radix_sort(K *keys, uint32_t *vals, int n, int passes, int
                 uint32_t base = 0;
                 if (d < 256u) base = run[d];
                 __syncwarp();
-                myrank[k] = base + __popc(peers & lt);
-                mydig[k] = d;
+                mine[k] = ((base + __popc(peers & lt)) << 9) | d;
                 if (d < 256u && (peers & lt) == 0) run[d] = base + __popc(peers);
                 __syncwarp();
             }
@@ -176,9 +171,9 @@ __device__ void block_radix_sort(K *keys, uint32_t *vals, int n, int passes, int
         __syncthreads();
 #pragma unroll
         for (int k = 0; k < BRS_SLOTS; k++) {
-            if (k < S && mydig[k] < 256u) {
+            if (k < S && (mine[k] & 511u) < 256u) {
                 const int i = w * 32 * S + 32 * k + lane;
-                const uint32_t pos = s_wc[w * 256 + mydig[k]] + myrank[k];
+                const uint32_t pos = s_wc[w * 256 + (mine[k] & 511u)] + (mine[k] >> 9);
                 kb[pos] = ka[i];
                 vb[pos] = va[i];
             }
@@ -196,6 +191,17 @@ __device__ void block_radix_sort(K *keys, uint32_t *vals, int n, int passes, int
         vals[i] = va[i];
     }
     __syncthreads();
+}
+
+// the same with both buffer pairs carved out of `smem` (`cap` entries each)
+template <class K>
+__device__ void block_radix_sort(K *keys, uint32_t *vals, int n, int passes, int cap, unsigned char *smem,
+                                 uint32_t *s_wc, uint32_t *s_hist) {
+    K *ka = reinterpret_cast<K *>(smem);
+    K *kb = ka + cap;
+    uint32_t *va = reinterpret_cast<uint32_t *>(kb + cap);
+    uint32_t *vb = va + cap;
+    block_radix_sort_buf<K>(keys, vals, n, passes, ka, kb, va, vb, s_wc, s_hist);
 }
 
 // Segmented sum over runs of equal, non-decreasing keys within a warp: every

@@ -718,8 +718,10 @@ __global__ void k_plist_tiny(const int32_t *off, const int32_t *pin, const int32
 // counters of one repetition (device)
 enum { C_CAND, C_MOVES, C_OVF, C_BAD, C_NH, C_BAD0, C_APPLIED, C_NV, C_HUB, C_CW, C_TOUCH, C_TTOUCH, C_N };
 
-// moves of at most SMALLM are sequenced and validated by one CTA each
-constexpr int SMALLM = 4096, SEQ_T = 1024;
+// moves of at most SMALLM are sequenced and validated by one CTA each, with
+// the sorts in shared memory; up to SEQ_MAX they are still sequenced by one
+// CTA (sort buffers in global memory) and validated by the multi-kernel path
+constexpr int SMALLM = 4096, SEQ_T = 1024, SEQ_MAX = 16 * SEQ_T;
 
 #define STRIDE(i, n, t0, nt) for (int64_t i = (t0); i < (int64_t)(n); i += (nt))
 #define G_T0 (blockIdx.x * (int64_t)blockDim.x + threadIdx.x)
@@ -1309,6 +1311,8 @@ struct SmallSeqArgs {
     Moves M, S;
     uint64_t *keys, *hkeys;
     uint32_t *idx, *heads;
+    uint64_t *gk;   // 2 * SEQ_MAX global sort buffers (used when m > SMALLM)
+    uint32_t *gv;
     int32_t *pc, *first, *lens, *starts, *cstart, *seqmove, *mvpos, *cnt;
     ChainCtx C;
     SeqCtx Q;
@@ -1322,17 +1326,30 @@ __global__ void __launch_bounds__(SEQ_T) k_seq_small(SmallSeqArgs A) {
     __shared__ uint32_t s_hist[256 + 33];
     __shared__ int32_t s_tmp[40];
     const int32_t m = A.cnt[C_MOVES];
-    if (m == 0 || m > SMALLM) return;
+    if (m == 0 || m > SEQ_MAX) return;
     const int64_t t0 = threadIdx.x, nt = blockDim.x;
+    uint64_t *ka, *kb;
+    uint32_t *va, *vb;
+    if (m <= SMALLM) {
+        ka = reinterpret_cast<uint64_t *>(smem);
+        kb = ka + SMALLM;
+        va = reinterpret_cast<uint32_t *>(kb + SMALLM);
+        vb = va + SMALLM;
+    } else {
+        ka = A.gk;
+        kb = A.gk + SEQ_MAX;
+        va = A.gv;
+        vb = A.gv + SEQ_MAX;
+    }
     if (A.sb + A.gb + A.nb <= 64) {
         ph_move_keys(A.M, m, A.gbound, A.gb, A.nb, -1, A.keys, A.idx, 1, t0, nt);
-        block_radix_sort<uint64_t>(A.keys, A.idx, m, (A.sb + A.gb + A.nb + 7) / 8, SMALLM, smem, s_wc, s_hist);
+        block_radix_sort_buf<uint64_t>(A.keys, A.idx, m, (A.sb + A.gb + A.nb + 7) / 8, ka, kb, va, vb, s_wc, s_hist);
     } else {
         const int fb[3] = {A.nb, A.gb, A.sb};
         for (int f = 0; f < 3; f++) {
             __syncthreads();
             ph_move_keys(A.M, m, A.gbound, A.gb, A.nb, f, A.keys, A.idx, f == 0, t0, nt);
-            block_radix_sort<uint64_t>(A.keys, A.idx, m, (fb[f] + 7) / 8, SMALLM, smem, s_wc, s_hist);
+            block_radix_sort_buf<uint64_t>(A.keys, A.idx, m, (fb[f] + 7) / 8, ka, kb, va, vb, s_wc, s_hist);
         }
     }
     ph_gather(A.M, A.idx, m, A.S, A.pc, t0, nt);
@@ -1361,13 +1378,13 @@ __global__ void __launch_bounds__(SEQ_T) k_seq_small(SmallSeqArgs A) {
     const int32_t nh = *(volatile int32_t *)&A.cnt[C_NH];
     if (A.cgb + A.nb <= 64) {
         ph_head_keys(A.heads, nh, A.Q.cgain, A.S.node, A.cgbound, A.nb, -1, A.hkeys, t0, nt);
-        block_radix_sort<uint64_t>(A.hkeys, A.heads, nh, (A.cgb + A.nb + 7) / 8, SMALLM, smem, s_wc, s_hist);
+        block_radix_sort_buf<uint64_t>(A.hkeys, A.heads, nh, (A.cgb + A.nb + 7) / 8, ka, kb, va, vb, s_wc, s_hist);
     } else {
         for (int f = 0; f < 2; f++) {
             __syncthreads();
             ph_head_keys(A.heads, nh, A.Q.cgain, A.S.node, A.cgbound, A.nb, f, A.hkeys, t0, nt);
-            block_radix_sort<uint64_t>(A.hkeys, A.heads, nh, ((f == 0 ? A.nb : A.cgb) + 7) / 8, SMALLM, smem, s_wc,
-                                       s_hist);
+            block_radix_sort_buf<uint64_t>(A.hkeys, A.heads, nh, ((f == 0 ? A.nb : A.cgb) + 7) / 8, ka, kb, va, vb,
+                                           s_wc, s_hist);
         }
     }
     ph_chain_lens(A.heads, nh, A.Q.clen, nh, A.lens, t0, nt);
@@ -1563,19 +1580,32 @@ __global__ void __launch_bounds__(256) k_inseq_big(SeqSim Q, const int32_t *list
 // In-sequence gains of hyperedges of at most TINY_E pins, one thread each:
 // the moved pins are taken in sequence order (ranks among at most TINY_E
 // distinct positions) and the parts they leave or enter are tracked in a
-// per-thread table of 2 TINY_E entries in shared memory.
+// per-thread table of 2 TINY_E entries in shared memory.  The r-th moves of
+// a warp's hyperedges are combined by sequence position (match_any) before
+// their atomics: a moved node with many hyperedges is one position.
 constexpr int IST_T = 128;
 __global__ void __launch_bounds__(IST_T) k_inseq_tiny(SeqSim Q, const int32_t *list, const int32_t *count_p,
                                                        const int32_t *mcount) {
     __shared__ int32_t s_tab[IST_T * 6 * TINY_E];
     if (*mcount == 0) return;
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const uint32_t lt = (1u << lane) - 1u;
     const int32_t count = *count_p;
     int32_t *tp = s_tab + threadIdx.x * 6 * TINY_E, *tc = tp + 2 * TINY_E, *tci = tc + 2 * TINY_E;
-    for (int64_t i = blockIdx.x * (int64_t)IST_T + threadIdx.x; i < count; i += (int64_t)gridDim.x * IST_T) {
-        const int32_t e = list[i];
-        const int32_t a = Q.off[e], sz = Q.off[e + 1] - a, d0 = Q.nsrc[e];
-        const long long we = Q.w[e];
-        const int32_t lam = Q.PL.lam[e];
+    const int64_t step = (int64_t)gridDim.x * IST_T;
+    for (int64_t base = blockIdx.x * (int64_t)IST_T + (threadIdx.x & ~31u); base < count; base += step) {
+        const int64_t i = base + lane;
+        int32_t a = 0, sz = 0, d0 = 0, lam = 0;
+        long long we = 0;
+        if (i < count) {
+            const int32_t e = list[i];
+            a = Q.off[e];
+            sz = Q.off[e + 1] - a;
+            d0 = Q.nsrc[e];
+            we = Q.w[e];
+            lam = Q.PL.lam[e];
+        }
         int32_t kk[TINY_E];
         int nm = 0;
 #pragma unroll
@@ -1589,45 +1619,57 @@ __global__ void __launch_bounds__(IST_T) k_inseq_tiny(SeqSim Q, const int32_t *l
                 }
             }
         }
+        const int rmax = (int)__reduce_max_sync(FULL, (unsigned)nm);
         int nt = 0;
-        for (int r = 0; r < nm; r++) {
-            // the moved pin of rank r (positions are distinct)
-            int32_t k = 0x7fffffff;
-            bool isdst = false;
+        for (int r = 0; r < rmax; r++) {
+            int32_t k = -1;
+            int g = 0, ds = 0, dd = 0;
+            if (r < nm) {
+                // the moved pin of rank r (positions are distinct)
+                bool isdst = false;
 #pragma unroll
-            for (int j = 0; j < TINY_E; j++) {
-                int32_t rk = 0;
+                for (int j = 0; j < TINY_E; j++) {
+                    int32_t rk = 0;
 #pragma unroll
-                for (int x = 0; x < TINY_E; x++) rk += kk[x] < kk[j];
-                if (kk[j] != 0x7fffffff && rk == r) {
-                    k = kk[j];
-                    isdst = j >= d0;
+                    for (int x = 0; x < TINY_E; x++) rk += kk[x] < kk[j];
+                    if (kk[j] != 0x7fffffff && rk == r) {
+                        k = kk[j];
+                        isdst = j >= d0;
+                    }
+                }
+                const int32_t mi = Q.seqmove[k];
+                const int32_t ps[2] = {Q.src[mi], Q.dst[mi]};
+                int32_t sl[2];
+                for (int h = 0; h < 2; h++) {
+                    int32_t x = 0;
+                    while (x < nt && tp[x] != ps[h]) x++;
+                    if (x == nt) {
+                        const int32_t f = plist_find(Q.PL, a, lam, ps[h]);
+                        tp[x] = ps[h];
+                        tc[x] = f >= 0 ? Q.PL.cnt[f] : 0;
+                        tci[x] = f >= 0 ? Q.PL.cin[f] : 0;
+                        nt++;
+                    }
+                    sl[h] = x;
+                }
+                if (tc[sl[0]] == 1) g += (int)we;
+                if (tc[sl[1]] == 0) g -= (int)we;
+                tc[sl[0]]--;
+                tc[sl[1]]++;
+                if (isdst) {
+                    if (--tci[sl[0]] == 0) ds = -1;
+                    if (++tci[sl[1]] == 1) dd = 1;
                 }
             }
-            const int32_t mi = Q.seqmove[k];
-            const int32_t ps[2] = {Q.src[mi], Q.dst[mi]};
-            int32_t sl[2];
-            for (int h = 0; h < 2; h++) {
-                int32_t x = 0;
-                while (x < nt && tp[x] != ps[h]) x++;
-                if (x == nt) {
-                    const int32_t f = plist_find(Q.PL, a, lam, ps[h]);
-                    tp[x] = ps[h];
-                    tc[x] = f >= 0 ? Q.PL.cnt[f] : 0;
-                    tci[x] = f >= 0 ? Q.PL.cin[f] : 0;
-                    nt++;
-                }
-                sl[h] = x;
-            }
-            long long g = 0;
-            if (tc[sl[0]] == 1) g += we;
-            if (tc[sl[1]] == 0) g -= we;
-            if (g) atomicAdd(&Q.gseq[k], (unsigned long long)g);
-            tc[sl[0]]--;
-            tc[sl[1]]++;
-            if (isdst) {
-                if (--tci[sl[0]] == 0) atomicAdd(&Q.dDs[k], -1);
-                if (++tci[sl[1]] == 1) atomicAdd(&Q.dDd[k], 1);
+            // |g| <= 65536 per lane, so the warp sums fit 32 bits
+            const unsigned grp = __match_any_sync(FULL, k);
+            const int gs = (int)__reduce_add_sync(grp, (unsigned)g);
+            const int dss = (int)__reduce_add_sync(grp, (unsigned)ds);
+            const int dds = (int)__reduce_add_sync(grp, (unsigned)dd);
+            if (k >= 0 && (grp & lt) == 0u) {
+                if (gs) atomicAdd(&Q.gseq[k], (unsigned long long)(long long)gs);
+                if (dss) atomicAdd(&Q.dDs[k], dss);
+                if (dds) atomicAdd(&Q.dDd[k], dds);
             }
         }
     }
@@ -1653,8 +1695,8 @@ struct LevelWs {
     int32_t *tiny, n_tiny;                   // hyperedges of 2..8 pins
     int32_t *touched, *ttouched;             // hyperedges with a moved pin (more than / at most 8 pins)
     Moves M, S;
-    uint64_t *keys;
-    uint32_t *idx;
+    uint64_t *keys, *sk;
+    uint32_t *idx, *sv;
     int32_t *first, *choice, *accnode, *pos, *clen, *lens, *starts, *cstart, *seqmove;
     unsigned long long *pen, *minpen, *acc1;
     uint32_t *heads;
@@ -1730,6 +1772,8 @@ LevelWs *refine_workspace(int32_t n, int64_t np, int32_t e, int32_t nparts, int3
     }
     W->keys = A.get<uint64_t>(n);
     W->idx = A.get<uint32_t>(n);
+    W->sk = A.get<uint64_t>(2 * (int64_t)SEQ_MAX);
+    W->sv = A.get<uint32_t>(2 * (int64_t)SEQ_MAX);
     W->first = A.get<int32_t>(nparts + 1);
     W->choice = A.get<int32_t>(n);
     W->accnode = A.get<int32_t>(n);
@@ -1781,7 +1825,7 @@ void refine_workspace_free(LevelWs *W, Arena &A) {
              W->act, W->big, W->wns, W->singin, W->PL.p, W->PL.cnt, W->PL.cin, W->PL.lam, W->R.cnt, W->R.linked,
              W->R.D0, W->R.psize, W->R.saving, W->R.pc, W->R.pred, W->R.succ, W->R.chain, W->R.mvpos, W->R.cgain,
              W->R.gseq, W->R.acc0, W->R.dDs, W->R.dDd, W->R.viol, W->cl, W->hubs, W->cw, W->cflag, W->cpos, W->cut, W->cut_off, W->tiny, W->touched, W->ttouched, W->M.node, W->M.src, W->M.dst, W->M.gain,
-             W->S.node, W->S.src, W->S.dst, W->S.gain, W->keys, W->idx, W->first, W->choice, W->accnode, W->pen,
+             W->S.node, W->S.src, W->S.dst, W->S.gain, W->keys, W->sk, W->idx, W->sv, W->first, W->choice, W->accnode, W->pen,
              W->minpen, W->acc1, W->pos, W->clen, W->lens, W->starts, W->cstart, W->seqmove, W->heads, W->hkeys,
              W->vkey, W->vidx, W->vsz, W->vdd, W->gsz, W->gdd, W->esz, W->edd, W->vhead, W->bgain, W->lvl, W->ovf, W->gk, W->gc, W->ptab, W->ibuf})
         A.release(p);
@@ -1924,9 +1968,9 @@ static int32_t rep_run(const Level &L, const int32_t *w, const Params &P, int32_
     SeqCtx Q{W.S.node, R.pred, R.succ, W.S.gain, R.chain, W.pos, W.clen, R.cgain, err_dev};
     ValCtx V{W.seqmove, L.size, W.singin, R.dDs, R.dDd, R.D0, R.gseq, W.S, R.psize, W.vkey, W.vidx, W.vsz, W.vdd,
              R.viol, P.omega, P.delta, W.gsz, W.gdd, W.esz, W.edd, W.vhead};
-    const bool small = m <= SMALLM;
-    if (small) {
-        SmallSeqArgs SA{W.M, W.S, W.keys, W.hkeys, W.idx, W.heads, R.pc, W.first, W.lens, W.starts, W.cstart,
+    const bool small = m <= SMALLM, one_cta = m <= SEQ_MAX;
+    if (one_cta) {
+        SmallSeqArgs SA{W.M, W.S, W.keys, W.hkeys, W.idx, W.heads, W.sk, W.sv, R.pc, W.first, W.lens, W.starts, W.cstart,
                         W.seqmove, R.mvpos, cnt, C, Q, nparts, P.o.chain_rounds, packed, gb, nb, sb, cgb, gbound,
                         cgbound};
         size_t sm = (size_t)SMALLM * 2 * (8 + 4);
