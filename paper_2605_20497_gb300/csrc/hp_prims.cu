@@ -265,6 +265,42 @@ __global__ void __launch_bounds__(SCAN_T) k_scan_tiles(const T *in, T *out, cons
     if (total && blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) *total = off + tile_tot;
 }
 
+// up to SCAN_SINGLE tiles: one CTA walks the tiles with a running carry
+// (one launch instead of three)
+constexpr int64_t SCAN_SINGLE = 4;
+template <class T> __global__ void __launch_bounds__(SCAN_T) k_scan_single(const T *in, T *out, int64_t n, T *total) {
+    __shared__ T s_val[SCAN_TILE];
+    __shared__ T s_warp[33];
+    T carry = 0;
+    for (int64_t base = 0; base < n; base += SCAN_TILE) {
+        for (int i = 0; i < SCAN_I; i++) {
+            const int64_t k = base + (int64_t)i * SCAN_T + threadIdx.x;
+            s_val[i * SCAN_T + threadIdx.x] = k < n ? in[k] : T(0);
+        }
+        __syncthreads();
+        T loc[SCAN_I];
+        T acc = 0;
+        for (int i = 0; i < SCAN_I; i++) {
+            loc[i] = s_val[threadIdx.x * SCAN_I + i];
+            acc += loc[i];
+        }
+        T tile_tot;
+        T run = block_excl_scan(acc, s_warp, &tile_tot) + carry;
+        for (int i = 0; i < SCAN_I; i++) {
+            s_val[threadIdx.x * SCAN_I + i] = run;
+            run += loc[i];
+        }
+        __syncthreads();
+        for (int i = 0; i < SCAN_I; i++) {
+            const int64_t k = base + (int64_t)i * SCAN_T + threadIdx.x;
+            if (k < n) out[k] = s_val[i * SCAN_T + threadIdx.x];
+        }
+        carry += tile_tot;
+        __syncthreads();
+    }
+    if (total && threadIdx.x == 0) *total = carry;
+}
+
 template <class T> static void scan_impl(const T *in, T *out, int64_t n, T *total_dev, Arena &A) {
     cudaStream_t s = A.stream();
     if (n <= 0) {
@@ -272,8 +308,8 @@ template <class T> static void scan_impl(const T *in, T *out, int64_t n, T *tota
         return;
     }
     int64_t tiles = cdiv(n, SCAN_TILE);
-    if (tiles == 1) {
-        k_scan_tiles<T><<<1, SCAN_T, 0, s>>>(in, out, nullptr, n, total_dev);
+    if (tiles <= SCAN_SINGLE) {
+        k_scan_single<T><<<1, SCAN_T, 0, s>>>(in, out, n, total_dev);
         HP_LAUNCH_CHECK();
         return;
     }

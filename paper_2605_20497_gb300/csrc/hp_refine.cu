@@ -795,7 +795,7 @@ __global__ void k_cut_fill(const int32_t *inc, const int32_t *flag, const int32_
 
 // candidates: nodes that can spare a cut, by number of cut hyperedges:
 // up to GW_DEG a warp each, up to HUB_DEG a CTA each, more a large CTA each
-constexpr int32_t HUB_DEG = 4096, GW_DEG = 256;
+constexpr int32_t HUB_DEG = 1024, GW_DEG = 256;
 __global__ void k_candidates(const long long *saving, const int32_t *cut_off, int32_t n, int32_t *list, int32_t *cnt,
                              int32_t *hubs, int32_t *hcnt, int32_t *wlist, int32_t *wcnt) {
     GRID_STRIDE(v, (int64_t)n) {
@@ -823,14 +823,18 @@ __device__ void ph_move_keys(const Moves &M, int32_t m, long long gbound, int gb
         else keys[i] = field == 0 ? (uint64_t)M.node[k] : field == 1 ? g : (uint64_t)M.src[k];
     }
 }
-__device__ void ph_gather(const Moves &M, const uint32_t *idx, int32_t m, const Moves &S, int32_t *pc, int64_t t0,
-                          int64_t nt) {
+// the moves in sorted order, with the size and |in| of each moved node
+__device__ void ph_gather(const Moves &M, const uint32_t *idx, int32_t m, const Moves &S, int32_t *pc,
+                          const int32_t *size, const int32_t *nin, int32_t *msz, int32_t *mni, int64_t t0, int64_t nt) {
     STRIDE(i, m, t0, nt) {
         uint32_t k = idx[i];
-        S.node[i] = M.node[k];
+        const int32_t v = M.node[k];
+        S.node[i] = v;
         S.src[i] = M.src[k];
         S.dst[i] = M.dst[k];
         S.gain[i] = M.gain[k];
+        msz[i] = size[v];
+        mni[i] = nin[v];
         atomicAdd(&pc[M.src[k]], 1);
     }
 }
@@ -838,6 +842,7 @@ __device__ void ph_gather(const Moves &M, const uint32_t *idx, int32_t m, const 
 struct ChainCtx {
     int32_t window;
     const int32_t *node, *src, *dst, *size, *nin;
+    const int32_t *msz, *mni;   // size and |in| of the node of each sorted move
     const long long *gain;
     const int32_t *first;   // [nparts+1]: moves leaving p are [first[p], first[p+1])
     int32_t *pred, *succ, *choice;
@@ -853,6 +858,7 @@ struct ChainCtx {
 // ties.  For a chosen move all choosers share gain(m), so the acceptor of
 // maximum (G, node id) is the chooser of minimum penalty, then maximum id.
 __device__ void ph_choose(const ChainCtx &C, int r, int packed, int32_t m, int64_t t0, int64_t nt) {
+    constexpr int B = 8;   // candidates loaded together, ahead of their evaluation
     STRIDE(i0, m, t0, nt) {
         int32_t i = (int32_t)i0;
         C.choice[i] = -1;
@@ -861,24 +867,39 @@ __device__ void ph_choose(const ChainCtx &C, int r, int packed, int32_t m, int64
             C.accnode[i] = -1;
         }
         if (C.succ[i] >= 0) continue;
-        int32_t d = C.dst[i];
+        const int32_t d = C.dst[i];
         int32_t seen = 0, best = -1;
         __int128 bG = 0;
         unsigned long long bpen = 0;
-        const int32_t vi = C.node[i];
-        for (int32_t j = C.first[d]; j < C.first[d + 1] && seen < C.window; j++) {
-            if (C.pred[j] >= 0 || j == i) continue;
-            seen++;
-            int32_t vj = C.node[j];
-            long long ds = (long long)C.size[vi] - C.size[vj];
-            long long di = (long long)C.nin[vi] - C.nin[vj];
-            unsigned long long pen =
-                10ull * (unsigned long long)(ds < 0 ? -ds : ds) + (unsigned long long)(di < 0 ? -di : di);
-            __int128 G = (__int128)C.gain[j] * 10000000 - (__int128)pen;
-            if (best < 0 || G > bG) {
-                best = j;
-                bG = G;
-                bpen = pen;
+        const int32_t vi = C.node[i], szi = C.msz[i], nii = C.mni[i];
+        const int32_t jend = C.first[d + 1];
+        for (int32_t j0 = C.first[d]; j0 < jend && seen < C.window; j0 += B) {
+            int32_t pr[B], sz[B], ni[B];
+            long long gn[B];
+#pragma unroll
+            for (int u = 0; u < B; u++) {
+                const int32_t j = j0 + u;
+                const bool ok = j < jend;
+                pr[u] = ok ? C.pred[j] : 0;
+                sz[u] = ok ? C.msz[j] : 0;
+                ni[u] = ok ? C.mni[j] : 0;
+                gn[u] = ok ? C.gain[j] : 0;
+            }
+#pragma unroll
+            for (int u = 0; u < B; u++) {
+                const int32_t j = j0 + u;
+                if (j >= jend || seen >= C.window) break;
+                if (pr[u] >= 0 || j == i) continue;
+                seen++;
+                const long long ds = (long long)szi - sz[u], di = (long long)nii - ni[u];
+                const unsigned long long pen =
+                    10ull * (unsigned long long)(ds < 0 ? -ds : ds) + (unsigned long long)(di < 0 ? -di : di);
+                const __int128 G = (__int128)gn[u] * 10000000 - (__int128)pen;
+                if (best < 0 || G > bG) {
+                    best = j;
+                    bG = G;
+                    bpen = pen;
+                }
             }
         }
         C.choice[i] = best;
@@ -1244,8 +1265,9 @@ __global__ void k_move_keys(const Moves M, const int32_t *cntp, long long gbound
                             uint64_t *keys, uint32_t *idx, int init_idx) {
     ph_move_keys(M, *cntp, gbound, gb, nb, field, keys, idx, init_idx, G_T0, G_NT);
 }
-__global__ void k_gather_moves(const Moves M, const uint32_t *idx, const int32_t *cntp, Moves S, int32_t *pc) {
-    ph_gather(M, idx, *cntp, S, pc, G_T0, G_NT);
+__global__ void k_gather_moves(const Moves M, const uint32_t *idx, const int32_t *cntp, Moves S, int32_t *pc,
+                               const int32_t *size, const int32_t *nin, int32_t *msz, int32_t *mni) {
+    ph_gather(M, idx, *cntp, S, pc, size, nin, msz, mni, G_T0, G_NT);
 }
 __global__ void k_choose(ChainCtx C, const int32_t *mcount, int r, int packed) {
     if (r > 0 && !C.linked[r - 1]) return;
@@ -1352,7 +1374,8 @@ __global__ void __launch_bounds__(SEQ_T) k_seq_small(SmallSeqArgs A) {
             block_radix_sort_buf<uint64_t>(A.keys, A.idx, m, (fb[f] + 7) / 8, ka, kb, va, vb, s_wc, s_hist);
         }
     }
-    ph_gather(A.M, A.idx, m, A.S, A.pc, t0, nt);
+    ph_gather(A.M, A.idx, m, A.S, A.pc, A.C.size, A.C.nin, const_cast<int32_t *>(A.C.msz),
+              const_cast<int32_t *>(A.C.mni), t0, nt);
     __syncthreads();
     block_scan_excl(A.pc, A.first, (int64_t)A.nparts + 1, s_tmp);
     __syncthreads();
@@ -1697,6 +1720,7 @@ struct LevelWs {
     Moves M, S;
     uint64_t *keys, *sk;
     uint32_t *idx, *sv;
+    int32_t *msz, *mni;
     int32_t *first, *choice, *accnode, *pos, *clen, *lens, *starts, *cstart, *seqmove;
     unsigned long long *pen, *minpen, *acc1;
     uint32_t *heads;
@@ -1773,6 +1797,8 @@ LevelWs *refine_workspace(int32_t n, int64_t np, int32_t e, int32_t nparts, int3
     W->keys = A.get<uint64_t>(n);
     W->idx = A.get<uint32_t>(n);
     W->sk = A.get<uint64_t>(2 * (int64_t)SEQ_MAX);
+    W->msz = A.get<int32_t>(n);
+    W->mni = A.get<int32_t>(n);
     W->sv = A.get<uint32_t>(2 * (int64_t)SEQ_MAX);
     W->first = A.get<int32_t>(nparts + 1);
     W->choice = A.get<int32_t>(n);
@@ -1825,7 +1851,7 @@ void refine_workspace_free(LevelWs *W, Arena &A) {
              W->act, W->big, W->wns, W->singin, W->PL.p, W->PL.cnt, W->PL.cin, W->PL.lam, W->R.cnt, W->R.linked,
              W->R.D0, W->R.psize, W->R.saving, W->R.pc, W->R.pred, W->R.succ, W->R.chain, W->R.mvpos, W->R.cgain,
              W->R.gseq, W->R.acc0, W->R.dDs, W->R.dDd, W->R.viol, W->cl, W->hubs, W->cw, W->cflag, W->cpos, W->cut, W->cut_off, W->tiny, W->touched, W->ttouched, W->M.node, W->M.src, W->M.dst, W->M.gain,
-             W->S.node, W->S.src, W->S.dst, W->S.gain, W->keys, W->sk, W->idx, W->sv, W->first, W->choice, W->accnode, W->pen,
+             W->S.node, W->S.src, W->S.dst, W->S.gain, W->keys, W->sk, W->idx, W->sv, W->msz, W->mni, W->first, W->choice, W->accnode, W->pen,
              W->minpen, W->acc1, W->pos, W->clen, W->lens, W->starts, W->cstart, W->seqmove, W->heads, W->hkeys,
              W->vkey, W->vidx, W->vsz, W->vdd, W->gsz, W->gdd, W->esz, W->edd, W->vhead, W->bgain, W->lvl, W->ovf, W->gk, W->gc, W->ptab, W->ibuf})
         A.release(p);
@@ -1928,8 +1954,9 @@ static int32_t rep_run(const Level &L, const int32_t *w, const Params &P, int32_
         int grid = std::max(1, std::min<int>(n, num_sms() * occ));
         k_gains_smem<GN_T><<<grid, GN_T, sm, s>>>(G, W.cl, cnt + C_CAND, cap, W.ovf, cnt + C_OVF);
         HP_LAUNCH_CHECK();
-        prepare_kernel((const void *)k_gains_smem<1024>, 1024, sm);
-        k_gains_smem<1024><<<num_sms(), 1024, sm, s>>>(G, W.hubs, cnt + C_HUB, cap, W.ovf, cnt + C_OVF);
+        const int occ_h = prepare_kernel((const void *)k_gains_smem<1024>, 1024, sm);
+        k_gains_smem<1024><<<num_sms() * std::max(occ_h, 1), 1024, sm, s>>>(G, W.hubs, cnt + C_HUB, cap, W.ovf,
+                                                                          cnt + C_OVF);
         HP_LAUNCH_CHECK();
         k_gains_global<<<W.gnb, GN_T, 0, s>>>(G, W.ovf, cnt + C_OVF, W.gcap, W.gk, W.gc, W.cl, cnt + C_BAD);
         HP_LAUNCH_CHECK();
@@ -1954,6 +1981,8 @@ static int32_t rep_run(const Level &L, const int32_t *w, const Params &P, int32_
     C.dst = W.S.dst;
     C.size = L.size;
     C.nin = L.nin;
+    C.msz = W.msz;
+    C.mni = W.mni;
     C.gain = W.S.gain;
     C.first = W.first;
     C.pred = R.pred;
@@ -1992,7 +2021,8 @@ static int32_t rep_run(const Level &L, const int32_t *w, const Params &P, int32_
                 radix_sort_dev(W.keys, W.idx, cnt + C_MOVES, m, fb[f], A);
             }
         }
-        k_gather_moves<<<grid_of(m, 256), 256, 0, s>>>(W.M, W.idx, cnt + C_MOVES, W.S, R.pc);
+        k_gather_moves<<<grid_of(m, 256), 256, 0, s>>>(W.M, W.idx, cnt + C_MOVES, W.S, R.pc, L.size, L.nin, W.msz,
+                                                       W.mni);
         HP_LAUNCH_CHECK();
         scan_excl(R.pc, W.first, nparts + 1, nullptr, A);
         // chaining (Sec. VI-C)
