@@ -55,6 +55,7 @@ struct PropCtx {
     int32_t *cand;         // [n*pi]
     uint64_t *cscore;      // [n*pi]
     int32_t *nbcnt;        // [n] unique neighbours found
+    const int32_t *canon;  // [e] hyperedges with equal destination lists share a value (or null)
 };
 
 // ---------------------------------------------------------------- per-level weights
@@ -223,13 +224,18 @@ __device__ __forceinline__ int32_t block_sum_i32(int32_t x, int32_t *s_tmp) {
 }
 
 // One chunk of v's incidence for the calling warp: lane l takes the
-// hyperedge at incidence index t = base + l (none when t >= deg).  Hyperedges
-// of 2..32 pins: the j-th pins of the warp's hyperedges are combined by
-// neighbour (match_any) and one table update per distinct neighbour carries
-// the warp's sums of q(e) and of the inbound-overlap counts; q(e) <= 2^40 is
-// summed as two 21-bit halves so that 32-bit warp reductions cannot
-// overflow.  Larger hyperedges go to big(e, t) when it is given, else the
-// warp takes them one at a time, lanes over pins.
+// hyperedge at incidence index t = base + l (none when t >= deg).
+// Hyperedges of 2..32 pins: the j-th pins of the warp's hyperedges are
+// combined by neighbour (match_any) and one table update per distinct
+// neighbour carries the warp's sums of q(e) and of the inbound-overlap
+// counts; q(e) <= 2^40 is summed as two 21-bit halves so that 32-bit warp
+// reductions cannot overflow.  Larger hyperedges: each lane inserts its own
+// source pins; the destination pins are walked once per group of the warp's
+// hyperedges with equal destination lists (C.canon; every hyperedge alone
+// when it is null), carrying the group's sum of q(e) and, when v is one of
+// those destinations, the group's size as the inbound overlap.  That walk is
+// handed to big(e, qsum, icnt) when it is given, else the warp takes the
+// groups one at a time, lanes over pins.
 template <class Ins, class Big>
 __device__ __forceinline__ void warp_chunk(const PropCtx &C, int32_t v, int32_t i0, int32_t deg, int32_t nin_v,
                                            int32_t t, Ins &ins, Big *big) {
@@ -252,7 +258,6 @@ __device__ __forceinline__ void warp_chunk(const PropCtx &C, int32_t v, int32_t 
         }
     }
     const bool large = sz > 32;
-    if (large && big) (*big)(e, t);
     const int32_t len = large ? 0 : sz;
     const int jmax = (int)__reduce_max_sync(FULL, (unsigned)len);
     for (int j = 0; j < jmax; j++) {
@@ -265,25 +270,41 @@ __device__ __forceinline__ void warp_chunk(const PropCtx &C, int32_t v, int32_t 
         const unsigned ic = __reduce_add_sync(g, (on && vin && a + j >= dst0) ? 1u : 0u);
         if (on && (g & lt) == 0u) ins(m, (unsigned long long)lo + ((unsigned long long)hi << 21), ic);
     }
-    if (!big) {
-        unsigned bm = __ballot_sync(FULL, large);
-        while (bm) {
-            const int l = __ffs(bm) - 1;
-            bm &= bm - 1;
-            const int32_t la = __shfl_sync(FULL, a, l), lb = la + __shfl_sync(FULL, sz, l);
-            const int32_t ld0 = __shfl_sync(FULL, dst0, l);
-            const unsigned long long lq = __shfl_sync(FULL, qe, l);
-            const bool lvin = __shfl_sync(FULL, vin, l);
-            for (int32_t j = la + lane; j < lb; j += 32) {
-                const int32_t m = C.pin[j];
-                if (m != v) ins(m, lq, (lvin && j >= ld0) ? 1u : 0u);
-            }
+    const unsigned bigm = __ballot_sync(FULL, large);
+    if (!bigm) return;
+    // groups of large hyperedges with equal destination lists
+    const int32_t key = large ? (C.canon ? C.canon[e] : e) : -1 - lane;
+    const unsigned grp = __match_any_sync(FULL, key);
+    const unsigned qlo = __reduce_add_sync(grp, large ? (unsigned)(qe & 0x1FFFFFull) : 0u);
+    const unsigned qhi = __reduce_add_sync(grp, large ? (unsigned)(qe >> 21) : 0u);
+    const unsigned long long qsum = (unsigned long long)qlo + ((unsigned long long)qhi << 21);
+    const uint32_t icnt = vin ? (uint32_t)__popc(grp) : 0u;
+    const bool lead = large && (grp & lt) == 0u;
+    if (large)
+        for (int32_t j = a; j < dst0; j++) {
+            const int32_t m = C.pin[j];
+            if (m != v) ins(m, qe, 0u);
+        }
+    if (big) {
+        if (lead) (*big)(e, qsum, icnt);
+        return;
+    }
+    unsigned lm = __ballot_sync(FULL, lead);
+    while (lm) {
+        const int l = __ffs(lm) - 1;
+        lm &= lm - 1;
+        const int32_t ld0 = __shfl_sync(FULL, dst0, l), lb = __shfl_sync(FULL, a, l) + __shfl_sync(FULL, sz, l);
+        const unsigned long long lq = __shfl_sync(FULL, qsum, l);
+        const uint32_t lc = __shfl_sync(FULL, icnt, l);
+        for (int32_t j = ld0 + lane; j < lb; j += 32) {
+            const int32_t m = C.pin[j];
+            if (m != v) ins(m, lq, lc);
         }
     }
 }
 
 struct NoBig {
-    __device__ void operator()(int32_t, int32_t) const {}
+    __device__ void operator()(int32_t, unsigned long long, uint32_t) const {}
 };
 
 // A warp's walk over all of v's hyperedges.
@@ -294,45 +315,107 @@ __device__ __forceinline__ void warp_walk(const PropCtx &C, int32_t v, int32_t i
         warp_chunk(C, v, i0, deg, nin_v, base + (int32_t)(threadIdx.x & 31), ins, (NoBig *)nullptr);
 }
 
+// Shared-memory queue of destination walks of one CTA: blockDim.x entries.
+struct BigQueue {
+    int32_t *e;
+    unsigned long long *q;
+    uint32_t *c;
+    int32_t *n;   // == 0 on entry and on exit of cta_walk
+};
+
 // A CTA's walk over all of v's hyperedges in chunks of blockDim.x: small
-// ones as above, larger ones queued in shared memory (s_big, blockDim.x
-// pairs (e, t); *s_nbig == 0 on entry and on exit) and then taken a warp
-// each, lanes over pins, so that every warp gets a share of them.  Stops
-// early (for every thread) once *stop is set.
+// ones and source pins as above, destination walks of large ones queued in
+// shared memory and then taken a warp each, lanes over pins, so that every
+// warp gets a share of them.  Stops early (for every thread) once *stop is
+// set.
 template <class Ins>
 __device__ void cta_walk(const PropCtx &C, int32_t v, int32_t i0, int32_t deg, int32_t nin_v, const int *stop,
-                         int32_t *s_big, int32_t *s_nbig, Ins ins) {
+                         BigQueue Q, Ins ins) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    auto push = [&](int32_t e, int32_t t) {
-        const int32_t i = atomicAdd(s_nbig, 1);
-        s_big[2 * i] = e;
-        s_big[2 * i + 1] = t;
+    auto push = [&](int32_t e, unsigned long long qsum, uint32_t icnt) {
+        const int32_t i = atomicAdd(Q.n, 1);
+        Q.e[i] = e;
+        Q.q[i] = qsum;
+        Q.c[i] = icnt;
     };
     for (int32_t base = 0; base < deg; base += blockDim.x) {
         if (__syncthreads_or(stop ? *(volatile const int *)stop : 0)) break;
         warp_chunk(C, v, i0, deg, nin_v, base + (int32_t)threadIdx.x, ins, &push);
         __syncthreads();
-        const int32_t nb = *(volatile int32_t *)s_nbig;
+        const int32_t nb = *(volatile int32_t *)Q.n;
         for (int32_t i = wid; i < nb; i += nw) {
-            const int32_t e = s_big[2 * i], t = s_big[2 * i + 1];
-            const int32_t a = C.off[e], b = C.off[e + 1];
-            const int32_t dst0 = a + C.nsrc[e];
-            const unsigned long long qe = C.q[e];
-            const bool vin = t < nin_v;
+            const int32_t e = Q.e[i];
+            const unsigned long long qsum = Q.q[i];
+            const uint32_t icnt = Q.c[i];
+            const int32_t b = C.off[e + 1];
             // the next pin is loaded before the current one is inserted
-            int32_t j = a + lane;
+            int32_t j = C.off[e] + C.nsrc[e] + lane;
             int32_t mn = j < b ? __ldg(&C.pin[j]) : -1;
             while (j < b) {
                 const int32_t m = mn, jn = j + 32;
                 mn = jn < b ? __ldg(&C.pin[jn]) : -1;
-                if (m != v) ins(m, qe, (vin && j >= dst0) ? 1u : 0u);
+                if (m != v) ins(m, qsum, icnt);
                 j = jn;
             }
         }
         __syncthreads();
-        if (threadIdx.x == 0) *s_nbig = 0;
+        if (threadIdx.x == 0) *Q.n = 0;
     }
     __syncthreads();
+}
+
+// ---------------------------------------------------------------- destination-list groups
+// canon[e] = one representative of the hyperedges whose destination pin
+// lists equal e's (level 0 only; the proposal walks such lists once per warp
+// group).  Lists are hashed, sorted by hash, and equal neighbours in that
+// order are confirmed pin by pin, so a hash collision only splits a group.
+__device__ __forceinline__ uint32_t fmix32(uint32_t h) {
+    h ^= h >> 16;
+    h *= 0x85EBCA6Bu;
+    h ^= h >> 13;
+    h *= 0xC2B2AE35u;
+    h ^= h >> 16;
+    return h;
+}
+__global__ void k_dst_hash(const int32_t *off, const int32_t *pin, const int32_t *nsrc, int32_t e, uint32_t *key,
+                           uint32_t *val) {
+    const int lane = threadIdx.x & 31;
+    const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5, nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t i = w0; i < e; i += nw) {
+        const int32_t d0 = off[i] + nsrc[i], b = off[i + 1];
+        uint32_t h = 0;
+        for (int32_t j = d0 + lane; j < b; j += 32) h += fmix32((uint32_t)pin[j] ^ ((uint32_t)(j - d0) * 0x9E3779B9u));
+        for (int o = 16; o > 0; o >>= 1) h += __shfl_xor_sync(0xffffffffu, h, o);
+        if (lane == 0) {
+            key[i] = fmix32(h ^ (uint32_t)(b - d0));
+            val[i] = (uint32_t)i;
+        }
+    }
+}
+__global__ void k_dst_runs(const uint32_t *key, const uint32_t *val, const int32_t *off, const int32_t *pin,
+                           const int32_t *nsrc, int32_t e, int32_t *newrun) {
+    const int lane = threadIdx.x & 31;
+    const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5, nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t i = w0; i < e; i += nw) {
+        bool same = i > 0 && key[i] == key[i - 1];
+        if (same) {
+            const int32_t x = (int32_t)val[i], y = (int32_t)val[i - 1];
+            const int32_t xa = off[x] + nsrc[x], xb = off[x + 1], ya = off[y] + nsrc[y], yb = off[y + 1];
+            same = xb - xa == yb - ya;
+            for (int32_t k = lane; same && k < xb - xa; k += 32)
+                same = __all_sync(__activemask(), pin[xa + k] == pin[ya + k]);
+        }
+        if (lane == 0) newrun[i] = same ? 0 : 1;
+    }
+}
+__global__ void k_dst_rep(const uint32_t *val, const int32_t *newrun, const int32_t *runpos, int32_t e, int32_t *rep) {
+    GRID_STRIDE(i, (int64_t)e) {
+        if (newrun[i]) rep[runpos[i]] = (int32_t)val[i];
+    }
+}
+__global__ void k_dst_canon(const uint32_t *val, const int32_t *newrun, const int32_t *runpos, const int32_t *rep,
+                            int32_t e, int32_t *canon) {
+    GRID_STRIDE(i, (int64_t)e) canon[val[i]] = rep[runpos[i] + newrun[i] - 1];
 }
 
 // ---------------------------------------------------------------- dense table
@@ -344,7 +427,9 @@ __global__ void __launch_bounds__(BT) k_propose_dense(PropCtx C, const int32_t *
     unsigned long long *eta = reinterpret_cast<unsigned long long *>(smem);
     uint32_t *inter = reinterpret_cast<uint32_t *>(eta + C.n);
     __shared__ Cand s_top[32 * PIMAX];
-    __shared__ int32_t s_big[2 * BT];
+    __shared__ int32_t s_qe[BT];
+    __shared__ unsigned long long s_qq[BT];
+    __shared__ uint32_t s_qc[BT];
     __shared__ int32_t s_nbig;
     __shared__ int32_t s_tmp[32];
     const int32_t count = *count_p;
@@ -359,7 +444,8 @@ __global__ void __launch_bounds__(BT) k_propose_dense(PropCtx C, const int32_t *
     for (int32_t k = blockIdx.x; k < count; k += gridDim.x) {
         const int32_t v = list[k];
         const int32_t i0 = C.ioff[v], deg = C.ioff[v + 1] - i0, nin_v = C.nin[v];
-        cta_walk(C, v, i0, deg, nin_v, nullptr, s_big, &s_nbig, [&](int32_t m, unsigned long long eq, uint32_t ic) {
+        cta_walk(C, v, i0, deg, nin_v, nullptr, BigQueue{s_qe, s_qq, s_qc, &s_nbig},
+                 [&](int32_t m, unsigned long long eq, uint32_t ic) {
             add_u64_split(&eta[m], eq);
             if (ic) atomicAdd(&inter[m], ic);
         });
@@ -487,7 +573,7 @@ template <int PIMAX>
 __device__ void propose_hashed_node(const PropCtx &C, int32_t v, int32_t *keys, unsigned long long *eta,
                                     uint32_t *inter, uint32_t cap, uint32_t limit, int32_t *slots, int32_t *ovf,
                                     int32_t *ovf_n, int *s_flag, int32_t *s_cnt, Cand *s_top,
-                                    int32_t *s_tmp, int32_t *s_big, int32_t *s_nbig) {
+                                    int32_t *s_tmp, BigQueue BQ) {
     const uint32_t mask = cap - 1;
     const int32_t i0 = C.ioff[v], deg = C.ioff[v + 1] - i0, nin_v = C.nin[v];
     auto insert_n = [&](int32_t m, unsigned long long qe, uint32_t ninter) {
@@ -513,7 +599,7 @@ __device__ void propose_hashed_node(const PropCtx &C, int32_t v, int32_t *keys, 
             h = (h + 1) & mask;
         }
     };
-    cta_walk(C, v, i0, deg, nin_v, s_flag, s_big, s_nbig, insert_n);
+    cta_walk(C, v, i0, deg, nin_v, s_flag, BQ, insert_n);
     __syncthreads();
     const int overflow = *s_flag;
     const uint64_t capn = *C.cap;
@@ -563,7 +649,9 @@ __global__ void __launch_bounds__(BT) k_propose_smem(PropCtx C, const int32_t *l
     int32_t *keys = reinterpret_cast<int32_t *>(inter + cap);
     int32_t *slots = keys + cap;
     __shared__ Cand s_top[32 * PIMAX];
-    __shared__ int32_t s_big[2 * BT];
+    __shared__ int32_t s_qe[BT];
+    __shared__ unsigned long long s_qq[BT];
+    __shared__ uint32_t s_qc[BT];
     __shared__ int32_t s_nbig;
     __shared__ int32_t s_tmp[32];
     __shared__ int s_flag;
@@ -583,7 +671,7 @@ __global__ void __launch_bounds__(BT) k_propose_smem(PropCtx C, const int32_t *l
     __syncthreads();
     for (int32_t k = blockIdx.x; k < count; k += gridDim.x)
         propose_hashed_node<PIMAX>(C, list[k], keys, eta, inter, cap, limit, slots, ovf, ovf_n, &s_flag, &s_cnt,
-                                   s_top, s_tmp, s_big, &s_nbig);
+                                   s_top, s_tmp, BigQueue{s_qe, s_qq, s_qc, &s_nbig});
 }
 
 // one CTA region of gcap slots in global memory per CTA (clean on entry and
@@ -594,7 +682,9 @@ __global__ void __launch_bounds__(PT) k_propose_global(PropCtx C, const int32_t 
                                                        uint32_t *ginter, int32_t *gslots, int32_t *err_list,
                                                        int32_t *err_n) {
     __shared__ Cand s_top[32 * PIMAX];
-    __shared__ int32_t s_big[2 * PT];
+    __shared__ int32_t s_qe[PT];
+    __shared__ unsigned long long s_qq[PT];
+    __shared__ uint32_t s_qc[PT];
     __shared__ int32_t s_nbig;
     __shared__ int32_t s_tmp[32];
     __shared__ int s_flag;
@@ -610,7 +700,7 @@ __global__ void __launch_bounds__(PT) k_propose_global(PropCtx C, const int32_t 
     __syncthreads();
     for (int32_t k = blockIdx.x; k < count; k += gridDim.x)
         propose_hashed_node<PIMAX>(C, list[k], gkeys + o, geta + o, ginter + o, gcap, gcap - 1, gslots + o, err_list,
-                                   err_n, &s_flag, &s_cnt, s_top, s_tmp, s_big, &s_nbig);
+                                   err_n, &s_flag, &s_cnt, s_top, s_tmp, BigQueue{s_qe, s_qq, s_qc, &s_nbig});
 }
 
 // ---------------------------------------------------------------- node tiers
@@ -637,6 +727,7 @@ __global__ void k_tiers(const int32_t *bound, const long long *vis, int32_t n, u
 struct CoarsenWs {
     int32_t cn, ce, pi;
     uint64_t *q;
+    int32_t *canon;   // destination-list groups of the level-0 hyperedges
     int32_t *cand;
     uint64_t *cscore;
     int32_t *lW, *lB, *lC, *lG, *lH, *lD, *lDH, *cnt;   // cnt: 0 W 1 B 2 C 3 G 4 errors 5 H 6 D 7 DH
@@ -909,6 +1000,7 @@ CoarsenWs *coarsen_workspace(int32_t n, int32_t e, const Params &P, Arena &A) {
     W->ce = e;
     W->pi = pi;
     W->q = A.get<uint64_t>(e);
+    W->canon = A.get<int32_t>(std::max(e, 1));
     W->cand = A.get<int32_t>((int64_t)n * pi);
     W->cscore = A.get<uint64_t>((int64_t)n * pi);
     W->lW = A.get<int32_t>(n);
@@ -951,7 +1043,7 @@ CoarsenWs *coarsen_workspace(int32_t n, int32_t e, const Params &P, Arena &A) {
 
 void coarsen_workspace_free(CoarsenWs *W, Arena &A) {
     if (!W) return;
-    for (void *p : {(void *)W->nsum, (void *)W->vis, (void *)W->q, (void *)W->cand, (void *)W->cscore, (void *)W->lW, (void *)W->lB, (void *)W->lC,
+    for (void *p : {(void *)W->nsum, (void *)W->vis, (void *)W->q, (void *)W->canon, (void *)W->cand, (void *)W->cscore, (void *)W->lW, (void *)W->lB, (void *)W->lC,
                     (void *)W->lG, (void *)W->lH, (void *)W->lD, (void *)W->lDH, (void *)W->cnt, (void *)W->gkeys, (void *)W->geta, (void *)W->ginter, (void *)W->gslots,
                     (void *)W->flag, (void *)W->pos, (void *)W->ikeys, (void *)W->iids, (void *)W->target,
                     (void *)W->score, (void *)W->ccount, (void *)W->fillpos,
@@ -964,6 +1056,26 @@ LevelBox *coarsen_box(CoarsenWs *W) { return W->box; }
 
 // One coarsening level, entirely on the device (no host synchronisation);
 // the counters end up in the workspace box.
+// canon[] of the level's hyperedges (see k_dst_hash)
+static void dst_groups(const Level &L, int32_t *canon, Arena &A) {
+    cudaStream_t s = A.stream();
+    const int32_t e = L.e;
+    if (e <= 0) return;
+    uint32_t *key = A.get<uint32_t>(e), *val = A.get<uint32_t>(e);
+    int32_t *nr = A.get<int32_t>(e), *rp = A.get<int32_t>(e + 1), *rep = A.get<int32_t>(e);
+    k_dst_hash<<<grid_of((int64_t)e * 32, 256), 256, 0, s>>>(L.off, L.pin, L.nsrc, e, key, val);
+    HP_LAUNCH_CHECK();
+    radix_sort(key, val, e, 32, A);
+    k_dst_runs<<<grid_of((int64_t)e * 32, 256), 256, 0, s>>>(key, val, L.off, L.pin, L.nsrc, e, nr);
+    HP_LAUNCH_CHECK();
+    scan_excl(nr, rp, e, rp + e, A);
+    k_dst_rep<<<grid_of(e, 256), 256, 0, s>>>(val, nr, rp, e, rep);
+    HP_LAUNCH_CHECK();
+    k_dst_canon<<<grid_of(e, 256), 256, 0, s>>>(val, nr, rp, rep, e, canon);
+    HP_LAUNCH_CHECK();
+    for (void *p : {(void *)key, (void *)val, (void *)nr, (void *)rp, (void *)rep}) A.release(p);
+}
+
 void coarsen_level(Level &L, int32_t level, const int32_t *w, const Params &P, int32_t *mate, CoarsenWs &W, Arena &A,
                    uint32_t *err_dev, int32_t *cand_out, uint64_t *score_out, cudaEvent_t *prop_events) {
     cudaStream_t s = A.stream();
@@ -1010,7 +1122,14 @@ void coarsen_level(Level &L, int32_t level, const int32_t *w, const Params &P, i
     C.cand = W.cand;
     C.cscore = W.cscore;
     C.nbcnt = L.nbnd;   // exact counts replace the bounds (used to size the next level)
-    if (prop_events) HPC(cudaEventRecord(prop_events[0], s));
+    C.canon = nullptr;
+    if (prop_events) HPC(cudaEventRecord(prop_events[0], s));   // the grouping counts as proposal time
+    if (level == 0) {
+        // large hyperedges with equal destination lists (the channels of one
+        // source in a layered network) are walked once per warp group
+        dst_groups(L, W.canon, A);
+        C.canon = W.canon;
+    }
     if (pi <= 4) run_proposal<4>(C, L, P, W, A);
     else run_proposal<16>(C, L, P, W, A);
     if (prop_events) HPC(cudaEventRecord(prop_events[1], s));
