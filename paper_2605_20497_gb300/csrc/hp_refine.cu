@@ -858,7 +858,7 @@ struct ChainCtx {
 // ties.  For a chosen move all choosers share gain(m), so the acceptor of
 // maximum (G, node id) is the chooser of minimum penalty, then maximum id.
 __device__ void ph_choose(const ChainCtx &C, int r, int packed, int32_t m, int64_t t0, int64_t nt) {
-    constexpr int B = 8;   // candidates loaded together, ahead of their evaluation
+    constexpr int B = 4;   // candidates loaded together, ahead of their evaluation
     STRIDE(i0, m, t0, nt) {
         int32_t i = (int32_t)i0;
         C.choice[i] = -1;
