@@ -366,7 +366,7 @@ __device__ void cta_walk(const PropCtx &C, int32_t v, int32_t i0, int32_t deg, i
 
 // ---------------------------------------------------------------- destination-list groups
 // canon[e] = one representative of the hyperedges whose destination pin
-// lists equal e's (level 0 only; the proposal walks such lists once per warp
+// lists equal e's (levels of large hyperedges; the proposal walks such lists once per warp
 // group).  Lists are hashed, sorted by hash, and equal neighbours in that
 // order are confirmed pin by pin, so a hash collision only splits a group.
 __device__ __forceinline__ uint32_t fmix32(uint32_t h) {
@@ -727,7 +727,7 @@ __global__ void k_tiers(const int32_t *bound, const long long *vis, int32_t n, u
 struct CoarsenWs {
     int32_t cn, ce, pi;
     uint64_t *q;
-    int32_t *canon;   // destination-list groups of the level-0 hyperedges
+    int32_t *canon;   // destination-list groups of the current level's hyperedges
     int32_t *cand;
     uint64_t *cscore;
     int32_t *lW, *lB, *lC, *lG, *lH, *lD, *lDH, *cnt;   // cnt: 0 W 1 B 2 C 3 G 4 errors 5 H 6 D 7 DH
@@ -1124,9 +1124,10 @@ void coarsen_level(Level &L, int32_t level, const int32_t *w, const Params &P, i
     C.nbcnt = L.nbnd;   // exact counts replace the bounds (used to size the next level)
     C.canon = nullptr;
     if (prop_events) HPC(cudaEventRecord(prop_events[0], s));   // the grouping counts as proposal time
-    if (level == 0) {
-        // large hyperedges with equal destination lists (the channels of one
-        // source in a layered network) are walked once per warp group
+    if (L.np >= 16 * (int64_t)L.e) {
+        // levels of large hyperedges: those with equal destination lists (the
+        // channels of one source in a layered network, before and after
+        // contraction) are walked once per warp group
         dst_groups(L, W.canon, A);
         C.canon = W.canon;
     }

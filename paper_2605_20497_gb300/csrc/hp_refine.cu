@@ -9,6 +9,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <climits>
 #include <initializer_list>
 
 #include "hp_internal.cuh"
@@ -611,12 +612,13 @@ __global__ void k_level_nodes(const int32_t *off, const int32_t *ioff, const int
 // (the in-sequence pass); tiny ones are also listed apart.
 constexpr int TINY_E = 8;
 __global__ void k_level_edges(const int32_t *off, int32_t e, int32_t small_max, int32_t *act, int32_t *big,
-                              int32_t *tiny, int32_t *cnt) {
+                              int32_t *tiny, int32_t *mid, int32_t *cnt) {
     GRID_STRIDE(i, (int64_t)e) {
         int32_t sz = off[i + 1] - off[i];
         if (sz >= 2 && sz <= small_max) {
             act[atomicAdd(&cnt[0], 1)] = (int32_t)i;
             if (sz <= TINY_E) tiny[atomicAdd(&cnt[3], 1)] = (int32_t)i;
+            else mid[atomicAdd(&cnt[4], 1)] = (int32_t)i;
         } else if (sz > small_max) big[atomicAdd(&cnt[1], 1)] = (int32_t)i;
     }
 }
@@ -1342,11 +1344,29 @@ struct SmallSeqArgs {
     long long gbound, cgbound;
 };
 // sort of the moves, chaining rounds, chain order, sequence positions
+// maximum over the CTA (all threads take part; s_ll holds 33 words)
+__device__ long long block_max_ll(long long x, long long *s_ll) {
+    for (int o = 16; o > 0; o >>= 1) x = max(x, __shfl_xor_sync(0xffffffffu, x, o));
+    if ((threadIdx.x & 31) == 0) s_ll[threadIdx.x >> 5] = x;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        long long y = threadIdx.x < (blockDim.x >> 5) ? s_ll[threadIdx.x] : LLONG_MIN;
+        for (int o = 16; o > 0; o >>= 1) y = max(y, __shfl_xor_sync(0xffffffffu, y, o));
+        if (threadIdx.x == 0) s_ll[32] = y;
+    }
+    __syncthreads();
+    const long long r = s_ll[32];
+    __syncthreads();
+    return r;
+}
+__device__ __forceinline__ int dev_bits(unsigned long long x) { return x ? 64 - __clzll((long long)x) : 0; }
+
 __global__ void __launch_bounds__(SEQ_T) k_seq_small(SmallSeqArgs A) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ uint32_t s_wc[32 * 256];
     __shared__ uint32_t s_hist[256 + 33];
     __shared__ int32_t s_tmp[40];
+    __shared__ long long s_ll[33];
     const int32_t m = A.cnt[C_MOVES];
     if (m == 0 || m > SEQ_MAX) return;
     const int64_t t0 = threadIdx.x, nt = blockDim.x;
@@ -1363,9 +1383,22 @@ __global__ void __launch_bounds__(SEQ_T) k_seq_small(SmallSeqArgs A) {
         va = A.gv;
         vb = A.gv + SEQ_MAX;
     }
-    if (A.sb + A.gb + A.nb <= 64) {
-        ph_move_keys(A.M, m, A.gbound, A.gb, A.nb, -1, A.keys, A.idx, 1, t0, nt);
-        block_radix_sort_buf<uint64_t>(A.keys, A.idx, m, (A.sb + A.gb + A.nb + 7) / 8, ka, kb, va, vb, s_wc, s_hist);
+    // key widths from this repetition's moves: gains and ids are far below
+    // their static bounds, so the sort takes fewer 8-bit passes
+    long long gmx = 0, smx = 0, nmx = 0;
+    for (int64_t i = t0; i < m; i += nt) {
+        gmx = max(gmx, A.M.gain[i]);
+        smx = max(smx, (long long)A.M.src[i]);
+        nmx = max(nmx, (long long)A.M.node[i]);
+    }
+    gmx = block_max_ll(gmx, s_ll);
+    smx = block_max_ll(smx, s_ll);
+    nmx = block_max_ll(nmx, s_ll);
+    const int gb = dev_bits((unsigned long long)gmx), nb = dev_bits((unsigned long long)nmx),
+              sb = dev_bits((unsigned long long)smx);
+    if (sb + gb + nb <= 64) {
+        ph_move_keys(A.M, m, gmx, gb, nb, -1, A.keys, A.idx, 1, t0, nt);
+        block_radix_sort_buf<uint64_t>(A.keys, A.idx, m, (sb + gb + nb + 7) / 8, ka, kb, va, vb, s_wc, s_hist);
     } else {
         const int fb[3] = {A.nb, A.gb, A.sb};
         for (int f = 0; f < 3; f++) {
@@ -1399,9 +1432,13 @@ __global__ void __launch_bounds__(SEQ_T) k_seq_small(SmallSeqArgs A) {
     ph_head_collect(A.Q, m, A.heads, &A.cnt[C_NH], t0, nt);
     __syncthreads();
     const int32_t nh = *(volatile int32_t *)&A.cnt[C_NH];
-    if (A.cgb + A.nb <= 64) {
-        ph_head_keys(A.heads, nh, A.Q.cgain, A.S.node, A.cgbound, A.nb, -1, A.hkeys, t0, nt);
-        block_radix_sort_buf<uint64_t>(A.hkeys, A.heads, nh, (A.cgb + A.nb + 7) / 8, ka, kb, va, vb, s_wc, s_hist);
+    long long cmx = 0;
+    for (int64_t k = t0; k < nh; k += nt) cmx = max(cmx, A.Q.cgain[A.heads[k]]);
+    cmx = block_max_ll(cmx, s_ll);
+    const int cgb = dev_bits((unsigned long long)cmx);
+    if (cgb + nb <= 64) {
+        ph_head_keys(A.heads, nh, A.Q.cgain, A.S.node, cmx, nb, -1, A.hkeys, t0, nt);
+        block_radix_sort_buf<uint64_t>(A.hkeys, A.heads, nh, (cgb + nb + 7) / 8, ka, kb, va, vb, s_wc, s_hist);
     } else {
         for (int f = 0; f < 2; f++) {
             __syncthreads();
@@ -1716,6 +1753,7 @@ struct LevelWs {
     int32_t *cl, *hubs, *cw;
     int32_t *cflag, *cpos, *cut, *cut_off;   // cut incident hyperedges per node
     int32_t *tiny, n_tiny;                   // hyperedges of 2..8 pins
+    int32_t *mid, n_mid;                     // hyperedges of 9..small_max pins
     int32_t *touched, *ttouched;             // hyperedges with a moved pin (more than / at most 8 pins)
     Moves M, S;
     uint64_t *keys, *sk;
@@ -1785,6 +1823,7 @@ LevelWs *refine_workspace(int32_t n, int64_t np, int32_t e, int32_t nparts, int3
     W->cut = A.get<int32_t>(np);
     W->cut_off = A.get<int32_t>(n + 1);
     W->tiny = A.get<int32_t>(e);
+    W->mid = A.get<int32_t>(e);
     W->touched = A.get<int32_t>(e);
     W->ttouched = A.get<int32_t>(e);
     for (Moves *m : {&W->M, &W->S}) {
@@ -1824,7 +1863,7 @@ LevelWs *refine_workspace(int32_t n, int64_t np, int32_t e, int32_t nparts, int3
     W->edd = A.get<long long>(2 * (int64_t)n);
     W->vhead = A.get<int32_t>(std::max<int64_t>(nparts, 1));
     W->bgain = A.get<long long>(1);
-    W->lvl = A.get<int32_t>(4);
+    W->lvl = A.get<int32_t>(5);
     // overflow tables of the gain kernel, one per CTA of its fallback grid
     W->gcap = pow2_at_least(2 * (int64_t)nparts + 2);
     W->gnb = (int)std::min<int64_t>(num_sms(), std::max<int64_t>(1, ((int64_t)1 << 27) / ((int64_t)W->gcap * 12)));
@@ -1850,7 +1889,7 @@ void refine_workspace_free(LevelWs *W, Arena &A) {
     for (void *p : std::initializer_list<void *>{
              W->act, W->big, W->wns, W->singin, W->PL.p, W->PL.cnt, W->PL.cin, W->PL.lam, W->R.cnt, W->R.linked,
              W->R.D0, W->R.psize, W->R.saving, W->R.pc, W->R.pred, W->R.succ, W->R.chain, W->R.mvpos, W->R.cgain,
-             W->R.gseq, W->R.acc0, W->R.dDs, W->R.dDd, W->R.viol, W->cl, W->hubs, W->cw, W->cflag, W->cpos, W->cut, W->cut_off, W->tiny, W->touched, W->ttouched, W->M.node, W->M.src, W->M.dst, W->M.gain,
+             W->R.gseq, W->R.acc0, W->R.dDs, W->R.dDd, W->R.viol, W->cl, W->hubs, W->cw, W->cflag, W->cpos, W->cut, W->cut_off, W->tiny, W->mid, W->touched, W->ttouched, W->M.node, W->M.src, W->M.dst, W->M.gain,
              W->S.node, W->S.src, W->S.dst, W->S.gain, W->keys, W->sk, W->idx, W->sv, W->msz, W->mni, W->first, W->choice, W->accnode, W->pen,
              W->minpen, W->acc1, W->pos, W->clen, W->lens, W->starts, W->cstart, W->seqmove, W->heads, W->hkeys,
              W->vkey, W->vidx, W->vsz, W->vdd, W->gsz, W->gdd, W->esz, W->edd, W->vhead, W->bgain, W->lvl, W->ovf, W->gk, W->gc, W->ptab, W->ibuf})
@@ -1865,7 +1904,7 @@ static void level_prepare(const Level &L, const int32_t *w, LevelWs &W, Arena &A
     W.n = n;
     W.R.n = n;
     W.R.e = e;
-    HPC(cudaMemsetAsync(W.lvl, 0, 4 * sizeof(int32_t), s));
+    HPC(cudaMemsetAsync(W.lvl, 0, 5 * sizeof(int32_t), s));
     if (e > 0) {
         k_max_edge<<<grid_of(e, 256), 256, 0, s>>>(L.off, e, W.lvl + 2);
         HP_LAUNCH_CHECK();
@@ -1874,7 +1913,7 @@ static void level_prepare(const Level &L, const int32_t *w, LevelWs &W, Arena &A
     W.small_max = std::min<int32_t>(std::max<int32_t>(W.max_e, 2), 512);
     W.pcap = pow2_at_least(2 * (int64_t)W.small_max);
     if (e > 0) {
-        k_level_edges<<<grid_of(e, 256), 256, 0, s>>>(L.off, e, W.small_max, W.act, W.big, W.tiny, W.lvl);
+        k_level_edges<<<grid_of(e, 256), 256, 0, s>>>(L.off, e, W.small_max, W.act, W.big, W.tiny, W.mid, W.lvl);
         HP_LAUNCH_CHECK();
     }
     HPC(cudaMemsetAsync(W.wns, 0, sizeof(long long) * n, s));
@@ -1884,11 +1923,12 @@ static void level_prepare(const Level &L, const int32_t *w, LevelWs &W, Arena &A
                                                           W.singin);
         HP_LAUNCH_CHECK();
     }
-    int32_t hc[4];
+    int32_t hc[5];
     fetch_bytes(hc, W.lvl, sizeof hc, s);
     W.n_act = hc[0];
     W.n_big = hc[1];
     W.n_tiny = hc[3];
+    W.n_mid = hc[4];
     if (W.n_big > 0 && !W.ptab) throw Error(HP_ERR_INTERNAL, "large hyperedge buffers missing");
 }
 
@@ -1906,13 +1946,13 @@ static int32_t rep_run(const Level &L, const int32_t *w, const Params &P, int32_
     k_rep_nodes<<<grid_of(n, 256), 256, 0, s>>>(rho, L.size, W.singin, n, R.psize, R.D0);
     HP_LAUNCH_CHECK();
     // pins(p,e), pins_in(p,e), D(p), saving(v)
-    if (W.n_act > 0) {
+    if (W.n_mid > 0) {
         const int per = 3 * (int)W.pcap + 4 * W.small_max + 1;
         size_t sm = (size_t)per * 4 * (PLW_T / 32);
         int occ = prepare_kernel((const void *)k_plist_small, PLW_T, sm);
-        int grid = (int)std::min<int64_t>(cdiv(W.n_act, PLW_T / 32), (int64_t)num_sms() * occ);
-        k_plist_small<<<std::max(grid, 1), PLW_T, sm, s>>>(L.off, L.pin, L.nsrc, w, rho, W.n_act, W.act, W.small_max,
-                                                           W.pcap, W.PL, R.D0, R.saving, TINY_E);
+        int grid = (int)std::min<int64_t>(cdiv(W.n_mid, PLW_T / 32), (int64_t)num_sms() * occ);
+        k_plist_small<<<std::max(grid, 1), PLW_T, sm, s>>>(L.off, L.pin, L.nsrc, w, rho, W.n_mid, W.mid, W.small_max,
+                                                           W.pcap, W.PL, R.D0, R.saving, 0);
         HP_LAUNCH_CHECK();
     }
     if (W.n_tiny > 0) {
