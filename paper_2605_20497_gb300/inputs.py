@@ -59,16 +59,43 @@ def _csr(rows, n, name="", src_counts=None, weights=None) -> Hypergraph:
     return Hypergraph(n, off.astype(np.int32), pins.astype(np.int32), src_counts, weights, name)
 
 
+_M64 = np.uint64(0xFFFFFFFFFFFFFFFF)
+
+
+def splitmix64(x: np.ndarray) -> np.ndarray:
+    """SplitMix64 output function (Steele, Lea, Flood 2014) of counters x
+    (uint64 arrays, wrapping arithmetic): the same stream on every machine
+    and numpy version."""
+    with np.errstate(over="ignore"):
+        z = x + np.uint64(0x9E3779B97F4A7C15)
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+        return z ^ (z >> np.uint64(31))
+
+
 def random_snn(n: int, k: int, seed: int = 0) -> Hypergraph:
-    """Node i owns hyperedge {i} + k distinct uniform targets != i (sorted)."""
-    rng = np.random.default_rng(seed)
+    """Node i owns hyperedge {i} + k distinct uniform targets != i (sorted).
+
+    Target candidates of node i are splitmix64(counter(seed, i, j)) mod
+    (n - 1), shifted past i, for j = 0, 1, ...; the first k distinct ones
+    are kept."""
+    assert n >= 2 and k <= n - 1 and n < (1 << 28)
     pins = np.empty((n, k + 1), dtype=np.int32)
     pins[:, 0] = np.arange(n, dtype=np.int32)
+    draw = 2 * k + 16
+    base = np.uint64(seed & 0xFFFF) << np.uint64(48)
     for i in range(n):
-        t = rng.choice(n - 1, size=k, replace=False)
-        t = t + (t >= i)          # skip the source itself
-        t.sort()
-        pins[i, 1:] = t
+        got = np.empty(0, dtype=np.int64)
+        j0 = 0
+        while got.size < k:
+            j = np.arange(j0, j0 + draw, dtype=np.uint64)
+            c = (splitmix64(base | (np.uint64(i) << np.uint64(20)) | j) % np.uint64(n - 1)).astype(np.int64)
+            c = c + (c >= i)          # skip the source itself
+            allc = np.concatenate([got, c])
+            _, first = np.unique(allc, return_index=True)
+            got = allc[np.sort(first)][:k]
+            j0 += draw
+        pins[i, 1:] = np.sort(got)
     off = np.arange(0, n * (k + 1) + 1, k + 1, dtype=np.int64)
     return Hypergraph(n, off.astype(np.int32), pins.reshape(-1), None, None, f"random_snn_{n}x{k}")
 

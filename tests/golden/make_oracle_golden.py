@@ -1,9 +1,10 @@
 """Writes the oracle's full-size results used by tests/test_gpu_fullsize.py.
 
-Runs only the CPU oracle (oracle/) on the deterministic layered spiking-
-network workloads (no random numbers in their generator) and stores, per
-workload: a hash of the generated input, the status, the statistics, the
-per-level trace and a hash of the part vector.  Usage (from the repository
+Runs only the CPU oracle (oracle/) on full-size workloads whose generators
+give the same input on every machine (the layered networks use no random
+numbers; the random one draws from a SplitMix64 counter stream) and stores,
+per workload: a hash of the generated input, the status, the statistics,
+the per-level trace and a hash of the part vector.  Usage (from the repository
 root): python tests/golden/make_oracle_golden.py [workload ...]
 """
 import hashlib
@@ -58,4 +59,4 @@ def main(names):
 
 
 if __name__ == "__main__":
-    main(sys.argv[1:] or ["layered_snn_65k", "layered_snn_262k"])
+    main(sys.argv[1:] or ["layered_snn_65k", "layered_snn_262k", "random_snn_16k"])

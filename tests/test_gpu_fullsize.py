@@ -1,6 +1,7 @@
 """Full-size parity: the CUDA path on the layered spiking-network workloads
 (65,536 and 262,144 nodes; the second is the one bench.py times, in the same
-call configuration) against the oracle's results stored by
+call configuration) and on the random one of 16,384 nodes with 127 targets
+each, against the oracle's results stored by
 tests/golden/make_oracle_golden.py.  The oracle takes minutes on these, so
 its part vector is compared by hash, with its statistics and its per-level
 trace compared value by value."""
@@ -34,7 +35,7 @@ def sha(a) -> str:
     return hashlib.sha256(np.ascontiguousarray(a, dtype="<i4").tobytes()).hexdigest()
 
 
-@pytest.mark.parametrize("name", ["layered_snn_65k", "layered_snn_262k"])
+@pytest.mark.parametrize("name", ["layered_snn_65k", "layered_snn_262k", "random_snn_16k"])
 def test_fullsize_matches_stored_oracle(torch, name):
     with open(os.path.join(GOLDEN, f"oracle_{name}.json")) as f:
         gold = json.load(f)
