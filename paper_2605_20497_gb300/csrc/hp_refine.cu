@@ -122,11 +122,11 @@ __global__ void __launch_bounds__(PLW_T) k_plist_small(const int32_t *off, const
                                                        int32_t *D, long long *saving, int32_t skip_below) {
     extern __shared__ __align__(16) int32_t sm[];
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int per = 3 * (int)cap + 4 * small_max + 1;
+    // table of cap slots; entry buffers of cap / 2 >= lambda(e) entries
+    const int per = 5 * (int)cap + 1, ent = (int)cap / 2;
     int32_t *base = sm + wid * per;
     int32_t *keys = base, *tc = base + cap, *tci = base + 2 * cap;
-    int32_t *es = base + 3 * cap, *ep = es + small_max, *ec = ep + small_max, *eci = ec + small_max,
-            *gcnt = eci + small_max;
+    int32_t *es = base + 3 * cap, *ep = es + ent, *ec = ep + ent, *eci = ec + ent, *gcnt = eci + ent;
     for (uint32_t i = lane; i < cap; i += 32) {
         keys[i] = -1;
         tc[i] = 0;
@@ -195,7 +195,7 @@ static void build_plist(const Level &L, const int32_t *w, const int32_t *rho, in
     if (L.e == 0) return;
     const int32_t small_max = std::min<int32_t>(std::max<int32_t>(max_e, 1), 512);
     const uint32_t cap = pow2_at_least(2 * (int64_t)small_max);
-    const int per = 3 * (int)cap + 4 * small_max + 1;
+    const int per = 5 * (int)cap + 1;
     size_t sm = (size_t)per * 4 * (PLW_T / 32);
     int occ = prepare_kernel((const void *)k_plist_small, PLW_T, sm);
     int grid = (int)std::min<int64_t>(cdiv(L.e, PLW_T / 32), (int64_t)num_sms() * std::max(occ, 1));
@@ -907,7 +907,8 @@ __device__ void ph_choose(const ChainCtx &C, int r, int packed, int32_t m, int64
         C.choice[i] = best;
         C.pen[i] = bpen;
         if (best >= 0 && packed)
-            atomicMax(&C.acc[r & 1][best], ((0xffffffffull - bpen) << 32) | (unsigned long long)(uint32_t)vi);
+            atomicMax(&((r & 1) ? C.acc[1] : C.acc[0])[best],
+                      ((0xffffffffull - bpen) << 32) | (unsigned long long)(uint32_t)vi);
     }
 }
 __device__ void ph_accept_min(const ChainCtx &C, int32_t m, int64_t t0, int64_t nt) {
@@ -929,7 +930,7 @@ __device__ void ph_link(const ChainCtx &C, int r, int packed, int32_t m, int64_t
         bool won = false;
         if (j >= 0) {
             if (packed)
-                won = C.acc[r & 1][j] ==
+                won = ((r & 1) ? C.acc[1] : C.acc[0])[j] ==
                       (((0xffffffffull - C.pen[i]) << 32) | (unsigned long long)(uint32_t)C.node[i]);
             else
                 won = C.pen[i] == C.minpen[j] && C.accnode[j] == C.node[i];
@@ -939,7 +940,7 @@ __device__ void ph_link(const ChainCtx &C, int r, int packed, int32_t m, int64_t
             C.succ[i] = j;
             C.linked[r] = 1;
         }
-        if (packed) C.acc[(r + 1) & 1][i] = 0;
+        if (packed) ((r & 1) ? C.acc[0] : C.acc[1])[i] = 0;
     }
 }
 
@@ -1412,17 +1413,42 @@ __global__ void __launch_bounds__(SEQ_T) k_seq_small(SmallSeqArgs A) {
     __syncthreads();
     block_scan_excl(A.pc, A.first, (int64_t)A.nparts + 1, s_tmp);
     __syncthreads();
+    // the arrays the window scans read per candidate move (gain, pred, size
+    // and |in| of its node) in shared memory, in the sort buffers, which are
+    // free now
+    ChainCtx CC = A.C;
+    const bool staged = m <= SMALLM;
+    if (staged) {
+        long long *s_gain = reinterpret_cast<long long *>(smem);
+        int32_t *s_pred = reinterpret_cast<int32_t *>(s_gain + SMALLM);
+        int32_t *s_msz = s_pred + SMALLM, *s_mni = s_msz + SMALLM;
+        for (int64_t i = t0; i < m; i += nt) {
+            s_gain[i] = A.C.gain[i];
+            s_pred[i] = A.C.pred[i];
+            s_msz[i] = A.C.msz[i];
+            s_mni[i] = A.C.mni[i];
+        }
+        CC.gain = s_gain;
+        CC.pred = s_pred;
+        CC.msz = s_msz;
+        CC.mni = s_mni;
+        __syncthreads();
+    }
     for (int r = 0; r < A.rounds; r++) {
         if (r > 0 && !*(volatile int32_t *)&A.C.linked[r - 1]) break;
-        ph_choose(A.C, r, A.packed, m, t0, nt);
+        ph_choose(CC, r, A.packed, m, t0, nt);
         __syncthreads();
         if (!A.packed) {
-            ph_accept_min(A.C, m, t0, nt);
+            ph_accept_min(CC, m, t0, nt);
             __syncthreads();
-            ph_accept_id(A.C, m, t0, nt);
+            ph_accept_id(CC, m, t0, nt);
             __syncthreads();
         }
-        ph_link(A.C, r, A.packed, m, t0, nt);
+        ph_link(CC, r, A.packed, m, t0, nt);
+        __syncthreads();
+    }
+    if (staged) {
+        for (int64_t i = t0; i < m; i += nt) A.C.pred[i] = CC.pred[i];
         __syncthreads();
     }
     ph_path_heads(A.Q, m, t0, nt);
@@ -1777,6 +1803,7 @@ struct LevelWs {
     int pnb;
     long long *bgain;
     int32_t *lvl;   // per-level counters
+    int32_t *pmark; // [nparts] parts in use
 };
 
 LevelWs *refine_workspace(int32_t n, int64_t np, int32_t e, int32_t nparts, int32_t max_e, const Params &P,
@@ -1863,7 +1890,8 @@ LevelWs *refine_workspace(int32_t n, int64_t np, int32_t e, int32_t nparts, int3
     W->edd = A.get<long long>(2 * (int64_t)n);
     W->vhead = A.get<int32_t>(std::max<int64_t>(nparts, 1));
     W->bgain = A.get<long long>(1);
-    W->lvl = A.get<int32_t>(5);
+    W->lvl = A.get<int32_t>(6);
+    W->pmark = A.get<int32_t>(std::max(nparts, 1));
     // overflow tables of the gain kernel, one per CTA of its fallback grid
     W->gcap = pow2_at_least(2 * (int64_t)nparts + 2);
     W->gnb = (int)std::min<int64_t>(num_sms(), std::max<int64_t>(1, ((int64_t)1 << 27) / ((int64_t)W->gcap * 12)));
@@ -1892,26 +1920,38 @@ void refine_workspace_free(LevelWs *W, Arena &A) {
              W->R.gseq, W->R.acc0, W->R.dDs, W->R.dDd, W->R.viol, W->cl, W->hubs, W->cw, W->cflag, W->cpos, W->cut, W->cut_off, W->tiny, W->mid, W->touched, W->ttouched, W->M.node, W->M.src, W->M.dst, W->M.gain,
              W->S.node, W->S.src, W->S.dst, W->S.gain, W->keys, W->sk, W->idx, W->sv, W->msz, W->mni, W->first, W->choice, W->accnode, W->pen,
              W->minpen, W->acc1, W->pos, W->clen, W->lens, W->starts, W->cstart, W->seqmove, W->heads, W->hkeys,
-             W->vkey, W->vidx, W->vsz, W->vdd, W->gsz, W->gdd, W->esz, W->edd, W->vhead, W->bgain, W->lvl, W->ovf, W->gk, W->gc, W->ptab, W->ibuf})
+             W->vkey, W->vidx, W->vsz, W->vdd, W->gsz, W->gdd, W->esz, W->edd, W->vhead, W->bgain, W->lvl, W->pmark, W->ovf, W->gk, W->gc, W->ptab, W->ibuf})
         A.release(p);
     delete W;
 }
 
 // per level: hyperedge classes and per-node constants
-static void level_prepare(const Level &L, const int32_t *w, LevelWs &W, Arena &A) {
+// parts holding at least one node (lambda(e) never exceeds it within a level:
+// moves only go to parts that exist)
+__global__ void k_used_parts(const int32_t *rho, int32_t n, int32_t *mark, int32_t *count) {
+    GRID_STRIDE(v, (int64_t)n) {
+        if (atomicExch(&mark[rho[v]], 1) == 0) atomicAdd(count, 1);
+    }
+}
+
+static void level_prepare(const Level &L, const int32_t *w, const int32_t *rho, LevelWs &W, Arena &A) {
     cudaStream_t s = A.stream();
     const int32_t n = L.n, e = L.e;
     W.n = n;
     W.R.n = n;
     W.R.e = e;
-    HPC(cudaMemsetAsync(W.lvl, 0, 5 * sizeof(int32_t), s));
+    HPC(cudaMemsetAsync(W.lvl, 0, 6 * sizeof(int32_t), s));
     if (e > 0) {
         k_max_edge<<<grid_of(e, 256), 256, 0, s>>>(L.off, e, W.lvl + 2);
         HP_LAUNCH_CHECK();
     }
+    HPC(cudaMemsetAsync(W.pmark, 0, sizeof(int32_t) * std::max(W.nparts, 1), s));
+    if (n > 0) {
+        k_used_parts<<<grid_of(n, 256), 256, 0, s>>>(rho, n, W.pmark, W.lvl + 5);
+        HP_LAUNCH_CHECK();
+    }
     W.max_e = fetch<int32_t>(W.lvl + 2, s);
     W.small_max = std::min<int32_t>(std::max<int32_t>(W.max_e, 2), 512);
-    W.pcap = pow2_at_least(2 * (int64_t)W.small_max);
     if (e > 0) {
         k_level_edges<<<grid_of(e, 256), 256, 0, s>>>(L.off, e, W.small_max, W.act, W.big, W.tiny, W.mid, W.lvl);
         HP_LAUNCH_CHECK();
@@ -1923,12 +1963,14 @@ static void level_prepare(const Level &L, const int32_t *w, LevelWs &W, Arena &A
                                                           W.singin);
         HP_LAUNCH_CHECK();
     }
-    int32_t hc[5];
+    int32_t hc[6];
     fetch_bytes(hc, W.lvl, sizeof hc, s);
     W.n_act = hc[0];
     W.n_big = hc[1];
     W.n_tiny = hc[3];
     W.n_mid = hc[4];
+    // pins lists of the level hold at most min(small_max, parts in use) entries
+    W.pcap = pow2_at_least(2 * (int64_t)std::max<int32_t>(2, std::min<int32_t>(W.small_max, hc[5])));
     if (W.n_big > 0 && !W.ptab) throw Error(HP_ERR_INTERNAL, "large hyperedge buffers missing");
 }
 
@@ -1947,7 +1989,7 @@ static int32_t rep_run(const Level &L, const int32_t *w, const Params &P, int32_
     HP_LAUNCH_CHECK();
     // pins(p,e), pins_in(p,e), D(p), saving(v)
     if (W.n_mid > 0) {
-        const int per = 3 * (int)W.pcap + 4 * W.small_max + 1;
+        const int per = 5 * (int)W.pcap + 1;
         size_t sm = (size_t)per * 4 * (PLW_T / 32);
         int occ = prepare_kernel((const void *)k_plist_small, PLW_T, sm);
         int grid = (int)std::min<int64_t>(cdiv(W.n_mid, PLW_T / 32), (int64_t)num_sms() * occ);
@@ -2190,7 +2232,7 @@ int32_t refine_rep_debug(const Level &L, const int32_t *w, int32_t nparts, const
     if (L.n == 0) return 0;
     const int32_t max_e = max_edge_size(L, A);
     LevelWs *W = refine_workspace(L.n, L.np, L.e, nparts, max_e, P, A);
-    level_prepare(L, w, *W, A);
+    level_prepare(L, w, rho, *W, A);
     int32_t k = rep_run(L, w, P, rho, second_half, *W, A, err_dev, &dbg);
     refine_workspace_free(W, A);
     return k;
@@ -2200,7 +2242,7 @@ RefineOut refine_level(const Level &L, const int32_t *w, const Params &P, int32_
                        uint32_t *err_dev) {
     RefineOut out;
     if (L.n == 0 || P.o.theta == 0) return out;
-    level_prepare(L, w, *W, A);
+    level_prepare(L, w, rho, *W, A);
     const int32_t half = P.o.theta / 2;
     for (int32_t rep = 0; rep < P.o.theta; rep++) {
         const int32_t k = rep_run(L, w, P, rho, rep >= half, *W, A, err_dev, nullptr);
