@@ -156,6 +156,33 @@ HP_API hp_status hp_partition_ex(const int32_t *pins, const int32_t *offsets, in
                           hp_level_trace *trace, int32_t trace_cap, void *stream);
 
 /*
+ * One hypergraph of a batch: the arguments of hp_partition, device pointers.
+ */
+typedef struct {
+    const int32_t *pins, *offsets, *src_counts, *weights;
+    int32_t num_hedges, num_nodes, omega, delta;
+    uint64_t seed;
+    int32_t *part_out;
+} hp_instance;
+
+/*
+ * hp_partition_batch -- partitions count independent hypergraphs (each one
+ *   exactly as hp_partition would, same part vector and stats) with up to
+ *   `concurrency` (1..64) of them in flight at once, largest first, each on a
+ *   stream of its own; the paper partitions one hypergraph per call, this
+ *   is the batched form for many small ones.
+ *   inst: host array [count]; opt: shared options (NULL = defaults);
+ *   stats_out, status_out: host arrays [count] or NULL, filled per instance.
+ *   The work starts after the work already queued on `stream`, and `stream`
+ *   waits for all of it.  Returns HP_OK when every instance succeeded, else
+ *   the status of the first failing instance (by index), whose message
+ *   hp_last_error gives; the other instances are still partitioned.
+ *   Synchronous with respect to the host.
+ */
+HP_API hp_status hp_partition_batch(const hp_instance *inst, int32_t count, const hp_options *opt,
+                                    int32_t concurrency, hp_stats *stats_out, int32_t *status_out, void *stream);
+
+/*
  * hp_partition_host -- the same with every array in host memory: the call
  * copies the hypergraph to the device once and the part vector back once
  * (the two transfers of Sec. VII-C).  part_out is host int32[num_nodes].

@@ -118,8 +118,9 @@ template unsigned long long fetch<unsigned long long>(const unsigned long long *
 template long long fetch<long long>(const long long *, cudaStream_t);
 
 int prepare_kernel(const void *func, int block, size_t smem) {
-    // per (kernel, device): the dynamic shared memory limit only ever grows,
-    // so a size admitted once stays admitted; occupancy cached per size
+    // per (kernel, device): the dynamic shared memory limit is set on first
+    // use and only ever grows, so a size admitted once stays admitted;
+    // occupancy cached per size
     struct Entry {
         const void *f;
         int dev, block;
@@ -136,7 +137,9 @@ int prepare_kernel(const void *func, int block, size_t smem) {
     for (auto &l : limit)
         if (l.first.first == func && l.first.second == dev) lim = &l.second;
     if (!lim) {
-        limit.push_back({{func, dev}, (size_t)48 * 1024});
+        // nothing assumed: without the attribute a kernel gets 48 KB minus
+        // its static shared memory, so the first request always sets it
+        limit.push_back({{func, dev}, (size_t)0});
         lim = &limit.back().second;
     }
     if (smem > *lim) {

@@ -26,7 +26,7 @@ HP_ERR_OOM, HP_ERR_CUDA, HP_ERR_TIMEOUT, HP_ERR_INTERNAL = 4, 5, 6, 7
 HP_COUNT_INBOUND, HP_COUNT_INCIDENT = 0, 1
 
 EXPORTS = ("hp_default_options", "hp_partition", "hp_partition_ex", "hp_partition_host", "hp_set_allocator",
-           "hp_status_string", "hp_last_error", "hp_connectivity", "hp_connectivity_noalloc", "hp_debug_coarsen_level",
+           "hp_status_string", "hp_last_error", "hp_connectivity", "hp_connectivity_noalloc", "hp_partition_batch", "hp_debug_coarsen_level",
            "hp_debug_refine_rep")
 
 
@@ -49,6 +49,13 @@ class hp_level_trace(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int32), ("pairs", ctypes.c_int32), ("iso_pairs", ctypes.c_int32),
                 ("reps", ctypes.c_int32), ("pins", ctypes.c_int64), ("conn", ctypes.c_int64),
                 ("moves", ctypes.c_int64)]
+
+
+class hp_instance(ctypes.Structure):
+    _fields_ = [("pins", ctypes.c_void_p), ("offsets", ctypes.c_void_p), ("src_counts", ctypes.c_void_p),
+                ("weights", ctypes.c_void_p), ("num_hedges", ctypes.c_int32), ("num_nodes", ctypes.c_int32),
+                ("omega", ctypes.c_int32), ("delta", ctypes.c_int32), ("seed", ctypes.c_uint64),
+                ("part_out", ctypes.c_void_p)]
 
 
 _lib = None
@@ -80,6 +87,9 @@ def load() -> ctypes.CDLL:
         L.hp_connectivity.argtypes = [P, P, I32, P, P, I32, I32, ctypes.POINTER(ctypes.c_int64),
                                       ctypes.POINTER(ctypes.c_int64), P]
         L.hp_connectivity.restype = ctypes.c_int
+        L.hp_partition_batch.argtypes = [ctypes.POINTER(hp_instance), I32, ctypes.POINTER(hp_options), I32,
+                                         ctypes.POINTER(hp_stats), ctypes.POINTER(ctypes.c_int32), P]
+        L.hp_partition_batch.restype = ctypes.c_int
         L.hp_connectivity_noalloc.argtypes = L.hp_connectivity.argtypes
         L.hp_connectivity_noalloc.restype = ctypes.c_int
         L.hp_debug_coarsen_level.argtypes = [I32, I32, P, P, P, P, P, I32, I32, U64, I32, ctypes.POINTER(hp_options),
@@ -222,3 +232,27 @@ def partition_host(g, omega: int, delta: int, seed: int = 0, stream=0, **opts) -
     rc = hp_partition_host(p(pins), p(off), g.num_hedges, g.num_nodes, p(src), p(w), omega, delta, seed,
                            ctypes.byref(options(**opts)), p(part), ctypes.byref(st), stream)
     return Result(rc, part[: g.num_nodes], _stats_dict(st), [])
+
+
+def partition_batch(graphs, concurrency: int = 8, stream=0, **opts):
+    """graphs: list of (Hypergraph, omega, delta, seed).  Returns (status,
+    [Result]) from one hp_partition_batch call on device copies."""
+    import torch
+    n = len(graphs)
+    devs, parts = [], []
+    arr = (hp_instance * max(n, 1))()
+    for i, (g, om, de, seed) in enumerate(graphs):
+        d = to_device(g)
+        part = torch.empty(max(g.num_nodes, 1), dtype=torch.int32, device="cuda")
+        devs.append(d)
+        parts.append(part)
+        ptr = lambda x: None if x is None else x.data_ptr()
+        arr[i] = hp_instance(ptr(d["pins"]), ptr(d["offsets"]), ptr(d["src_counts"]), ptr(d["weights"]), g.num_hedges,
+                             g.num_nodes, om, de, seed & (2**64 - 1), part.data_ptr())
+    st = (hp_stats * max(n, 1))()
+    ss = (ctypes.c_int32 * max(n, 1))()
+    rc = load().hp_partition_batch(arr, n, ctypes.byref(options(**opts)), concurrency, st, ss, stream)
+    torch.cuda.synchronize()
+    out = [Result(int(ss[i]), parts[i][: graphs[i][0].num_nodes].cpu().numpy(), _stats_dict(st[i]), [])
+           for i in range(n)]
+    return rc, out

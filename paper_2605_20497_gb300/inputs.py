@@ -100,6 +100,85 @@ def random_snn(n: int, k: int, seed: int = 0) -> Hypergraph:
     return Hypergraph(n, off.astype(np.int32), pins.reshape(-1), None, None, f"random_snn_{n}x{k}")
 
 
+def _uniform01(x: np.ndarray) -> np.ndarray:
+    """Doubles in [0, 1) from the top 53 bits of splitmix64(x)."""
+    return (splitmix64(x) >> np.uint64(11)).astype(np.float64) * (1.0 / (1 << 53))
+
+
+def powerlaw_snn(n: int, seed: int, alpha: float = 2.2, smin: int = 2, smax: int = 1024) -> Hypergraph:
+    """Node i owns hyperedge {i} + (s_i - 1) distinct uniform targets != i,
+    s_i from the discrete power law P(s) ~ s^-alpha on [smin, min(smax, n)]
+    (inverse CDF), targets from a SplitMix64 counter stream; pins sorted."""
+    hi = min(smax, n)
+    sv = np.arange(smin, hi + 1, dtype=np.float64)
+    cdf = np.cumsum(sv ** -alpha)
+    cdf /= cdf[-1]
+    base = np.uint64(seed & 0xFFFF) << np.uint64(48)
+    u = _uniform01(base | np.arange(n, dtype=np.uint64))
+    sizes = (smin + np.searchsorted(cdf, u, side="right")).astype(np.int64)
+    sizes = np.minimum(sizes, hi)
+    need = sizes - 1
+    # candidates in rounds: 2 * need + 8 draws per hyperedge, then more for
+    # the hyperedges still short of distinct targets; first occurrences kept
+    tgt_c = np.empty(0, dtype=np.int64)
+    tgt_e = np.empty(0, dtype=np.int64)
+    tgt_j = np.empty(0, dtype=np.int64)
+    draws = 2 * need + 8
+    done = np.zeros(n, dtype=np.int64)   # draws used so far per hyperedge
+    got = np.zeros(n, dtype=np.int64)
+    while True:
+        todo = np.nonzero(got < need)[0]
+        if todo.size == 0:
+            break
+        cnt = draws[todo]
+        e_idx = np.repeat(todo, cnt)
+        j = np.repeat(done[todo], cnt) + np.arange(cnt.sum(), dtype=np.int64) - np.repeat(np.cumsum(cnt) - cnt, cnt)
+        ctr = base | (np.uint64(1) << np.uint64(47)) | (e_idx.astype(np.uint64) << np.uint64(24)) | j.astype(np.uint64)
+        c = (splitmix64(ctr) % np.uint64(max(n - 1, 1))).astype(np.int64)
+        c = c + (c >= e_idx)
+        done[todo] += cnt
+        draws[todo] *= 2
+        c = np.concatenate([tgt_c, c])
+        e_idx = np.concatenate([tgt_e, e_idx])
+        j = np.concatenate([tgt_j, j])
+        order = np.lexsort((j, c, e_idx))
+        c, e_idx, j = c[order], e_idx[order], j[order]
+        first = np.ones(c.size, dtype=bool)
+        first[1:] = (c[1:] != c[:-1]) | (e_idx[1:] != e_idx[:-1])
+        c, e_idx, j = c[first], e_idx[first], j[first]
+        order = np.lexsort((j, e_idx))
+        c, e_idx, j = c[order], e_idx[order], j[order]
+        start = np.searchsorted(e_idx, np.arange(n))
+        rank = np.arange(c.size) - start[e_idx]
+        keep = rank < need[e_idx]
+        tgt_c, tgt_e, tgt_j = c[keep], e_idx[keep], j[keep]
+        got = np.bincount(tgt_e, minlength=n)
+    order = np.lexsort((tgt_c, tgt_e))
+    tgt = tgt_c[order]
+    off = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(sizes, out=off[1:])
+    pins = np.empty(int(off[-1]), dtype=np.int32)
+    pins[off[:-1]] = np.arange(n, dtype=np.int32)
+    mask = np.ones(pins.size, dtype=bool)
+    mask[off[:-1]] = False
+    pins[mask] = tgt.astype(np.int32)
+    return Hypergraph(n, off.astype(np.int32), pins, None, None, f"powerlaw_snn_{n}_{seed}")
+
+
+def batch_snn(count: int, seed: int = 0, n_min: int = 1000, n_max: int = 64000):
+    """Independent instances: n log-uniform in [n_min, n_max], power-law
+    hyperedge sizes (powerlaw_snn), Omega uniform in {2^8..2^12}, Delta =
+    4 Omega.  Returns [(Hypergraph, Omega, Delta, partition seed)]."""
+    base = (np.uint64(seed & 0xFFFF) << np.uint64(48)) | (np.uint64(1) << np.uint64(46))
+    u = _uniform01(base | np.arange(2 * count, dtype=np.uint64))
+    out = []
+    for i in range(count):
+        n = int(np.exp(np.log(n_min) + u[2 * i] * (np.log(n_max) - np.log(n_min))))
+        om = 1 << (8 + min(int(u[2 * i + 1] * 5), 4))
+        out.append((powerlaw_snn(n, (seed * 7919 + i) & 0xFFFF), om, 4 * om, i))
+    return out
+
+
 def layered_snn(layers: int = 8, h: int = 32, w: int = 32, ch: int = 32) -> Hypergraph:
     """Locally connected layered net; node id = ((L*h + y)*w + x)*ch + c."""
     n = layers * h * w * ch

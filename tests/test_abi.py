@@ -52,3 +52,4 @@ def test_struct_layout_matches_header(lib):
     assert ctypes.sizeof(hp.hp_options) == 8 * 4
     assert ctypes.sizeof(hp.hp_stats) == 8 + 8 + 6 * 4 + 8 + 8 + 3 * 8 + 3 * 8 + 8
     assert ctypes.sizeof(hp.hp_level_trace) == 4 * 4 + 3 * 8
+    assert ctypes.sizeof(hp.hp_instance) == 4 * 8 + 4 * 4 + 8 + 8

@@ -152,3 +152,28 @@ def test_connectivity_entry_point(gpu):
                                    d["weights"].data_ptr(), part.data_ptr(), 500, 7)
     assert st == hp.HP_OK
     assert (c, cn) == oracle.objective(g, rho, 7)
+
+
+def test_powerlaw_instances_in_a_fresh_process(gpu):
+    """Power-law hyperedges send small levels' hub nodes to the direct-indexed
+    proposal tier with little shared memory; in a fresh process no earlier
+    call has raised that kernel's shared-memory limit, so this is where a
+    launch that relied on one would fail."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    code = (
+        "import sys, numpy as np; sys.path.insert(0, %r)\n"
+        "import oracle\n"
+        "from paper_2605_20497_gb300 import hp, inputs\n"
+        "oracle.build()\n"
+        "for n, seed, om in ((2000, 7, 512), (700, 3, 256), (5000, 11, 4096)):\n"
+        "    g = inputs.powerlaw_snn(n, seed)\n"
+        "    r = hp.partition(g, om, 4 * om, seed=seed)\n"
+        "    o = oracle.partition(g, om, 4 * om, seed=seed)\n"
+        "    assert r.status == o.status == 0, (r.status, hp.hp_last_error())\n"
+        "    assert np.array_equal(r.part, o.part)\n"
+        "print('ok')\n" % root)
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=600)
+    assert out.returncode == 0 and "ok" in out.stdout, out.stdout + out.stderr
