@@ -705,15 +705,17 @@ __global__ void __launch_bounds__(PT) k_propose_global(PropCtx C, const int32_t 
 
 // ---------------------------------------------------------------- node tiers
 // warp tier: small neighbourhood bound and little traversal work; hub
-// tier: traversals large enough to keep a 1024-thread CTA busy
+// tier: traversals (pin visits or incidence entries) large enough to keep a
+// 1024-thread CTA busy
 // dense tier (level of at most DENSE_N nodes): neighbourhood bound above
 // dense_bound; the others use hashed tables
 constexpr long long WARP_VISITS = 4096, HUB_VISITS = 262144;
-__global__ void k_tiers(const int32_t *bound, const long long *vis, int32_t n, uint32_t warp_limit,
-                        int32_t dense_bound, int32_t *lW, int32_t *lB, int32_t *lH, int32_t *lD, int32_t *lDH,
-                        int32_t *cnt) {
+constexpr int32_t HUB_INCIDENCE = 4096;   // incidence entries: chunks of a 512-thread walk
+__global__ void k_tiers(const int32_t *bound, const long long *vis, const int32_t *ioff, int32_t n,
+                        uint32_t warp_limit, int32_t dense_bound, int32_t *lW, int32_t *lB, int32_t *lH, int32_t *lD,
+                        int32_t *lDH, int32_t *cnt) {
     GRID_STRIDE(v, (int64_t)n) {
-        const bool hub = vis[v] > HUB_VISITS;
+        const bool hub = vis[v] > HUB_VISITS || ioff[v + 1] - ioff[v] > HUB_INCIDENCE;
         if ((uint32_t)bound[v] <= warp_limit && vis[v] <= WARP_VISITS) lW[atomicAdd(&cnt[0], 1)] = (int32_t)v;
         else if (bound[v] > dense_bound) {
             if (hub) lDH[atomicAdd(&cnt[7], 1)] = (int32_t)v;
@@ -728,6 +730,8 @@ struct CoarsenWs {
     int32_t cn, ce, pi;
     uint64_t *q;
     int32_t *canon;   // destination-list groups of the current level's hyperedges
+    cudaStream_t side[3] = {nullptr, nullptr, nullptr};   // side streams of the proposal tiers
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     int32_t *cand;
     uint64_t *cscore;
     int32_t *lW, *lB, *lC, *lG, *lH, *lD, *lDH, *cnt;   // cnt: 0 W 1 B 2 C 3 G 4 errors 5 H 6 D 7 DH
@@ -757,36 +761,45 @@ static void run_proposal(const PropCtx &C, Level &L, const Params &P, CoarsenWs 
     // dense tables only on small levels, for neighbourhoods too large for the first hashed table
     const int32_t dense_bound = (C.n <= DENSE_N && dbg == 0) ? (int32_t)(capB / 2) : 0x7fffffff;
     HPC(cudaMemsetAsync(W.cnt, 0, 8 * sizeof(int32_t), s));
-    k_tiers<<<grid_of(C.n, 256), 256, 0, s>>>(L.nbnd, W.vis, C.n, wcap / 2, dense_bound, W.lW, W.lB, W.lH, W.lD,
-                                              W.lDH, W.cnt);
+    k_tiers<<<grid_of(C.n, 256), 256, 0, s>>>(L.nbnd, W.vis, L.ioff, C.n, wcap / 2, dense_bound, W.lW, W.lB, W.lH,
+                                              W.lD, W.lDH, W.cnt);
     HP_LAUNCH_CHECK();
+    // the tiers take disjoint node lists, so they run side by side: the warp
+    // tier, the dense tier and the hub tier each on a side stream, tier B on
+    // the main one; tier C (overflows of B and the hubs) waits for the hubs,
+    // and the global tier (whose error list reuses the warp list) for all
+    cudaStream_t sw = W.side[0], sd = W.side[1], sh = W.side[2];
+    HPC(cudaEventRecord(W.ev[0], s));
+    for (cudaStream_t x : {sw, sd, sh}) HPC(cudaStreamWaitEvent(x, W.ev[0], 0));
     {
         size_t sm = (size_t)wcap * 16 * (WP_T / 32);
         int occ = prepare_kernel((const void *)k_propose_warp<PIMAX>, WP_T, sm);
         int grid = (int)std::min<int64_t>(cdiv(C.n, WP_T / 32), (int64_t)sms * occ);
-        k_propose_warp<PIMAX><<<std::max(grid, 1), WP_T, sm, s>>>(C, W.lW, W.cnt + 0, wcap);
+        k_propose_warp<PIMAX><<<std::max(grid, 1), WP_T, sm, sw>>>(C, W.lW, W.cnt + 0, wcap);
         HP_LAUNCH_CHECK();
     }
     if (dense_bound != 0x7fffffff) {
         size_t sm = (size_t)C.n * 12;
         int occ = prepare_kernel((const void *)k_propose_dense<PIMAX, PT>, PT, sm);
-        k_propose_dense<PIMAX, PT><<<std::max(1, std::min<int>(C.n, sms * occ)), PT, sm, s>>>(C, W.lD, W.cnt + 6);
+        k_propose_dense<PIMAX, PT><<<std::max(1, std::min<int>(C.n, sms * occ)), PT, sm, sd>>>(C, W.lD, W.cnt + 6);
         HP_LAUNCH_CHECK();
         prepare_kernel((const void *)k_propose_dense<PIMAX, 1024>, 1024, sm);
-        k_propose_dense<PIMAX, 1024><<<sms, 1024, sm, s>>>(C, W.lDH, W.cnt + 7);
+        k_propose_dense<PIMAX, 1024><<<sms, 1024, sm, sd>>>(C, W.lDH, W.cnt + 7);
         HP_LAUNCH_CHECK();
     }
     auto smem_of = [](uint32_t cap) { return (size_t)cap * 16 + (size_t)(cap * 3 / 4) * 4; };
     {
         size_t sm = smem_of(capB);
+        prepare_kernel((const void *)k_propose_smem<PIMAX, 1024>, 1024, sm);
+        k_propose_smem<PIMAX, 1024><<<sms, 1024, sm, sh>>>(C, W.lH, W.cnt + 5, capB, capB * 3 / 4, W.lC, W.cnt + 2);
+        HP_LAUNCH_CHECK();
         int occ = prepare_kernel((const void *)k_propose_smem<PIMAX, 512>, 512, sm);
         k_propose_smem<PIMAX, 512><<<std::max(1, std::min<int>(C.n, sms * occ)), 512, sm, s>>>(
             C, W.lB, W.cnt + 1, capB, capB * 3 / 4, W.lC, W.cnt + 2);
         HP_LAUNCH_CHECK();
-        prepare_kernel((const void *)k_propose_smem<PIMAX, 1024>, 1024, sm);
-        k_propose_smem<PIMAX, 1024><<<sms, 1024, sm, s>>>(C, W.lH, W.cnt + 5, capB, capB * 3 / 4, W.lC, W.cnt + 2);
-        HP_LAUNCH_CHECK();
     }
+    HPC(cudaEventRecord(W.ev[3], sh));
+    HPC(cudaStreamWaitEvent(s, W.ev[3], 0));
     {
         // nodes whose neighbourhood outgrew the first table (the bound can be far above the truth)
         size_t sm = smem_of(capC);
@@ -795,6 +808,10 @@ static void run_proposal(const PropCtx &C, Level &L, const Params &P, CoarsenWs 
             C, W.lC, W.cnt + 2, capC, capC * 3 / 4, W.lG, W.cnt + 3);
         HP_LAUNCH_CHECK();
     }
+    HPC(cudaEventRecord(W.ev[1], sw));
+    HPC(cudaEventRecord(W.ev[2], sd));
+    HPC(cudaStreamWaitEvent(s, W.ev[1], 0));
+    HPC(cudaStreamWaitEvent(s, W.ev[2], 0));
     k_propose_global<PIMAX><<<W.gnb, PT, 0, s>>>(C, W.lG, W.cnt + 3, W.gcap, W.gkeys, W.geta, W.ginter, W.gslots,
                                                   W.lW, W.cnt + 4);
     HP_LAUNCH_CHECK();
@@ -995,6 +1012,8 @@ __global__ void k_flag_if_nonzero(const int32_t *x, uint32_t *err) {
 CoarsenWs *coarsen_workspace(int32_t n, int32_t e, const Params &P, Arena &A) {
     cudaStream_t s = A.stream();
     CoarsenWs *W = new CoarsenWs();
+    for (cudaStream_t &x : W->side) HPC(cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking));
+    for (cudaEvent_t &x : W->ev) HPC(cudaEventCreateWithFlags(&x, cudaEventDisableTiming));
     const int32_t pi = P.o.pi;
     W->cn = n;
     W->ce = e;
@@ -1043,6 +1062,10 @@ CoarsenWs *coarsen_workspace(int32_t n, int32_t e, const Params &P, Arena &A) {
 
 void coarsen_workspace_free(CoarsenWs *W, Arena &A) {
     if (!W) return;
+    for (cudaStream_t x : W->side)
+        if (x) cudaStreamDestroy(x);
+    for (cudaEvent_t x : W->ev)
+        if (x) cudaEventDestroy(x);
     for (void *p : {(void *)W->nsum, (void *)W->vis, (void *)W->q, (void *)W->canon, (void *)W->cand, (void *)W->cscore, (void *)W->lW, (void *)W->lB, (void *)W->lC,
                     (void *)W->lG, (void *)W->lH, (void *)W->lD, (void *)W->lDH, (void *)W->cnt, (void *)W->gkeys, (void *)W->geta, (void *)W->ginter, (void *)W->gslots,
                     (void *)W->flag, (void *)W->pos, (void *)W->ikeys, (void *)W->iids, (void *)W->target,

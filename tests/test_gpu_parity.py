@@ -177,3 +177,34 @@ def test_powerlaw_instances_in_a_fresh_process(gpu):
         "print('ok')\n" % root)
     out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=600)
     assert out.returncode == 0 and "ok" in out.stdout, out.stdout + out.stderr
+
+
+def grouped_hypergraph(seed):
+    """Hyperedges in groups that share one destination list of 33..120 pins
+    but differ in their 1..3 sources and their weights: the proposal walks
+    such a list once per warp group, carrying the group's summed q(e)."""
+    rng = np.random.default_rng(seed)
+    n = 3000
+    rows, src, w = [], [], []
+    for t in range(60):
+        lo = int(rng.integers(0, n - 400))
+        dst = np.sort(rng.choice(np.arange(lo, lo + 400), size=int(rng.integers(33, 121)), replace=False))
+        others = np.setdiff1d(np.arange(n), dst)
+        for _ in range(int(rng.integers(3, 12))):
+            k = int(rng.integers(1, 4))
+            s = np.sort(rng.choice(others, size=k, replace=False))
+            rows.append(np.concatenate([s, dst]).astype(np.int32))
+            src.append(k)
+            w.append(int(rng.integers(1, 5001)))
+    sizes = [len(r) for r in rows]
+    off = np.zeros(len(rows) + 1, dtype=np.int32)
+    off[1:] = np.cumsum(sizes)
+    return inputs.Hypergraph(n, off, np.concatenate(rows).astype(np.int32), np.asarray(src, dtype=np.int32),
+                             np.asarray(w, dtype=np.int32), f"grouped_{seed}")
+
+
+@pytest.mark.parametrize("seed,kind", [(1, 0), (2, 0), (3, 1)])
+def test_equal_destination_groups_parity(seed, kind):
+    g = grouped_hypergraph(seed)
+    assert g.num_pins >= 16 * g.num_hedges   # the level walks its destination groups
+    check_same(g, 300, 2000, seed=seed, count_kind=kind)
