@@ -1780,6 +1780,9 @@ struct LevelWs {
     int32_t *cflag, *cpos, *cut, *cut_off;   // cut incident hyperedges per node
     int32_t *tiny, n_tiny;                   // hyperedges of 2..8 pins
     int32_t *mid, n_mid;                     // hyperedges of 9..small_max pins
+    int32_t parts_used;                      // parts holding a node at the level's start
+    cudaStream_t side = nullptr;             // side stream of the hub gains
+    cudaEvent_t ev[2] = {nullptr, nullptr};
     int32_t *touched, *ttouched;             // hyperedges with a moved pin (more than / at most 8 pins)
     Moves M, S;
     uint64_t *keys, *sk;
@@ -1810,6 +1813,8 @@ LevelWs *refine_workspace(int32_t n, int64_t np, int32_t e, int32_t nparts, int3
                           Arena &A) {
     cudaStream_t s = A.stream();
     LevelWs *W = new LevelWs();
+    HPC(cudaStreamCreateWithFlags(&W->side, cudaStreamNonBlocking));
+    for (cudaEvent_t &x : W->ev) HPC(cudaEventCreateWithFlags(&x, cudaEventDisableTiming));
     W->cn = n;
     W->cnp = np;
     W->ce = e;
@@ -1914,6 +1919,9 @@ LevelWs *refine_workspace(int32_t n, int64_t np, int32_t e, int32_t nparts, int3
 
 void refine_workspace_free(LevelWs *W, Arena &A) {
     if (!W) return;
+    if (W->side) cudaStreamDestroy(W->side);
+    for (cudaEvent_t x : W->ev)
+        if (x) cudaEventDestroy(x);
     for (void *p : std::initializer_list<void *>{
              W->act, W->big, W->wns, W->singin, W->PL.p, W->PL.cnt, W->PL.cin, W->PL.lam, W->R.cnt, W->R.linked,
              W->R.D0, W->R.psize, W->R.saving, W->R.pc, W->R.pred, W->R.succ, W->R.chain, W->R.mvpos, W->R.cgain,
@@ -1969,6 +1977,7 @@ static void level_prepare(const Level &L, const int32_t *w, const int32_t *rho, 
     W.n_big = hc[1];
     W.n_tiny = hc[3];
     W.n_mid = hc[4];
+    W.parts_used = hc[5];
     // pins lists of the level hold at most min(small_max, parts in use) entries
     W.pcap = pow2_at_least(2 * (int64_t)std::max<int32_t>(2, std::min<int32_t>(W.small_max, hc[5])));
     if (W.n_big > 0 && !W.ptab) throw Error(HP_ERR_INTERNAL, "large hyperedge buffers missing");
@@ -2020,6 +2029,20 @@ static int32_t rep_run(const Level &L, const int32_t *w, const Params &P, int32_
                                                  W.cw, cnt + C_CW);
     HP_LAUNCH_CHECK();
     GainArgs G{L.off, W.cut_off, W.cut, w, rho, L.size, R.psize, R.saving, W.wns, W.PL, P.omega, second_half, W.M};
+    uint32_t gcap_smem = 2048;
+    if (P.o.debug_table_cap > 0) gcap_smem = (uint32_t)P.o.debug_table_cap;
+    const size_t gsm = (size_t)gcap_smem * 12 + (size_t)(gcap_smem * 3 / 4) * 4;
+    {
+        // hub nodes on the side stream, beside the warp and CTA tiers (disjoint
+        // node lists; all append to the same move and overflow lists by atomics)
+        HPC(cudaEventRecord(W.ev[0], s));
+        HPC(cudaStreamWaitEvent(W.side, W.ev[0], 0));
+        const int occ_h = prepare_kernel((const void *)k_gains_smem<1024>, 1024, gsm);
+        k_gains_smem<1024><<<num_sms() * std::max(occ_h, 1), 1024, gsm, W.side>>>(G, W.hubs, cnt + C_HUB, gcap_smem,
+                                                                                 W.ovf, cnt + C_OVF);
+        HP_LAUNCH_CHECK();
+        HPC(cudaEventRecord(W.ev[1], W.side));
+    }
     {
         const uint32_t wlimit = P.o.debug_table_cap > 0 ? std::min<uint32_t>(GW_SLOTS * 3 / 4, P.o.debug_table_cap / 2)
                                                         : GW_SLOTS * 3 / 4;
@@ -2029,17 +2052,11 @@ static int32_t rep_run(const Level &L, const int32_t *w, const Params &P, int32_
         HP_LAUNCH_CHECK();
     }
     {
-        uint32_t cap = 2048;
-        if (P.o.debug_table_cap > 0) cap = (uint32_t)P.o.debug_table_cap;
-        size_t sm = (size_t)cap * 12 + (size_t)(cap * 3 / 4) * 4;
-        int occ = prepare_kernel((const void *)k_gains_smem<GN_T>, GN_T, sm);
+        int occ = prepare_kernel((const void *)k_gains_smem<GN_T>, GN_T, gsm);
         int grid = std::max(1, std::min<int>(n, num_sms() * occ));
-        k_gains_smem<GN_T><<<grid, GN_T, sm, s>>>(G, W.cl, cnt + C_CAND, cap, W.ovf, cnt + C_OVF);
+        k_gains_smem<GN_T><<<grid, GN_T, gsm, s>>>(G, W.cl, cnt + C_CAND, gcap_smem, W.ovf, cnt + C_OVF);
         HP_LAUNCH_CHECK();
-        const int occ_h = prepare_kernel((const void *)k_gains_smem<1024>, 1024, sm);
-        k_gains_smem<1024><<<num_sms() * std::max(occ_h, 1), 1024, sm, s>>>(G, W.hubs, cnt + C_HUB, cap, W.ovf,
-                                                                          cnt + C_OVF);
-        HP_LAUNCH_CHECK();
+        HPC(cudaStreamWaitEvent(s, W.ev[1], 0));
         k_gains_global<<<W.gnb, GN_T, 0, s>>>(G, W.ovf, cnt + C_OVF, W.gcap, W.gk, W.gc, W.cl, cnt + C_BAD);
         HP_LAUNCH_CHECK();
     }
@@ -2079,7 +2096,12 @@ static int32_t rep_run(const Level &L, const int32_t *w, const Params &P, int32_
     SeqCtx Q{W.S.node, R.pred, R.succ, W.S.gain, R.chain, W.pos, W.clen, R.cgain, err_dev};
     ValCtx V{W.seqmove, L.size, W.singin, R.dDs, R.dDd, R.D0, R.gseq, W.S, R.psize, W.vkey, W.vidx, W.vsz, W.vdd,
              R.viol, P.omega, P.delta, W.gsz, W.gdd, W.esz, W.edd, W.vhead};
-    const bool small = m <= SMALLM, one_cta = m <= SEQ_MAX;
+    // one CTA sequences the moves unless the chaining window scans would be
+    // long: every free end scans up to min(window, moves per part) moves of
+    // its destination, each round (few parts in use make that quadratic)
+    const int64_t per_part = cdiv(m, std::max<int32_t>(W.parts_used, 1));
+    const int64_t scan_work = (int64_t)m * std::min<int64_t>(P.o.chain_window, per_part);
+    const bool small = m <= SMALLM, one_cta = m <= SEQ_MAX && scan_work <= (int64_t(1) << 20);
     if (one_cta) {
         SmallSeqArgs SA{W.M, W.S, W.keys, W.hkeys, W.idx, W.heads, W.sk, W.sv, R.pc, W.first, W.lens, W.starts, W.cstart,
                         W.seqmove, R.mvpos, cnt, C, Q, nparts, P.o.chain_rounds, packed, gb, nb, sb, cgb, gbound,
