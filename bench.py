@@ -28,6 +28,10 @@ import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
+# more hardware work queues than the default 8: the library runs side streams
+# and the batch workload one stream per instance in flight (read at context
+# creation, so it is set before anything touches CUDA)
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
 
 WORKLOAD = "layered_snn_262k"
 WORKLOAD_DESC = ("layered SNN hypergraph: 8 layers x 32x32 grid x 32 channels = 262,144 nodes; each neuron of "
