@@ -48,6 +48,17 @@ def test_host_only_calls(lib):
     assert hp.hp_last_error() == ""
 
 
+def test_argument_checks_before_any_device_work(lib):
+    # these return before touching CUDA, so they run without a GPU
+    assert lib.hp_partition_batch(None, 0, None, 4, None, None, None) == hp.HP_OK
+    assert lib.hp_partition_batch(None, 1, None, 4, None, None, None) == hp.HP_ERR_INVALID_ARG
+    one = (hp.hp_instance * 1)()
+    assert lib.hp_partition_batch(one, 1, None, 0, None, None, None) == hp.HP_ERR_INVALID_ARG
+    assert lib.hp_partition_batch(one, 1, None, 65, None, None, None) == hp.HP_ERR_INVALID_ARG
+    assert lib.hp_connectivity_noalloc(None, None, -1, None, None, 0, 0, None, None, None) == hp.HP_ERR_INVALID_ARG
+    assert hp.hp_last_error() == "invalid argument"
+
+
 def test_struct_layout_matches_header(lib):
     assert ctypes.sizeof(hp.hp_options) == 8 * 4
     assert ctypes.sizeof(hp.hp_stats) == 8 + 8 + 6 * 4 + 8 + 8 + 3 * 8 + 3 * 8 + 8

@@ -561,3 +561,67 @@ def test_error_statuses():
     empty = inputs.Hypergraph(0, np.array([0], np.int32), np.zeros(0, np.int32))
     r = oracle.partition(empty, 4, 3)
     assert r.status == oracle.OK and r.stats["num_parts"] == 0
+
+
+def all_set_partitions(n):
+    """Every set partition of range(n) as a label array (restricted growth
+    strings: label i is at most 1 + the largest label before it), built
+    column by column: Bell(n) rows."""
+    rows = np.zeros((1, 1), dtype=np.int8)
+    for _ in range(1, n):
+        mx = rows.max(axis=1).astype(np.int64)
+        cnt = mx + 2
+        rep = np.repeat(rows, cnt, axis=0)
+        nxt = np.arange(cnt.sum()) - np.repeat(np.cumsum(cnt) - cnt, cnt)
+        rows = np.concatenate([rep, nxt[:, None].astype(np.int8)], axis=1)
+    return rows
+
+
+def brute_force_optimum(g, omega, delta):
+    """Minimum connectivity (Eq. 1) over every feasible set partition, by
+    exhaustive enumeration (vectorised over the partitions)."""
+    n = g.num_nodes
+    lab = all_set_partitions(n).astype(np.int64)
+    w = np.ones(g.num_hedges, dtype=np.int64) if g.weights is None else g.weights.astype(np.int64)
+    conn = np.zeros(lab.shape[0], dtype=np.int64)
+    inmask = np.zeros(n, dtype=np.int64)
+    for e, (src, dst) in enumerate(g.edges()):
+        pins = list(src) + list(dst)
+        s = np.sort(lab[:, pins], axis=1)
+        lam = 1 + (np.diff(s, axis=1) != 0).sum(axis=1)
+        conn += w[e] * (lam - 1)
+        for v in dst:
+            inmask[v] |= np.int64(1) << e
+    ok = np.ones(lab.shape[0], dtype=bool)
+    for p in range(n):
+        members = lab == p
+        ok &= members.sum(axis=1) <= omega
+        m = np.bitwise_or.reduce(np.where(members, inmask[None, :], 0), axis=1)
+        bits = np.zeros_like(m)
+        for b in range(g.num_hedges):
+            bits += (m >> b) & 1
+        ok &= bits <= delta
+    return int(conn[ok].min()), int(ok.sum())
+
+
+def test_set_partition_enumeration_counts():
+    # Bell numbers B(1..8) and B(12)
+    assert [all_set_partitions(n).shape[0] for n in range(1, 9)] == [1, 2, 5, 15, 52, 203, 877, 4140]
+    assert all_set_partitions(12).shape[0] == 4213597
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_end_to_end_vs_brute_force_optimum_12_nodes(seed):
+    """12 nodes: the oracle's result is feasible, its connectivity is the
+    one recomputed by set comprehension, and no feasible partition of the
+    4,213,597 is better than the exhaustive optimum it is compared to."""
+    n = 12
+    g = inputs.random_hypergraph(n, 9, 5, seed=300 + seed, multi_src=seed == 1, weights=seed == 2)
+    omega, delta = 4, 5
+    r = oracle.partition(g, omega, delta, seed)
+    assert r.status == oracle.OK
+    assert feasible(g, r.part, omega, delta)
+    assert r.stats["connectivity"] == conn_bf(g, r.part)
+    opt, nfeas = brute_force_optimum(g, omega, delta)
+    assert nfeas > 0
+    assert opt <= r.stats["connectivity"] <= conn_bf(g, np.arange(n))
