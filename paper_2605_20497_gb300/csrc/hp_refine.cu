@@ -744,15 +744,17 @@ struct RepArrays {
 __device__ __forceinline__ int64_t rep_zero_span(const RepArrays &R) {
     return max(max((int64_t)R.n, (int64_t)R.nparts + 1), max((int64_t)C_N, (int64_t)R.rounds + 1));
 }
-__global__ void k_rep_zero(RepArrays R) {
+// keep: the partition is the one of the previous repetition (it applied
+// nothing), so D(p), |p| and saving(v) are still valid
+__global__ void k_rep_zero(RepArrays R, int keep) {
     GRID_STRIDE(i, rep_zero_span(R)) {
-        if (i < R.nparts) {
+        if (i < R.nparts && !keep) {
             R.D0[i] = 0;
             R.psize[i] = 0;
         }
         if (i <= R.nparts) R.pc[i] = 0;
         if (i < R.n) {
-            R.saving[i] = 0;
+            if (!keep) R.saving[i] = 0;
             R.pred[i] = -1;
             R.succ[i] = -1;
             R.chain[i] = -1;
@@ -1984,47 +1986,52 @@ static void level_prepare(const Level &L, const int32_t *w, const int32_t *rho, 
 }
 
 // One repetition; returns the number of moves applied.
+// reuse: rho is unchanged since the previous repetition of this level (which
+// applied nothing), so its pins lists, D(p), |p|, saving(v) and cut lists,
+// all functions of rho, are reused instead of rebuilt
 static int32_t rep_run(const Level &L, const int32_t *w, const Params &P, int32_t *rho, int second_half, LevelWs &W,
-                       Arena &A, uint32_t *err_dev, const RepDebug *dbg) {
+                       Arena &A, uint32_t *err_dev, const RepDebug *dbg, bool reuse = false) {
     cudaStream_t s = A.stream();
     const int32_t n = L.n, nparts = W.nparts;
     RepArrays &R = W.R;
     int32_t *cnt = R.cnt;
     const int64_t zspan = std::max<int64_t>(std::max<int64_t>(n, (int64_t)nparts + 1),
                                             std::max<int64_t>((int64_t)C_N, (int64_t)P.o.chain_rounds + 1));
-    k_rep_zero<<<grid_of(zspan, 256), 256, 0, s>>>(R);
+    k_rep_zero<<<grid_of(zspan, 256), 256, 0, s>>>(R, reuse ? 1 : 0);
     HP_LAUNCH_CHECK();
-    k_rep_nodes<<<grid_of(n, 256), 256, 0, s>>>(rho, L.size, W.singin, n, R.psize, R.D0);
-    HP_LAUNCH_CHECK();
-    // pins(p,e), pins_in(p,e), D(p), saving(v)
-    if (W.n_mid > 0) {
-        const int per = 5 * (int)W.pcap + 1;
-        size_t sm = (size_t)per * 4 * (PLW_T / 32);
-        int occ = prepare_kernel((const void *)k_plist_small, PLW_T, sm);
-        int grid = (int)std::min<int64_t>(cdiv(W.n_mid, PLW_T / 32), (int64_t)num_sms() * occ);
-        k_plist_small<<<std::max(grid, 1), PLW_T, sm, s>>>(L.off, L.pin, L.nsrc, w, rho, W.n_mid, W.mid, W.small_max,
-                                                           W.pcap, W.PL, R.D0, R.saving, 0);
+    if (!reuse) {
+        k_rep_nodes<<<grid_of(n, 256), 256, 0, s>>>(rho, L.size, W.singin, n, R.psize, R.D0);
+        HP_LAUNCH_CHECK();
+        // pins(p,e), pins_in(p,e), D(p), saving(v)
+        if (W.n_mid > 0) {
+            const int per = 5 * (int)W.pcap + 1;
+            size_t sm = (size_t)per * 4 * (PLW_T / 32);
+            int occ = prepare_kernel((const void *)k_plist_small, PLW_T, sm);
+            int grid = (int)std::min<int64_t>(cdiv(W.n_mid, PLW_T / 32), (int64_t)num_sms() * occ);
+            k_plist_small<<<std::max(grid, 1), PLW_T, sm, s>>>(L.off, L.pin, L.nsrc, w, rho, W.n_mid, W.mid, W.small_max,
+                                                               W.pcap, W.PL, R.D0, R.saving, 0);
+            HP_LAUNCH_CHECK();
+        }
+        if (W.n_tiny > 0) {
+            k_plist_tiny<<<grid_of(W.n_tiny, 128), 128, 0, s>>>(L.off, L.pin, L.nsrc, w, rho, W.tiny, W.n_tiny, W.PL, R.D0,
+                                                                R.saving);
+            HP_LAUNCH_CHECK();
+        }
+        if (W.n_big > 0) {
+            k_plist_big<<<W.pnb, 256, 0, s>>>(L.off, L.pin, L.nsrc, w, rho, W.big, W.n_big, W.bcap, W.ptab, W.cmax_e,
+                                               W.PL, R.D0, R.saving);
+            HP_LAUNCH_CHECK();
+        }
+        // moves in isolation (Eq. 13)
+        if (L.np > 0) {
+            k_cut_flags<<<grid_of(L.np, 256), 256, 0, s>>>(L.off, L.inc, W.PL.lam, L.np, W.cflag);
+            HP_LAUNCH_CHECK();
+        }
+        scan_excl(W.cflag, W.cpos, L.np, W.cpos + L.np, A);
+        k_cut_fill<<<grid_of(std::max<int64_t>(L.np, (int64_t)n + 1), 256), 256, 0, s>>>(L.inc, W.cflag, W.cpos, L.ioff,
+                                                                                           L.np, n, W.cut, W.cut_off);
         HP_LAUNCH_CHECK();
     }
-    if (W.n_tiny > 0) {
-        k_plist_tiny<<<grid_of(W.n_tiny, 128), 128, 0, s>>>(L.off, L.pin, L.nsrc, w, rho, W.tiny, W.n_tiny, W.PL, R.D0,
-                                                            R.saving);
-        HP_LAUNCH_CHECK();
-    }
-    if (W.n_big > 0) {
-        k_plist_big<<<W.pnb, 256, 0, s>>>(L.off, L.pin, L.nsrc, w, rho, W.big, W.n_big, W.bcap, W.ptab, W.cmax_e,
-                                           W.PL, R.D0, R.saving);
-        HP_LAUNCH_CHECK();
-    }
-    // moves in isolation (Eq. 13)
-    if (L.np > 0) {
-        k_cut_flags<<<grid_of(L.np, 256), 256, 0, s>>>(L.off, L.inc, W.PL.lam, L.np, W.cflag);
-        HP_LAUNCH_CHECK();
-    }
-    scan_excl(W.cflag, W.cpos, L.np, W.cpos + L.np, A);
-    k_cut_fill<<<grid_of(std::max<int64_t>(L.np, (int64_t)n + 1), 256), 256, 0, s>>>(L.inc, W.cflag, W.cpos, L.ioff,
-                                                                                       L.np, n, W.cut, W.cut_off);
-    HP_LAUNCH_CHECK();
     k_candidates<<<grid_of(n, 256), 256, 0, s>>>(R.saving, W.cut_off, n, W.cl, cnt + C_CAND, W.hubs, cnt + C_HUB,
                                                  W.cw, cnt + C_CW);
     HP_LAUNCH_CHECK();
@@ -2266,8 +2273,10 @@ RefineOut refine_level(const Level &L, const int32_t *w, const Params &P, int32_
     if (L.n == 0 || P.o.theta == 0) return out;
     level_prepare(L, w, rho, *W, A);
     const int32_t half = P.o.theta / 2;
+    bool same_rho = false;   // the previous repetition applied nothing
     for (int32_t rep = 0; rep < P.o.theta; rep++) {
-        const int32_t k = rep_run(L, w, P, rho, rep >= half, *W, A, err_dev, nullptr);
+        const int32_t k = rep_run(L, w, P, rho, rep >= half, *W, A, err_dev, nullptr, same_rho);
+        same_rho = k == 0;
         out.reps++;
         out.moves += k;
         if (k == 0) {
