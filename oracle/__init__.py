@@ -22,8 +22,11 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 OK, ERR_INVALID_ARG, ERR_BAD_CSR, ERR_INFEASIBLE = 0, 1, 2, 3
 COUNT_INBOUND, COUNT_INCIDENT = 0, 1
 # layout of the option vector (see hp_oracle.c)
-OPT_KEYS = ("pi", "theta", "chain_window", "chain_rounds", "noise_permille", "count_kind", "max_levels")
-DEFAULTS = dict(pi=4, theta=16, chain_window=256, chain_rounds=16, noise_permille=100, count_kind=0, max_levels=256)
+OPT_KEYS = ("pi", "theta", "chain_window", "chain_rounds", "noise_permille", "count_kind", "max_levels",
+            "learned_k")
+DEFAULTS = dict(pi=4, theta=16, chain_window=256, chain_rounds=16, noise_permille=100, count_kind=0, max_levels=256,
+                learned_k=0)
+MODEL_LEN = 64 * 16 + 64 * 64 + 64 * 3 + 3   # layout of the model vector (see hp_oracle.c)
 STAT_KEYS = ("connectivity", "cut_net", "num_parts", "max_part_size", "max_part_distinct",
              "violations", "levels", "moves_applied")
 TRACE_KEYS = ("n", "pins", "pairs", "iso_pairs", "conn", "moves", "reps", "parts")
@@ -55,6 +58,14 @@ I32, I64, U64 = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64
 def _declare(L):
     L.or_partition.argtypes = [I32, I32, P, P, P, P, I32, I32, U64, P, P, P, P]
     L.or_partition.restype = ctypes.c_int
+    L.or_partition_ml.argtypes = [I32, I32, P, P, P, P, I32, I32, U64, P, P, P, P, P]
+    L.or_partition_ml.restype = ctypes.c_int
+    L.or_mlp_scores.argtypes = [P, I64, P, P]
+    L.or_mlp_scores.restype = ctypes.c_int
+    L.or_learned_level.argtypes = [I32, I32, P, P, P, P, I32, I32, I32, I32, P, P, I32, P, P, P, P, P]
+    L.or_learned_level.restype = ctypes.c_int
+    L.or_log_code.argtypes = [U64]
+    L.or_log_code.restype = I32
     L.or_node_histogram.argtypes = [I32, I32, P, P, P, P, I32, I32, P, P, P]
     L.or_node_histogram.restype = I32
     L.or_pair_noise.argtypes = [U64, I32, I32, I32, U64]
@@ -97,21 +108,33 @@ class Result:
     trace: list
 
 
-def partition(g, omega: int, delta: int, seed: int = 0, trace: bool = False, **opts) -> Result:
-    """Full multilevel partition of hypergraph ``g`` (see paper Sec. III)."""
+def model_vector(m) -> np.ndarray:
+    """The oracle's int32 vector of a MergeModel: w1, w2, w3, b1, b2, b3,
+    shift1, shift2."""
+    v = np.concatenate([np.asarray(m.w1, np.int32).ravel(), np.asarray(m.w2, np.int32).ravel(),
+                        np.asarray(m.w3, np.int32).ravel(), np.asarray(m.b1, np.int32).ravel(),
+                        np.asarray(m.b2, np.int32).ravel(), np.array([m.b3, m.shift1, m.shift2], np.int32)])
+    assert v.size == MODEL_LEN
+    return np.ascontiguousarray(v, dtype=np.int32)
+
+
+def partition(g, omega: int, delta: int, seed: int = 0, trace: bool = False, model=None, **opts) -> Result:
+    """Full multilevel partition of hypergraph ``g`` (see paper Sec. III).
+    ``model``: a MergeModel, used when the option ``learned_k`` is set."""
     unknown = set(opts) - set(DEFAULTS)
     if unknown:
         raise TypeError(f"unknown oracle option(s): {sorted(unknown)}")
     o = dict(DEFAULTS)
     o.update(opts)
     optv = np.array([o[k] for k in OPT_KEYS] + [0], dtype=np.int32)
+    mv = None if model is None else model_vector(model)
     off, pins = _i32(g.offsets), _i32(g.pins)
     nsrc, w = _i32(g.src_counts), _i32(g.weights)
     part = np.zeros(max(g.num_nodes, 1), dtype=np.int32)
     stats = np.zeros(16, dtype=np.int64)
     tr = np.zeros(8 * (o["max_levels"] + 1), dtype=np.int64) if trace else None
-    st = lib().or_partition(g.num_nodes, g.num_hedges, _p(off), _p(pins), _p(nsrc), _p(w), omega, delta,
-                            ctypes.c_uint64(seed & (2**64 - 1)), _p(optv), _p(part), _p(stats), _p(tr))
+    st = lib().or_partition_ml(g.num_nodes, g.num_hedges, _p(off), _p(pins), _p(nsrc), _p(w), omega, delta,
+                               ctypes.c_uint64(seed & (2**64 - 1)), _p(optv), _p(mv), _p(part), _p(stats), _p(tr))
     sd = {k: int(stats[i]) for i, k in enumerate(STAT_KEYS)}
     levels = []
     if tr is not None and st == OK:
@@ -226,3 +249,37 @@ def refine_rep(g, size, rho, nparts, second_half, omega, delta, window=256, roun
                             _p(_i32(g.src_counts)), _p(_i32(g.weights)), _p(_i32(size)), _p(rho), nparts,
                             int(second_half), omega, delta, window, rounds)
     return int(k), rho
+
+
+# ---- learned merge priority ----
+def mlp_scores(feat, model):
+    """Scores of the integer MLP on feature rows feat[count, 16] (uint8)."""
+    f = np.ascontiguousarray(feat, dtype=np.uint8).reshape(-1, 16)
+    out = np.zeros(max(len(f), 1), dtype=np.int64)
+    st = lib().or_mlp_scores(_p(f), len(f), _p(model_vector(model)), _p(out))
+    if st != OK:
+        raise ValueError("invalid model")
+    return out[: len(f)]
+
+
+def learned_level(g, size, omega, delta, level, candK, csK, pi, model):
+    """Learned priority on one level graph: (features [n*K, 16], rank of the
+    node in its candidate's list or -1 [n*K], C(n) [n*pi], eta [n*pi])."""
+    n = g.num_nodes
+    candK = np.ascontiguousarray(candK, dtype=np.int32)
+    csK = np.ascontiguousarray(csK, dtype=np.uint64)
+    K = candK.size // max(n, 1)
+    feat = np.zeros((max(n * K, 1), 16), dtype=np.uint8)
+    rank = np.zeros(max(n * K, 1), dtype=np.int32)
+    cand = np.zeros(max(n * pi, 1), dtype=np.int32)
+    cs = np.zeros(max(n * pi, 1), dtype=np.uint64)
+    st = lib().or_learned_level(n, g.num_hedges, _p(_i32(g.offsets)), _p(_i32(g.pins)), _p(_i32(g.src_counts)),
+                                _p(_i32(size)), omega, delta, level, K, _p(candK), _p(csK), pi,
+                                _p(model_vector(model)), _p(feat), _p(rank), _p(cand), _p(cs))
+    if st != OK:
+        raise ValueError(f"or_learned_level: status {st}")
+    return feat[: n * K], rank[: n * K], cand[: n * pi], cs[: n * pi]
+
+
+def log_code(x: int) -> int:
+    return int(lib().or_log_code(ctypes.c_uint64(x)))

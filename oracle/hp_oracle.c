@@ -52,6 +52,14 @@
  *     (the next repetition would recompute the same moves).
  *   - count_kind = incident: every pin counts as a destination for the
  *     constraint (src sets emptied); the objective is unchanged.
+ *
+ * Learned merge priority (option learned_k; a growth of Sec. V-C that the
+ * paper does not have): the top-K candidate lists by (eta, id), pairs kept
+ * only when mutual, C(n) = top Pi of those by (s, eta, id) with s an integer
+ * MLP 16 -> 64 -> 64 -> 1 of symmetric pair features; the matching weight
+ * stays eta and the best-effort pairing still takes the nodes with no valid
+ * neighbour.  Mutual lists keep the proposal graph free of cycles longer
+ * than two.
  */
 #include <stdint.h>
 #include <stdio.h>
@@ -61,7 +69,7 @@
 enum { OR_OK = 0, OR_ERR_INVALID_ARG = 1, OR_ERR_BAD_CSR = 2, OR_ERR_INFEASIBLE = 3 };
 
 /* option vector layout shared with the Python wrapper of this file */
-enum { OPT_PI, OPT_THETA, OPT_WINDOW, OPT_ROUNDS, OPT_PERMILLE, OPT_KIND, OPT_MAXLEV, OPT_N };
+enum { OPT_PI, OPT_THETA, OPT_WINDOW, OPT_ROUNDS, OPT_PERMILLE, OPT_KIND, OPT_MAXLEV, OPT_LK, OPT_N };
 /* stats vector layout */
 enum { ST_CONN, ST_CUTNET, ST_PARTS, ST_MAXSIZE, ST_MAXDIST, ST_VIOL, ST_LEVELS, ST_MOVES, ST_N = 16 };
 /* per-level trace record layout */
@@ -387,6 +395,153 @@ static int64_t match_all(int32_t n, int32_t pi, const int32_t *cand, const uint6
     }
     free(target); free(score); free(rmate);
     return pairs;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Learned merge priority: a growth of Sec. V-C that is not in the paper.      */
+/* Each node keeps its top-K valid candidates by (eta, id) (Eq. 6 with K for  */
+/* Pi); a pair is kept only when each end is in the other's list, and C(n) is  */
+/* the top Pi of those by (s, eta, id), s being an integer MLP of sixteen      */
+/* symmetric pair features.  The matching weight stays eta.                   */
+/* ------------------------------------------------------------------------ */
+enum { ML_IN = 16, ML_HID = 64 };
+/* model vector layout shared with the Python wrapper of this file */
+enum {
+    MD_W1 = 0,                          /* [64][16] codes in [-127, 127] */
+    MD_W2 = MD_W1 + ML_HID * ML_IN,     /* [64][64] */
+    MD_W3 = MD_W2 + ML_HID * ML_HID,    /* [64] */
+    MD_B1 = MD_W3 + ML_HID,             /* [64], |b| <= 2^30 */
+    MD_B2 = MD_B1 + ML_HID,             /* [64] */
+    MD_B3 = MD_B2 + ML_HID,
+    MD_S1, MD_S2,                       /* right shifts, 0..30 */
+    MD_N
+};
+
+static int model_ok(const int32_t *md)
+{
+    for (int i = MD_W1; i < MD_B1; i++)
+        if (md[i] < -127 || md[i] > 127) return 0;
+    for (int i = MD_B1; i <= MD_B3; i++)
+        if (md[i] < -(1 << 30) || md[i] > (1 << 30)) return 0;
+    return md[MD_S1] >= 0 && md[MD_S1] <= 30 && md[MD_S2] >= 0 && md[MD_S2] <= 30;
+}
+
+/* log code of x >= 0: 0 for 0, else 1 + 4 floor(log2 x) + the two bits after
+ * the leading one, at most 255 */
+static int32_t log_code(uint64_t x)
+{
+    if (x == 0) return 0;
+    int b = 63;
+    while (!((x >> b) & 1u)) b--;
+    uint64_t frac = b >= 2 ? (x >> (b - 2)) & 3u : (x << (2 - b)) & 3u;
+    int64_t c = 1 + 4 * (int64_t)b + (int64_t)frac;
+    return (int32_t)(c > 255 ? 255 : c);
+}
+
+static int32_t imin32(int32_t a, int32_t b) { return a < b ? a : b; }
+static int32_t imax32(int32_t a, int32_t b) { return a > b ? a : b; }
+
+/* The sixteen features of the pair (v, m), each in 0..255 and each symmetric
+ * in v and m.  eta is the pair's Eq. 5 value with noise; rv, rm the
+ * positions of m in v's list and of v in m's list.  emark is a zeroed
+ * scratch of |E| bytes, left zeroed. */
+static void pair_features(const hg_t *g, int32_t level, int32_t v, int32_t m, uint64_t eta, int32_t rv,
+                          int32_t rm, int32_t omega, int32_t delta, uint8_t *emark, uint8_t *f)
+{
+    /* hyperedges holding both ends (shared) and inbound to both (inter) */
+    for (int64_t t = g->ioff[m]; t < g->ioff[m + 1]; t++)
+        emark[g->inc[t]] = t < g->ioff[m] + g->nin[m] ? 1 : 2;
+    int64_t shared = 0, inter = 0;
+    for (int64_t t = g->ioff[v]; t < g->ioff[v + 1]; t++) {
+        uint8_t k = emark[g->inc[t]];
+        if (k) shared++;
+        if (k == 1 && t < g->ioff[v] + g->nin[v]) inter++;
+    }
+    for (int64_t t = g->ioff[m]; t < g->ioff[m + 1]; t++) emark[g->inc[t]] = 0;
+    int64_t sv = g->size[v], sm = g->size[m], iv = g->nin[v], im = g->nin[m];
+    int64_t dv = g->ioff[v + 1] - g->ioff[v], dm = g->ioff[m + 1] - g->ioff[m];
+    int64_t uni = iv + im - inter;
+    f[0] = (uint8_t)log_code(eta);
+    f[1] = (uint8_t)log_code((uint64_t)shared);
+    f[2] = (uint8_t)log_code((uint64_t)inter);
+    f[3] = (uint8_t)log_code((uint64_t)(sv < sm ? sv : sm));
+    f[4] = (uint8_t)log_code((uint64_t)(sv > sm ? sv : sm));
+    f[5] = (uint8_t)log_code((uint64_t)(iv < im ? iv : im));
+    f[6] = (uint8_t)log_code((uint64_t)(iv > im ? iv : im));
+    f[7] = (uint8_t)log_code((uint64_t)(dv < dm ? dv : dm));
+    f[8] = (uint8_t)log_code((uint64_t)(dv > dm ? dv : dm));
+    f[9] = (uint8_t)(255 * (sv + sm) / omega);              /* valid: sv + sm <= omega */
+    f[10] = (uint8_t)(delta > 0 ? 255 * uni / delta : 0);   /* valid: uni <= delta */
+    f[11] = (uint8_t)(level < 255 ? level : 255);
+    f[12] = (uint8_t)(uni > 0 ? 255 * inter / uni : 0);
+    f[13] = (uint8_t)imin32(rv, rm);
+    f[14] = (uint8_t)imax32(rv, rm);
+    f[15] = (uint8_t)log_code((uint64_t)(iv + im));
+}
+
+/* s = b3 + w3 . a2, a2 = clamp((b2 + W2 a1) >> s2, 0, 255),
+ * a1 = clamp((b1 + W1 f) >> s1, 0, 255): integers throughout */
+static int64_t mlp_score(const int32_t *md, const uint8_t *f)
+{
+    int64_t a1[ML_HID], a2[ML_HID];
+    for (int j = 0; j < ML_HID; j++) {
+        int64_t h = md[MD_B1 + j];
+        for (int i = 0; i < ML_IN; i++) h += (int64_t)md[MD_W1 + j * ML_IN + i] * f[i];
+        a1[j] = h <= 0 ? 0 : ((h >> md[MD_S1]) > 255 ? 255 : (h >> md[MD_S1]));
+    }
+    for (int k = 0; k < ML_HID; k++) {
+        int64_t h = md[MD_B2 + k];
+        for (int j = 0; j < ML_HID; j++) h += (int64_t)md[MD_W2 + k * ML_HID + j] * a1[j];
+        a2[k] = h <= 0 ? 0 : ((h >> md[MD_S2]) > 255 ? 255 : (h >> md[MD_S2]));
+    }
+    int64_t out = md[MD_B3];
+    for (int k = 0; k < ML_HID; k++) out += (int64_t)md[MD_W3 + k] * a2[k];
+    return out;
+}
+
+static int learned_gt(int64_t s1, uint64_t e1, int32_t m1, int64_t s2, uint64_t e2, int32_t m2)
+{
+    if (s1 != s2) return s1 > s2;
+    return key_gt(e1, m1, e2, m2);
+}
+
+/* C(n) of the learned priority from the top-K lists candK/csK */
+static void learned_candidates(const hg_t *g, int32_t level, int32_t K, const int32_t *candK, const uint64_t *csK,
+                               int32_t pi, const int32_t *md, int32_t omega, int32_t delta, int32_t *cand,
+                               uint64_t *cscore)
+{
+    uint8_t *emark = xcalloc((size_t)g->e + 1, 1);
+    int64_t *sk = xcalloc((size_t)pi, sizeof(int64_t));
+    for (int32_t v = 0; v < g->n; v++) {
+        int32_t *cv = cand + (int64_t)v * pi;
+        uint64_t *ev = cscore + (int64_t)v * pi;
+        int32_t have = 0;
+        for (int32_t i = 0; i < pi; i++) { cv[i] = -1; ev[i] = 0; }
+        for (int32_t j = 0; j < K; j++) {
+            int32_t m = candK[(int64_t)v * K + j];
+            if (m < 0) break;
+            int32_t rm = -1;
+            for (int32_t i = 0; i < K; i++)
+                if (candK[(int64_t)m * K + i] == v) { rm = i; break; }
+            if (rm < 0) continue;   /* v is not among m's candidates */
+            uint8_t f[ML_IN];
+            uint64_t eta = csK[(int64_t)v * K + j];
+            pair_features(g, level, v, m, eta, j, rm, omega, delta, emark, f);
+            int64_t s = mlp_score(md, f);
+            int32_t pos = have;
+            while (pos > 0 && learned_gt(s, eta, m, sk[pos - 1], ev[pos - 1], cv[pos - 1])) pos--;
+            if (pos < pi) {
+                int32_t last = have < pi ? have : pi - 1;
+                for (int32_t t = last; t > pos; t--) { cv[t] = cv[t - 1]; ev[t] = ev[t - 1]; sk[t] = sk[t - 1]; }
+                cv[pos] = m;
+                ev[pos] = eta;
+                sk[pos] = s;
+                if (have < pi) have++;
+            }
+        }
+    }
+    free(emark);
+    free(sk);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -773,6 +928,7 @@ static int32_t best_prefix(const hg_t *g, const int32_t *rho, int32_t nparts, co
 
 typedef struct {
     int32_t pi, theta, window, rounds, permille, kind, maxlev;
+    int32_t lk;   /* 0: C(n) by (eta, id); else K of the learned priority */
 } opts_t;
 
 /* one refinement repetition (Sec. VI); returns the number of moves applied */
@@ -807,6 +963,7 @@ static void default_opts(opts_t *o)
 {
     o->pi = 4; o->theta = 16; o->window = 256; o->rounds = 16; o->permille = 100; o->kind = 0;
     o->maxlev = 256;
+    o->lk = 0;
 }
 
 static int read_opts(const int32_t *opt, opts_t *o)
@@ -816,10 +973,12 @@ static int read_opts(const int32_t *opt, opts_t *o)
         o->pi = opt[OPT_PI]; o->theta = opt[OPT_THETA]; o->window = opt[OPT_WINDOW];
         o->rounds = opt[OPT_ROUNDS]; o->permille = opt[OPT_PERMILLE]; o->kind = opt[OPT_KIND];
         o->maxlev = opt[OPT_MAXLEV];
+        o->lk = opt[OPT_LK];
     }
     if (o->pi < 1 || o->pi > 16 || o->theta < 0 || o->theta > 1024 || o->window < 1 ||
         o->rounds < 0 || o->rounds > 1024 || o->permille < 0 || o->permille > 1000 ||
-        (o->kind != 0 && o->kind != 1) || o->maxlev < 0 || o->maxlev > 4096)
+        (o->kind != 0 && o->kind != 1) || o->maxlev < 0 || o->maxlev > 4096 ||
+        (o->lk != 0 && (o->lk < o->pi || o->lk > 16)))
         return OR_ERR_INVALID_ARG;
     return OR_OK;
 }
@@ -875,14 +1034,17 @@ static int make_level0(int32_t n, int32_t e, const int32_t *off, const int32_t *
 /* ------------------------------------------------------------------------ */
 /* Sec. III: the multilevel driver                                           */
 /* ------------------------------------------------------------------------ */
-int or_partition(int32_t n, int32_t e, const int32_t *off, const int32_t *pins, const int32_t *nsrc,
-                 const int32_t *w, int32_t omega, int32_t delta, uint64_t seed, const int32_t *opt,
-                 int32_t *part_out, int64_t *stats, int64_t *trace)
+/* model: NULL, or the MD_N-vector of the learned priority (needed when the
+ * option learned_k is set) */
+int or_partition_ml(int32_t n, int32_t e, const int32_t *off, const int32_t *pins, const int32_t *nsrc,
+                    const int32_t *w, int32_t omega, int32_t delta, uint64_t seed, const int32_t *opt,
+                    const int32_t *model, int32_t *part_out, int64_t *stats, int64_t *trace)
 {
     opts_t o;
     if (n < 0 || e < 0 || omega < 1 || delta < 0 || (n > 0 && !part_out) || (e > 0 && (!off || !pins)))
         return OR_ERR_INVALID_ARG;
     if (read_opts(opt, &o) != OR_OK) return OR_ERR_INVALID_ARG;
+    if (o.lk > 0 && (!model || !model_ok(model))) return OR_ERR_INVALID_ARG;
     int32_t zero = 0;
     if (!off) off = &zero;
     hg_t *lv = xcalloc((size_t)o.maxlev + 1, sizeof(hg_t));
@@ -898,12 +1060,23 @@ int or_partition(int32_t n, int32_t e, const int32_t *off, const int32_t *pins, 
         hg_t *g = &lv[L];
         if (trace) { trace[L * TR_W + TR_N] = g->n; trace[L * TR_W + TR_PINS] = g->np; }
         if ((int64_t)g->n <= target_n || L == o.maxlev) break;
-        int32_t *cand = xcalloc((size_t)g->n * o.pi, sizeof(int32_t));
-        uint64_t *cs = xcalloc((size_t)g->n * o.pi, sizeof(uint64_t));
+        /* the learned priority ranks the top-K lists (K >= Pi); the
+         * best-effort pairing takes the nodes with no valid neighbour either way */
+        int32_t K = o.lk > 0 ? o.lk : o.pi;
+        int32_t *cand = xcalloc((size_t)g->n * K, sizeof(int32_t));
+        uint64_t *cs = xcalloc((size_t)g->n * K, sizeof(uint64_t));
         int32_t *mate = xcalloc((size_t)g->n, sizeof(int32_t));
         for (int32_t v = 0; v < g->n; v++) mate[v] = -1;
-        propose_pairs(g, L, seed, omega, delta, o.pi, o.permille, cand, cs);
-        int64_t iso = pair_isolated(g, o.pi, cand, omega, delta, mate);
+        propose_pairs(g, L, seed, omega, delta, K, o.permille, cand, cs);
+        int64_t iso = pair_isolated(g, K, cand, omega, delta, mate);
+        if (o.lk > 0) {
+            int32_t *c2 = xcalloc((size_t)g->n * o.pi, sizeof(int32_t));
+            uint64_t *s2 = xcalloc((size_t)g->n * o.pi, sizeof(uint64_t));
+            learned_candidates(g, L, K, cand, cs, o.pi, model, omega, delta, c2, s2);
+            free(cand); free(cs);
+            cand = c2;
+            cs = s2;
+        }
         int64_t pairs = iso + match_all(g->n, o.pi, cand, cs, mate);
         free(cand); free(cs);
         if (trace) { trace[L * TR_W + TR_PAIRS] = pairs; trace[L * TR_W + TR_ISOPAIRS] = iso; }
@@ -987,6 +1160,13 @@ int or_partition(int32_t n, int32_t e, const int32_t *off, const int32_t *pins, 
     for (int32_t l = 0; l <= L; l++) { hg_free(&lv[l]); free(gam[l]); }
     free(lv); free(gam);
     return OR_OK;
+}
+
+int or_partition(int32_t n, int32_t e, const int32_t *off, const int32_t *pins, const int32_t *nsrc,
+                 const int32_t *w, int32_t omega, int32_t delta, uint64_t seed, const int32_t *opt,
+                 int32_t *part_out, int64_t *stats, int64_t *trace)
+{
+    return or_partition_ml(n, e, off, pins, nsrc, w, omega, delta, seed, opt, NULL, part_out, stats, trace);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -1167,3 +1347,39 @@ int32_t or_refine_rep(int32_t n, int32_t e, const int32_t *off, const int32_t *p
     hg_free(&g);
     return k;
 }
+
+/* learned priority: the MLP on count feature rows (16 bytes each) */
+int or_mlp_scores(const uint8_t *feat, int64_t count, const int32_t *model, int64_t *out)
+{
+    if (!model_ok(model)) return OR_ERR_INVALID_ARG;
+    for (int64_t i = 0; i < count; i++) out[i] = mlp_score(model, feat + i * ML_IN);
+    return OR_OK;
+}
+
+/* learned priority on one level: top-K lists in, features of every listed
+ * pair (zero rows and rank -1 where the pair is not mutual) and C(n) out */
+int or_learned_level(int32_t n, int32_t e, const int32_t *off, const int32_t *pins, const int32_t *nsrc,
+                     const int32_t *size, int32_t omega, int32_t delta, int32_t level, int32_t K,
+                     const int32_t *candK, const uint64_t *csK, int32_t pi, const int32_t *model, uint8_t *feat,
+                     int32_t *rank, int32_t *cand, uint64_t *cscore)
+{
+    if (!model_ok(model) || K < pi || K > 16) return OR_ERR_INVALID_ARG;
+    hg_t g;
+    make_level(n, e, off, pins, nsrc, NULL, size, &g);
+    uint8_t *emark = xcalloc((size_t)e + 1, 1);
+    for (int64_t p = 0; p < (int64_t)n * K; p++) {
+        int32_t v = (int32_t)(p / K), j = (int32_t)(p % K), m = candK[p];
+        memset(feat + p * ML_IN, 0, ML_IN);
+        rank[p] = -1;
+        if (m < 0) continue;
+        for (int32_t i = 0; i < K; i++)
+            if (candK[(int64_t)m * K + i] == v) { rank[p] = i; break; }
+        if (rank[p] >= 0) pair_features(&g, level, v, m, csK[p], j, rank[p], omega, delta, emark, feat + p * ML_IN);
+    }
+    learned_candidates(&g, level, K, candK, csK, pi, model, omega, delta, cand, cscore);
+    free(emark);
+    hg_free(&g);
+    return OR_OK;
+}
+
+int32_t or_log_code(uint64_t x) { return log_code(x); }

@@ -18,6 +18,9 @@ The shapes follow the spiking-network workloads of the paper's Table I
   (8 x 32 x 32 x 32 = 262,144 nodes, ~63.6M pins).
 * :func:`random_hypergraph` -- small irregular hypergraphs for tests
   (optional multi-source hyperedges, weights, isolated nodes).
+
+:class:`MergeModel` holds the integer parameters of the learned merge
+priority (16 -> 64 -> 64 -> 1); :func:`random_merge_model` draws seeded ones.
 """
 from __future__ import annotations
 
@@ -266,3 +269,39 @@ CONSTRAINTS = {
     "layered_snn_16k": (1 << 10, 1 << 14),
     "layered_snn_65k": (1 << 12, 1 << 16),
 }
+
+
+@dataclass
+class MergeModel:
+    """Parameters of the learned merge priority: weight codes in [-127, 127],
+    biases with |b| <= 2^30, right shifts 0..30 after the two hidden layers."""
+    w1: np.ndarray   # int8 [64, 16]
+    w2: np.ndarray   # int8 [64, 64]
+    w3: np.ndarray   # int8 [64]
+    b1: np.ndarray   # int32 [64]
+    b2: np.ndarray   # int32 [64]
+    b3: int
+    shift1: int
+    shift2: int
+
+
+def random_merge_model(seed: int, bias_scale: int = 2048, shift1: int = 6, shift2: int = 8,
+                       wmax: int = 127) -> MergeModel:
+    """Uniform weight codes in [-wmax, wmax] and biases in
+    [-bias_scale, bias_scale]; the default shifts keep most hidden codes
+    inside 0..255 for features of the usual magnitude."""
+    r = np.random.default_rng(seed)
+    return MergeModel(
+        w1=r.integers(-wmax, wmax + 1, size=(64, 16)).astype(np.int8),
+        w2=r.integers(-wmax, wmax + 1, size=(64, 64)).astype(np.int8),
+        w3=r.integers(-wmax, wmax + 1, size=64).astype(np.int8),
+        b1=r.integers(-bias_scale, bias_scale + 1, size=64).astype(np.int32),
+        b2=r.integers(-bias_scale, bias_scale + 1, size=64).astype(np.int32),
+        b3=int(r.integers(-bias_scale, bias_scale + 1)),
+        shift1=shift1, shift2=shift2)
+
+
+def constant_merge_model(b3: int = 7) -> MergeModel:
+    """All weights zero: every pair scores b3."""
+    return MergeModel(w1=np.zeros((64, 16), np.int8), w2=np.zeros((64, 64), np.int8), w3=np.zeros(64, np.int8),
+                      b1=np.zeros(64, np.int32), b2=np.zeros(64, np.int32), b3=b3, shift1=0, shift2=0)
