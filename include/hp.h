@@ -85,7 +85,13 @@ typedef enum {
  *   debug_table_cap  0 in normal use; a positive power of two caps the shared-
  *                  memory neighbour table of the proposal kernel so that tests
  *                  can force its overflow path on small inputs (result-neutral)
+ *   learned_k      0 (default): C(n) is the top-pi valid neighbours by
+ *                  (eta, id), as in the paper.  pi..16: the learned merge
+ *                  priority below ranks each node's top-learned_k list.
+ *   merge_model    host pointer to the model of the learned priority (read
+ *                  during the call; required when learned_k > 0, else ignored)
  */
+typedef struct hp_merge_model hp_merge_model;
 typedef struct {
     int32_t pi;
     int32_t theta;
@@ -95,7 +101,49 @@ typedef struct {
     int32_t count_kind;
     int32_t max_levels;
     int32_t debug_table_cap;
+    int32_t learned_k;
+    int32_t reserved;     /* 0 */
+    const hp_merge_model *merge_model;
 } hp_options;
+
+/*
+ * Learned merge priority -- a growth of Sec. V-C that the paper does not
+ * have.  Each node keeps its top-K valid neighbours by (eta, id) (Eq. 5-6
+ * with K in place of pi); a pair stays a candidate only when each end is in
+ * the other's list; C(n) is then the top pi of the node's candidates by
+ * (s, eta, id), descending, where s is the score of the MLP below on sixteen
+ * features of the pair, each in 0..255 and symmetric in the two ends.  The
+ * matching of Sec. V-D keeps eta as its weight and the best-effort pairing
+ * still takes the nodes with no valid neighbour.  Because s and the candidate
+ * relation are symmetric, the proposal graph keeps only 2-cycles, so the
+ * matching stays exact.
+ *
+ * Features, with L(x) = 0 for x = 0, else min(255, 1 + 4 floor(log2 x) + the
+ * two bits that follow the leading one), for the pair (v, m):
+ *   0 L(eta)  1 L(|I(v) & I(m)|)  2 L(inter = |in(v) & in(m)|)
+ *   3,4 L(min, max of the sizes)  5,6 L(min, max of |in|)  7,8 L(min, max of |I|)
+ *   9 floor(255 (size(v)+size(m)) / Omega)  10 floor(255 |in(v) U in(m)| / Delta)
+ *   11 min(level, 255)  12 floor(255 inter / |in(v) U in(m)|) (0 if empty)
+ *   13,14 min, max of the two list positions  15 L(|in(v)| + |in(m)|)
+ * MLP, integers throughout (floor shifts; every product and partial sum is
+ * an integer below 2^21, so bf16 operands with fp32 accumulation compute it
+ * exactly):
+ *   a1 = clamp((b1 + W1 f) >> shift1, 0, 255)     W1 [64][16]
+ *   a2 = clamp((b2 + W2 a1) >> shift2, 0, 255)    W2 [64][64]
+ *   s  = b3 + w3 . a2                              w3 [64]
+ * Weight codes lie in [-127, 127], biases in [-2^30, 2^30], shifts in 0..30;
+ * anything else is HP_ERR_INVALID_ARG.
+ */
+struct hp_merge_model {
+    int8_t w1[64][16];
+    int8_t w2[64][64];
+    int8_t w3[64];
+    int32_t b1[64];
+    int32_t b2[64];
+    int32_t b3;
+    int32_t shift1;
+    int32_t shift2;
+};
 
 /* Per-call statistics (host struct filled on HP_OK). */
 typedef struct {
@@ -246,6 +294,16 @@ HP_API hp_status hp_connectivity_noalloc(const int32_t *pins, const int32_t *off
                                          int32_t num_parts, int64_t *conn_out, int64_t *cutnet_out, void *stream);
 
 /*
+ * hp_merge_scores -- the MLP of the learned merge priority on `count` feature
+ *   rows: feat is device uint8[count][16], score_out device int32[count],
+ *   model a host pointer.  HP_ERR_INVALID_ARG for a model out of range, a
+ *   negative count or a NULL pointer (count 0 needs none).  Synchronises
+ *   `stream` before returning.
+ */
+HP_API hp_status hp_merge_scores(const uint8_t *feat, int64_t count, const hp_merge_model *model,
+                                 int32_t *score_out, void *stream);
+
+/*
  * Step-level entry points (test hooks) on one level graph given in device
  * memory: num_nodes, num_hedges, offsets, pins, src_counts (required, one
  * count per hyperedge), weights (required) and node sizes.  They run one step
@@ -255,7 +313,8 @@ HP_API hp_status hp_connectivity_noalloc(const int32_t *pins, const int32_t *off
  *   candidates of every node (cand_out[n*pi], -1 padded; score_out[n*pi] the
  *   fixed-point eta plus noise of Eq. 5, noise keyed by seed and level), then
  *   best-effort pairing and pi rounds of matching; mate_out[n] is the
- *   partner or -1; *pairs_out (host) counts the pairs.
+ *   partner or -1; *pairs_out (host) counts the pairs.  With learned_k set,
+ *   cand_out/score_out hold C(n) of the learned priority and eta.
  */
 HP_API hp_status hp_debug_coarsen_level(int32_t num_nodes, int32_t num_hedges, const int32_t *offsets,
                                         const int32_t *pins, const int32_t *src_counts, const int32_t *weights,

@@ -61,6 +61,9 @@ static bool options_ok(const hp_options &o) {
         int c = o.debug_table_cap;
         if (c < 64 || c > 65536 || (c & (c - 1))) return false;
     }
+    if (o.learned_k != 0 &&
+        (o.learned_k < o.pi || o.learned_k > 16 || !o.merge_model || !merge_model_ok(*o.merge_model)))
+        return false;
     return true;
 }
 
@@ -269,6 +272,25 @@ void hp_default_options(hp_options *o) {
     o->count_kind = HP_COUNT_INBOUND;
     o->max_levels = 256;
     o->debug_table_cap = 0;
+    o->learned_k = 0;
+    o->reserved = 0;
+    o->merge_model = nullptr;
+}
+
+hp_status hp_merge_scores(const uint8_t *feat, int64_t count, const hp_merge_model *model, int32_t *score_out,
+                          void *stream) {
+    return hp::guarded([&]() -> hp_status {
+        if (count < 0 || !model || (count > 0 && (!feat || !score_out)) || !hp::merge_model_ok(*model))
+            return HP_ERR_INVALID_ARG;
+        if (count == 0) return HP_OK;
+        cudaStream_t s = static_cast<cudaStream_t>(stream);
+        hp::Arena A(s);
+        hp_merge_model *dm = A.get<hp_merge_model>(1);
+        HPC(cudaMemcpyAsync(dm, model, sizeof(hp_merge_model), cudaMemcpyHostToDevice, s));
+        hp::merge_scores(feat, count, dm, score_out, s);
+        HPC(cudaStreamSynchronize(s));
+        return HP_OK;
+    });
 }
 
 hp_status hp_partition_ex(const int32_t *pins, const int32_t *offsets, int32_t num_hedges, int32_t num_nodes,

@@ -732,8 +732,13 @@ struct CoarsenWs {
     int32_t *canon;   // destination-list groups of the current level's hyperedges
     cudaStream_t side[3] = {nullptr, nullptr, nullptr};   // side streams of the proposal tiers
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
-    int32_t *cand;
+    int32_t *cand;      // [n*K] top-K lists of the proposal (K = learned_k, else Pi)
     uint64_t *cscore;
+    // learned merge priority (learned_k > 0)
+    hp_merge_model *model = nullptr;
+    uint8_t *feat = nullptr;
+    int32_t *rank = nullptr, *lscore = nullptr, *lcand = nullptr;
+    uint64_t *lcs = nullptr;
     int32_t *lW, *lB, *lC, *lG, *lH, *lD, *lDH, *cnt;   // cnt: 0 W 1 B 2 C 3 G 4 errors 5 H 6 D 7 DH
     long long *nsum, *vis;             // per node: sum of (|e|-1), sum of |e| over I(v)
     uint32_t gcap;
@@ -1014,14 +1019,23 @@ CoarsenWs *coarsen_workspace(int32_t n, int32_t e, const Params &P, Arena &A) {
     CoarsenWs *W = new CoarsenWs();
     for (cudaStream_t &x : W->side) HPC(cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking));
     for (cudaEvent_t &x : W->ev) HPC(cudaEventCreateWithFlags(&x, cudaEventDisableTiming));
-    const int32_t pi = P.o.pi;
+    const int32_t pi = P.o.pi, K = P.o.learned_k > 0 ? P.o.learned_k : pi;
     W->cn = n;
     W->ce = e;
     W->pi = pi;
     W->q = A.get<uint64_t>(e);
     W->canon = A.get<int32_t>(std::max(e, 1));
-    W->cand = A.get<int32_t>((int64_t)n * pi);
-    W->cscore = A.get<uint64_t>((int64_t)n * pi);
+    W->cand = A.get<int32_t>((int64_t)n * K);
+    W->cscore = A.get<uint64_t>((int64_t)n * K);
+    if (P.o.learned_k > 0) {
+        W->model = A.get<hp_merge_model>(1);
+        HPC(cudaMemcpyAsync(W->model, P.o.merge_model, sizeof(hp_merge_model), cudaMemcpyHostToDevice, s));
+        W->feat = A.get<uint8_t>((int64_t)n * K * 16);
+        W->rank = A.get<int32_t>((int64_t)n * K);
+        W->lscore = A.get<int32_t>((int64_t)n * K);
+        W->lcand = A.get<int32_t>((int64_t)n * pi);
+        W->lcs = A.get<uint64_t>((int64_t)n * pi);
+    }
     W->lW = A.get<int32_t>(n);
     W->lB = A.get<int32_t>(n);
     W->lC = A.get<int32_t>(n);
@@ -1072,6 +1086,9 @@ void coarsen_workspace_free(CoarsenWs *W, Arena &A) {
                     (void *)W->score, (void *)W->ccount, (void *)W->fillpos,
                     (void *)W->best, (void *)W->ss0, (void *)W->ss10, (void *)W->sum0, (void *)W->kmax, (void *)W->box})
         A.release(p);
+    for (void *p : {(void *)W->model, (void *)W->feat, (void *)W->rank, (void *)W->lscore, (void *)W->lcand,
+                    (void *)W->lcs})
+        if (p) A.release(p);
     delete W;
 }
 
@@ -1103,6 +1120,8 @@ void coarsen_level(Level &L, int32_t level, const int32_t *w, const Params &P, i
                    uint32_t *err_dev, int32_t *cand_out, uint64_t *score_out, cudaEvent_t *prop_events) {
     cudaStream_t s = A.stream();
     const int32_t n = L.n, pi = P.o.pi;
+    const bool learned = P.o.learned_k > 0;
+    const int32_t K = learned ? P.o.learned_k : pi;   // length of the proposal's lists
     LevelBox *box = W.box;
     HPC(cudaMemsetAsync(box, 0, sizeof(LevelBox), s));
     if (L.e > 0) {
@@ -1123,7 +1142,7 @@ void coarsen_level(Level &L, int32_t level, const int32_t *w, const Params &P, i
     HP_LAUNCH_CHECK();
     PropCtx C;
     C.n = n;
-    C.pi = pi;
+    C.pi = K;
     C.off = L.off;
     C.pin = L.pin;
     C.nsrc = L.nsrc;
@@ -1154,20 +1173,45 @@ void coarsen_level(Level &L, int32_t level, const int32_t *w, const Params &P, i
         dst_groups(L, W.canon, A);
         C.canon = W.canon;
     }
-    if (pi <= 4) run_proposal<4>(C, L, P, W, A);
+    if (K <= 4) run_proposal<4>(C, L, P, W, A);
     else run_proposal<16>(C, L, P, W, A);
+    // C(n) and its matching weights
+    int32_t *cand = W.cand;
+    uint64_t *cscore = W.cscore;
+    if (learned) {
+        LearnIn X;
+        X.n = n;
+        X.K = K;
+        X.pi = pi;
+        X.level = level;
+        X.omega = P.omega;
+        X.delta = P.delta;
+        X.size = L.size;
+        X.ioff = L.ioff;
+        X.inc = L.inc;
+        X.nin = L.nin;
+        X.candK = W.cand;
+        X.csK = W.cscore;
+        X.model = W.model;
+        X.feat = W.feat;
+        X.rank = W.rank;
+        X.score = W.lscore;
+        X.cand = cand = W.lcand;
+        X.cscore = cscore = W.lcs;
+        learned_candidates(X, s);
+    }
     if (prop_events) HPC(cudaEventRecord(prop_events[1], s));
     k_flag_if_nonzero<<<1, 1, 0, s>>>(W.cnt + 4, err_dev);
     HP_LAUNCH_CHECK();
     k_sum_i32<<<grid_of(n, 256), 256, 0, s>>>(L.nbnd, n, &box->nbrs);
     HP_LAUNCH_CHECK();
     if (cand_out) {
-        HPC(cudaMemcpyAsync(cand_out, W.cand, sizeof(int32_t) * n * pi, cudaMemcpyDeviceToDevice, s));
-        HPC(cudaMemcpyAsync(score_out, W.cscore, sizeof(uint64_t) * n * pi, cudaMemcpyDeviceToDevice, s));
+        HPC(cudaMemcpyAsync(cand_out, cand, sizeof(int32_t) * n * pi, cudaMemcpyDeviceToDevice, s));
+        HPC(cudaMemcpyAsync(score_out, cscore, sizeof(uint64_t) * n * pi, cudaMemcpyDeviceToDevice, s));
     }
 
     // best-effort pairing of nodes with no valid neighbour (Sec. V-C)
-    k_iso_flags<<<grid_of(n, 256), 256, 0, s>>>(W.cand, pi, n, W.flag);
+    k_iso_flags<<<grid_of(n, 256), 256, 0, s>>>(W.cand, K, n, W.flag);
     HP_LAUNCH_CHECK();
     scan_excl(W.flag, W.pos, n, W.pos + n, A);
     k_iso_compact<<<grid_of(n, 256), 256, 0, s>>>(W.flag, W.pos, L.size, n, W.ikeys, W.iids);
@@ -1191,7 +1235,7 @@ void coarsen_level(Level &L, int32_t level, const int32_t *w, const Params &P, i
     D.best = W.best;
     D.err = err_dev;
     for (int32_t r = 0; r < pi; r++) {
-        k_targets<<<grid_of(n, 256), 256, 0, s>>>(W.cand, W.cscore, pi, mate, n, W.target, W.score, W.sum0, W.kmax,
+        k_targets<<<grid_of(n, 256), 256, 0, s>>>(cand, cscore, pi, mate, n, W.target, W.score, W.sum0, W.kmax,
                                                   W.best, W.ccount, W.fillpos);
         HP_LAUNCH_CHECK();
         k_child_count<<<grid_of(n, 256), 256, 0, s>>>(W.target, n, W.ccount, W.fillpos);

@@ -321,6 +321,23 @@ void coarsen_level(Level &L, int32_t level, const int32_t *w, const Params &P, i
                    uint32_t *err_dev, int32_t *cand_out = nullptr, uint64_t *score_out = nullptr,
                    cudaEvent_t *prop_events = nullptr);
 
+// learned merge priority (hp_learned.cu)
+bool merge_model_ok(const hp_merge_model &m);
+struct LearnIn {
+    int32_t n, K, pi, level, omega, delta;
+    const int32_t *size, *ioff, *inc, *nin;   // the level graph
+    const int32_t *candK;                     // [n*K] top-K valid neighbours by (eta, id), -1 padded
+    const uint64_t *csK;                      // [n*K] their eta (with noise)
+    const hp_merge_model *model;              // device copy
+    uint8_t *feat;                            // [n*K][16] scratch, 16-byte aligned
+    int32_t *rank;                            // [n*K] scratch
+    int32_t *score;                           // [n*K] scratch
+    int32_t *cand;                            // [n*pi] out: C(n)
+    uint64_t *cscore;                         // [n*pi] out: eta of C(n)
+};
+void learned_candidates(const LearnIn &X, cudaStream_t s);
+void merge_scores(const uint8_t *feat, int64_t count, const hp_merge_model *dmodel, int32_t *out, cudaStream_t s);
+
 // refinement (hp_refine.cu)
 // optional copies of the intermediate results of one repetition (device
 // buffers of n entries; m and best_gain are host / device scalars)

@@ -26,13 +26,32 @@ HP_ERR_OOM, HP_ERR_CUDA, HP_ERR_TIMEOUT, HP_ERR_INTERNAL = 4, 5, 6, 7
 HP_COUNT_INBOUND, HP_COUNT_INCIDENT = 0, 1
 
 EXPORTS = ("hp_default_options", "hp_partition", "hp_partition_ex", "hp_partition_host", "hp_set_allocator",
-           "hp_status_string", "hp_last_error", "hp_connectivity", "hp_connectivity_noalloc", "hp_partition_batch", "hp_debug_coarsen_level",
-           "hp_debug_refine_rep")
+           "hp_status_string", "hp_last_error", "hp_connectivity", "hp_connectivity_noalloc", "hp_partition_batch", "hp_merge_scores",
+           "hp_debug_coarsen_level", "hp_debug_refine_rep")
+
+
+class hp_merge_model(ctypes.Structure):
+    _fields_ = [("w1", ctypes.c_int8 * 1024), ("w2", ctypes.c_int8 * 4096), ("w3", ctypes.c_int8 * 64),
+                ("b1", ctypes.c_int32 * 64), ("b2", ctypes.c_int32 * 64), ("b3", ctypes.c_int32),
+                ("shift1", ctypes.c_int32), ("shift2", ctypes.c_int32)]
 
 
 class hp_options(ctypes.Structure):
     _fields_ = [(k, ctypes.c_int32) for k in ("pi", "theta", "chain_window", "chain_rounds", "noise_permille",
-                                               "count_kind", "max_levels", "debug_table_cap")]
+                                               "count_kind", "max_levels", "debug_table_cap", "learned_k",
+                                               "reserved")] + [("merge_model", ctypes.POINTER(hp_merge_model))]
+
+
+def merge_model(m) -> hp_merge_model:
+    """ctypes hp_merge_model of an inputs.MergeModel."""
+    x = hp_merge_model()
+    ctypes.memmove(x.w1, np.ascontiguousarray(m.w1, dtype=np.int8).ctypes.data, 1024)
+    ctypes.memmove(x.w2, np.ascontiguousarray(m.w2, dtype=np.int8).ctypes.data, 4096)
+    ctypes.memmove(x.w3, np.ascontiguousarray(m.w3, dtype=np.int8).ctypes.data, 64)
+    ctypes.memmove(x.b1, np.ascontiguousarray(m.b1, dtype=np.int32).ctypes.data, 256)
+    ctypes.memmove(x.b2, np.ascontiguousarray(m.b2, dtype=np.int32).ctypes.data, 256)
+    x.b3, x.shift1, x.shift2 = int(m.b3), int(m.shift1), int(m.shift2)
+    return x
 
 
 class hp_stats(ctypes.Structure):
@@ -90,6 +109,8 @@ def load() -> ctypes.CDLL:
         L.hp_partition_batch.argtypes = [ctypes.POINTER(hp_instance), I32, ctypes.POINTER(hp_options), I32,
                                          ctypes.POINTER(hp_stats), ctypes.POINTER(ctypes.c_int32), P]
         L.hp_partition_batch.restype = ctypes.c_int
+        L.hp_merge_scores.argtypes = [P, ctypes.c_int64, ctypes.POINTER(hp_merge_model), P, P]
+        L.hp_merge_scores.restype = ctypes.c_int
         L.hp_connectivity_noalloc.argtypes = L.hp_connectivity.argtypes
         L.hp_connectivity_noalloc.restype = ctypes.c_int
         L.hp_debug_coarsen_level.argtypes = [I32, I32, P, P, P, P, P, I32, I32, U64, I32, ctypes.POINTER(hp_options),
@@ -180,11 +201,33 @@ class Result:
     trace: list
 
 
-def options(**kw) -> hp_options:
+def options(model=None, **kw) -> hp_options:
+    """hp_options from keyword values; ``model`` (an inputs.MergeModel) is
+    converted and kept alive with the returned struct."""
     o = hp_default_options()
     for k, v in kw.items():
         setattr(o, k, int(v))
+    if model is not None:
+        o._model = merge_model(model)
+        o.merge_model = ctypes.pointer(o._model)
     return o
+
+
+def hp_merge_scores(feat, count, model, score_out, stream=0):
+    return load().hp_merge_scores(feat, count, model, score_out, stream)
+
+
+def merge_scores(feat, model, stream=0):
+    """Scores of the learned priority's MLP for feature rows feat[count, 16]
+    (uint8 torch tensor on the GPU); returns (status, int32 tensor)."""
+    import torch
+    count = feat.shape[0]
+    out = torch.empty(max(count, 1), dtype=torch.int32, device=feat.device)
+    m = merge_model(model)
+    rc = hp_merge_scores(feat.data_ptr() if count else None, count, ctypes.byref(m),
+                         out.data_ptr() if count else None, stream)
+    torch.cuda.synchronize()
+    return rc, out[:count]
 
 
 def _stats_dict(s: hp_stats) -> dict:

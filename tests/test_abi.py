@@ -42,7 +42,8 @@ def test_only_declared_symbols_are_exported(lib):
 def test_host_only_calls(lib):
     o = hp.hp_default_options()
     assert (o.pi, o.theta, o.chain_window, o.chain_rounds, o.noise_permille, o.count_kind, o.max_levels,
-            o.debug_table_cap) == (4, 16, 256, 16, 100, 0, 256, 0)
+            o.debug_table_cap, o.learned_k) == (4, 16, 256, 16, 100, 0, 256, 0, 0)
+    assert not o.merge_model
     assert hp.hp_status_string(hp.HP_OK) == "ok"
     assert "CSR" in hp.hp_status_string(hp.HP_ERR_BAD_CSR)
     assert hp.hp_last_error() == ""
@@ -60,7 +61,32 @@ def test_argument_checks_before_any_device_work(lib):
 
 
 def test_struct_layout_matches_header(lib):
-    assert ctypes.sizeof(hp.hp_options) == 8 * 4
+    assert ctypes.sizeof(hp.hp_options) == 10 * 4 + 8
+    assert ctypes.sizeof(hp.hp_merge_model) == 64 * 16 + 64 * 64 + 64 + 4 * (64 + 64 + 3)
     assert ctypes.sizeof(hp.hp_stats) == 8 + 8 + 6 * 4 + 8 + 8 + 3 * 8 + 3 * 8 + 8
     assert ctypes.sizeof(hp.hp_level_trace) == 4 * 4 + 3 * 8
     assert ctypes.sizeof(hp.hp_instance) == 4 * 8 + 4 * 4 + 8 + 8
+
+
+def test_learned_priority_checks_before_any_device_work(lib):
+    from paper_2605_20497_gb300 import inputs
+    good = hp.merge_model(inputs.random_merge_model(0))
+    bad = hp.merge_model(inputs.random_merge_model(0))
+    bad.w2[17] = -128
+    assert lib.hp_merge_scores(None, 0, ctypes.byref(good), None, None) == hp.HP_OK
+    assert lib.hp_merge_scores(None, -1, ctypes.byref(good), None, None) == hp.HP_ERR_INVALID_ARG
+    assert lib.hp_merge_scores(None, 0, ctypes.byref(bad), None, None) == hp.HP_ERR_INVALID_ARG
+    assert lib.hp_merge_scores(None, 5, ctypes.byref(good), None, None) == hp.HP_ERR_INVALID_ARG
+    off = (ctypes.c_int32 * 1)(0)   # a valid empty hypergraph: only the options are wrong
+    for kw in (dict(learned_k=16), dict(learned_k=3, model=inputs.random_merge_model(0)),
+               dict(learned_k=17, model=inputs.random_merge_model(0))):
+        o = hp.options(**kw)
+        st = hp.hp_stats()
+        assert lib.hp_partition(None, off, 0, 0, None, None, 4, 4, 0, ctypes.byref(o), None,
+                                ctypes.byref(st), None) == hp.HP_ERR_INVALID_ARG, kw
+    m = inputs.random_merge_model(0)
+    m.shift2 = 31
+    o = hp.options(learned_k=16, model=m)
+    st = hp.hp_stats()
+    assert lib.hp_partition(None, off, 0, 0, None, None, 4, 4, 0, ctypes.byref(o), None, ctypes.byref(st),
+                            None) == hp.HP_ERR_INVALID_ARG

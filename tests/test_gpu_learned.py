@@ -1,0 +1,149 @@
+"""GPU parity of the learned merge priority (option learned_k): the
+tensor-core MLP, one coarsening level and whole partitions against the
+oracle, bit for bit."""
+import ctypes
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2605_20497_gb300 import hp, inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    t = pytest.importorskip("torch")
+    if not t.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2605_20497_gb300 import build
+    build.build()
+    oracle.build()
+    hp.load()
+    return t
+
+
+def extreme_model(sign: int):
+    # every weight at the code limit: the largest products and partial sums
+    # the MLP can meet (layer 2: 64 * 127 * 255 = 2,072,640 < 2^21)
+    m = inputs.constant_merge_model(0)
+    m.w1[:] = 127 * sign
+    m.w2[:] = 127
+    m.w3[:] = 127
+    m.b1[:] = 2**30 if sign < 0 else 0
+    m.b2[:] = -(2**20)
+    m.shift1, m.shift2 = 12, 13
+    return m
+
+
+def models():
+    yield inputs.random_merge_model(1)
+    yield inputs.random_merge_model(2, bias_scale=2**30, shift1=0, shift2=30)
+    yield inputs.random_merge_model(3, shift1=0, shift2=0)
+    yield extreme_model(1)
+    yield extreme_model(-1)
+    m = inputs.random_merge_model(4)
+    m.w1[:, ::2] = -127
+    m.w2[::3] = 127
+    yield m
+
+
+@pytest.mark.parametrize("count", [0, 1, 15, 16, 17, 16 * 37 + 5, 200_003])
+def test_merge_scores_match_oracle(torch, count):
+    rng = np.random.default_rng(count)
+    feat = rng.integers(0, 256, size=(count, 16)).astype(np.uint8)
+    if count > 20:
+        feat[:7] = 255
+        feat[7:9] = 0
+    fd = torch.from_numpy(feat).cuda()
+    for m in models():
+        rc, s = hp.merge_scores(fd, m)
+        assert rc == hp.HP_OK, hp.hp_last_error()
+        want = oracle.mlp_scores(feat, m) if count else np.zeros(0, np.int64)
+        assert np.array_equal(s.cpu().numpy().astype(np.int64), want)
+
+
+def test_merge_scores_rejects_bad_model(torch):
+    m = inputs.random_merge_model(0)
+    m.w3[3] = -128
+    rc, _ = hp.merge_scores(torch.zeros((4, 16), dtype=torch.uint8, device="cuda"), m)
+    assert rc == hp.HP_ERR_INVALID_ARG
+
+
+def _gpu_coarsen(torch, g, size, omega, delta, seed, level, **opts):
+    from test_gpu_steps import gpu_coarsen
+    return gpu_coarsen(torch, g, size, omega, delta, seed, level, **opts)
+
+
+@pytest.mark.parametrize("case", range(4))
+def test_one_level_matches_oracle(torch, case):
+    if case == 0:
+        g, omega, delta = inputs.random_snn(1500, 13, seed=1), 8, 40
+    elif case == 1:
+        g, omega, delta = inputs.random_hypergraph(900, 1400, 24, seed=2, multi_src=True, weights=True), 12, 60
+    elif case == 2:
+        g, omega, delta = inputs.powerlaw_snn(2500, seed=3), 32, 128
+    else:
+        g, omega, delta = inputs.random_snn(3000, 31, seed=4), 64, 1024
+    rng = np.random.default_rng(case)
+    size = rng.integers(1, 4, size=g.num_nodes).astype(np.int32)
+    K, pi, seed, level = 16, 4, 5, 2 + case
+    model = inputs.random_merge_model(10 + case)
+    cand, score, mate, pairs = _gpu_coarsen(torch, g, size, omega, delta, seed, level, learned_k=K, model=model)
+    candK, csK = oracle.propose(g, size, omega, delta, seed=seed, level=level, pi=K)
+    _, _, oc, ocs = oracle.learned_level(g, size, omega, delta, level, candK.ravel(), csK.ravel(), pi, model)
+    assert np.array_equal(cand, oc.reshape(-1, pi))
+    assert np.array_equal(score, ocs.reshape(-1, pi))
+    omate = np.full(g.num_nodes, -1, np.int32)
+    iso, omate = oracle.pair_isolated(g, size, omega, delta, candK, omate)
+    total, omate = oracle.match_all(oc.reshape(-1, pi), ocs.reshape(-1, pi), omate)
+    assert np.array_equal(mate, omate)
+    assert pairs == iso + total
+
+
+def _cases():
+    yield "snn", inputs.random_snn(2000, 15, seed=1), 16, 80, {}
+    yield "multi_src_weighted", inputs.random_hypergraph(1200, 2000, 20, seed=3, multi_src=True, weights=True), 10, 50, {}
+    yield "powerlaw", inputs.powerlaw_snn(3000, seed=4), 64, 256, {}
+    yield "incident", inputs.random_snn(1500, 9, seed=6), 16, 120, dict(count_kind=1)
+    yield "k8_pi2", inputs.random_snn(1800, 11, seed=7), 12, 60, dict(pi=2)
+    yield "random_snn_4k", inputs.workload("random_snn_4k"), 256, 1024, {}
+
+
+@pytest.mark.parametrize("idx", range(6))
+def test_partition_matches_oracle(torch, idx):
+    name, g, omega, delta, extra = list(_cases())[idx]
+    K = 8 if extra.get("pi") == 2 else 16
+    model = inputs.random_merge_model(20 + idx)
+    r = hp.partition(g, omega, delta, seed=3, trace=True, learned_k=K, model=model, **extra)
+    o = oracle.partition(g, omega, delta, seed=3, trace=True, learned_k=K, model=model, **extra)
+    assert r.status == o.status == hp.HP_OK, (name, hp.hp_last_error())
+    assert np.array_equal(r.part, o.part), name
+    for k, v in o.stats.items():
+        assert r.stats[k] == v, (name, k)
+    assert len(r.trace) == len(o.trace)
+    for a, b in zip(r.trace, o.trace):
+        for k in ("n", "pins", "pairs", "iso_pairs", "conn", "moves", "reps"):
+            assert a[k] == b[k], (name, k)
+
+
+def test_constant_model_is_plain_partition_on_gpu(torch):
+    rng = np.random.default_rng(9)
+    g = inputs.planted_components(rng.integers(3, 17, size=300).tolist(), 9, 4, seed=9)
+    plain = hp.partition(g, 8, 40, seed=2)
+    lrn = hp.partition(g, 8, 40, seed=2, learned_k=16, model=inputs.constant_merge_model(5))
+    assert plain.status == lrn.status == hp.HP_OK
+    assert np.array_equal(plain.part, lrn.part)
+
+
+def test_learned_batch_and_host_entry_points(torch):
+    graphs = inputs.batch_snn(6, seed=8, n_min=300, n_max=2500)
+    model = inputs.random_merge_model(31)
+    rc, res = hp.partition_batch(graphs, concurrency=3, learned_k=16, model=model)
+    assert rc == hp.HP_OK, hp.hp_last_error()
+    for (g, om, de, sd), r in zip(graphs, res):
+        one = hp.partition(g, om, de, seed=sd, learned_k=16, model=model)
+        assert np.array_equal(r.part, one.part)
+        host = hp.partition_host(g, om, de, seed=sd, learned_k=16, model=model)
+        assert host.status == hp.HP_OK and np.array_equal(host.part, one.part)
