@@ -268,6 +268,62 @@ def run_batch(args):
     return 0
 
 
+def run_merge_mlp(args):
+    """The learned priority's MLP alone: hp_merge_scores over `rows` random
+    feature rows (16 B in, 4 B out each; inputs above L2 size), timed with
+    CUDA events on the launching stream."""
+    import numpy as np
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2605_20497_gb300 import hp, inputs
+    rows = args.rows
+    feat = torch.from_numpy(np.random.default_rng(rank).integers(0, 256, size=(rows, 16), dtype=np.uint8)).cuda()
+    out = torch.empty(rows, dtype=torch.int32, device="cuda")
+    model = hp.merge_model(inputs.random_merge_model(args.model_seed))
+    stream = torch.cuda.current_stream()
+    lib = hp.load()
+
+    def step():
+        rc = lib.hp_merge_scores(feat.data_ptr(), rows, ctypes.byref(model), out.data_ptr(), stream.cuda_stream)
+        if rc != hp.HP_OK:
+            raise RuntimeError(hp.hp_last_error())
+
+    for _ in range(args.warmup):
+        step()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            step()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    flops = 2 * (16 * 64 + 64 * 64) * rows   # the two tensor-core layers
+    tf = flops / (ms / 1e3) / 1e12
+    peaks = {}
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            peaks = json.load(f)
+    peak_tf = float(peaks.get("bf16_tflops", 1900.0))
+    res = {"metric": "merge-pair scores/s on 1 GB300", "value": rows / (ms / 1e3), "unit": "scores/s",
+           "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "bf16 operands, fp32 accumulate (integer-exact)",
+           "data": "synthetic",
+           "config": {"workload": f"{rows} random feature rows, random-init model (seed {args.model_seed})",
+                      "bytes_per_step": 20 * rows, "includes": "host model upload + one kernel + stream sync"},
+           "roofline": {"bound": "tensor", "achieved": tf, "peak": peak_tf, "unit": "TFLOP/s",
+                        "frac": tf / peak_tf, "traffic": None, "hbm_gbs": 20 * rows / (ms / 1e3) / 1e9,
+                        "peak_source": "measured bf16_tflops" if "bf16_tflops" in peaks else "fallback"},
+           "clocks": clk.summary()}
+    print(json.dumps(res), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -275,8 +331,13 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "batch"],
-                    help="batch: many small power-law hypergraphs through hp_partition_batch")
+    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "batch", "merge_mlp"],
+                    help="batch: many small power-law hypergraphs through hp_partition_batch; merge_mlp: the "
+                         "learned priority's MLP alone (hp_merge_scores)")
+    ap.add_argument("--learned-k", type=int, default=0,
+                    help="partition with the learned merge priority ranking top-K lists (0: the paper's priority)")
+    ap.add_argument("--model-seed", type=int, default=0, help="seed of the random-init merge model")
+    ap.add_argument("--rows", type=int, default=1 << 24, help="feature rows of the merge_mlp workload")
     ap.add_argument("--count", type=int, default=128, help="instances of the batch workload")
     ap.add_argument("--concurrency", type=int, default=16, help="instances in flight in the batch workload")
     args = ap.parse_args()
@@ -286,6 +347,8 @@ def main():
         return run_reference(args)
     if args.workload == "batch":
         return run_batch(args)
+    if args.workload == "merge_mlp":
+        return run_merge_mlp(args)
 
     import torch
     rank, world, local = dist_env()
@@ -304,7 +367,10 @@ def main():
     part = torch.empty(n, dtype=torch.int32, device="cuda")
     stream = torch.cuda.current_stream()
     sp = stream.cuda_stream
-    opt = hp.hp_default_options()
+    if args.learned_k:
+        opt = hp.options(learned_k=args.learned_k, model=inputs.random_merge_model(args.model_seed))
+    else:
+        opt = hp.hp_default_options()
     st = hp.hp_stats()
 
     def step():
@@ -390,6 +456,12 @@ def main():
         "gpu_launches": launches,
         "clocks": clocks,
     }
+    if args.learned_k:
+        out["config"]["merge_priority"] = (f"learned: top-{args.learned_k} lists re-ranked by the integer MLP "
+                                           f"16-64-64-1, random-init weights (seed {args.model_seed})")
+        out["roofline"]["kernel"] = ("level-0 candidate proposal with top-16 lists, then the learned re-ranking "
+                                     "(features, MLP, selection)")
+        out["roofline"]["traffic"] = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(*CPU_SAMPLE)
     if rank == 0:
