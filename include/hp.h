@@ -304,6 +304,62 @@ HP_API hp_status hp_merge_scores(const uint8_t *feat, int64_t count, const hp_me
                                  int32_t *score_out, void *stream);
 
 /*
+ * Training the learned merge priority.  The trainable form is the same
+ * network in fp32 on scaled features x = f / 256:
+ *   z1 = W1 x + b1, h1 = max(z1, 0), z2 = W2 h1 + b2, h2 = max(z2, 0),
+ *   o = w3 . h2 + b3, loss = mean over rows of BCE(sigmoid(o), y).
+ * Its parameters are one fp32 array of HP_MERGE_NPARAM values, in this order:
+ * W1[64][16], b1[64], W2[64][64], b2[64], w3[64], b3.
+ */
+#define HP_MERGE_NPARAM 5313
+
+/*
+ * hp_merge_features -- the level-0 training rows of one hypergraph: the
+ *   proposal's top-K lists (K = opt->learned_k, pi <= K <= 16; no model
+ *   needed) and the sixteen features of every listed pair, exactly as the
+ *   partitioner computes them at level 0.  Inputs as for hp_partition (device
+ *   pointers).  Device outputs of num_nodes*K entries: cand_out[v*K+j] the
+ *   j-th candidate of v (-1 padded), rank_out the position of v in that
+ *   candidate's list (-1 when the pair is not mutual), feat_out 16 bytes per
+ *   entry (zero unless mutual).  Synchronises `stream` before returning.
+ */
+HP_API hp_status hp_merge_features(const int32_t *pins, const int32_t *offsets, int32_t num_hedges, int32_t num_nodes,
+                                   const int32_t *src_counts, const int32_t *weights, int32_t omega, int32_t delta,
+                                   uint64_t seed, const hp_options *opt, int32_t *cand_out, int32_t *rank_out,
+                                   uint8_t *feat_out, void *stream);
+
+/*
+ * hp_merge_grad -- loss and gradient of the trainable form over `count` rows
+ *   (device: feat uint8[count][16], label float[count] in [0, 1], params
+ *   float[HP_MERGE_NPARAM]; grad_out float[HP_MERGE_NPARAM] is overwritten).
+ *   *loss_out (host, optional): the mean loss.  fp32 arithmetic; the
+ *   reduction over rows has a fixed order, so results repeat bit for bit.
+ *   Synchronises `stream` before returning.
+ */
+HP_API hp_status hp_merge_grad(const uint8_t *feat, const float *label, int64_t count, const float *params,
+                               float *grad_out, double *loss_out, void *stream);
+
+/*
+ * hp_merge_adam -- one Adam step (Kingma & Ba 2015) with decoupled weight
+ *   decay on params, using grad; m and v are the moment arrays (device,
+ *   HP_MERGE_NPARAM each, zero before step 1); step counts from 1.
+ */
+HP_API hp_status hp_merge_adam(float *params, const float *grad, float *m, float *v, int64_t step, float lr,
+                               float beta1, float beta2, float eps, float weight_decay, void *stream);
+
+/*
+ * hp_merge_quantize -- the integer model (hp_merge_model) of trained
+ *   parameters (host float[HP_MERGE_NPARAM]).  Each layer's weights are
+ *   scaled so that their largest magnitude becomes 127 and rounded; biases
+ *   are carried into the integer scale; each shift is the smallest one that
+ *   keeps the layer's largest activation over the `count` calibration rows
+ *   (host uint8[count][16]) within 255.  The score is then, up to rounding, a
+ *   positive multiple of the float output o, so it ranks pairs the same way.
+ *   Host only.
+ */
+HP_API hp_status hp_merge_quantize(const float *params, const uint8_t *calib, int64_t count, hp_merge_model *out);
+
+/*
  * Step-level entry points (test hooks) on one level graph given in device
  * memory: num_nodes, num_hedges, offsets, pins, src_counts (required, one
  * count per hyperedge), weights (required) and node sizes.  They run one step

@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <new>
 #include <string>
@@ -275,6 +276,81 @@ void hp_default_options(hp_options *o) {
     o->learned_k = 0;
     o->reserved = 0;
     o->merge_model = nullptr;
+}
+
+hp_status hp_merge_features(const int32_t *pins, const int32_t *offsets, int32_t num_hedges, int32_t num_nodes,
+                            const int32_t *src_counts, const int32_t *weights, int32_t omega, int32_t delta,
+                            uint64_t seed, const hp_options *opt, int32_t *cand_out, int32_t *rank_out,
+                            uint8_t *feat_out, void *stream) {
+    return hp::guarded([&]() -> hp_status {
+        if (!opt || num_nodes < 0 || num_hedges < 0 || omega < 1 || delta < 0 || !offsets) return HP_ERR_INVALID_ARG;
+        hp::Params P;
+        P.omega = omega;
+        P.delta = delta;
+        P.seed = seed;
+        P.o = *opt;
+        const int32_t K = P.o.learned_k;
+        hp_options plain = P.o;   // every other option as hp_partition checks it
+        plain.learned_k = 0;
+        if (K < P.o.pi || K > 16 || !hp::options_ok(plain)) return HP_ERR_INVALID_ARG;
+        if (num_nodes > 0 && (!cand_out || !rank_out || !feat_out || (reinterpret_cast<uintptr_t>(feat_out) & 15)))
+            return HP_ERR_INVALID_ARG;
+        P.o.merge_model = nullptr;
+        cudaStream_t s = static_cast<cudaStream_t>(stream);
+        hp::Arena A(s);
+        int32_t *w = A.get<int32_t>(num_hedges);
+        hp::Level L;
+        uint32_t err = hp::validate_and_build_level0(pins, offsets, num_hedges, num_nodes, src_counts, weights, P, L, w,
+                                                     A);
+        if (err) return hp::status_of(err);
+        if (num_nodes == 0) return HP_OK;
+        uint32_t *err_dev = A.get<uint32_t>(1);
+        HPC(cudaMemsetAsync(err_dev, 0, sizeof(uint32_t), s));
+        hp::CoarsenWs *CW = hp::coarsen_workspace(num_nodes, num_hedges, P, A);
+        hp::level_features(L, w, P, *CW, A, err_dev, cand_out, rank_out, feat_out);
+        hp::coarsen_workspace_free(CW, A);
+        const uint32_t e = hp::fetch<uint32_t>(err_dev, s);
+        if (e) return hp::status_of(e);
+        HPC(cudaStreamSynchronize(s));
+        return HP_OK;
+    });
+}
+
+hp_status hp_merge_grad(const uint8_t *feat, const float *label, int64_t count, const float *params, float *grad_out,
+                        double *loss_out, void *stream) {
+    return hp::guarded([&]() -> hp_status {
+        if (count < 0 || !params || !grad_out || (count > 0 && (!feat || !label))) return HP_ERR_INVALID_ARG;
+        cudaStream_t s = static_cast<cudaStream_t>(stream);
+        hp::Arena A(s);
+        const double loss = hp::merge_grad(feat, label, count, params, grad_out, A);
+        if (loss_out) *loss_out = loss;
+        HPC(cudaStreamSynchronize(s));
+        return HP_OK;
+    });
+}
+
+hp_status hp_merge_adam(float *params, const float *grad, float *m, float *v, int64_t step, float lr, float beta1,
+                        float beta2, float eps, float weight_decay, void *stream) {
+    return hp::guarded([&]() -> hp_status {
+        if (!params || !grad || !m || !v || step < 1 || !(lr >= 0.f) || !(beta1 >= 0.f && beta1 < 1.f) ||
+            !(beta2 >= 0.f && beta2 < 1.f) || !(eps > 0.f) || !(weight_decay >= 0.f))
+            return HP_ERR_INVALID_ARG;
+        hp::merge_adam(params, grad, m, v, step, lr, beta1, beta2, eps, weight_decay,
+                       static_cast<cudaStream_t>(stream));
+        return HP_OK;
+    });
+}
+
+hp_status hp_merge_quantize(const float *params, const uint8_t *calib, int64_t count, hp_merge_model *out) {
+    return hp::guarded([&]() -> hp_status {
+        if (!params || !calib || count < 1 || !out) return HP_ERR_INVALID_ARG;
+        for (int i = 0; i < HP_MERGE_NPARAM; i++)
+            if (!std::isfinite(params[i])) return HP_ERR_INVALID_ARG;
+        hp_merge_model m;
+        hp::merge_quantize(params, calib, count, m);
+        *out = m;
+        return HP_OK;
+    });
 }
 
 hp_status hp_merge_scores(const uint8_t *feat, int64_t count, const hp_merge_model *model, int32_t *score_out,

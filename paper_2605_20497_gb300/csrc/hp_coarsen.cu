@@ -1028,8 +1028,11 @@ CoarsenWs *coarsen_workspace(int32_t n, int32_t e, const Params &P, Arena &A) {
     W->cand = A.get<int32_t>((int64_t)n * K);
     W->cscore = A.get<uint64_t>((int64_t)n * K);
     if (P.o.learned_k > 0) {
-        W->model = A.get<hp_merge_model>(1);
-        HPC(cudaMemcpyAsync(W->model, P.o.merge_model, sizeof(hp_merge_model), cudaMemcpyHostToDevice, s));
+        // no model: the workspace of the feature extraction alone
+        if (P.o.merge_model) {
+            W->model = A.get<hp_merge_model>(1);
+            HPC(cudaMemcpyAsync(W->model, P.o.merge_model, sizeof(hp_merge_model), cudaMemcpyHostToDevice, s));
+        }
         W->feat = A.get<uint8_t>((int64_t)n * K * 16);
         W->rank = A.get<int32_t>((int64_t)n * K);
         W->lscore = A.get<int32_t>((int64_t)n * K);
@@ -1116,12 +1119,13 @@ static void dst_groups(const Level &L, int32_t *canon, Arena &A) {
     for (void *p : {(void *)key, (void *)val, (void *)nr, (void *)rp, (void *)rep}) A.release(p);
 }
 
-void coarsen_level(Level &L, int32_t level, const int32_t *w, const Params &P, int32_t *mate, CoarsenWs &W, Arena &A,
-                   uint32_t *err_dev, int32_t *cand_out, uint64_t *score_out, cudaEvent_t *prop_events) {
+// The top-K valid neighbours by (eta, id) of every node of the level into
+// W.cand / W.cscore (Sec. V-C, Eq. 5-6), and the level's counters into the
+// box.  The level must have at least one node.
+static void propose_lists(Level &L, int32_t level, const int32_t *w, const Params &P, int32_t K, CoarsenWs &W,
+                          Arena &A, cudaEvent_t *prop_events) {
     cudaStream_t s = A.stream();
-    const int32_t n = L.n, pi = P.o.pi;
-    const bool learned = P.o.learned_k > 0;
-    const int32_t K = learned ? P.o.learned_k : pi;   // length of the proposal's lists
+    const int32_t n = L.n;
     LevelBox *box = W.box;
     HPC(cudaMemsetAsync(box, 0, sizeof(LevelBox), s));
     if (L.e > 0) {
@@ -1130,8 +1134,6 @@ void coarsen_level(Level &L, int32_t level, const int32_t *w, const Params &P, i
     }
     k_level_cap<<<1, 1, 0, s>>>(&box->qsum, L.e, P.o.noise_permille, &box->cap);
     HP_LAUNCH_CHECK();
-    fill_i32(mate, n, -1, s);
-    if (n == 0) return;
     HPC(cudaMemsetAsync(W.nsum, 0, sizeof(long long) * n, s));
     HPC(cudaMemsetAsync(W.vis, 0, sizeof(long long) * n, s));
     if (L.np > 0) {
@@ -1175,29 +1177,67 @@ void coarsen_level(Level &L, int32_t level, const int32_t *w, const Params &P, i
     }
     if (K <= 4) run_proposal<4>(C, L, P, W, A);
     else run_proposal<16>(C, L, P, W, A);
+}
+
+// the learned priority's view of a level whose top-K lists are in W
+static LearnIn learn_in(const Level &L, int32_t level, const Params &P, int32_t K, CoarsenWs &W) {
+    LearnIn X;
+    X.n = L.n;
+    X.K = K;
+    X.pi = P.o.pi;
+    X.level = level;
+    X.omega = P.omega;
+    X.delta = P.delta;
+    X.size = L.size;
+    X.ioff = L.ioff;
+    X.inc = L.inc;
+    X.nin = L.nin;
+    X.candK = W.cand;
+    X.csK = W.cscore;
+    X.model = W.model;
+    X.feat = W.feat;
+    X.rank = W.rank;
+    X.score = W.lscore;
+    X.cand = W.lcand;
+    X.cscore = W.lcs;
+    return X;
+}
+
+void level_features(Level &L, const int32_t *w, const Params &P, CoarsenWs &W, Arena &A, uint32_t *err_dev,
+                    int32_t *cand_out, int32_t *rank_out, uint8_t *feat_out) {
+    cudaStream_t s = A.stream();
+    const int32_t K = P.o.learned_k;
+    if (L.n == 0) return;
+    propose_lists(L, 0, w, P, K, W, A, nullptr);
+    k_flag_if_nonzero<<<1, 1, 0, s>>>(W.cnt + 4, err_dev);
+    HP_LAUNCH_CHECK();
+    LearnIn X = learn_in(L, 0, P, K, W);
+    X.feat = feat_out;
+    X.rank = rank_out;
+    merge_features(X, s);
+    HPC(cudaMemcpyAsync(cand_out, W.cand, sizeof(int32_t) * L.n * K, cudaMemcpyDeviceToDevice, s));
+}
+
+void coarsen_level(Level &L, int32_t level, const int32_t *w, const Params &P, int32_t *mate, CoarsenWs &W, Arena &A,
+                   uint32_t *err_dev, int32_t *cand_out, uint64_t *score_out, cudaEvent_t *prop_events) {
+    cudaStream_t s = A.stream();
+    const int32_t n = L.n, pi = P.o.pi;
+    const bool learned = P.o.learned_k > 0;
+    const int32_t K = learned ? P.o.learned_k : pi;   // length of the proposal's lists
+    LevelBox *box = W.box;
+    fill_i32(mate, n, -1, s);
+    if (n == 0) {
+        HPC(cudaMemsetAsync(box, 0, sizeof(LevelBox), s));
+        return;
+    }
+    propose_lists(L, level, w, P, K, W, A, prop_events);
     // C(n) and its matching weights
     int32_t *cand = W.cand;
     uint64_t *cscore = W.cscore;
     if (learned) {
-        LearnIn X;
-        X.n = n;
-        X.K = K;
-        X.pi = pi;
-        X.level = level;
-        X.omega = P.omega;
-        X.delta = P.delta;
-        X.size = L.size;
-        X.ioff = L.ioff;
-        X.inc = L.inc;
-        X.nin = L.nin;
-        X.candK = W.cand;
-        X.csK = W.cscore;
-        X.model = W.model;
-        X.feat = W.feat;
-        X.rank = W.rank;
-        X.score = W.lscore;
-        X.cand = cand = W.lcand;
-        X.cscore = cscore = W.lcs;
+        LearnIn X = learn_in(L, level, P, K, W);
+        cand = X.cand;
+        cscore = X.cscore;
         learned_candidates(X, s);
     }
     if (prop_events) HPC(cudaEventRecord(prop_events[1], s));

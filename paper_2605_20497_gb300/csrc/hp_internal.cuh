@@ -336,6 +336,16 @@ struct LearnIn {
     uint64_t *cscore;                         // [n*pi] out: eta of C(n)
 };
 void learned_candidates(const LearnIn &X, cudaStream_t s);
+void merge_features(const LearnIn &X, cudaStream_t s);   // k_merge_feats alone into X.feat / X.rank
+// level-0 top-K lists (K = P.o.learned_k) and the features of every listed pair
+void level_features(Level &L, const int32_t *w, const Params &P, CoarsenWs &W, Arena &A, uint32_t *err_dev,
+                    int32_t *cand_out, int32_t *rank_out, uint8_t *feat_out);
+// training of the merge MLP: mean loss and gradient (synchronises), AdamW step, integer model
+double merge_grad(const uint8_t *feat, const float *label, int64_t count, const float *params, float *grad,
+                  Arena &A);
+void merge_adam(float *p, const float *g, float *m, float *v, int64_t step, float lr, float b1, float b2, float eps,
+                float wd, cudaStream_t s);
+void merge_quantize(const float *params, const uint8_t *calib, int64_t count, hp_merge_model &M);
 void merge_scores(const uint8_t *feat, int64_t count, const hp_merge_model *dmodel, int32_t *out, cudaStream_t s);
 
 // refinement (hp_refine.cu)

@@ -16,6 +16,8 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
+#include <vector>
 
 #include "hp_internal.cuh"
 
@@ -272,7 +274,259 @@ __global__ void k_merge_select(LearnIn X) {
     }
 }
 
+// ---------------------------------------------------------------- training
+// The trainable form: the same network in fp32 on features scaled by 1/256
+// (z1 = W1 x + b1, h1 = relu(z1), z2 = W2 h1 + b2, h2 = relu(z2),
+// o = w3 . h2 + b3), loss = mean binary cross-entropy of sigmoid(o).
+// Parameters, one flat array: W1[64][16], b1[64], W2[64][64], b2[64], w3[64], b3.
+constexpr int NPAR = HP_MERGE_NPARAM;
+constexpr int P_W1 = 0, P_B1 = 1024, P_W2 = 1088, P_B2 = 5184, P_W3 = 5248, P_B3 = 5312;
+static_assert(P_B3 + 1 == NPAR, "parameter layout");
+constexpr int GRAD_CTAS = 256;   // fixed: the reduction order does not depend on the GPU
+constexpr int GRAD_T = 256;
+constexpr int GRAD_R = 32;       // rows per tile
+constexpr int NPAR_PAD = 5376;   // NPAR rounded up to 128 floats
+constexpr size_t GRAD_SMEM = sizeof(float) * (NPAR_PAD + GRAD_R * 16 + 4 * GRAD_R * 64 + GRAD_R);
+
+// One CTA takes a contiguous range of rows, 32 at a time: forward, backward,
+// and the tile's gradient added to per-thread accumulators (thread t owns
+// W2 entries t + 256q, W1 entries t + 256q and one bias or w3 entry).  The
+// CTA's sums go to its own slot of `partial`, summed later in CTA order.
+__global__ void __launch_bounds__(GRAD_T) k_merge_grad(const uint8_t *feat, const float *label, int64_t count,
+                                                        const float *params, float *partial, double *loss_part) {
+    extern __shared__ float sm[];
+    float *sp = sm;
+    float *sx = sp + NPAR_PAD;          // [R][16] scaled features
+    float *sh1 = sx + GRAD_R * 16;      // [R][64]
+    float *sh2 = sh1 + GRAD_R * 64;     // [R][64]
+    float *sd2 = sh2 + GRAD_R * 64;     // [R][64] dL/dz2
+    float *sd1 = sd2 + GRAD_R * 64;     // [R][64] dL/dz1
+    float *sdo = sd1 + GRAD_R * 64;     // [R] dL/do
+    __shared__ double s_loss[GRAD_T / 32];
+    const int tid = threadIdx.x;
+    for (int i = tid; i < NPAR; i += GRAD_T) sp[i] = params[i];
+    const int64_t chunk = (count + gridDim.x - 1) / gridDim.x;
+    const int64_t rb = (int64_t)blockIdx.x * chunk, re = min(count, rb + chunk);
+    float gw2[16], gw1[4], gb = 0.f;
+#pragma unroll
+    for (int q = 0; q < 16; q++) gw2[q] = 0.f;
+#pragma unroll
+    for (int q = 0; q < 4; q++) gw1[q] = 0.f;
+    double loss = 0.0;
+    const float inv_count = count > 0 ? 1.0f / (float)count : 0.f;
+    __syncthreads();
+    for (int64_t r0 = rb; r0 < re; r0 += GRAD_R) {
+        const int nr = (int)(re - r0 < GRAD_R ? re - r0 : GRAD_R);
+        for (int t = tid; t < GRAD_R * 16; t += GRAD_T) {
+            const int r = t >> 4;
+            sx[t] = r < nr ? (float)feat[(r0 + r) * 16 + (t & 15)] * (1.0f / 256.0f) : 0.f;
+        }
+        __syncthreads();
+        for (int t = tid; t < GRAD_R * 64; t += GRAD_T) {
+            const int r = t >> 6, j = t & 63;
+            float z = sp[P_B1 + j];
+#pragma unroll
+            for (int i = 0; i < 16; i++) z = fmaf(sp[P_W1 + j * 16 + i], sx[r * 16 + i], z);
+            sh1[t] = fmaxf(z, 0.f);
+        }
+        __syncthreads();
+        for (int t = tid; t < GRAD_R * 64; t += GRAD_T) {
+            const int r = t >> 6, k = t & 63;
+            float z = sp[P_B2 + k];
+            for (int j = 0; j < 64; j++) z = fmaf(sp[P_W2 + k * 64 + j], sh1[r * 64 + j], z);
+            sh2[t] = fmaxf(z, 0.f);
+        }
+        __syncthreads();
+        if (tid < GRAD_R) {
+            float d = 0.f;
+            if (tid < nr) {
+                float o = sp[P_B3];
+                for (int k = 0; k < 64; k++) o = fmaf(sp[P_W3 + k], sh2[tid * 64 + k], o);
+                const float y = label[r0 + tid];
+                // stable binary cross-entropy of sigmoid(o): max(o,0) - o y + log(1 + e^-|o|)
+                loss += (double)(fmaxf(o, 0.f) - o * y + log1pf(expf(-fabsf(o))));
+                const float p = 1.0f / (1.0f + expf(-o));
+                d = (p - y) * inv_count;
+            }
+            sdo[tid] = d;
+        }
+        __syncthreads();
+        for (int t = tid; t < GRAD_R * 64; t += GRAD_T) {
+            const int r = t >> 6, k = t & 63;
+            sd2[t] = sh2[t] > 0.f ? sdo[r] * sp[P_W3 + k] : 0.f;
+        }
+        __syncthreads();
+        for (int t = tid; t < GRAD_R * 64; t += GRAD_T) {
+            const int r = t >> 6, j = t & 63;
+            float a = 0.f;
+            for (int k = 0; k < 64; k++) a = fmaf(sd2[r * 64 + k], sp[P_W2 + k * 64 + j], a);
+            sd1[t] = sh1[t] > 0.f ? a : 0.f;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < 16; q++) {
+            const int idx = tid + GRAD_T * q, k = idx >> 6, j = idx & 63;
+            float a = gw2[q];
+            for (int r = 0; r < GRAD_R; r++) a = fmaf(sd2[r * 64 + k], sh1[r * 64 + j], a);
+            gw2[q] = a;
+        }
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            const int idx = tid + GRAD_T * q, j = idx >> 4, i = idx & 15;
+            float a = gw1[q];
+            for (int r = 0; r < GRAD_R; r++) a = fmaf(sd1[r * 64 + j], sx[r * 16 + i], a);
+            gw1[q] = a;
+        }
+        if (tid < 64) {
+            for (int r = 0; r < GRAD_R; r++) gb += sd1[r * 64 + tid];
+        } else if (tid < 128) {
+            for (int r = 0; r < GRAD_R; r++) gb += sd2[r * 64 + tid - 64];
+        } else if (tid < 192) {
+            for (int r = 0; r < GRAD_R; r++) gb = fmaf(sdo[r], sh2[r * 64 + tid - 128], gb);
+        } else if (tid == 192) {
+            for (int r = 0; r < GRAD_R; r++) gb += sdo[r];
+        }
+        __syncthreads();
+    }
+    float *pp = partial + (int64_t)blockIdx.x * NPAR;
+#pragma unroll
+    for (int q = 0; q < 16; q++) pp[P_W2 + tid + GRAD_T * q] = gw2[q];
+#pragma unroll
+    for (int q = 0; q < 4; q++) pp[P_W1 + tid + GRAD_T * q] = gw1[q];
+    if (tid < 64) pp[P_B1 + tid] = gb;
+    else if (tid < 128) pp[P_B2 + tid - 64] = gb;
+    else if (tid < 192) pp[P_W3 + tid - 128] = gb;
+    else if (tid == 192) pp[P_B3] = gb;
+    // the loss terms live in the first warp
+    for (int o = 16; o > 0; o >>= 1) loss += __shfl_down_sync(0xffffffffu, loss, o);
+    if ((tid & 31) == 0) s_loss[tid >> 5] = loss;
+    __syncthreads();
+    if (tid == 0) {
+        double t = 0.0;
+        for (int w = 0; w < GRAD_T / 32; w++) t += s_loss[w];
+        loss_part[blockIdx.x] = t;
+    }
+}
+
+// the CTAs' partial gradients summed in CTA order (deterministic)
+__global__ void k_merge_grad_sum(const float *partial, const double *loss_part, int64_t count, float *grad,
+                                 double *loss) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < NPAR) {
+        float a = 0.f;
+        for (int c = 0; c < GRAD_CTAS; c++) a += partial[(int64_t)c * NPAR + i];
+        grad[i] = a;
+    }
+    if (i == 0) {
+        double t = 0.0;
+        for (int c = 0; c < GRAD_CTAS; c++) t += loss_part[c];
+        *loss = count > 0 ? t / (double)count : 0.0;
+    }
+}
+
+// AdamW: m, v moments; c1 = 1 - beta1^t, c2 = 1 - beta2^t
+__global__ void k_merge_adam(float *p, const float *g, float *m, float *v, float lr, float b1, float b2, float eps,
+                             float wd, float c1, float c2) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= NPAR) return;
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    const float mh = mi / c1, vh = vi / c2;
+    p[i] -= lr * (mh / (sqrtf(vh) + eps) + wd * p[i]);
+}
+
+double merge_grad(const uint8_t *feat, const float *label, int64_t count, const float *params, float *grad,
+                  Arena &A) {
+    cudaStream_t s = A.stream();
+    float *partial = A.get<float>((int64_t)GRAD_CTAS * NPAR);
+    double *lp = A.get<double>(GRAD_CTAS + 1);
+    prepare_kernel((const void *)k_merge_grad, GRAD_T, GRAD_SMEM);
+    k_merge_grad<<<GRAD_CTAS, GRAD_T, GRAD_SMEM, s>>>(feat, label, count, params, partial, lp);
+    HP_LAUNCH_CHECK();
+    k_merge_grad_sum<<<(NPAR + 255) / 256, 256, 0, s>>>(partial, lp, count, grad, lp + GRAD_CTAS);
+    HP_LAUNCH_CHECK();
+    const double loss = fetch<double>(lp + GRAD_CTAS, s);
+    A.release(partial);
+    A.release(lp);
+    return loss;
+}
+
+void merge_adam(float *p, const float *g, float *m, float *v, int64_t step, float lr, float b1, float b2, float eps,
+                float wd, cudaStream_t s) {
+    const float c1 = (float)(1.0 - std::pow((double)b1, (double)step));
+    const float c2 = (float)(1.0 - std::pow((double)b2, (double)step));
+    k_merge_adam<<<(NPAR + 255) / 256, 256, 0, s>>>(p, g, m, v, lr, b1, b2, eps, wd, c1, c2);
+    HP_LAUNCH_CHECK();
+}
+
+// Integer model of trained parameters.  With x = f / 256 and a layer's
+// weights scaled by alpha (largest magnitude -> 127), the integer
+// pre-activation is kappa times the float one (kappa = 256 alpha for layer 1,
+// alpha / c for the next, c being the float value of one activation code of
+// the layer below); the shift keeps the calibration rows' largest
+// activation within 255.
+void merge_quantize(const float *P, const uint8_t *calib, int64_t count, hp_merge_model &M) {
+    auto alpha_of = [](const float *w, int k) {
+        double m = 0.0;
+        for (int i = 0; i < k; i++) m = std::max(m, (double)std::fabs(w[i]));
+        return m > 0.0 ? 127.0 / m : 1.0;
+    };
+    auto code = [](double x) { return (int8_t)std::max(-127.0, std::min(127.0, std::nearbyint(x))); };
+    auto bias = [](double x) {
+        const double lim = (double)(1 << 30);
+        return (int32_t)std::max(-lim, std::min(lim, std::nearbyint(x)));
+    };
+    auto shift_for = [](int64_t hmax) {
+        int sft = 0;
+        while (sft < 30 && (hmax >> sft) > 255) sft++;
+        return sft;
+    };
+    const double a1 = alpha_of(P + P_W1, 1024), k1 = 256.0 * a1;
+    for (int j = 0; j < 64; j++) {
+        for (int i = 0; i < 16; i++) M.w1[j][i] = code(P[P_W1 + j * 16 + i] * a1);
+        M.b1[j] = bias(P[P_B1 + j] * k1);
+    }
+    std::vector<int32_t> act1((size_t)count * 64);
+    int64_t hmax = 0;
+    for (int64_t r = 0; r < count; r++)
+        for (int j = 0; j < 64; j++) {
+            int64_t h = M.b1[j];
+            for (int i = 0; i < 16; i++) h += (int64_t)M.w1[j][i] * calib[r * 16 + i];
+            hmax = std::max(hmax, h);
+            act1[(size_t)r * 64 + j] = (int32_t)std::max<int64_t>(h, 0);
+        }
+    M.shift1 = shift_for(hmax);
+    for (auto &h : act1) h = std::min<int32_t>(255, h >> M.shift1);
+    const double c1 = std::ldexp(1.0, M.shift1) / k1;
+    const double a2 = alpha_of(P + P_W2, 4096), k2 = a2 / c1;
+    for (int k = 0; k < 64; k++) {
+        for (int j = 0; j < 64; j++) M.w2[k][j] = code(P[P_W2 + k * 64 + j] * a2);
+        M.b2[k] = bias(P[P_B2 + k] * k2);
+    }
+    hmax = 0;
+    for (int64_t r = 0; r < count; r++)
+        for (int k = 0; k < 64; k++) {
+            int64_t h = M.b2[k];
+            for (int j = 0; j < 64; j++) h += (int64_t)M.w2[k][j] * act1[(size_t)r * 64 + j];
+            hmax = std::max(hmax, h);
+        }
+    M.shift2 = shift_for(hmax);
+    const double c2 = std::ldexp(1.0, M.shift2) / k2;
+    const double a3 = alpha_of(P + P_W3, 64), k3 = a3 / c2;
+    for (int k = 0; k < 64; k++) M.w3[k] = code(P[P_W3 + k] * a3);
+    M.b3 = bias(P[P_B3] * k3);
+}
+
 // ---------------------------------------------------------------- host
+void merge_features(const LearnIn &X, cudaStream_t s) {
+    if (X.n <= 0) return;
+    k_merge_feats<<<grid_for((int64_t)X.n * X.K, 256), 256, 0, s>>>(X);
+    HP_LAUNCH_CHECK();
+}
+
 void merge_scores(const uint8_t *feat, int64_t count, const hp_merge_model *dmodel, int32_t *out, cudaStream_t s) {
     if (count <= 0) return;
     const int64_t tiles = cdiv(count, 16);

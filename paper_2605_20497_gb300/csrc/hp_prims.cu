@@ -116,6 +116,7 @@ template uint32_t fetch<uint32_t>(const uint32_t *, cudaStream_t);
 template uint64_t fetch<uint64_t>(const uint64_t *, cudaStream_t);
 template unsigned long long fetch<unsigned long long>(const unsigned long long *, cudaStream_t);
 template long long fetch<long long>(const long long *, cudaStream_t);
+template double fetch<double>(const double *, cudaStream_t);
 
 int prepare_kernel(const void *func, int block, size_t smem) {
     // per (kernel, device): the dynamic shared memory limit is set on first

@@ -27,7 +27,9 @@ HP_COUNT_INBOUND, HP_COUNT_INCIDENT = 0, 1
 
 EXPORTS = ("hp_default_options", "hp_partition", "hp_partition_ex", "hp_partition_host", "hp_set_allocator",
            "hp_status_string", "hp_last_error", "hp_connectivity", "hp_connectivity_noalloc", "hp_partition_batch", "hp_merge_scores",
-           "hp_debug_coarsen_level", "hp_debug_refine_rep")
+           "hp_merge_features", "hp_merge_grad", "hp_merge_adam", "hp_merge_quantize", "hp_debug_coarsen_level",
+           "hp_debug_refine_rep")
+HP_MERGE_NPARAM = 5313
 
 
 class hp_merge_model(ctypes.Structure):
@@ -111,6 +113,15 @@ def load() -> ctypes.CDLL:
         L.hp_partition_batch.restype = ctypes.c_int
         L.hp_merge_scores.argtypes = [P, ctypes.c_int64, ctypes.POINTER(hp_merge_model), P, P]
         L.hp_merge_scores.restype = ctypes.c_int
+        L.hp_merge_features.argtypes = [P, P, I32, I32, P, P, I32, I32, U64, ctypes.POINTER(hp_options), P, P, P, P]
+        L.hp_merge_features.restype = ctypes.c_int
+        L.hp_merge_grad.argtypes = [P, P, ctypes.c_int64, P, P, ctypes.POINTER(ctypes.c_double), P]
+        L.hp_merge_grad.restype = ctypes.c_int
+        F = ctypes.c_float
+        L.hp_merge_adam.argtypes = [P, P, P, P, ctypes.c_int64, F, F, F, F, F, P]
+        L.hp_merge_adam.restype = ctypes.c_int
+        L.hp_merge_quantize.argtypes = [P, P, ctypes.c_int64, ctypes.POINTER(hp_merge_model)]
+        L.hp_merge_quantize.restype = ctypes.c_int
         L.hp_connectivity_noalloc.argtypes = L.hp_connectivity.argtypes
         L.hp_connectivity_noalloc.restype = ctypes.c_int
         L.hp_debug_coarsen_level.argtypes = [I32, I32, P, P, P, P, P, I32, I32, U64, I32, ctypes.POINTER(hp_options),
@@ -298,4 +309,57 @@ def partition_batch(graphs, concurrency: int = 8, stream=0, **opts):
     torch.cuda.synchronize()
     out = [Result(int(ss[i]), parts[i][: graphs[i][0].num_nodes].cpu().numpy(), _stats_dict(st[i]), [])
            for i in range(n)]
+    return rc, out
+
+
+# ------------------------------------------------------------- learned priority training
+def merge_features(g, omega: int, delta: int, seed: int = 0, learned_k: int = 16, dev=None, stream=0, **opts):
+    """Level-0 training rows of hypergraph g (hp_merge_features): returns
+    (status, cand, rank, feat) as GPU tensors of num_nodes*K entries."""
+    import torch
+    d = dev if dev is not None else to_device(g)
+    n, K = g.num_nodes, learned_k
+    cand = torch.empty(max(n * K, 1), dtype=torch.int32, device="cuda")
+    rank = torch.empty(max(n * K, 1), dtype=torch.int32, device="cuda")
+    feat = torch.empty((max(n * K, 1), 16), dtype=torch.uint8, device="cuda")
+    ptr = lambda x: None if x is None else x.data_ptr()
+    o = options(learned_k=K, **opts)
+    rc = load().hp_merge_features(ptr(d["pins"]), ptr(d["offsets"]), g.num_hedges, n, ptr(d["src_counts"]),
+                                  ptr(d["weights"]), omega, delta, seed & (2**64 - 1), ctypes.byref(o),
+                                  cand.data_ptr(), rank.data_ptr(), feat.data_ptr(), stream)
+    torch.cuda.synchronize()
+    return rc, cand[: n * K], rank[: n * K], feat[: n * K]
+
+
+def merge_grad(feat, label, params, stream=0):
+    """(status, grad, mean loss) of the trainable form over rows feat[count,16]
+    (uint8) with labels label[count] (float32); GPU tensors."""
+    import torch
+    count = feat.shape[0]
+    grad = torch.empty(HP_MERGE_NPARAM, dtype=torch.float32, device=params.device)
+    loss = ctypes.c_double(0.0)
+    rc = load().hp_merge_grad(feat.data_ptr() if count else None, label.data_ptr() if count else None, count,
+                              params.data_ptr(), grad.data_ptr(), ctypes.byref(loss), stream)
+    return rc, grad, loss.value
+
+
+def merge_adam(params, grad, m, v, step, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, weight_decay=0.0, stream=0):
+    return load().hp_merge_adam(params.data_ptr(), grad.data_ptr(), m.data_ptr(), v.data_ptr(), step, lr, beta1,
+                                beta2, eps, weight_decay, stream)
+
+
+def merge_quantize(params, calib):
+    """(status, inputs.MergeModel) from float parameters (numpy float32
+    [HP_MERGE_NPARAM]) and calibration rows (numpy uint8 [count, 16])."""
+    from . import inputs
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    c = np.ascontiguousarray(calib, dtype=np.uint8).reshape(-1, 16)
+    m = hp_merge_model()
+    rc = load().hp_merge_quantize(p.ctypes.data, c.ctypes.data if len(c) else None, len(c), ctypes.byref(m))
+    out = inputs.MergeModel(
+        w1=np.ctypeslib.as_array(m.w1).astype(np.int8).reshape(64, 16).copy(),
+        w2=np.ctypeslib.as_array(m.w2).astype(np.int8).reshape(64, 64).copy(),
+        w3=np.ctypeslib.as_array(m.w3).astype(np.int8).copy(),
+        b1=np.ctypeslib.as_array(m.b1).astype(np.int32).copy(), b2=np.ctypeslib.as_array(m.b2).astype(np.int32).copy(),
+        b3=int(m.b3), shift1=int(m.shift1), shift2=int(m.shift2))
     return rc, out
