@@ -337,6 +337,8 @@ def main():
     ap.add_argument("--learned-k", type=int, default=0,
                     help="partition with the learned merge priority ranking top-K lists (0: the paper's priority)")
     ap.add_argument("--model-seed", type=int, default=0, help="seed of the random-init merge model")
+    ap.add_argument("--model-file", default="",
+                    help="trained merge model (.npz of paper_2605_20497_gb300.train_merge) instead of a random one")
     ap.add_argument("--rows", type=int, default=1 << 24, help="feature rows of the merge_mlp workload")
     ap.add_argument("--count", type=int, default=128, help="instances of the batch workload")
     ap.add_argument("--concurrency", type=int, default=16, help="instances in flight in the batch workload")
@@ -368,7 +370,12 @@ def main():
     stream = torch.cuda.current_stream()
     sp = stream.cuda_stream
     if args.learned_k:
-        opt = hp.options(learned_k=args.learned_k, model=inputs.random_merge_model(args.model_seed))
+        if args.model_file:
+            from paper_2605_20497_gb300 import train_merge
+            model = train_merge.load(args.model_file)
+        else:
+            model = inputs.random_merge_model(args.model_seed)
+        opt = hp.options(learned_k=args.learned_k, model=model)
     else:
         opt = hp.hp_default_options()
     st = hp.hp_stats()
@@ -457,8 +464,10 @@ def main():
         "clocks": clocks,
     }
     if args.learned_k:
+        weights = (f"trained weights {os.path.basename(args.model_file)}" if args.model_file
+                   else f"random-init weights (seed {args.model_seed})")
         out["config"]["merge_priority"] = (f"learned: top-{args.learned_k} lists re-ranked by the integer MLP "
-                                           f"16-64-64-1, random-init weights (seed {args.model_seed})")
+                                           f"16-64-64-1, {weights}")
         out["roofline"]["kernel"] = ("level-0 candidate proposal with top-16 lists, then the learned re-ranking "
                                      "(features, MLP, selection)")
         out["roofline"]["traffic"] = None

@@ -54,7 +54,9 @@ def test_adam_matches_reference(torch):
     t = [torch.from_numpy(a.copy()).cuda() for a in (p, g, m, v)]
     assert hp.merge_adam(t[0], t[1], t[2], t[3], 7, lr=0.01, weight_decay=0.01) == hp.HP_OK
     torch.cuda.synchronize()
-    q, m2, v2 = mt.adamw_step(p, g, m, v, 7, 0.01, 0.9, 0.999, 1e-8, 0.01)
+    # the kernel takes its hyperparameters in fp32: 1 - fp32(0.999) differs from 0.001 by 1.3e-5
+    f = lambda x: float(np.float32(x))
+    q, m2, v2 = mt.adamw_step(p, g, m, v, 7, f(0.01), f(0.9), f(0.999), f(1e-8), f(0.01))
     assert np.allclose(t[0].cpu().numpy(), q, rtol=1e-5, atol=1e-6)
     assert np.allclose(t[2].cpu().numpy(), m2, rtol=1e-5, atol=1e-7)
     assert np.allclose(t[3].cpu().numpy(), v2, rtol=1e-5, atol=1e-9)
