@@ -207,6 +207,39 @@ __device__ void block_emit_top(TopList<PIMAX> &tl, const PropCtx &C, int32_t v, 
     __syncthreads();
 }
 
+// Lists longer than four (PIMAX > 4) are emitted in rounds of four so that
+// every thread keeps a TopList<4> only: round r writes entries r0..r0+nr-1
+// of v's list, the nr best candidates strictly below `thr` (the last entry
+// of the previous round).  Returns the last entry written, the same in every
+// thread of the block; {0, -1} once the candidates run out, below which
+// nothing lies.
+constexpr int EMIT_W = 4;
+__device__ Cand block_emit_range(TopList<EMIT_W> &tl, const PropCtx &C, int32_t v, Cand *s_top, int r0, int nr,
+                                 Cand *s_last) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int r = 0; r < nr; r++) {
+        const Cand b = warp_pop_best(tl);
+        if (lane == 0) s_top[wid * EMIT_W + r] = b;
+    }
+    __syncthreads();
+    if (wid == 0) {
+        TopList<EMIT_W> m;
+        m.init();
+        for (int i = lane; i < nw * nr; i += 32) m.push(s_top[(i / nr) * EMIT_W + (i % nr)]);
+        Cand b{0, -1};
+        for (int r = 0; r < nr; r++) {
+            b = warp_pop_best(m);
+            if (lane == 0) {
+                C.cand[(int64_t)v * C.pi + r0 + r] = b.id;
+                C.cscore[(int64_t)v * C.pi + r0 + r] = b.id >= 0 ? b.eta : 0;
+            }
+        }
+        if (lane == 0) *s_last = b;
+    }
+    __syncthreads();
+    return *s_last;
+}
+
 __device__ __forceinline__ bool pair_valid(const PropCtx &C, int32_t v, int32_t m, int32_t inter) {
     if ((int64_t)C.size[v] + C.size[m] > C.omega) return false;
     return (int64_t)C.nin[v] + C.nin[m] - inter <= C.delta;
@@ -450,22 +483,48 @@ __global__ void __launch_bounds__(BT) k_propose_dense(PropCtx C, const int32_t *
             if (ic) atomicAdd(&inter[m], ic);
         });
         __syncthreads();
-        TopList<PIMAX> tl;
-        tl.init();
-        int32_t cnt = 0;
-        for (int32_t m = threadIdx.x; m < C.n; m += BT) {
-            unsigned long long em = eta[m];
-            if (em) {
-                cnt++;
-                int32_t it = (int32_t)inter[m];
-                if (pair_valid(C, v, m, it)) tl.push(Cand{em + pair_noise(C.level_key, v, m, cap), m});
-                eta[m] = 0;
-                inter[m] = 0;
+        if constexpr (PIMAX <= EMIT_W) {
+            TopList<PIMAX> tl;
+            tl.init();
+            int32_t cnt = 0;
+            for (int32_t m = threadIdx.x; m < C.n; m += BT) {
+                unsigned long long em = eta[m];
+                if (em) {
+                    cnt++;
+                    int32_t it = (int32_t)inter[m];
+                    if (pair_valid(C, v, m, it)) tl.push(Cand{em + pair_noise(C.level_key, v, m, cap), m});
+                    eta[m] = 0;
+                    inter[m] = 0;
+                }
             }
+            int32_t tot = block_sum_i32(cnt, s_tmp);
+            if (threadIdx.x == 0) C.nbcnt[v] = tot;
+            block_emit_top<PIMAX>(tl, C, v, s_top);
+        } else {
+            Cand thr{~0ull, INT32_MAX};
+            for (int r0 = 0; r0 < C.pi; r0 += EMIT_W) {
+                TopList<EMIT_W> tl;
+                tl.init();
+                for (int32_t m = threadIdx.x; m < C.n; m += BT) {
+                    const unsigned long long em = eta[m];
+                    if (em && pair_valid(C, v, m, (int32_t)inter[m])) {
+                        const Cand c{em + pair_noise(C.level_key, v, m, cap), m};
+                        if (cand_gt(thr, c)) tl.push(c);
+                    }
+                }
+                thr = block_emit_range(tl, C, v, s_top, r0, min(EMIT_W, C.pi - r0), &s_top[32 * PIMAX - 1]);
+            }
+            int32_t cnt = 0;
+            for (int32_t m = threadIdx.x; m < C.n; m += BT) {
+                if (eta[m]) {
+                    cnt++;
+                    eta[m] = 0;
+                    inter[m] = 0;
+                }
+            }
+            int32_t tot = block_sum_i32(cnt, s_tmp);
+            if (threadIdx.x == 0) C.nbcnt[v] = tot;
         }
-        int32_t tot = block_sum_i32(cnt, s_tmp);
-        if (threadIdx.x == 0) C.nbcnt[v] = tot;
-        block_emit_top<PIMAX>(tl, C, v, s_top);
     }
 }
 
@@ -525,38 +584,73 @@ __global__ void __launch_bounds__(WP_T) k_propose_warp(PropCtx C, const int32_t 
             warp_insert(keys, eta, inter, mask, cap, m, eq, ic);
         });
         __syncwarp();
-        TopList<PIMAX> tl;
-        tl.init();
-        int32_t cnt = 0;
-        for (uint32_t h = lane; h < cap; h += 32) {
-            const int32_t m = keys[h];
-            if (m >= 0) {
-                cnt++;
-                if (pair_valid(C, v, m, (int32_t)inter[h])) tl.push(Cand{eta[h] + pair_noise(C.level_key, v, m, capn), m});
-                keys[h] = -1;
-                eta[h] = 0;
-                inter[h] = 0;
+        // the warp's best entries r0.. of v's list from the lanes' lists
+        auto emit = [&](auto &tl, int r0, int nr) {
+            Cand last{0, -1};
+            for (int r = 0; r < nr; r++) {
+                Cand best = tl.c[0];
+                int owner = lane;
+                for (int o = 16; o > 0; o >>= 1) {
+                    Cand ob{__shfl_xor_sync(0xffffffffu, best.eta, o), __shfl_xor_sync(0xffffffffu, best.id, o)};
+                    int oo = __shfl_xor_sync(0xffffffffu, owner, o);
+                    if (cand_gt(ob, best)) {
+                        best = ob;
+                        owner = oo;
+                    }
+                }
+                if (lane == 0) {
+                    C.cand[(int64_t)v * C.pi + r0 + r] = best.id;
+                    C.cscore[(int64_t)v * C.pi + r0 + r] = best.id >= 0 ? best.eta : 0;
+                }
+                if (best.id >= 0 && lane == owner) tl.pop();
+                last = best;
             }
-        }
-        __syncwarp();
-        for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
-        if (lane == 0) C.nbcnt[v] = cnt;
-        for (int r = 0; r < C.pi; r++) {
-            Cand best = tl.c[0];
-            int owner = lane;
-            for (int o = 16; o > 0; o >>= 1) {
-                Cand ob{__shfl_xor_sync(0xffffffffu, best.eta, o), __shfl_xor_sync(0xffffffffu, best.id, o)};
-                int oo = __shfl_xor_sync(0xffffffffu, owner, o);
-                if (cand_gt(ob, best)) {
-                    best = ob;
-                    owner = oo;
+            return last;
+        };
+        int32_t cnt = 0;
+        if constexpr (PIMAX <= EMIT_W) {
+            TopList<PIMAX> tl;
+            tl.init();
+            for (uint32_t h = lane; h < cap; h += 32) {
+                const int32_t m = keys[h];
+                if (m >= 0) {
+                    cnt++;
+                    if (pair_valid(C, v, m, (int32_t)inter[h])) tl.push(Cand{eta[h] + pair_noise(C.level_key, v, m, capn), m});
+                    keys[h] = -1;
+                    eta[h] = 0;
+                    inter[h] = 0;
                 }
             }
-            if (lane == 0) {
-                C.cand[(int64_t)v * C.pi + r] = best.id;
-                C.cscore[(int64_t)v * C.pi + r] = best.id >= 0 ? best.eta : 0;
+            __syncwarp();
+            for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+            if (lane == 0) C.nbcnt[v] = cnt;
+            emit(tl, 0, C.pi);
+        } else {
+            // rounds of four, each below the last entry of the round before
+            Cand thr{~0ull, INT32_MAX};
+            for (int r0 = 0; r0 < C.pi; r0 += EMIT_W) {
+                TopList<EMIT_W> tl;
+                tl.init();
+                for (uint32_t h = lane; h < cap; h += 32) {
+                    const int32_t m = keys[h];
+                    if (m >= 0 && pair_valid(C, v, m, (int32_t)inter[h])) {
+                        const Cand c{eta[h] + pair_noise(C.level_key, v, m, capn), m};
+                        if (cand_gt(thr, c)) tl.push(c);
+                    }
+                }
+                thr = emit(tl, r0, min(EMIT_W, C.pi - r0));
             }
-            if (best.id >= 0 && lane == owner) tl.pop();
+            for (uint32_t h = lane; h < cap; h += 32) {
+                if (keys[h] >= 0) {
+                    cnt++;
+                    keys[h] = -1;
+                    eta[h] = 0;
+                    inter[h] = 0;
+                }
+            }
+            __syncwarp();
+            for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+            if (lane == 0) C.nbcnt[v] = cnt;
         }
     }
 }
@@ -603,8 +697,6 @@ __device__ void propose_hashed_node(const PropCtx &C, int32_t v, int32_t *keys, 
     __syncthreads();
     const int overflow = *s_flag;
     const uint64_t capn = *C.cap;
-    TopList<PIMAX> tl;
-    tl.init();
     if (overflow) {
         // the slot list is incomplete: clear the whole table, redo the node in a larger one
         for (uint32_t h = threadIdx.x; h < cap; h += blockDim.x) {
@@ -623,21 +715,53 @@ __device__ void propose_hashed_node(const PropCtx &C, int32_t v, int32_t *keys, 
     }
     // only the occupied slots, from the slot list
     const int32_t used = *(volatile int32_t *)s_cnt;
-    for (int32_t i = threadIdx.x; i < used; i += blockDim.x) {
-        const int32_t h = slots[i];
-        const int32_t m = keys[h];
-        if (pair_valid(C, v, m, (int32_t)inter[h])) tl.push(Cand{eta[h] + pair_noise(C.level_key, v, m, capn), m});
-        keys[h] = -1;
-        eta[h] = 0;
-        inter[h] = 0;
+    if constexpr (PIMAX <= EMIT_W) {
+        TopList<PIMAX> tl;
+        tl.init();
+        for (int32_t i = threadIdx.x; i < used; i += blockDim.x) {
+            const int32_t h = slots[i];
+            const int32_t m = keys[h];
+            if (pair_valid(C, v, m, (int32_t)inter[h])) tl.push(Cand{eta[h] + pair_noise(C.level_key, v, m, capn), m});
+            keys[h] = -1;
+            eta[h] = 0;
+            inter[h] = 0;
+        }
+        int32_t tot = used;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            C.nbcnt[v] = tot;
+            *s_cnt = 0;
+        }
+        block_emit_top<PIMAX>(tl, C, v, s_top);
+    } else {
+        // rounds of four over the slot list, each below the last entry of the round before
+        Cand thr{~0ull, INT32_MAX};
+        for (int r0 = 0; r0 < C.pi; r0 += EMIT_W) {
+            TopList<EMIT_W> tl;
+            tl.init();
+            for (int32_t i = threadIdx.x; i < used; i += blockDim.x) {
+                const int32_t h = slots[i];
+                const int32_t m = keys[h];
+                if (pair_valid(C, v, m, (int32_t)inter[h])) {
+                    const Cand c{eta[h] + pair_noise(C.level_key, v, m, capn), m};
+                    if (cand_gt(thr, c)) tl.push(c);
+                }
+            }
+            thr = block_emit_range(tl, C, v, s_top, r0, min(EMIT_W, C.pi - r0), &s_top[32 * PIMAX - 1]);
+        }
+        for (int32_t i = threadIdx.x; i < used; i += blockDim.x) {
+            const int32_t h = slots[i];
+            keys[h] = -1;
+            eta[h] = 0;
+            inter[h] = 0;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            C.nbcnt[v] = used;
+            *s_cnt = 0;
+        }
+        __syncthreads();
     }
-    int32_t tot = used;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        C.nbcnt[v] = tot;
-        *s_cnt = 0;
-    }
-    block_emit_top<PIMAX>(tl, C, v, s_top);
 }
 
 template <int PIMAX, int BT>
