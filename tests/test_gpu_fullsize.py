@@ -1,7 +1,8 @@
 """Full-size parity: the CUDA path on the layered spiking-network workloads
 (65,536 and 262,144 nodes; the second is the one bench.py times, in the same
 call configuration) and on the random one of 16,384 nodes with 127 targets
-each, against the oracle's results stored by
+each (also with the learned merge priority and a seeded random model),
+against the oracle's results stored by
 tests/golden/make_oracle_golden.py.  The oracle takes minutes on these, so
 its part vector is compared by hash, with its statistics and its per-level
 trace compared value by value."""
@@ -35,16 +36,20 @@ def sha(a) -> str:
     return hashlib.sha256(np.ascontiguousarray(a, dtype="<i4").tobytes()).hexdigest()
 
 
-@pytest.mark.parametrize("name", ["layered_snn_65k", "layered_snn_262k", "random_snn_16k"])
+@pytest.mark.parametrize("name", ["layered_snn_65k", "layered_snn_262k", "random_snn_16k", "random_snn_16k_learned"])
 def test_fullsize_matches_stored_oracle(torch, name):
     with open(os.path.join(GOLDEN, f"oracle_{name}.json")) as f:
         gold = json.load(f)
-    g = inputs.workload(name)
+    g = inputs.workload(gold["workload"])
+    opts = {}
+    if isinstance(gold["options"], dict):
+        opts = dict(learned_k=gold["options"]["learned_k"],
+                    model=inputs.random_merge_model(gold["options"]["random_merge_model_seed"]))
     h = hashlib.sha256()
     h.update(np.ascontiguousarray(g.offsets, dtype="<i4").tobytes())
     h.update(np.ascontiguousarray(g.pins, dtype="<i4").tobytes())
     assert h.hexdigest() == gold["input_sha256"], "the generator no longer builds the stored input"
-    r = hp.partition(g, gold["omega"], gold["delta"], seed=gold["seed"], trace=True)
+    r = hp.partition(g, gold["omega"], gold["delta"], seed=gold["seed"], trace=True, **opts)
     assert r.status == gold["status"] == hp.HP_OK, hp.hp_last_error()
     for k, v in gold["stats"].items():
         assert r.stats[k] == v, (k, r.stats[k], v)

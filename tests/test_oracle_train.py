@@ -84,3 +84,29 @@ def test_quantise_checks_arguments(lib):
     assert rc == hp.HP_ERR_INVALID_ARG
     rc, _ = hp.merge_quantize(np.zeros(mt.NPARAM, np.float32), np.zeros((0, 16), np.uint8))
     assert rc == hp.HP_ERR_INVALID_ARG
+
+
+def test_model_file_round_trip_and_init(tmp_path):
+    from paper_2605_20497_gb300 import inputs, train_merge
+    m = inputs.random_merge_model(4)
+    path = str(tmp_path / "m.npz")
+    train_merge.save(path, m)
+    back = train_merge.load(path)
+    for k in ("w1", "w2", "w3", "b1", "b2"):
+        assert np.array_equal(getattr(m, k), getattr(back, k)), k
+    assert (back.b3, back.shift1, back.shift2) == (m.b3, m.shift1, m.shift2)
+    p = train_merge.init_params(3)
+    assert p.dtype == np.float32 and p.size == mt.NPARAM
+    assert np.array_equal(p, train_merge.init_params(3)) and not np.array_equal(p, train_merge.init_params(4))
+    assert p[-1] == 0.0 and np.all(np.abs(p[:1024]) <= np.sqrt(6 / 16))
+
+
+def test_shipped_model_is_valid():
+    import os
+    import oracle
+    from paper_2605_20497_gb300 import train_merge
+    path = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "paper_2605_20497_gb300",
+                        "merge_random_snn_16k.npz")
+    m = train_merge.load(path)
+    s = oracle.mlp_scores(np.random.default_rng(0).integers(0, 256, size=(100, 16)).astype(np.uint8), m)
+    assert len(np.unique(s)) > 10   # not a constant model
