@@ -43,6 +43,9 @@ CPU_SAMPLE = ("layered_snn_65k", "layered SNN 8 layers x 16x16 grid x 32 channel
 REF_SAMPLE = ("layered 8x8x8x32", "layered SNN 8 layers x 8x8 grid x 32 channels (16,384 nodes), Omega=4096, "
               "Delta=65536")
 METRIC = "pins partitioned/s on 1 GB300"
+GRAPHS = [WORKLOAD, "layered_snn_65k", "random_snn_16k", "random_snn_4k", "gaussian_layered_snn_4m"]
+L2_BYTES = 129_000_000       # GB300 L2
+L2_FLUSH_BYTES = 256 << 20   # a write this large evicts it
 CLOCK_QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
                "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -139,9 +142,10 @@ def proposal_bytes(stats: dict, num_pins: int, num_nodes: int, pi: int = 4) -> i
             + num_nodes * (12 * pi + 4))
 
 
-def traffic_for_current_kernel():
+def traffic_for_current_kernel(workload: str = WORKLOAD):
     """DRAM bytes per launch of the level-0 proposal from the committed ncu
-    summary, if it was taken on the current kernel source (else None)."""
+    summary, if it was taken on the current kernel source and on this
+    workload (else None)."""
     p = os.path.join(ROOT, "profiles", "roofline_traffic.json")
     if not os.path.exists(p):
         return None
@@ -149,7 +153,7 @@ def traffic_for_current_kernel():
         d = json.load(f)
     src = os.path.join(ROOT, "paper_2605_20497_gb300", "csrc", "hp_coarsen.cu")
     h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    if d.get("source_sha256_16") != h or d.get("workload") != WORKLOAD:
+    if d.get("source_sha256_16") != h or d.get("workload") != workload:
         return None
     return d.get("dram_bytes_per_launch")
 
@@ -340,6 +344,8 @@ def main():
     ap.add_argument("--model-file", default="",
                     help="trained merge model (.npz of paper_2605_20497_gb300.train_merge) instead of a random one")
     ap.add_argument("--rows", type=int, default=1 << 24, help="feature rows of the merge_mlp workload")
+    ap.add_argument("--graph", default=WORKLOAD, choices=GRAPHS,
+                    help="the hypergraph one partition step runs on (named workloads of the input generators)")
     ap.add_argument("--count", type=int, default=128, help="instances of the batch workload")
     ap.add_argument("--concurrency", type=int, default=16, help="instances in flight in the batch workload")
     args = ap.parse_args()
@@ -362,9 +368,12 @@ def main():
     __graft_entry__.build()
     from paper_2605_20497_gb300 import hp, inputs
 
-    g = inputs.workload(WORKLOAD)
-    omega, delta = inputs.CONSTRAINTS[WORKLOAD]
+    g = inputs.workload(args.graph)
+    omega, delta = inputs.CONSTRAINTS[args.graph]
     d = hp.to_device(g)
+    in_bytes = int(g.offsets.nbytes + g.pins.nbytes)
+    # inputs that fit in L2: a 256 MB write before every timed step evicts them
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda") if in_bytes <= L2_BYTES else None
     n = g.num_nodes
     part = torch.empty(n, dtype=torch.int32, device="cuda")
     stream = torch.cuda.current_stream()
@@ -381,6 +390,8 @@ def main():
     st = hp.hp_stats()
 
     def step():
+        if flush is not None:
+            flush.fill_(1)
         rc = hp.hp_partition(d["pins"].data_ptr(), d["offsets"].data_ptr(), g.num_hedges, n, None, None, omega,
                              delta, 0, ctypes.byref(opt), part.data_ptr(), ctypes.byref(st), sp)
         if rc != hp.HP_OK:
@@ -443,8 +454,12 @@ def main():
         "metric": METRIC, "value": value, "unit": "pins/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "description": WORKLOAD_DESC, "pins": g.num_pins, "nodes": n,
-                   "omega": omega, "delta": delta, "l2": "inputs (254 MB) exceed L2; no flush",
+        "config": {"workload": args.graph,
+                   "description": WORKLOAD_DESC if args.graph == WORKLOAD else (
+                       f"{g.name}: {n} nodes, {g.num_hedges} hyperedges, {g.num_pins} pins, seed 0"),
+                   "pins": g.num_pins, "nodes": n, "omega": omega, "delta": delta,
+                   "l2": (f"inputs ({in_bytes / 1e6:.0f} MB) exceed L2; no flush" if flush is None else
+                          f"inputs ({in_bytes / 1e6:.0f} MB) fit in L2: a 256 MB write before each timed step"),
                    "parallelism": "replicas" if world > 1 else "single",
                    "connectivity": last["connectivity"], "num_parts": last["num_parts"],
                    "violations": last["violations"], "levels": last["levels"],
@@ -453,7 +468,7 @@ def main():
         "e2e": {"value": replica_value(g.num_pins, world, ms_e2e), "unit": "pins/s",
                 "h2d_bytes_per_step": int(g.offsets.nbytes + g.pins.nbytes), "d2h_bytes_per_step": int(4 * n)},
         "roofline": {"bound": "hbm", "kernel": "level-0 candidate proposal (k_propose_smem)", "achieved": achieved,
-                     "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic_for_current_kernel(),
+                     "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic_for_current_kernel(args.graph),
                      "algorithmic_bytes": alg, "ms_per_launch": prop_ms,
                      "peak_source": f"{peak_kind} hbm_gbs",
                      "basis": ("4 B per pin of every incident hyperedge of every node (the Eq. 5 traversal), "

@@ -16,6 +16,9 @@ The shapes follow the spiking-network workloads of the paper's Table I
   of every layer but the last owns a hyperedge to all channels of the 3x3
   window (border-clipped) around its position in the next layer
   (8 x 32 x 32 x 32 = 262,144 nodes, ~63.6M pins).
+* :func:`gaussian_layered_snn` -- a large sparse layered network: 16 grids
+  of 512 x 512 neurons; hyperedge sizes geometric (mean 84, cap 1024),
+  targets Gaussian-local (sigma = 4 cells) in the next layer.
 * :func:`random_hypergraph` -- small irregular hypergraphs for tests
   (optional multi-source hyperedges, weights, isolated nodes).
 
@@ -245,6 +248,135 @@ def planted_components(sizes, edges_per_comp: int, edge_size: int, seed: int = 0
     return _csr(rows, int(sum(sizes)), "planted")
 
 
+def _popcount64(x: np.ndarray) -> np.ndarray:
+    """Set bits of each uint64 (SWAR bit counting, wrapping arithmetic)."""
+    with np.errstate(over="ignore"):
+        x = x - ((x >> np.uint64(1)) & np.uint64(0x5555555555555555))
+        x = (x & np.uint64(0x3333333333333333)) + ((x >> np.uint64(2)) & np.uint64(0x3333333333333333))
+        x = (x + (x >> np.uint64(4))) & np.uint64(0x0F0F0F0F0F0F0F0F)
+        return ((x * np.uint64(0x0101010101010101)) >> np.uint64(56)).astype(np.int64)
+
+
+def _geometric_thresholds(mean: int, cap: int) -> np.ndarray:
+    """P(s > k) = (1 - 1/mean)^k for k = 1 .. cap-1, each the correctly
+    rounded double of the exact rational power, ascending."""
+    from fractions import Fraction
+    q = Fraction(mean - 1, mean)
+    t, x = [], Fraction(1)
+    for _ in range(1, cap):
+        x *= q
+        t.append(float(x))
+    return np.asarray(t[::-1], dtype=np.float64)
+
+
+def _gaussian_key(seed: int, stream: int, e: np.ndarray, j: np.ndarray) -> np.ndarray:
+    # counter of draw j of hyperedge e in one of the streams (0 size, 1 rows, 2 columns)
+    return ((np.uint64(seed & 0xFF) << np.uint64(56)) | (np.uint64(stream) << np.uint64(52))
+            | (e.astype(np.uint64) << np.uint64(28)) | j.astype(np.uint64))
+
+
+def gaussian_offsets(seed: int, stream: int, e: np.ndarray, j: np.ndarray) -> np.ndarray:
+    """Centred binomial B(64, 1/2) - 32 of the counters: mean 0, variance 16
+    (sigma = 4 cells), support -32..32; the de Moivre-Laplace approximation of
+    round(N(0, 16)) in exact integer arithmetic."""
+    return _popcount64(splitmix64(_gaussian_key(seed, stream, e, j))) - 32
+
+
+def _gaussian_chunk(args):
+    """Pins and hyperedge sizes of hyperedges a..b-1 of gaussian_layered_snn."""
+    a, b, h, w, mean, cap, seed, rounds = args
+    n_layer = h * w
+    thr = _geometric_thresholds(mean, cap)
+    e = np.arange(a, b, dtype=np.int64)
+    m = b - a
+    u = _uniform01(_gaussian_key(seed, 0, e, np.zeros(m, np.int64)))
+    need = (thr.size - np.searchsorted(thr, u, side="right")).astype(np.int64)   # s - 1
+    lay, y, x = e // n_layer, (e // w) % h, e % w
+    # accepted targets, as packed keys row << 40 | draw << 23 | target offset in the next layer
+    done = []
+    acc = np.zeros(0, np.uint64)
+    have = np.zeros(m, np.int64)
+    next_j = np.zeros(m, np.int64)
+    base_t = (lay + 1) * n_layer
+    M23, M17 = np.uint64((1 << 23) - 1), np.uint64((1 << 17) - 1)
+    for _ in range(rounds):
+        deficit = need - have
+        cnt = np.where(deficit > 0, (deficit * 5 + 3) // 4 + 4, 0)
+        tot = int(cnt.sum())
+        if tot == 0:
+            break
+        rows = np.repeat(np.arange(m, dtype=np.int64), cnt)
+        start = np.cumsum(cnt) - cnt
+        j = next_j[rows] + (np.arange(tot, dtype=np.int64) - start[rows])
+        next_j += cnt
+        ty = y[rows] + gaussian_offsets(seed, 1, e[rows], j)
+        tx = x[rows] + gaussian_offsets(seed, 2, e[rows], j)
+        ok = (ty >= 0) & (ty < h) & (tx >= 0) & (tx < w)
+        new = ((rows[ok].astype(np.uint64) << np.uint64(40)) | (j[ok].astype(np.uint64) << np.uint64(23))
+               | (ty[ok] * w + tx[ok]).astype(np.uint64))
+        # rows still short of targets: their accepted and new draws, first draw of each target
+        allk = np.concatenate([acc, new])
+        rt = ((allk >> np.uint64(40)) << np.uint64(23)) | (allk & M23)   # row, target
+        srt = np.lexsort(((allk >> np.uint64(23)) & M17, rt))
+        rt_s = rt[srt]
+        first = np.ones(rt_s.size, bool)
+        first[1:] = rt_s[1:] != rt_s[:-1]
+        allk = np.sort(allk[srt[first]])                                # by row, then draw
+        r_all = (allk >> np.uint64(40)).astype(np.int64)
+        cnt_r = np.bincount(r_all, minlength=m)
+        rank = np.arange(r_all.size) - (np.cumsum(cnt_r) - cnt_r)[r_all]
+        allk = allk[rank < need[r_all]]
+        r_all = (allk >> np.uint64(40)).astype(np.int64)
+        have = np.where(deficit > 0, np.bincount(r_all, minlength=m), have)   # rows done earlier keep theirs
+        full = have[r_all] == need[r_all]
+        done.append(allk[full])                                          # complete rows leave the loop
+        acc = allk[~full]
+    done.append(acc)
+    allk = np.concatenate(done)
+    acc_r = (allk >> np.uint64(40)).astype(np.int64)
+    acc_t = base_t[acc_r] + (allk & M23).astype(np.int64)
+    srt = np.lexsort((acc_t, acc_r))
+    acc_r, acc_t = acc_r[srt], acc_t[srt]
+    size = 1 + have
+    off = np.cumsum(size) - size
+    out = np.empty(int(size.sum()), dtype=np.int32)
+    out[off] = e
+    rank = np.arange(acc_r.size) - (np.cumsum(have) - have)[acc_r]
+    out[off[acc_r] + 1 + rank] = acc_t
+    return out, size
+
+
+def gaussian_layered_snn(layers: int = 16, h: int = 512, w: int = 512, mean: int = 84, cap: int = 1024,
+                         seed: int = 0, rounds: int = 8, chunk: int = 1 << 16, workers: int = 1) -> Hypergraph:
+    """Large sparse layered network: every node of layers 0..layers-2 owns a
+    hyperedge {itself} + (s - 1) distinct targets in the next layer.  s is
+    geometric with the given mean, capped at `cap` (P(s > k) = (1-1/mean)^k).
+    A target lies at (y + dy, x + dx) in the next layer, with dy, dx drawn
+    from gaussian_offsets (sigma = 4 cells); draws that leave the grid or
+    repeat a target are drawn again.  Redrawing is bounded: `rounds` rounds,
+    each drawing 1.25 x the missing targets + 4; a hyperedge that still lacks
+    targets (only nodes near a border with large s) keeps those it has.
+    Targets are sorted ascending after the source.  Chunks of `chunk`
+    hyperedges are independent; `workers` > 1 generates them in a process
+    pool (started with spawn) with the same result."""
+    n_layer = h * w
+    n, E = layers * n_layer, (layers - 1) * n_layer
+    assert E < (1 << 24) and cap <= 1024 and h <= 1 << 16 and w <= 1 << 16
+    jobs = [(a, min(E, a + chunk), h, w, mean, cap, seed, rounds) for a in range(0, E, chunk)]
+    if workers > 1 and len(jobs) > 1:
+        import multiprocessing
+        from concurrent.futures import ProcessPoolExecutor
+        with ProcessPoolExecutor(max_workers=workers, mp_context=multiprocessing.get_context("spawn")) as ex:
+            res = list(ex.map(_gaussian_chunk, jobs))
+    else:
+        res = [_gaussian_chunk(j) for j in jobs]
+    offs = np.zeros(E + 1, dtype=np.int64)
+    np.cumsum(np.concatenate([r[1] for r in res]) if res else np.zeros(0, np.int64), out=offs[1:])
+    assert offs[-1] < (1 << 31)
+    pins = np.concatenate([r[0] for r in res]) if res else np.zeros(0, np.int32)
+    return Hypergraph(n, offs.astype(np.int32), pins, None, None, f"gaussian_layered_snn_{layers}x{h}x{w}")
+
+
 def workload(name: str, seed: int = 0) -> Hypergraph:
     """Named workloads used by the benchmark and the parity tests."""
     if name == "random_snn_4k":
@@ -257,6 +389,9 @@ def workload(name: str, seed: int = 0) -> Hypergraph:
         return layered_snn(4, 16, 16, 16)
     if name == "layered_snn_65k":
         return layered_snn(8, 16, 16, 32)
+    if name == "gaussian_layered_snn_4m":
+        import os
+        return gaussian_layered_snn(16, 512, 512, 84, 1024, seed, workers=min(16, os.cpu_count() or 1))
     raise KeyError(name)
 
 
@@ -268,6 +403,7 @@ CONSTRAINTS = {
     "layered_snn_262k": (1 << 12, 1 << 16),
     "layered_snn_16k": (1 << 10, 1 << 14),
     "layered_snn_65k": (1 << 12, 1 << 16),
+    "gaussian_layered_snn_4m": (1 << 12, 1 << 16),
 }
 
 
