@@ -224,7 +224,14 @@ def run_batch(args):
     for i, ((g, om, de, sd), d) in enumerate(zip(graphs, devs)):
         arr[i] = hp.hp_instance(ptr(d["pins"]), ptr(d["offsets"]), None, None, g.num_hedges, g.num_nodes, om, de, sd,
                                 parts[i].data_ptr())
-    opt = hp.hp_default_options()
+    plain = hp.hp_default_options()
+    if args.learned_k:
+        from paper_2605_20497_gb300 import train_merge
+        model = (train_merge.load(args.model_file) if args.model_file
+                 else inputs.random_merge_model(args.model_seed))
+        opt = hp.options(learned_k=args.learned_k, model=model)
+    else:
+        opt = plain
     stats = (hp.hp_stats * len(graphs))()
     status = (ctypes.c_int32 * len(graphs))()
     stream = torch.cuda.current_stream()
@@ -237,11 +244,12 @@ def run_batch(args):
             raise RuntimeError(hp.hp_last_error())
 
     def seq_step():
+        # the same instances one after another with the paper's priority
         st = hp.hp_stats()
         for i, (g, om, de, sd) in enumerate(graphs):
             x = arr[i]
             rc = hp.hp_partition(x.pins, x.offsets, g.num_hedges, g.num_nodes, None, None, om, de, sd,
-                                 ctypes.byref(opt), x.part_out, ctypes.byref(st), stream.cuda_stream)
+                                 ctypes.byref(plain), x.part_out, ctypes.byref(st), stream.cuda_stream)
             if rc != hp.HP_OK:
                 raise RuntimeError(hp.hp_last_error())
 
@@ -265,7 +273,8 @@ def run_batch(args):
            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
            "config": {"workload": f"batch of {len(graphs)} power-law SNN hypergraphs", "pins": pins,
                       "nodes": sum(g.num_nodes for g, _, _, _ in graphs), "concurrency": args.concurrency,
-                      "sequential_ms": ms_seq, "speedup_vs_sequential": ms_seq / ms,
+                      "merge_priority": (f"learned (top-{args.learned_k})" if args.learned_k else "plain"),
+                      "sequential_plain_ms": ms_seq, "speedup_vs_sequential_plain": ms_seq / ms,
                       "violations": int(sum(stats[i].violations for i in range(len(graphs))))},
            "clocks": clk.summary()}
     print(json.dumps(out), flush=True)
