@@ -132,9 +132,12 @@ def _lc(x):
     return min(255, 1 + 4 * b + (top3 & 3))
 
 
-@pytest.mark.parametrize("seed", [0, 1, 2])
-def test_features_brute_force(seed):
+@pytest.mark.parametrize("seed,incident", [(0, False), (1, False), (2, False), (3, True)])
+def test_features_brute_force(seed, incident):
     g = inputs.random_hypergraph(60, 90, 7, seed=seed, multi_src=True)
+    if incident:   # every pin a destination: in(v) = I(v)
+        g = inputs.Hypergraph(num_nodes=g.num_nodes, offsets=g.offsets, pins=g.pins,
+                              src_counts=np.zeros(g.num_hedges, np.int32))
     rng = np.random.default_rng(seed)
     size = rng.integers(1, 4, size=g.num_nodes).astype(np.int32)
     omega, delta, K, level = 9, 14, 8, 3
@@ -284,3 +287,33 @@ def test_learned_options_checked():
     assert oracle.partition(g, 8, 40, learned_k=16).status == oracle.ERR_INVALID_ARG   # no model
     assert oracle.partition(g, 8, 40, learned_k=3, model=zero_model()).status == oracle.ERR_INVALID_ARG   # K < Pi
     assert oracle.partition(g, 8, 40, learned_k=17, model=zero_model()).status == oracle.ERR_INVALID_ARG
+
+
+def test_hand_derived_example():
+    """tests/golden/learned_small.json: features, scores and C(n) of a 5-node
+    level, each derived by hand (the derivation is in the file)."""
+    import json
+    import os
+    d = json.load(open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "learned_small.json")))
+    g = inputs.Hypergraph(num_nodes=d["num_nodes"], offsets=np.array(d["offsets"], np.int32),
+                          pins=np.array(d["pins"], np.int32))
+    size = np.ones(d["num_nodes"], np.int32)
+    K, pi = d["K"], d["pi"]
+    candK, csK = oracle.propose(g, size, d["omega"], d["delta"], seed=0, level=d["level"], pi=K,
+                                permille=d["permille"])
+    assert candK.tolist() == d["cand_K"]
+    m = inputs.constant_merge_model(0)
+    m.b1[0], m.w1[0, 0], m.w2[0, 0], m.w3[0] = (d["model"][k] for k in ("b1_0", "w1_0_0", "w2_0_0", "w3_0"))
+    feat, rank, cand, cs = oracle.learned_level(g, size, d["omega"], d["delta"], d["level"], candK.ravel(),
+                                                csK.ravel(), pi, m)
+    s = oracle.mlp_scores(feat, m)
+    for v in range(d["num_nodes"]):
+        for j in range(K):
+            u = candK[v, j]
+            if u < 0:
+                continue
+            assert rank[v * K + j] >= 0
+            assert feat[v * K + j].tolist() == d["features"][f"{v},{u}"], (v, u)
+            assert s[v * K + j] == d["scores"][f"{v},{u}"], (v, u)
+    assert cand.reshape(-1, pi).tolist() == d["C"]
+    assert cs.reshape(-1, pi).tolist() == d["C_eta"]
