@@ -1,7 +1,8 @@
 """Full-size parity: the CUDA path on the layered spiking-network workloads
 (65,536 and 262,144 nodes; the second is the one bench.py times, in the same
 call configuration) and on the random one of 16,384 nodes with 127 targets
-each (also with the learned merge priority and a seeded random model),
+each (the 65k layered and the random one also with the learned merge
+priority and a seeded random model),
 against the oracle's results stored by
 tests/golden/make_oracle_golden.py.  The oracle takes minutes on these, so
 its part vector is compared by hash, with its statistics and its per-level
@@ -36,7 +37,8 @@ def sha(a) -> str:
     return hashlib.sha256(np.ascontiguousarray(a, dtype="<i4").tobytes()).hexdigest()
 
 
-@pytest.mark.parametrize("name", ["layered_snn_65k", "layered_snn_262k", "random_snn_16k", "random_snn_16k_learned"])
+@pytest.mark.parametrize("name", ["layered_snn_65k", "layered_snn_262k", "random_snn_16k", "random_snn_16k_learned",
+                                  "layered_snn_65k_learned"])
 def test_fullsize_matches_stored_oracle(torch, name):
     with open(os.path.join(GOLDEN, f"oracle_{name}.json")) as f:
         gold = json.load(f)
