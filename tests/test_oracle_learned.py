@@ -317,3 +317,23 @@ def test_hand_derived_example():
             assert s[v * K + j] == d["scores"][f"{v},{u}"], (v, u)
     assert cand.reshape(-1, pi).tolist() == d["C"]
     assert cs.reshape(-1, pi).tolist() == d["C_eta"]
+
+
+@pytest.mark.parametrize("case", ["empty", "one_node", "no_hyperedges", "singletons", "two_components"])
+def test_degenerate_inputs_match_plain(case):
+    # with no candidate pairs at all (or only pairs that every priority ranks alike) the
+    # learned priority must give the plain result
+    if case == "empty":
+        g = inputs.Hypergraph(num_nodes=0, offsets=np.zeros(1, np.int32), pins=np.zeros(0, np.int32))
+    elif case == "one_node":
+        g = inputs.Hypergraph(num_nodes=1, offsets=np.array([0, 1], np.int32), pins=np.array([0], np.int32))
+    elif case == "no_hyperedges":
+        g = inputs.Hypergraph(num_nodes=9, offsets=np.zeros(1, np.int32), pins=np.zeros(0, np.int32))
+    elif case == "singletons":
+        g = inputs.Hypergraph(num_nodes=6, offsets=np.arange(7, dtype=np.int32), pins=np.arange(6, dtype=np.int32))
+    else:   # two disjoint pairs: each node has exactly one valid neighbour
+        g = inputs.Hypergraph(num_nodes=4, offsets=np.array([0, 2, 4], np.int32), pins=np.array([0, 1, 2, 3], np.int32))
+    plain = oracle.partition(g, 2, 8, seed=3, trace=True)
+    lrn = oracle.partition(g, 2, 8, seed=3, trace=True, learned_k=4, model=inputs.random_merge_model(1))
+    assert plain.status == lrn.status == oracle.OK
+    assert np.array_equal(plain.part, lrn.part) and plain.stats == lrn.stats
