@@ -8,9 +8,11 @@ not.  It shares no code with the CUDA library.
 """
 from __future__ import annotations
 
+import contextlib
 import ctypes
 import os
 import subprocess
+import tempfile
 from dataclasses import dataclass
 
 import numpy as np
@@ -49,6 +51,32 @@ def lib() -> ctypes.CDLL:
         _lib = ctypes.CDLL(build())
         _declare(_lib)
     return _lib
+
+
+@contextlib.contextmanager
+def variant(substitutions):
+    """Runs the wrapper on a copy of the oracle compiled with textual
+    substitutions ``[(old, new), ...]`` (each ``old`` must occur exactly once).
+    Used by the tests that check that a planted mistake fails a pin."""
+    global _lib
+    src = open(_SRC).read()
+    for old, new in substitutions:
+        if src.count(old) != 1:
+            raise ValueError(f"substitution target must occur once: {old!r}")
+        src = src.replace(old, new)
+    with tempfile.TemporaryDirectory() as d:
+        c, so = os.path.join(d, "variant.c"), os.path.join(d, "libvariant.so")
+        with open(c, "w") as f:
+            f.write(src)
+        subprocess.check_call(["gcc", "-O1", "-std=c11", "-fPIC", "-shared", "-o", so, c])
+        saved = lib()
+        v = ctypes.CDLL(so)
+        _declare(v)
+        _lib = v
+        try:
+            yield
+        finally:
+            _lib = saved
 
 
 P = ctypes.c_void_p
@@ -90,6 +118,8 @@ def _declare(L):
     L.or_inseq_and_prefix.restype = I32
     L.or_refine_rep.argtypes = [I32, I32, P, P, P, P, P, P, I32, I32, I32, I32, I32, I32]
     L.or_refine_rep.restype = I32
+    L.or_splitmix64_mix.argtypes = [U64]
+    L.or_splitmix64_mix.restype = U64
 
 
 def _p(a):
@@ -154,6 +184,10 @@ def node_histogram(g, v: int, permille: int = 100):
                                 _p(_i32(g.src_counts)), _p(_i32(g.weights)), v, permille,
                                 _p(eta0), _p(inter), ctypes.byref(cap))
     return k, eta0[:n], inter[:n], int(cap.value)
+
+
+def splitmix64_mix(z: int) -> int:
+    return int(lib().or_splitmix64_mix(ctypes.c_uint64(z & (2**64 - 1))))
 
 
 def pair_noise(seed: int, level: int, a: int, b: int, cap: int) -> int:

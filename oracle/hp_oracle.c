@@ -1383,3 +1383,6 @@ int or_learned_level(int32_t n, int32_t e, const int32_t *off, const int32_t *pi
 }
 
 int32_t or_log_code(uint64_t x) { return log_code(x); }
+
+/* the SplitMix64 output function alone (pinned to the published stream) */
+uint64_t or_splitmix64_mix(uint64_t z) { return splitmix64_mix(z); }
