@@ -484,6 +484,16 @@ def main():
                                "8 B per distinct neighbour, 12 B per incidence entry, 12*pi+4 B per node; the "
                                "kernel walks equal destination lists once per warp group and L2 serves re-reads, "
                                "so its DRAM traffic (ncu, 'traffic') is far below these bytes")},
+        "roofline_step": {
+            "bound": "hbm", "scope": "whole partition (every coarsening level and refinement repetition)",
+            "achieved": last["alg_bytes"] / (ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
+            "frac": last["alg_bytes"] / (ms / 1e3) / 1e9 / peak, "algorithmic_bytes": last["alg_bytes"],
+            "peak_source": f"{peak_kind} hbm_gbs",
+            "basis": ("hp_stats.alg_bytes: per coarsening level the proposal traversal (as in 'roofline'), 48 B "
+                      "per node per matching round and 12 B per pin + 8 B per coarse pin + 16 B per node of "
+                      "contraction; per refinement repetition 12 B per pin + 12 B per pins-list entry when the "
+                      "lists are rebuilt, 4 B per cut incidence entry + 12 B per list entry behind it, 48 B per "
+                      "proposed move; divided by ms_per_step")},
         "gpu_launches": launches,
         "clocks": clocks,
     }

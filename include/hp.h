@@ -85,6 +85,11 @@ typedef enum {
  *   debug_table_cap  0 in normal use; a positive power of two caps the shared-
  *                  memory neighbour table of the proposal kernel so that tests
  *                  can force its overflow path on small inputs (result-neutral)
+ *   debug_walk_cap 0 in normal use; a positive value bounds each tree walk of
+ *                  the matching (Sec. V-D) to that many steps instead of the
+ *                  level's node count, so that a test can make the bounded
+ *                  loop give up: the call then returns HP_ERR_TIMEOUT before
+ *                  the level is contracted
  *   learned_k      0 (default): C(n) is the top-pi valid neighbours by
  *                  (eta, id), as in the paper.  pi..16: the learned merge
  *                  priority below ranks each node's top-learned_k list.
@@ -102,7 +107,7 @@ typedef struct {
     int32_t max_levels;
     int32_t debug_table_cap;
     int32_t learned_k;
-    int32_t reserved;     /* 0 */
+    int32_t debug_walk_cap;
     const hp_merge_model *merge_model;
 } hp_options;
 
@@ -164,6 +169,14 @@ typedef struct {
     int64_t l0_pin_visits;     /* sum_e |e|^2 of level 0: pins read by the level-0 proposal */
     int64_t l0_neighbours;     /* sum over nodes of |N(n)| at level 0 */
     double ms_propose_l0;      /* CUDA-event time of the level-0 candidate proposal (Sec. V-C) */
+    int64_t alg_bytes;         /* algorithmic bytes of the whole call: per coarsening level the
+                                  proposal traversal (4 B per pin visit, 8 B per distinct
+                                  neighbour, 12 B per incidence entry, 12*pi+4 B per node), the
+                                  matching (48 B per node per round) and the contraction (12 B per
+                                  pin, 8 B per coarse pin, 16 B per node); per refinement
+                                  repetition the pins lists when rebuilt (12 B per pin + 12 B per
+                                  list entry), the cut entries and their list entries (4 B + 12 B),
+                                  and 48 B per proposed move */
 } hp_stats;
 
 /* Per-level trace record (optional output of hp_partition_ex). */
@@ -175,6 +188,13 @@ typedef struct {
     int64_t pins;          /* sum_e |e| of the level */
     int64_t conn;          /* connectivity after refining this level */
     int64_t moves;         /* moves applied at this level */
+    /* how the level paired (Sec. V-C, V-D; 0 at the coarsest level): */
+    int32_t valid;         /* nodes with at least one valid neighbour */
+    int32_t iso_list;      /* nodes without one: the best-effort pairing's list */
+    int32_t targets_r1;    /* distinct targets of the first proposal graph */
+    int32_t max_indeg_r1;  /* largest number of nodes targeting one node in it */
+    int32_t pairs_r1;      /* pairs formed by the first matching round */
+    int32_t reserved;
 } hp_level_trace;
 
 HP_API void hp_default_options(hp_options *opt);
@@ -277,10 +297,16 @@ HP_API hp_status hp_connectivity(const int32_t *pins, const int32_t *offsets, in
  *   Scratch: a fixed area inside the loaded library, one per device (256 B of
  *   result words, zeroed by each call on `stream` before use, and an 8 MiB
  *   hash table that is zero at load and that every call returns to zero).
- *   The first call on a device looks up the area's device address with the
- *   device current; make that first call before capturing `stream` into a
- *   graph.  Calls that can overlap on one device (two streams, two host
- *   threads) share the area and race: serialise them.
+ *   The area is device memory of the library, placed on a device when the
+ *   library's kernels are loaded there.  The first call on a device of this
+ *   function, hp_partition, hp_partition_ex, hp_partition_host or
+ *   hp_connectivity loads them (and looks up the area's device address with
+ *   the device current), so a caller that hands all free device memory to
+ *   another pool makes one such call on each device first; make that first
+ *   call before any stream capture too.  The looked-up address belongs to the
+ *   device's context: do not call the library on a device after
+ *   cudaDeviceReset.  Calls that can overlap on one device (two streams, two
+ *   host threads) share the area and race: serialise them.
  *   Limit: a hyperedge of more than 262,144 pins returns HP_ERR_INVALID_ARG
  *   (hp_last_error names the size), with nothing written.
  *   Errors: HP_ERR_BAD_CSR for offsets that are not strictly increasing from

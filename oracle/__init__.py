@@ -31,7 +31,9 @@ DEFAULTS = dict(pi=4, theta=16, chain_window=256, chain_rounds=16, noise_permill
 MODEL_LEN = 64 * 16 + 64 * 64 + 64 * 3 + 3   # layout of the model vector (see hp_oracle.c)
 STAT_KEYS = ("connectivity", "cut_net", "num_parts", "max_part_size", "max_part_distinct",
              "violations", "levels", "moves_applied")
-TRACE_KEYS = ("n", "pins", "pairs", "iso_pairs", "conn", "moves", "reps", "parts")
+TRACE_KEYS = ("n", "pins", "pairs", "iso_pairs", "conn", "moves", "reps", "parts", "valid", "iso_list",
+              "targets_r1", "max_indeg_r1", "pairs_r1")
+TRACE_W = len(TRACE_KEYS)   # layout of a trace record (see hp_oracle.c)
 
 _lib = None
 
@@ -162,14 +164,14 @@ def partition(g, omega: int, delta: int, seed: int = 0, trace: bool = False, mod
     nsrc, w = _i32(g.src_counts), _i32(g.weights)
     part = np.zeros(max(g.num_nodes, 1), dtype=np.int32)
     stats = np.zeros(16, dtype=np.int64)
-    tr = np.zeros(8 * (o["max_levels"] + 1), dtype=np.int64) if trace else None
+    tr = np.zeros(TRACE_W * (o["max_levels"] + 1), dtype=np.int64) if trace else None
     st = lib().or_partition_ml(g.num_nodes, g.num_hedges, _p(off), _p(pins), _p(nsrc), _p(w), omega, delta,
                                ctypes.c_uint64(seed & (2**64 - 1)), _p(optv), _p(mv), _p(part), _p(stats), _p(tr))
     sd = {k: int(stats[i]) for i, k in enumerate(STAT_KEYS)}
     levels = []
     if tr is not None and st == OK:
         for l in range(sd["levels"]):
-            levels.append({k: int(tr[8 * l + i]) for i, k in enumerate(TRACE_KEYS)})
+            levels.append({k: int(tr[TRACE_W * l + i]) for i, k in enumerate(TRACE_KEYS)})
     return Result(st, part[: g.num_nodes], sd, levels)
 
 

@@ -73,7 +73,12 @@ enum { OPT_PI, OPT_THETA, OPT_WINDOW, OPT_ROUNDS, OPT_PERMILLE, OPT_KIND, OPT_MA
 /* stats vector layout */
 enum { ST_CONN, ST_CUTNET, ST_PARTS, ST_MAXSIZE, ST_MAXDIST, ST_VIOL, ST_LEVELS, ST_MOVES, ST_N = 16 };
 /* per-level trace record layout */
-enum { TR_N, TR_PINS, TR_PAIRS, TR_ISOPAIRS, TR_CONN, TR_MOVES, TR_REPS, TR_PARTS, TR_W = 8 };
+/* per-level trace record layout; the last five describe the level's pairing:
+ * nodes with a valid neighbour, nodes left without one (the best-effort
+ * pairing's list), distinct targets and largest in-degree of the first
+ * proposal graph, pairs of the first matching round */
+enum { TR_N, TR_PINS, TR_PAIRS, TR_ISOPAIRS, TR_CONN, TR_MOVES, TR_REPS, TR_PARTS, TR_VALID, TR_ISOLIST, TR_TGT1,
+       TR_MAXIN1, TR_PAIRS1, TR_W };
 
 static void *xcalloc(size_t n, size_t sz)
 {
@@ -366,8 +371,11 @@ static int64_t match_round(int32_t n, const int32_t *target, const uint64_t *sco
     return pairs;
 }
 
-/* Pi rounds; nodes matched earlier leave later proposal graphs (Sec. V-D) */
-static int64_t match_all(int32_t n, int32_t pi, const int32_t *cand, const uint64_t *cscore, int32_t *mate)
+/* Pi rounds; nodes matched earlier leave later proposal graphs (Sec. V-D).
+ * r1 (NULL or 3 values): distinct targets and largest in-degree of the first
+ * proposal graph, pairs formed by the first round. */
+static int64_t match_all(int32_t n, int32_t pi, const int32_t *cand, const uint64_t *cscore, int32_t *mate,
+                         int64_t *r1)
 {
     int32_t *target = xcalloc((size_t)n, sizeof(int32_t));
     uint64_t *score = xcalloc((size_t)n, sizeof(uint64_t));
@@ -389,7 +397,20 @@ static int64_t match_all(int32_t n, int32_t pi, const int32_t *cand, const uint6
                 }
             }
         }
-        pairs += match_round(n, target, score, rmate);
+        if (r == 0 && r1) {
+            int32_t *indeg = xcalloc((size_t)n + 1, sizeof(int32_t));
+            for (int32_t v = 0; v < n; v++)
+                if (target[v] >= 0) indeg[target[v]]++;
+            r1[0] = r1[1] = 0;
+            for (int32_t v = 0; v < n; v++) {
+                if (indeg[v] > 0) r1[0]++;
+                if (indeg[v] > r1[1]) r1[1] = indeg[v];
+            }
+            free(indeg);
+        }
+        int64_t pr = match_round(n, target, score, rmate);
+        if (r == 0 && r1) r1[2] = pr;
+        pairs += pr;
         for (int32_t v = 0; v < n; v++)
             if (rmate[v] >= 0) mate[v] = rmate[v];
     }
@@ -1068,6 +1089,8 @@ int or_partition_ml(int32_t n, int32_t e, const int32_t *off, const int32_t *pin
         int32_t *mate = xcalloc((size_t)g->n, sizeof(int32_t));
         for (int32_t v = 0; v < g->n; v++) mate[v] = -1;
         propose_pairs(g, L, seed, omega, delta, K, o.permille, cand, cs);
+        int64_t nlist = 0;
+        for (int32_t v = 0; v < g->n; v++) nlist += cand[(int64_t)v * K] < 0;
         int64_t iso = pair_isolated(g, K, cand, omega, delta, mate);
         if (o.lk > 0) {
             int32_t *c2 = xcalloc((size_t)g->n * o.pi, sizeof(int32_t));
@@ -1077,9 +1100,19 @@ int or_partition_ml(int32_t n, int32_t e, const int32_t *off, const int32_t *pin
             cand = c2;
             cs = s2;
         }
-        int64_t pairs = iso + match_all(g->n, o.pi, cand, cs, mate);
+        int64_t r1[3] = {0, 0, 0};
+        int64_t pairs = iso + match_all(g->n, o.pi, cand, cs, mate, r1);
         free(cand); free(cs);
-        if (trace) { trace[L * TR_W + TR_PAIRS] = pairs; trace[L * TR_W + TR_ISOPAIRS] = iso; }
+        if (trace) {
+            int64_t *t = trace + (int64_t)L * TR_W;
+            t[TR_PAIRS] = pairs;
+            t[TR_ISOPAIRS] = iso;
+            t[TR_VALID] = g->n - nlist;
+            t[TR_ISOLIST] = nlist;
+            t[TR_TGT1] = r1[0];
+            t[TR_MAXIN1] = r1[1];
+            t[TR_PAIRS1] = r1[2];
+        }
         if (pairs == 0) { free(mate); break; }
         gam[L] = xcalloc((size_t)g->n, sizeof(int32_t));
         contract(g, mate, &lv[L + 1], gam[L]);
@@ -1243,7 +1276,7 @@ int64_t or_match_round(int32_t n, const int32_t *target, const uint64_t *score, 
 
 int64_t or_match_all(int32_t n, int32_t pi, const int32_t *cand, const uint64_t *cscore, int32_t *mate)
 {
-    return match_all(n, pi, cand, cscore, mate);
+    return match_all(n, pi, cand, cscore, mate, NULL);
 }
 
 /* coarse graph into caller arrays sized n (size_out), e+1 (off_out), e

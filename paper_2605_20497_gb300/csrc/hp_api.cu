@@ -58,6 +58,7 @@ static bool options_ok(const hp_options &o) {
         (o.count_kind != HP_COUNT_INBOUND && o.count_kind != HP_COUNT_INCIDENT) || o.max_levels < 0 ||
         o.max_levels > 4096)
         return false;
+    if (o.debug_walk_cap < 0) return false;
     if (o.debug_table_cap != 0) {
         int c = o.debug_table_cap;
         if (c < 64 || c > 65536 || (c & (c - 1))) return false;
@@ -67,6 +68,19 @@ static bool options_ok(const hp_options &o) {
         return false;
     return true;
 }
+
+// releases the level workspaces (streams, events, device memory) when a
+// call ends early with an exception
+struct WsGuard {
+    Arena &A;
+    CoarsenWs *cw = nullptr;
+    LevelWs *rw = nullptr;
+    explicit WsGuard(Arena &a) : A(a) {}
+    ~WsGuard() {
+        coarsen_workspace_free(cw, A);
+        refine_workspace_free(rw, A);
+    }
+};
 
 struct Timer {
     cudaEvent_t a, b, c, p[2];
@@ -99,6 +113,7 @@ static hp_status run(const int32_t *pins, const int32_t *offsets, int32_t e, int
     if (n < 0 || e < 0 || omega < 1 || delta < 0 || !offsets || (n > 0 && !part_out) || !options_ok(P.o) ||
         (trace_cap > 0 && !trace))
         return HP_ERR_INVALID_ARG;
+    noalloc_prepare();
     Timer T(s);
     const int64_t launches0 = t_launches;
     HPC(cudaEventRecord(T.a, s));
@@ -123,7 +138,8 @@ static hp_status run(const int32_t *pins, const int32_t *offsets, int32_t e, int
     const int64_t target_n = ((int64_t)n + omega - 1) / omega;
     int32_t L = 0;
     bool prop0_timed = false;
-    CoarsenWs *CW = coarsen_workspace(n, e, P, A);
+    WsGuard guard(A);
+    CoarsenWs *CW = guard.cw = coarsen_workspace(n, e, P, A);
     int32_t *mate = A.get<int32_t>(n);
     for (;;) {
         hp_level_trace t;
@@ -138,7 +154,21 @@ static hp_status run(const int32_t *pins, const int32_t *offsets, int32_t e, int
         lv.emplace_back();
         LevelBox hb;
         const bool go = contract_level(lv[L], mate, coarsen_box(CW), &hb, lv[L + 1], A);
+        if (hb.err) {
+            // a bounded device loop of the level gave up: its matching is not
+            // to be contracted
+            t_last_error = "device check failed in coarsening level " + std::to_string(L) + " (error bits " +
+                           std::to_string(hb.err) + ")";
+            return status_of(hb.err);
+        }
         st.pin_visits += (int64_t)hb.visits;
+        {
+            // algorithmic bytes of the level (see hp_stats.alg_bytes)
+            const int64_t nl = lv[L].n, pl = lv[L].np, pi = P.o.pi;
+            st.alg_bytes += 4 * (int64_t)hb.visits + 8 * (int64_t)hb.nbrs + 12 * pl + nl * (12 * pi + 4);
+            st.alg_bytes += 48 * pi * nl;
+            st.alg_bytes += 12 * pl + 16 * nl + (go ? 8 * (int64_t)hb.cnp : 0);
+        }
         if (L == 0) {
             prop0_timed = true;
             st.l0_pin_visits = (int64_t)hb.visits;
@@ -146,6 +176,11 @@ static hp_status run(const int32_t *pins, const int32_t *offsets, int32_t e, int
         }
         t.pairs = (int32_t)(hb.pairs + hb.iso);
         t.iso_pairs = (int32_t)hb.iso;
+        t.valid = t.n - hb.isolist;
+        t.iso_list = hb.isolist;
+        t.targets_r1 = hb.ntargets;
+        t.max_indeg_r1 = hb.maxin;
+        t.pairs_r1 = (int32_t)hb.pairs1;
         tr.push_back(t);
         if (!go) {
             lv.pop_back();
@@ -157,6 +192,7 @@ static hp_status run(const int32_t *pins, const int32_t *offsets, int32_t e, int
         L++;
     }
     coarsen_workspace_free(CW, A);
+    guard.cw = nullptr;
     A.release(mate);
     HPC(cudaEventRecord(T.b, s));
 
@@ -165,7 +201,7 @@ static hp_status run(const int32_t *pins, const int32_t *offsets, int32_t e, int
     int32_t *rho = A.get<int32_t>(nparts);
     iota_i32(rho, nparts, s);
     int64_t *obj = A.get<int64_t>(2);
-    LevelWs *RW = refine_workspace(lv[0].n, lv[0].np, lv[0].e, nparts, max_e0, P, A);
+    LevelWs *RW = guard.rw = refine_workspace(lv[0].n, lv[0].np, lv[0].e, nparts, max_e0, P, A);
     for (int32_t l = L; l >= 0; l--) {
         Level &g = lv[l];
         if (l < L) {
@@ -182,6 +218,7 @@ static hp_status run(const int32_t *pins, const int32_t *offsets, int32_t e, int
         }
         RefineOut ro = refine_level(g, w, P, rho, RW, A, err_dev);
         st.moves_applied += ro.moves;
+        st.alg_bytes += ro.alg_bytes;
         tr[l].reps = ro.reps;
         tr[l].moves = ro.moves;
         if (trace_cap > 0 && l < trace_cap) {
@@ -190,6 +227,7 @@ static hp_status run(const int32_t *pins, const int32_t *offsets, int32_t e, int
         }
     }
     refine_workspace_free(RW, A);
+    guard.rw = nullptr;
     HPC(cudaEventRecord(T.c, s));
 
     // ---- compact part ids (ascending internal id) and statistics
@@ -274,7 +312,7 @@ void hp_default_options(hp_options *o) {
     o->max_levels = 256;
     o->debug_table_cap = 0;
     o->learned_k = 0;
-    o->reserved = 0;
+    o->debug_walk_cap = 0;
     o->merge_model = nullptr;
 }
 
@@ -442,6 +480,7 @@ hp_status hp_connectivity(const int32_t *pins, const int32_t *offsets, int32_t n
         if (num_hedges < 0 || num_nodes < 0 || num_parts < 0 || !offsets || (num_nodes > 0 && !part))
             return HP_ERR_INVALID_ARG;
         cudaStream_t s = static_cast<cudaStream_t>(stream);
+        hp::noalloc_prepare();
         hp::Arena A(s);
         hp::Params P;
         P.omega = 1;

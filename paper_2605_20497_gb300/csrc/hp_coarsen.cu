@@ -15,6 +15,7 @@
 #include <algorithm>
 #include <climits>
 
+#include "hp_cluster.cuh"
 #include "hp_internal.cuh"
 
 namespace hp {
@@ -54,9 +55,22 @@ struct PropCtx {
     int32_t omega, delta;
     int32_t *cand;         // [n*pi]
     uint64_t *cscore;      // [n*pi]
-    int32_t *nbcnt;        // [n] unique neighbours found
+    int32_t *nbcnt;        // [n] unique neighbours found (those that pass the size filter)
     const int32_t *canon;  // [e] hyperedges with equal destination lists share a value (or null)
+    int32_t size_filter;   // 1: neighbours m with size(v) + size(m) > Omega are not entered in v's table
 };
+
+// A neighbour that fails the size half of Eq. 6 can never be a candidate,
+// so with the filter on it is not entered in the table at all.  The count of
+// entered neighbours then bounds the size-valid neighbours of the cluster at
+// the next level (sizes only grow), and a node whose bound is 0 has no valid
+// neighbour: result-neutral either way.
+__device__ __forceinline__ int32_t size_slack(const PropCtx &C, int32_t v) {
+    return C.size_filter ? C.omega - C.size[v] : INT32_MAX;
+}
+__device__ __forceinline__ bool size_ok(const PropCtx &C, int32_t slack, int32_t m) {
+    return !C.size_filter || C.size[m] <= slack;
+}
 
 // ---------------------------------------------------------------- per-level weights
 __global__ void k_level_q(const int32_t *off, const int32_t *w, int32_t e, uint64_t *q, unsigned long long *sum) {
@@ -292,6 +306,7 @@ __device__ __forceinline__ void warp_chunk(const PropCtx &C, int32_t v, int32_t 
     }
     const bool large = sz > 32;
     const int32_t len = large ? 0 : sz;
+    const int32_t slack = size_slack(C, v);
     const int jmax = (int)__reduce_max_sync(FULL, (unsigned)len);
     for (int j = 0; j < jmax; j++) {
         int32_t m = j < len ? C.pin[a + j] : -1;
@@ -301,7 +316,8 @@ __device__ __forceinline__ void warp_chunk(const PropCtx &C, int32_t v, int32_t 
         const unsigned lo = __reduce_add_sync(g, on ? (unsigned)(qe & 0x1FFFFFull) : 0u);
         const unsigned hi = __reduce_add_sync(g, on ? (unsigned)(qe >> 21) : 0u);
         const unsigned ic = __reduce_add_sync(g, (on && vin && a + j >= dst0) ? 1u : 0u);
-        if (on && (g & lt) == 0u) ins(m, (unsigned long long)lo + ((unsigned long long)hi << 21), ic);
+        if (on && (g & lt) == 0u && size_ok(C, slack, m))
+            ins(m, (unsigned long long)lo + ((unsigned long long)hi << 21), ic);
     }
     const unsigned bigm = __ballot_sync(FULL, large);
     if (!bigm) return;
@@ -316,7 +332,7 @@ __device__ __forceinline__ void warp_chunk(const PropCtx &C, int32_t v, int32_t 
     if (large)
         for (int32_t j = a; j < dst0; j++) {
             const int32_t m = C.pin[j];
-            if (m != v) ins(m, qe, 0u);
+            if (m != v && size_ok(C, slack, m)) ins(m, qe, 0u);
         }
     if (big) {
         if (lead) (*big)(e, qsum, icnt);
@@ -331,7 +347,7 @@ __device__ __forceinline__ void warp_chunk(const PropCtx &C, int32_t v, int32_t 
         const uint32_t lc = __shfl_sync(FULL, icnt, l);
         for (int32_t j = ld0 + lane; j < lb; j += 32) {
             const int32_t m = C.pin[j];
-            if (m != v) ins(m, lq, lc);
+            if (m != v && size_ok(C, slack, m)) ins(m, lq, lc);
         }
     }
 }
@@ -365,6 +381,7 @@ template <class Ins>
 __device__ void cta_walk(const PropCtx &C, int32_t v, int32_t i0, int32_t deg, int32_t nin_v, const int *stop,
                          BigQueue Q, Ins ins) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int32_t slack = size_slack(C, v);
     auto push = [&](int32_t e, unsigned long long qsum, uint32_t icnt) {
         const int32_t i = atomicAdd(Q.n, 1);
         Q.e[i] = e;
@@ -387,7 +404,7 @@ __device__ void cta_walk(const PropCtx &C, int32_t v, int32_t i0, int32_t deg, i
             while (j < b) {
                 const int32_t m = mn, jn = j + 32;
                 mn = jn < b ? __ldg(&C.pin[jn]) : -1;
-                if (m != v) ins(m, qsum, icnt);
+                if (m != v && size_ok(C, slack, m)) ins(m, qsum, icnt);
                 j = jn;
             }
         }
@@ -837,8 +854,16 @@ constexpr long long WARP_VISITS = 4096, HUB_VISITS = 262144;
 constexpr int32_t HUB_INCIDENCE = 4096;   // incidence entries: chunks of a 512-thread walk
 __global__ void k_tiers(const int32_t *bound, const long long *vis, const int32_t *ioff, int32_t n,
                         uint32_t warp_limit, int32_t dense_bound, int32_t *lW, int32_t *lB, int32_t *lH, int32_t *lD,
-                        int32_t *lDH, int32_t *cnt) {
+                        int32_t *lDH, int32_t *cnt, int32_t pi, int32_t *cand, uint64_t *cscore) {
     GRID_STRIDE(v, (int64_t)n) {
+        if (bound[v] == 0) {
+            // no (size-valid) neighbour: an empty candidate list, no walk
+            for (int32_t r = 0; r < pi; r++) {
+                cand[v * (int64_t)pi + r] = -1;
+                cscore[v * (int64_t)pi + r] = 0;
+            }
+            continue;
+        }
         const bool hub = vis[v] > HUB_VISITS || ioff[v + 1] - ioff[v] > HUB_INCIDENCE;
         if ((uint32_t)bound[v] <= warp_limit && vis[v] <= WARP_VISITS) lW[atomicAdd(&cnt[0], 1)] = (int32_t)v;
         else if (bound[v] > dense_bound) {
@@ -891,7 +916,7 @@ static void run_proposal(const PropCtx &C, Level &L, const Params &P, CoarsenWs 
     const int32_t dense_bound = (C.n <= DENSE_N && dbg == 0) ? (int32_t)(capB / 2) : 0x7fffffff;
     HPC(cudaMemsetAsync(W.cnt, 0, 8 * sizeof(int32_t), s));
     k_tiers<<<grid_of(C.n, 256), 256, 0, s>>>(L.nbnd, W.vis, L.ioff, C.n, wcap / 2, dense_bound, W.lW, W.lB, W.lH,
-                                              W.lD, W.lDH, W.cnt);
+                                              W.lD, W.lDH, W.cnt, C.pi, C.cand, C.cscore);
     HP_LAUNCH_CHECK();
     // the tiers take disjoint node lists, so they run side by side: the warp
     // tier, the dense tier and the hub tier each on a side stream, tier B on
@@ -947,22 +972,29 @@ static void run_proposal(const PropCtx &C, Level &L, const Params &P, CoarsenWs 
 }
 
 // ---------------------------------------------------------------- best-effort pairing
-__global__ void k_iso_flags(const int32_t *cand, int32_t pi, int32_t n, int32_t *flag) {
-    GRID_STRIDE(v, (int64_t)n) flag[v] = cand[(int64_t)v * pi] < 0 ? 1 : 0;
+// Each step is a strided loop (t0, nt): a kernel runs it over its grid, the
+// one-cluster matching kernel over its cluster, with a barrier in between.
+#define CSTRIDE(i, n, t0, nt) for (int64_t i = (t0); i < (int64_t)(n); i += (nt))
+#define K_T0 (blockIdx.x * (int64_t)blockDim.x + threadIdx.x)
+#define K_NT ((int64_t)gridDim.x * blockDim.x)
+
+__device__ __forceinline__ void ph_iso_flags(const int32_t *cand, int32_t pi, int32_t n, int32_t *flag, int64_t t0,
+                                             int64_t nt) {
+    CSTRIDE(v, n, t0, nt) flag[v] = cand[(int64_t)v * pi] < 0 ? 1 : 0;
 }
-__global__ void k_iso_compact(const int32_t *flag, const int32_t *pos, const int32_t *size, int32_t n, uint32_t *keys,
-                              uint32_t *vals) {
-    GRID_STRIDE(v, (int64_t)n) {
+__device__ __forceinline__ void ph_iso_compact(const int32_t *flag, const int32_t *pos, const int32_t *size,
+                                               int32_t n, uint32_t *keys, uint32_t *vals, int64_t t0, int64_t nt) {
+    CSTRIDE(v, n, t0, nt) {
         if (flag[v]) {
             keys[pos[v]] = (uint32_t)size[v];
             vals[pos[v]] = (uint32_t)v;
         }
     }
 }
-__global__ void k_iso_pair(const uint32_t *ids, const int32_t *cntp, const int32_t *size, const int32_t *nin,
-                           int32_t omega, int32_t delta, int32_t *mate, unsigned long long *pairs) {
-    int32_t k = *cntp;
-    GRID_STRIDE(i, (int64_t)(k / 2)) {
+__device__ __forceinline__ void ph_iso_pair(const uint32_t *ids, int32_t k, const int32_t *size, const int32_t *nin,
+                                            int32_t omega, int32_t delta, int32_t *mate, unsigned long long *pairs,
+                                            int64_t t0, int64_t nt) {
+    CSTRIDE(i, k / 2, t0, nt) {
         int32_t a = (int32_t)ids[i], b = (int32_t)ids[k - 1 - i];
         if ((int64_t)size[a] + size[b] <= omega && (int64_t)nin[a] + nin[b] <= delta) {
             mate[a] = b;
@@ -971,12 +1003,24 @@ __global__ void k_iso_pair(const uint32_t *ids, const int32_t *cntp, const int32
         }
     }
 }
+__global__ void k_iso_flags(const int32_t *cand, int32_t pi, int32_t n, int32_t *flag) {
+    ph_iso_flags(cand, pi, n, flag, K_T0, K_NT);
+}
+__global__ void k_iso_compact(const int32_t *flag, const int32_t *pos, const int32_t *size, int32_t n, uint32_t *keys,
+                              uint32_t *vals) {
+    ph_iso_compact(flag, pos, size, n, keys, vals, K_T0, K_NT);
+}
+__global__ void k_iso_pair(const uint32_t *ids, const int32_t *cntp, const int32_t *size, const int32_t *nin,
+                           int32_t omega, int32_t delta, int32_t *mate, unsigned long long *pairs) {
+    ph_iso_pair(ids, *cntp, size, nin, omega, delta, mate, pairs, K_T0, K_NT);
+}
 
 // ---------------------------------------------------------------- matching
-__global__ void k_targets(const int32_t *cand, const uint64_t *cscore, int32_t pi, const int32_t *mate, int32_t n,
-                          int32_t *target, uint64_t *score, long long *sum0, long long *kmax, int32_t *best,
-                          int32_t *ccount, int32_t *pending) {
-    GRID_STRIDE(v, (int64_t)n) {
+__device__ __forceinline__ void ph_targets(const int32_t *cand, const uint64_t *cscore, int32_t pi,
+                                           const int32_t *mate, int32_t n, int32_t *target, uint64_t *score,
+                                           long long *sum0, long long *kmax, int32_t *best, int32_t *ccount,
+                                           int32_t *pending, int64_t t0, int64_t nt) {
+    CSTRIDE(v, n, t0, nt) {
         sum0[v] = 0;
         kmax[v] = LLONG_MIN;
         best[v] = -1;
@@ -1001,14 +1045,24 @@ __global__ void k_targets(const int32_t *cand, const uint64_t *cscore, int32_t p
 }
 
 // |child(n) \ R| per node, twice: the count and the counter of children still to finish
-__global__ void k_child_count(const int32_t *target, int32_t n, int32_t *ccount, int32_t *pending) {
-    GRID_STRIDE(v, (int64_t)n) {
+__device__ __forceinline__ void ph_child_count(const int32_t *target, int32_t n, int32_t *ccount, int32_t *pending,
+                                               int64_t t0, int64_t nt) {
+    CSTRIDE(v, n, t0, nt) {
         int32_t t = target[v];
         if (t >= 0 && target[t] != v) {
             atomicAdd(&ccount[t], 1);
             atomicAdd(&pending[t], 1);
         }
     }
+}
+
+__global__ void k_targets(const int32_t *cand, const uint64_t *cscore, int32_t pi, const int32_t *mate, int32_t n,
+                          int32_t *target, uint64_t *score, long long *sum0, long long *kmax, int32_t *best,
+                          int32_t *ccount, int32_t *pending) {
+    ph_targets(cand, cscore, pi, mate, n, target, score, sum0, kmax, best, ccount, pending, K_T0, K_NT);
+}
+__global__ void k_child_count(const int32_t *target, int32_t n, int32_t *ccount, int32_t *pending) {
+    ph_child_count(target, n, ccount, pending, K_T0, K_NT);
 }
 
 struct DpCtx {
@@ -1021,7 +1075,13 @@ struct DpCtx {
     long long *kmax;                  // max of the children's ss1-0 (accumulated by them)
     int32_t *best;
     uint32_t *err;
+    uint32_t *level_err;              // the level's error word, read by the host before contraction
+    int32_t walk_cap;                 // steps a walk may take (n, or less in the bounded-loop test)
 };
+__device__ __forceinline__ void dp_timeout(const DpCtx &D) {
+    atomicOr(D.err, E_TIMEOUT);
+    atomicOr(D.level_err, E_TIMEOUT);
+}
 
 // Bottom-up (Eq. 7, 8, 10): a thread starts at every leaf and climbs.  A
 // finished child adds its ss0 to the parent's sum0 and raises the parent's
@@ -1031,8 +1091,8 @@ struct DpCtx {
 // single child takes the child's values from registers (plain stores, no
 // fence, no counter).  The best child itself (largest ss1-0, ties to the
 // larger id) is found afterwards by k_best_child.
-__global__ void k_dp_up(DpCtx D) {
-    GRID_STRIDE(v0, (int64_t)D.n) {
+__device__ __forceinline__ void ph_dp_up(const DpCtx &D, int64_t t0, int64_t nt) {
+    CSTRIDE(v0, D.n, t0, nt) {
         int32_t v = (int32_t)v0;
         if (D.ccount[v] != 0) continue;             // not a leaf
         if (D.target[v] < 0) continue;              // isolated, no proposal edge
@@ -1040,8 +1100,8 @@ __global__ void k_dp_up(DpCtx D) {
         bool carried = false;                       // cur's single child's values in registers
         long long cs0 = 0, cmax = 0;
         for (int32_t steps = 0;; steps++) {
-            if (steps > D.n) {
-                atomicOr(D.err, E_TIMEOUT);
+            if (steps > D.walk_cap) {
+                dp_timeout(D);
                 break;
             }
             const int32_t nk = D.ccount[cur];
@@ -1080,8 +1140,8 @@ __global__ void k_dp_up(DpCtx D) {
 
 // best(t) = the child of t (partner root excluded) with the largest ss1-0,
 // ties to the larger id
-__global__ void k_best_child(DpCtx D) {
-    GRID_STRIDE(v0, (int64_t)D.n) {
+__device__ __forceinline__ void ph_best_child(const DpCtx &D, int64_t t0, int64_t nt) {
+    CSTRIDE(v0, D.n, t0, nt) {
         const int32_t v = (int32_t)v0, t = D.target[v];
         if (t >= 0 && D.target[t] != v && __ldcg(&D.ss10[v]) == __ldcg(&D.kmax[t])) atomicMax(&D.best[t], v);
     }
@@ -1090,15 +1150,16 @@ __global__ void k_best_child(DpCtx D) {
 // Top-down (Eq. 11, 12): up(v) = v matched to target(v).  A node is up iff
 // it is its parent's best child with ss1-0 > 0 and the parent is not up; the
 // chain of such links ends at a node that is not up or at a root.
-__global__ void k_dp_down(DpCtx D, const int32_t *target, int32_t *mate, unsigned long long *pairs) {
-    GRID_STRIDE(v0, (int64_t)D.n) {
+__device__ __forceinline__ void ph_dp_down(const DpCtx &D, const int32_t *target, int32_t *mate,
+                                           unsigned long long *pairs, int64_t t0, int64_t nt) {
+    CSTRIDE(v0, D.n, t0, nt) {
         int32_t v = (int32_t)v0;
         if (target[v] < 0) continue;
         int32_t cur = v, k = 0;
         bool base = false;
         for (int32_t steps = 0;; steps++) {
-            if (steps > D.n) {
-                atomicOr(D.err, E_TIMEOUT);
+            if (steps > D.walk_cap) {
+                dp_timeout(D);
                 break;
             }
             int32_t t = target[cur];
@@ -1128,6 +1189,97 @@ __global__ void k_dp_down(DpCtx D, const int32_t *target, int32_t *mate, unsigne
     }
 }
 
+// In-degree of every node in the first proposal graph (its non-root children
+// plus its 2-cycle partner): the number of distinct targets and the largest
+// in-degree go to the level's box (a diagnostic of the pairing).
+__device__ __forceinline__ void ph_indeg(const int32_t *target, const int32_t *ccount, int32_t n, LevelBox *box,
+                                         int64_t t0, int64_t nt) {
+    int32_t mx = 0, cnt = 0;
+    CSTRIDE(v, n, t0, nt) {
+        const int32_t t = target[v];
+        const int32_t d = ccount[v] + ((t >= 0 && target[t] == (int32_t)v) ? 1 : 0);
+        mx = max(mx, d);
+        cnt += d > 0 ? 1 : 0;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        mx = max(mx, __shfl_down_sync(0xffffffffu, mx, o));
+        cnt += __shfl_down_sync(0xffffffffu, cnt, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (mx) atomicMax(&box->maxin, mx);
+        if (cnt) atomicAdd(&box->ntargets, cnt);
+    }
+}
+__global__ void k_indeg(const int32_t *target, const int32_t *ccount, int32_t n, LevelBox *box) {
+    ph_indeg(target, ccount, n, box, K_T0, K_NT);
+}
+__global__ void k_dp_up(DpCtx D) { ph_dp_up(D, K_T0, K_NT); }
+__global__ void k_best_child(DpCtx D) { ph_best_child(D, K_T0, K_NT); }
+__global__ void k_dp_down(DpCtx D, const int32_t *target, int32_t *mate, unsigned long long *pairs) {
+    ph_dp_down(D, target, mate, pairs, K_T0, K_NT);
+}
+
+// ---------------------------------------------------------------- one-cluster matching
+// The best-effort pairing and the pi matching rounds of a level of at most
+// SQ_MAX nodes in one launch: the steps of the multi-kernel form, each a
+// strided loop over the cluster's threads, separated by cluster barriers.
+struct MatchArgs {
+    const int32_t *candK;   // proposal lists (K entries): nodes without a valid neighbour
+    int32_t K;
+    const int32_t *cand;    // C(n) and its weights (pi entries)
+    const uint64_t *cscore;
+    int32_t pi, n, omega, delta;
+    const int32_t *size, *nin;
+    int32_t *flag, *pos;
+    uint32_t *ikeys, *iids;
+    int32_t isobits;
+    int32_t *mate;
+    LevelBox *box;
+    int32_t *target, *ccount;   // the writable views of D's arrays
+    uint64_t *score;
+    DpCtx D;
+};
+__global__ void __cluster_dims__(SQ_CS, 1, 1) __launch_bounds__(SQ_T) k_match_cluster(MatchArgs A) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ uint32_t s_wc[32 * 256];
+    __shared__ uint32_t s_tot[256];
+    __shared__ uint32_t s_base[512];
+    __shared__ int32_t s_tmp[40];
+    __shared__ int32_t s_part;
+    cg::cluster_group cl = cg::this_cluster();
+    const int64_t t0 = (int64_t)cl.block_rank() * blockDim.x + threadIdx.x, nt = (int64_t)SQ_CS * blockDim.x;
+    uint32_t *ka = reinterpret_cast<uint32_t *>(smem), *kb = ka + SQ_CHUNK;
+    uint32_t *va = kb + SQ_CHUNK, *vb = va + SQ_CHUNK, *rk = vb + SQ_CHUNK;
+    const int32_t n = A.n;
+    // best-effort pairing (Sec. V-C): nodes with no valid neighbour, by (size, id)
+    ph_iso_flags(A.candK, A.K, n, A.flag, t0, nt);
+    cl.sync();
+    const int32_t k = cluster_scan_excl(cl, A.flag, A.pos, n, s_tmp, &s_part);
+    if (t0 == 0) A.box->isolist = k;
+    ph_iso_compact(A.flag, A.pos, A.size, n, A.ikeys, A.iids, t0, nt);
+    cl.sync();
+    cluster_radix_sort<uint32_t>(cl, A.ikeys, A.iids, k, (A.isobits + 7) / 8, ka, kb, va, vb, rk, s_wc, s_tot, s_base);
+    ph_iso_pair(A.iids, k, A.size, A.nin, A.omega, A.delta, A.mate, &A.box->iso, t0, nt);
+    cl.sync();
+    // pi rounds of maximum-weight matching (Sec. V-D)
+    const DpCtx &D = A.D;
+    for (int32_t r = 0; r < A.pi; r++) {
+        ph_targets(A.cand, A.cscore, A.pi, A.mate, n, A.target, A.score, D.sum0, D.kmax, D.best, A.ccount, D.pending,
+                   t0, nt);
+        cl.sync();
+        ph_child_count(A.target, n, A.ccount, D.pending, t0, nt);
+        cl.sync();
+        if (r == 0) ph_indeg(A.target, A.ccount, n, A.box, t0, nt);
+        ph_dp_up(D, t0, nt);
+        cl.sync();
+        ph_best_child(D, t0, nt);
+        cl.sync();
+        ph_dp_down(D, D.target, A.mate, &A.box->pairs, t0, nt);
+        cl.sync();
+        if (r == 0 && t0 == 0) A.box->pairs1 = A.box->pairs;
+    }
+}
+
 __global__ void k_sum_i32(const int32_t *x, int32_t n, unsigned long long *sum) {
     unsigned long long loc = 0;
     GRID_STRIDE(i, (int64_t)n) loc += (unsigned long long)x[i];
@@ -1138,9 +1290,26 @@ __global__ void k_flag_if_nonzero(const int32_t *x, uint32_t *err) {
     if (*x) atomicOr(err, E_INTERNAL);
 }
 
+static CoarsenWs *coarsen_workspace_body(CoarsenWs *W, int32_t n, int32_t e, const Params &P, Arena &A);
+
+// on a failure half-way, the streams and events made so far are destroyed
+// (the arena frees the device memory taken so far)
 CoarsenWs *coarsen_workspace(int32_t n, int32_t e, const Params &P, Arena &A) {
-    cudaStream_t s = A.stream();
     CoarsenWs *W = new CoarsenWs();
+    try {
+        return coarsen_workspace_body(W, n, e, P, A);
+    } catch (...) {
+        for (cudaStream_t x : W->side)
+            if (x) cudaStreamDestroy(x);
+        for (cudaEvent_t x : W->ev)
+            if (x) cudaEventDestroy(x);
+        delete W;
+        throw;
+    }
+}
+
+static CoarsenWs *coarsen_workspace_body(CoarsenWs *W, int32_t n, int32_t e, const Params &P, Arena &A) {
+    cudaStream_t s = A.stream();
     for (cudaStream_t &x : W->side) HPC(cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking));
     for (cudaEvent_t &x : W->ev) HPC(cudaEventCreateWithFlags(&x, cudaEventDisableTiming));
     const int32_t pi = P.o.pi, K = P.o.learned_k > 0 ? P.o.learned_k : pi;
@@ -1203,8 +1372,13 @@ CoarsenWs *coarsen_workspace(int32_t n, int32_t e, const Params &P, Arena &A) {
 
 void coarsen_workspace_free(CoarsenWs *W, Arena &A) {
     if (!W) return;
+    // side-stream work must be done before the arena hands its memory back
+    // (it is, unless the call is ending early on an error)
     for (cudaStream_t x : W->side)
-        if (x) cudaStreamDestroy(x);
+        if (x) {
+            (void)cudaStreamSynchronize(x);
+            cudaStreamDestroy(x);
+        }
     for (cudaEvent_t x : W->ev)
         if (x) cudaEventDestroy(x);
     for (void *p : {(void *)W->nsum, (void *)W->vis, (void *)W->q, (void *)W->canon, (void *)W->cand, (void *)W->cscore, (void *)W->lW, (void *)W->lB, (void *)W->lC,
@@ -1291,6 +1465,9 @@ static void propose_lists(Level &L, int32_t level, const int32_t *w, const Param
     C.cscore = W.cscore;
     C.nbcnt = L.nbnd;   // exact counts replace the bounds (used to size the next level)
     C.canon = nullptr;
+    // level 0 of a call has unit sizes (every pair passes when Omega >= 2):
+    // no filter there, no size gathers
+    C.size_filter = level > 0 ? 1 : 0;
     if (prop_events) HPC(cudaEventRecord(prop_events[0], s));   // the grouping counts as proposal time
     if (L.np >= 16 * (int64_t)L.e) {
         // levels of large hyperedges: those with equal destination lists (the
@@ -1374,18 +1551,6 @@ void coarsen_level(Level &L, int32_t level, const int32_t *w, const Params &P, i
         HPC(cudaMemcpyAsync(score_out, cscore, sizeof(uint64_t) * n * pi, cudaMemcpyDeviceToDevice, s));
     }
 
-    // best-effort pairing of nodes with no valid neighbour (Sec. V-C)
-    k_iso_flags<<<grid_of(n, 256), 256, 0, s>>>(W.cand, K, n, W.flag);
-    HP_LAUNCH_CHECK();
-    scan_excl(W.flag, W.pos, n, W.pos + n, A);
-    k_iso_compact<<<grid_of(n, 256), 256, 0, s>>>(W.flag, W.pos, L.size, n, W.ikeys, W.iids);
-    HP_LAUNCH_CHECK();
-    radix_sort_dev(W.ikeys, W.iids, W.pos + n, n, bits_for((uint64_t)P.omega), A);
-    k_iso_pair<<<grid_of(n / 2 + 1, 256), 256, 0, s>>>(W.iids, W.pos + n, L.size, L.nin, P.omega, P.delta, mate,
-                                                         &box->iso);
-    HP_LAUNCH_CHECK();
-
-    // Pi rounds of maximum-weight matching (Sec. V-D)
     DpCtx D;
     D.n = n;
     D.target = W.target;
@@ -1398,18 +1563,49 @@ void coarsen_level(Level &L, int32_t level, const int32_t *w, const Params &P, i
     D.kmax = W.kmax;
     D.best = W.best;
     D.err = err_dev;
+    D.level_err = &box->err;
+    D.walk_cap = P.o.debug_walk_cap > 0 ? std::min(P.o.debug_walk_cap, n) : n;
+    if (n <= SQ_MAX) {
+        // small level: pairing and matching by one cluster, one launch
+        MatchArgs M{W.cand, K, cand, cscore, pi, n, P.omega, P.delta, L.size, L.nin, W.flag, W.pos, W.ikeys, W.iids,
+                    bits_for((uint64_t)P.omega), mate, box, W.target, W.ccount, W.score, D};
+        prepare_kernel((const void *)k_match_cluster, SQ_T, SQ_SMEM);
+        k_match_cluster<<<SQ_CS, SQ_T, SQ_SMEM, s>>>(M);
+        HP_LAUNCH_CHECK();
+        return;
+    }
+
+    // best-effort pairing of nodes with no valid neighbour (Sec. V-C)
+    k_iso_flags<<<grid_of(n, 256), 256, 0, s>>>(W.cand, K, n, W.flag);
+    HP_LAUNCH_CHECK();
+    scan_excl(W.flag, W.pos, n, W.pos + n, A);
+    HPC(cudaMemcpyAsync(&box->isolist, W.pos + n, sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+    k_iso_compact<<<grid_of(n, 256), 256, 0, s>>>(W.flag, W.pos, L.size, n, W.ikeys, W.iids);
+    HP_LAUNCH_CHECK();
+    radix_sort_dev(W.ikeys, W.iids, W.pos + n, n, bits_for((uint64_t)P.omega), A);
+    k_iso_pair<<<grid_of(n / 2 + 1, 256), 256, 0, s>>>(W.iids, W.pos + n, L.size, L.nin, P.omega, P.delta, mate,
+                                                         &box->iso);
+    HP_LAUNCH_CHECK();
+
+    // Pi rounds of maximum-weight matching (Sec. V-D)
     for (int32_t r = 0; r < pi; r++) {
         k_targets<<<grid_of(n, 256), 256, 0, s>>>(cand, cscore, pi, mate, n, W.target, W.score, W.sum0, W.kmax,
                                                   W.best, W.ccount, W.fillpos);
         HP_LAUNCH_CHECK();
         k_child_count<<<grid_of(n, 256), 256, 0, s>>>(W.target, n, W.ccount, W.fillpos);
         HP_LAUNCH_CHECK();
+        if (r == 0) {
+            k_indeg<<<grid_of(n, 256), 256, 0, s>>>(W.target, W.ccount, n, box);
+            HP_LAUNCH_CHECK();
+        }
         k_dp_up<<<grid_of(n, 256), 256, 0, s>>>(D);
         HP_LAUNCH_CHECK();
         k_best_child<<<grid_of(n, 256), 256, 0, s>>>(D);
         HP_LAUNCH_CHECK();
         k_dp_down<<<grid_of(n, 256), 256, 0, s>>>(D, W.target, mate, &box->pairs);
         HP_LAUNCH_CHECK();
+        if (r == 0)
+            HPC(cudaMemcpyAsync(&box->pairs1, &box->pairs, sizeof(unsigned long long), cudaMemcpyDeviceToDevice, s));
     }
 }
 

@@ -304,11 +304,20 @@ struct LevelBox {
     unsigned long long qsum, visits, pairs, iso, nbrs;
     uint64_t cap;      // noise cap of the level
     int32_t cn, cnp;   // nodes and pins of the coarse level
+    uint32_t err;      // error bits raised by the level's matching
+    int32_t isolist;   // nodes without a valid neighbour (the best-effort pairing's list)
+    int32_t ntargets;  // distinct targets of the first proposal graph
+    int32_t maxin;     // largest in-degree of the first proposal graph
+    unsigned long long pairs1;   // pairs of the first matching round
 };
 // Contraction (Sec. V-E): computes the coarse sizes into box_dev, reads the
 // box once into box_host; returns false and builds nothing when the level
 // formed no pair.
 bool contract_level(const Level &L, const int32_t *mate, LevelBox *box_dev, LevelBox *box_host, Level &C, Arena &A);
+
+// loads the no-allocation entry point's module on the current device, once
+// per device (hp_noalloc.cu)
+void noalloc_prepare();
 
 // coarsening (hp_coarsen.cu)
 struct CoarsenWs;
@@ -364,6 +373,7 @@ int32_t refine_rep_debug(const Level &L, const int32_t *w, int32_t nparts, const
 struct RefineOut {
     int64_t moves = 0;
     int32_t reps = 0;
+    int64_t alg_bytes = 0;   // algorithmic bytes of the level's repetitions
 };
 struct LevelWs;
 // refinement workspace for levels of at most n nodes, np pins, e hyperedges

@@ -27,10 +27,20 @@
 // scratch clean.  There is one scratch area per device, so calls that could
 // overlap on one device (two streams, two host threads) race on it and give
 // wrong results: callers serialise them.
+//
+// Placement: the scratch is device memory of this file's module, placed when
+// the module is loaded on a device.  Under CUDA's lazy module loading that
+// would be the first use of one of its kernels or of the array, possibly at
+// a moment when the caller has no free device memory left.  So the
+// library's main entry points (hp_partition*, hp_connectivity) and this call
+// load the module on their first call on each device: they resolve the
+// array's address and query each kernel here (noalloc_prepare below).
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstring>
+#include <mutex>
 #include <string>
 
 #include "hp_internal.cuh"
@@ -53,7 +63,7 @@ constexpr int NA_T = 256;                      // threads of the warp kernel (8 
 constexpr int NA_BIG_T = 1024;                 // threads of the CTA kernels
 
 // result words (64-bit values at even word indices)
-enum : int { W_CONN = 0, W_CUT = 2, W_ERR = 4, W_BAD_EDGE = 5 };
+enum : int { W_CONN = 0, W_CUT = 2, W_ERR = 4, W_BAD_EDGE = 5, W_LARGE = 6 };
 // error bits
 enum : uint32_t { NE_CSR = 1u, NE_PART = 2u, NE_WEIGHT = 4u, NE_SIZE = 8u };
 
@@ -151,7 +161,11 @@ __global__ void __launch_bounds__(NA_T) k_na_small(const int32_t *pins, const in
     __syncwarp();
     for (int64_t e = gw; e < num_hedges; e += nw) {
         const int32_t a = off[e], b = off[e + 1];
-        if (b - a > NA_WARP_MAX) continue;
+        if (b - a > NA_WARP_MAX) {
+            // tells k_na_large that it has work
+            if (lane == 0 && b - a > NA_CTA_MAX) atomicOr(&head[W_LARGE], 1u);
+            continue;
+        }
         if (lane == 0) s_cnt[wid] = 0;
         __syncwarp();
         na_distinct(a, b, lane, 32, pins, part, num_nodes, num_parts, s_tab[wid], na_cap_for(b - a), head,
@@ -184,30 +198,41 @@ __global__ void __launch_bounds__(NA_BIG_T) k_na_mid(const int32_t *pins, const 
 }
 
 // hyperedges of more than NA_CTA_MAX pins: NA_REGIONS CTAs, each with its
-// own region of the scratch table; larger than NA_MAX_EDGE is an error
+// own region of the scratch table; larger than NA_MAX_EDGE is an error.
+// Returns at once unless k_na_small saw such a hyperedge; else each CTA
+// reads NA_BIG_T offsets per step and walks the large hyperedges among them.
 __global__ void __launch_bounds__(NA_BIG_T) k_na_large(const int32_t *pins, const int32_t *off, const int32_t *w,
                                                        const int32_t *part, int32_t num_hedges, int32_t num_nodes,
                                                        int32_t num_parts, uint32_t *head, uint32_t *table) {
-    __shared__ int32_t s_cnt;
-    if (!na_sound(head)) return;
+    __shared__ int32_t s_cnt, s_nbig;
+    __shared__ int32_t s_big[NA_BIG_T];
+    if (!na_sound(head) || *(volatile const uint32_t *)&head[W_LARGE] == 0u) return;
     uint32_t *tab = table + (int64_t)blockIdx.x * NA_REGION_SLOTS;
-    for (int64_t e = blockIdx.x; e < num_hedges; e += gridDim.x) {
-        const int32_t a = off[e], b = off[e + 1];
-        if (b - a <= NA_CTA_MAX) continue;
-        if (b - a > NA_MAX_EDGE) {
-            if (threadIdx.x == 0) {
+    for (int64_t base = (int64_t)blockIdx.x * NA_BIG_T; base < num_hedges; base += (int64_t)gridDim.x * NA_BIG_T) {
+        if (threadIdx.x == 0) s_nbig = 0;
+        __syncthreads();
+        const int64_t e = base + threadIdx.x;
+        if (e < num_hedges) {
+            const int32_t len = off[e + 1] - off[e];
+            if (len > NA_MAX_EDGE) {
                 na_flag(head, NE_SIZE);
-                atomicMax((int *)&head[W_BAD_EDGE], b - a);
+                atomicMax((int *)&head[W_BAD_EDGE], len);
+            } else if (len > NA_CTA_MAX) {
+                s_big[atomicAdd(&s_nbig, 1)] = (int32_t)e;
             }
-            continue;
         }
-        if (threadIdx.x == 0) s_cnt = 0;
         __syncthreads();
-        na_distinct(a, b, threadIdx.x, NA_BIG_T, pins, part, num_nodes, num_parts, tab, na_cap_for(b - a), head,
-                    &s_cnt, BlockSync());
-        __syncthreads();
-        if (threadIdx.x == 0) na_add_result(head, na_weight(w, (int32_t)e), s_cnt);
-        __syncthreads();
+        const int32_t nbig = s_nbig;
+        for (int32_t k = 0; k < nbig; k++) {
+            const int32_t eb = s_big[k], a = off[eb], b = off[eb + 1];
+            if (threadIdx.x == 0) s_cnt = 0;
+            __syncthreads();
+            na_distinct(a, b, threadIdx.x, NA_BIG_T, pins, part, num_nodes, num_parts, tab, na_cap_for(b - a),
+                        head, &s_cnt, BlockSync());
+            __syncthreads();
+            if (threadIdx.x == 0) na_add_result(head, na_weight(w, eb), s_cnt);
+            __syncthreads();
+        }
     }
 }
 
@@ -220,20 +245,40 @@ static __device__ __align__(256) uint32_t g_na_scratch[hp::NA_HEAD + hp::NA_TABL
 
 // ------------------------------------------------------------------ C ABI
 namespace {
-// device address of the scratch, looked up once per device
+constexpr int NA_MAX_DEVICES = 64;
+std::atomic<uint32_t *> g_na_addr[NA_MAX_DEVICES];
+std::mutex g_na_mu;
+
+// Device address of the scratch on the current device, looked up once per
+// device with that device current (the first lookup also loads this
+// module's kernels, so the scratch is placed then).  The cached address
+// belongs to the device's context: after cudaDeviceReset it is stale, so a
+// process that resets a device must not call this library on it again.
 uint32_t *na_scratch_of_current_device() {
-    static uint32_t *addr[64] = {};
     int dev = 0;
     HPC(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= 64) throw hp::Error(HP_ERR_INTERNAL, "device index out of range");
-    if (!addr[dev]) {
-        void *p = nullptr;
-        HPC(cudaGetSymbolAddress(&p, g_na_scratch));
-        addr[dev] = static_cast<uint32_t *>(p);
-    }
-    return addr[dev];
+    if (dev < 0 || dev >= NA_MAX_DEVICES) throw hp::Error(HP_ERR_INTERNAL, "device index out of range");
+    uint32_t *a = g_na_addr[dev].load(std::memory_order_acquire);
+    if (a) return a;
+    std::lock_guard<std::mutex> lk(g_na_mu);
+    a = g_na_addr[dev].load(std::memory_order_relaxed);
+    if (a) return a;
+    void *p = nullptr;
+    HPC(cudaGetSymbolAddress(&p, g_na_scratch));
+    cudaFuncAttributes fa;
+    for (const void *f : {(const void *)hp::k_na_check, (const void *)hp::k_na_small, (const void *)hp::k_na_mid,
+                          (const void *)hp::k_na_large})
+        HPC(cudaFuncGetAttributes(&fa, f));
+    a = static_cast<uint32_t *>(p);
+    g_na_addr[dev].store(a, std::memory_order_release);
+    return a;
 }
 }  // namespace
+
+namespace hp {
+// called by the library's main entry points on their first call per device
+void noalloc_prepare() { (void)na_scratch_of_current_device(); }
+}  // namespace hp
 
 extern "C" hp_status hp_connectivity_noalloc(const int32_t *pins, const int32_t *offsets, int32_t num_hedges,
                                              const int32_t *weights, const int32_t *part, int32_t num_nodes,

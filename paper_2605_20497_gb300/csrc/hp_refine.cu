@@ -8,10 +8,13 @@
 // the hyperedge's own pin segment: (p, pins(p,e), pins_in(p,e)).
 #include <cuda_runtime.h>
 
+#include <cstring>
+
 #include <algorithm>
 #include <climits>
 #include <initializer_list>
 
+#include "hp_cluster.cuh"
 #include "hp_internal.cuh"
 
 namespace hp {
@@ -718,12 +721,14 @@ __global__ void k_plist_tiny(const int32_t *off, const int32_t *pin, const int32
 }
 
 // counters of one repetition (device)
-enum { C_CAND, C_MOVES, C_OVF, C_BAD, C_NH, C_BAD0, C_APPLIED, C_NV, C_HUB, C_CW, C_TOUCH, C_TTOUCH, C_N };
+enum { C_CAND, C_MOVES, C_OVF, C_BAD, C_NH, C_BAD0, C_APPLIED, C_NV, C_HUB, C_CW, C_TOUCH, C_TTOUCH,
+       C_ACC,          // three 64-bit byte counters (even index: 8-byte aligned), see k_cut_flags
+       C_N = C_ACC + 6 };
 
-// moves of at most SMALLM are sequenced and validated by one CTA each, with
-// the sorts in shared memory; up to SEQ_MAX they are still sequenced by one
-// CTA (sort buffers in global memory) and validated by the multi-kernel path
-constexpr int SMALLM = 4096, SEQ_T = 1024, SEQ_MAX = 16 * SEQ_T;
+// moves of at most SMALLM are validated by one CTA (k_val_small) with the
+// sorts in shared memory; moves of at most SQ_MAX are sequenced by one
+// thread-block cluster (k_seq_cluster); more take the multi-kernel path
+constexpr int SMALLM = 6144, SEQ_T = 1024;
 
 #define STRIDE(i, n, t0, nt) for (int64_t i = (t0); i < (int64_t)(n); i += (nt))
 #define G_T0 (blockIdx.x * (int64_t)blockDim.x + threadIdx.x)
@@ -783,10 +788,31 @@ __global__ void k_rep_nodes(const int32_t *rho, const int32_t *size, const int32
 // Cut incident hyperedges (|e| >= 2 and more than one part): the only ones
 // that add to conn(v, p) for p != rho(v).  Compacted per node, in incidence
 // order, for the gain kernels.
-__global__ void k_cut_flags(const int32_t *off, const int32_t *inc, const int32_t *lam, int64_t np, int32_t *flag) {
+// Also counts, for the step's algorithmic bytes, the pins-list entries of
+// the level (sum of lambda(e), once per hyperedge: at the entry of its first
+// pin), the cut incidence entries and the list entries the gain kernels walk
+// for them (sum of lambda(e) over cut entries), into acc[0..2].
+__global__ void k_cut_flags(const int32_t *off, const int32_t *pin, const int32_t *inc, const int32_t *inode,
+                            const int32_t *lam, int64_t np, int32_t *flag, unsigned long long *acc) {
+    unsigned long long lsum = 0, cuts = 0, clam = 0;
     GRID_STRIDE(t, np) {
         const int32_t e = inc[t];
-        flag[t] = (off[e + 1] - off[e] >= 2 && lam[e] >= 2) ? 1 : 0;
+        const bool listed = off[e + 1] - off[e] >= 2;   // single-pin hyperedges have no pins list
+        const int32_t f = (listed && lam[e] >= 2) ? 1 : 0;
+        flag[t] = f;
+        if (listed && inode[t] == pin[off[e]]) lsum += (unsigned long long)lam[e];
+        cuts += (unsigned long long)f;
+        if (f) clam += (unsigned long long)lam[e];
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        lsum += __shfl_down_sync(0xffffffffu, lsum, o);
+        cuts += __shfl_down_sync(0xffffffffu, cuts, o);
+        clam += __shfl_down_sync(0xffffffffu, clam, o);
+    }
+    if ((threadIdx.x & 31) == 0 && (lsum | cuts | clam)) {
+        atomicAdd(&acc[0], lsum);
+        atomicAdd(&acc[1], cuts);
+        atomicAdd(&acc[2], clam);
     }
 }
 __global__ void k_cut_fill(const int32_t *inc, const int32_t *flag, const int32_t *cpos, const int32_t *ioff,
@@ -1102,50 +1128,6 @@ __device__ void ph_apply(const int32_t *seqmove, const int32_t *node, const int3
 }
 
 // ---- block-level helpers of the single-CTA kernels (blockDim = SEQ_T)
-__device__ int32_t block_sum(int32_t x, int32_t *s_tmp) {
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
-    if ((threadIdx.x & 31) == 0) s_tmp[threadIdx.x >> 5] = x;
-    __syncthreads();
-    int32_t t = 0;
-    if (threadIdx.x < 32) {
-        t = threadIdx.x < (blockDim.x >> 5) ? s_tmp[threadIdx.x] : 0;
-        for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
-        if (threadIdx.x == 0) s_tmp[32] = t;
-    }
-    __syncthreads();
-    t = s_tmp[32];
-    __syncthreads();
-    return t;
-}
-// exclusive prefix sum of in[0..n) into out, by one CTA
-__device__ void block_scan_excl(const int32_t *in, int32_t *out, int64_t n, int32_t *s_tmp) {
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    int32_t carry = 0;
-    for (int64_t base = 0; base < n; base += blockDim.x) {
-        int64_t i = base + threadIdx.x;
-        int32_t x = i < n ? in[i] : 0, inc = x;
-        for (int o = 1; o < 32; o <<= 1) {
-            int32_t u = __shfl_up_sync(0xffffffffu, inc, o);
-            if (lane >= o) inc += u;
-        }
-        if (lane == 31) s_tmp[wid] = inc;
-        __syncthreads();
-        if (wid == 0) {
-            int32_t y = lane < nw ? s_tmp[lane] : 0, yi = y;
-            for (int o = 1; o < 32; o <<= 1) {
-                int32_t u = __shfl_up_sync(0xffffffffu, yi, o);
-                if (lane >= o) yi += u;
-            }
-            if (lane < nw) s_tmp[lane] = yi - y;
-            if (lane == nw - 1) s_tmp[32] = yi;
-        }
-        __syncthreads();
-        if (i < n) out[i] = carry + s_tmp[wid] + inc - x;
-        carry += s_tmp[32];
-        __syncthreads();
-    }
-}
-
 // the same for int64 values, in place allowed (in == out)
 __device__ void block_scan_excl_ll(const long long *in, long long *out, int64_t n, long long *s_tmp) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -1333,155 +1315,137 @@ __global__ void k_apply(const int32_t *seqmove, const int32_t *node, const int32
     ph_apply(seqmove, node, dst, *lenp, rho, G_T0, G_NT);
 }
 
-// ---------------------------------------------------------------- single-CTA path (M <= SMALLM)
-struct SmallSeqArgs {
+// ---------------------------------------------------------------- cluster path (M <= SQ_MAX)
+// Sort of the moves, chaining rounds, chain order and sequence positions of
+// one repetition by one thread-block cluster (hp_cluster.cuh): every phase is
+// a strided loop over the cluster's threads on the global arrays (L2
+// resident at these sizes), separated by cluster barriers; the two sorts are
+// cluster radix sorts.  Eight times the threads of one CTA, so the latency of
+// each phase's global loads is spread over 8 SMs.
+static_assert(SQ_T == SEQ_T, "cluster CTA size");
+
+struct ClusterSeqArgs {
     Moves M, S;
     uint64_t *keys, *hkeys;
     uint32_t *idx, *heads;
-    uint64_t *gk;   // 2 * SEQ_MAX global sort buffers (used when m > SMALLM)
-    uint32_t *gv;
-    int32_t *pc, *first, *lens, *starts, *cstart, *seqmove, *mvpos, *cnt;
+    int32_t *first, *lens, *starts, *cstart, *seqmove, *mvpos, *cnt;
     ChainCtx C;
     SeqCtx Q;
     int32_t nparts, rounds, packed, gb, nb, sb, cgb;
     long long gbound, cgbound;
 };
-// sort of the moves, chaining rounds, chain order, sequence positions
-// maximum over the CTA (all threads take part; s_ll holds 33 words)
-__device__ long long block_max_ll(long long x, long long *s_ll) {
-    for (int o = 16; o > 0; o >>= 1) x = max(x, __shfl_xor_sync(0xffffffffu, x, o));
-    if ((threadIdx.x & 31) == 0) s_ll[threadIdx.x >> 5] = x;
-    __syncthreads();
-    if (threadIdx.x < 32) {
-        long long y = threadIdx.x < (blockDim.x >> 5) ? s_ll[threadIdx.x] : LLONG_MIN;
-        for (int o = 16; o > 0; o >>= 1) y = max(y, __shfl_xor_sync(0xffffffffu, y, o));
-        if (threadIdx.x == 0) s_ll[32] = y;
-    }
-    __syncthreads();
-    const long long r = s_ll[32];
-    __syncthreads();
-    return r;
-}
-__device__ __forceinline__ int dev_bits(unsigned long long x) { return x ? 64 - __clzll((long long)x) : 0; }
 
-__global__ void __launch_bounds__(SEQ_T) k_seq_small(SmallSeqArgs A) {
+// first[p] = number of sorted moves leaving a part below p, for p in [0, nparts]
+__device__ void ph_first_of(const int32_t *src, int32_t m, int32_t nparts, int32_t *first, int64_t t0, int64_t nt) {
+    STRIDE(p, (int64_t)nparts + 1, t0, nt) {
+        int32_t a = 0, b = m;
+        while (a < b) {
+            const int32_t mid = (a + b) >> 1;
+            if (src[mid] < (int32_t)p) a = mid + 1;
+            else b = mid;
+        }
+        first[p] = a;
+    }
+}
+
+__global__ void __cluster_dims__(SQ_CS, 1, 1) __launch_bounds__(SEQ_T) k_seq_cluster(ClusterSeqArgs A) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ uint32_t s_wc[32 * 256];
-    __shared__ uint32_t s_hist[256 + 33];
+    __shared__ uint32_t s_tot[256];
+    __shared__ uint32_t s_base[512];
     __shared__ int32_t s_tmp[40];
-    __shared__ long long s_ll[33];
+    __shared__ int32_t s_part;
+    __shared__ long long s_ll[34];
+    cg::cluster_group cl = cg::this_cluster();
     const int32_t m = A.cnt[C_MOVES];
-    if (m == 0 || m > SEQ_MAX) return;
-    const int64_t t0 = threadIdx.x, nt = blockDim.x;
-    uint64_t *ka, *kb;
-    uint32_t *va, *vb;
-    if (m <= SMALLM) {
-        ka = reinterpret_cast<uint64_t *>(smem);
-        kb = ka + SMALLM;
-        va = reinterpret_cast<uint32_t *>(kb + SMALLM);
-        vb = va + SMALLM;
-    } else {
-        ka = A.gk;
-        kb = A.gk + SEQ_MAX;
-        va = A.gv;
-        vb = A.gv + SEQ_MAX;
-    }
-    // key widths from this repetition's moves: gains and ids are far below
-    // their static bounds, so the sort takes fewer 8-bit passes
+    if (m == 0 || m > SQ_MAX) return;   // uniform: no CTA of the cluster runs on
+    const int64_t t0 = (int64_t)cl.block_rank() * blockDim.x + threadIdx.x, nt = (int64_t)SQ_CS * blockDim.x;
+    uint64_t *ka = reinterpret_cast<uint64_t *>(smem), *kb = ka + SQ_CHUNK;
+    uint32_t *va = reinterpret_cast<uint32_t *>(kb + SQ_CHUNK), *vb = va + SQ_CHUNK, *rk = vb + SQ_CHUNK;
+    // key widths from this repetition's moves
     long long gmx = 0, smx = 0, nmx = 0;
-    for (int64_t i = t0; i < m; i += nt) {
+    STRIDE(i, m, t0, nt) {
         gmx = max(gmx, A.M.gain[i]);
         smx = max(smx, (long long)A.M.src[i]);
         nmx = max(nmx, (long long)A.M.node[i]);
     }
-    gmx = block_max_ll(gmx, s_ll);
-    smx = block_max_ll(smx, s_ll);
-    nmx = block_max_ll(nmx, s_ll);
+    gmx = cluster_max_ll(cl, gmx, s_ll);
+    smx = cluster_max_ll(cl, smx, s_ll);
+    nmx = cluster_max_ll(cl, nmx, s_ll);
     const int gb = dev_bits((unsigned long long)gmx), nb = dev_bits((unsigned long long)nmx),
               sb = dev_bits((unsigned long long)smx);
+    // sort (p_s asc, gain desc, node asc)
     if (sb + gb + nb <= 64) {
         ph_move_keys(A.M, m, gmx, gb, nb, -1, A.keys, A.idx, 1, t0, nt);
-        block_radix_sort_buf<uint64_t>(A.keys, A.idx, m, (sb + gb + nb + 7) / 8, ka, kb, va, vb, s_wc, s_hist);
+        cl.sync();
+        cluster_radix_sort<uint64_t>(cl, A.keys, A.idx, m, (sb + gb + nb + 7) / 8, ka, kb, va, vb, rk, s_wc, s_tot, s_base);
     } else {
         const int fb[3] = {A.nb, A.gb, A.sb};
         for (int f = 0; f < 3; f++) {
-            __syncthreads();
             ph_move_keys(A.M, m, A.gbound, A.gb, A.nb, f, A.keys, A.idx, f == 0, t0, nt);
-            block_radix_sort_buf<uint64_t>(A.keys, A.idx, m, (fb[f] + 7) / 8, ka, kb, va, vb, s_wc, s_hist);
+            cl.sync();
+            cluster_radix_sort<uint64_t>(cl, A.keys, A.idx, m, (fb[f] + 7) / 8, ka, kb, va, vb, rk, s_wc, s_tot, s_base);
         }
     }
-    ph_gather(A.M, A.idx, m, A.S, A.pc, A.C.size, A.C.nin, const_cast<int32_t *>(A.C.msz),
-              const_cast<int32_t *>(A.C.mni), t0, nt);
-    __syncthreads();
-    block_scan_excl(A.pc, A.first, (int64_t)A.nparts + 1, s_tmp);
-    __syncthreads();
-    // the arrays the window scans read per candidate move (gain, pred, size
-    // and |in| of its node) in shared memory, in the sort buffers, which are
-    // free now
-    ChainCtx CC = A.C;
-    const bool staged = m <= SMALLM;
-    if (staged) {
-        long long *s_gain = reinterpret_cast<long long *>(smem);
-        int32_t *s_pred = reinterpret_cast<int32_t *>(s_gain + SMALLM);
-        int32_t *s_msz = s_pred + SMALLM, *s_mni = s_msz + SMALLM;
-        for (int64_t i = t0; i < m; i += nt) {
-            s_gain[i] = A.C.gain[i];
-            s_pred[i] = A.C.pred[i];
-            s_msz[i] = A.C.msz[i];
-            s_mni[i] = A.C.mni[i];
-        }
-        CC.gain = s_gain;
-        CC.pred = s_pred;
-        CC.msz = s_msz;
-        CC.mni = s_mni;
-        __syncthreads();
+    // the moves in sorted order, with the size and |in| of each moved node
+    STRIDE(i, m, t0, nt) {
+        const uint32_t k = A.idx[i];
+        const int32_t v = A.M.node[k];
+        A.S.node[i] = v;
+        A.S.src[i] = A.M.src[k];
+        A.S.dst[i] = A.M.dst[k];
+        A.S.gain[i] = A.M.gain[k];
+        const_cast<int32_t *>(A.C.msz)[i] = A.C.size[v];
+        const_cast<int32_t *>(A.C.mni)[i] = A.C.nin[v];
     }
-    for (int r = 0; r < A.rounds; r++) {
-        if (r > 0 && !*(volatile int32_t *)&A.C.linked[r - 1]) break;
-        ph_choose(CC, r, A.packed, m, t0, nt);
-        __syncthreads();
+    cl.sync();
+    ph_first_of(A.S.src, m, A.nparts, A.first, t0, nt);
+    cl.sync();
+    // chaining rounds (Sec. VI-C)
+    for (int rr = 0; rr < A.rounds; rr++) {
+        if (rr > 0 && !*(volatile int32_t *)&A.C.linked[rr - 1]) break;
+        ph_choose(A.C, rr, A.packed, m, t0, nt);
+        cl.sync();
         if (!A.packed) {
-            ph_accept_min(CC, m, t0, nt);
-            __syncthreads();
-            ph_accept_id(CC, m, t0, nt);
-            __syncthreads();
+            ph_accept_min(A.C, m, t0, nt);
+            cl.sync();
+            ph_accept_id(A.C, m, t0, nt);
+            cl.sync();
         }
-        ph_link(CC, r, A.packed, m, t0, nt);
-        __syncthreads();
+        ph_link(A.C, rr, A.packed, m, t0, nt);
+        cl.sync();
     }
-    if (staged) {
-        for (int64_t i = t0; i < m; i += nt) A.C.pred[i] = CC.pred[i];
-        __syncthreads();
-    }
+    // chains, ordered by (total gain desc, head node asc)
     ph_path_heads(A.Q, m, t0, nt);
-    __syncthreads();
+    cl.sync();
     ph_cycle_heads(A.Q, m, t0, nt);
-    __syncthreads();
+    cl.sync();
     ph_head_collect(A.Q, m, A.heads, &A.cnt[C_NH], t0, nt);
-    __syncthreads();
+    cl.sync();
     const int32_t nh = *(volatile int32_t *)&A.cnt[C_NH];
     long long cmx = 0;
-    for (int64_t k = t0; k < nh; k += nt) cmx = max(cmx, A.Q.cgain[A.heads[k]]);
-    cmx = block_max_ll(cmx, s_ll);
+    STRIDE(k, nh, t0, nt) cmx = max(cmx, A.Q.cgain[A.heads[k]]);
+    cmx = cluster_max_ll(cl, cmx, s_ll);
     const int cgb = dev_bits((unsigned long long)cmx);
     if (cgb + nb <= 64) {
         ph_head_keys(A.heads, nh, A.Q.cgain, A.S.node, cmx, nb, -1, A.hkeys, t0, nt);
-        block_radix_sort_buf<uint64_t>(A.hkeys, A.heads, nh, (cgb + nb + 7) / 8, ka, kb, va, vb, s_wc, s_hist);
+        cl.sync();
+        cluster_radix_sort<uint64_t>(cl, A.hkeys, A.heads, nh, (cgb + nb + 7) / 8, ka, kb, va, vb, rk, s_wc, s_tot, s_base);
     } else {
         for (int f = 0; f < 2; f++) {
-            __syncthreads();
             ph_head_keys(A.heads, nh, A.Q.cgain, A.S.node, A.cgbound, A.nb, f, A.hkeys, t0, nt);
-            block_radix_sort_buf<uint64_t>(A.hkeys, A.heads, nh, ((f == 0 ? A.nb : A.cgb) + 7) / 8, ka, kb, va, vb,
-                                           s_wc, s_hist);
+            cl.sync();
+            cluster_radix_sort<uint64_t>(cl, A.hkeys, A.heads, nh, ((f == 0 ? A.nb : A.cgb) + 7) / 8, ka, kb, va, vb,
+                                         rk, s_wc, s_tot, s_base);
         }
     }
     ph_chain_lens(A.heads, nh, A.Q.clen, nh, A.lens, t0, nt);
-    __syncthreads();
-    block_scan_excl(A.lens, A.starts, nh, s_tmp);
-    __syncthreads();
+    cl.sync();
+    cluster_scan_excl(cl, A.lens, A.starts, nh, s_tmp, &s_part);
     ph_chain_start(A.heads, nh, A.starts, A.cstart, t0, nt);
-    __syncthreads();
+    cl.sync();
     ph_seq_pos(A.Q.chain, A.Q.pos, A.cstart, m, A.S.node, A.seqmove, A.mvpos, t0, nt);
+    cl.sync();   // no CTA leaves while another may still read its shared memory
 }
 
 // validity of every prefix, best prefix, apply
@@ -1785,10 +1749,13 @@ struct LevelWs {
     int32_t parts_used;                      // parts holding a node at the level's start
     cudaStream_t side = nullptr;             // side stream of the hub gains
     cudaEvent_t ev[2] = {nullptr, nullptr};
+    // algorithmic bytes of the repetitions (host): running total, and the cut
+    // entries and their list entries of the last rebuilt repetition
+    int64_t alg_bytes = 0, cuts = 0, cut_lam = 0;
     int32_t *touched, *ttouched;             // hyperedges with a moved pin (more than / at most 8 pins)
     Moves M, S;
-    uint64_t *keys, *sk;
-    uint32_t *idx, *sv;
+    uint64_t *keys;
+    uint32_t *idx;
     int32_t *msz, *mni;
     int32_t *first, *choice, *accnode, *pos, *clen, *lens, *starts, *cstart, *seqmove;
     unsigned long long *pen, *minpen, *acc1;
@@ -1811,10 +1778,28 @@ struct LevelWs {
     int32_t *pmark; // [nparts] parts in use
 };
 
+static LevelWs *refine_workspace_body(LevelWs *W, int32_t n, int64_t np, int32_t e, int32_t nparts, int32_t max_e,
+                                      const Params &P, Arena &A);
+
+// on a failure half-way, the stream and events made so far are destroyed
+// (the arena frees the device memory taken so far)
 LevelWs *refine_workspace(int32_t n, int64_t np, int32_t e, int32_t nparts, int32_t max_e, const Params &P,
                           Arena &A) {
-    cudaStream_t s = A.stream();
     LevelWs *W = new LevelWs();
+    try {
+        return refine_workspace_body(W, n, np, e, nparts, max_e, P, A);
+    } catch (...) {
+        if (W->side) cudaStreamDestroy(W->side);
+        for (cudaEvent_t x : W->ev)
+            if (x) cudaEventDestroy(x);
+        delete W;
+        throw;
+    }
+}
+
+static LevelWs *refine_workspace_body(LevelWs *W, int32_t n, int64_t np, int32_t e, int32_t nparts, int32_t max_e,
+                                      const Params &P, Arena &A) {
+    cudaStream_t s = A.stream();
     HPC(cudaStreamCreateWithFlags(&W->side, cudaStreamNonBlocking));
     for (cudaEvent_t &x : W->ev) HPC(cudaEventCreateWithFlags(&x, cudaEventDisableTiming));
     W->cn = n;
@@ -1869,10 +1854,8 @@ LevelWs *refine_workspace(int32_t n, int64_t np, int32_t e, int32_t nparts, int3
     }
     W->keys = A.get<uint64_t>(n);
     W->idx = A.get<uint32_t>(n);
-    W->sk = A.get<uint64_t>(2 * (int64_t)SEQ_MAX);
     W->msz = A.get<int32_t>(n);
     W->mni = A.get<int32_t>(n);
-    W->sv = A.get<uint32_t>(2 * (int64_t)SEQ_MAX);
     W->first = A.get<int32_t>(nparts + 1);
     W->choice = A.get<int32_t>(n);
     W->accnode = A.get<int32_t>(n);
@@ -1921,14 +1904,19 @@ LevelWs *refine_workspace(int32_t n, int64_t np, int32_t e, int32_t nparts, int3
 
 void refine_workspace_free(LevelWs *W, Arena &A) {
     if (!W) return;
-    if (W->side) cudaStreamDestroy(W->side);
+    // side-stream work must be done before the arena hands its memory back
+    // (it is, unless the call is ending early on an error)
+    if (W->side) {
+        (void)cudaStreamSynchronize(W->side);
+        cudaStreamDestroy(W->side);
+    }
     for (cudaEvent_t x : W->ev)
         if (x) cudaEventDestroy(x);
     for (void *p : std::initializer_list<void *>{
              W->act, W->big, W->wns, W->singin, W->PL.p, W->PL.cnt, W->PL.cin, W->PL.lam, W->R.cnt, W->R.linked,
              W->R.D0, W->R.psize, W->R.saving, W->R.pc, W->R.pred, W->R.succ, W->R.chain, W->R.mvpos, W->R.cgain,
              W->R.gseq, W->R.acc0, W->R.dDs, W->R.dDd, W->R.viol, W->cl, W->hubs, W->cw, W->cflag, W->cpos, W->cut, W->cut_off, W->tiny, W->mid, W->touched, W->ttouched, W->M.node, W->M.src, W->M.dst, W->M.gain,
-             W->S.node, W->S.src, W->S.dst, W->S.gain, W->keys, W->sk, W->idx, W->sv, W->msz, W->mni, W->first, W->choice, W->accnode, W->pen,
+             W->S.node, W->S.src, W->S.dst, W->S.gain, W->keys, W->idx, W->msz, W->mni, W->first, W->choice, W->accnode, W->pen,
              W->minpen, W->acc1, W->pos, W->clen, W->lens, W->starts, W->cstart, W->seqmove, W->heads, W->hkeys,
              W->vkey, W->vidx, W->vsz, W->vdd, W->gsz, W->gdd, W->esz, W->edd, W->vhead, W->bgain, W->lvl, W->pmark, W->ovf, W->gk, W->gc, W->ptab, W->ibuf})
         A.release(p);
@@ -2024,7 +2012,8 @@ static int32_t rep_run(const Level &L, const int32_t *w, const Params &P, int32_
         }
         // moves in isolation (Eq. 13)
         if (L.np > 0) {
-            k_cut_flags<<<grid_of(L.np, 256), 256, 0, s>>>(L.off, L.inc, W.PL.lam, L.np, W.cflag);
+            k_cut_flags<<<grid_of(L.np, 256), 256, 0, s>>>(L.off, L.pin, L.inc, L.inode, W.PL.lam, L.np, W.cflag,
+                                                            reinterpret_cast<unsigned long long *>(cnt + C_ACC));
             HP_LAUNCH_CHECK();
         }
         scan_excl(W.cflag, W.cpos, L.np, W.cpos + L.np, A);
@@ -2071,6 +2060,22 @@ static int32_t rep_run(const Level &L, const int32_t *w, const Params &P, int32_
     fetch_bytes(hc, cnt, sizeof hc, s);
     if (hc[C_BAD]) throw Error(HP_ERR_INTERNAL, "gain table overflow");
     const int32_t m = hc[C_MOVES];
+    {
+        // algorithmic bytes (scope of Sec. VI-B..VI-D): a rebuilt repetition
+        // reads each pin and its part (8 B) and writes the pins-list entries
+        // (12 B each) and scans the incidence for cut hyperedges (4 B per
+        // entry); every repetition reads the cut entries (4 B) and the list
+        // entries behind them (12 B), and moves 48 B per proposed move (sort
+        // read and write, sequence, in-sequence gain, two capacity events, apply)
+        unsigned long long acc[3];
+        std::memcpy(acc, hc + C_ACC, sizeof acc);
+        if (!reuse) {
+            W.alg_bytes += 12 * L.np + 12 * (int64_t)acc[0];
+            W.cuts = (int64_t)acc[1];
+            W.cut_lam = (int64_t)acc[2];
+        }
+        W.alg_bytes += 4 * W.cuts + 12 * W.cut_lam + 48 * (int64_t)m;
+    }
     if (dbg) *dbg->m = m;
     if (m == 0) return 0;
 
@@ -2108,14 +2113,14 @@ static int32_t rep_run(const Level &L, const int32_t *w, const Params &P, int32_
     // its destination, each round (few parts in use make that quadratic)
     const int64_t per_part = cdiv(m, std::max<int32_t>(W.parts_used, 1));
     const int64_t scan_work = (int64_t)m * std::min<int64_t>(P.o.chain_window, per_part);
-    const bool small = m <= SMALLM, one_cta = m <= SEQ_MAX && scan_work <= (int64_t(1) << 20);
-    if (one_cta) {
-        SmallSeqArgs SA{W.M, W.S, W.keys, W.hkeys, W.idx, W.heads, W.sk, W.sv, R.pc, W.first, W.lens, W.starts, W.cstart,
-                        W.seqmove, R.mvpos, cnt, C, Q, nparts, P.o.chain_rounds, packed, gb, nb, sb, cgb, gbound,
-                        cgbound};
-        size_t sm = (size_t)SMALLM * 2 * (8 + 4);
-        prepare_kernel((const void *)k_seq_small, SEQ_T, sm);
-        k_seq_small<<<1, SEQ_T, sm, s>>>(SA);
+    const bool small = m <= SMALLM, one_cluster = m <= SQ_MAX && scan_work <= (int64_t(1) << 23);
+    if (one_cluster) {
+        ClusterSeqArgs SA{W.M, W.S, W.keys, W.hkeys, W.idx, W.heads, W.first, W.lens, W.starts, W.cstart,
+                          W.seqmove, R.mvpos, cnt, C, Q, nparts, P.o.chain_rounds, packed, gb, nb, sb, cgb, gbound,
+                          cgbound};
+        const size_t sm = SQ_SMEM;
+        prepare_kernel((const void *)k_seq_cluster, SEQ_T, sm);
+        k_seq_cluster<<<SQ_CS, SEQ_T, sm, s>>>(SA);
         HP_LAUNCH_CHECK();
     } else {
         // sort (p_s asc, gain desc, node asc)
@@ -2272,6 +2277,7 @@ RefineOut refine_level(const Level &L, const int32_t *w, const Params &P, int32_
     RefineOut out;
     if (L.n == 0 || P.o.theta == 0) return out;
     level_prepare(L, w, rho, *W, A);
+    const int64_t bytes0 = W->alg_bytes;
     const int32_t half = P.o.theta / 2;
     bool same_rho = false;   // the previous repetition applied nothing
     for (int32_t rep = 0; rep < P.o.theta; rep++) {
@@ -2284,6 +2290,7 @@ RefineOut refine_level(const Level &L, const int32_t *w, const Params &P, int32_
             else break;
         }
     }
+    out.alg_bytes = W->alg_bytes - bytes0;
     return out;
 }
 

@@ -41,7 +41,7 @@ class hp_merge_model(ctypes.Structure):
 class hp_options(ctypes.Structure):
     _fields_ = [(k, ctypes.c_int32) for k in ("pi", "theta", "chain_window", "chain_rounds", "noise_permille",
                                                "count_kind", "max_levels", "debug_table_cap", "learned_k",
-                                               "reserved")] + [("merge_model", ctypes.POINTER(hp_merge_model))]
+                                               "debug_walk_cap")] + [("merge_model", ctypes.POINTER(hp_merge_model))]
 
 
 def merge_model(m) -> hp_merge_model:
@@ -63,13 +63,15 @@ class hp_stats(ctypes.Structure):
                 ("moves_applied", ctypes.c_int64), ("pin_visits", ctypes.c_int64), ("ms_total", ctypes.c_double),
                 ("ms_coarsen", ctypes.c_double), ("ms_refine", ctypes.c_double),
                 ("kernel_launches", ctypes.c_int64), ("l0_pin_visits", ctypes.c_int64),
-                ("l0_neighbours", ctypes.c_int64), ("ms_propose_l0", ctypes.c_double)]
+                ("l0_neighbours", ctypes.c_int64), ("ms_propose_l0", ctypes.c_double), ("alg_bytes", ctypes.c_int64)]
 
 
 class hp_level_trace(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int32), ("pairs", ctypes.c_int32), ("iso_pairs", ctypes.c_int32),
                 ("reps", ctypes.c_int32), ("pins", ctypes.c_int64), ("conn", ctypes.c_int64),
-                ("moves", ctypes.c_int64)]
+                ("moves", ctypes.c_int64), ("valid", ctypes.c_int32), ("iso_list", ctypes.c_int32),
+                ("targets_r1", ctypes.c_int32), ("max_indeg_r1", ctypes.c_int32), ("pairs_r1", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 class hp_instance(ctypes.Structure):
@@ -272,7 +274,8 @@ def partition(g, omega: int, delta: int, seed: int = 0, trace: bool = False, dev
         for l in range(min(sd["levels"], cap)):
             x = tr[l]
             levels.append(dict(n=x.n, pins=x.pins, pairs=x.pairs, iso_pairs=x.iso_pairs, conn=x.conn,
-                               moves=x.moves, reps=x.reps))
+                               moves=x.moves, reps=x.reps, valid=x.valid, iso_list=x.iso_list,
+                               targets_r1=x.targets_r1, max_indeg_r1=x.max_indeg_r1, pairs_r1=x.pairs_r1))
     return Result(rc, part[: g.num_nodes].cpu().numpy(), sd, levels)
 
 

@@ -25,7 +25,8 @@ from paper_2605_20497_gb300 import inputs  # noqa: E402
 
 STAT_KEYS = ("connectivity", "cut_net", "num_parts", "max_part_size", "max_part_distinct", "violations", "levels",
              "moves_applied")
-TRACE_KEYS = ("n", "pins", "pairs", "iso_pairs", "conn", "moves", "reps")
+TRACE_KEYS = ("n", "pins", "pairs", "iso_pairs", "conn", "moves", "reps", "valid", "iso_list", "targets_r1",
+              "max_indeg_r1", "pairs_r1")
 LEARNED_SUFFIX, LEARNED_K, LEARNED_MODEL_SEED = "+learned", 16, 7
 
 

@@ -19,7 +19,8 @@ from paper_2605_20497_gb300 import hp, inputs
 pytestmark = pytest.mark.gpu
 
 GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
-TRACE_KEYS = ("n", "pins", "pairs", "iso_pairs", "conn", "moves", "reps")
+TRACE_KEYS = ("n", "pins", "pairs", "iso_pairs", "conn", "moves", "reps", "valid", "iso_list", "targets_r1",
+              "max_indeg_r1", "pairs_r1")
 
 
 @pytest.fixture(scope="module")

@@ -111,3 +111,42 @@ def test_noalloc_errors_and_empty(torch):
     assert z == (hp.HP_OK, 0, 0)
     st = hp.load().hp_connectivity_noalloc(None, None, -1, None, None, 0, 0, None, None, None)
     assert st == hp.HP_ERR_INVALID_ARG
+
+
+ALLOC_T = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+FREE_T = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+
+
+def test_noalloc_works_while_the_allocator_refuses(torch):
+    """With an allocator hook that refuses every request, hp_connectivity
+    fails for lack of workspace while hp_connectivity_noalloc still returns
+    the same numbers; and a call after a first call takes no device memory."""
+    n = 300_000
+    g = mixed_graph(11, sizes_of(11), n)
+    rho = np.random.default_rng(12).integers(0, 31, n).astype(np.int32)
+    ref = call(hp.hp_connectivity, torch, g, rho, 31)
+    assert ref[0] == hp.HP_OK
+    d = hp.to_device(g)
+    part = torch.from_numpy(rho).cuda()
+    args = (d["pins"].data_ptr(), d["offsets"].data_ptr(), g.num_hedges, d["weights"].data_ptr(), part.data_ptr(),
+            n, 31)
+    assert hp.hp_connectivity_noalloc(*args) == ref          # first call on this device done
+    torch.cuda.synchronize()
+    requests = []
+    refuse = ALLOC_T(lambda size, ctx: requests.append(size))   # returns None: refused
+    never = FREE_T(lambda p, ctx: None)
+    L = hp.load()
+    assert L.hp_set_allocator(ctypes.cast(refuse, ctypes.c_void_p), ctypes.cast(never, ctypes.c_void_p), None) == 0
+    try:
+        free0 = torch.cuda.mem_get_info()[0]
+        a = hp.hp_connectivity_noalloc(*args)
+        b = hp.hp_connectivity_noalloc(*args)
+        free1 = torch.cuda.mem_get_info()[0]
+        assert requests == []
+        assert a == b == ref
+        assert free1 == free0
+        st = hp.hp_connectivity(*args)[0]
+        assert st == hp.HP_ERR_OOM and len(requests) >= 1
+    finally:
+        assert L.hp_set_allocator(None, None, None) == 0
+    assert call(hp.hp_connectivity, torch, g, rho, 31) == ref
