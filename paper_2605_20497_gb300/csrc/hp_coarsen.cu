@@ -377,10 +377,23 @@ struct BigQueue {
 // shared memory and then taken a warp each, lanes over pins, so that every
 // warp gets a share of them.  Stops early (for every thread) once *stop is
 // set.
+//
+// On levels without destination-list groups (C.canon null: small hyperedges,
+// the coarse levels) the warps walk their own 32-entry chunks one after
+// another with no CTA barrier between chunks, each warp taking its large
+// hyperedges itself: the chunks' load chains then overlap across warps.
 template <class Ins>
 __device__ void cta_walk(const PropCtx &C, int32_t v, int32_t i0, int32_t deg, int32_t nin_v, const int *stop,
                          BigQueue Q, Ins ins) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (!C.canon) {
+        for (int32_t base = wid * 32; base < deg; base += nw * 32) {
+            if (__any_sync(0xffffffffu, stop ? *(volatile const int *)stop : 0)) break;
+            warp_chunk(C, v, i0, deg, nin_v, base + lane, ins, (NoBig *)nullptr);
+        }
+        __syncthreads();
+        return;
+    }
     const int32_t slack = size_slack(C, v);
     auto push = [&](int32_t e, unsigned long long qsum, uint32_t icnt) {
         const int32_t i = atomicAdd(Q.n, 1);
@@ -1092,14 +1105,43 @@ __device__ __forceinline__ void dp_timeout(const DpCtx &D) {
 // fence, no counter).  The best child itself (largest ss1-0, ties to the
 // larger id) is found afterwards by k_best_child.
 __device__ __forceinline__ void ph_dp_up(const DpCtx &D, int64_t t0, int64_t nt) {
+    const int lane = threadIdx.x & 31;
     CSTRIDE(v0, D.n, t0, nt) {
-        int32_t v = (int32_t)v0;
-        if (D.ccount[v] != 0) continue;             // not a leaf
-        if (D.target[v] < 0) continue;              // isolated, no proposal edge
-        int32_t cur = v;
+        const unsigned act = __activemask();
+        const int32_t v = (int32_t)v0;
+        const bool leaf = D.ccount[v] == 0 && D.target[v] >= 0;   // a leaf with a proposal edge
+        const int32_t tv = leaf ? D.target[v] : -1;
+        const bool multi = leaf && D.target[tv] != v && D.ccount[tv] > 1;
+        // Leaves whose parent has several children take their first step with
+        // the warp's other leaves of that parent: a leaf's ss0 is 0, so it adds
+        // nothing to the parent's sum0; each raises kmax (a load first: most
+        // are below it); one counter update per group, and the group that
+        // finishes the parent's children climbs on from it.  Star-shaped
+        // proposal graphs (a hub with a thousand leaves) then cost a few
+        // atomics per warp instead of three per leaf.
+        const unsigned g = __match_any_sync(act, multi ? tv : -1 - lane);
+        int32_t cur = v, steps0 = 0;
+        if (multi) {
+            const long long my10 = (long long)D.score[v];
+            __stcg(&D.ss0[v], 0ll);
+            __stcg(&D.ss10[v], my10);
+            if (my10 > __ldcg(&D.kmax[tv])) atomicMax(&D.kmax[tv], my10);
+            __syncwarp(g);
+            bool last = false;
+            if ((g & ((1u << lane) - 1u)) == 0u) {
+                __threadfence();
+                last = atomicSub(&D.pending[tv], (int)__popc(g)) == (int)__popc(g);
+                __threadfence();
+            }
+            if (!last) continue;
+            cur = tv;
+            steps0 = 1;
+        } else if (!leaf) {
+            continue;
+        }
         bool carried = false;                       // cur's single child's values in registers
         long long cs0 = 0, cmax = 0;
-        for (int32_t steps = 0;; steps++) {
+        for (int32_t steps = steps0;; steps++) {
             if (steps > D.walk_cap) {
                 dp_timeout(D);
                 break;
@@ -1221,7 +1263,7 @@ __global__ void k_dp_down(DpCtx D, const int32_t *target, int32_t *mate, unsigne
 
 // ---------------------------------------------------------------- one-cluster matching
 // The best-effort pairing and the pi matching rounds of a level of at most
-// SQ_MAX nodes in one launch: the steps of the multi-kernel form, each a
+// sq_max<uint32_t>() nodes in one launch: the steps of the multi-kernel form, each a
 // strided loop over the cluster's threads, separated by cluster barriers.
 struct MatchArgs {
     const int32_t *candK;   // proposal lists (K entries): nodes without a valid neighbour
@@ -1248,21 +1290,21 @@ __global__ void __cluster_dims__(SQ_CS, 1, 1) __launch_bounds__(SQ_T) k_match_cl
     __shared__ int32_t s_part;
     cg::cluster_group cl = cg::this_cluster();
     const int64_t t0 = (int64_t)cl.block_rank() * blockDim.x + threadIdx.x, nt = (int64_t)SQ_CS * blockDim.x;
-    uint32_t *ka = reinterpret_cast<uint32_t *>(smem), *kb = ka + SQ_CHUNK;
-    uint32_t *va = kb + SQ_CHUNK, *vb = va + SQ_CHUNK, *rk = vb + SQ_CHUNK;
+    const SqBuf<uint32_t> B(smem);
     const int32_t n = A.n;
     // best-effort pairing (Sec. V-C): nodes with no valid neighbour, by (size, id)
     ph_iso_flags(A.candK, A.K, n, A.flag, t0, nt);
     cl.sync();
-    const int32_t k = cluster_scan_excl(cl, A.flag, A.pos, n, s_tmp, &s_part);
+    const int32_t k = cluster_scan_excl<int32_t>(cl, A.flag, A.pos, n, s_tmp, &s_part);
     if (t0 == 0) A.box->isolist = k;
     ph_iso_compact(A.flag, A.pos, A.size, n, A.ikeys, A.iids, t0, nt);
     cl.sync();
-    cluster_radix_sort<uint32_t>(cl, A.ikeys, A.iids, k, (A.isobits + 7) / 8, ka, kb, va, vb, rk, s_wc, s_tot, s_base);
+    cluster_radix_sort<uint32_t>(cl, A.ikeys, A.iids, k, (A.isobits + 7) / 8, B, s_wc, s_tot, s_base);
     ph_iso_pair(A.iids, k, A.size, A.nin, A.omega, A.delta, A.mate, &A.box->iso, t0, nt);
     cl.sync();
     // pi rounds of maximum-weight matching (Sec. V-D)
     const DpCtx &D = A.D;
+    unsigned long long before = 0;   // pairs before the round
     for (int32_t r = 0; r < A.pi; r++) {
         ph_targets(A.cand, A.cscore, A.pi, A.mate, n, A.target, A.score, D.sum0, D.kmax, D.best, A.ccount, D.pending,
                    t0, nt);
@@ -1277,6 +1319,11 @@ __global__ void __cluster_dims__(SQ_CS, 1, 1) __launch_bounds__(SQ_T) k_match_cl
         ph_dp_down(D, D.target, A.mate, &A.box->pairs, t0, nt);
         cl.sync();
         if (r == 0 && t0 == 0) A.box->pairs1 = A.box->pairs;
+        // a round that forms no pair leaves every target as it was, so every
+        // later round would form none either
+        const unsigned long long after = *(volatile unsigned long long *)&A.box->pairs;
+        if (after == before) break;
+        before = after;   // (the count changes again only after two more cluster barriers)
     }
 }
 
@@ -1565,7 +1612,7 @@ void coarsen_level(Level &L, int32_t level, const int32_t *w, const Params &P, i
     D.err = err_dev;
     D.level_err = &box->err;
     D.walk_cap = P.o.debug_walk_cap > 0 ? std::min(P.o.debug_walk_cap, n) : n;
-    if (n <= SQ_MAX) {
+    if (n <= sq_max<uint32_t>()) {
         // small level: pairing and matching by one cluster, one launch
         MatchArgs M{W.cand, K, cand, cscore, pi, n, P.omega, P.delta, L.size, L.nin, W.flag, W.pos, W.ikeys, W.iids,
                     bits_for((uint64_t)P.omega), mate, box, W.target, W.ccount, W.score, D};

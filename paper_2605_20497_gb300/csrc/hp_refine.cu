@@ -614,8 +614,11 @@ __global__ void k_level_nodes(const int32_t *off, const int32_t *ioff, const int
 // small_max (a warp each), larger (a CTA each).  All of them form `act`
 // (the in-sequence pass); tiny ones are also listed apart.
 constexpr int TINY_E = 8;
-__global__ void k_level_edges(const int32_t *off, int32_t e, int32_t small_max, int32_t *act, int32_t *big,
+// largest hyperedge handled a warp each: the level's largest, at least 2, at most 512
+__host__ __device__ inline int32_t level_small_max(int32_t max_e) { return max_e < 2 ? 2 : (max_e > 512 ? 512 : max_e); }
+__global__ void k_level_edges(const int32_t *off, int32_t e, const int32_t *max_e, int32_t *act, int32_t *big,
                               int32_t *tiny, int32_t *mid, int32_t *cnt) {
+    const int32_t small_max = level_small_max(*max_e);
     GRID_STRIDE(i, (int64_t)e) {
         int32_t sz = off[i + 1] - off[i];
         if (sz >= 2 && sz <= small_max) {
@@ -726,9 +729,12 @@ enum { C_CAND, C_MOVES, C_OVF, C_BAD, C_NH, C_BAD0, C_APPLIED, C_NV, C_HUB, C_CW
        C_N = C_ACC + 6 };
 
 // moves of at most SMALLM are validated by one CTA (k_val_small) with the
-// sorts in shared memory; moves of at most SQ_MAX are sequenced by one
+// sorts in shared memory; moves of at most sq_max<uint64_t>() are sequenced by one
 // thread-block cluster (k_seq_cluster); more take the multi-kernel path
 constexpr int SMALLM = 6144, SEQ_T = 1024;
+// refinement levels of at most this many nodes run their repetitions on the
+// cluster kernels with one read-back each (every move count fits them)
+constexpr int32_t SMALL_LEVEL = 32768;
 
 #define STRIDE(i, n, t0, nt) for (int64_t i = (t0); i < (int64_t)(n); i += (nt))
 #define G_T0 (blockIdx.x * (int64_t)blockDim.x + threadIdx.x)
@@ -804,16 +810,22 @@ __global__ void k_cut_flags(const int32_t *off, const int32_t *pin, const int32_
         cuts += (unsigned long long)f;
         if (f) clam += (unsigned long long)lam[e];
     }
+    // one update of each counter per CTA (all CTAs hit the same three words)
+    __shared__ unsigned long long s_acc[3];
+    if (threadIdx.x < 3) s_acc[threadIdx.x] = 0;
+    __syncthreads();
     for (int o = 16; o > 0; o >>= 1) {
         lsum += __shfl_down_sync(0xffffffffu, lsum, o);
         cuts += __shfl_down_sync(0xffffffffu, cuts, o);
         clam += __shfl_down_sync(0xffffffffu, clam, o);
     }
     if ((threadIdx.x & 31) == 0 && (lsum | cuts | clam)) {
-        atomicAdd(&acc[0], lsum);
-        atomicAdd(&acc[1], cuts);
-        atomicAdd(&acc[2], clam);
+        atomicAdd(&s_acc[0], lsum);
+        atomicAdd(&s_acc[1], cuts);
+        atomicAdd(&s_acc[2], clam);
     }
+    __syncthreads();
+    if (threadIdx.x < 3 && s_acc[threadIdx.x]) atomicAdd(&acc[threadIdx.x], s_acc[threadIdx.x]);
 }
 __global__ void k_cut_fill(const int32_t *inc, const int32_t *flag, const int32_t *cpos, const int32_t *ioff,
                            int64_t np, int32_t n, int32_t *cut, int32_t *cut_off) {
@@ -1315,7 +1327,7 @@ __global__ void k_apply(const int32_t *seqmove, const int32_t *node, const int32
     ph_apply(seqmove, node, dst, *lenp, rho, G_T0, G_NT);
 }
 
-// ---------------------------------------------------------------- cluster path (M <= SQ_MAX)
+// ---------------------------------------------------------------- cluster path (M <= sq_max<uint64_t>())
 // Sort of the moves, chaining rounds, chain order and sequence positions of
 // one repetition by one thread-block cluster (hp_cluster.cuh): every phase is
 // a strided loop over the cluster's threads on the global arrays (L2
@@ -1323,6 +1335,8 @@ __global__ void k_apply(const int32_t *seqmove, const int32_t *node, const int32
 // cluster radix sorts.  Eight times the threads of one CTA, so the latency of
 // each phase's global loads is spread over 8 SMs.
 static_assert(SQ_T == SEQ_T, "cluster CTA size");
+static_assert(SMALL_LEVEL <= sq_max<uint64_t>() && 2 * SMALL_LEVEL <= sq_max<uint32_t>(),
+              "a small level's moves fit the cluster sorts");
 
 struct ClusterSeqArgs {
     Moves M, S;
@@ -1355,13 +1369,12 @@ __global__ void __cluster_dims__(SQ_CS, 1, 1) __launch_bounds__(SEQ_T) k_seq_clu
     __shared__ uint32_t s_base[512];
     __shared__ int32_t s_tmp[40];
     __shared__ int32_t s_part;
-    __shared__ long long s_ll[34];
+    __shared__ long long s_ll[40];
     cg::cluster_group cl = cg::this_cluster();
     const int32_t m = A.cnt[C_MOVES];
-    if (m == 0 || m > SQ_MAX) return;   // uniform: no CTA of the cluster runs on
+    if (m == 0 || m > sq_max<uint64_t>()) return;   // uniform: no CTA of the cluster runs on
     const int64_t t0 = (int64_t)cl.block_rank() * blockDim.x + threadIdx.x, nt = (int64_t)SQ_CS * blockDim.x;
-    uint64_t *ka = reinterpret_cast<uint64_t *>(smem), *kb = ka + SQ_CHUNK;
-    uint32_t *va = reinterpret_cast<uint32_t *>(kb + SQ_CHUNK), *vb = va + SQ_CHUNK, *rk = vb + SQ_CHUNK;
+    const SqBuf<uint64_t> B(smem);
     // key widths from this repetition's moves
     long long gmx = 0, smx = 0, nmx = 0;
     STRIDE(i, m, t0, nt) {
@@ -1369,22 +1382,20 @@ __global__ void __cluster_dims__(SQ_CS, 1, 1) __launch_bounds__(SEQ_T) k_seq_clu
         smx = max(smx, (long long)A.M.src[i]);
         nmx = max(nmx, (long long)A.M.node[i]);
     }
-    gmx = cluster_max_ll(cl, gmx, s_ll);
-    smx = cluster_max_ll(cl, smx, s_ll);
-    nmx = cluster_max_ll(cl, nmx, s_ll);
+    cluster_max3_ll(cl, gmx, smx, nmx, s_ll);
     const int gb = dev_bits((unsigned long long)gmx), nb = dev_bits((unsigned long long)nmx),
               sb = dev_bits((unsigned long long)smx);
     // sort (p_s asc, gain desc, node asc)
     if (sb + gb + nb <= 64) {
         ph_move_keys(A.M, m, gmx, gb, nb, -1, A.keys, A.idx, 1, t0, nt);
         cl.sync();
-        cluster_radix_sort<uint64_t>(cl, A.keys, A.idx, m, (sb + gb + nb + 7) / 8, ka, kb, va, vb, rk, s_wc, s_tot, s_base);
+        cluster_radix_sort<uint64_t>(cl, A.keys, A.idx, m, (sb + gb + nb + 7) / 8, B, s_wc, s_tot, s_base);
     } else {
         const int fb[3] = {A.nb, A.gb, A.sb};
         for (int f = 0; f < 3; f++) {
             ph_move_keys(A.M, m, A.gbound, A.gb, A.nb, f, A.keys, A.idx, f == 0, t0, nt);
             cl.sync();
-            cluster_radix_sort<uint64_t>(cl, A.keys, A.idx, m, (fb[f] + 7) / 8, ka, kb, va, vb, rk, s_wc, s_tot, s_base);
+            cluster_radix_sort<uint64_t>(cl, A.keys, A.idx, m, (fb[f] + 7) / 8, B, s_wc, s_tot, s_base);
         }
     }
     // the moves in sorted order, with the size and |in| of each moved node
@@ -1430,18 +1441,18 @@ __global__ void __cluster_dims__(SQ_CS, 1, 1) __launch_bounds__(SEQ_T) k_seq_clu
     if (cgb + nb <= 64) {
         ph_head_keys(A.heads, nh, A.Q.cgain, A.S.node, cmx, nb, -1, A.hkeys, t0, nt);
         cl.sync();
-        cluster_radix_sort<uint64_t>(cl, A.hkeys, A.heads, nh, (cgb + nb + 7) / 8, ka, kb, va, vb, rk, s_wc, s_tot, s_base);
+        cluster_radix_sort<uint64_t>(cl, A.hkeys, A.heads, nh, (cgb + nb + 7) / 8, B, s_wc, s_tot, s_base);
     } else {
         for (int f = 0; f < 2; f++) {
             ph_head_keys(A.heads, nh, A.Q.cgain, A.S.node, A.cgbound, A.nb, f, A.hkeys, t0, nt);
             cl.sync();
-            cluster_radix_sort<uint64_t>(cl, A.hkeys, A.heads, nh, ((f == 0 ? A.nb : A.cgb) + 7) / 8, ka, kb, va, vb,
-                                         rk, s_wc, s_tot, s_base);
+            cluster_radix_sort<uint64_t>(cl, A.hkeys, A.heads, nh, ((f == 0 ? A.nb : A.cgb) + 7) / 8, B, s_wc,
+                                         s_tot, s_base);
         }
     }
     ph_chain_lens(A.heads, nh, A.Q.clen, nh, A.lens, t0, nt);
     cl.sync();
-    cluster_scan_excl(cl, A.lens, A.starts, nh, s_tmp, &s_part);
+    cluster_scan_excl<int32_t>(cl, A.lens, A.starts, nh, s_tmp, &s_part);
     ph_chain_start(A.heads, nh, A.starts, A.cstart, t0, nt);
     cl.sync();
     ph_seq_pos(A.Q.chain, A.Q.pos, A.cstart, m, A.S.node, A.seqmove, A.mvpos, t0, nt);
@@ -1472,6 +1483,148 @@ __global__ void __launch_bounds__(SEQ_T) k_val_small(ValCtx V, int32_t *cnt, int
     best_prefix_block(V.gseq, V.viol, m, bad, &cnt[C_APPLIED], bgain);
     const int32_t L = *(volatile int32_t *)&cnt[C_APPLIED];
     ph_apply(V.seqmove, V.S.node, V.S.dst, L, rho, t0, nt);
+}
+
+// The same on one thread-block cluster, for up to sq_max<uint32_t>() / 2
+// moves: events, cluster radix sort by part, the two prefix sums, the
+// validity transitions, the count of invalid parts, the best prefix and the
+// apply, separated by cluster barriers.
+__global__ void __cluster_dims__(SQ_CS, 1, 1) __launch_bounds__(SQ_T)
+    k_val_cluster(ValCtx V, int32_t *cnt, int32_t nparts, int sb, long long *bgain, int32_t *rho) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ uint32_t s_wc[32 * 256];
+    __shared__ uint32_t s_tot[256];
+    __shared__ uint32_t s_base[512];
+    __shared__ long long s_ll[40];
+    __shared__ int32_t s_tmp[40];
+    __shared__ long long s_part;
+    __shared__ int32_t s_ipart;
+    __shared__ long long s_bg[32];
+    __shared__ int32_t s_bk[32];
+    cg::cluster_group cl = cg::this_cluster();
+    const int32_t m = cnt[C_MOVES];
+    if (m == 0 || 2 * (int64_t)m > sq_max<uint32_t>()) return;   // uniform over the cluster
+    const int r = (int)cl.block_rank(), t = threadIdx.x, lane = t & 31, wid = t >> 5, nw = blockDim.x >> 5;
+    const int64_t t0 = (int64_t)r * blockDim.x + t, nt = (int64_t)SQ_CS * blockDim.x;
+    const int32_t c = 2 * m;
+    ph_val_entries(V, m, t0, nt);
+    cl.sync();
+    cluster_radix_sort<uint32_t>(cl, V.vkey, V.vidx, c, (sb + 7) / 8, SqBuf<uint32_t>(smem), s_wc, s_tot, s_base);
+    ph_val_gather(V, c, t0, nt);
+    cl.sync();
+    cluster_scan_excl<long long>(cl, V.gsz, V.esz, c, s_ll, &s_part);
+    cluster_scan_excl<long long>(cl, V.gdd, V.edd, c, s_ll, &s_part);
+    ph_val_trans(V, c, t0, nt);
+    const int32_t bad0 = cluster_sum_i32(cl, ph_initial_bad(V.psize, V.D0, nparts, V.omega, V.delta, t0, nt), s_tmp,
+                                         &s_ipart);
+    // best prefix (Sec. VI-D): the largest cumulative gain over prefixes with
+    // no invalid part, the longest on ties; this CTA takes moves [lo, hi)
+    const int32_t chunk = (m + SQ_CS - 1) / SQ_CS, lo = min(m, r * chunk), hi = min(m, lo + chunk);
+    long long gl = 0;
+    int32_t vl = 0;
+    for (int32_t k = lo + t; k < hi; k += blockDim.x) {
+        gl += (long long)V.gseq[k];
+        vl += V.viol[k];
+    }
+    gl = block_sum_ll(gl, s_ll);
+    vl = block_sum(vl, s_tmp);
+    if (t == 0) {
+        s_ll[36] = gl;
+        s_ll[37] = vl;
+    }
+    cl.sync();
+    long long gc = 0, vc = bad0;   // sums over the moves before lo
+    for (int q = 0; q < r; q++) {
+        const long long *o = cl.map_shared_rank(s_ll, q);
+        gc += o[36];
+        vc += o[37];
+    }
+    long long bestg = 0;
+    int32_t bestk = 0;
+    for (int32_t base = lo; base < hi; base += blockDim.x) {
+        const int32_t k = base + t;
+        const long long g = k < hi ? (long long)V.gseq[k] : 0;
+        const long long dv = k < hi ? V.viol[k] : 0;
+        long long gi = g, vi = dv;
+        for (int o = 1; o < 32; o <<= 1) {
+            const long long ug = __shfl_up_sync(0xffffffffu, gi, o), uv = __shfl_up_sync(0xffffffffu, vi, o);
+            if (lane >= o) {
+                gi += ug;
+                vi += uv;
+            }
+        }
+        if (lane == 31) {
+            s_ll[wid] = gi;
+            s_bg[wid] = vi;
+        }
+        __syncthreads();
+        if (wid == 0) {
+            const long long x = lane < nw ? s_ll[lane] : 0, y = lane < nw ? s_bg[lane] : 0;
+            long long xi = x, yi = y;
+            for (int o = 1; o < 32; o <<= 1) {
+                const long long ux = __shfl_up_sync(0xffffffffu, xi, o), uy = __shfl_up_sync(0xffffffffu, yi, o);
+                if (lane >= o) {
+                    xi += ux;
+                    yi += uy;
+                }
+            }
+            if (lane < nw) {
+                s_ll[lane] = xi - x;
+                s_bg[lane] = yi - y;
+            }
+            if (lane == nw - 1) {
+                s_ll[32] = xi;
+                s_ll[33] = yi;
+            }
+        }
+        __syncthreads();
+        const long long cum = gc + s_ll[wid] + gi, vio = vc + s_bg[wid] + vi;
+        if (k < hi && vio == 0 && cum >= bestg) {
+            bestg = cum;
+            bestk = k + 1;
+        }
+        gc += s_ll[32];
+        vc += s_ll[33];
+        __syncthreads();
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const long long og = __shfl_down_sync(0xffffffffu, bestg, o);
+        const int32_t ok = __shfl_down_sync(0xffffffffu, bestk, o);
+        if (og > bestg || (og == bestg && ok > bestk)) {
+            bestg = og;
+            bestk = ok;
+        }
+    }
+    if (lane == 0) {
+        s_bg[wid] = bestg;
+        s_bk[wid] = bestk;
+    }
+    __syncthreads();
+    if (t == 0) {
+        for (int k = 1; k < nw; k++)
+            if (s_bg[k] > bestg || (s_bg[k] == bestg && s_bk[k] > bestk)) {
+                bestg = s_bg[k];
+                bestk = s_bk[k];
+            }
+        s_ll[38] = bestg;
+        s_ll[39] = bestk;
+    }
+    cl.sync();
+    if (r == 0 && t == 0) {
+        for (int q = 1; q < SQ_CS; q++) {
+            const long long *o = cl.map_shared_rank(s_ll, q);
+            if (o[38] > bestg || (o[38] == bestg && o[39] > bestk)) {
+                bestg = o[38];
+                bestk = (int32_t)o[39];
+            }
+        }
+        *bgain = bestg;
+        cnt[C_APPLIED] = bestg > 0 ? bestk : 0;
+    }
+    cl.sync();
+    const int32_t L = *(volatile int32_t *)&cnt[C_APPLIED];
+    ph_apply(V.seqmove, V.S.node, V.S.dst, L, rho, t0, nt);
+    cl.sync();   // no CTA leaves while another may still read its shared memory
 }
 
 // ---------------------------------------------------------------- in-sequence gains
@@ -1948,10 +2101,9 @@ static void level_prepare(const Level &L, const int32_t *w, const int32_t *rho, 
         k_used_parts<<<grid_of(n, 256), 256, 0, s>>>(rho, n, W.pmark, W.lvl + 5);
         HP_LAUNCH_CHECK();
     }
-    W.max_e = fetch<int32_t>(W.lvl + 2, s);
-    W.small_max = std::min<int32_t>(std::max<int32_t>(W.max_e, 2), 512);
     if (e > 0) {
-        k_level_edges<<<grid_of(e, 256), 256, 0, s>>>(L.off, e, W.small_max, W.act, W.big, W.tiny, W.mid, W.lvl);
+        // the size classes take the largest hyperedge from the device (no read-back here)
+        k_level_edges<<<grid_of(e, 256), 256, 0, s>>>(L.off, e, W.lvl + 2, W.act, W.big, W.tiny, W.mid, W.lvl);
         HP_LAUNCH_CHECK();
     }
     HPC(cudaMemsetAsync(W.wns, 0, sizeof(long long) * n, s));
@@ -1963,6 +2115,8 @@ static void level_prepare(const Level &L, const int32_t *w, const int32_t *rho, 
     }
     int32_t hc[6];
     fetch_bytes(hc, W.lvl, sizeof hc, s);
+    W.max_e = hc[2];
+    W.small_max = level_small_max(W.max_e);
     W.n_act = hc[0];
     W.n_big = hc[1];
     W.n_tiny = hc[3];
@@ -2056,11 +2210,12 @@ static int32_t rep_run(const Level &L, const int32_t *w, const Params &P, int32_
         k_gains_global<<<W.gnb, GN_T, 0, s>>>(G, W.ovf, cnt + C_OVF, W.gcap, W.gk, W.gc, W.cl, cnt + C_BAD);
         HP_LAUNCH_CHECK();
     }
-    int32_t hc[C_N];
-    fetch_bytes(hc, cnt, sizeof hc, s);
-    if (hc[C_BAD]) throw Error(HP_ERR_INTERNAL, "gain table overflow");
-    const int32_t m = hc[C_MOVES];
-    {
+    // The rest of the repetition; `end` reads its counters back (the one
+    // host read of a repetition on a small level) and returns the moves applied.
+    auto end = [&]() -> int32_t {
+        int32_t hc[C_N];
+        fetch_bytes(hc, cnt, sizeof hc, s);
+        if (hc[C_BAD]) throw Error(HP_ERR_INTERNAL, "gain table overflow");
         // algorithmic bytes (scope of Sec. VI-B..VI-D): a rebuilt repetition
         // reads each pin and its part (8 B) and writes the pins-list entries
         // (12 B each) and scans the incidence for cut hyperedges (4 B per
@@ -2074,10 +2229,22 @@ static int32_t rep_run(const Level &L, const int32_t *w, const Params &P, int32_
             W.cuts = (int64_t)acc[1];
             W.cut_lam = (int64_t)acc[2];
         }
-        W.alg_bytes += 4 * W.cuts + 12 * W.cut_lam + 48 * (int64_t)m;
+        W.alg_bytes += 4 * W.cuts + 12 * W.cut_lam + 48 * (int64_t)hc[C_MOVES];
+        return hc[C_APPLIED];
+    };
+    // Levels of at most SMALL_LEVEL nodes have at most that many moves, which
+    // the cluster kernels sequence and validate whatever their number (none
+    // included): no read-back is needed before the end of the repetition.
+    const bool small_level = n <= SMALL_LEVEL && !dbg;
+    int32_t m = n;   // an upper bound of the moves on small levels
+    if (!small_level) {
+        int32_t hc[C_N];
+        fetch_bytes(hc, cnt, sizeof hc, s);
+        if (hc[C_BAD]) throw Error(HP_ERR_INTERNAL, "gain table overflow");
+        m = hc[C_MOVES];
+        if (dbg) *dbg->m = m;
+        if (m == 0) return end();
     }
-    if (dbg) *dbg->m = m;
-    if (m == 0) return 0;
 
     const long long gbound = std::max<long long>(P.wsum, 1);
     const int nb = bits_for((uint64_t)std::max(n - 1, 1)), gb = bits_for((uint64_t)gbound),
@@ -2113,7 +2280,8 @@ static int32_t rep_run(const Level &L, const int32_t *w, const Params &P, int32_
     // its destination, each round (few parts in use make that quadratic)
     const int64_t per_part = cdiv(m, std::max<int32_t>(W.parts_used, 1));
     const int64_t scan_work = (int64_t)m * std::min<int64_t>(P.o.chain_window, per_part);
-    const bool small = m <= SMALLM, one_cluster = m <= SQ_MAX && scan_work <= (int64_t(1) << 23);
+    const bool small = m <= SMALLM,
+               one_cluster = small_level || (m <= sq_max<uint64_t>() && scan_work <= (int64_t(1) << 23));
     if (one_cluster) {
         ClusterSeqArgs SA{W.M, W.S, W.keys, W.hkeys, W.idx, W.heads, W.first, W.lens, W.starts, W.cstart,
                           W.seqmove, R.mvpos, cnt, C, Q, nparts, P.o.chain_rounds, packed, gb, nb, sb, cgb, gbound,
@@ -2211,7 +2379,11 @@ static int32_t rep_run(const Level &L, const int32_t *w, const Params &P, int32_
     }
 
     // validity of every prefix (Sec. VI-D), best valid prefix, apply
-    if (small) {
+    if (small_level) {
+        prepare_kernel((const void *)k_val_cluster, SQ_T, SQ_SMEM);
+        k_val_cluster<<<SQ_CS, SQ_T, SQ_SMEM, s>>>(V, cnt, nparts, sb, W.bgain, rho);
+        HP_LAUNCH_CHECK();
+    } else if (small) {
         size_t sm = (size_t)2 * SMALLM * 2 * (4 + 4);
         prepare_kernel((const void *)k_val_small, SEQ_T, sm);
         k_val_small<<<1, SEQ_T, sm, s>>>(V, cnt, nparts, sb, W.bgain, rho);
@@ -2237,7 +2409,7 @@ static int32_t rep_run(const Level &L, const int32_t *w, const Params &P, int32_
         HPC(cudaMemcpyAsync(dbg->gseq, R.gseq, sizeof(long long) * m, cudaMemcpyDeviceToDevice, s));
         HPC(cudaMemcpyAsync(dbg->best_gain, W.bgain, sizeof(long long), cudaMemcpyDeviceToDevice, s));
     }
-    return fetch<int32_t>(cnt + C_APPLIED, s);
+    return end();
 }
 
 __global__ void k_max_edge_i(const int32_t *off, int32_t e, int32_t *maxe) {
