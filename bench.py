@@ -355,6 +355,8 @@ def main():
     ap.add_argument("--rows", type=int, default=1 << 24, help="feature rows of the merge_mlp workload")
     ap.add_argument("--graph", default=WORKLOAD, choices=GRAPHS,
                     help="the hypergraph one partition step runs on (named workloads of the input generators)")
+    ap.add_argument("--pi", type=int, default=0, help="candidates per node / matching rounds (default 4)")
+    ap.add_argument("--theta", type=int, default=None, help="refinement repetitions per level (default 16)")
     ap.add_argument("--count", type=int, default=128, help="instances of the batch workload")
     ap.add_argument("--concurrency", type=int, default=16, help="instances in flight in the batch workload")
     args = ap.parse_args()
@@ -396,6 +398,11 @@ def main():
         opt = hp.options(learned_k=args.learned_k, model=model)
     else:
         opt = hp.hp_default_options()
+    # parameter study (Sec. VII-D): candidates per node and repetitions per level
+    if args.pi:
+        opt.pi = args.pi
+    if args.theta is not None:
+        opt.theta = args.theta
     st = hp.hp_stats()
 
     def step():
@@ -473,7 +480,7 @@ def main():
                    "connectivity": last["connectivity"], "num_parts": last["num_parts"],
                    "violations": last["violations"], "levels": last["levels"],
                    "moves_applied": last["moves_applied"], "ms_coarsen": last["ms_coarsen"],
-                   "ms_refine": last["ms_refine"]},
+                   "ms_refine": last["ms_refine"], "pi": opt.pi, "theta": opt.theta},
         "e2e": {"value": replica_value(g.num_pins, world, ms_e2e), "unit": "pins/s",
                 "h2d_bytes_per_step": int(g.offsets.nbytes + g.pins.nbytes), "d2h_bytes_per_step": int(4 * n)},
         "roofline": {"bound": "hbm", "kernel": "level-0 candidate proposal (k_propose_smem)", "achieved": achieved,

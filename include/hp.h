@@ -95,6 +95,11 @@ typedef enum {
  *                  priority below ranks each node's top-learned_k list.
  *   merge_model    host pointer to the model of the learned priority (read
  *                  during the call; required when learned_k > 0, else ignored)
+ *   node_batch     0 (default): every node of a level at once.  n > 0: the
+ *                  learned priority scores the pairs of n nodes per pass, so
+ *                  its per-pair rows (24 B per listed pair) take n*learned_k
+ *                  rows instead of one per listed pair of the level (the
+ *                  node-batched coarsening of Sec. VII-C; result-neutral)
  */
 typedef struct hp_merge_model hp_merge_model;
 typedef struct {
@@ -109,6 +114,7 @@ typedef struct {
     int32_t learned_k;
     int32_t debug_walk_cap;
     const hp_merge_model *merge_model;
+    int32_t node_batch;
 } hp_options;
 
 /*

@@ -1373,9 +1373,11 @@ static CoarsenWs *coarsen_workspace_body(CoarsenWs *W, int32_t n, int32_t e, con
             W->model = A.get<hp_merge_model>(1);
             HPC(cudaMemcpyAsync(W->model, P.o.merge_model, sizeof(hp_merge_model), cudaMemcpyHostToDevice, s));
         }
-        W->feat = A.get<uint8_t>((int64_t)n * K * 16);
-        W->rank = A.get<int32_t>((int64_t)n * K);
-        W->lscore = A.get<int32_t>((int64_t)n * K);
+        // per-pair rows of one pass of node_batch nodes (all nodes without it)
+        const int64_t rows = (int64_t)(P.o.node_batch > 0 ? std::min(P.o.node_batch, std::max(n, 1)) : n) * K;
+        W->feat = A.get<uint8_t>(rows * 16);
+        W->rank = A.get<int32_t>(rows);
+        W->lscore = A.get<int32_t>(rows);
         W->lcand = A.get<int32_t>((int64_t)n * pi);
         W->lcs = A.get<uint64_t>((int64_t)n * pi);
     }
@@ -1586,7 +1588,7 @@ void coarsen_level(Level &L, int32_t level, const int32_t *w, const Params &P, i
         LearnIn X = learn_in(L, level, P, K, W);
         cand = X.cand;
         cscore = X.cscore;
-        learned_candidates(X, s);
+        learned_candidates(X, P.o.node_batch, s);
     }
     if (prop_events) HPC(cudaEventRecord(prop_events[1], s));
     k_flag_if_nonzero<<<1, 1, 0, s>>>(W.cnt + 4, err_dev);

@@ -334,17 +334,22 @@ void coarsen_level(Level &L, int32_t level, const int32_t *w, const Params &P, i
 bool merge_model_ok(const hp_merge_model &m);
 struct LearnIn {
     int32_t n, K, pi, level, omega, delta;
+    // nodes [v0, v1) are scored by one pass; feat, rank and score hold the
+    // rows of those nodes only, row (v - v0) * K + j (the whole level: 0, n)
+    int32_t v0 = 0, v1 = 0;
     const int32_t *size, *ioff, *inc, *nin;   // the level graph
     const int32_t *candK;                     // [n*K] top-K valid neighbours by (eta, id), -1 padded
     const uint64_t *csK;                      // [n*K] their eta (with noise)
     const hp_merge_model *model;              // device copy
-    uint8_t *feat;                            // [n*K][16] scratch, 16-byte aligned
-    int32_t *rank;                            // [n*K] scratch
-    int32_t *score;                           // [n*K] scratch
+    uint8_t *feat;                            // [(v1-v0)*K][16] scratch, 16-byte aligned
+    int32_t *rank;                            // [(v1-v0)*K] scratch
+    int32_t *score;                           // [(v1-v0)*K] scratch
     int32_t *cand;                            // [n*pi] out: C(n)
     uint64_t *cscore;                         // [n*pi] out: eta of C(n)
 };
-void learned_candidates(const LearnIn &X, cudaStream_t s);
+// C(n) of every node, in passes of `batch` nodes (0: one pass); X.feat,
+// X.rank and X.score hold batch * K rows
+void learned_candidates(LearnIn X, int32_t batch, cudaStream_t s);
 void merge_features(const LearnIn &X, cudaStream_t s);   // k_merge_feats alone into X.feat / X.rank
 // level-0 top-K lists (K = P.o.learned_k) and the features of every listed pair
 void level_features(Level &L, const int32_t *w, const Params &P, CoarsenWs &W, Arena &A, uint32_t *err_dev,

@@ -69,8 +69,9 @@ __device__ __forceinline__ bool sorted_has(const int32_t *a, int32_t len, int32_
 // j-th candidate m (-1: not mutual, or no candidate), and the pair's sixteen
 // feature bytes (zero unless mutual)
 __global__ void k_merge_feats(LearnIn X) {
-    const int64_t total = (int64_t)X.n * X.K;
-    GRID_STRIDE(p, total) {
+    const int64_t base = (int64_t)X.v0 * X.K, total = (int64_t)(X.v1 - X.v0) * X.K;
+    GRID_STRIDE(q, total) {
+        const int64_t p = base + q;   // the pair; q its row in this pass
         const int32_t v = (int32_t)(p / X.K), j = (int32_t)(p % X.K);
         const int32_t m = X.candK[p];
         int32_t rm = -1;
@@ -119,8 +120,8 @@ __global__ void k_merge_feats(LearnIn X) {
             w2 = f8 | f9 << 8 | f10 << 16 | f11 << 24;
             w3 = f12 | f13 << 8 | f14 << 16 | f15 << 24;
         }
-        reinterpret_cast<uint4 *>(X.feat)[p] = make_uint4(w0, w1, w2, w3);
-        X.rank[p] = rm;
+        reinterpret_cast<uint4 *>(X.feat)[q] = make_uint4(w0, w1, w2, w3);
+        X.rank[q] = rm;
     }
 }
 
@@ -240,18 +241,19 @@ __device__ __forceinline__ bool learned_gt(int32_t s1, uint64_t e1, int32_t m1, 
     return e1 > e2 || (e1 == e2 && m1 > m2);
 }
 
-// one thread per node: C(n) = the top Pi mutual candidates by (s, eta, id)
+// one thread per node of the pass: C(n) = the top Pi mutual candidates by (s, eta, id)
 __global__ void k_merge_select(LearnIn X) {
-    GRID_STRIDE(v, (int64_t)X.n) {
+    GRID_STRIDE(v0, (int64_t)(X.v1 - X.v0)) {
+        const int64_t v = X.v0 + v0;
         int32_t c[16], sc[16];
         uint64_t et[16];
         int32_t have = 0;
         for (int32_t j = 0; j < X.K; j++) {
-            const int64_t p = v * X.K + j;
+            const int64_t p = v * X.K + j, q = v0 * X.K + j;   // the pair; its row in this pass
             const int32_t m = X.candK[p];
             if (m < 0) break;
-            if (X.rank[p] < 0) continue;
-            const int32_t s = X.score[p];
+            if (X.rank[q] < 0) continue;
+            const int32_t s = X.score[q];
             const uint64_t e = X.csK[p];
             int32_t pos = have;
             while (pos > 0 && learned_gt(s, e, m, sc[pos - 1], et[pos - 1], c[pos - 1])) pos--;
@@ -523,7 +525,10 @@ void merge_quantize(const float *P, const uint8_t *calib, int64_t count, hp_merg
 // ---------------------------------------------------------------- host
 void merge_features(const LearnIn &X, cudaStream_t s) {
     if (X.n <= 0) return;
-    k_merge_feats<<<grid_for((int64_t)X.n * X.K, 256), 256, 0, s>>>(X);
+    LearnIn Y = X;
+    Y.v0 = 0;
+    Y.v1 = X.n;
+    k_merge_feats<<<grid_for((int64_t)X.n * X.K, 256), 256, 0, s>>>(Y);
     HP_LAUNCH_CHECK();
 }
 
@@ -535,14 +540,23 @@ void merge_scores(const uint8_t *feat, int64_t count, const hp_merge_model *dmod
     HP_LAUNCH_CHECK();
 }
 
-void learned_candidates(const LearnIn &X, cudaStream_t s) {
+// Node-batched (the memory remedy of Sec. VII-C applied to this design's
+// per-pair rows): each pass extracts the features of `batch` nodes' listed
+// pairs, scores them and selects those nodes' C(n); the mutual check reads
+// the complete top-K lists, so the result does not depend on the batch.
+void learned_candidates(LearnIn X, int32_t batch, cudaStream_t s) {
     if (X.n <= 0) return;
-    const int64_t pairs = (int64_t)X.n * X.K;
-    k_merge_feats<<<grid_for(pairs, 256), 256, 0, s>>>(X);
-    HP_LAUNCH_CHECK();
-    merge_scores(X.feat, pairs, X.model, X.score, s);
-    k_merge_select<<<grid_for(X.n, 128), 128, 0, s>>>(X);
-    HP_LAUNCH_CHECK();
+    const int32_t B = batch > 0 && batch < X.n ? batch : X.n;
+    for (int32_t v0 = 0; v0 < X.n; v0 += B) {
+        X.v0 = v0;
+        X.v1 = std::min<int64_t>((int64_t)v0 + B, X.n);
+        const int64_t pairs = (int64_t)(X.v1 - X.v0) * X.K;
+        k_merge_feats<<<grid_for(pairs, 256), 256, 0, s>>>(X);
+        HP_LAUNCH_CHECK();
+        merge_scores(X.feat, pairs, X.model, X.score, s);
+        k_merge_select<<<grid_for(X.v1 - X.v0, 128), 128, 0, s>>>(X);
+        HP_LAUNCH_CHECK();
+    }
 }
 
 }  // namespace hp

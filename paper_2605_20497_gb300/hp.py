@@ -41,7 +41,8 @@ class hp_merge_model(ctypes.Structure):
 class hp_options(ctypes.Structure):
     _fields_ = [(k, ctypes.c_int32) for k in ("pi", "theta", "chain_window", "chain_rounds", "noise_permille",
                                                "count_kind", "max_levels", "debug_table_cap", "learned_k",
-                                               "debug_walk_cap")] + [("merge_model", ctypes.POINTER(hp_merge_model))]
+                                               "debug_walk_cap")] + [("merge_model", ctypes.POINTER(hp_merge_model)),
+                                                                     ("node_batch", ctypes.c_int32)]
 
 
 def merge_model(m) -> hp_merge_model:

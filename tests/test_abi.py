@@ -61,7 +61,7 @@ def test_argument_checks_before_any_device_work(lib):
 
 
 def test_struct_layout_matches_header(lib):
-    assert ctypes.sizeof(hp.hp_options) == 10 * 4 + 8
+    assert ctypes.sizeof(hp.hp_options) == 10 * 4 + 8 + 8
     assert ctypes.sizeof(hp.hp_merge_model) == 64 * 16 + 64 * 64 + 64 + 4 * (64 + 64 + 3)
     assert ctypes.sizeof(hp.hp_stats) == 8 + 8 + 6 * 4 + 8 + 8 + 3 * 8 + 3 * 8 + 8 + 8
     assert ctypes.sizeof(hp.hp_level_trace) == 4 * 4 + 3 * 8 + 6 * 4

@@ -147,3 +147,58 @@ def test_learned_batch_and_host_entry_points(torch):
         assert np.array_equal(r.part, one.part)
         host = hp.partition_host(g, om, de, seed=sd, learned_k=16, model=model)
         assert host.status == hp.HP_OK and np.array_equal(host.part, one.part)
+
+
+ALLOC_T = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+FREE_T = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class PeakHook:
+    """Allocator hook over torch's caching allocator that records the peak of
+    the library's live workspace bytes."""
+
+    def __init__(self, torch):
+        self.torch, self.live, self.cur, self.peak = torch, {}, 0, 0
+        self._a, self._f = ALLOC_T(self.alloc), FREE_T(self.free)
+
+    def alloc(self, size, ctx):
+        p = self.torch.cuda.caching_allocator_alloc(size, device=self.torch.cuda.current_device())
+        self.live[p] = size
+        self.cur += size
+        self.peak = max(self.peak, self.cur)
+        return p
+
+    def free(self, p, ctx):
+        self.cur -= self.live.pop(p)
+        self.torch.cuda.caching_allocator_delete(p)
+
+    def __enter__(self):
+        assert hp.load().hp_set_allocator(ctypes.cast(self._a, ctypes.c_void_p),
+                                          ctypes.cast(self._f, ctypes.c_void_p), None) == hp.HP_OK
+        return self
+
+    def __exit__(self, *exc):
+        assert hp.load().hp_set_allocator(None, None, None) == hp.HP_OK
+        return False
+
+
+def test_node_batched_learned_priority_is_the_same_with_less_workspace(torch):
+    """The node-batched re-ranking (option node_batch, Sec. VII-C) gives the
+    same partition, bit for bit, for every batch size, and its per-pair rows
+    take less workspace."""
+    g = inputs.workload("random_snn_4k")
+    om, de = inputs.CONSTRAINTS["random_snn_4k"]
+    model = inputs.random_merge_model(5)
+    o = oracle.partition(g, om, de, seed=2, trace=True, learned_k=16, model=model)
+    peaks = {}
+    for nb in (0, 1, 1000, 4095, 4096, 100000):
+        with PeakHook(torch) as h:
+            r = hp.partition(g, om, de, seed=2, trace=True, learned_k=16, model=model, node_batch=nb)
+        assert r.status == hp.HP_OK, hp.hp_last_error()
+        assert np.array_equal(r.part, o.part), nb
+        assert r.stats["connectivity"] == o.stats["connectivity"]
+        assert [t["pairs"] for t in r.trace] == [t["pairs"] for t in o.trace]
+        peaks[nb] = h.peak
+    # 24 B per listed pair of every node against those of 1000 nodes
+    assert peaks[1000] < peaks[0] - 20 * 16 * (4096 - 1000)
+    assert peaks[4096] == peaks[0] and peaks[100000] == peaks[0]
