@@ -43,7 +43,8 @@ CPU_SAMPLE = ("layered_snn_65k", "layered SNN 8 layers x 16x16 grid x 32 channel
 REF_SAMPLE = ("layered 8x8x8x32", "layered SNN 8 layers x 8x8 grid x 32 channels (16,384 nodes), Omega=4096, "
               "Delta=65536")
 METRIC = "pins partitioned/s on 1 GB300"
-GRAPHS = [WORKLOAD, "layered_snn_65k", "random_snn_16k", "random_snn_4k", "gaussian_layered_snn_4m"]
+GRAPHS = [WORKLOAD, "layered_snn_65k", "random_snn_16k", "random_snn_4k", "gaussian_layered_snn_4m",
+          "gaussian_layered_snn_1m"]
 L2_BYTES = 129_000_000       # GB300 L2
 L2_FLUSH_BYTES = 256 << 20   # a write this large evicts it
 CLOCK_QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"

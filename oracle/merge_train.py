@@ -28,12 +28,25 @@ def pack(w1, b1, w2, b2, w3, b3):
     return np.concatenate([np.ravel(w1), b1, np.ravel(w2), b2, w3, [b3]]).astype(np.float64)
 
 
-def forward(p, feat):
+def bf16(a):
+    """a rounded to the nearest bfloat16 (ties to even), from its float32
+    value: the top 16 bits of the float32 after adding 0x7FFF plus the lowest
+    kept bit (the rounding of the bf16 operands of the tensor-core form)."""
+    f = np.ascontiguousarray(np.asarray(a, dtype=np.float32))
+    u = f.view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def forward(p, feat, mixed=False):
+    """mixed: the weights W1, W2 and the hidden activations h1 enter the two
+    matrix products as bf16 (the tensor-core form); sums stay exact here."""
     w1, b1, w2, b2, w3, b3 = unpack(p)
     x = np.asarray(feat, dtype=np.float64).reshape(-1, 16) / 256.0
-    z1 = x @ w1.T + b1
+    r = bf16 if mixed else (lambda a: a)
+    z1 = x @ r(w1).T + b1
     h1 = np.maximum(z1, 0.0)
-    z2 = h1 @ w2.T + b2
+    z2 = r(h1) @ r(w2).T + b2
     h2 = np.maximum(z2, 0.0)
     o = h2 @ w3 + b3
     return x, z1, h1, z2, h2, o
@@ -45,10 +58,14 @@ def loss(p, feat, y):
     return float(np.mean(np.maximum(o, 0.0) - o * y + np.log1p(np.exp(-np.abs(o))))) if len(y) else 0.0
 
 
-def loss_and_grad(p, feat, y):
-    """Mean loss and its gradient with respect to the flat parameters."""
+def loss_and_grad(p, feat, y, mixed=False):
+    """Mean loss and its gradient with respect to the flat parameters.
+    mixed: the tensor-core form, where every operand of the five matrix
+    products (W1, W2, h1, dL/dz2, dL/dz1; x is exact) is rounded to bf16 and
+    the bias, w3 and b3 gradients and the output layer stay in full precision."""
     w1, b1, w2, b2, w3, b3 = unpack(p)
-    x, z1, h1, z2, h2, o = forward(p, feat)
+    x, z1, h1, z2, h2, o = forward(p, feat, mixed)
+    r = bf16 if mixed else (lambda a: a)
     y = np.asarray(y, dtype=np.float64)
     n = len(y)
     if n == 0:
@@ -58,10 +75,10 @@ def loss_and_grad(p, feat, y):
     g_w3 = h2.T @ d_o
     g_b3 = d_o.sum()
     d_z2 = np.outer(d_o, w3) * (z2 > 0)      # d loss / d z2
-    g_w2 = d_z2.T @ h1
+    g_w2 = r(d_z2).T @ r(h1)
     g_b2 = d_z2.sum(axis=0)
-    d_z1 = (d_z2 @ w2) * (z1 > 0)            # d loss / d z1
-    g_w1 = d_z1.T @ x
+    d_z1 = (r(d_z2) @ r(w2)) * (z1 > 0)      # d loss / d z1
+    g_w1 = r(d_z1).T @ x
     g_b1 = d_z1.sum(axis=0)
     l = float(np.mean(np.maximum(o, 0.0) - o * y + np.log1p(np.exp(-np.abs(o)))))
     return l, pack(g_w1, g_b1, g_w2, g_b2, g_w3, g_b3)

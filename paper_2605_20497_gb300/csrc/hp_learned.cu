@@ -285,128 +285,296 @@ constexpr int NPAR = HP_MERGE_NPARAM;
 constexpr int P_W1 = 0, P_B1 = 1024, P_W2 = 1088, P_B2 = 5184, P_W3 = 5248, P_B3 = 5312;
 static_assert(P_B3 + 1 == NPAR, "parameter layout");
 constexpr int GRAD_CTAS = 256;   // fixed: the reduction order does not depend on the GPU
-constexpr int GRAD_T = 256;
-constexpr int GRAD_R = 32;       // rows per tile
-constexpr int NPAR_PAD = 5376;   // NPAR rounded up to 128 floats
-constexpr size_t GRAD_SMEM = sizeof(float) * (NPAR_PAD + GRAD_R * 16 + 4 * GRAD_R * 64 + GRAD_R);
+constexpr int GRAD_W = 8;        // warps per CTA, 16 rows each
+constexpr int GRAD_T = GRAD_W * 32;
+constexpr int GRAD_R = GRAD_W * 16;   // rows per tile
+constexpr int GR_W = GRAD_R / 2 + 4;  // words per row of the transposed bf16 tiles (pairs along rows, padded)
 
-// One CTA takes a contiguous range of rows, 32 at a time: forward, backward,
-// and the tile's gradient added to per-thread accumulators (thread t owns
-// W2 entries t + 256q, W1 entries t + 256q and one bias or w3 entry).  The
-// CTA's sums go to its own slot of `partial`, summed later in CTA order.
+// bf16 bits of x, rounded to nearest (ties to even)
+__device__ __forceinline__ uint32_t bf16_rn(float x) {
+    const uint32_t u = __float_as_uint(x);
+    return (u + 0x7FFFu + ((u >> 16) & 1u)) >> 16;
+}
+__device__ __forceinline__ uint32_t pack2_rn(float lo, float hi) { return bf16_rn(lo) | (bf16_rn(hi) << 16); }
+
+struct GradSmem {
+    uint32_t w1[64 * 8];            // W1[j][i pair], bf16
+    uint32_t w2[64 * W2_STRIDE];    // W2[k][j pair], bf16 (layer 2: B fragments over j)
+    uint32_t w2t[64 * W2_STRIDE];   // W2[k][j] transposed: [j][k pair] (back-propagation: B over k)
+    float b1[64], b2[64], w3[64];
+    // the tile's operands of the weight gradients, transposed: [column][row pair]
+    uint32_t d2t[64 * GR_W], h1t[64 * GR_W], d1t[64 * GR_W], xt[16 * GR_W];
+    double loss[GRAD_W];
+};
+
+// The training step on the tensor cores.  Per tile of 128 rows, each warp
+// takes 16 rows: layer 1 (8 MMAs m16n8k16, bf16 in, fp32 accumulate), layer 2
+// with the clamped layer-1 accumulators as its A operand (32 MMAs), the
+// output and dL/do on the CUDA cores, dL/dz1 = (dL/dz2 . W2) o [z1 > 0]
+// (32 MMAs, dL/dz2 again straight from the accumulator layout); then the CTA
+// forms dW2 = dz2^T h1 and dW1 = dz1^T x over the tile's rows from shared
+// memory (32 + 8 MMAs over 8 warps).  Operands are rounded to bf16: W1, W2,
+// h1, dL/dz2, dL/dz1 (x = f/256 is exact).  Bias, w3 and b3 gradients are
+// fp32 sums.  One CTA takes a contiguous range of rows; its sums go to its
+// own slot of `partial`, summed later in CTA order.
+//
+// m16n8k16 fragments (g = lane / 4, t = lane % 4):
+//   A regs: (row g, k 2t..2t+1), (row g+8, k 2t..), (row g, k 2t+8..), (row g+8, k 2t+8..)
+//   B regs: (k 2t..2t+1, col g), (k 2t+8..2t+9, col g)
+//   C/D:    (row g, col 2t), (row g, col 2t+1), (row g+8, col 2t), (row g+8, col 2t+1)
 __global__ void __launch_bounds__(GRAD_T) k_merge_grad(const uint8_t *feat, const float *label, int64_t count,
                                                         const float *params, float *partial, double *loss_part) {
-    extern __shared__ float sm[];
-    float *sp = sm;
-    float *sx = sp + NPAR_PAD;          // [R][16] scaled features
-    float *sh1 = sx + GRAD_R * 16;      // [R][64]
-    float *sh2 = sh1 + GRAD_R * 64;     // [R][64]
-    float *sd2 = sh2 + GRAD_R * 64;     // [R][64] dL/dz2
-    float *sd1 = sd2 + GRAD_R * 64;     // [R][64] dL/dz1
-    float *sdo = sd1 + GRAD_R * 64;     // [R] dL/do
-    __shared__ double s_loss[GRAD_T / 32];
-    const int tid = threadIdx.x;
-    for (int i = tid; i < NPAR; i += GRAD_T) sp[i] = params[i];
+    extern __shared__ __align__(16) unsigned char grad_smem[];
+    GradSmem &S = *reinterpret_cast<GradSmem *>(grad_smem);
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5, g = lane >> 2, t = lane & 3;
+    for (int i = tid; i < 64 * 8; i += GRAD_T) {
+        const int j = i >> 3, q = i & 7;
+        S.w1[i] = pack2_rn(params[P_W1 + j * 16 + 2 * q], params[P_W1 + j * 16 + 2 * q + 1]);
+    }
+    for (int i = tid; i < 64 * 32; i += GRAD_T) {
+        const int k = i >> 5, q = i & 31;
+        S.w2[k * W2_STRIDE + q] = pack2_rn(params[P_W2 + k * 64 + 2 * q], params[P_W2 + k * 64 + 2 * q + 1]);
+        // transposed: row j = k here, pairs of W2 rows 2q, 2q+1 at column j
+        S.w2t[k * W2_STRIDE + q] = pack2_rn(params[P_W2 + (2 * q) * 64 + k], params[P_W2 + (2 * q + 1) * 64 + k]);
+    }
+    for (int i = tid; i < 64; i += GRAD_T) {
+        S.b1[i] = params[P_B1 + i];
+        S.b2[i] = params[P_B2 + i];
+        S.w3[i] = params[P_W3 + i];
+    }
+    const float b3 = params[P_B3];
     const int64_t chunk = (count + gridDim.x - 1) / gridDim.x;
     const int64_t rb = (int64_t)blockIdx.x * chunk, re = min(count, rb + chunk);
-    float gw2[16], gw1[4], gb = 0.f;
-#pragma unroll
-    for (int q = 0; q < 16; q++) gw2[q] = 0.f;
-#pragma unroll
-    for (int q = 0; q < 4; q++) gw1[q] = 0.f;
-    double loss = 0.0;
     const float inv_count = count > 0 ? 1.0f / (float)count : 0.f;
+    // persistent gradient accumulators: dW2 tiles (m-tile w&3, n-tiles 4(w>>2)..+3), one dW1 tile
+    // (m-tile w&3, n-tile w>>2), and this lane's column sums of the warp's rows
+    float gw2[4][4], gw1[4];
+    float sb1[8][2], sb2[8][2], sw3[8][2], sb3 = 0.f;
+#pragma unroll
+    for (int a = 0; a < 4; a++) {
+        gw1[a] = 0.f;
+#pragma unroll
+        for (int b = 0; b < 4; b++) gw2[a][b] = 0.f;
+    }
+#pragma unroll
+    for (int c = 0; c < 8; c++)
+#pragma unroll
+        for (int e = 0; e < 2; e++) sb1[c][e] = sb2[c][e] = sw3[c][e] = 0.f;
+    double loss = 0.0;
     __syncthreads();
     for (int64_t r0 = rb; r0 < re; r0 += GRAD_R) {
-        const int nr = (int)(re - r0 < GRAD_R ? re - r0 : GRAD_R);
-        for (int t = tid; t < GRAD_R * 16; t += GRAD_T) {
-            const int r = t >> 4;
-            sx[t] = r < nr ? (float)feat[(r0 + r) * 16 + (t & 15)] * (1.0f / 256.0f) : 0.f;
+        const int64_t rw = r0 + 16 * w;   // this warp's first row
+        const int64_t ra = rw + g, rbb = rw + g + 8;
+        const bool va = ra < re, vb = rbb < re;
+        // ---- layer 1: x (16x16, exact bf16 of f/256) . W1^T
+        uint32_t xa[4];
+        {
+            const uint8_t *fa = feat + ra * 16, *fb = feat + rbb * 16;
+            auto xv = [&](const uint8_t *f, bool ok, int i) { return ok ? (float)f[i] * (1.0f / 256.0f) : 0.f; };
+            xa[0] = pack2_rn(xv(fa, va, 2 * t), xv(fa, va, 2 * t + 1));
+            xa[1] = pack2_rn(xv(fb, vb, 2 * t), xv(fb, vb, 2 * t + 1));
+            xa[2] = pack2_rn(xv(fa, va, 2 * t + 8), xv(fa, va, 2 * t + 9));
+            xa[3] = pack2_rn(xv(fb, vb, 2 * t + 8), xv(fb, vb, 2 * t + 9));
+            // x transposed for dW1: column i, rows in pairs
+            const int rl = 16 * w + g;   // local row of ra (rbb = rl + 8)
+            const uint32_t *xh = xa;
+            // element (row, i) of the tile -> xt[i][row]; written as 16-bit halves
+            uint16_t *xt16 = reinterpret_cast<uint16_t *>(S.xt);
+            xt16[(2 * t) * (2 * GR_W) + rl] = (uint16_t)(xh[0] & 0xFFFF);
+            xt16[(2 * t + 1) * (2 * GR_W) + rl] = (uint16_t)(xh[0] >> 16);
+            xt16[(2 * t) * (2 * GR_W) + rl + 8] = (uint16_t)(xh[1] & 0xFFFF);
+            xt16[(2 * t + 1) * (2 * GR_W) + rl + 8] = (uint16_t)(xh[1] >> 16);
+            xt16[(2 * t + 8) * (2 * GR_W) + rl] = (uint16_t)(xh[2] & 0xFFFF);
+            xt16[(2 * t + 9) * (2 * GR_W) + rl] = (uint16_t)(xh[2] >> 16);
+            xt16[(2 * t + 8) * (2 * GR_W) + rl + 8] = (uint16_t)(xh[3] & 0xFFFF);
+            xt16[(2 * t + 9) * (2 * GR_W) + rl + 8] = (uint16_t)(xh[3] >> 16);
         }
-        __syncthreads();
-        for (int t = tid; t < GRAD_R * 64; t += GRAD_T) {
-            const int r = t >> 6, j = t & 63;
-            float z = sp[P_B1 + j];
+        float z1[8][4];
 #pragma unroll
-            for (int i = 0; i < 16; i++) z = fmaf(sp[P_W1 + j * 16 + i], sx[r * 16 + i], z);
-            sh1[t] = fmaxf(z, 0.f);
+        for (int c = 0; c < 8; c++) {
+            const float bl = S.b1[8 * c + 2 * t], bh = S.b1[8 * c + 2 * t + 1];
+            z1[c][0] = bl;
+            z1[c][1] = bh;
+            z1[c][2] = bl;
+            z1[c][3] = bh;
+            const uint32_t *wr = S.w1 + (8 * c + g) * 8;
+            mma_16816(z1[c], xa[0], xa[1], xa[2], xa[3], wr[t], wr[t + 4]);
         }
-        __syncthreads();
-        for (int t = tid; t < GRAD_R * 64; t += GRAD_T) {
-            const int r = t >> 6, k = t & 63;
-            float z = sp[P_B2 + k];
-            for (int j = 0; j < 64; j++) z = fmaf(sp[P_W2 + k * 64 + j], sh1[r * 64 + j], z);
-            sh2[t] = fmaxf(z, 0.f);
+        // ---- layer 2: relu(z1) as the A operand, bf16
+        float z2[8][4];
+#pragma unroll
+        for (int c = 0; c < 8; c++) {
+            const float bl = S.b2[8 * c + 2 * t], bh = S.b2[8 * c + 2 * t + 1];
+            z2[c][0] = bl;
+            z2[c][1] = bh;
+            z2[c][2] = bl;
+            z2[c][3] = bh;
         }
-        __syncthreads();
-        if (tid < GRAD_R) {
-            float d = 0.f;
-            if (tid < nr) {
-                float o = sp[P_B3];
-                for (int k = 0; k < 64; k++) o = fmaf(sp[P_W3 + k], sh2[tid * 64 + k], o);
-                const float y = label[r0 + tid];
-                // stable binary cross-entropy of sigmoid(o): max(o,0) - o y + log(1 + e^-|o|)
-                loss += (double)(fmaxf(o, 0.f) - o * y + log1pf(expf(-fabsf(o))));
-                const float p = 1.0f / (1.0f + expf(-o));
-                d = (p - y) * inv_count;
+#pragma unroll
+        for (int kc = 0; kc < 4; kc++) {
+            const float *u = z1[2 * kc], *v = z1[2 * kc + 1];
+            const uint32_t a0 = pack2_rn(fmaxf(u[0], 0.f), fmaxf(u[1], 0.f)), a1 = pack2_rn(fmaxf(u[2], 0.f), fmaxf(u[3], 0.f));
+            const uint32_t a2 = pack2_rn(fmaxf(v[0], 0.f), fmaxf(v[1], 0.f)), a3 = pack2_rn(fmaxf(v[2], 0.f), fmaxf(v[3], 0.f));
+#pragma unroll
+            for (int c = 0; c < 8; c++) {
+                const uint32_t *wr = S.w2 + (8 * c + g) * W2_STRIDE + 8 * kc;
+                mma_16816(z2[c], a0, a1, a2, a3, wr[t], wr[t + 4]);
             }
-            sdo[tid] = d;
         }
-        __syncthreads();
-        for (int t = tid; t < GRAD_R * 64; t += GRAD_T) {
-            const int r = t >> 6, k = t & 63;
-            sd2[t] = sh2[t] > 0.f ? sdo[r] * sp[P_W3 + k] : 0.f;
-        }
-        __syncthreads();
-        for (int t = tid; t < GRAD_R * 64; t += GRAD_T) {
-            const int r = t >> 6, j = t & 63;
-            float a = 0.f;
-            for (int k = 0; k < 64; k++) a = fmaf(sd2[r * 64 + k], sp[P_W2 + k * 64 + j], a);
-            sd1[t] = sh1[t] > 0.f ? a : 0.f;
-        }
-        __syncthreads();
+        // ---- output, dL/do (rows g and g+8; the row's four lanes share it)
+        float oa = 0.f, ob = 0.f;
 #pragma unroll
-        for (int q = 0; q < 16; q++) {
-            const int idx = tid + GRAD_T * q, k = idx >> 6, j = idx & 63;
-            float a = gw2[q];
-            for (int r = 0; r < GRAD_R; r++) a = fmaf(sd2[r * 64 + k], sh1[r * 64 + j], a);
-            gw2[q] = a;
+        for (int c = 0; c < 8; c++) {
+            const float wl = S.w3[8 * c + 2 * t], wh = S.w3[8 * c + 2 * t + 1];
+            oa = fmaf(wl, fmaxf(z2[c][0], 0.f), fmaf(wh, fmaxf(z2[c][1], 0.f), oa));
+            ob = fmaf(wl, fmaxf(z2[c][2], 0.f), fmaf(wh, fmaxf(z2[c][3], 0.f), ob));
         }
+        oa += __shfl_xor_sync(0xffffffffu, oa, 1);
+        oa += __shfl_xor_sync(0xffffffffu, oa, 2);
+        ob += __shfl_xor_sync(0xffffffffu, ob, 1);
+        ob += __shfl_xor_sync(0xffffffffu, ob, 2);
+        oa += b3;
+        ob += b3;
+        float da = 0.f, db = 0.f;
+        if (va) {
+            const float y = label[ra];
+            if (t == 0) loss += (double)(fmaxf(oa, 0.f) - oa * y + log1pf(expf(-fabsf(oa))));
+            da = (1.0f / (1.0f + expf(-oa)) - y) * inv_count;
+        }
+        if (vb) {
+            const float y = label[rbb];
+            if (t == 0) loss += (double)(fmaxf(ob, 0.f) - ob * y + log1pf(expf(-fabsf(ob))));
+            db = (1.0f / (1.0f + expf(-ob)) - y) * inv_count;
+        }
+        if (t == 0) sb3 += da + db;
+        // ---- dL/dz2 = dL/do * w3 o [z2 > 0] (accumulator layout); dL/dz1 = (dz2 . W2) o [z1 > 0]
+        float d2[8][4];
 #pragma unroll
-        for (int q = 0; q < 4; q++) {
-            const int idx = tid + GRAD_T * q, j = idx >> 4, i = idx & 15;
-            float a = gw1[q];
-            for (int r = 0; r < GRAD_R; r++) a = fmaf(sd1[r * 64 + j], sx[r * 16 + i], a);
-            gw1[q] = a;
+        for (int c = 0; c < 8; c++) {
+            const float wl = S.w3[8 * c + 2 * t], wh = S.w3[8 * c + 2 * t + 1];
+            d2[c][0] = z2[c][0] > 0.f ? da * wl : 0.f;
+            d2[c][1] = z2[c][1] > 0.f ? da * wh : 0.f;
+            d2[c][2] = z2[c][2] > 0.f ? db * wl : 0.f;
+            d2[c][3] = z2[c][3] > 0.f ? db * wh : 0.f;
+            sb2[c][0] += d2[c][0] + d2[c][2];
+            sb2[c][1] += d2[c][1] + d2[c][3];
+            sw3[c][0] += da * fmaxf(z2[c][0], 0.f) + db * fmaxf(z2[c][2], 0.f);
+            sw3[c][1] += da * fmaxf(z2[c][1], 0.f) + db * fmaxf(z2[c][3], 0.f);
         }
-        if (tid < 64) {
-            for (int r = 0; r < GRAD_R; r++) gb += sd1[r * 64 + tid];
-        } else if (tid < 128) {
-            for (int r = 0; r < GRAD_R; r++) gb += sd2[r * 64 + tid - 64];
-        } else if (tid < 192) {
-            for (int r = 0; r < GRAD_R; r++) gb = fmaf(sdo[r], sh2[r * 64 + tid - 128], gb);
-        } else if (tid == 192) {
-            for (int r = 0; r < GRAD_R; r++) gb += sdo[r];
+        float d1[8][4];
+#pragma unroll
+        for (int c = 0; c < 8; c++) d1[c][0] = d1[c][1] = d1[c][2] = d1[c][3] = 0.f;
+#pragma unroll
+        for (int kc = 0; kc < 4; kc++) {
+            const float *u = d2[2 * kc], *v = d2[2 * kc + 1];
+            const uint32_t a0 = pack2_rn(u[0], u[1]), a1 = pack2_rn(u[2], u[3]);
+            const uint32_t a2 = pack2_rn(v[0], v[1]), a3 = pack2_rn(v[2], v[3]);
+#pragma unroll
+            for (int c = 0; c < 8; c++) {
+                const uint32_t *wr = S.w2t + (8 * c + g) * W2_STRIDE + 8 * kc;
+                mma_16816(d1[c], a0, a1, a2, a3, wr[t], wr[t + 4]);
+            }
+        }
+        // the operands of the weight gradients, transposed into shared memory
+        {
+            const int rl = 16 * w + g;
+            uint16_t *d2t = reinterpret_cast<uint16_t *>(S.d2t), *h1t = reinterpret_cast<uint16_t *>(S.h1t),
+                     *d1t = reinterpret_cast<uint16_t *>(S.d1t);
+#pragma unroll
+            for (int c = 0; c < 8; c++) {
+#pragma unroll
+                for (int e = 0; e < 4; e++) {
+                    const int col = 8 * c + 2 * t + (e & 1), row = rl + ((e & 2) ? 8 : 0);
+                    const float m1 = z1[c][e] > 0.f ? 1.f : 0.f;
+                    d1[c][e] *= m1;
+                    d2t[col * (2 * GR_W) + row] = (uint16_t)bf16_rn(d2[c][e]);
+                    h1t[col * (2 * GR_W) + row] = (uint16_t)bf16_rn(fmaxf(z1[c][e], 0.f));
+                    d1t[col * (2 * GR_W) + row] = (uint16_t)bf16_rn(d1[c][e]);
+                }
+                sb1[c][0] += d1[c][0] + d1[c][2];
+                sb1[c][1] += d1[c][1] + d1[c][3];
+            }
+        }
+        __syncthreads();
+        // ---- dW2[k][j] += sum_r dz2[r][k] h1[r][j]: warp w owns m-tile (k) w&3, n-tiles (j) 4(w>>2)..+3
+        {
+            const int mt = w & 3, nt0 = 4 * (w >> 2);
+#pragma unroll
+            for (int ks = 0; ks < GRAD_R / 16; ks++) {
+                const uint32_t *ar0 = S.d2t + (16 * mt + g) * GR_W + 8 * ks, *ar1 = ar0 + 8 * GR_W;
+                const uint32_t a0 = ar0[t], a1 = ar1[t], a2 = ar0[t + 4], a3 = ar1[t + 4];
+#pragma unroll
+                for (int q = 0; q < 4; q++) {
+                    const uint32_t *br = S.h1t + (8 * (nt0 + q) + g) * GR_W + 8 * ks;
+                    mma_16816(gw2[q], a0, a1, a2, a3, br[t], br[t + 4]);
+                }
+            }
+            // dW1[j][i] += sum_r dz1[r][j] x[r][i]: m-tile (j) w&3, n-tile (i) w>>2
+#pragma unroll
+            for (int ks = 0; ks < GRAD_R / 16; ks++) {
+                const uint32_t *ar0 = S.d1t + (16 * mt + g) * GR_W + 8 * ks, *ar1 = ar0 + 8 * GR_W;
+                const uint32_t *br = S.xt + (8 * (w >> 2) + g) * GR_W + 8 * ks;
+                mma_16816(gw1, ar0[t], ar1[t], ar0[t + 4], ar1[t + 4], br[t], br[t + 4]);
+            }
         }
         __syncthreads();
     }
+    // ---- this CTA's sums into its slot, in a fixed order
     float *pp = partial + (int64_t)blockIdx.x * NPAR;
+    {
+        const int mt = w & 3, nt0 = 4 * (w >> 2);
 #pragma unroll
-    for (int q = 0; q < 16; q++) pp[P_W2 + tid + GRAD_T * q] = gw2[q];
+        for (int q = 0; q < 4; q++) {
+            const int k0 = 16 * mt + g, j0 = 8 * (nt0 + q) + 2 * t;
+            pp[P_W2 + k0 * 64 + j0] = gw2[q][0];
+            pp[P_W2 + k0 * 64 + j0 + 1] = gw2[q][1];
+            pp[P_W2 + (k0 + 8) * 64 + j0] = gw2[q][2];
+            pp[P_W2 + (k0 + 8) * 64 + j0 + 1] = gw2[q][3];
+        }
+        const int j0 = 16 * mt + g, i0 = 8 * (w >> 2) + 2 * t;
+        pp[P_W1 + j0 * 16 + i0] = gw1[0];
+        pp[P_W1 + j0 * 16 + i0 + 1] = gw1[1];
+        pp[P_W1 + (j0 + 8) * 16 + i0] = gw1[2];
+        pp[P_W1 + (j0 + 8) * 16 + i0 + 1] = gw1[3];
+    }
+    // column sums: over the 8 lanes of equal t (the warp's rows), then over the warps in order
+    float *colsum = reinterpret_cast<float *>(S.d2t);   // [warp][3 * 64 + 1] scratch
 #pragma unroll
-    for (int q = 0; q < 4; q++) pp[P_W1 + tid + GRAD_T * q] = gw1[q];
-    if (tid < 64) pp[P_B1 + tid] = gb;
-    else if (tid < 128) pp[P_B2 + tid - 64] = gb;
-    else if (tid < 192) pp[P_W3 + tid - 128] = gb;
-    else if (tid == 192) pp[P_B3] = gb;
-    // the loss terms live in the first warp
+    for (int c = 0; c < 8; c++)
+#pragma unroll
+        for (int e = 0; e < 2; e++)
+#pragma unroll
+            for (int o = 4; o < 32; o <<= 1) {
+                sb1[c][e] += __shfl_xor_sync(0xffffffffu, sb1[c][e], o);
+                sb2[c][e] += __shfl_xor_sync(0xffffffffu, sb2[c][e], o);
+                sw3[c][e] += __shfl_xor_sync(0xffffffffu, sw3[c][e], o);
+            }
+    if (g == 0) {
+#pragma unroll
+        for (int c = 0; c < 8; c++)
+#pragma unroll
+            for (int e = 0; e < 2; e++) {
+                const int col = 8 * c + 2 * t + e;
+                colsum[w * 193 + col] = sb1[c][e];
+                colsum[w * 193 + 64 + col] = sb2[c][e];
+                colsum[w * 193 + 128 + col] = sw3[c][e];
+            }
+    }
+    for (int o = 4; o < 32; o <<= 1) sb3 += __shfl_xor_sync(0xffffffffu, sb3, o);
+    if (lane == 0) colsum[w * 193 + 192] = sb3;
     for (int o = 16; o > 0; o >>= 1) loss += __shfl_down_sync(0xffffffffu, loss, o);
-    if ((tid & 31) == 0) s_loss[tid >> 5] = loss;
+    if (lane == 0) S.loss[w] = loss;
     __syncthreads();
+    if (tid < 193) {
+        float a = 0.f;
+        for (int ww = 0; ww < GRAD_W; ww++) a += colsum[ww * 193 + tid];
+        const int at = tid < 64 ? P_B1 + tid : tid < 128 ? P_B2 + tid - 64 : tid < 192 ? P_W3 + tid - 128 : P_B3;
+        pp[at] = a;
+    }
     if (tid == 0) {
-        double t = 0.0;
-        for (int w = 0; w < GRAD_T / 32; w++) t += s_loss[w];
-        loss_part[blockIdx.x] = t;
+        double tl = 0.0;
+        for (int ww = 0; ww < GRAD_W; ww++) tl += S.loss[ww];
+        loss_part[blockIdx.x] = tl;
     }
 }
 
@@ -445,8 +613,8 @@ double merge_grad(const uint8_t *feat, const float *label, int64_t count, const 
     cudaStream_t s = A.stream();
     float *partial = A.get<float>((int64_t)GRAD_CTAS * NPAR);
     double *lp = A.get<double>(GRAD_CTAS + 1);
-    prepare_kernel((const void *)k_merge_grad, GRAD_T, GRAD_SMEM);
-    k_merge_grad<<<GRAD_CTAS, GRAD_T, GRAD_SMEM, s>>>(feat, label, count, params, partial, lp);
+    prepare_kernel((const void *)k_merge_grad, GRAD_T, sizeof(GradSmem));
+    k_merge_grad<<<GRAD_CTAS, GRAD_T, sizeof(GradSmem), s>>>(feat, label, count, params, partial, lp);
     HP_LAUNCH_CHECK();
     k_merge_grad_sum<<<(NPAR + 255) / 256, 256, 0, s>>>(partial, lp, count, grad, lp + GRAD_CTAS);
     HP_LAUNCH_CHECK();

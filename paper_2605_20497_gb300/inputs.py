@@ -392,6 +392,10 @@ def workload(name: str, seed: int = 0) -> Hypergraph:
     if name == "gaussian_layered_snn_4m":
         import os
         return gaussian_layered_snn(16, 512, 512, 84, 1024, seed, workers=min(16, os.cpu_count() or 1))
+    if name == "gaussian_layered_snn_1m":
+        # the same family on 256 x 256 grids: a quarter of the nodes and pins
+        import os
+        return gaussian_layered_snn(16, 256, 256, 84, 1024, seed, workers=min(16, os.cpu_count() or 1))
     raise KeyError(name)
 
 
@@ -404,6 +408,7 @@ CONSTRAINTS = {
     "layered_snn_16k": (1 << 10, 1 << 14),
     "layered_snn_65k": (1 << 12, 1 << 16),
     "gaussian_layered_snn_4m": (1 << 12, 1 << 16),
+    "gaussian_layered_snn_1m": (1 << 12, 1 << 16),
 }
 
 

@@ -37,12 +37,15 @@ def test_gradient_matches_fp64_reference(torch, count):
     fd, yd, pd = (torch.from_numpy(a).cuda() for a in (feat, y, p))
     rc, g, loss = hp.merge_grad(fd, yd, pd)
     assert rc == hp.HP_OK, hp.hp_last_error()
-    lref, gref = mt.loss_and_grad(p.astype(np.float64), feat, y.astype(np.float64))
-    assert loss == pytest.approx(lref, rel=1e-5)
+    # the tensor-core form: bf16 operands of the five matrix products, fp32 sums
+    lref, gref = mt.loss_and_grad(p.astype(np.float64), feat, y.astype(np.float64), mixed=True)
+    assert loss == pytest.approx(lref, rel=1e-4)
     g = g.cpu().numpy()
-    # per tensor, relative to its largest entry (fp32 sums over up to 10^5 rows)
+    # per tensor, relative to its largest entry: fp32 sums over up to 10^5
+    # rows, and the rare bf16 operand whose fp32 value falls on the other
+    # side of a rounding boundary than its fp64 value (one bf16 step, 2^-8)
     for lo, hi in [(0, 1024), (1024, 1088), (1088, 5184), (5184, 5248), (5248, 5312), (5312, 5313)]:
-        assert close(g[lo:hi], gref[lo:hi], 2e-4), (count, lo)
+        assert close(g[lo:hi], gref[lo:hi], 2e-3), (count, lo)
     rc2, g2, loss2 = hp.merge_grad(fd, yd, pd)
     assert np.array_equal(g, g2.cpu().numpy()) and loss == loss2   # fixed reduction order
 
@@ -107,3 +110,27 @@ def test_training_learns_a_separable_rule(torch):
     s = oracle.mlp_scores(feat, model)
     o = mt.forward(p.cpu().numpy().astype(np.float64), feat)[-1]
     assert np.mean((s > np.median(s)) == (o > np.median(o))) > 0.95
+
+
+def test_trained_priority_gains_on_held_out_graphs(torch):
+    """The committed model (trained by train_merge on 64 random SNN
+    hypergraphs of 16,384 nodes, generator seeds 1..64) against the plain
+    priority on held-out graphs of the same generator (seeds 100..102): the
+    learned priority's connectivity is at most the plain one on each, with no
+    Omega/Delta violation.  Partitions are bit-exact and deterministic, so
+    this compares fixed numbers."""
+    import os
+    from paper_2605_20497_gb300 import train_merge
+    path = os.path.join(os.path.dirname(hp.__file__), "merge_random_snn_16k.npz")
+    model = train_merge.load(path)
+    gains = []
+    for s in (100, 101, 102):
+        g = inputs.random_snn(16384, 127, seed=s)
+        d = hp.to_device(g)
+        a = hp.partition(g, 1024, 4096, seed=0, dev=d)
+        b = hp.partition(g, 1024, 4096, seed=0, dev=d, learned_k=16, model=model)
+        assert a.status == b.status == hp.HP_OK, hp.hp_last_error()
+        assert b.stats["violations"] == 0
+        assert b.stats["connectivity"] <= a.stats["connectivity"], (s, b.stats["connectivity"], a.stats["connectivity"])
+        gains.append(a.stats["connectivity"] - b.stats["connectivity"])
+    assert sum(gains) > 0

@@ -110,3 +110,28 @@ def test_shipped_model_is_valid():
     m = train_merge.load(path)
     s = oracle.mlp_scores(np.random.default_rng(0).integers(0, 256, size=(100, 16)).astype(np.uint8), m)
     assert len(np.unique(s)) > 10   # not a constant model
+
+
+def test_bf16_rounding_pins():
+    # round to nearest, ties to even, on the 8-bit significand of bfloat16
+    x = np.array([1.0, 1 + 2**-8, 1 + 3 * 2**-8, 1 + 2**-7, -(2 + 2**-7 + 2**-9), 3.0, 0.0])
+    want = np.array([1.0, 1.0, 1 + 2**-6, 1 + 2**-7, -(2 + 2**-6), 3.0, 0.0])
+    assert np.array_equal(mt.bf16(x), want)
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_mixed_form_is_the_same_function_up_to_bf16(seed):
+    r = np.random.default_rng(seed)
+    feat = r.integers(0, 256, size=(300, 16))
+    y = r.random(300)
+    p = mt.random_params(seed)
+    l0, g0 = mt.loss_and_grad(p, feat, y)
+    l1, g1 = mt.loss_and_grad(p, feat, y, mixed=True)
+    assert abs(l1 - l0) <= 1e-2 * abs(l0)
+    assert np.max(np.abs(g1 - g0)) <= 3e-2 * np.max(np.abs(g0))
+    # parameters and features that are exact bf16 with exact products leave
+    # the forward pass unchanged
+    q = mt.bf16(p)
+    assert np.array_equal(mt.bf16(q), q)
+    x1 = mt.forward(q, feat[:, :], mixed=False)
+    assert np.allclose(x1[1], mt.forward(q, feat, mixed=True)[1])
