@@ -230,7 +230,7 @@ def run_batch(args):
         from paper_2605_20497_gb300 import train_merge
         model = (train_merge.load(args.model_file) if args.model_file
                  else inputs.random_merge_model(args.model_seed))
-        opt = hp.options(learned_k=args.learned_k, model=model)
+        opt = hp.options(learned_k=args.learned_k, model=model, learned_levels=args.learned_levels)
     else:
         opt = plain
     stats = (hp.hp_stats * len(graphs))()
@@ -273,7 +273,10 @@ def run_batch(args):
            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
            "config": {"workload": f"batch of {len(graphs)} power-law SNN hypergraphs", "pins": pins,
-                      "nodes": sum(g.num_nodes for g, _, _, _ in graphs), "concurrency": args.concurrency,
+                      "nodes": sum(g.num_nodes for g, _, _, _ in graphs),
+                      "concurrency": (args.concurrency if args.concurrency else
+                                      "autotuned per size class: " + str(
+                                          [lib.hp_batch_tuned_concurrency(local, c) for c in range(6)])),
                       "merge_priority": (f"learned (top-{args.learned_k})" if args.learned_k else "plain"),
                       "sequential_plain_ms": ms_seq, "speedup_vs_sequential_plain": ms_seq / ms,
                       "violations": int(sum(stats[i].violations for i in range(len(graphs))))},
@@ -356,10 +359,14 @@ def main():
     ap.add_argument("--rows", type=int, default=1 << 24, help="feature rows of the merge_mlp workload")
     ap.add_argument("--graph", default=WORKLOAD, choices=GRAPHS,
                     help="the hypergraph one partition step runs on (named workloads of the input generators)")
+    ap.add_argument("--learned-levels", type=int, default=0,
+                    help="coarsening levels the learned priority ranks (0: all)")
+    ap.add_argument("--node-batch", type=int, default=0, help="nodes per pass of the learned re-ranking (0: all)")
     ap.add_argument("--pi", type=int, default=0, help="candidates per node / matching rounds (default 4)")
     ap.add_argument("--theta", type=int, default=None, help="refinement repetitions per level (default 16)")
     ap.add_argument("--count", type=int, default=128, help="instances of the batch workload")
-    ap.add_argument("--concurrency", type=int, default=16, help="instances in flight in the batch workload")
+    ap.add_argument("--concurrency", type=int, default=0,
+                    help="instances in flight in the batch workload (0: autotuned per size class)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -396,7 +403,8 @@ def main():
             model = train_merge.load(args.model_file)
         else:
             model = inputs.random_merge_model(args.model_seed)
-        opt = hp.options(learned_k=args.learned_k, model=model)
+        opt = hp.options(learned_k=args.learned_k, model=model, learned_levels=args.learned_levels,
+                         node_batch=args.node_batch)
     else:
         opt = hp.hp_default_options()
     # parameter study (Sec. VII-D): candidates per node and repetitions per level
@@ -509,7 +517,9 @@ def main():
         weights = (f"trained weights {os.path.basename(args.model_file)}" if args.model_file
                    else f"random-init weights (seed {args.model_seed})")
         out["config"]["merge_priority"] = (f"learned: top-{args.learned_k} lists re-ranked by the integer MLP "
-                                           f"16-64-64-1, {weights}")
+                                           f"16-64-64-1, {weights}, "
+                                           + (f"first {args.learned_levels} levels" if args.learned_levels
+                                              else "every level"))
         out["roofline"]["kernel"] = ("level-0 candidate proposal with top-16 lists, then the learned re-ranking "
                                      "(features, MLP, selection)")
         out["roofline"]["traffic"] = None

@@ -95,6 +95,10 @@ typedef enum {
  *                  priority below ranks each node's top-learned_k list.
  *   merge_model    host pointer to the model of the learned priority (read
  *                  during the call; required when learned_k > 0, else ignored)
+ *   learned_levels 0 (default): with learned_k > 0 the learned priority ranks
+ *                  the candidates of every coarsening level; n > 0: of the first n
+ *                  levels only, deeper levels taking the paper's (eta, id) order
+ *                  (the model is trained on level-0 pairs)
  *   node_batch     0 (default): every node of a level at once.  n > 0: the
  *                  learned priority scores the pairs of n nodes per pass, so
  *                  its per-pair rows (24 B per listed pair) take n*learned_k
@@ -115,6 +119,7 @@ typedef struct {
     int32_t debug_walk_cap;
     const hp_merge_model *merge_model;
     int32_t node_batch;
+    int32_t learned_levels;
 } hp_options;
 
 /*
@@ -245,6 +250,13 @@ typedef struct {
  *   `concurrency` (1..64) of them in flight at once, largest first, each on a
  *   stream of its own; the paper partitions one hypergraph per call, this
  *   is the batched form for many small ones.
+ *   concurrency 0: autotuned.  Instances are grouped into size classes by
+ *   nodes + hyperedges ([0, 2^12), then factors of 4), largest class first;
+ *   the first instances of a class not tuned yet on this device run in
+ *   groups of 2c at c = 4, 8, 16, 32, 64 in flight, and the rest of the class
+ *   (and that class in later calls) at the c with the most nodes + hyperedges
+ *   per second.  Only the schedule is tuned: every instance is partitioned
+ *   once, with the result hp_partition gives.
  *   inst: host array [count]; opt: shared options (NULL = defaults);
  *   stats_out, status_out: host arrays [count] or NULL, filled per instance.
  *   The work starts after the work already queued on `stream`, and `stream`
@@ -255,6 +267,13 @@ typedef struct {
  */
 HP_API hp_status hp_partition_batch(const hp_instance *inst, int32_t count, const hp_options *opt,
                                     int32_t concurrency, hp_stats *stats_out, int32_t *status_out, void *stream);
+
+/*
+ * hp_batch_tuned_concurrency -- the concurrency the autotuner of
+ *   hp_partition_batch settled on for size class `size_class` (0..5) on CUDA
+ *   device `device`, or 0 when that class has not been tuned there.
+ */
+HP_API int32_t hp_batch_tuned_concurrency(int32_t device, int32_t size_class);
 
 /*
  * hp_partition_host -- the same with every array in host memory: the call

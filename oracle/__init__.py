@@ -25,9 +25,9 @@ OK, ERR_INVALID_ARG, ERR_BAD_CSR, ERR_INFEASIBLE = 0, 1, 2, 3
 COUNT_INBOUND, COUNT_INCIDENT = 0, 1
 # layout of the option vector (see hp_oracle.c)
 OPT_KEYS = ("pi", "theta", "chain_window", "chain_rounds", "noise_permille", "count_kind", "max_levels",
-            "learned_k")
+            "learned_k", "learned_levels")
 DEFAULTS = dict(pi=4, theta=16, chain_window=256, chain_rounds=16, noise_permille=100, count_kind=0, max_levels=256,
-                learned_k=0)
+                learned_k=0, learned_levels=0)
 MODEL_LEN = 64 * 16 + 64 * 64 + 64 * 3 + 3   # layout of the model vector (see hp_oracle.c)
 STAT_KEYS = ("connectivity", "cut_net", "num_parts", "max_part_size", "max_part_distinct",
              "violations", "levels", "moves_applied")

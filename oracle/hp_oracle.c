@@ -69,7 +69,7 @@
 enum { OR_OK = 0, OR_ERR_INVALID_ARG = 1, OR_ERR_BAD_CSR = 2, OR_ERR_INFEASIBLE = 3 };
 
 /* option vector layout shared with the Python wrapper of this file */
-enum { OPT_PI, OPT_THETA, OPT_WINDOW, OPT_ROUNDS, OPT_PERMILLE, OPT_KIND, OPT_MAXLEV, OPT_LK, OPT_N };
+enum { OPT_PI, OPT_THETA, OPT_WINDOW, OPT_ROUNDS, OPT_PERMILLE, OPT_KIND, OPT_MAXLEV, OPT_LK, OPT_LL, OPT_N };
 /* stats vector layout */
 enum { ST_CONN, ST_CUTNET, ST_PARTS, ST_MAXSIZE, ST_MAXDIST, ST_VIOL, ST_LEVELS, ST_MOVES, ST_N = 16 };
 /* per-level trace record layout */
@@ -950,6 +950,7 @@ static int32_t best_prefix(const hg_t *g, const int32_t *rho, int32_t nparts, co
 typedef struct {
     int32_t pi, theta, window, rounds, permille, kind, maxlev;
     int32_t lk;   /* 0: C(n) by (eta, id); else K of the learned priority */
+    int32_t ll;   /* levels the learned priority ranks (0: all); deeper levels use (eta, id) */
 } opts_t;
 
 /* one refinement repetition (Sec. VI); returns the number of moves applied */
@@ -985,6 +986,7 @@ static void default_opts(opts_t *o)
     o->pi = 4; o->theta = 16; o->window = 256; o->rounds = 16; o->permille = 100; o->kind = 0;
     o->maxlev = 256;
     o->lk = 0;
+    o->ll = 0;
 }
 
 static int read_opts(const int32_t *opt, opts_t *o)
@@ -995,11 +997,12 @@ static int read_opts(const int32_t *opt, opts_t *o)
         o->rounds = opt[OPT_ROUNDS]; o->permille = opt[OPT_PERMILLE]; o->kind = opt[OPT_KIND];
         o->maxlev = opt[OPT_MAXLEV];
         o->lk = opt[OPT_LK];
+        o->ll = opt[OPT_LL];
     }
     if (o->pi < 1 || o->pi > 16 || o->theta < 0 || o->theta > 1024 || o->window < 1 ||
         o->rounds < 0 || o->rounds > 1024 || o->permille < 0 || o->permille > 1000 ||
         (o->kind != 0 && o->kind != 1) || o->maxlev < 0 || o->maxlev > 4096 ||
-        (o->lk != 0 && (o->lk < o->pi || o->lk > 16)))
+        (o->lk != 0 && (o->lk < o->pi || o->lk > 16)) || o->ll < 0)
         return OR_ERR_INVALID_ARG;
     return OR_OK;
 }
@@ -1083,7 +1086,8 @@ int or_partition_ml(int32_t n, int32_t e, const int32_t *off, const int32_t *pin
         if ((int64_t)g->n <= target_n || L == o.maxlev) break;
         /* the learned priority ranks the top-K lists (K >= Pi); the
          * best-effort pairing takes the nodes with no valid neighbour either way */
-        int32_t K = o.lk > 0 ? o.lk : o.pi;
+        const int learned = o.lk > 0 && (o.ll == 0 || L < o.ll);
+        int32_t K = learned ? o.lk : o.pi;
         int32_t *cand = xcalloc((size_t)g->n * K, sizeof(int32_t));
         uint64_t *cs = xcalloc((size_t)g->n * K, sizeof(uint64_t));
         int32_t *mate = xcalloc((size_t)g->n, sizeof(int32_t));
@@ -1092,7 +1096,7 @@ int or_partition_ml(int32_t n, int32_t e, const int32_t *off, const int32_t *pin
         int64_t nlist = 0;
         for (int32_t v = 0; v < g->n; v++) nlist += cand[(int64_t)v * K] < 0;
         int64_t iso = pair_isolated(g, K, cand, omega, delta, mate);
-        if (o.lk > 0) {
+        if (learned) {
             int32_t *c2 = xcalloc((size_t)g->n * o.pi, sizeof(int32_t));
             uint64_t *s2 = xcalloc((size_t)g->n * o.pi, sizeof(uint64_t));
             learned_candidates(g, L, K, cand, cs, o.pi, model, omega, delta, c2, s2);

@@ -58,7 +58,7 @@ static bool options_ok(const hp_options &o) {
         (o.count_kind != HP_COUNT_INBOUND && o.count_kind != HP_COUNT_INCIDENT) || o.max_levels < 0 ||
         o.max_levels > 4096)
         return false;
-    if (o.debug_walk_cap < 0 || o.node_batch < 0) return false;
+    if (o.debug_walk_cap < 0 || o.node_batch < 0 || o.learned_levels < 0) return false;
     if (o.debug_table_cap != 0) {
         int c = o.debug_table_cap;
         if (c < 64 || c > 65536 || (c & (c - 1))) return false;
@@ -315,6 +315,7 @@ void hp_default_options(hp_options *o) {
     o->debug_walk_cap = 0;
     o->merge_model = nullptr;
     o->node_batch = 0;
+    o->learned_levels = 0;
 }
 
 hp_status hp_merge_features(const int32_t *pins, const int32_t *offsets, int32_t num_hedges, int32_t num_nodes,

@@ -1572,7 +1572,7 @@ void coarsen_level(Level &L, int32_t level, const int32_t *w, const Params &P, i
                    uint32_t *err_dev, int32_t *cand_out, uint64_t *score_out, cudaEvent_t *prop_events) {
     cudaStream_t s = A.stream();
     const int32_t n = L.n, pi = P.o.pi;
-    const bool learned = P.o.learned_k > 0;
+    const bool learned = P.o.learned_k > 0 && (P.o.learned_levels == 0 || level < P.o.learned_levels);
     const int32_t K = learned ? P.o.learned_k : pi;   // length of the proposal's lists
     LevelBox *box = W.box;
     fill_i32(mate, n, -1, s);

@@ -28,7 +28,7 @@ HP_COUNT_INBOUND, HP_COUNT_INCIDENT = 0, 1
 EXPORTS = ("hp_default_options", "hp_partition", "hp_partition_ex", "hp_partition_host", "hp_set_allocator",
            "hp_status_string", "hp_last_error", "hp_connectivity", "hp_connectivity_noalloc", "hp_partition_batch", "hp_merge_scores",
            "hp_merge_features", "hp_merge_grad", "hp_merge_adam", "hp_merge_quantize", "hp_debug_coarsen_level",
-           "hp_debug_refine_rep")
+           "hp_debug_refine_rep", "hp_batch_tuned_concurrency")
 HP_MERGE_NPARAM = 5313
 
 
@@ -42,7 +42,8 @@ class hp_options(ctypes.Structure):
     _fields_ = [(k, ctypes.c_int32) for k in ("pi", "theta", "chain_window", "chain_rounds", "noise_permille",
                                                "count_kind", "max_levels", "debug_table_cap", "learned_k",
                                                "debug_walk_cap")] + [("merge_model", ctypes.POINTER(hp_merge_model)),
-                                                                     ("node_batch", ctypes.c_int32)]
+                                                                     ("node_batch", ctypes.c_int32),
+                                                                     ("learned_levels", ctypes.c_int32)]
 
 
 def merge_model(m) -> hp_merge_model:
@@ -114,6 +115,8 @@ def load() -> ctypes.CDLL:
         L.hp_partition_batch.argtypes = [ctypes.POINTER(hp_instance), I32, ctypes.POINTER(hp_options), I32,
                                          ctypes.POINTER(hp_stats), ctypes.POINTER(ctypes.c_int32), P]
         L.hp_partition_batch.restype = ctypes.c_int
+        L.hp_batch_tuned_concurrency.argtypes = [I32, I32]
+        L.hp_batch_tuned_concurrency.restype = I32
         L.hp_merge_scores.argtypes = [P, ctypes.c_int64, ctypes.POINTER(hp_merge_model), P, P]
         L.hp_merge_scores.restype = ctypes.c_int
         L.hp_merge_features.argtypes = [P, P, I32, I32, P, P, I32, I32, U64, ctypes.POINTER(hp_options), P, P, P, P]

@@ -54,10 +54,11 @@ def test_argument_checks_before_any_device_work(lib):
     assert lib.hp_partition_batch(None, 0, None, 4, None, None, None) == hp.HP_OK
     assert lib.hp_partition_batch(None, 1, None, 4, None, None, None) == hp.HP_ERR_INVALID_ARG
     one = (hp.hp_instance * 1)()
-    assert lib.hp_partition_batch(one, 1, None, 0, None, None, None) == hp.HP_ERR_INVALID_ARG
+    assert lib.hp_partition_batch(one, 1, None, -1, None, None, None) == hp.HP_ERR_INVALID_ARG
     assert lib.hp_partition_batch(one, 1, None, 65, None, None, None) == hp.HP_ERR_INVALID_ARG
     assert lib.hp_connectivity_noalloc(None, None, -1, None, None, 0, 0, None, None, None) == hp.HP_ERR_INVALID_ARG
     assert hp.hp_last_error() == "invalid argument"
+    assert lib.hp_batch_tuned_concurrency(0, 99) == 0 and lib.hp_batch_tuned_concurrency(-1, 0) == 0
 
 
 def test_struct_layout_matches_header(lib):

@@ -85,3 +85,23 @@ def test_batch_arguments(torch):
     one = (hp.hp_instance * 1)()
     assert lib.hp_partition_batch(one, 1, None, 0, None, None, None) == hp.HP_ERR_INVALID_ARG
     assert ctypes.sizeof(hp.hp_instance) == 64
+
+
+def test_autotuned_batch_matches_single_calls(torch):
+    """concurrency 0: the size-class autotuner only changes the schedule;
+    every instance is the single call's, bit for bit, and the classes with
+    enough instances get a tuned concurrency."""
+    graphs = inputs.batch_snn(40, seed=6, n_min=500, n_max=6000)
+    rc, res = hp.partition_batch(graphs, concurrency=0)
+    assert rc == hp.HP_OK, hp.hp_last_error()
+    for (g, om, de, sd), r in zip(graphs, res):
+        same(r, hp.partition(g, om, de, seed=sd))
+    dev = torch.cuda.current_device()
+    lib = hp.load()
+    tuned = [lib.hp_batch_tuned_concurrency(dev, c) for c in range(6)]
+    assert all(t in (0, 4, 8, 16, 32, 64) for t in tuned)
+    # a second call with the same classes reuses the tuned schedule
+    rc2, res2 = hp.partition_batch(graphs, concurrency=0)
+    assert rc2 == hp.HP_OK
+    for a, b in zip(res, res2):
+        same(a, b)

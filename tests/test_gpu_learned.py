@@ -128,6 +128,19 @@ def test_partition_matches_oracle(torch, idx):
             assert a[k] == b[k], (name, k)
 
 
+@pytest.mark.parametrize("levels", [1, 2, 5])
+def test_learned_levels_match_oracle(torch, levels):
+    g, omega, delta = inputs.workload("random_snn_4k"), 256, 1024
+    model = inputs.random_merge_model(31)
+    kw = dict(learned_k=16, model=model, learned_levels=levels)
+    r = hp.partition(g, omega, delta, seed=4, trace=True, **kw)
+    o = oracle.partition(g, omega, delta, seed=4, trace=True, **kw)
+    assert r.status == o.status == hp.HP_OK, hp.hp_last_error()
+    assert np.array_equal(r.part, o.part)
+    assert [t["pairs"] for t in r.trace] == [t["pairs"] for t in o.trace]
+    assert [t["targets_r1"] for t in r.trace] == [t["targets_r1"] for t in o.trace]
+
+
 def test_constant_model_is_plain_partition_on_gpu(torch):
     rng = np.random.default_rng(9)
     g = inputs.planted_components(rng.integers(3, 17, size=300).tolist(), 9, 4, seed=9)

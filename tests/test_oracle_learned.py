@@ -337,3 +337,29 @@ def test_degenerate_inputs_match_plain(case):
     lrn = oracle.partition(g, 2, 8, seed=3, trace=True, learned_k=4, model=inputs.random_merge_model(1))
     assert plain.status == lrn.status == oracle.OK
     assert np.array_equal(plain.part, lrn.part) and plain.stats == lrn.stats
+
+
+@pytest.mark.parametrize("k", [1, 2, 3])
+def test_learned_levels_limit_the_learned_ranking_to_the_first_levels(k):
+    """learned_levels = k: the first k levels are those of the fully learned
+    run (a level depends only on the levels before it); the deeper levels are
+    those a plain proposal makes of the hierarchy it receives."""
+    g = inputs.random_snn(600, 15, seed=11)
+    full = oracle.partition(g, 24, 96, seed=0, trace=True, learned_k=16, model=inputs.random_merge_model(3))
+    part = oracle.partition(g, 24, 96, seed=0, trace=True, learned_k=16, model=inputs.random_merge_model(3),
+                            learned_levels=k)
+    assert full.status == part.status == oracle.OK
+    nlev = min(k, len(full.trace) - 1)
+    for lv in range(nlev):
+        for key in ("n", "pins", "pairs", "iso_pairs", "valid", "iso_list", "targets_r1", "max_indeg_r1", "pairs_r1"):
+            assert part.trace[lv][key] == full.trace[lv][key], (k, lv, key)
+    assert part.trace[nlev]["n"] == full.trace[nlev]["n"]
+    assert part.stats["violations"] == 0
+    # a limit beyond the level count is the fully learned run
+    same = oracle.partition(g, 24, 96, seed=0, learned_k=16, model=inputs.random_merge_model(3), learned_levels=500)
+    assert np.array_equal(same.part, full.part)
+    # without learned_k the limit changes nothing
+    plain = oracle.partition(g, 24, 96, seed=0)
+    p2 = oracle.partition(g, 24, 96, seed=0, learned_levels=1)
+    assert np.array_equal(plain.part, p2.part)
+    assert oracle.partition(g, 24, 96, learned_levels=-1).status == oracle.ERR_INVALID_ARG
