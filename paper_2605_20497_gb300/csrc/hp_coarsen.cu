@@ -57,8 +57,16 @@ struct PropCtx {
     uint64_t *cscore;      // [n*pi]
     int32_t *nbcnt;        // [n] unique neighbours found (those that pass the size filter)
     const int32_t *canon;  // [e] hyperedges with equal destination lists share a value (or null)
+    const int32_t *canon_on;   // device scalar: nonzero when canon groups hyperedges (used only with canon)
     int32_t size_filter;   // 1: neighbours m with size(v) + size(m) > Omega are not entered in v's table
 };
+
+// The destination-list groups when they pay: a level whose lists are all
+// distinct (no group of two) walks every hyperedge alone, without the
+// CTA-wide queue of group walks.  Result-neutral: the table sums are the same.
+__device__ __forceinline__ const int32_t *dst_groups_of(const PropCtx &C) {
+    return (C.canon && *C.canon_on) ? C.canon : nullptr;
+}
 
 // A neighbour that fails the size half of Eq. 6 can never be a candidate,
 // so with the filter on it is not entered in the table at all.  The count of
@@ -322,7 +330,8 @@ __device__ __forceinline__ void warp_chunk(const PropCtx &C, int32_t v, int32_t 
     const unsigned bigm = __ballot_sync(FULL, large);
     if (!bigm) return;
     // groups of large hyperedges with equal destination lists
-    const int32_t key = large ? (C.canon ? C.canon[e] : e) : -1 - lane;
+    const int32_t *canon = dst_groups_of(C);
+    const int32_t key = large ? (canon ? canon[e] : e) : -1 - lane;
     const unsigned grp = __match_any_sync(FULL, key);
     const unsigned qlo = __reduce_add_sync(grp, large ? (unsigned)(qe & 0x1FFFFFull) : 0u);
     const unsigned qhi = __reduce_add_sync(grp, large ? (unsigned)(qe >> 21) : 0u);
@@ -378,18 +387,20 @@ struct BigQueue {
 // warp gets a share of them.  Stops early (for every thread) once *stop is
 // set.
 //
-// On levels without destination-list groups (C.canon null: small hyperedges,
-// the coarse levels) the warps walk their own 32-entry chunks one after
-// another with no CTA barrier between chunks, each warp taking its large
-// hyperedges itself: the chunks' load chains then overlap across warps.
+// On levels without destination-list groups (small hyperedges, the coarse
+// levels, nets whose lists are all distinct) every warp walks its own
+// contiguous share of ceil(deg / warps) incidence entries, 32 at a time, with
+// no CTA barrier until the end, and walks its large hyperedges itself: even
+// a node of a few dozen hyperedges spreads them over all warps.
 template <class Ins>
 __device__ void cta_walk(const PropCtx &C, int32_t v, int32_t i0, int32_t deg, int32_t nin_v, const int *stop,
                          BigQueue Q, Ins ins) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    if (!C.canon) {
-        for (int32_t base = wid * 32; base < deg; base += nw * 32) {
+    if (!dst_groups_of(C)) {
+        const int32_t share = (deg + nw - 1) / nw, lo = wid * share, hi = min(deg, lo + share);
+        for (int32_t base = lo; base < hi; base += 32) {
             if (__any_sync(0xffffffffu, stop ? *(volatile const int *)stop : 0)) break;
-            warp_chunk(C, v, i0, deg, nin_v, base + lane, ins, (NoBig *)nullptr);
+            warp_chunk(C, v, i0, deg, nin_v, base + lane < hi ? base + lane : deg, ins, (NoBig *)nullptr);
         }
         __syncthreads();
         return;
@@ -657,14 +668,26 @@ __global__ void __launch_bounds__(WP_T) k_propose_warp(PropCtx C, const int32_t 
             emit(tl, 0, C.pi);
         } else {
             // rounds of four, each below the last entry of the round before
+            // the first round stores each neighbour's noised score in its eta
+            // slot and its validity in its inter slot, the later rounds only
+            // compare
             Cand thr{~0ull, INT32_MAX};
             for (int r0 = 0; r0 < C.pi; r0 += EMIT_W) {
                 TopList<EMIT_W> tl;
                 tl.init();
                 for (uint32_t h = lane; h < cap; h += 32) {
                     const int32_t m = keys[h];
-                    if (m >= 0 && pair_valid(C, v, m, (int32_t)inter[h])) {
-                        const Cand c{eta[h] + pair_noise(C.level_key, v, m, capn), m};
+                    if (m < 0) continue;
+                    unsigned long long sc = eta[h];
+                    bool ok = inter[h] != 0;
+                    if (r0 == 0) {
+                        ok = pair_valid(C, v, m, (int32_t)inter[h]);
+                        if (ok) sc += pair_noise(C.level_key, v, m, capn);
+                        eta[h] = sc;
+                        inter[h] = ok ? 1u : 0u;
+                    }
+                    if (ok) {
+                        const Cand c{sc, m};
                         if (cand_gt(thr, c)) tl.push(c);
                     }
                 }
@@ -765,6 +788,8 @@ __device__ void propose_hashed_node(const PropCtx &C, int32_t v, int32_t *keys, 
         block_emit_top<PIMAX>(tl, C, v, s_top);
     } else {
         // rounds of four over the slot list, each below the last entry of the round before
+        // (the first round stores the noised scores in eta and the validity
+        // in inter)
         Cand thr{~0ull, INT32_MAX};
         for (int r0 = 0; r0 < C.pi; r0 += EMIT_W) {
             TopList<EMIT_W> tl;
@@ -772,8 +797,16 @@ __device__ void propose_hashed_node(const PropCtx &C, int32_t v, int32_t *keys, 
             for (int32_t i = threadIdx.x; i < used; i += blockDim.x) {
                 const int32_t h = slots[i];
                 const int32_t m = keys[h];
-                if (pair_valid(C, v, m, (int32_t)inter[h])) {
-                    const Cand c{eta[h] + pair_noise(C.level_key, v, m, capn), m};
+                unsigned long long sc = eta[h];
+                bool ok = inter[h] != 0;
+                if (r0 == 0) {
+                    ok = pair_valid(C, v, m, (int32_t)inter[h]);
+                    if (ok) sc += pair_noise(C.level_key, v, m, capn);
+                    eta[h] = sc;
+                    inter[h] = ok ? 1u : 0u;
+                }
+                if (ok) {
+                    const Cand c{sc, m};
                     if (cand_gt(thr, c)) tl.push(c);
                 }
             }
@@ -1364,7 +1397,7 @@ static CoarsenWs *coarsen_workspace_body(CoarsenWs *W, int32_t n, int32_t e, con
     W->ce = e;
     W->pi = pi;
     W->q = A.get<uint64_t>(e);
-    W->canon = A.get<int32_t>(std::max(e, 1));
+    W->canon = A.get<int32_t>(std::max(e, 1) + 1);   // + the flag of dst_groups_of
     W->cand = A.get<int32_t>((int64_t)n * K);
     W->cscore = A.get<uint64_t>((int64_t)n * K);
     if (P.o.learned_k > 0) {
@@ -1446,8 +1479,11 @@ LevelBox *coarsen_box(CoarsenWs *W) { return W->box; }
 
 // One coarsening level, entirely on the device (no host synchronisation);
 // the counters end up in the workspace box.
-// canon[] of the level's hyperedges (see k_dst_hash)
-static void dst_groups(const Level &L, int32_t *canon, Arena &A) {
+// on: the groups pay (on average two hyperedges or more per group)
+__global__ void k_dst_flag(const int32_t *ngroups, int32_t e, int32_t *on) { *on = 2 * (int64_t)*ngroups <= e; }
+
+// canon[] of the level's hyperedges (see k_dst_hash) and canon_on
+static void dst_groups(const Level &L, int32_t *canon, int32_t *canon_on, Arena &A) {
     cudaStream_t s = A.stream();
     const int32_t e = L.e;
     if (e <= 0) return;
@@ -1462,6 +1498,8 @@ static void dst_groups(const Level &L, int32_t *canon, Arena &A) {
     k_dst_rep<<<grid_of(e, 256), 256, 0, s>>>(val, nr, rp, e, rep);
     HP_LAUNCH_CHECK();
     k_dst_canon<<<grid_of(e, 256), 256, 0, s>>>(val, nr, rp, rep, e, canon);
+    HP_LAUNCH_CHECK();
+    k_dst_flag<<<1, 1, 0, s>>>(rp + e, e, canon_on);
     HP_LAUNCH_CHECK();
     for (void *p : {(void *)key, (void *)val, (void *)nr, (void *)rp, (void *)rep}) A.release(p);
 }
@@ -1514,6 +1552,7 @@ static void propose_lists(Level &L, int32_t level, const int32_t *w, const Param
     C.cscore = W.cscore;
     C.nbcnt = L.nbnd;   // exact counts replace the bounds (used to size the next level)
     C.canon = nullptr;
+    C.canon_on = W.canon + std::max(W.ce, 1);
     // level 0 of a call has unit sizes (every pair passes when Omega >= 2):
     // no filter there, no size gathers
     C.size_filter = level > 0 ? 1 : 0;
@@ -1522,7 +1561,7 @@ static void propose_lists(Level &L, int32_t level, const int32_t *w, const Param
         // levels of large hyperedges: those with equal destination lists (the
         // channels of one source in a layered network, before and after
         // contraction) are walked once per warp group
-        dst_groups(L, W.canon, A);
+        dst_groups(L, W.canon, W.canon + std::max(W.ce, 1), A);
         C.canon = W.canon;
     }
     if (K <= 4) run_proposal<4>(C, L, P, W, A);

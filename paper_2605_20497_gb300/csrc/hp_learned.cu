@@ -65,63 +65,129 @@ __device__ __forceinline__ bool sorted_has(const int32_t *a, int32_t len, int32_
     return lo < len && a[lo] == x;
 }
 
-// one thread per listed pair (v, j): rank = position of v in the list of its
-// j-th candidate m (-1: not mutual, or no candidate), and the pair's sixteen
-// feature bytes (zero unless mutual)
-__global__ void k_merge_feats(LearnIn X) {
-    const int64_t base = (int64_t)X.v0 * X.K, total = (int64_t)(X.v1 - X.v0) * X.K;
-    GRID_STRIDE(q, total) {
-        const int64_t p = base + q;   // the pair; q its row in this pass
-        const int32_t v = (int32_t)(p / X.K), j = (int32_t)(p % X.K);
-        const int32_t m = X.candK[p];
-        int32_t rm = -1;
-        if (m >= 0) {
-            const int32_t *lm = X.candK + (int64_t)m * X.K;
-            for (int32_t i = 0; i < X.K; i++)
-                if (lm[i] == v) {
-                    rm = i;
-                    break;
-                }
-        }
-        uint32_t w0 = 0, w1 = 0, w2 = 0, w3 = 0;
-        if (rm >= 0) {
-            // walk the shorter incidence list; search the other's sorted in- and out-halves
-            const int32_t dv = X.ioff[v + 1] - X.ioff[v], dm = X.ioff[m + 1] - X.ioff[m];
-            const int32_t a = dv <= dm ? v : m, b = dv <= dm ? m : v;
-            const int32_t a0 = X.ioff[a], a1 = X.ioff[a + 1], a_in_end = a0 + X.nin[a];
-            const int32_t *b_in = X.inc + X.ioff[b];
-            const int32_t nb_in = X.nin[b], nb_out = X.ioff[b + 1] - X.ioff[b] - X.nin[b];
-            int64_t shared = 0, inter = 0;
-            for (int32_t t = a0; t < a1; t++) {
-                const int32_t e = X.inc[t];
-                if (sorted_has(b_in, nb_in, e)) {
-                    shared++;
-                    if (t < a_in_end) inter++;
-                } else if (sorted_has(b_in + nb_in, nb_out, e)) {
-                    shared++;
-                }
+// The sixteen feature bytes of the mutual pair (v, m), v's j-th candidate and
+// m's rm-th, from the shared and inbound-shared hyperedge counts.
+__device__ __forceinline__ uint4 pair_feature_bytes(const LearnIn &X, int64_t p, int32_t v, int32_t m, int32_t j,
+                                                    int32_t rm, int64_t shared, int64_t inter) {
+    const int32_t dv = X.ioff[v + 1] - X.ioff[v], dm = X.ioff[m + 1] - X.ioff[m];
+    const int64_t sv = X.size[v], sm = X.size[m], iv = X.nin[v], im = X.nin[m];
+    const int64_t uni = iv + im - inter;
+    const uint32_t f0 = log_code(X.csK[p]);
+    const uint32_t f1 = log_code((uint64_t)shared);
+    const uint32_t f2 = log_code((uint64_t)inter);
+    const uint32_t f3 = log_code((uint64_t)min(sv, sm)), f4 = log_code((uint64_t)max(sv, sm));
+    const uint32_t f5 = log_code((uint64_t)min(iv, im)), f6 = log_code((uint64_t)max(iv, im));
+    const uint32_t f7 = log_code((uint64_t)min(dv, dm)), f8 = log_code((uint64_t)max(dv, dm));
+    const uint32_t f9 = (uint32_t)(255 * (sv + sm) / X.omega);
+    const uint32_t f10 = X.delta > 0 ? (uint32_t)(255 * uni / X.delta) : 0u;
+    const uint32_t f11 = (uint32_t)min(X.level, 255);
+    const uint32_t f12 = uni > 0 ? (uint32_t)(255 * inter / uni) : 0u;
+    const uint32_t f13 = (uint32_t)min(j, rm), f14 = (uint32_t)max(j, rm);
+    const uint32_t f15 = log_code((uint64_t)(iv + im));
+    return make_uint4(f0 | f1 << 8 | f2 << 16 | f3 << 24, f4 | f5 << 8 | f6 << 16 | f7 << 24,
+                      f8 | f9 << 8 | f10 << 16 | f11 << 24, f12 | f13 << 8 | f14 << 16 | f15 << 24);
+}
+
+// position of v in the list of its j-th candidate m (-1: not mutual, or no candidate)
+__device__ __forceinline__ int32_t mutual_rank(const LearnIn &X, int32_t v, int32_t m) {
+    if (m < 0) return -1;
+    const int32_t *lm = X.candK + (int64_t)m * X.K;
+    for (int32_t i = 0; i < X.K; i++)
+        if (lm[i] == v) return i;
+    return -1;
+}
+
+// one listed pair (v, j) by one thread: its rank and, when mutual, its
+// features from the shorter incidence list searched in the other's sorted
+// in- and out-halves (zero bytes unless mutual)
+__device__ void merge_feats_pair(const LearnIn &X, int64_t q) {
+    const int64_t p = (int64_t)X.v0 * X.K + q;   // the pair; q its row in this pass
+    const int32_t v = (int32_t)(p / X.K), j = (int32_t)(p % X.K);
+    const int32_t m = X.candK[p];
+    const int32_t rm = mutual_rank(X, v, m);
+    uint4 f = make_uint4(0, 0, 0, 0);
+    if (rm >= 0) {
+        const int32_t dv = X.ioff[v + 1] - X.ioff[v], dm = X.ioff[m + 1] - X.ioff[m];
+        const int32_t a = dv <= dm ? v : m, b = dv <= dm ? m : v;
+        const int32_t a0 = X.ioff[a], a1 = X.ioff[a + 1], a_in_end = a0 + X.nin[a];
+        const int32_t *b_in = X.inc + X.ioff[b];
+        const int32_t nb_in = X.nin[b], nb_out = X.ioff[b + 1] - X.ioff[b] - X.nin[b];
+        int64_t shared = 0, inter = 0;
+        for (int32_t t = a0; t < a1; t++) {
+            const int32_t e = X.inc[t];
+            if (sorted_has(b_in, nb_in, e)) {
+                shared++;
+                if (t < a_in_end) inter++;
+            } else if (sorted_has(b_in + nb_in, nb_out, e)) {
+                shared++;
             }
-            const int64_t sv = X.size[v], sm = X.size[m], iv = X.nin[v], im = X.nin[m];
-            const int64_t uni = iv + im - inter;
-            const uint32_t f0 = log_code(X.csK[p]);
-            const uint32_t f1 = log_code((uint64_t)shared);
-            const uint32_t f2 = log_code((uint64_t)inter);
-            const uint32_t f3 = log_code((uint64_t)min(sv, sm)), f4 = log_code((uint64_t)max(sv, sm));
-            const uint32_t f5 = log_code((uint64_t)min(iv, im)), f6 = log_code((uint64_t)max(iv, im));
-            const uint32_t f7 = log_code((uint64_t)min(dv, dm)), f8 = log_code((uint64_t)max(dv, dm));
-            const uint32_t f9 = (uint32_t)(255 * (sv + sm) / X.omega);
-            const uint32_t f10 = X.delta > 0 ? (uint32_t)(255 * uni / X.delta) : 0u;
-            const uint32_t f11 = (uint32_t)min(X.level, 255);
-            const uint32_t f12 = uni > 0 ? (uint32_t)(255 * inter / uni) : 0u;
-            const uint32_t f13 = (uint32_t)min(j, rm), f14 = (uint32_t)max(j, rm);
-            const uint32_t f15 = log_code((uint64_t)(iv + im));
-            w0 = f0 | f1 << 8 | f2 << 16 | f3 << 24;
-            w1 = f4 | f5 << 8 | f6 << 16 | f7 << 24;
-            w2 = f8 | f9 << 8 | f10 << 16 | f11 << 24;
-            w3 = f12 | f13 << 8 | f14 << 16 | f15 << 24;
         }
-        reinterpret_cast<uint4 *>(X.feat)[q] = make_uint4(w0, w1, w2, w3);
-        X.rank[q] = rm;
+        f = pair_feature_bytes(X, p, v, m, j, rm, shared, inter);
+    }
+    reinterpret_cast<uint4 *>(X.feat)[q] = f;
+    X.rank[q] = rm;
+}
+
+// one thread per listed pair (the whole level, or the nodes of a pass)
+__global__ void k_merge_feats(LearnIn X) {
+    GRID_STRIDE(q, (int64_t)(X.v1 - X.v0) * X.K) merge_feats_pair(X, q);
+}
+
+// One warp per node v: v's incidence list is staged in shared memory, and
+// for each mutual candidate m the lanes walk m's list (coalesced) and look
+// each hyperedge up in v's sorted in- and out-halves there.  The counts are
+// the same set intersections as above.  A node whose list exceeds the
+// staging area takes the one-thread-per-pair form.
+constexpr int MF_T = 256, MF_CAP = 512;
+__global__ void __launch_bounds__(MF_T) k_merge_feats_node(LearnIn X) {
+    __shared__ int32_t s_inc[MF_T / 32][MF_CAP];
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int32_t *mine = s_inc[wid];
+    const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t u = gw; u < X.v1 - X.v0; u += nw) {
+        const int32_t v = X.v0 + (int32_t)u;
+        const int32_t v0i = X.ioff[v], dv = X.ioff[v + 1] - v0i, niv = X.nin[v];
+        if (dv > MF_CAP) {
+            for (int32_t j = lane; j < X.K; j += 32) merge_feats_pair(X, u * X.K + j);
+            continue;
+        }
+        for (int32_t t = lane; t < dv; t += 32) mine[t] = X.inc[v0i + t];
+        __syncwarp();
+        for (int32_t j = 0; j < X.K; j++) {
+            const int64_t q = u * X.K + j, p = (int64_t)v * X.K + j;
+            const int32_t m = X.candK[p];
+            // v's position in m's list: lane i checks entry i
+            int32_t rm = -1;
+            if (m >= 0) {
+                const bool hit = lane < X.K && X.candK[(int64_t)m * X.K + lane] == v;
+                const unsigned bal = __ballot_sync(FULL, hit);
+                rm = bal ? __ffs(bal) - 1 : -1;
+            }
+            uint4 f = make_uint4(0, 0, 0, 0);
+            if (rm >= 0) {
+                const int32_t m0 = X.ioff[m], dm = X.ioff[m + 1] - m0, nim = X.nin[m];
+                int32_t sh = 0, in = 0;
+                for (int32_t t = lane; t < dm; t += 32) {
+                    const int32_t e = X.inc[m0 + t];
+                    if (sorted_has(mine, niv, e)) {
+                        sh++;
+                        if (t < nim) in++;
+                    } else if (sorted_has(mine + niv, dv - niv, e)) {
+                        sh++;
+                    }
+                }
+                sh = __reduce_add_sync(FULL, sh);
+                in = __reduce_add_sync(FULL, in);
+                f = pair_feature_bytes(X, p, v, m, j, rm, sh, in);
+            }
+            if (lane == 0) {
+                reinterpret_cast<uint4 *>(X.feat)[q] = f;
+                X.rank[q] = rm;
+            }
+        }
+        __syncwarp();
     }
 }
 
@@ -719,7 +785,7 @@ void learned_candidates(LearnIn X, int32_t batch, cudaStream_t s) {
         X.v0 = v0;
         X.v1 = std::min<int64_t>((int64_t)v0 + B, X.n);
         const int64_t pairs = (int64_t)(X.v1 - X.v0) * X.K;
-        k_merge_feats<<<grid_for(pairs, 256), 256, 0, s>>>(X);
+        k_merge_feats_node<<<grid_for((int64_t)(X.v1 - X.v0) * 32, MF_T), MF_T, 0, s>>>(X);
         HP_LAUNCH_CHECK();
         merge_scores(X.feat, pairs, X.model, X.score, s);
         k_merge_select<<<grid_for(X.v1 - X.v0, 128), 128, 0, s>>>(X);

@@ -117,12 +117,14 @@ __device__ void plist_edge(int32_t e, int gt, const int32_t *off, const int32_t 
 }
 
 constexpr int PLW_T = 128;  // warp-per-edge kernel: 4 warps
+constexpr int32_t MID_SPLIT = 128;   // warp-tier hyperedges up to this size get small tables
 
 // edges with |e| <= small_max, one warp each, tables in shared memory
 __global__ void __launch_bounds__(PLW_T) k_plist_small(const int32_t *off, const int32_t *pin, const int32_t *nsrc,
                                                        const int32_t *w, const int32_t *rho, int32_t e,
                                                        const int32_t *list, int32_t small_max, uint32_t cap, Plist PL,
-                                                       int32_t *D, long long *saving, int32_t skip_below) {
+                                                       int32_t *D, long long *saving, int32_t skip_below,
+                                                       int32_t skip_above = INT32_MAX) {
     extern __shared__ __align__(16) int32_t sm[];
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
     // table of cap slots; entry buffers of cap / 2 >= lambda(e) entries
@@ -139,11 +141,11 @@ __global__ void __launch_bounds__(PLW_T) k_plist_small(const int32_t *off, const
     int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     // all hyperedges up to small_max pins, or the given list (count e) skipping
-    // the ones of at most skip_below pins
+    // the ones of at most skip_below or more than skip_above pins
     for (int64_t i = warp; i < e; i += nw) {
         const int32_t ed = list ? list[i] : (int32_t)i;
         const int32_t sz = off[ed + 1] - off[ed];
-        if ((!list && sz > small_max) || sz <= skip_below) continue;
+        if ((!list && sz > small_max) || sz <= skip_below || sz > skip_above) continue;
         plist_edge<32>(ed, lane, off, pin, nsrc, w, rho, keys, tc, tci, cap, es, ep, ec, eci, gcnt, PL, D, saving);
     }
 }
@@ -1335,6 +1337,7 @@ __global__ void k_apply(const int32_t *seqmove, const int32_t *node, const int32
 // cluster radix sorts.  Eight times the threads of one CTA, so the latency of
 // each phase's global loads is spread over 8 SMs.
 static_assert(SQ_T == SEQ_T, "cluster CTA size");
+constexpr int32_t SEQ_CLUSTER_M = 4096;   // moves of a larger level sequenced by one cluster
 static_assert(SMALL_LEVEL <= sq_max<uint64_t>() && 2 * SMALL_LEVEL <= sq_max<uint32_t>(),
               "a small level's moves fit the cluster sorts");
 
@@ -1651,7 +1654,12 @@ __device__ __forceinline__ int32_t plist_find(const Plist &PL, int32_t a, int32_
     return (lo < lam && PL.p[a + lo] == p) ? a + lo : -1;
 }
 
-// group of G threads; buffers: bk/bd/ord >= |e|, table tp/tc/tci >= 2|e|
+// group of G threads; buffers: bk/bd/ord >= |e|, tp/tc/tci >= 2|e|.
+// The running counts are not simulated move by move: the move at sequence
+// rank r sees pins(p,e) = the pins list's count + (moves of ranks < r into p)
+// - (moves of ranks < r out of p), and pins_in(p,e) the same over the moves
+// of destination pins, so every rank is evaluated at once (threads over
+// ranks, each counting over the ranks before it in shared memory).
 template <int G>
 __device__ void inseq_edge(const SeqSim &Q, int32_t e, int gt, int32_t *bk, int32_t *bd, int32_t *ord, int32_t *tp,
                            int32_t *tc, int32_t *tci, int32_t *g_cnt) {
@@ -1678,37 +1686,40 @@ __device__ void inseq_edge(const SeqSim &Q, int32_t e, int gt, int32_t *bk, int3
         ord[r] = i;
     }
     gsync<G>();
-    if (gt == 0) {
-        const long long we = Q.w[e];
-        const int32_t lam = Q.PL.lam[e];
-        int32_t nt = 0;
-        for (int32_t r = 0; r < c; r++) {
-            const int32_t i = ord[r], k = bk[i];
-            const int32_t mi = Q.seqmove[k];
-            const int32_t ps[2] = {Q.src[mi], Q.dst[mi]};
-            int32_t slot[2];
-            for (int h = 0; h < 2; h++) {
-                int32_t x = 0;
-                while (x < nt && tp[x] != ps[h]) x++;
-                if (x == nt) {
-                    int32_t f = plist_find(Q.PL, a, lam, ps[h]);
-                    tp[x] = ps[h];
-                    tc[x] = f >= 0 ? Q.PL.cnt[f] : 0;
-                    tci[x] = f >= 0 ? Q.PL.cin[f] : 0;
-                    nt++;
-                }
-                slot[h] = x;
+    // by rank: source part, destination part, destination-pin flag
+    int32_t *rs = tp, *rd = tp + c, *rf = tc;
+    for (int32_t r = gt; r < c; r += G) {
+        const int32_t i = ord[r], mi = Q.seqmove[bk[i]];
+        rs[r] = Q.src[mi];
+        rd[r] = Q.dst[mi];
+        rf[r] = bd[i];
+    }
+    gsync<G>();
+    const long long we = Q.w[e];
+    const int32_t lam = Q.PL.lam[e];
+    for (int32_t r = gt; r < c; r += G) {
+        const int32_t ps = rs[r], pd = rd[r];
+        const int32_t fs = plist_find(Q.PL, a, lam, ps), fd = plist_find(Q.PL, a, lam, pd);
+        int32_t cs = fs >= 0 ? Q.PL.cnt[fs] : 0, cd = fd >= 0 ? Q.PL.cnt[fd] : 0;
+        int32_t is = fs >= 0 ? Q.PL.cin[fs] : 0, id = fd >= 0 ? Q.PL.cin[fd] : 0;
+        for (int32_t t = 0; t < r; t++) {
+            const int32_t xs = rs[t], xd = rd[t];
+            const int32_t ds = (xd == ps) - (xs == ps), dd = (xd == pd) - (xs == pd);
+            cs += ds;
+            cd += dd;
+            if (rf[t]) {
+                is += ds;
+                id += dd;
             }
-            long long g = 0;
-            if (tc[slot[0]] == 1) g += we;
-            if (tc[slot[1]] == 0) g -= we;
-            if (g) atomicAdd(&Q.gseq[k], (unsigned long long)g);
-            tc[slot[0]]--;
-            tc[slot[1]]++;
-            if (bd[i]) {
-                if (--tci[slot[0]] == 0) atomicAdd(&Q.dDs[k], -1);
-                if (++tci[slot[1]] == 1) atomicAdd(&Q.dDd[k], 1);
-            }
+        }
+        const int32_t k = bk[ord[r]];
+        long long g = 0;
+        if (cs == 1) g += we;
+        if (cd == 0) g -= we;
+        if (g) atomicAdd(&Q.gseq[k], (unsigned long long)g);
+        if (rf[r]) {
+            if (is == 1) atomicAdd(&Q.dDs[k], -1);
+            if (id == 0) atomicAdd(&Q.dDd[k], 1);
         }
     }
     gsync<G>();
@@ -1757,8 +1768,9 @@ __global__ void k_touched(const int32_t *off, const int32_t *pin, const int32_t 
 }
 
 constexpr int IS_T = 128;
+// hyperedges of lo < |e| <= emax pins from the list, a warp each
 __global__ void __launch_bounds__(IS_T) k_inseq_small(SeqSim Q, const int32_t *list, const int32_t *count_p,
-                                                      int32_t emax, const int32_t *mcount) {
+                                                      int32_t emax, const int32_t *mcount, int32_t lo) {
     if (*mcount == 0) return;
     const int32_t count = *count_p;
     extern __shared__ __align__(16) int32_t sm[];
@@ -1768,7 +1780,10 @@ __global__ void __launch_bounds__(IS_T) k_inseq_small(SeqSim Q, const int32_t *l
             *tci = tc + 2 * emax, *gc = tci + 2 * emax;
     int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t i = warp; i < count; i += nw) inseq_edge<32>(Q, list[i], lane, bk, bd, ord, tp, tc, tci, gc);
+    for (int64_t i = warp; i < count; i += nw) {
+        const int32_t e = list[i], sz = Q.off[e + 1] - Q.off[e];
+        if (sz > lo && sz <= emax) inseq_edge<32>(Q, e, lane, bk, bd, ord, tp, tc, tci, gc);
+    }
 }
 __global__ void __launch_bounds__(256) k_inseq_big(SeqSim Q, const int32_t *list, int32_t count, int32_t emax,
                                                    int32_t *gbuf, const int32_t *mcount) {
@@ -2146,13 +2161,23 @@ static int32_t rep_run(const Level &L, const int32_t *w, const Params &P, int32_
         HP_LAUNCH_CHECK();
         // pins(p,e), pins_in(p,e), D(p), saving(v)
         if (W.n_mid > 0) {
-            const int per = 5 * (int)W.pcap + 1;
-            size_t sm = (size_t)per * 4 * (PLW_T / 32);
-            int occ = prepare_kernel((const void *)k_plist_small, PLW_T, sm);
-            int grid = (int)std::min<int64_t>(cdiv(W.n_mid, PLW_T / 32), (int64_t)num_sms() * occ);
-            k_plist_small<<<std::max(grid, 1), PLW_T, sm, s>>>(L.off, L.pin, L.nsrc, w, rho, W.n_mid, W.mid, W.small_max,
-                                                               W.pcap, W.PL, R.D0, R.saving, 0);
-            HP_LAUNCH_CHECK();
+            // hyperedges of up to MID_SPLIT pins in small tables (many warps
+            // per SM), the rest of the warp tier in tables for small_max pins
+            auto plist_mid = [&](uint32_t cap, int32_t lo, int32_t hi) {
+                const int per = 5 * (int)cap + 1;
+                size_t sm = (size_t)per * 4 * (PLW_T / 32);
+                int occ = prepare_kernel((const void *)k_plist_small, PLW_T, sm);
+                int grid = (int)std::min<int64_t>(cdiv(W.n_mid, PLW_T / 32), (int64_t)num_sms() * occ);
+                k_plist_small<<<std::max(grid, 1), PLW_T, sm, s>>>(L.off, L.pin, L.nsrc, w, rho, W.n_mid, W.mid,
+                                                                   W.small_max, cap, W.PL, R.D0, R.saving, lo, hi);
+                HP_LAUNCH_CHECK();
+            };
+            if (W.pcap > pow2_at_least(2 * MID_SPLIT)) {
+                plist_mid(pow2_at_least(2 * MID_SPLIT), 0, MID_SPLIT);
+                plist_mid(W.pcap, MID_SPLIT, INT32_MAX);
+            } else {
+                plist_mid(W.pcap, 0, INT32_MAX);
+            }
         }
         if (W.n_tiny > 0) {
             k_plist_tiny<<<grid_of(W.n_tiny, 128), 128, 0, s>>>(L.off, L.pin, L.nsrc, w, rho, W.tiny, W.n_tiny, W.PL, R.D0,
@@ -2280,8 +2305,10 @@ static int32_t rep_run(const Level &L, const int32_t *w, const Params &P, int32_
     // its destination, each round (few parts in use make that quadratic)
     const int64_t per_part = cdiv(m, std::max<int32_t>(W.parts_used, 1));
     const int64_t scan_work = (int64_t)m * std::min<int64_t>(P.o.chain_window, per_part);
+    // (on a larger level the device-wide path takes over above a few thousand
+    // moves: the cluster's eight SMs then lose to the whole GPU's phases)
     const bool small = m <= SMALLM,
-               one_cluster = small_level || (m <= sq_max<uint64_t>() && scan_work <= (int64_t(1) << 23));
+               one_cluster = small_level || (m <= SEQ_CLUSTER_M && scan_work <= (int64_t(1) << 21));
     if (one_cluster) {
         ClusterSeqArgs SA{W.M, W.S, W.keys, W.hkeys, W.idx, W.heads, W.first, W.lens, W.starts, W.cstart,
                           W.seqmove, R.mvpos, cnt, C, Q, nparts, P.o.chain_rounds, packed, gb, nb, sb, cgb, gbound,
@@ -2362,16 +2389,24 @@ static int32_t rep_run(const Level &L, const int32_t *w, const Params &P, int32_
     // in-sequence gains and distinct-inbound changes per move
     SeqSim Z{L.off, L.pin, L.nsrc, w, R.mvpos, W.seqmove, W.S.src, W.S.dst, W.PL, R.gseq, R.dDs, R.dDd};
     if (W.n_act > 0) {
-        size_t sm = (size_t)(9 * W.small_max + 1) * 4 * (IS_T / 32);
         k_touched<<<grid_of(W.n_act, 256), 256, 0, s>>>(L.off, L.pin, R.mvpos, W.act, W.n_act, W.touched,
                                                          cnt + C_TOUCH, W.ttouched, cnt + C_TTOUCH, cnt + C_MOVES);
         HP_LAUNCH_CHECK();
         k_inseq_tiny<<<grid_of(W.n_act, IST_T), IST_T, 0, s>>>(Z, W.ttouched, cnt + C_TTOUCH, cnt + C_MOVES);
         HP_LAUNCH_CHECK();
-        int occ = prepare_kernel((const void *)k_inseq_small, IS_T, sm);
-        int grid = (int)std::min<int64_t>(cdiv(W.n_act, IS_T / 32), (int64_t)num_sms() * occ);
-        k_inseq_small<<<std::max(grid, 1), IS_T, sm, s>>>(Z, W.touched, cnt + C_TOUCH, W.small_max, cnt + C_MOVES);
-        HP_LAUNCH_CHECK();
+        auto inseq_mid = [&](int32_t lo, int32_t emax) {
+            size_t sm = (size_t)(9 * emax + 1) * 4 * (IS_T / 32);
+            int occ = prepare_kernel((const void *)k_inseq_small, IS_T, sm);
+            int grid = (int)std::min<int64_t>(cdiv(W.n_act, IS_T / 32), (int64_t)num_sms() * occ);
+            k_inseq_small<<<std::max(grid, 1), IS_T, sm, s>>>(Z, W.touched, cnt + C_TOUCH, emax, cnt + C_MOVES, lo);
+            HP_LAUNCH_CHECK();
+        };
+        if (W.small_max > MID_SPLIT) {
+            inseq_mid(0, MID_SPLIT);
+            inseq_mid(MID_SPLIT, W.small_max);
+        } else {
+            inseq_mid(0, W.small_max);
+        }
     }
     if (W.n_big > 0) {
         k_inseq_big<<<W.pnb, 256, 0, s>>>(Z, W.big, W.n_big, W.cmax_e, W.ibuf, cnt + C_MOVES);
