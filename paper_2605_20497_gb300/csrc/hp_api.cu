@@ -29,15 +29,19 @@ static int grid_of(int64_t n, int block) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (n); i += (int64_t)gridDim.x * blockDim.x)
 
 __global__ void k_project(const int32_t *gamma, const int32_t *rho_coarse, int32_t n, int32_t *rho) {
+    HP_KERNEL_ENTER();
     GRID_STRIDE(v, (int64_t)n) rho[v] = rho_coarse[gamma[v]];
 }
 __global__ void k_used(const int32_t *rho, int32_t n, int32_t *used) {
+    HP_KERNEL_ENTER();
     GRID_STRIDE(v, (int64_t)n) used[rho[v]] = 1;
 }
 __global__ void k_compact_ids(const int32_t *rho, const int32_t *newid, int32_t n, int32_t *part) {
+    HP_KERNEL_ENTER();
     GRID_STRIDE(v, (int64_t)n) part[v] = newid[rho[v]];
 }
 __global__ void k_check_parts(const int32_t *part, int32_t n, int32_t nparts, uint32_t *err) {
+    HP_KERNEL_ENTER();
     GRID_STRIDE(v, (int64_t)n) {
         if (part[v] < 0 || part[v] >= nparts) atomicOr(err, E_INTERNAL);
     }
@@ -206,7 +210,7 @@ static hp_status run(const int32_t *pins, const int32_t *offsets, int32_t e, int
         Level &g = lv[l];
         if (l < L) {
             int32_t *r = A.get<int32_t>(g.n);
-            k_project<<<grid_of(g.n, 256), 256, 0, s>>>(g.gamma, rho, g.n, r);
+            launch_k(k_project, grid_of(g.n, 256), 256, 0, s, g.gamma, rho, g.n, r);
             HP_LAUNCH_CHECK();
             A.release(rho);
             rho = r;
@@ -234,14 +238,14 @@ static hp_status run(const int32_t *pins, const int32_t *offsets, int32_t e, int
     int32_t *used = A.get<int32_t>(nparts + 1);
     int32_t *newid = A.get<int32_t>(nparts + 1);
     HPC(cudaMemsetAsync(used, 0, sizeof(int32_t) * (nparts + 1), s));
-    k_used<<<grid_of(n, 256), 256, 0, s>>>(rho, n, used);
+    launch_k(k_used, grid_of(n, 256), 256, 0, s, rho, n, used);
     HP_LAUNCH_CHECK();
     scan_excl(used, newid, nparts, newid + nparts, A);
     const int32_t k = fetch<int32_t>(newid + nparts, s);
     int32_t *part = A.get<int32_t>(n);
-    k_compact_ids<<<grid_of(n, 256), 256, 0, s>>>(rho, newid, n, part);
+    launch_k(k_compact_ids, grid_of(n, 256), 256, 0, s, rho, newid, n, part);
     HP_LAUNCH_CHECK();
-    k_check_parts<<<grid_of(n, 256), 256, 0, s>>>(part, n, k, err_dev);
+    launch_k(k_check_parts, grid_of(n, 256), 256, 0, s, part, n, k, err_dev);
     HP_LAUNCH_CHECK();
     int64_t *ps = A.get<int64_t>(5);
     part_stats(lv[0], w, part, k, omega, delta, ps, A);
@@ -496,7 +500,7 @@ hp_status hp_connectivity(const int32_t *pins, const int32_t *offsets, int32_t n
         uint32_t *e2 = A.get<uint32_t>(1);
         HPC(cudaMemsetAsync(e2, 0, sizeof(uint32_t), s));
         if (num_nodes > 0) {
-            hp::k_check_parts<<<hp::grid_of(num_nodes, 256), 256, 0, s>>>(part, num_nodes, num_parts, e2);
+            hp::launch_k(hp::k_check_parts, hp::grid_of(num_nodes, 256), 256, 0, s, part, num_nodes, num_parts, e2);
             HP_LAUNCH_CHECK();
         }
         if (hp::fetch<uint32_t>(e2, s)) return HP_ERR_INVALID_ARG;

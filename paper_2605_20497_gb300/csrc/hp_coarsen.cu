@@ -82,6 +82,7 @@ __device__ __forceinline__ bool size_ok(const PropCtx &C, int32_t slack, int32_t
 
 // ---------------------------------------------------------------- per-level weights
 __global__ void k_level_q(const int32_t *off, const int32_t *w, int32_t e, uint64_t *q, unsigned long long *sum) {
+    HP_KERNEL_ENTER();
     __shared__ unsigned long long s;
     if (threadIdx.x == 0) s = 0;
     __syncthreads();
@@ -102,6 +103,7 @@ __global__ void k_level_q(const int32_t *off, const int32_t *w, int32_t e, uint6
 }
 
 __global__ void k_level_cap(const unsigned long long *sum, int32_t e, int32_t permille, uint64_t *cap) {
+    HP_KERNEL_ENTER();
     *cap = e > 0 ? (uint64_t)((*sum / (unsigned long long)e) * (unsigned long long)permille / 1000ull) : 0ull;
 }
 
@@ -110,6 +112,7 @@ __global__ void k_level_cap(const unsigned long long *sum, int32_t e, int32_t pe
 // inside a warp, so hub nodes with huge incidence lists spread over threads
 __global__ void k_node_sums(const int32_t *off, const int32_t *inc, const int32_t *inode, int64_t np,
                             long long *nsum, long long *vis, unsigned long long *visits) {
+    HP_KERNEL_ENTER();
     const int lane = threadIdx.x & 31;
     const int64_t wbase = ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5) << 5;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -137,6 +140,7 @@ __global__ void k_node_sums(const int32_t *off, const int32_t *inc, const int32_
 }
 
 __global__ void k_node_bounds(const long long *nsum, int32_t n, int32_t *bound) {
+    HP_KERNEL_ENTER();
     GRID_STRIDE(v, (int64_t)n) {
         long long b = bound[v];
         if (nsum[v] < b) b = nsum[v];
@@ -453,6 +457,7 @@ __device__ __forceinline__ uint32_t fmix32(uint32_t h) {
 }
 __global__ void k_dst_hash(const int32_t *off, const int32_t *pin, const int32_t *nsrc, int32_t e, uint32_t *key,
                            uint32_t *val) {
+    HP_KERNEL_ENTER();
     const int lane = threadIdx.x & 31;
     const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5, nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t i = w0; i < e; i += nw) {
@@ -468,6 +473,7 @@ __global__ void k_dst_hash(const int32_t *off, const int32_t *pin, const int32_t
 }
 __global__ void k_dst_runs(const uint32_t *key, const uint32_t *val, const int32_t *off, const int32_t *pin,
                            const int32_t *nsrc, int32_t e, int32_t *newrun) {
+    HP_KERNEL_ENTER();
     const int lane = threadIdx.x & 31;
     const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5, nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t i = w0; i < e; i += nw) {
@@ -483,12 +489,14 @@ __global__ void k_dst_runs(const uint32_t *key, const uint32_t *val, const int32
     }
 }
 __global__ void k_dst_rep(const uint32_t *val, const int32_t *newrun, const int32_t *runpos, int32_t e, int32_t *rep) {
+    HP_KERNEL_ENTER();
     GRID_STRIDE(i, (int64_t)e) {
         if (newrun[i]) rep[runpos[i]] = (int32_t)val[i];
     }
 }
 __global__ void k_dst_canon(const uint32_t *val, const int32_t *newrun, const int32_t *runpos, const int32_t *rep,
                             int32_t e, int32_t *canon) {
+    HP_KERNEL_ENTER();
     GRID_STRIDE(i, (int64_t)e) canon[val[i]] = rep[runpos[i] + newrun[i] - 1];
 }
 
@@ -497,6 +505,7 @@ __global__ void k_dst_canon(const uint32_t *val, const int32_t *newrun, const in
 // most DENSE_N nodes, nodes with large neighbourhoods).
 template <int PIMAX, int BT>
 __global__ void __launch_bounds__(BT) k_propose_dense(PropCtx C, const int32_t *list, const int32_t *count_p) {
+    HP_KERNEL_ENTER();
     extern __shared__ __align__(16) unsigned char smem[];
     unsigned long long *eta = reinterpret_cast<unsigned long long *>(smem);
     uint32_t *inter = reinterpret_cast<uint32_t *>(eta + C.n);
@@ -597,6 +606,7 @@ __device__ __forceinline__ void warp_insert(int32_t *keys, unsigned long long *e
 template <int PIMAX>
 __global__ void __launch_bounds__(WP_T) k_propose_warp(PropCtx C, const int32_t *list, const int32_t *count_p,
                                                        uint32_t cap) {
+    HP_KERNEL_ENTER();
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwb = WP_T / 32;
     unsigned long long *eta = reinterpret_cast<unsigned long long *>(smem) + (size_t)wid * cap;
@@ -830,6 +840,7 @@ __device__ void propose_hashed_node(const PropCtx &C, int32_t v, int32_t *keys, 
 template <int PIMAX, int BT>
 __global__ void __launch_bounds__(BT) k_propose_smem(PropCtx C, const int32_t *list, const int32_t *count_p,
                                                      uint32_t cap, uint32_t limit, int32_t *ovf, int32_t *ovf_n) {
+    HP_KERNEL_ENTER();
     extern __shared__ __align__(16) unsigned char smem[];
     unsigned long long *eta = reinterpret_cast<unsigned long long *>(smem);
     uint32_t *inter = reinterpret_cast<uint32_t *>(eta + cap);
@@ -868,6 +879,7 @@ __global__ void __launch_bounds__(PT) k_propose_global(PropCtx C, const int32_t 
                                                        uint32_t gcap, int32_t *gkeys, unsigned long long *geta,
                                                        uint32_t *ginter, int32_t *gslots, int32_t *err_list,
                                                        int32_t *err_n) {
+    HP_KERNEL_ENTER();
     __shared__ Cand s_top[32 * PIMAX];
     __shared__ int32_t s_qe[PT];
     __shared__ unsigned long long s_qq[PT];
@@ -901,6 +913,7 @@ constexpr int32_t HUB_INCIDENCE = 4096;   // incidence entries: chunks of a 512-
 __global__ void k_tiers(const int32_t *bound, const long long *vis, const int32_t *ioff, int32_t n,
                         uint32_t warp_limit, int32_t dense_bound, int32_t *lW, int32_t *lB, int32_t *lH, int32_t *lD,
                         int32_t *lDH, int32_t *cnt, int32_t pi, int32_t *cand, uint64_t *cscore) {
+    HP_KERNEL_ENTER();
     GRID_STRIDE(v, (int64_t)n) {
         if (bound[v] == 0) {
             // no (size-valid) neighbour: an empty candidate list, no walk
@@ -961,7 +974,7 @@ static void run_proposal(const PropCtx &C, Level &L, const Params &P, CoarsenWs 
     // dense tables only on small levels, for neighbourhoods too large for the first hashed table
     const int32_t dense_bound = (C.n <= DENSE_N && dbg == 0) ? (int32_t)(capB / 2) : 0x7fffffff;
     HPC(cudaMemsetAsync(W.cnt, 0, 8 * sizeof(int32_t), s));
-    k_tiers<<<grid_of(C.n, 256), 256, 0, s>>>(L.nbnd, W.vis, L.ioff, C.n, wcap / 2, dense_bound, W.lW, W.lB, W.lH,
+    launch_k(k_tiers, grid_of(C.n, 256), 256, 0, s, L.nbnd, W.vis, L.ioff, C.n, wcap / 2, dense_bound, W.lW, W.lB, W.lH,
                                               W.lD, W.lDH, W.cnt, C.pi, C.cand, C.cscore);
     HP_LAUNCH_CHECK();
     // the tiers take disjoint node lists, so they run side by side: the warp
@@ -975,26 +988,26 @@ static void run_proposal(const PropCtx &C, Level &L, const Params &P, CoarsenWs 
         size_t sm = (size_t)wcap * 16 * (WP_T / 32);
         int occ = prepare_kernel((const void *)k_propose_warp<PIMAX>, WP_T, sm);
         int grid = (int)std::min<int64_t>(cdiv(C.n, WP_T / 32), (int64_t)sms * occ);
-        k_propose_warp<PIMAX><<<std::max(grid, 1), WP_T, sm, sw>>>(C, W.lW, W.cnt + 0, wcap);
+        launch_k(k_propose_warp<PIMAX>, std::max(grid, 1), WP_T, sm, sw, C, W.lW, W.cnt + 0, wcap);
         HP_LAUNCH_CHECK();
     }
     if (dense_bound != 0x7fffffff) {
         size_t sm = (size_t)C.n * 12;
         int occ = prepare_kernel((const void *)k_propose_dense<PIMAX, PT>, PT, sm);
-        k_propose_dense<PIMAX, PT><<<std::max(1, std::min<int>(C.n, sms * occ)), PT, sm, sd>>>(C, W.lD, W.cnt + 6);
+        launch_k(k_propose_dense<PIMAX, PT>, std::max(1, std::min<int>(C.n, sms * occ)), PT, sm, sd, C, W.lD, W.cnt + 6);
         HP_LAUNCH_CHECK();
         prepare_kernel((const void *)k_propose_dense<PIMAX, 1024>, 1024, sm);
-        k_propose_dense<PIMAX, 1024><<<sms, 1024, sm, sd>>>(C, W.lDH, W.cnt + 7);
+        launch_k(k_propose_dense<PIMAX, 1024>, sms, 1024, sm, sd, C, W.lDH, W.cnt + 7);
         HP_LAUNCH_CHECK();
     }
     auto smem_of = [](uint32_t cap) { return (size_t)cap * 16 + (size_t)(cap * 3 / 4) * 4; };
     {
         size_t sm = smem_of(capB);
         prepare_kernel((const void *)k_propose_smem<PIMAX, 1024>, 1024, sm);
-        k_propose_smem<PIMAX, 1024><<<sms, 1024, sm, sh>>>(C, W.lH, W.cnt + 5, capB, capB * 3 / 4, W.lC, W.cnt + 2);
+        launch_k(k_propose_smem<PIMAX, 1024>, sms, 1024, sm, sh, C, W.lH, W.cnt + 5, capB, capB * 3 / 4, W.lC, W.cnt + 2);
         HP_LAUNCH_CHECK();
         int occ = prepare_kernel((const void *)k_propose_smem<PIMAX, 512>, 512, sm);
-        k_propose_smem<PIMAX, 512><<<std::max(1, std::min<int>(C.n, sms * occ)), 512, sm, s>>>(
+        launch_k(k_propose_smem<PIMAX, 512>, std::max(1, std::min<int>(C.n, sms * occ)), 512, sm, s,
             C, W.lB, W.cnt + 1, capB, capB * 3 / 4, W.lC, W.cnt + 2);
         HP_LAUNCH_CHECK();
     }
@@ -1004,7 +1017,7 @@ static void run_proposal(const PropCtx &C, Level &L, const Params &P, CoarsenWs 
         // nodes whose neighbourhood outgrew the first table (the bound can be far above the truth)
         size_t sm = smem_of(capC);
         int occ = prepare_kernel((const void *)k_propose_smem<PIMAX, PT>, PT, sm);
-        k_propose_smem<PIMAX, PT><<<std::max(1, std::min<int>(C.n, sms * occ)), PT, sm, s>>>(
+        launch_k(k_propose_smem<PIMAX, PT>, std::max(1, std::min<int>(C.n, sms * occ)), PT, sm, s,
             C, W.lC, W.cnt + 2, capC, capC * 3 / 4, W.lG, W.cnt + 3);
         HP_LAUNCH_CHECK();
     }
@@ -1012,7 +1025,7 @@ static void run_proposal(const PropCtx &C, Level &L, const Params &P, CoarsenWs 
     HPC(cudaEventRecord(W.ev[2], sd));
     HPC(cudaStreamWaitEvent(s, W.ev[1], 0));
     HPC(cudaStreamWaitEvent(s, W.ev[2], 0));
-    k_propose_global<PIMAX><<<W.gnb, PT, 0, s>>>(C, W.lG, W.cnt + 3, W.gcap, W.gkeys, W.geta, W.ginter, W.gslots,
+    launch_k(k_propose_global<PIMAX>, W.gnb, PT, 0, s, C, W.lG, W.cnt + 3, W.gcap, W.gkeys, W.geta, W.ginter, W.gslots,
                                                   W.lW, W.cnt + 4);
     HP_LAUNCH_CHECK();
 }
@@ -1050,14 +1063,17 @@ __device__ __forceinline__ void ph_iso_pair(const uint32_t *ids, int32_t k, cons
     }
 }
 __global__ void k_iso_flags(const int32_t *cand, int32_t pi, int32_t n, int32_t *flag) {
+    HP_KERNEL_ENTER();
     ph_iso_flags(cand, pi, n, flag, K_T0, K_NT);
 }
 __global__ void k_iso_compact(const int32_t *flag, const int32_t *pos, const int32_t *size, int32_t n, uint32_t *keys,
                               uint32_t *vals) {
+    HP_KERNEL_ENTER();
     ph_iso_compact(flag, pos, size, n, keys, vals, K_T0, K_NT);
 }
 __global__ void k_iso_pair(const uint32_t *ids, const int32_t *cntp, const int32_t *size, const int32_t *nin,
                            int32_t omega, int32_t delta, int32_t *mate, unsigned long long *pairs) {
+    HP_KERNEL_ENTER();
     ph_iso_pair(ids, *cntp, size, nin, omega, delta, mate, pairs, K_T0, K_NT);
 }
 
@@ -1105,9 +1121,11 @@ __device__ __forceinline__ void ph_child_count(const int32_t *target, int32_t n,
 __global__ void k_targets(const int32_t *cand, const uint64_t *cscore, int32_t pi, const int32_t *mate, int32_t n,
                           int32_t *target, uint64_t *score, long long *sum0, long long *kmax, int32_t *best,
                           int32_t *ccount, int32_t *pending) {
+    HP_KERNEL_ENTER();
     ph_targets(cand, cscore, pi, mate, n, target, score, sum0, kmax, best, ccount, pending, K_T0, K_NT);
 }
 __global__ void k_child_count(const int32_t *target, int32_t n, int32_t *ccount, int32_t *pending) {
+    HP_KERNEL_ENTER();
     ph_child_count(target, n, ccount, pending, K_T0, K_NT);
 }
 
@@ -1286,11 +1304,13 @@ __device__ __forceinline__ void ph_indeg(const int32_t *target, const int32_t *c
     }
 }
 __global__ void k_indeg(const int32_t *target, const int32_t *ccount, int32_t n, LevelBox *box) {
+    HP_KERNEL_ENTER();
     ph_indeg(target, ccount, n, box, K_T0, K_NT);
 }
-__global__ void k_dp_up(DpCtx D) { ph_dp_up(D, K_T0, K_NT); }
-__global__ void k_best_child(DpCtx D) { ph_best_child(D, K_T0, K_NT); }
+__global__ void k_dp_up(DpCtx D) { HP_KERNEL_ENTER(); ph_dp_up(D, K_T0, K_NT); }
+__global__ void k_best_child(DpCtx D) { HP_KERNEL_ENTER(); ph_best_child(D, K_T0, K_NT); }
 __global__ void k_dp_down(DpCtx D, const int32_t *target, int32_t *mate, unsigned long long *pairs) {
+    HP_KERNEL_ENTER();
     ph_dp_down(D, target, mate, pairs, K_T0, K_NT);
 }
 
@@ -1315,6 +1335,7 @@ struct MatchArgs {
     DpCtx D;
 };
 __global__ void __cluster_dims__(SQ_CS, 1, 1) __launch_bounds__(SQ_T) k_match_cluster(MatchArgs A) {
+    HP_KERNEL_ENTER();
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ uint32_t s_wc[32 * 256];
     __shared__ uint32_t s_tot[256];
@@ -1361,12 +1382,14 @@ __global__ void __cluster_dims__(SQ_CS, 1, 1) __launch_bounds__(SQ_T) k_match_cl
 }
 
 __global__ void k_sum_i32(const int32_t *x, int32_t n, unsigned long long *sum) {
+    HP_KERNEL_ENTER();
     unsigned long long loc = 0;
     GRID_STRIDE(i, (int64_t)n) loc += (unsigned long long)x[i];
     for (int o = 16; o > 0; o >>= 1) loc += __shfl_down_sync(0xffffffffu, loc, o);
     if ((threadIdx.x & 31) == 0) atomicAdd(sum, loc);
 }
 __global__ void k_flag_if_nonzero(const int32_t *x, uint32_t *err) {
+    HP_KERNEL_ENTER();
     if (*x) atomicOr(err, E_INTERNAL);
 }
 
@@ -1480,7 +1503,7 @@ LevelBox *coarsen_box(CoarsenWs *W) { return W->box; }
 // One coarsening level, entirely on the device (no host synchronisation);
 // the counters end up in the workspace box.
 // on: the groups pay (on average two hyperedges or more per group)
-__global__ void k_dst_flag(const int32_t *ngroups, int32_t e, int32_t *on) { *on = 2 * (int64_t)*ngroups <= e; }
+__global__ void k_dst_flag(const int32_t *ngroups, int32_t e, int32_t *on) { HP_KERNEL_ENTER(); *on = 2 * (int64_t)*ngroups <= e; }
 
 // canon[] of the level's hyperedges (see k_dst_hash) and canon_on
 static void dst_groups(const Level &L, int32_t *canon, int32_t *canon_on, Arena &A) {
@@ -1489,17 +1512,17 @@ static void dst_groups(const Level &L, int32_t *canon, int32_t *canon_on, Arena 
     if (e <= 0) return;
     uint32_t *key = A.get<uint32_t>(e), *val = A.get<uint32_t>(e);
     int32_t *nr = A.get<int32_t>(e), *rp = A.get<int32_t>(e + 1), *rep = A.get<int32_t>(e);
-    k_dst_hash<<<grid_of((int64_t)e * 32, 256), 256, 0, s>>>(L.off, L.pin, L.nsrc, e, key, val);
+    launch_k(k_dst_hash, grid_of((int64_t)e * 32, 256), 256, 0, s, L.off, L.pin, L.nsrc, e, key, val);
     HP_LAUNCH_CHECK();
     radix_sort(key, val, e, 32, A);
-    k_dst_runs<<<grid_of((int64_t)e * 32, 256), 256, 0, s>>>(key, val, L.off, L.pin, L.nsrc, e, nr);
+    launch_k(k_dst_runs, grid_of((int64_t)e * 32, 256), 256, 0, s, key, val, L.off, L.pin, L.nsrc, e, nr);
     HP_LAUNCH_CHECK();
     scan_excl(nr, rp, e, rp + e, A);
-    k_dst_rep<<<grid_of(e, 256), 256, 0, s>>>(val, nr, rp, e, rep);
+    launch_k(k_dst_rep, grid_of(e, 256), 256, 0, s, val, nr, rp, e, rep);
     HP_LAUNCH_CHECK();
-    k_dst_canon<<<grid_of(e, 256), 256, 0, s>>>(val, nr, rp, rep, e, canon);
+    launch_k(k_dst_canon, grid_of(e, 256), 256, 0, s, val, nr, rp, rep, e, canon);
     HP_LAUNCH_CHECK();
-    k_dst_flag<<<1, 1, 0, s>>>(rp + e, e, canon_on);
+    launch_k(k_dst_flag, 1, 1, 0, s, rp + e, e, canon_on);
     HP_LAUNCH_CHECK();
     for (void *p : {(void *)key, (void *)val, (void *)nr, (void *)rp, (void *)rep}) A.release(p);
 }
@@ -1514,18 +1537,18 @@ static void propose_lists(Level &L, int32_t level, const int32_t *w, const Param
     LevelBox *box = W.box;
     HPC(cudaMemsetAsync(box, 0, sizeof(LevelBox), s));
     if (L.e > 0) {
-        k_level_q<<<grid_of(L.e, 256), 256, 0, s>>>(L.off, w, L.e, W.q, &box->qsum);
+        launch_k(k_level_q, grid_of(L.e, 256), 256, 0, s, L.off, w, L.e, W.q, &box->qsum);
         HP_LAUNCH_CHECK();
     }
-    k_level_cap<<<1, 1, 0, s>>>(&box->qsum, L.e, P.o.noise_permille, &box->cap);
+    launch_k(k_level_cap, 1, 1, 0, s, &box->qsum, L.e, P.o.noise_permille, &box->cap);
     HP_LAUNCH_CHECK();
     HPC(cudaMemsetAsync(W.nsum, 0, sizeof(long long) * n, s));
     HPC(cudaMemsetAsync(W.vis, 0, sizeof(long long) * n, s));
     if (L.np > 0) {
-        k_node_sums<<<grid_of(L.np, 256), 256, 0, s>>>(L.off, L.inc, L.inode, L.np, W.nsum, W.vis, &box->visits);
+        launch_k(k_node_sums, grid_of(L.np, 256), 256, 0, s, L.off, L.inc, L.inode, L.np, W.nsum, W.vis, &box->visits);
         HP_LAUNCH_CHECK();
     }
-    k_node_bounds<<<grid_of(n, 256), 256, 0, s>>>(W.nsum, n, L.nbnd);
+    launch_k(k_node_bounds, grid_of(n, 256), 256, 0, s, W.nsum, n, L.nbnd);
     HP_LAUNCH_CHECK();
     PropCtx C;
     C.n = n;
@@ -1598,7 +1621,7 @@ void level_features(Level &L, const int32_t *w, const Params &P, CoarsenWs &W, A
     const int32_t K = P.o.learned_k;
     if (L.n == 0) return;
     propose_lists(L, 0, w, P, K, W, A, nullptr);
-    k_flag_if_nonzero<<<1, 1, 0, s>>>(W.cnt + 4, err_dev);
+    launch_k(k_flag_if_nonzero, 1, 1, 0, s, W.cnt + 4, err_dev);
     HP_LAUNCH_CHECK();
     LearnIn X = learn_in(L, 0, P, K, W);
     X.feat = feat_out;
@@ -1630,9 +1653,9 @@ void coarsen_level(Level &L, int32_t level, const int32_t *w, const Params &P, i
         learned_candidates(X, P.o.node_batch, s);
     }
     if (prop_events) HPC(cudaEventRecord(prop_events[1], s));
-    k_flag_if_nonzero<<<1, 1, 0, s>>>(W.cnt + 4, err_dev);
+    launch_k(k_flag_if_nonzero, 1, 1, 0, s, W.cnt + 4, err_dev);
     HP_LAUNCH_CHECK();
-    k_sum_i32<<<grid_of(n, 256), 256, 0, s>>>(L.nbnd, n, &box->nbrs);
+    launch_k(k_sum_i32, grid_of(n, 256), 256, 0, s, L.nbnd, n, &box->nbrs);
     HP_LAUNCH_CHECK();
     if (cand_out) {
         HPC(cudaMemcpyAsync(cand_out, cand, sizeof(int32_t) * n * pi, cudaMemcpyDeviceToDevice, s));
@@ -1658,39 +1681,39 @@ void coarsen_level(Level &L, int32_t level, const int32_t *w, const Params &P, i
         MatchArgs M{W.cand, K, cand, cscore, pi, n, P.omega, P.delta, L.size, L.nin, W.flag, W.pos, W.ikeys, W.iids,
                     bits_for((uint64_t)P.omega), mate, box, W.target, W.ccount, W.score, D};
         prepare_kernel((const void *)k_match_cluster, SQ_T, SQ_SMEM);
-        k_match_cluster<<<SQ_CS, SQ_T, SQ_SMEM, s>>>(M);
+        launch_k(k_match_cluster, SQ_CS, SQ_T, SQ_SMEM, s, M);
         HP_LAUNCH_CHECK();
         return;
     }
 
     // best-effort pairing of nodes with no valid neighbour (Sec. V-C)
-    k_iso_flags<<<grid_of(n, 256), 256, 0, s>>>(W.cand, K, n, W.flag);
+    launch_k(k_iso_flags, grid_of(n, 256), 256, 0, s, W.cand, K, n, W.flag);
     HP_LAUNCH_CHECK();
     scan_excl(W.flag, W.pos, n, W.pos + n, A);
     HPC(cudaMemcpyAsync(&box->isolist, W.pos + n, sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
-    k_iso_compact<<<grid_of(n, 256), 256, 0, s>>>(W.flag, W.pos, L.size, n, W.ikeys, W.iids);
+    launch_k(k_iso_compact, grid_of(n, 256), 256, 0, s, W.flag, W.pos, L.size, n, W.ikeys, W.iids);
     HP_LAUNCH_CHECK();
     radix_sort_dev(W.ikeys, W.iids, W.pos + n, n, bits_for((uint64_t)P.omega), A);
-    k_iso_pair<<<grid_of(n / 2 + 1, 256), 256, 0, s>>>(W.iids, W.pos + n, L.size, L.nin, P.omega, P.delta, mate,
+    launch_k(k_iso_pair, grid_of(n / 2 + 1, 256), 256, 0, s, W.iids, W.pos + n, L.size, L.nin, P.omega, P.delta, mate,
                                                          &box->iso);
     HP_LAUNCH_CHECK();
 
     // Pi rounds of maximum-weight matching (Sec. V-D)
     for (int32_t r = 0; r < pi; r++) {
-        k_targets<<<grid_of(n, 256), 256, 0, s>>>(cand, cscore, pi, mate, n, W.target, W.score, W.sum0, W.kmax,
+        launch_k(k_targets, grid_of(n, 256), 256, 0, s, cand, cscore, pi, mate, n, W.target, W.score, W.sum0, W.kmax,
                                                   W.best, W.ccount, W.fillpos);
         HP_LAUNCH_CHECK();
-        k_child_count<<<grid_of(n, 256), 256, 0, s>>>(W.target, n, W.ccount, W.fillpos);
+        launch_k(k_child_count, grid_of(n, 256), 256, 0, s, W.target, n, W.ccount, W.fillpos);
         HP_LAUNCH_CHECK();
         if (r == 0) {
-            k_indeg<<<grid_of(n, 256), 256, 0, s>>>(W.target, W.ccount, n, box);
+            launch_k(k_indeg, grid_of(n, 256), 256, 0, s, W.target, W.ccount, n, box);
             HP_LAUNCH_CHECK();
         }
-        k_dp_up<<<grid_of(n, 256), 256, 0, s>>>(D);
+        launch_k(k_dp_up, grid_of(n, 256), 256, 0, s, D);
         HP_LAUNCH_CHECK();
-        k_best_child<<<grid_of(n, 256), 256, 0, s>>>(D);
+        launch_k(k_best_child, grid_of(n, 256), 256, 0, s, D);
         HP_LAUNCH_CHECK();
-        k_dp_down<<<grid_of(n, 256), 256, 0, s>>>(D, W.target, mate, &box->pairs);
+        launch_k(k_dp_down, grid_of(n, 256), 256, 0, s, D, W.target, mate, &box->pairs);
         HP_LAUNCH_CHECK();
         if (r == 0)
             HPC(cudaMemcpyAsync(&box->pairs1, &box->pairs, sizeof(unsigned long long), cudaMemcpyDeviceToDevice, s));

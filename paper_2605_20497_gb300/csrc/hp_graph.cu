@@ -17,6 +17,7 @@ static int grid_of(int64_t n, int block) {
 
 // ---------------------------------------------------------------- checks
 __global__ void k_check_offsets(const int32_t *off, int32_t e, uint32_t *err) {
+    HP_KERNEL_ENTER();
     GRID_STRIDE(i, (int64_t)e) {
         if (off[i + 1] <= off[i]) atomicOr(err, E_OFFSETS);
     }
@@ -25,6 +26,7 @@ __global__ void k_check_offsets(const int32_t *off, int32_t e, uint32_t *err) {
 
 __global__ void k_edges_level0(const int32_t *off, int32_t e, const int32_t *src_counts, const int32_t *weights,
                                int32_t kind, int32_t *nsrc, int32_t *w, unsigned long long *wsum, uint32_t *err) {
+    HP_KERNEL_ENTER();
     GRID_STRIDE(i, (int64_t)e) {
         int32_t sz = off[i + 1] - off[i];
         int32_t s = src_counts ? src_counts[i] : 1;
@@ -39,6 +41,7 @@ __global__ void k_edges_level0(const int32_t *off, int32_t e, const int32_t *src
 
 // pedge[j] = hyperedge of pin position j (one warp per hyperedge)
 __global__ void k_pin_edges(const int32_t *off, int32_t e, int32_t *pedge) {
+    HP_KERNEL_ENTER();
     int lane = threadIdx.x & 31;
     int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -47,6 +50,7 @@ __global__ void k_pin_edges(const int32_t *off, int32_t e, int32_t *pedge) {
 }
 
 __global__ void k_check_pins(const int32_t *pin, int64_t np, int32_t n, uint32_t *err) {
+    HP_KERNEL_ENTER();
     GRID_STRIDE(j, np) {
         int32_t v = pin[j];
         if (v < 0 || v >= n) atomicOr(err, E_PIN);
@@ -56,6 +60,7 @@ __global__ void k_check_pins(const int32_t *pin, int64_t np, int32_t n, uint32_t
 // duplicates: an edge twice in in(v) or out(v), or in both (src & dst overlap)
 __global__ void k_check_dups(const int32_t *ioff, const int32_t *inc, const int32_t *nin, int32_t n, int32_t delta,
                              uint32_t *err) {
+    HP_KERNEL_ENTER();
     GRID_STRIDE(v, (int64_t)n) {
         int32_t a = ioff[v], m = a + nin[v], b = ioff[v + 1];
         bool dup = false;
@@ -80,6 +85,7 @@ __global__ void k_check_dups(const int32_t *ioff, const int32_t *inc, const int3
 // before the atomics (hub nodes appear in many hyperedges of a warp)
 __global__ void k_inc_keys(const int32_t *pin, const int32_t *pedge, const int32_t *off, const int32_t *nsrc,
                            int64_t np, uint32_t *keys, uint32_t *vals, int32_t *cnt, int32_t *nin) {
+    HP_KERNEL_ENTER();
     const int lane = threadIdx.x & 31;
     const int64_t wbase = ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5) << 5;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -105,6 +111,7 @@ __global__ void k_inc_keys(const int32_t *pin, const int32_t *pedge, const int32
 }
 
 __global__ void k_inc_nodes(const uint32_t *keys, int64_t np, int32_t *inode) {
+    HP_KERNEL_ENTER();
     GRID_STRIDE(j, np) inode[j] = (int32_t)(keys[j] >> 1);
 }
 
@@ -118,7 +125,7 @@ void build_incidence(Level &L, Arena &A) {
     HPC(cudaMemsetAsync(L.nin, 0, sizeof(int32_t) * L.n, s));
     uint32_t *keys = A.get<uint32_t>(L.np);
     if (L.np > 0) {
-        k_inc_keys<<<grid_of(L.np, 256), 256, 0, s>>>(L.pin, L.pedge, L.off, L.nsrc, L.np, keys,
+        launch_k(k_inc_keys, grid_of(L.np, 256), 256, 0, s, L.pin, L.pedge, L.off, L.nsrc, L.np, keys,
                                                        reinterpret_cast<uint32_t *>(L.inc), cnt, L.nin);
         HP_LAUNCH_CHECK();
         radix_sort(keys, reinterpret_cast<uint32_t *>(L.inc), L.np, bits_for(2ull * (uint64_t)L.n - 1), A);
@@ -126,7 +133,7 @@ void build_incidence(Level &L, Arena &A) {
     scan_excl(cnt, L.ioff, L.n + 1, nullptr, A);
     L.inode = A.get<int32_t>(L.np);
     if (L.np > 0) {
-        k_inc_nodes<<<grid_of(L.np, 256), 256, 0, s>>>(keys, L.np, L.inode);
+        launch_k(k_inc_nodes, grid_of(L.np, 256), 256, 0, s, keys, L.np, L.inode);
         HP_LAUNCH_CHECK();
     }
     A.release(keys);
@@ -145,7 +152,7 @@ uint32_t validate_and_build_level0(const int32_t *pins, const int32_t *offsets, 
     Box *box = A.get<Box>(1);
     HPC(cudaMemsetAsync(box, 0, sizeof(Box), s));
     if (e > 0) {
-        k_check_offsets<<<grid_of(e, 256), 256, 0, s>>>(offsets, e, &box->err);
+        launch_k(k_check_offsets, grid_of(e, 256), 256, 0, s, offsets, e, &box->err);
         HP_LAUNCH_CHECK();
         HPC(cudaMemcpyAsync(&box->np, offsets + e, sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
     } else {
@@ -166,14 +173,14 @@ uint32_t validate_and_build_level0(const int32_t *pins, const int32_t *offsets, 
     L.nsrc = A.get<int32_t>(e);
     L.pedge = A.get<int32_t>(L.np);
     if (e > 0) {
-        k_edges_level0<<<grid_of(e, 256), 256, 0, s>>>(L.off, e, src_counts, weights, P.o.count_kind, L.nsrc, w,
+        launch_k(k_edges_level0, grid_of(e, 256), 256, 0, s, L.off, e, src_counts, weights, P.o.count_kind, L.nsrc, w,
                                                         &box->wsum, &box->err);
         HP_LAUNCH_CHECK();
-        k_pin_edges<<<grid_of((int64_t)e * 32, 256), 256, 0, s>>>(L.off, e, L.pedge);
+        launch_k(k_pin_edges, grid_of((int64_t)e * 32, 256), 256, 0, s, L.off, e, L.pedge);
         HP_LAUNCH_CHECK();
     }
     if (L.np) {
-        k_check_pins<<<grid_of(L.np, 256), 256, 0, s>>>(L.pin, L.np, n, &box->err);
+        launch_k(k_check_pins, grid_of(L.np, 256), 256, 0, s, L.pin, L.np, n, &box->err);
         HP_LAUNCH_CHECK();
     }
     fetch_bytes(&hb, box, sizeof(Box), s);
@@ -181,7 +188,7 @@ uint32_t validate_and_build_level0(const int32_t *pins, const int32_t *offsets, 
     if (hb.err & (E_PIN | E_SRC)) return hb.err;
     build_incidence(L, A);
     if (n > 0) {
-        k_check_dups<<<grid_of(n, 256), 256, 0, s>>>(L.ioff, L.inc, L.nin, n, P.delta, &box->err);
+        launch_k(k_check_dups, grid_of(n, 256), 256, 0, s, L.ioff, L.inc, L.nin, n, P.delta, &box->err);
         HP_LAUNCH_CHECK();
     }
     L.size = A.get<int32_t>(n);
@@ -211,7 +218,7 @@ void make_level(int32_t n, int32_t e, const int32_t *off, const int32_t *pins, c
     if (n) HPC(cudaMemcpyAsync(L.size, size, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s));
     L.pedge = A.get<int32_t>(L.np);
     if (e > 0) {
-        k_pin_edges<<<grid_of((int64_t)e * 32, 256), 256, 0, s>>>(L.off, e, L.pedge);
+        launch_k(k_pin_edges, grid_of((int64_t)e * 32, 256), 256, 0, s, L.off, e, L.pedge);
         HP_LAUNCH_CHECK();
     }
     build_incidence(L, A);
@@ -221,6 +228,7 @@ void make_level(int32_t n, int32_t e, const int32_t *off, const int32_t *pins, c
 
 // ---------------------------------------------------------------- contraction
 __global__ void k_rep_flags(const int32_t *mate, int32_t n, int32_t *isrep) {
+    HP_KERNEL_ENTER();
     GRID_STRIDE(v, (int64_t)n) {
         int32_t m = mate[v];
         isrep[v] = (m < 0 || v < m) ? 1 : 0;
@@ -229,6 +237,7 @@ __global__ void k_rep_flags(const int32_t *mate, int32_t n, int32_t *isrep) {
 
 __global__ void k_gamma(const int32_t *mate, const int32_t *cid, const int32_t *size, const int32_t *nbcnt, int32_t n,
                         int32_t *gamma, int32_t *csize, int32_t *cnb) {
+    HP_KERNEL_ENTER();
     GRID_STRIDE(v, (int64_t)n) {
         int32_t m = mate[v];
         int32_t r = (m >= 0 && m < v) ? m : (int32_t)v;
@@ -258,6 +267,7 @@ __device__ __forceinline__ int32_t lower_bound_seg(const int32_t *a, int32_t lo,
 __global__ void k_keep(const int32_t *pin, const int32_t *pedge, const int32_t *off, const int32_t *nsrc,
                        const int32_t *mate, const int32_t *ioff, const int32_t *inc, const int32_t *nin, int64_t np,
                        int32_t *keep) {
+    HP_KERNEL_ENTER();
     GRID_STRIDE(j, np) {
         int32_t e = pedge[j], p = pin[j];
         bool p_src = (int32_t)j - off[e] < nsrc[e];
@@ -281,6 +291,7 @@ __global__ void k_keep(const int32_t *pin, const int32_t *pedge, const int32_t *
 
 __global__ void k_coarse_edges(const int32_t *off, const int32_t *nsrc, const int32_t *newpos, int32_t e,
                                int32_t *coff, int32_t *cnsrc) {
+    HP_KERNEL_ENTER();
     GRID_STRIDE(i, (int64_t)e) {
         int32_t a = newpos[off[i]];
         coff[i] = a;
@@ -290,6 +301,7 @@ __global__ void k_coarse_edges(const int32_t *off, const int32_t *nsrc, const in
 
 __global__ void k_coarse_pins(const int32_t *pin, const int32_t *pedge, const int32_t *keep, const int32_t *newpos,
                               const int32_t *gamma, int64_t np, int32_t *cpin, int32_t *cpedge) {
+    HP_KERNEL_ENTER();
     GRID_STRIDE(j, np) {
         if (keep[j]) {
             int32_t k = newpos[j];
@@ -303,13 +315,13 @@ bool contract_level(const Level &L, const int32_t *mate, LevelBox *box, LevelBox
     cudaStream_t s = A.stream();
     int32_t *isrep = A.get<int32_t>(L.n);
     int32_t *cid = A.get<int32_t>(L.n + 1);
-    k_rep_flags<<<grid_of(L.n, 256), 256, 0, s>>>(mate, L.n, isrep);
+    launch_k(k_rep_flags, grid_of(L.n, 256), 256, 0, s, mate, L.n, isrep);
     HP_LAUNCH_CHECK();
     scan_excl(isrep, cid, L.n, &box->cn, A);
     int32_t *keep = A.get<int32_t>(L.np);
     int32_t *newpos = A.get<int32_t>(L.np + 1);
     if (L.np) {
-        k_keep<<<grid_of(L.np, 256), 256, 0, s>>>(L.pin, L.pedge, L.off, L.nsrc, mate, L.ioff, L.inc, L.nin, L.np,
+        launch_k(k_keep, grid_of(L.np, 256), 256, 0, s, L.pin, L.pedge, L.off, L.nsrc, mate, L.ioff, L.inc, L.nin, L.np,
                                                    keep);
         HP_LAUNCH_CHECK();
     }
@@ -326,7 +338,7 @@ bool contract_level(const Level &L, const int32_t *mate, LevelBox *box, LevelBox
     C.size = A.get<int32_t>(C.n);
     C.nbnd = A.get<int32_t>(C.n);
     const_cast<Level &>(L).gamma = A.get<int32_t>(L.n);
-    k_gamma<<<grid_of(L.n, 256), 256, 0, s>>>(mate, cid, L.size, L.nbnd, L.n, L.gamma, C.size, C.nbnd);
+    launch_k(k_gamma, grid_of(L.n, 256), 256, 0, s, mate, cid, L.size, L.nbnd, L.n, L.gamma, C.size, C.nbnd);
     HP_LAUNCH_CHECK();
     A.release(isrep);
     A.release(cid);
@@ -335,12 +347,12 @@ bool contract_level(const Level &L, const int32_t *mate, LevelBox *box, LevelBox
     C.pin = A.get<int32_t>(C.np);
     C.pedge = A.get<int32_t>(C.np);
     if (C.e > 0) {
-        k_coarse_edges<<<grid_of(C.e, 256), 256, 0, s>>>(L.off, L.nsrc, newpos, C.e, C.off, C.nsrc);
+        launch_k(k_coarse_edges, grid_of(C.e, 256), 256, 0, s, L.off, L.nsrc, newpos, C.e, C.off, C.nsrc);
         HP_LAUNCH_CHECK();
     }
     HPC(cudaMemcpyAsync(C.off + C.e, newpos + L.np, sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
     if (L.np) {
-        k_coarse_pins<<<grid_of(L.np, 256), 256, 0, s>>>(L.pin, L.pedge, keep, newpos, L.gamma, L.np, C.pin, C.pedge);
+        launch_k(k_coarse_pins, grid_of(L.np, 256), 256, 0, s, L.pin, L.pedge, keep, newpos, L.gamma, L.np, C.pin, C.pedge);
         HP_LAUNCH_CHECK();
     }
     A.release(keep);

@@ -7,6 +7,7 @@
 #include <cstdint>
 #include <stdexcept>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "hp.h"
@@ -25,6 +26,41 @@ void cuda_check(cudaError_t e, const char *what, const char *file, int line);
 extern thread_local int64_t t_launches;
 #define HP_LAUNCH_CHECK() \
     (::hp::t_launches++, ::hp::cuda_check(cudaGetLastError(), "kernel launch", __FILE__, __LINE__))
+
+// ---------------------------------------------------------------- launches
+// Every kernel of the path is launched with programmatic stream
+// serialisation: a kernel may be scheduled while the one before it on the
+// stream is still running, so that its launch and block set-up overlap the
+// predecessor's tail (the path is a chain of tens of thousands of short
+// dependent kernels).  Each kernel therefore starts with HP_KERNEL_ENTER():
+// its threads wait there until the preceding kernel has finished and its
+// writes are visible (before any read or write of memory), then allow the
+// next kernel to be scheduled.  Work issued to a stream other than as a
+// kernel (copies, memsets, event waits) keeps the full ordering.
+#define HP_KERNEL_ENTER()                                          \
+    do {                                                           \
+        asm volatile("griddepcontrol.wait;" ::: "memory");         \
+        asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); \
+    } while (0)
+
+// launches were made with the attribute unless HP_PDL=0 was set in the
+// environment when the library first launched a kernel
+bool pdl_enabled();
+
+template <class... E, class... A>
+inline void launch_k(void (*kernel)(E...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, A &&...args) {
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cfg.attrs = at;
+    cfg.numAttrs = pdl_enabled() ? 1 : 0;
+    cuda_check(cudaLaunchKernelEx(&cfg, kernel, std::forward<A>(args)...), "kernel launch", __FILE__, __LINE__);
+}
 
 // bits of the device error word
 enum : uint32_t {

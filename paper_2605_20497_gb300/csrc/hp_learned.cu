@@ -130,6 +130,7 @@ __device__ void merge_feats_pair(const LearnIn &X, int64_t q) {
 
 // one thread per listed pair (the whole level, or the nodes of a pass)
 __global__ void k_merge_feats(LearnIn X) {
+    HP_KERNEL_ENTER();
     GRID_STRIDE(q, (int64_t)(X.v1 - X.v0) * X.K) merge_feats_pair(X, q);
 }
 
@@ -140,6 +141,7 @@ __global__ void k_merge_feats(LearnIn X) {
 // staging area takes the one-thread-per-pair form.
 constexpr int MF_T = 256, MF_CAP = 512;
 __global__ void __launch_bounds__(MF_T) k_merge_feats_node(LearnIn X) {
+    HP_KERNEL_ENTER();
     __shared__ int32_t s_inc[MF_T / 32][MF_CAP];
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -224,6 +226,7 @@ constexpr int W2_STRIDE = 36;   // words per row of the packed W2 (32 + 4: confl
 // registers, the A operand of layer 2 for k-chunk c.
 __global__ void __launch_bounds__(MLP_WARPS * 32) k_merge_mlp(const uint8_t *feat, int64_t count,
                                                                const hp_merge_model *M, int32_t *out) {
+    HP_KERNEL_ENTER();
     __shared__ uint32_t s_w1[64 * 8];           // [hidden j][feature pair]
     __shared__ uint32_t s_w2[64 * W2_STRIDE];   // [hidden k][hidden pair]
     __shared__ int32_t s_b1[64], s_b2[64], s_w3[64];
@@ -309,6 +312,7 @@ __device__ __forceinline__ bool learned_gt(int32_t s1, uint64_t e1, int32_t m1, 
 
 // one thread per node of the pass: C(n) = the top Pi mutual candidates by (s, eta, id)
 __global__ void k_merge_select(LearnIn X) {
+    HP_KERNEL_ENTER();
     GRID_STRIDE(v0, (int64_t)(X.v1 - X.v0)) {
         const int64_t v = X.v0 + v0;
         int32_t c[16], sc[16];
@@ -390,6 +394,7 @@ struct GradSmem {
 //   C/D:    (row g, col 2t), (row g, col 2t+1), (row g+8, col 2t), (row g+8, col 2t+1)
 __global__ void __launch_bounds__(GRAD_T) k_merge_grad(const uint8_t *feat, const float *label, int64_t count,
                                                         const float *params, float *partial, double *loss_part) {
+    HP_KERNEL_ENTER();
     extern __shared__ __align__(16) unsigned char grad_smem[];
     GradSmem &S = *reinterpret_cast<GradSmem *>(grad_smem);
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5, g = lane >> 2, t = lane & 3;
@@ -647,6 +652,7 @@ __global__ void __launch_bounds__(GRAD_T) k_merge_grad(const uint8_t *feat, cons
 // the CTAs' partial gradients summed in CTA order (deterministic)
 __global__ void k_merge_grad_sum(const float *partial, const double *loss_part, int64_t count, float *grad,
                                  double *loss) {
+    HP_KERNEL_ENTER();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < NPAR) {
         float a = 0.f;
@@ -663,6 +669,7 @@ __global__ void k_merge_grad_sum(const float *partial, const double *loss_part, 
 // AdamW: m, v moments; c1 = 1 - beta1^t, c2 = 1 - beta2^t
 __global__ void k_merge_adam(float *p, const float *g, float *m, float *v, float lr, float b1, float b2, float eps,
                              float wd, float c1, float c2) {
+    HP_KERNEL_ENTER();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= NPAR) return;
     const float gi = g[i];
@@ -680,9 +687,9 @@ double merge_grad(const uint8_t *feat, const float *label, int64_t count, const 
     float *partial = A.get<float>((int64_t)GRAD_CTAS * NPAR);
     double *lp = A.get<double>(GRAD_CTAS + 1);
     prepare_kernel((const void *)k_merge_grad, GRAD_T, sizeof(GradSmem));
-    k_merge_grad<<<GRAD_CTAS, GRAD_T, sizeof(GradSmem), s>>>(feat, label, count, params, partial, lp);
+    launch_k(k_merge_grad, GRAD_CTAS, GRAD_T, sizeof(GradSmem), s, feat, label, count, params, partial, lp);
     HP_LAUNCH_CHECK();
-    k_merge_grad_sum<<<(NPAR + 255) / 256, 256, 0, s>>>(partial, lp, count, grad, lp + GRAD_CTAS);
+    launch_k(k_merge_grad_sum, (NPAR + 255) / 256, 256, 0, s, partial, lp, count, grad, lp + GRAD_CTAS);
     HP_LAUNCH_CHECK();
     const double loss = fetch<double>(lp + GRAD_CTAS, s);
     A.release(partial);
@@ -694,7 +701,7 @@ void merge_adam(float *p, const float *g, float *m, float *v, int64_t step, floa
                 float wd, cudaStream_t s) {
     const float c1 = (float)(1.0 - std::pow((double)b1, (double)step));
     const float c2 = (float)(1.0 - std::pow((double)b2, (double)step));
-    k_merge_adam<<<(NPAR + 255) / 256, 256, 0, s>>>(p, g, m, v, lr, b1, b2, eps, wd, c1, c2);
+    launch_k(k_merge_adam, (NPAR + 255) / 256, 256, 0, s, p, g, m, v, lr, b1, b2, eps, wd, c1, c2);
     HP_LAUNCH_CHECK();
 }
 
@@ -762,7 +769,7 @@ void merge_features(const LearnIn &X, cudaStream_t s) {
     LearnIn Y = X;
     Y.v0 = 0;
     Y.v1 = X.n;
-    k_merge_feats<<<grid_for((int64_t)X.n * X.K, 256), 256, 0, s>>>(Y);
+    launch_k(k_merge_feats, grid_for((int64_t)X.n * X.K, 256), 256, 0, s, Y);
     HP_LAUNCH_CHECK();
 }
 
@@ -770,7 +777,7 @@ void merge_scores(const uint8_t *feat, int64_t count, const hp_merge_model *dmod
     if (count <= 0) return;
     const int64_t tiles = cdiv(count, 16);
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(cdiv(tiles, MLP_WARPS), (int64_t)num_sms() * 8));
-    k_merge_mlp<<<grid, MLP_WARPS * 32, 0, s>>>(feat, count, dmodel, out);
+    launch_k(k_merge_mlp, grid, MLP_WARPS * 32, 0, s, feat, count, dmodel, out);
     HP_LAUNCH_CHECK();
 }
 
@@ -785,10 +792,10 @@ void learned_candidates(LearnIn X, int32_t batch, cudaStream_t s) {
         X.v0 = v0;
         X.v1 = std::min<int64_t>((int64_t)v0 + B, X.n);
         const int64_t pairs = (int64_t)(X.v1 - X.v0) * X.K;
-        k_merge_feats_node<<<grid_for((int64_t)(X.v1 - X.v0) * 32, MF_T), MF_T, 0, s>>>(X);
+        launch_k(k_merge_feats_node, grid_for((int64_t)(X.v1 - X.v0) * 32, MF_T), MF_T, 0, s, X);
         HP_LAUNCH_CHECK();
         merge_scores(X.feat, pairs, X.model, X.score, s);
-        k_merge_select<<<grid_for(X.v1 - X.v0, 128), 128, 0, s>>>(X);
+        launch_k(k_merge_select, grid_for(X.v1 - X.v0, 128), 128, 0, s, X);
         HP_LAUNCH_CHECK();
     }
 }

@@ -3,6 +3,8 @@
 // build incidence sets).
 #include <cuda_runtime.h>
 
+#include <cstdlib>
+
 #include <cstring>
 #include <mutex>
 
@@ -156,6 +158,14 @@ int prepare_kernel(const void *func, int block, size_t smem) {
     return occ;
 }
 
+bool pdl_enabled() {
+    static const bool on = [] {
+        const char *e = std::getenv("HP_PDL");
+        return !(e && e[0] == '0');
+    }();
+    return on;
+}
+
 int num_sms() {
     static int sms[64] = {0};
     int dev = 0;
@@ -169,10 +179,12 @@ int num_sms() {
 
 // ================================================================ fill / iota
 __global__ void k_fill(int32_t *p, int64_t n, int32_t v) {
+    HP_KERNEL_ENTER();
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         p[i] = v;
 }
 __global__ void k_iota(int32_t *p, int64_t n) {
+    HP_KERNEL_ENTER();
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         p[i] = (int32_t)i;
 }
@@ -184,12 +196,12 @@ static int grid_for(int64_t n, int block) {
 }
 void fill_i32(int32_t *p, int64_t n, int32_t v, cudaStream_t s) {
     if (n <= 0) return;
-    k_fill<<<grid_for(n, 256), 256, 0, s>>>(p, n, v);
+    launch_k(k_fill, grid_for(n, 256), 256, 0, s, p, n, v);
     HP_LAUNCH_CHECK();
 }
 void iota_i32(int32_t *p, int64_t n, cudaStream_t s) {
     if (n <= 0) return;
-    k_iota<<<grid_for(n, 256), 256, 0, s>>>(p, n);
+    launch_k(k_iota, grid_for(n, 256), 256, 0, s, p, n);
     HP_LAUNCH_CHECK();
 }
 
@@ -225,6 +237,7 @@ template <class T> __device__ T block_excl_scan(T v, T *s_warp, T *total) {
 }
 
 template <class T> __global__ void __launch_bounds__(SCAN_T) k_scan_reduce(const T *in, T *bsum, int64_t n) {
+    HP_KERNEL_ENTER();
     __shared__ T s_warp[33];
     int64_t base = (int64_t)blockIdx.x * SCAN_TILE;
     T acc = 0;
@@ -239,6 +252,7 @@ template <class T> __global__ void __launch_bounds__(SCAN_T) k_scan_reduce(const
 
 template <class T>
 __global__ void __launch_bounds__(SCAN_T) k_scan_tiles(const T *in, T *out, const T *boff, int64_t n, T *total) {
+    HP_KERNEL_ENTER();
     __shared__ T s_val[SCAN_TILE];
     __shared__ T s_warp[33];
     int64_t base = (int64_t)blockIdx.x * SCAN_TILE;
@@ -273,6 +287,7 @@ __global__ void __launch_bounds__(SCAN_T) k_scan_tiles(const T *in, T *out, cons
 // (one launch instead of three)
 constexpr int64_t SCAN_SINGLE = 4;
 template <class T> __global__ void __launch_bounds__(SCAN_T) k_scan_single(const T *in, T *out, int64_t n, T *total) {
+    HP_KERNEL_ENTER();
     __shared__ T s_val[SCAN_TILE];
     __shared__ T s_warp[33];
     T carry = 0;
@@ -313,16 +328,16 @@ template <class T> static void scan_impl(const T *in, T *out, int64_t n, T *tota
     }
     int64_t tiles = cdiv(n, SCAN_TILE);
     if (tiles <= SCAN_SINGLE) {
-        k_scan_single<T><<<1, SCAN_T, 0, s>>>(in, out, n, total_dev);
+        launch_k(k_scan_single<T>, 1, SCAN_T, 0, s, in, out, n, total_dev);
         HP_LAUNCH_CHECK();
         return;
     }
     T *bsum = A.get<T>(tiles);
     T *boff = A.get<T>(tiles);
-    k_scan_reduce<T><<<(unsigned)tiles, SCAN_T, 0, s>>>(in, bsum, n);
+    launch_k(k_scan_reduce<T>, (unsigned)tiles, SCAN_T, 0, s, in, bsum, n);
     HP_LAUNCH_CHECK();
     scan_impl<T>(bsum, boff, tiles, nullptr, A);
-    k_scan_tiles<T><<<(unsigned)tiles, SCAN_T, 0, s>>>(in, out, boff, n, total_dev);
+    launch_k(k_scan_tiles<T>, (unsigned)tiles, SCAN_T, 0, s, in, out, boff, n, total_dev);
     HP_LAUNCH_CHECK();
     A.release(bsum);
     A.release(boff);
@@ -343,6 +358,7 @@ constexpr int RS_T = 256, RS_R = 16, RS_TILE = RS_T * RS_R;
 
 template <class K>
 __global__ void __launch_bounds__(RS_T) k_radix_hist(const K *keys, int64_t n, int shift, uint32_t *hist, int tiles) {
+    HP_KERNEL_ENTER();
     __shared__ uint32_t cnt[256];
     cnt[threadIdx.x] = 0;
     __syncthreads();
@@ -358,6 +374,7 @@ __global__ void __launch_bounds__(RS_T) k_radix_hist(const K *keys, int64_t n, i
 template <class K>
 __global__ void __launch_bounds__(RS_T) k_radix_scatter(const K *kin, const uint32_t *vin, K *kout, uint32_t *vout,
                                                         int64_t n, int shift, const uint32_t *offs, int tiles) {
+    HP_KERNEL_ENTER();
     __shared__ uint32_t s_off[256];
     __shared__ uint32_t s_wc[8][256];
     const int t = threadIdx.x, lane = t & 31, w = t >> 5;
@@ -407,11 +424,11 @@ template <class K> static void radix_impl(K *keys, uint32_t *vals, int64_t n, in
     uint32_t *va = vals, *vb = v2;
     for (int p = 0; p < passes; p++) {
         int shift = 8 * p;
-        k_radix_hist<K><<<tiles, RS_T, 0, s>>>(ka, n, shift, hist, tiles);
+        launch_k(k_radix_hist<K>, tiles, RS_T, 0, s, ka, n, shift, hist, tiles);
         HP_LAUNCH_CHECK();
         scan_excl(reinterpret_cast<int32_t *>(hist), reinterpret_cast<int32_t *>(hist), (int64_t)256 * tiles,
                   nullptr, A);
-        k_radix_scatter<K><<<tiles, RS_T, 0, s>>>(ka, va, kb, vb, n, shift, hist, tiles);
+        launch_k(k_radix_scatter<K>, tiles, RS_T, 0, s, ka, va, kb, vb, n, shift, hist, tiles);
         HP_LAUNCH_CHECK();
         std::swap(ka, kb);
         std::swap(va, vb);
@@ -430,6 +447,7 @@ template <class K> static void radix_impl(K *keys, uint32_t *vals, int64_t n, in
 template <class K>
 __global__ void __launch_bounds__(RS_T) k_radix_hist_dev(const K *keys, const int32_t *n_dev, int shift, uint32_t *hist,
                                                          int tiles) {
+    HP_KERNEL_ENTER();
     __shared__ uint32_t cnt[256];
     cnt[threadIdx.x] = 0;
     __syncthreads();
@@ -447,6 +465,7 @@ template <class K>
 __global__ void __launch_bounds__(RS_T) k_radix_scatter_dev(const K *kin, const uint32_t *vin, K *kout,
                                                             uint32_t *vout, const int32_t *n_dev, int shift,
                                                             const uint32_t *offs, int tiles) {
+    HP_KERNEL_ENTER();
     __shared__ uint32_t s_off[256];
     __shared__ uint32_t s_wc[8][256];
     const int t = threadIdx.x, lane = t & 31, w = t >> 5;
@@ -491,6 +510,7 @@ __global__ void __launch_bounds__(RS_T) k_radix_scatter_dev(const K *kin, const 
 constexpr int SS_T = 1024, SMALL_SORT = 4096;
 template <class K>
 __global__ void __launch_bounds__(SS_T) k_small_sort(K *keys, uint32_t *vals, const int32_t *n_dev, int passes) {
+    HP_KERNEL_ENTER();
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ uint32_t s_wc[32][256];
     __shared__ uint32_t s_hist[256 + 33];
@@ -505,7 +525,7 @@ static void radix_dev_impl(K *keys, uint32_t *vals, const int32_t *n_dev, int64_
     if (cap <= SMALL_SORT) {
         size_t sm = (size_t)SMALL_SORT * 2 * (sizeof(K) + sizeof(uint32_t));
         prepare_kernel((const void *)k_small_sort<K>, SS_T, sm);
-        k_small_sort<K><<<1, SS_T, sm, s>>>(keys, vals, n_dev, passes);
+        launch_k(k_small_sort<K>, 1, SS_T, sm, s, keys, vals, n_dev, passes);
         HP_LAUNCH_CHECK();
         return;
     }
@@ -516,11 +536,11 @@ static void radix_dev_impl(K *keys, uint32_t *vals, const int32_t *n_dev, int64_
     K *ka = keys, *kb = k2;
     uint32_t *va = vals, *vb = v2;
     for (int p = 0; p < passes; p++) {
-        k_radix_hist_dev<K><<<tiles, RS_T, 0, s>>>(ka, n_dev, 8 * p, hist, tiles);
+        launch_k(k_radix_hist_dev<K>, tiles, RS_T, 0, s, ka, n_dev, 8 * p, hist, tiles);
         HP_LAUNCH_CHECK();
         scan_excl(reinterpret_cast<int32_t *>(hist), reinterpret_cast<int32_t *>(hist), (int64_t)256 * tiles,
                   nullptr, A);
-        k_radix_scatter_dev<K><<<tiles, RS_T, 0, s>>>(ka, va, kb, vb, n_dev, 8 * p, hist, tiles);
+        launch_k(k_radix_scatter_dev<K>, tiles, RS_T, 0, s, ka, va, kb, vb, n_dev, 8 * p, hist, tiles);
         HP_LAUNCH_CHECK();
         std::swap(ka, kb);
         std::swap(va, vb);

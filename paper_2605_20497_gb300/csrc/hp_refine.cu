@@ -124,7 +124,8 @@ __global__ void __launch_bounds__(PLW_T) k_plist_small(const int32_t *off, const
                                                        const int32_t *w, const int32_t *rho, int32_t e,
                                                        const int32_t *list, int32_t small_max, uint32_t cap, Plist PL,
                                                        int32_t *D, long long *saving, int32_t skip_below,
-                                                       int32_t skip_above = INT32_MAX) {
+                                                       int32_t skip_above) {
+    HP_KERNEL_ENTER();
     extern __shared__ __align__(16) int32_t sm[];
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
     // table of cap slots; entry buffers of cap / 2 >= lambda(e) entries
@@ -155,6 +156,7 @@ __global__ void __launch_bounds__(256) k_plist_big(const int32_t *off, const int
                                                    const int32_t *w, const int32_t *rho, const int32_t *list,
                                                    int32_t count, uint32_t cap, int32_t *gtab, int32_t max_e, Plist PL,
                                                    int32_t *D, long long *saving) {
+    HP_KERNEL_ENTER();
     __shared__ int32_t gcnt;
     int32_t *mine = gtab + (int64_t)blockIdx.x * (3 * (int64_t)cap + 4 * (int64_t)max_e);
     int32_t *keys = mine, *tc = mine + cap, *tci = mine + 2 * cap;
@@ -172,6 +174,7 @@ __global__ void __launch_bounds__(256) k_plist_big(const int32_t *off, const int
 
 __global__ void k_big_edges(const int32_t *off, int32_t e, int32_t small_max, int32_t *list, int32_t *cnt,
                             int32_t *maxe) {
+    HP_KERNEL_ENTER();
     GRID_STRIDE(i, (int64_t)e) {
         int32_t sz = off[i + 1] - off[i];
         if (sz > small_max) {
@@ -182,6 +185,7 @@ __global__ void k_big_edges(const int32_t *off, int32_t e, int32_t small_max, in
 }
 
 __global__ void k_max_edge(const int32_t *off, int32_t e, int32_t *maxe) {
+    HP_KERNEL_ENTER();
     int32_t m = 0;
     GRID_STRIDE(i, (int64_t)e) m = max(m, off[i + 1] - off[i]);
     for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_down_sync(0xffffffffu, m, o));
@@ -204,14 +208,14 @@ static void build_plist(const Level &L, const int32_t *w, const int32_t *rho, in
     size_t sm = (size_t)per * 4 * (PLW_T / 32);
     int occ = prepare_kernel((const void *)k_plist_small, PLW_T, sm);
     int grid = (int)std::min<int64_t>(cdiv(L.e, PLW_T / 32), (int64_t)num_sms() * std::max(occ, 1));
-    k_plist_small<<<std::max(grid, 1), PLW_T, sm, s>>>(L.off, L.pin, L.nsrc, w, rho, L.e, nullptr, small_max, cap,
-                                                       PL, D, saving, 0);
+    launch_k(k_plist_small, std::max(grid, 1), PLW_T, sm, s, L.off, L.pin, L.nsrc, w, rho, L.e, nullptr, small_max, cap,
+             PL, D, saving, 0, INT32_MAX);
     HP_LAUNCH_CHECK();
     if (max_e > small_max) {
         int32_t *list = A.get<int32_t>(L.e);
         int32_t *cnt = A.get<int32_t>(2);
         HPC(cudaMemsetAsync(cnt, 0, 2 * sizeof(int32_t), s));
-        k_big_edges<<<grid_of(L.e, 256), 256, 0, s>>>(L.off, L.e, small_max, list, cnt, cnt + 1);
+        launch_k(k_big_edges, grid_of(L.e, 256), 256, 0, s, L.off, L.e, small_max, list, cnt, cnt + 1);
         HP_LAUNCH_CHECK();
         int32_t hc[2];
         fetch_bytes(hc, cnt, sizeof hc, s);
@@ -219,7 +223,7 @@ static void build_plist(const Level &L, const int32_t *w, const int32_t *rho, in
             uint32_t bcap = pow2_at_least(2 * (int64_t)hc[1]);
             int nb = std::min<int>(hc[0], num_sms() * 2);
             int32_t *gtab = A.get<int32_t>((int64_t)nb * (3 * (int64_t)bcap + 4 * (int64_t)hc[1]));
-            k_plist_big<<<nb, 256, 0, s>>>(L.off, L.pin, L.nsrc, w, rho, list, hc[0], bcap, gtab, hc[1], PL, D,
+            launch_k(k_plist_big, nb, 256, 0, s, L.off, L.pin, L.nsrc, w, rho, list, hc[0], bcap, gtab, hc[1], PL, D,
                                             saving);
             HP_LAUNCH_CHECK();
             A.release(gtab);
@@ -232,6 +236,7 @@ static void build_plist(const Level &L, const int32_t *w, const int32_t *rho, in
 // ---------------------------------------------------------------- objective
 __global__ void k_objective(const int32_t *lam, const int32_t *w, int32_t e, unsigned long long *conn,
                             unsigned long long *cutnet) {
+    HP_KERNEL_ENTER();
     unsigned long long c = 0, cn = 0;
     GRID_STRIDE(i, (int64_t)e) {
         int32_t l = lam[i];
@@ -257,7 +262,7 @@ void objective(const Level &L, const int32_t *w, const int32_t *rho, int32_t npa
     if (L.e == 0) return;
     int32_t *maxe = A.get<int32_t>(1);
     HPC(cudaMemsetAsync(maxe, 0, sizeof(int32_t), s));
-    k_max_edge<<<grid_of(L.e, 256), 256, 0, s>>>(L.off, L.e, maxe);
+    launch_k(k_max_edge, grid_of(L.e, 256), 256, 0, s, L.off, L.e, maxe);
     HP_LAUNCH_CHECK();
     int32_t me = fetch<int32_t>(maxe, s);
     Plist PL;
@@ -266,7 +271,7 @@ void objective(const Level &L, const int32_t *w, const int32_t *rho, int32_t npa
     PL.cin = A.get<int32_t>(L.np);
     PL.lam = A.get<int32_t>(L.e);
     build_plist(L, w, rho, me, PL, nullptr, nullptr, A);
-    k_objective<<<grid_of(L.e, 256), 256, 0, s>>>(PL.lam, w, L.e, (unsigned long long *)conn_dev,
+    launch_k(k_objective, grid_of(L.e, 256), 256, 0, s, PL.lam, w, L.e, (unsigned long long *)conn_dev,
                                                   (unsigned long long *)cutnet_dev);
     HP_LAUNCH_CHECK();
     A.release(PL.p);
@@ -423,6 +428,7 @@ struct GainArgs {
 template <int BT>
 __global__ void __launch_bounds__(BT) k_gains_smem(GainArgs G, const int32_t *list, const int32_t *count_p,
                                                      uint32_t cap, int32_t *ovf, int32_t *ovf_n) {
+    HP_KERNEL_ENTER();
     const int32_t count = *count_p;
     extern __shared__ __align__(16) unsigned char smem[];
     long long *conn = reinterpret_cast<long long *>(smem);
@@ -449,6 +455,7 @@ __global__ void __launch_bounds__(BT) k_gains_smem(GainArgs G, const int32_t *li
 __global__ void __launch_bounds__(GN_T) k_gains_global(GainArgs G, const int32_t *list, const int32_t *count_p,
                                                        uint32_t cap, int32_t *gkeys, long long *gconn, int32_t *bad,
                                                        int32_t *bad_n) {
+    HP_KERNEL_ENTER();
     const int32_t count = *count_p;
     if (count == 0) return;
     __shared__ int32_t s_cnt;
@@ -479,6 +486,7 @@ __global__ void __launch_bounds__(GN_T) k_gains_global(GainArgs G, const int32_t
 constexpr int GW_T = 256, GW_SLOTS = 256;
 __global__ void __launch_bounds__(GW_T) k_gains_warp(GainArgs G, const int32_t *list, const int32_t *count_p,
                                                      uint32_t limit, int32_t *spill, int32_t *spill_n) {
+    HP_KERNEL_ENTER();
     __shared__ int32_t s_keys[GW_T / 32][GW_SLOTS];
     __shared__ long long s_conn[GW_T / 32][GW_SLOTS];
     __shared__ int32_t s_used[GW_T / 32];
@@ -588,6 +596,7 @@ __global__ void __launch_bounds__(GW_T) k_gains_warp(GainArgs G, const int32_t *
 // singleton at p_s (-) and at p_d (+): they are handled per node.
 __global__ void k_level_nodes(const int32_t *off, const int32_t *ioff, const int32_t *inc, const int32_t *inode,
                               const int32_t *nin, const int32_t *w, int64_t np, long long *wns, int32_t *singin) {
+    HP_KERNEL_ENTER();
     const int lane = threadIdx.x & 31;
     const int64_t wbase = ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5) << 5;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -620,6 +629,7 @@ constexpr int TINY_E = 8;
 __host__ __device__ inline int32_t level_small_max(int32_t max_e) { return max_e < 2 ? 2 : (max_e > 512 ? 512 : max_e); }
 __global__ void k_level_edges(const int32_t *off, int32_t e, const int32_t *max_e, int32_t *act, int32_t *big,
                               int32_t *tiny, int32_t *mid, int32_t *cnt) {
+    HP_KERNEL_ENTER();
     const int32_t small_max = level_small_max(*max_e);
     GRID_STRIDE(i, (int64_t)e) {
         int32_t sz = off[i + 1] - off[i];
@@ -638,6 +648,7 @@ __global__ void k_level_edges(const int32_t *off, int32_t e, const int32_t *max_
 __global__ void k_plist_tiny(const int32_t *off, const int32_t *pin, const int32_t *nsrc, const int32_t *w,
                              const int32_t *rho, const int32_t *list, int32_t count, Plist PL, int32_t *D,
                              long long *saving) {
+    HP_KERNEL_ENTER();
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < count; base += (int64_t)gridDim.x * blockDim.x) {
@@ -760,6 +771,7 @@ __device__ __forceinline__ int64_t rep_zero_span(const RepArrays &R) {
 // keep: the partition is the one of the previous repetition (it applied
 // nothing), so D(p), |p| and saving(v) are still valid
 __global__ void k_rep_zero(RepArrays R, int keep) {
+    HP_KERNEL_ENTER();
     GRID_STRIDE(i, rep_zero_span(R)) {
         if (i < R.nparts && !keep) {
             R.D0[i] = 0;
@@ -786,6 +798,7 @@ __global__ void k_rep_zero(RepArrays R, int keep) {
 
 __global__ void k_rep_nodes(const int32_t *rho, const int32_t *size, const int32_t *singin, int32_t n,
                             long long *psize, int32_t *D0) {
+    HP_KERNEL_ENTER();
     GRID_STRIDE(v, (int64_t)n) {
         int32_t p = rho[v];
         atomicAdd((unsigned long long *)&psize[p], (unsigned long long)size[v]);
@@ -802,6 +815,7 @@ __global__ void k_rep_nodes(const int32_t *rho, const int32_t *size, const int32
 // for them (sum of lambda(e) over cut entries), into acc[0..2].
 __global__ void k_cut_flags(const int32_t *off, const int32_t *pin, const int32_t *inc, const int32_t *inode,
                             const int32_t *lam, int64_t np, int32_t *flag, unsigned long long *acc) {
+    HP_KERNEL_ENTER();
     unsigned long long lsum = 0, cuts = 0, clam = 0;
     GRID_STRIDE(t, np) {
         const int32_t e = inc[t];
@@ -831,6 +845,7 @@ __global__ void k_cut_flags(const int32_t *off, const int32_t *pin, const int32_
 }
 __global__ void k_cut_fill(const int32_t *inc, const int32_t *flag, const int32_t *cpos, const int32_t *ioff,
                            int64_t np, int32_t n, int32_t *cut, int32_t *cut_off) {
+    HP_KERNEL_ENTER();
     GRID_STRIDE(t, np) {
         if (flag[t]) cut[cpos[t]] = inc[t];
     }
@@ -842,6 +857,7 @@ __global__ void k_cut_fill(const int32_t *inc, const int32_t *flag, const int32_
 constexpr int32_t HUB_DEG = 1024, GW_DEG = 256;
 __global__ void k_candidates(const long long *saving, const int32_t *cut_off, int32_t n, int32_t *list, int32_t *cnt,
                              int32_t *hubs, int32_t *hcnt, int32_t *wlist, int32_t *wcnt) {
+    HP_KERNEL_ENTER();
     GRID_STRIDE(v, (int64_t)n) {
         if (saving[v] > 0) {
             const int32_t d = cut_off[v + 1] - cut_off[v];
@@ -1264,57 +1280,70 @@ __device__ void best_prefix_block(const unsigned long long *gseq, const int32_t 
 // ---------------------------------------------------------------- multi-kernel path
 __global__ void k_move_keys(const Moves M, const int32_t *cntp, long long gbound, int gb, int nb, int field,
                             uint64_t *keys, uint32_t *idx, int init_idx) {
+    HP_KERNEL_ENTER();
     ph_move_keys(M, *cntp, gbound, gb, nb, field, keys, idx, init_idx, G_T0, G_NT);
 }
 __global__ void k_gather_moves(const Moves M, const uint32_t *idx, const int32_t *cntp, Moves S, int32_t *pc,
                                const int32_t *size, const int32_t *nin, int32_t *msz, int32_t *mni) {
+    HP_KERNEL_ENTER();
     ph_gather(M, idx, *cntp, S, pc, size, nin, msz, mni, G_T0, G_NT);
 }
 __global__ void k_choose(ChainCtx C, const int32_t *mcount, int r, int packed) {
+    HP_KERNEL_ENTER();
     if (r > 0 && !C.linked[r - 1]) return;
     ph_choose(C, r, packed, *mcount, G_T0, G_NT);
 }
 __global__ void k_accept_min(ChainCtx C, const int32_t *mcount, int r) {
+    HP_KERNEL_ENTER();
     if (r > 0 && !C.linked[r - 1]) return;
     ph_accept_min(C, *mcount, G_T0, G_NT);
 }
 __global__ void k_accept_id(ChainCtx C, const int32_t *mcount, int r) {
+    HP_KERNEL_ENTER();
     if (r > 0 && !C.linked[r - 1]) return;
     ph_accept_id(C, *mcount, G_T0, G_NT);
 }
 __global__ void k_link(ChainCtx C, const int32_t *mcount, int r, int packed) {
+    HP_KERNEL_ENTER();
     if (r > 0 && !C.linked[r - 1]) return;
     ph_link(C, r, packed, *mcount, G_T0, G_NT);
 }
-__global__ void k_path_heads(SeqCtx S, const int32_t *mcount) { ph_path_heads(S, *mcount, G_T0, G_NT); }
-__global__ void k_cycle_heads(SeqCtx S, const int32_t *mcount) { ph_cycle_heads(S, *mcount, G_T0, G_NT); }
+__global__ void k_path_heads(SeqCtx S, const int32_t *mcount) { HP_KERNEL_ENTER(); ph_path_heads(S, *mcount, G_T0, G_NT); }
+__global__ void k_cycle_heads(SeqCtx S, const int32_t *mcount) { HP_KERNEL_ENTER(); ph_cycle_heads(S, *mcount, G_T0, G_NT); }
 __global__ void k_head_collect(SeqCtx S, const int32_t *mcount, uint32_t *heads, int32_t *nh) {
+    HP_KERNEL_ENTER();
     ph_head_collect(S, *mcount, heads, nh, G_T0, G_NT);
 }
 __global__ void k_head_keys(const uint32_t *heads, const int32_t *nh, const long long *cgain, const int32_t *node,
                             long long cgbound, int nb, int field, uint64_t *keys) {
+    HP_KERNEL_ENTER();
     ph_head_keys(heads, *nh, cgain, node, cgbound, nb, field, keys, G_T0, G_NT);
 }
 __global__ void k_chain_lens(const uint32_t *heads, const int32_t *nh, const int32_t *clen, int32_t cap,
                              int32_t *lens) {
+    HP_KERNEL_ENTER();
     ph_chain_lens(heads, *nh, clen, cap, lens, G_T0, G_NT);
 }
 __global__ void k_chain_start(const uint32_t *heads, const int32_t *nh, const int32_t *starts, int32_t *cstart) {
+    HP_KERNEL_ENTER();
     ph_chain_start(heads, *nh, starts, cstart, G_T0, G_NT);
 }
 __global__ void k_seq_pos(const int32_t *chain, const int32_t *pos, const int32_t *cstart, const int32_t *mcount,
                           const int32_t *node, int32_t *seqmove, int32_t *mvpos) {
+    HP_KERNEL_ENTER();
     ph_seq_pos(chain, pos, cstart, *mcount, node, seqmove, mvpos, G_T0, G_NT);
 }
 __global__ void k_val_entries(ValCtx V, const int32_t *mcount, int32_t *nv) {
+    HP_KERNEL_ENTER();
     const int32_t m = *mcount;
     if (blockIdx.x == 0 && threadIdx.x == 0) *nv = 2 * m;
     ph_val_entries(V, m, G_T0, G_NT);
 }
-__global__ void k_val_gather(ValCtx V, const int32_t *nv) { ph_val_gather(V, *nv, G_T0, G_NT); }
-__global__ void k_val_trans(ValCtx V, const int32_t *nv) { ph_val_trans(V, *nv, G_T0, G_NT); }
+__global__ void k_val_gather(ValCtx V, const int32_t *nv) { HP_KERNEL_ENTER(); ph_val_gather(V, *nv, G_T0, G_NT); }
+__global__ void k_val_trans(ValCtx V, const int32_t *nv) { HP_KERNEL_ENTER(); ph_val_trans(V, *nv, G_T0, G_NT); }
 __global__ void k_initial_bad(const long long *psize, const int32_t *D0, int32_t nparts, int32_t omega, int32_t delta,
                               int32_t *bad) {
+    HP_KERNEL_ENTER();
     int32_t c = ph_initial_bad(psize, D0, nparts, omega, delta, G_T0, G_NT);
     for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
     if ((threadIdx.x & 31) == 0 && c) atomicAdd(bad, c);
@@ -1322,10 +1351,12 @@ __global__ void k_initial_bad(const long long *psize, const int32_t *D0, int32_t
 __global__ void __launch_bounds__(1024) k_best_prefix(const unsigned long long *gseq, const int32_t *violc,
                                                       const int32_t *mcount, const int32_t *bad0, int32_t *best_len,
                                                       long long *best_gain) {
+    HP_KERNEL_ENTER();
     best_prefix_block(gseq, violc, *mcount, *bad0, best_len, best_gain);
 }
 __global__ void k_apply(const int32_t *seqmove, const int32_t *node, const int32_t *dst, const int32_t *lenp,
                         int32_t *rho) {
+    HP_KERNEL_ENTER();
     ph_apply(seqmove, node, dst, *lenp, rho, G_T0, G_NT);
 }
 
@@ -1366,6 +1397,7 @@ __device__ void ph_first_of(const int32_t *src, int32_t m, int32_t nparts, int32
 }
 
 __global__ void __cluster_dims__(SQ_CS, 1, 1) __launch_bounds__(SEQ_T) k_seq_cluster(ClusterSeqArgs A) {
+    HP_KERNEL_ENTER();
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ uint32_t s_wc[32 * 256];
     __shared__ uint32_t s_tot[256];
@@ -1465,6 +1497,7 @@ __global__ void __cluster_dims__(SQ_CS, 1, 1) __launch_bounds__(SEQ_T) k_seq_clu
 // validity of every prefix, best prefix, apply
 __global__ void __launch_bounds__(SEQ_T) k_val_small(ValCtx V, int32_t *cnt, int32_t nparts, int sb, long long *bgain,
                                                      int32_t *rho) {
+    HP_KERNEL_ENTER();
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ uint32_t s_wc[32 * 256];
     __shared__ uint32_t s_hist[256 + 33];
@@ -1494,6 +1527,7 @@ __global__ void __launch_bounds__(SEQ_T) k_val_small(ValCtx V, int32_t *cnt, int
 // apply, separated by cluster barriers.
 __global__ void __cluster_dims__(SQ_CS, 1, 1) __launch_bounds__(SQ_T)
     k_val_cluster(ValCtx V, int32_t *cnt, int32_t nparts, int sb, long long *bgain, int32_t *rho) {
+    HP_KERNEL_ENTER();
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ uint32_t s_wc[32 * 256];
     __shared__ uint32_t s_tot[256];
@@ -1730,6 +1764,7 @@ __device__ void inseq_edge(const SeqSim &Q, int32_t e, int gt, int32_t *bk, int3
 __global__ void k_touched(const int32_t *off, const int32_t *pin, const int32_t *mvpos, const int32_t *list,
                           int32_t count, int32_t *out, int32_t *out_n, int32_t *tout, int32_t *tout_n,
                           const int32_t *mcount) {
+    HP_KERNEL_ENTER();
     if (*mcount == 0) return;
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
@@ -1771,6 +1806,7 @@ constexpr int IS_T = 128;
 // hyperedges of lo < |e| <= emax pins from the list, a warp each
 __global__ void __launch_bounds__(IS_T) k_inseq_small(SeqSim Q, const int32_t *list, const int32_t *count_p,
                                                       int32_t emax, const int32_t *mcount, int32_t lo) {
+    HP_KERNEL_ENTER();
     if (*mcount == 0) return;
     const int32_t count = *count_p;
     extern __shared__ __align__(16) int32_t sm[];
@@ -1787,6 +1823,7 @@ __global__ void __launch_bounds__(IS_T) k_inseq_small(SeqSim Q, const int32_t *l
 }
 __global__ void __launch_bounds__(256) k_inseq_big(SeqSim Q, const int32_t *list, int32_t count, int32_t emax,
                                                    int32_t *gbuf, const int32_t *mcount) {
+    HP_KERNEL_ENTER();
     if (*mcount == 0) return;
     __shared__ int32_t gc;
     int32_t *base = gbuf + (int64_t)blockIdx.x * 9 * (int64_t)emax;
@@ -1806,6 +1843,7 @@ __global__ void __launch_bounds__(256) k_inseq_big(SeqSim Q, const int32_t *list
 constexpr int IST_T = 128;
 __global__ void __launch_bounds__(IST_T) k_inseq_tiny(SeqSim Q, const int32_t *list, const int32_t *count_p,
                                                        const int32_t *mcount) {
+    HP_KERNEL_ENTER();
     __shared__ int32_t s_tab[IST_T * 6 * TINY_E];
     if (*mcount == 0) return;
     const unsigned FULL = 0xffffffffu;
@@ -2095,6 +2133,7 @@ void refine_workspace_free(LevelWs *W, Arena &A) {
 // parts holding at least one node (lambda(e) never exceeds it within a level:
 // moves only go to parts that exist)
 __global__ void k_used_parts(const int32_t *rho, int32_t n, int32_t *mark, int32_t *count) {
+    HP_KERNEL_ENTER();
     GRID_STRIDE(v, (int64_t)n) {
         if (atomicExch(&mark[rho[v]], 1) == 0) atomicAdd(count, 1);
     }
@@ -2108,23 +2147,23 @@ static void level_prepare(const Level &L, const int32_t *w, const int32_t *rho, 
     W.R.e = e;
     HPC(cudaMemsetAsync(W.lvl, 0, 6 * sizeof(int32_t), s));
     if (e > 0) {
-        k_max_edge<<<grid_of(e, 256), 256, 0, s>>>(L.off, e, W.lvl + 2);
+        launch_k(k_max_edge, grid_of(e, 256), 256, 0, s, L.off, e, W.lvl + 2);
         HP_LAUNCH_CHECK();
     }
     HPC(cudaMemsetAsync(W.pmark, 0, sizeof(int32_t) * std::max(W.nparts, 1), s));
     if (n > 0) {
-        k_used_parts<<<grid_of(n, 256), 256, 0, s>>>(rho, n, W.pmark, W.lvl + 5);
+        launch_k(k_used_parts, grid_of(n, 256), 256, 0, s, rho, n, W.pmark, W.lvl + 5);
         HP_LAUNCH_CHECK();
     }
     if (e > 0) {
         // the size classes take the largest hyperedge from the device (no read-back here)
-        k_level_edges<<<grid_of(e, 256), 256, 0, s>>>(L.off, e, W.lvl + 2, W.act, W.big, W.tiny, W.mid, W.lvl);
+        launch_k(k_level_edges, grid_of(e, 256), 256, 0, s, L.off, e, W.lvl + 2, W.act, W.big, W.tiny, W.mid, W.lvl);
         HP_LAUNCH_CHECK();
     }
     HPC(cudaMemsetAsync(W.wns, 0, sizeof(long long) * n, s));
     HPC(cudaMemsetAsync(W.singin, 0, sizeof(int32_t) * n, s));
     if (L.np > 0) {
-        k_level_nodes<<<grid_of(L.np, 256), 256, 0, s>>>(L.off, L.ioff, L.inc, L.inode, L.nin, w, L.np, W.wns,
+        launch_k(k_level_nodes, grid_of(L.np, 256), 256, 0, s, L.off, L.ioff, L.inc, L.inode, L.nin, w, L.np, W.wns,
                                                           W.singin);
         HP_LAUNCH_CHECK();
     }
@@ -2154,10 +2193,10 @@ static int32_t rep_run(const Level &L, const int32_t *w, const Params &P, int32_
     int32_t *cnt = R.cnt;
     const int64_t zspan = std::max<int64_t>(std::max<int64_t>(n, (int64_t)nparts + 1),
                                             std::max<int64_t>((int64_t)C_N, (int64_t)P.o.chain_rounds + 1));
-    k_rep_zero<<<grid_of(zspan, 256), 256, 0, s>>>(R, reuse ? 1 : 0);
+    launch_k(k_rep_zero, grid_of(zspan, 256), 256, 0, s, R, reuse ? 1 : 0);
     HP_LAUNCH_CHECK();
     if (!reuse) {
-        k_rep_nodes<<<grid_of(n, 256), 256, 0, s>>>(rho, L.size, W.singin, n, R.psize, R.D0);
+        launch_k(k_rep_nodes, grid_of(n, 256), 256, 0, s, rho, L.size, W.singin, n, R.psize, R.D0);
         HP_LAUNCH_CHECK();
         // pins(p,e), pins_in(p,e), D(p), saving(v)
         if (W.n_mid > 0) {
@@ -2168,7 +2207,7 @@ static int32_t rep_run(const Level &L, const int32_t *w, const Params &P, int32_
                 size_t sm = (size_t)per * 4 * (PLW_T / 32);
                 int occ = prepare_kernel((const void *)k_plist_small, PLW_T, sm);
                 int grid = (int)std::min<int64_t>(cdiv(W.n_mid, PLW_T / 32), (int64_t)num_sms() * occ);
-                k_plist_small<<<std::max(grid, 1), PLW_T, sm, s>>>(L.off, L.pin, L.nsrc, w, rho, W.n_mid, W.mid,
+                launch_k(k_plist_small, std::max(grid, 1), PLW_T, sm, s, L.off, L.pin, L.nsrc, w, rho, W.n_mid, W.mid,
                                                                    W.small_max, cap, W.PL, R.D0, R.saving, lo, hi);
                 HP_LAUNCH_CHECK();
             };
@@ -2180,27 +2219,27 @@ static int32_t rep_run(const Level &L, const int32_t *w, const Params &P, int32_
             }
         }
         if (W.n_tiny > 0) {
-            k_plist_tiny<<<grid_of(W.n_tiny, 128), 128, 0, s>>>(L.off, L.pin, L.nsrc, w, rho, W.tiny, W.n_tiny, W.PL, R.D0,
+            launch_k(k_plist_tiny, grid_of(W.n_tiny, 128), 128, 0, s, L.off, L.pin, L.nsrc, w, rho, W.tiny, W.n_tiny, W.PL, R.D0,
                                                                 R.saving);
             HP_LAUNCH_CHECK();
         }
         if (W.n_big > 0) {
-            k_plist_big<<<W.pnb, 256, 0, s>>>(L.off, L.pin, L.nsrc, w, rho, W.big, W.n_big, W.bcap, W.ptab, W.cmax_e,
+            launch_k(k_plist_big, W.pnb, 256, 0, s, L.off, L.pin, L.nsrc, w, rho, W.big, W.n_big, W.bcap, W.ptab, W.cmax_e,
                                                W.PL, R.D0, R.saving);
             HP_LAUNCH_CHECK();
         }
         // moves in isolation (Eq. 13)
         if (L.np > 0) {
-            k_cut_flags<<<grid_of(L.np, 256), 256, 0, s>>>(L.off, L.pin, L.inc, L.inode, W.PL.lam, L.np, W.cflag,
+            launch_k(k_cut_flags, grid_of(L.np, 256), 256, 0, s, L.off, L.pin, L.inc, L.inode, W.PL.lam, L.np, W.cflag,
                                                             reinterpret_cast<unsigned long long *>(cnt + C_ACC));
             HP_LAUNCH_CHECK();
         }
         scan_excl(W.cflag, W.cpos, L.np, W.cpos + L.np, A);
-        k_cut_fill<<<grid_of(std::max<int64_t>(L.np, (int64_t)n + 1), 256), 256, 0, s>>>(L.inc, W.cflag, W.cpos, L.ioff,
+        launch_k(k_cut_fill, grid_of(std::max<int64_t>(L.np, (int64_t)n + 1), 256), 256, 0, s, L.inc, W.cflag, W.cpos, L.ioff,
                                                                                            L.np, n, W.cut, W.cut_off);
         HP_LAUNCH_CHECK();
     }
-    k_candidates<<<grid_of(n, 256), 256, 0, s>>>(R.saving, W.cut_off, n, W.cl, cnt + C_CAND, W.hubs, cnt + C_HUB,
+    launch_k(k_candidates, grid_of(n, 256), 256, 0, s, R.saving, W.cut_off, n, W.cl, cnt + C_CAND, W.hubs, cnt + C_HUB,
                                                  W.cw, cnt + C_CW);
     HP_LAUNCH_CHECK();
     GainArgs G{L.off, W.cut_off, W.cut, w, rho, L.size, R.psize, R.saving, W.wns, W.PL, P.omega, second_half, W.M};
@@ -2213,7 +2252,7 @@ static int32_t rep_run(const Level &L, const int32_t *w, const Params &P, int32_
         HPC(cudaEventRecord(W.ev[0], s));
         HPC(cudaStreamWaitEvent(W.side, W.ev[0], 0));
         const int occ_h = prepare_kernel((const void *)k_gains_smem<1024>, 1024, gsm);
-        k_gains_smem<1024><<<num_sms() * std::max(occ_h, 1), 1024, gsm, W.side>>>(G, W.hubs, cnt + C_HUB, gcap_smem,
+        launch_k(k_gains_smem<1024>, num_sms() * std::max(occ_h, 1), 1024, gsm, W.side, G, W.hubs, cnt + C_HUB, gcap_smem,
                                                                                  W.ovf, cnt + C_OVF);
         HP_LAUNCH_CHECK();
         HPC(cudaEventRecord(W.ev[1], W.side));
@@ -2223,16 +2262,16 @@ static int32_t rep_run(const Level &L, const int32_t *w, const Params &P, int32_
                                                         : GW_SLOTS * 3 / 4;
         int occ = prepare_kernel((const void *)k_gains_warp, GW_T, 0);
         int grid = (int)std::max<int64_t>(1, std::min<int64_t>(cdiv(n, GW_T / 32), (int64_t)num_sms() * occ));
-        k_gains_warp<<<grid, GW_T, 0, s>>>(G, W.cw, cnt + C_CW, wlimit, W.cl, cnt + C_CAND);
+        launch_k(k_gains_warp, grid, GW_T, 0, s, G, W.cw, cnt + C_CW, wlimit, W.cl, cnt + C_CAND);
         HP_LAUNCH_CHECK();
     }
     {
         int occ = prepare_kernel((const void *)k_gains_smem<GN_T>, GN_T, gsm);
         int grid = std::max(1, std::min<int>(n, num_sms() * occ));
-        k_gains_smem<GN_T><<<grid, GN_T, gsm, s>>>(G, W.cl, cnt + C_CAND, gcap_smem, W.ovf, cnt + C_OVF);
+        launch_k(k_gains_smem<GN_T>, grid, GN_T, gsm, s, G, W.cl, cnt + C_CAND, gcap_smem, W.ovf, cnt + C_OVF);
         HP_LAUNCH_CHECK();
         HPC(cudaStreamWaitEvent(s, W.ev[1], 0));
-        k_gains_global<<<W.gnb, GN_T, 0, s>>>(G, W.ovf, cnt + C_OVF, W.gcap, W.gk, W.gc, W.cl, cnt + C_BAD);
+        launch_k(k_gains_global, W.gnb, GN_T, 0, s, G, W.ovf, cnt + C_OVF, W.gcap, W.gk, W.gc, W.cl, cnt + C_BAD);
         HP_LAUNCH_CHECK();
     }
     // The rest of the repetition; `end` reads its counters back (the one
@@ -2315,66 +2354,66 @@ static int32_t rep_run(const Level &L, const int32_t *w, const Params &P, int32_
                           cgbound};
         const size_t sm = SQ_SMEM;
         prepare_kernel((const void *)k_seq_cluster, SEQ_T, sm);
-        k_seq_cluster<<<SQ_CS, SEQ_T, sm, s>>>(SA);
+        launch_k(k_seq_cluster, SQ_CS, SEQ_T, sm, s, SA);
         HP_LAUNCH_CHECK();
     } else {
         // sort (p_s asc, gain desc, node asc)
         if (sb + gb + nb <= 64) {
-            k_move_keys<<<grid_of(m, 256), 256, 0, s>>>(W.M, cnt + C_MOVES, gbound, gb, nb, -1, W.keys, W.idx, 1);
+            launch_k(k_move_keys, grid_of(m, 256), 256, 0, s, W.M, cnt + C_MOVES, gbound, gb, nb, -1, W.keys, W.idx, 1);
             HP_LAUNCH_CHECK();
             radix_sort_dev(W.keys, W.idx, cnt + C_MOVES, m, sb + gb + nb, A);
         } else {
             const int fb[3] = {nb, gb, sb};
             for (int f = 0; f < 3; f++) {
-                k_move_keys<<<grid_of(m, 256), 256, 0, s>>>(W.M, cnt + C_MOVES, gbound, gb, nb, f, W.keys, W.idx,
+                launch_k(k_move_keys, grid_of(m, 256), 256, 0, s, W.M, cnt + C_MOVES, gbound, gb, nb, f, W.keys, W.idx,
                                                             f == 0);
                 HP_LAUNCH_CHECK();
                 radix_sort_dev(W.keys, W.idx, cnt + C_MOVES, m, fb[f], A);
             }
         }
-        k_gather_moves<<<grid_of(m, 256), 256, 0, s>>>(W.M, W.idx, cnt + C_MOVES, W.S, R.pc, L.size, L.nin, W.msz,
+        launch_k(k_gather_moves, grid_of(m, 256), 256, 0, s, W.M, W.idx, cnt + C_MOVES, W.S, R.pc, L.size, L.nin, W.msz,
                                                        W.mni);
         HP_LAUNCH_CHECK();
         scan_excl(R.pc, W.first, nparts + 1, nullptr, A);
         // chaining (Sec. VI-C)
         for (int32_t r = 0; r < P.o.chain_rounds; r++) {
-            k_choose<<<grid_of(m, 128), 128, 0, s>>>(C, cnt + C_MOVES, r, packed);
+            launch_k(k_choose, grid_of(m, 128), 128, 0, s, C, cnt + C_MOVES, r, packed);
             HP_LAUNCH_CHECK();
             if (!packed) {
-                k_accept_min<<<grid_of(m, 256), 256, 0, s>>>(C, cnt + C_MOVES, r);
+                launch_k(k_accept_min, grid_of(m, 256), 256, 0, s, C, cnt + C_MOVES, r);
                 HP_LAUNCH_CHECK();
-                k_accept_id<<<grid_of(m, 256), 256, 0, s>>>(C, cnt + C_MOVES, r);
+                launch_k(k_accept_id, grid_of(m, 256), 256, 0, s, C, cnt + C_MOVES, r);
                 HP_LAUNCH_CHECK();
             }
-            k_link<<<grid_of(m, 256), 256, 0, s>>>(C, cnt + C_MOVES, r, packed);
+            launch_k(k_link, grid_of(m, 256), 256, 0, s, C, cnt + C_MOVES, r, packed);
             HP_LAUNCH_CHECK();
         }
         // chains in order of (total gain desc, head node asc)
-        k_path_heads<<<grid_of(m, 256), 256, 0, s>>>(Q, cnt + C_MOVES);
+        launch_k(k_path_heads, grid_of(m, 256), 256, 0, s, Q, cnt + C_MOVES);
         HP_LAUNCH_CHECK();
-        k_cycle_heads<<<grid_of(m, 256), 256, 0, s>>>(Q, cnt + C_MOVES);
+        launch_k(k_cycle_heads, grid_of(m, 256), 256, 0, s, Q, cnt + C_MOVES);
         HP_LAUNCH_CHECK();
-        k_head_collect<<<grid_of(m, 256), 256, 0, s>>>(Q, cnt + C_MOVES, W.heads, cnt + C_NH);
+        launch_k(k_head_collect, grid_of(m, 256), 256, 0, s, Q, cnt + C_MOVES, W.heads, cnt + C_NH);
         HP_LAUNCH_CHECK();
         if (cgb + nb <= 64) {
-            k_head_keys<<<grid_of(m, 256), 256, 0, s>>>(W.heads, cnt + C_NH, R.cgain, W.S.node, cgbound, nb, -1,
+            launch_k(k_head_keys, grid_of(m, 256), 256, 0, s, W.heads, cnt + C_NH, R.cgain, W.S.node, cgbound, nb, -1,
                                                          W.hkeys);
             HP_LAUNCH_CHECK();
             radix_sort_dev(W.hkeys, W.heads, cnt + C_NH, m, cgb + nb, A);
         } else {
             for (int f = 0; f < 2; f++) {
-                k_head_keys<<<grid_of(m, 256), 256, 0, s>>>(W.heads, cnt + C_NH, R.cgain, W.S.node, cgbound, nb, f,
+                launch_k(k_head_keys, grid_of(m, 256), 256, 0, s, W.heads, cnt + C_NH, R.cgain, W.S.node, cgbound, nb, f,
                                                              W.hkeys);
                 HP_LAUNCH_CHECK();
                 radix_sort_dev(W.hkeys, W.heads, cnt + C_NH, m, f == 0 ? nb : cgb, A);
             }
         }
-        k_chain_lens<<<grid_of(m, 256), 256, 0, s>>>(W.heads, cnt + C_NH, W.clen, m, W.lens);
+        launch_k(k_chain_lens, grid_of(m, 256), 256, 0, s, W.heads, cnt + C_NH, W.clen, m, W.lens);
         HP_LAUNCH_CHECK();
         scan_excl(W.lens, W.starts, m, nullptr, A);
-        k_chain_start<<<grid_of(m, 256), 256, 0, s>>>(W.heads, cnt + C_NH, W.starts, W.cstart);
+        launch_k(k_chain_start, grid_of(m, 256), 256, 0, s, W.heads, cnt + C_NH, W.starts, W.cstart);
         HP_LAUNCH_CHECK();
-        k_seq_pos<<<grid_of(m, 256), 256, 0, s>>>(R.chain, W.pos, W.cstart, cnt + C_MOVES, W.S.node, W.seqmove,
+        launch_k(k_seq_pos, grid_of(m, 256), 256, 0, s, R.chain, W.pos, W.cstart, cnt + C_MOVES, W.S.node, W.seqmove,
                                                   R.mvpos);
         HP_LAUNCH_CHECK();
     }
@@ -2389,16 +2428,16 @@ static int32_t rep_run(const Level &L, const int32_t *w, const Params &P, int32_
     // in-sequence gains and distinct-inbound changes per move
     SeqSim Z{L.off, L.pin, L.nsrc, w, R.mvpos, W.seqmove, W.S.src, W.S.dst, W.PL, R.gseq, R.dDs, R.dDd};
     if (W.n_act > 0) {
-        k_touched<<<grid_of(W.n_act, 256), 256, 0, s>>>(L.off, L.pin, R.mvpos, W.act, W.n_act, W.touched,
+        launch_k(k_touched, grid_of(W.n_act, 256), 256, 0, s, L.off, L.pin, R.mvpos, W.act, W.n_act, W.touched,
                                                          cnt + C_TOUCH, W.ttouched, cnt + C_TTOUCH, cnt + C_MOVES);
         HP_LAUNCH_CHECK();
-        k_inseq_tiny<<<grid_of(W.n_act, IST_T), IST_T, 0, s>>>(Z, W.ttouched, cnt + C_TTOUCH, cnt + C_MOVES);
+        launch_k(k_inseq_tiny, grid_of(W.n_act, IST_T), IST_T, 0, s, Z, W.ttouched, cnt + C_TTOUCH, cnt + C_MOVES);
         HP_LAUNCH_CHECK();
         auto inseq_mid = [&](int32_t lo, int32_t emax) {
             size_t sm = (size_t)(9 * emax + 1) * 4 * (IS_T / 32);
             int occ = prepare_kernel((const void *)k_inseq_small, IS_T, sm);
             int grid = (int)std::min<int64_t>(cdiv(W.n_act, IS_T / 32), (int64_t)num_sms() * occ);
-            k_inseq_small<<<std::max(grid, 1), IS_T, sm, s>>>(Z, W.touched, cnt + C_TOUCH, emax, cnt + C_MOVES, lo);
+            launch_k(k_inseq_small, std::max(grid, 1), IS_T, sm, s, Z, W.touched, cnt + C_TOUCH, emax, cnt + C_MOVES, lo);
             HP_LAUNCH_CHECK();
         };
         if (W.small_max > MID_SPLIT) {
@@ -2409,35 +2448,35 @@ static int32_t rep_run(const Level &L, const int32_t *w, const Params &P, int32_
         }
     }
     if (W.n_big > 0) {
-        k_inseq_big<<<W.pnb, 256, 0, s>>>(Z, W.big, W.n_big, W.cmax_e, W.ibuf, cnt + C_MOVES);
+        launch_k(k_inseq_big, W.pnb, 256, 0, s, Z, W.big, W.n_big, W.cmax_e, W.ibuf, cnt + C_MOVES);
         HP_LAUNCH_CHECK();
     }
 
     // validity of every prefix (Sec. VI-D), best valid prefix, apply
     if (small_level) {
         prepare_kernel((const void *)k_val_cluster, SQ_T, SQ_SMEM);
-        k_val_cluster<<<SQ_CS, SQ_T, SQ_SMEM, s>>>(V, cnt, nparts, sb, W.bgain, rho);
+        launch_k(k_val_cluster, SQ_CS, SQ_T, SQ_SMEM, s, V, cnt, nparts, sb, W.bgain, rho);
         HP_LAUNCH_CHECK();
     } else if (small) {
         size_t sm = (size_t)2 * SMALLM * 2 * (4 + 4);
         prepare_kernel((const void *)k_val_small, SEQ_T, sm);
-        k_val_small<<<1, SEQ_T, sm, s>>>(V, cnt, nparts, sb, W.bgain, rho);
+        launch_k(k_val_small, 1, SEQ_T, sm, s, V, cnt, nparts, sb, W.bgain, rho);
         HP_LAUNCH_CHECK();
     } else {
-        k_val_entries<<<grid_of(m, 256), 256, 0, s>>>(V, cnt + C_MOVES, cnt + C_NV);
+        launch_k(k_val_entries, grid_of(m, 256), 256, 0, s, V, cnt + C_MOVES, cnt + C_NV);
         HP_LAUNCH_CHECK();
         radix_sort_dev(W.vkey, W.vidx, cnt + C_NV, 2 * (int64_t)m, sb, A);
-        k_val_gather<<<grid_of(2 * (int64_t)m, 256), 256, 0, s>>>(V, cnt + C_NV);
+        launch_k(k_val_gather, grid_of(2 * (int64_t)m, 256), 256, 0, s, V, cnt + C_NV);
         HP_LAUNCH_CHECK();
         scan_excl((const int64_t *)W.gsz, (int64_t *)W.esz, 2 * (int64_t)m, nullptr, A);
         scan_excl((const int64_t *)W.gdd, (int64_t *)W.edd, 2 * (int64_t)m, nullptr, A);
-        k_val_trans<<<grid_of(2 * (int64_t)m, 256), 256, 0, s>>>(V, cnt + C_NV);
+        launch_k(k_val_trans, grid_of(2 * (int64_t)m, 256), 256, 0, s, V, cnt + C_NV);
         HP_LAUNCH_CHECK();
-        k_initial_bad<<<grid_of(nparts, 256), 256, 0, s>>>(R.psize, R.D0, nparts, P.omega, P.delta, cnt + C_BAD0);
+        launch_k(k_initial_bad, grid_of(nparts, 256), 256, 0, s, R.psize, R.D0, nparts, P.omega, P.delta, cnt + C_BAD0);
         HP_LAUNCH_CHECK();
-        k_best_prefix<<<1, 1024, 0, s>>>(R.gseq, R.viol, cnt + C_MOVES, cnt + C_BAD0, cnt + C_APPLIED, W.bgain);
+        launch_k(k_best_prefix, 1, 1024, 0, s, R.gseq, R.viol, cnt + C_MOVES, cnt + C_BAD0, cnt + C_APPLIED, W.bgain);
         HP_LAUNCH_CHECK();
-        k_apply<<<grid_of(m, 256), 256, 0, s>>>(W.seqmove, W.S.node, W.S.dst, cnt + C_APPLIED, rho);
+        launch_k(k_apply, grid_of(m, 256), 256, 0, s, W.seqmove, W.S.node, W.S.dst, cnt + C_APPLIED, rho);
         HP_LAUNCH_CHECK();
     }
     if (dbg) {
@@ -2448,6 +2487,7 @@ static int32_t rep_run(const Level &L, const int32_t *w, const Params &P, int32_
 }
 
 __global__ void k_max_edge_i(const int32_t *off, int32_t e, int32_t *maxe) {
+    HP_KERNEL_ENTER();
     int32_t m = 0;
     GRID_STRIDE(i, (int64_t)e) m = max(m, off[i + 1] - off[i]);
     for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_down_sync(0xffffffffu, m, o));
@@ -2459,7 +2499,7 @@ int32_t max_edge_size(const Level &L, Arena &A) {
     int32_t *mx = A.get<int32_t>(1);
     HPC(cudaMemsetAsync(mx, 0, sizeof(int32_t), s));
     if (L.e > 0) {
-        k_max_edge_i<<<grid_of(L.e, 256), 256, 0, s>>>(L.off, L.e, mx);
+        launch_k(k_max_edge_i, grid_of(L.e, 256), 256, 0, s, L.off, L.e, mx);
         HP_LAUNCH_CHECK();
     }
     const int32_t r = fetch<int32_t>(mx, s);
@@ -2503,10 +2543,12 @@ RefineOut refine_level(const Level &L, const int32_t *w, const Params &P, int32_
 
 // ---------------------------------------------------------------- final statistics
 __global__ void k_part_sizes(const int32_t *part, int32_t n, long long *psize) {
+    HP_KERNEL_ENTER();
     GRID_STRIDE(v, (int64_t)n) atomicAdd((unsigned long long *)&psize[part[v]], 1ull);
 }
 __global__ void k_part_max(const long long *psize, const int32_t *D, int32_t nparts, int32_t omega, int32_t delta,
                            long long *out) {
+    HP_KERNEL_ENTER();
     long long ms = 0, md = 0, bad = 0;
     GRID_STRIDE(p, (int64_t)nparts) {
         ms = max(ms, psize[p]);
@@ -2539,7 +2581,7 @@ void part_stats(const Level &L, const int32_t *w, const int32_t *part, int32_t n
     if (L.e > 0) {
         int32_t *maxe = A.get<int32_t>(1);
         HPC(cudaMemsetAsync(maxe, 0, sizeof(int32_t), s));
-        k_max_edge<<<grid_of(L.e, 256), 256, 0, s>>>(L.off, L.e, maxe);
+        launch_k(k_max_edge, grid_of(L.e, 256), 256, 0, s, L.off, L.e, maxe);
         HP_LAUNCH_CHECK();
         int32_t me = fetch<int32_t>(maxe, s);
         Plist PL;
@@ -2548,7 +2590,7 @@ void part_stats(const Level &L, const int32_t *w, const int32_t *part, int32_t n
         PL.cin = A.get<int32_t>(L.np);
         PL.lam = A.get<int32_t>(L.e);
         build_plist(L, w, part, me, PL, D, nullptr, A);
-        k_objective<<<grid_of(L.e, 256), 256, 0, s>>>(PL.lam, w, L.e, (unsigned long long *)out,
+        launch_k(k_objective, grid_of(L.e, 256), 256, 0, s, PL.lam, w, L.e, (unsigned long long *)out,
                                                       (unsigned long long *)(out + 1));
         HP_LAUNCH_CHECK();
         A.release(PL.p);
@@ -2557,9 +2599,9 @@ void part_stats(const Level &L, const int32_t *w, const int32_t *part, int32_t n
         A.release(PL.lam);
         A.release(maxe);
     }
-    k_part_sizes<<<grid_of(L.n, 256), 256, 0, s>>>(part, L.n, psize);
+    launch_k(k_part_sizes, grid_of(L.n, 256), 256, 0, s, part, L.n, psize);
     HP_LAUNCH_CHECK();
-    k_part_max<<<grid_of(nparts, 256), 256, 0, s>>>(psize, D, nparts, omega, delta, (long long *)out);
+    launch_k(k_part_max, grid_of(nparts, 256), 256, 0, s, psize, D, nparts, omega, delta, (long long *)out);
     HP_LAUNCH_CHECK();
     A.release(D);
     A.release(psize);
