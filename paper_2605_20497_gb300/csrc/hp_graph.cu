@@ -2,6 +2,7 @@
 // hypergraph construction (Sec. V-E).
 #include <cuda_runtime.h>
 
+#include "hp_cluster.cuh"
 #include "hp_internal.cuh"
 
 namespace hp {
@@ -14,6 +15,7 @@ static int grid_of(int64_t n, int block) {
 }
 #define GRID_STRIDE(i, n) \
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (n); i += (int64_t)gridDim.x * blockDim.x)
+#define CSTRIDE_G(i, n, t0, nt) for (int64_t i = (t0); i < (int64_t)(n); i += (nt))
 
 // ---------------------------------------------------------------- checks
 __global__ void k_check_offsets(const int32_t *off, int32_t e, uint32_t *err) {
@@ -227,30 +229,6 @@ void make_level(int32_t n, int32_t e, const int32_t *off, const int32_t *pins, c
 }
 
 // ---------------------------------------------------------------- contraction
-__global__ void k_rep_flags(const int32_t *mate, int32_t n, int32_t *isrep) {
-    HP_KERNEL_ENTER();
-    GRID_STRIDE(v, (int64_t)n) {
-        int32_t m = mate[v];
-        isrep[v] = (m < 0 || v < m) ? 1 : 0;
-    }
-}
-
-__global__ void k_gamma(const int32_t *mate, const int32_t *cid, const int32_t *size, const int32_t *nbcnt, int32_t n,
-                        int32_t *gamma, int32_t *csize, int32_t *cnb) {
-    HP_KERNEL_ENTER();
-    GRID_STRIDE(v, (int64_t)n) {
-        int32_t m = mate[v];
-        int32_t r = (m >= 0 && m < v) ? m : (int32_t)v;
-        int32_t g = cid[r];
-        gamma[v] = g;
-        if (r == v) {
-            csize[g] = size[v] + (m >= 0 ? size[m] : 0);
-            int64_t b = (int64_t)nbcnt[v] + (m >= 0 ? nbcnt[m] : 0);
-            cnb[g] = b > 0x7fffffff ? 0x7fffffff : (int32_t)b;
-        }
-    }
-}
-
 __device__ __forceinline__ int32_t lower_bound_seg(const int32_t *a, int32_t lo, int32_t hi, int32_t x) {
     while (lo < hi) {
         int32_t mid = (lo + hi) >> 1;
@@ -264,100 +242,289 @@ __device__ __forceinline__ int32_t lower_bound_seg(const int32_t *a, int32_t lo,
 // one copy per cluster: a pin whose partner is not in e is kept; two
 // destinations (or two sources) keep the smaller id; a source whose partner
 // is a destination of e is dropped (the cluster is in dst').
-__global__ void k_keep(const int32_t *pin, const int32_t *pedge, const int32_t *off, const int32_t *nsrc,
-                       const int32_t *mate, const int32_t *ioff, const int32_t *inc, const int32_t *nin, int64_t np,
-                       int32_t *keep) {
-    HP_KERNEL_ENTER();
-    GRID_STRIDE(j, np) {
-        int32_t e = pedge[j], p = pin[j];
-        bool p_src = (int32_t)j - off[e] < nsrc[e];
-        int32_t q = mate[p];
-        int k = 1;
-        if (q >= 0) {
-            int32_t a = ioff[q], m = a + nin[q], b = ioff[q + 1];
-            int32_t t = lower_bound_seg(inc, a, m, e);
-            bool q_dst = t < m && inc[t] == e;
-            bool q_src = false;
-            if (!q_dst) {
-                t = lower_bound_seg(inc, m, b, e);
-                q_src = t < b && inc[t] == e;
+__device__ __forceinline__ int32_t pin_keep(const int32_t *pin, const int32_t *pedge, const int32_t *off,
+                                            const int32_t *nsrc, const int32_t *mate, const int32_t *ioff,
+                                            const int32_t *inc, const int32_t *nin, int64_t j) {
+    int32_t e = pedge[j], p = pin[j];
+    bool p_src = (int32_t)j - off[e] < nsrc[e];
+    int32_t q = mate[p];
+    int k = 1;
+    if (q >= 0) {
+        int32_t a = ioff[q], m = a + nin[q], b = ioff[q + 1];
+        int32_t t = lower_bound_seg(inc, a, m, e);
+        bool q_dst = t < m && inc[t] == e;
+        bool q_src = false;
+        if (!q_dst) {
+            t = lower_bound_seg(inc, m, b, e);
+            q_src = t < b && inc[t] == e;
+        }
+        if (p_src) k = (!q_dst && !q_src) || (q_src && p < q);
+        else k = (!q_dst && !q_src) || q_src || p < q;
+    }
+    return k;
+}
+
+
+
+// ---------------------------------------------------------------- coarse incidence by rank
+// The coarse incidence is not sorted anew.  A coarse node c = {u, w} has
+// in(c) = in(u) U in(w) and out(c) = (out(u) U out(w)) \ in(c), each
+// ascending by hyperedge, and an incidence entry (v, e) survives exactly when
+// the pin v of e survives (the keep rule above, seen from the node's side).
+// So every surviving entry of u or w is written straight to its place: its
+// rank among the surviving entries of its own list plus the number of
+// surviving entries of the partner's list below it (one binary search), both
+// read off one prefix sum over the keep flags of the fine incidence.
+// Levels of up to CONTRACT_CLUSTER_NP pins run the steps in one launch on one
+// thread-block cluster; larger ones as a few grid-wide kernels.
+constexpr int64_t CONTRACT_CLUSTER_NP = int64_t(1) << 15;
+
+struct ContractArgs {
+    Level L;                 // the fine level
+    const int32_t *mate;
+    LevelBox *box;           // cn, cnp are written here
+    int32_t *isrep, *cid, *keep, *newpos, *ik, *ipos, *rep_of, *ccnt;   // scratch: n, n, np, np, np, np+1, n, n
+    Level C;                 // coarse arrays allocated for L.n nodes and L.np pins (ioff: n + 1)
+    int32_t *gamma;          // [L.n]
+};
+
+__device__ __forceinline__ bool in_sorted(const int32_t *a, int32_t lo, int32_t hi, int32_t x) {
+    const int32_t t = lower_bound_seg(a, lo, hi, x);
+    return t < hi && a[t] == x;
+}
+
+// whether incidence entry t of the fine level survives contraction: the
+// entry (v, e) of a destination survives unless v is the larger member of
+// its pair and the partner is also a destination of e; the entry of a
+// source survives unless the partner is a destination of e, or v is the
+// larger member and the partner is also a source of e
+__device__ __forceinline__ int32_t inc_keep(const Level &L, const int32_t *mate, int64_t t) {
+    const int32_t v = L.inode[t], w = mate[v];
+    if (w < 0) return 1;
+    const int32_t e = L.inc[t];
+    const int32_t wa = L.ioff[w], wm = wa + L.nin[w], wb = L.ioff[w + 1];
+    const bool w_dst = in_sorted(L.inc, wa, wm, e);
+    if (t < (int64_t)L.ioff[v] + L.nin[v]) return (v < w || !w_dst) ? 1 : 0;
+    if (w_dst) return 0;
+    return (v < w || !in_sorted(L.inc, wm, wb, e)) ? 1 : 0;
+}
+
+// a level whose matching formed no pair is not contracted; one whose
+// matching gave up is reported by the host and not contracted either
+__device__ __forceinline__ bool contract_off(const LevelBox *box) {
+    return box->err != 0u || box->pairs + box->iso == 0ull;
+}
+
+// representatives (the smaller member of a pair), surviving pins and
+// surviving incidence entries
+__device__ __forceinline__ void ph_c_flags(const ContractArgs &A, int64_t t0, int64_t nt) {
+    const Level &L = A.L;
+    CSTRIDE_G(v, L.n, t0, nt) {
+        const int32_t m = A.mate[v];
+        A.isrep[v] = (m < 0 || (int32_t)v < m) ? 1 : 0;
+    }
+    CSTRIDE_G(j, L.np, t0, nt) {
+        A.keep[j] = pin_keep(L.pin, L.pedge, L.off, L.nsrc, A.mate, L.ioff, L.inc, L.nin, j);
+        A.ik[j] = inc_keep(L, A.mate, j);
+    }
+}
+
+// gamma, coarse sizes and neighbour bounds, the representative of every
+// coarse node, coarse hyperedge segments
+__device__ __forceinline__ void ph_c_map(const ContractArgs &A, int64_t t0, int64_t nt) {
+    const Level &L = A.L;
+    const Level &C = A.C;
+    const int32_t cnp = A.box->cnp;
+    CSTRIDE_G(v0, L.n, t0, nt) {
+        const int32_t v = (int32_t)v0, m = A.mate[v];
+        const int32_t r = (m >= 0 && m < v) ? m : v, g = A.cid[r];
+        A.gamma[v] = g;
+        if (r == v) {
+            C.size[g] = L.size[v] + (m >= 0 ? L.size[m] : 0);
+            const int64_t b = (int64_t)L.nbnd[v] + (m >= 0 ? L.nbnd[m] : 0);
+            C.nbnd[g] = b > 0x7fffffff ? 0x7fffffff : (int32_t)b;
+            A.rep_of[g] = v;
+        }
+    }
+    CSTRIDE_G(i, L.e, t0, nt) {
+        const int32_t a = A.newpos[L.off[i]];
+        const int64_t k = (int64_t)L.off[i] + L.nsrc[i];
+        C.off[i] = a;
+        C.nsrc[i] = (k < L.np ? A.newpos[k] : cnp) - a;
+    }
+    if (t0 == 0) C.off[L.e] = cnp;
+}
+
+// coarse pins; surviving incidence entries per coarse node (0 beyond the
+// last coarse node, so that a scan over L.n entries ends every segment)
+__device__ __forceinline__ void ph_c_pins(const ContractArgs &A, int64_t t0, int64_t nt) {
+    const Level &L = A.L;
+    const Level &C = A.C;
+    const int32_t cn = A.box->cn;
+    CSTRIDE_G(j, L.np, t0, nt) {
+        if (A.keep[j]) {
+            const int32_t k = A.newpos[j];
+            C.pin[k] = A.gamma[L.pin[j]];
+            C.pedge[k] = L.pedge[j];
+        }
+    }
+    CSTRIDE_G(c, L.n, t0, nt) {
+        int32_t kd = 0, ks = 0;
+        if (c < cn) {
+            const int32_t u = A.rep_of[c], w = A.mate[u];
+            for (int k = 0; k < 2; k++) {
+                const int32_t v = k == 0 ? u : w;
+                if (v < 0) break;
+                const int32_t a = L.ioff[v], m = a + L.nin[v], b = L.ioff[v + 1];
+                kd += A.ipos[m] - A.ipos[a];
+                ks += A.ipos[b] - A.ipos[m];
             }
-            if (p_src) k = (!q_dst && !q_src) || (q_src && p < q);
-            else k = (!q_dst && !q_src) || q_src || p < q;
+            C.nin[c] = kd;
         }
-        keep[j] = k;
+        A.ccnt[c] = kd + ks;
     }
 }
 
-__global__ void k_coarse_edges(const int32_t *off, const int32_t *nsrc, const int32_t *newpos, int32_t e,
-                               int32_t *coff, int32_t *cnsrc) {
-    HP_KERNEL_ENTER();
-    GRID_STRIDE(i, (int64_t)e) {
-        int32_t a = newpos[off[i]];
-        coff[i] = a;
-        cnsrc[i] = newpos[off[i] + nsrc[i]] - a;
+// every surviving incidence entry at its rank in the coarse lists
+__device__ __forceinline__ void ph_c_fill(const ContractArgs &A, int64_t t0, int64_t nt) {
+    const Level &L = A.L;
+    const Level &C = A.C;
+    if (t0 == 0 && A.ipos[L.np] != A.box->cnp) atomicOr(&A.box->err, E_INTERNAL);
+    CSTRIDE_G(t, L.np, t0, nt) {
+        if (!A.ik[t]) continue;
+        const int32_t v = L.inode[t], c = A.gamma[v], u = A.rep_of[c];
+        const int32_t other = v == u ? A.mate[u] : u;
+        const int32_t x = L.inc[t];
+        const int32_t va = L.ioff[v], vm = va + L.nin[v];
+        const bool dst = t < (int64_t)vm;
+        int32_t r = A.ipos[t] - A.ipos[dst ? va : vm];
+        if (other >= 0) {
+            const int32_t oa = L.ioff[other], om = oa + L.nin[other], ob = L.ioff[other + 1];
+            const int32_t lo = dst ? oa : om, hi = dst ? om : ob;
+            r += A.ipos[lower_bound_seg(L.inc, lo, hi, x)] - A.ipos[lo];
+        }
+        const int32_t pos = C.ioff[c] + (dst ? 0 : C.nin[c]) + r;
+        if (pos < C.ioff[c + 1]) {
+            C.inc[pos] = x;
+            C.inode[pos] = c;
+        } else {
+            atomicOr(&A.box->err, E_INTERNAL);
+        }
     }
 }
 
-__global__ void k_coarse_pins(const int32_t *pin, const int32_t *pedge, const int32_t *keep, const int32_t *newpos,
-                              const int32_t *gamma, int64_t np, int32_t *cpin, int32_t *cpedge) {
+__global__ void __cluster_dims__(SQ_CS, 1, 1) __launch_bounds__(SQ_T) k_contract_cluster(ContractArgs A) {
     HP_KERNEL_ENTER();
-    GRID_STRIDE(j, np) {
-        if (keep[j]) {
-            int32_t k = newpos[j];
-            cpin[k] = gamma[pin[j]];
-            cpedge[k] = pedge[j];
-        }
+    __shared__ int32_t s_tmp[40];
+    __shared__ int32_t s_part;
+    cg::cluster_group cl = cg::this_cluster();
+    if (contract_off(A.box)) return;   // uniform over the cluster
+    const int64_t t0 = (int64_t)cl.block_rank() * blockDim.x + threadIdx.x, nt = (int64_t)SQ_CS * blockDim.x;
+    const int32_t n = A.L.n, np = (int32_t)A.L.np;
+    ph_c_flags(A, t0, nt);
+    cl.sync();
+    const int32_t cn = cluster_scan_excl<int32_t>(cl, A.isrep, A.cid, n, s_tmp, &s_part);
+    const int32_t cnp = cluster_scan_excl<int32_t>(cl, A.keep, A.newpos, np, s_tmp, &s_part);
+    const int32_t cni = cluster_scan_excl<int32_t>(cl, A.ik, A.ipos, np, s_tmp, &s_part);
+    if (t0 == 0) {
+        A.box->cn = cn;
+        A.box->cnp = cnp;
+        A.ipos[np] = cni;
     }
+    cl.sync();
+    ph_c_map(A, t0, nt);
+    cl.sync();
+    ph_c_pins(A, t0, nt);
+    cl.sync();
+    const int32_t total = cluster_scan_excl<int32_t>(cl, A.ccnt, A.C.ioff, n, s_tmp, &s_part);
+    if (t0 == 0) A.C.ioff[n] = total;
+    cl.sync();
+    ph_c_fill(A, t0, nt);
+}
+
+__global__ void k_c_flags(ContractArgs A) {
+    HP_KERNEL_ENTER();
+    ph_c_flags(A, blockIdx.x * (int64_t)blockDim.x + threadIdx.x, (int64_t)gridDim.x * blockDim.x);
+}
+__global__ void k_c_map(ContractArgs A) {
+    HP_KERNEL_ENTER();
+    if (contract_off(A.box)) return;
+    ph_c_map(A, blockIdx.x * (int64_t)blockDim.x + threadIdx.x, (int64_t)gridDim.x * blockDim.x);
+}
+__global__ void k_c_pins(ContractArgs A) {
+    HP_KERNEL_ENTER();
+    if (contract_off(A.box)) return;
+    ph_c_pins(A, blockIdx.x * (int64_t)blockDim.x + threadIdx.x, (int64_t)gridDim.x * blockDim.x);
+}
+__global__ void k_c_fill(ContractArgs A) {
+    HP_KERNEL_ENTER();
+    if (contract_off(A.box)) return;
+    ph_c_fill(A, blockIdx.x * (int64_t)blockDim.x + threadIdx.x, (int64_t)gridDim.x * blockDim.x);
 }
 
 bool contract_level(const Level &L, const int32_t *mate, LevelBox *box, LevelBox *hb, Level &C, Arena &A) {
     cudaStream_t s = A.stream();
-    int32_t *isrep = A.get<int32_t>(L.n);
-    int32_t *cid = A.get<int32_t>(L.n + 1);
-    launch_k(k_rep_flags, grid_of(L.n, 256), 256, 0, s, mate, L.n, isrep);
-    HP_LAUNCH_CHECK();
-    scan_excl(isrep, cid, L.n, &box->cn, A);
-    int32_t *keep = A.get<int32_t>(L.np);
-    int32_t *newpos = A.get<int32_t>(L.np + 1);
-    if (L.np) {
-        launch_k(k_keep, grid_of(L.np, 256), 256, 0, s, L.pin, L.pedge, L.off, L.nsrc, mate, L.ioff, L.inc, L.nin, L.np,
-                                                   keep);
+    const int32_t n = L.n, e = L.e;
+    const int64_t np = L.np;
+    ContractArgs X;
+    X.L = L;
+    X.mate = mate;
+    X.box = box;
+    X.isrep = A.get<int32_t>(n);
+    X.cid = A.get<int32_t>(n);
+    X.keep = A.get<int32_t>(np);
+    X.newpos = A.get<int32_t>(np);
+    X.ik = A.get<int32_t>(np);
+    X.ipos = A.get<int32_t>(np + 1);
+    X.rep_of = A.get<int32_t>(n);
+    X.ccnt = A.get<int32_t>(n);
+    // the coarse level at the fine level's sizes (nodes and pins only shrink)
+    Level K;
+    K.size = A.get<int32_t>(n);
+    K.nbnd = A.get<int32_t>(n);
+    K.off = A.get<int32_t>(e + 1);
+    K.nsrc = A.get<int32_t>(e);
+    K.pin = A.get<int32_t>(np);
+    K.pedge = A.get<int32_t>(np);
+    K.ioff = A.get<int32_t>(n + 1);
+    K.nin = A.get<int32_t>(n);
+    K.inc = A.get<int32_t>(np);
+    K.inode = A.get<int32_t>(np);
+    X.C = K;
+    X.gamma = A.get<int32_t>(n);
+    if (np <= CONTRACT_CLUSTER_NP && np > 0 && n > 0) {
+        launch_k(k_contract_cluster, SQ_CS, SQ_T, 0, s, X);
+        HP_LAUNCH_CHECK();
+    } else {
+        const int g = grid_of(std::max<int64_t>(n, np), 256);
+        launch_k(k_c_flags, g, 256, 0, s, X);
+        HP_LAUNCH_CHECK();
+        scan_excl(X.isrep, X.cid, n, &box->cn, A);
+        scan_excl(X.keep, X.newpos, np, &box->cnp, A);
+        scan_excl(X.ik, X.ipos, np, X.ipos + np, A);
+        launch_k(k_c_map, grid_of(std::max<int64_t>(n, e), 256), 256, 0, s, X);
+        HP_LAUNCH_CHECK();
+        launch_k(k_c_pins, g, 256, 0, s, X);
+        HP_LAUNCH_CHECK();
+        scan_excl(X.ccnt, K.ioff, n, K.ioff + n, A);
+        launch_k(k_c_fill, grid_of(np, 256), 256, 0, s, X);
         HP_LAUNCH_CHECK();
     }
-    scan_excl(keep, newpos, L.np, &box->cnp, A);
-    HPC(cudaMemcpyAsync(newpos + L.np, &box->cnp, sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
     fetch_bytes(hb, box, sizeof(LevelBox), s);
+    for (void *p : {(void *)X.isrep, (void *)X.cid, (void *)X.keep, (void *)X.newpos, (void *)X.ik, (void *)X.ipos,
+                    (void *)X.rep_of, (void *)X.ccnt})
+        A.release(p);
     if (hb->pairs + hb->iso == 0) {
-        for (void *p : {(void *)isrep, (void *)cid, (void *)keep, (void *)newpos}) A.release(p);
+        for (void *p : {(void *)K.size, (void *)K.nbnd, (void *)K.off, (void *)K.nsrc, (void *)K.pin, (void *)K.pedge,
+                        (void *)K.ioff, (void *)K.nin, (void *)K.inc, (void *)K.inode, (void *)X.gamma})
+            A.release(p);
         return false;
     }
+    const_cast<Level &>(L).gamma = X.gamma;
+    C = K;
     C.n = hb->cn;
-    C.e = L.e;
+    C.e = e;
     C.np = hb->cnp;
-    C.size = A.get<int32_t>(C.n);
-    C.nbnd = A.get<int32_t>(C.n);
-    const_cast<Level &>(L).gamma = A.get<int32_t>(L.n);
-    launch_k(k_gamma, grid_of(L.n, 256), 256, 0, s, mate, cid, L.size, L.nbnd, L.n, L.gamma, C.size, C.nbnd);
-    HP_LAUNCH_CHECK();
-    A.release(isrep);
-    A.release(cid);
-    C.off = A.get<int32_t>(C.e + 1);
-    C.nsrc = A.get<int32_t>(C.e);
-    C.pin = A.get<int32_t>(C.np);
-    C.pedge = A.get<int32_t>(C.np);
-    if (C.e > 0) {
-        launch_k(k_coarse_edges, grid_of(C.e, 256), 256, 0, s, L.off, L.nsrc, newpos, C.e, C.off, C.nsrc);
-        HP_LAUNCH_CHECK();
-    }
-    HPC(cudaMemcpyAsync(C.off + C.e, newpos + L.np, sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
-    if (L.np) {
-        launch_k(k_coarse_pins, grid_of(L.np, 256), 256, 0, s, L.pin, L.pedge, keep, newpos, L.gamma, L.np, C.pin, C.pedge);
-        HP_LAUNCH_CHECK();
-    }
-    A.release(keep);
-    A.release(newpos);
-    build_incidence(C, A);
     return true;
 }
 
