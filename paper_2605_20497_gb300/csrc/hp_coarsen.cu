@@ -1109,11 +1109,16 @@ __device__ __forceinline__ void ph_targets(const int32_t *cand, const uint64_t *
 // |child(n) \ R| per node, twice: the count and the counter of children still to finish
 __device__ __forceinline__ void ph_child_count(const int32_t *target, int32_t n, int32_t *ccount, int32_t *pending,
                                                int64_t t0, int64_t nt) {
+    const int lane = threadIdx.x & 31;
     CSTRIDE(v, n, t0, nt) {
-        int32_t t = target[v];
-        if (t >= 0 && target[t] != v) {
-            atomicAdd(&ccount[t], 1);
-            atomicAdd(&pending[t], 1);
+        // the lanes of a warp with the same parent count once (stars)
+        const unsigned act = __activemask();
+        const int32_t t = target[v];
+        const bool child = t >= 0 && target[t] != v;
+        const unsigned g = __match_any_sync(act, child ? t : -1 - lane);
+        if (child && (g & ((1u << lane) - 1u)) == 0u) {
+            atomicAdd(&ccount[t], __popc(g));
+            atomicAdd(&pending[t], __popc(g));
         }
     }
 }

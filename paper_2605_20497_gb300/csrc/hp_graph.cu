@@ -283,7 +283,11 @@ struct ContractArgs {
     Level L;                 // the fine level
     const int32_t *mate;
     LevelBox *box;           // cn, cnp are written here
-    int32_t *isrep, *cid, *keep, *newpos, *ik, *ipos, *rep_of, *ccnt;   // scratch: n, n, np, np, np, np+1, n, n
+    int32_t *isrep, *cid, *rep_of, *ccnt;   // scratch of n entries
+    // per fine pin position / incidence entry: (pin survives) << 32 | (entry
+    // survives), and its exclusive prefix sum (np + 1 entries): the high
+    // words number the coarse pins, the low words the coarse incidence
+    int64_t *kflag, *kscan;
     Level C;                 // coarse arrays allocated for L.n nodes and L.np pins (ioff: n + 1)
     int32_t *gamma;          // [L.n]
 };
@@ -309,6 +313,9 @@ __device__ __forceinline__ int32_t inc_keep(const Level &L, const int32_t *mate,
     return (v < w || !in_sorted(L.inc, wm, wb, e)) ? 1 : 0;
 }
 
+__device__ __forceinline__ int32_t newpos_of(const ContractArgs &A, int64_t j) { return (int32_t)(A.kscan[j] >> 32); }
+__device__ __forceinline__ int32_t ipos_of(const ContractArgs &A, int64_t t) { return (int32_t)(uint32_t)A.kscan[t]; }
+
 // a level whose matching formed no pair is not contracted; one whose
 // matching gave up is reported by the host and not contracted either
 __device__ __forceinline__ bool contract_off(const LevelBox *box) {
@@ -323,10 +330,9 @@ __device__ __forceinline__ void ph_c_flags(const ContractArgs &A, int64_t t0, in
         const int32_t m = A.mate[v];
         A.isrep[v] = (m < 0 || (int32_t)v < m) ? 1 : 0;
     }
-    CSTRIDE_G(j, L.np, t0, nt) {
-        A.keep[j] = pin_keep(L.pin, L.pedge, L.off, L.nsrc, A.mate, L.ioff, L.inc, L.nin, j);
-        A.ik[j] = inc_keep(L, A.mate, j);
-    }
+    CSTRIDE_G(j, L.np, t0, nt)
+        A.kflag[j] = ((int64_t)pin_keep(L.pin, L.pedge, L.off, L.nsrc, A.mate, L.ioff, L.inc, L.nin, j) << 32) |
+                     (int64_t)inc_keep(L, A.mate, j);
 }
 
 // gamma, coarse sizes and neighbour bounds, the representative of every
@@ -334,7 +340,7 @@ __device__ __forceinline__ void ph_c_flags(const ContractArgs &A, int64_t t0, in
 __device__ __forceinline__ void ph_c_map(const ContractArgs &A, int64_t t0, int64_t nt) {
     const Level &L = A.L;
     const Level &C = A.C;
-    const int32_t cnp = A.box->cnp;
+    const int32_t cnp = newpos_of(A, L.np);
     CSTRIDE_G(v0, L.n, t0, nt) {
         const int32_t v = (int32_t)v0, m = A.mate[v];
         const int32_t r = (m >= 0 && m < v) ? m : v, g = A.cid[r];
@@ -347,12 +353,14 @@ __device__ __forceinline__ void ph_c_map(const ContractArgs &A, int64_t t0, int6
         }
     }
     CSTRIDE_G(i, L.e, t0, nt) {
-        const int32_t a = A.newpos[L.off[i]];
-        const int64_t k = (int64_t)L.off[i] + L.nsrc[i];
+        const int32_t a = newpos_of(A, L.off[i]);
         C.off[i] = a;
-        C.nsrc[i] = (k < L.np ? A.newpos[k] : cnp) - a;
+        C.nsrc[i] = newpos_of(A, (int64_t)L.off[i] + L.nsrc[i]) - a;
     }
-    if (t0 == 0) C.off[L.e] = cnp;
+    if (t0 == 0) {
+        C.off[L.e] = cnp;
+        A.box->cnp = cnp;
+    }
 }
 
 // coarse pins; surviving incidence entries per coarse node (0 beyond the
@@ -362,8 +370,8 @@ __device__ __forceinline__ void ph_c_pins(const ContractArgs &A, int64_t t0, int
     const Level &C = A.C;
     const int32_t cn = A.box->cn;
     CSTRIDE_G(j, L.np, t0, nt) {
-        if (A.keep[j]) {
-            const int32_t k = A.newpos[j];
+        if (A.kflag[j] >> 32) {
+            const int32_t k = newpos_of(A, j);
             C.pin[k] = A.gamma[L.pin[j]];
             C.pedge[k] = L.pedge[j];
         }
@@ -376,8 +384,8 @@ __device__ __forceinline__ void ph_c_pins(const ContractArgs &A, int64_t t0, int
                 const int32_t v = k == 0 ? u : w;
                 if (v < 0) break;
                 const int32_t a = L.ioff[v], m = a + L.nin[v], b = L.ioff[v + 1];
-                kd += A.ipos[m] - A.ipos[a];
-                ks += A.ipos[b] - A.ipos[m];
+                kd += ipos_of(A, m) - ipos_of(A, a);
+                ks += ipos_of(A, b) - ipos_of(A, m);
             }
             C.nin[c] = kd;
         }
@@ -389,19 +397,19 @@ __device__ __forceinline__ void ph_c_pins(const ContractArgs &A, int64_t t0, int
 __device__ __forceinline__ void ph_c_fill(const ContractArgs &A, int64_t t0, int64_t nt) {
     const Level &L = A.L;
     const Level &C = A.C;
-    if (t0 == 0 && A.ipos[L.np] != A.box->cnp) atomicOr(&A.box->err, E_INTERNAL);
+    if (t0 == 0 && ipos_of(A, L.np) != newpos_of(A, L.np)) atomicOr(&A.box->err, E_INTERNAL);
     CSTRIDE_G(t, L.np, t0, nt) {
-        if (!A.ik[t]) continue;
+        if (!(A.kflag[t] & 1)) continue;
         const int32_t v = L.inode[t], c = A.gamma[v], u = A.rep_of[c];
         const int32_t other = v == u ? A.mate[u] : u;
         const int32_t x = L.inc[t];
         const int32_t va = L.ioff[v], vm = va + L.nin[v];
         const bool dst = t < (int64_t)vm;
-        int32_t r = A.ipos[t] - A.ipos[dst ? va : vm];
+        int32_t r = ipos_of(A, t) - ipos_of(A, dst ? va : vm);
         if (other >= 0) {
             const int32_t oa = L.ioff[other], om = oa + L.nin[other], ob = L.ioff[other + 1];
             const int32_t lo = dst ? oa : om, hi = dst ? om : ob;
-            r += A.ipos[lower_bound_seg(L.inc, lo, hi, x)] - A.ipos[lo];
+            r += ipos_of(A, lower_bound_seg(L.inc, lo, hi, x)) - ipos_of(A, lo);
         }
         const int32_t pos = C.ioff[c] + (dst ? 0 : C.nin[c]) + r;
         if (pos < C.ioff[c + 1]) {
@@ -417,6 +425,8 @@ __global__ void __cluster_dims__(SQ_CS, 1, 1) __launch_bounds__(SQ_T) k_contract
     HP_KERNEL_ENTER();
     __shared__ int32_t s_tmp[40];
     __shared__ int32_t s_part;
+    __shared__ long long s_ll[40];
+    __shared__ long long s_pll;
     cg::cluster_group cl = cg::this_cluster();
     if (contract_off(A.box)) return;   // uniform over the cluster
     const int64_t t0 = (int64_t)cl.block_rank() * blockDim.x + threadIdx.x, nt = (int64_t)SQ_CS * blockDim.x;
@@ -424,12 +434,11 @@ __global__ void __cluster_dims__(SQ_CS, 1, 1) __launch_bounds__(SQ_T) k_contract
     ph_c_flags(A, t0, nt);
     cl.sync();
     const int32_t cn = cluster_scan_excl<int32_t>(cl, A.isrep, A.cid, n, s_tmp, &s_part);
-    const int32_t cnp = cluster_scan_excl<int32_t>(cl, A.keep, A.newpos, np, s_tmp, &s_part);
-    const int32_t cni = cluster_scan_excl<int32_t>(cl, A.ik, A.ipos, np, s_tmp, &s_part);
+    const long long tot = cluster_scan_excl<long long>(cl, reinterpret_cast<long long *>(A.kflag),
+                                                       reinterpret_cast<long long *>(A.kscan), np, s_ll, &s_pll);
     if (t0 == 0) {
         A.box->cn = cn;
-        A.box->cnp = cnp;
-        A.ipos[np] = cni;
+        A.kscan[np] = tot;
     }
     cl.sync();
     ph_c_map(A, t0, nt);
@@ -472,10 +481,8 @@ bool contract_level(const Level &L, const int32_t *mate, LevelBox *box, LevelBox
     X.box = box;
     X.isrep = A.get<int32_t>(n);
     X.cid = A.get<int32_t>(n);
-    X.keep = A.get<int32_t>(np);
-    X.newpos = A.get<int32_t>(np);
-    X.ik = A.get<int32_t>(np);
-    X.ipos = A.get<int32_t>(np + 1);
+    X.kflag = A.get<int64_t>(np);
+    X.kscan = A.get<int64_t>(np + 1);
     X.rep_of = A.get<int32_t>(n);
     X.ccnt = A.get<int32_t>(n);
     // the coarse level at the fine level's sizes (nodes and pins only shrink)
@@ -500,8 +507,7 @@ bool contract_level(const Level &L, const int32_t *mate, LevelBox *box, LevelBox
         launch_k(k_c_flags, g, 256, 0, s, X);
         HP_LAUNCH_CHECK();
         scan_excl(X.isrep, X.cid, n, &box->cn, A);
-        scan_excl(X.keep, X.newpos, np, &box->cnp, A);
-        scan_excl(X.ik, X.ipos, np, X.ipos + np, A);
+        scan_excl(X.kflag, X.kscan, np, X.kscan + np, A);
         launch_k(k_c_map, grid_of(std::max<int64_t>(n, e), 256), 256, 0, s, X);
         HP_LAUNCH_CHECK();
         launch_k(k_c_pins, g, 256, 0, s, X);
@@ -511,8 +517,7 @@ bool contract_level(const Level &L, const int32_t *mate, LevelBox *box, LevelBox
         HP_LAUNCH_CHECK();
     }
     fetch_bytes(hb, box, sizeof(LevelBox), s);
-    for (void *p : {(void *)X.isrep, (void *)X.cid, (void *)X.keep, (void *)X.newpos, (void *)X.ik, (void *)X.ipos,
-                    (void *)X.rep_of, (void *)X.ccnt})
+    for (void *p : {(void *)X.isrep, (void *)X.cid, (void *)X.kflag, (void *)X.kscan, (void *)X.rep_of, (void *)X.ccnt})
         A.release(p);
     if (hb->pairs + hb->iso == 0) {
         for (void *p : {(void *)K.size, (void *)K.nbnd, (void *)K.off, (void *)K.nsrc, (void *)K.pin, (void *)K.pedge,

@@ -908,7 +908,7 @@ struct ChainCtx {
     int32_t *pred, *succ, *choice;
     unsigned long long *pen, *minpen;     // general acceptance
     int32_t *accnode;
-    unsigned long long *acc[2];           // packed acceptance (penalty < 2^32)
+    unsigned long long *acc[3];           // packed acceptance (penalty < 2^32)
     int32_t *linked;                      // linked[r]: round r linked something
 };
 
@@ -999,6 +999,91 @@ __device__ void ph_link(const ChainCtx &C, int r, int packed, int32_t m, int64_t
             C.linked[r] = 1;
         }
         if (packed) ((r & 1) ? C.acc[0] : C.acc[1])[i] = 0;
+    }
+}
+
+// One chaining round with one barrier (packed acceptance only).  Round r's
+// winners are linked in round r + 1's pass instead of a pass of their own:
+// the chooser of a move j won it in round r iff acc_r[j] holds its key, and a
+// move j already has a predecessor in round r + 1 iff pred[j] >= 0 (rounds
+// before r) or acc_r[j] != 0 (round r: every chosen move gets exactly one
+// winner).  The slots rotate over three arrays, round r in acc[r % 3]; the
+// pass of round r clears acc[(r + 1) % 3], which the pass of round r - 1 read
+// and the pass of round r + 1 fills.  The links of the last round are made by
+// ph_link_last.  The result equals the two-pass round above.
+__device__ __forceinline__ unsigned long long chain_key(unsigned long long pen, int32_t node) {
+    return ((0xffffffffull - pen) << 32) | (unsigned long long)(uint32_t)node;
+}
+__device__ void ph_round(const ChainCtx &C, int r, int32_t m, int64_t t0, int64_t nt) {
+    constexpr int B = 4;
+    unsigned long long *accr = C.acc[r % 3], *accp = C.acc[(r + 2) % 3], *accn = C.acc[(r + 1) % 3];
+    STRIDE(i0, m, t0, nt) {
+        const int32_t i = (int32_t)i0;
+        bool taken_end = C.succ[i] >= 0;
+        if (r > 0) {
+            const int32_t j = C.choice[i];
+            if (j >= 0 && accp[j] == chain_key(C.pen[i], C.node[i])) {
+                C.pred[j] = i;
+                C.succ[i] = j;
+                taken_end = true;
+            }
+        }
+        accn[i] = 0;
+        C.choice[i] = -1;
+        if (taken_end) continue;
+        const int32_t d = C.dst[i];
+        int32_t seen = 0, best = -1;
+        __int128 bG = 0;
+        unsigned long long bpen = 0;
+        const int32_t szi = C.msz[i], nii = C.mni[i];
+        const int32_t jend = C.first[d + 1];
+        for (int32_t j0 = C.first[d]; j0 < jend && seen < C.window; j0 += B) {
+            bool tk[B];
+            int32_t sz[B], ni[B];
+            long long gn[B];
+#pragma unroll
+            for (int u = 0; u < B; u++) {
+                const int32_t j = j0 + u;
+                const bool ok = j < jend;
+                tk[u] = ok ? (C.pred[j] >= 0 || (r > 0 && accp[j] != 0ull)) : true;
+                sz[u] = ok ? C.msz[j] : 0;
+                ni[u] = ok ? C.mni[j] : 0;
+                gn[u] = ok ? C.gain[j] : 0;
+            }
+#pragma unroll
+            for (int u = 0; u < B; u++) {
+                const int32_t j = j0 + u;
+                if (j >= jend || seen >= C.window) break;
+                if (tk[u] || j == i) continue;
+                seen++;
+                const long long ds = (long long)szi - sz[u], di = (long long)nii - ni[u];
+                const unsigned long long pen =
+                    10ull * (unsigned long long)(ds < 0 ? -ds : ds) + (unsigned long long)(di < 0 ? -di : di);
+                const __int128 G = (__int128)gn[u] * 10000000 - (__int128)pen;
+                if (best < 0 || G > bG) {
+                    best = j;
+                    bG = G;
+                    bpen = pen;
+                }
+            }
+        }
+        C.choice[i] = best;
+        C.pen[i] = bpen;
+        if (best >= 0) {
+            atomicMax(&accr[best], chain_key(bpen, C.node[i]));
+            C.linked[r] = 1;
+        }
+    }
+}
+// the links of round r, the last round run (nothing when it chose nothing)
+__device__ void ph_link_last(const ChainCtx &C, int r, int32_t m, int64_t t0, int64_t nt) {
+    const unsigned long long *accr = C.acc[r % 3];
+    STRIDE(i0, m, t0, nt) {
+        const int32_t i = (int32_t)i0, j = C.choice[i];
+        if (j >= 0 && accr[j] == chain_key(C.pen[i], C.node[i])) {
+            C.pred[j] = i;
+            C.succ[i] = j;
+        }
     }
 }
 
@@ -1308,6 +1393,16 @@ __global__ void k_link(ChainCtx C, const int32_t *mcount, int r, int packed) {
     if (r > 0 && !C.linked[r - 1]) return;
     ph_link(C, r, packed, *mcount, G_T0, G_NT);
 }
+__global__ void k_round(ChainCtx C, const int32_t *mcount, int r) {
+    HP_KERNEL_ENTER();
+    if (r > 0 && !C.linked[r - 1]) return;
+    ph_round(C, r, *mcount, G_T0, G_NT);
+}
+__global__ void k_link_last(ChainCtx C, const int32_t *mcount, int r) {
+    HP_KERNEL_ENTER();
+    if (!C.linked[r]) return;
+    ph_link_last(C, r, *mcount, G_T0, G_NT);
+}
 __global__ void k_path_heads(SeqCtx S, const int32_t *mcount) { HP_KERNEL_ENTER(); ph_path_heads(S, *mcount, G_T0, G_NT); }
 __global__ void k_cycle_heads(SeqCtx S, const int32_t *mcount) { HP_KERNEL_ENTER(); ph_cycle_heads(S, *mcount, G_T0, G_NT); }
 __global__ void k_head_collect(SeqCtx S, const int32_t *mcount, uint32_t *heads, int32_t *nh) {
@@ -1450,15 +1545,22 @@ __global__ void __cluster_dims__(SQ_CS, 1, 1) __launch_bounds__(SEQ_T) k_seq_clu
     // chaining rounds (Sec. VI-C)
     for (int rr = 0; rr < A.rounds; rr++) {
         if (rr > 0 && !*(volatile int32_t *)&A.C.linked[rr - 1]) break;
+        if (A.packed) {
+            ph_round(A.C, rr, m, t0, nt);
+            cl.sync();
+            continue;
+        }
         ph_choose(A.C, rr, A.packed, m, t0, nt);
         cl.sync();
-        if (!A.packed) {
-            ph_accept_min(A.C, m, t0, nt);
-            cl.sync();
-            ph_accept_id(A.C, m, t0, nt);
-            cl.sync();
-        }
+        ph_accept_min(A.C, m, t0, nt);
+        cl.sync();
+        ph_accept_id(A.C, m, t0, nt);
+        cl.sync();
         ph_link(A.C, rr, A.packed, m, t0, nt);
+        cl.sync();
+    }
+    if (A.packed && A.rounds > 0 && *(volatile int32_t *)&A.C.linked[A.rounds - 1]) {
+        ph_link_last(A.C, A.rounds - 1, m, t0, nt);
         cl.sync();
     }
     // chains, ordered by (total gain desc, head node asc)
@@ -1964,7 +2066,7 @@ struct LevelWs {
     uint32_t *idx;
     int32_t *msz, *mni;
     int32_t *first, *choice, *accnode, *pos, *clen, *lens, *starts, *cstart, *seqmove;
-    unsigned long long *pen, *minpen, *acc1;
+    unsigned long long *pen, *minpen, *acc1, *acc2;
     uint32_t *heads;
     uint64_t *hkeys;
     uint32_t *vkey, *vidx;
@@ -2068,6 +2170,7 @@ static LevelWs *refine_workspace_body(LevelWs *W, int32_t n, int64_t np, int32_t
     W->pen = A.get<unsigned long long>(n);
     W->minpen = A.get<unsigned long long>(n);
     W->acc1 = A.get<unsigned long long>(n);
+    W->acc2 = A.get<unsigned long long>(n);
     W->pos = A.get<int32_t>(n);
     W->clen = A.get<int32_t>(n);
     W->lens = A.get<int32_t>(n);
@@ -2123,7 +2226,7 @@ void refine_workspace_free(LevelWs *W, Arena &A) {
              W->R.D0, W->R.psize, W->R.saving, W->R.pc, W->R.pred, W->R.succ, W->R.chain, W->R.mvpos, W->R.cgain,
              W->R.gseq, W->R.acc0, W->R.dDs, W->R.dDd, W->R.viol, W->cl, W->hubs, W->cw, W->cflag, W->cpos, W->cut, W->cut_off, W->tiny, W->mid, W->touched, W->ttouched, W->M.node, W->M.src, W->M.dst, W->M.gain,
              W->S.node, W->S.src, W->S.dst, W->S.gain, W->keys, W->idx, W->msz, W->mni, W->first, W->choice, W->accnode, W->pen,
-             W->minpen, W->acc1, W->pos, W->clen, W->lens, W->starts, W->cstart, W->seqmove, W->heads, W->hkeys,
+             W->minpen, W->acc1, W->acc2, W->pos, W->clen, W->lens, W->starts, W->cstart, W->seqmove, W->heads, W->hkeys,
              W->vkey, W->vidx, W->vsz, W->vdd, W->gsz, W->gdd, W->esz, W->edd, W->vhead, W->bgain, W->lvl, W->pmark, W->ovf, W->gk, W->gc, W->ptab, W->ibuf})
         A.release(p);
     delete W;
@@ -2335,6 +2438,7 @@ static int32_t rep_run(const Level &L, const int32_t *w, const Params &P, int32_
     C.accnode = W.accnode;
     C.acc[0] = R.acc0;
     C.acc[1] = W.acc1;
+    C.acc[2] = W.acc2;
     C.linked = R.linked;
     SeqCtx Q{W.S.node, R.pred, R.succ, W.S.gain, R.chain, W.pos, W.clen, R.cgain, err_dev};
     ValCtx V{W.seqmove, L.size, W.singin, R.dDs, R.dDd, R.D0, R.gseq, W.S, R.psize, W.vkey, W.vidx, W.vsz, W.vdd,
@@ -2377,15 +2481,22 @@ static int32_t rep_run(const Level &L, const int32_t *w, const Params &P, int32_
         scan_excl(R.pc, W.first, nparts + 1, nullptr, A);
         // chaining (Sec. VI-C)
         for (int32_t r = 0; r < P.o.chain_rounds; r++) {
+            if (packed) {
+                launch_k(k_round, grid_of(m, 128), 128, 0, s, C, cnt + C_MOVES, r);
+                HP_LAUNCH_CHECK();
+                continue;
+            }
             launch_k(k_choose, grid_of(m, 128), 128, 0, s, C, cnt + C_MOVES, r, packed);
             HP_LAUNCH_CHECK();
-            if (!packed) {
-                launch_k(k_accept_min, grid_of(m, 256), 256, 0, s, C, cnt + C_MOVES, r);
-                HP_LAUNCH_CHECK();
-                launch_k(k_accept_id, grid_of(m, 256), 256, 0, s, C, cnt + C_MOVES, r);
-                HP_LAUNCH_CHECK();
-            }
+            launch_k(k_accept_min, grid_of(m, 256), 256, 0, s, C, cnt + C_MOVES, r);
+            HP_LAUNCH_CHECK();
+            launch_k(k_accept_id, grid_of(m, 256), 256, 0, s, C, cnt + C_MOVES, r);
+            HP_LAUNCH_CHECK();
             launch_k(k_link, grid_of(m, 256), 256, 0, s, C, cnt + C_MOVES, r, packed);
+            HP_LAUNCH_CHECK();
+        }
+        if (packed && P.o.chain_rounds > 0) {
+            launch_k(k_link_last, grid_of(m, 256), 256, 0, s, C, cnt + C_MOVES, P.o.chain_rounds - 1);
             HP_LAUNCH_CHECK();
         }
         // chains in order of (total gain desc, head node asc)
