@@ -44,6 +44,7 @@ static double run_group(const hp_instance *inst, const std::vector<int32_t> &ids
     std::atomic<size_t> next{0};
     auto work = [&](int w) {
         cudaSetDevice(dev);
+        t_plain_launches = true;
         for (;;) {
             const size_t k = next.fetch_add(1);
             if (k >= ids.size()) break;

@@ -43,8 +43,12 @@ extern thread_local int64_t t_launches;
         asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); \
     } while (0)
 
-// launches were made with the attribute unless HP_PDL=0 was set in the
-// environment when the library first launched a kernel
+// launches are made with the attribute unless HP_PDL=0 was set in the
+// environment when the library first launched a kernel, or the calling
+// thread set t_plain_launches.  The batch workers set it: with many streams
+// in flight, a kernel's blocks waiting at entry for their predecessor hold
+// SM slots that the other streams' kernels would use.
+extern thread_local bool t_plain_launches;
 bool pdl_enabled();
 
 template <class... E, class... A>

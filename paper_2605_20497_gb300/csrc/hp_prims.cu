@@ -158,12 +158,14 @@ int prepare_kernel(const void *func, int block, size_t smem) {
     return occ;
 }
 
+thread_local bool t_plain_launches = false;
+
 bool pdl_enabled() {
     static const bool on = [] {
         const char *e = std::getenv("HP_PDL");
         return !(e && e[0] == '0');
     }();
-    return on;
+    return on && !t_plain_launches;
 }
 
 int num_sms() {

@@ -209,3 +209,35 @@ def test_equal_destination_groups_parity(seed, kind):
     g = grouped_hypergraph(seed)
     assert g.num_pins >= 16 * g.num_hedges   # the level walks its destination groups
     check_same(g, 300, 2000, seed=seed, count_kind=kind)
+
+
+_PDL_OFF_SCRIPT = r"""
+import hashlib, sys
+sys.path.insert(0, sys.argv[1])
+from paper_2605_20497_gb300 import hp, inputs
+g = inputs.layered_snn(4, 16, 16, 16)
+r = hp.partition(g, 1 << 10, 1 << 14, seed=5)
+assert r.status == hp.HP_OK, hp.hp_last_error()
+print(hashlib.sha256(r.part.tobytes()).hexdigest(), r.stats["connectivity"], r.stats["levels"])
+"""
+
+
+def test_same_result_without_programmatic_launch():
+    """Every kernel is launched so that it may be scheduled while its
+    predecessor runs and waits at entry for it (HP_PDL=0 launches them
+    plainly): both launch modes give the same partition, equal to the
+    oracle's."""
+    import hashlib
+    import os
+    import subprocess
+    import sys
+
+    g = inputs.layered_snn(4, 16, 16, 16)
+    r, _ = check_same(g, 1 << 10, 1 << 14, seed=5, trace=False)
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = subprocess.run([sys.executable, "-c", _PDL_OFF_SCRIPT, root], env=dict(os.environ, HP_PDL="0"),
+                         capture_output=True, text=True, timeout=600)
+    assert out.returncode == 0, out.stderr[-2000:]
+    h, conn, levels = out.stdout.split()
+    assert h == hashlib.sha256(r.part.tobytes()).hexdigest()
+    assert int(conn) == r.stats["connectivity"] and int(levels) == r.stats["levels"]
