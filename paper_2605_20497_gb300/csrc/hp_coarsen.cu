@@ -102,9 +102,18 @@ __global__ void k_level_q(const int32_t *off, const int32_t *w, int32_t e, uint6
     if (threadIdx.x == 0) atomicAdd(sum, s);
 }
 
-__global__ void k_level_cap(const unsigned long long *sum, int32_t e, int32_t permille, uint64_t *cap) {
+// the level's counters, node sums and tier counts start at zero (one launch
+// instead of four memsets, which would each end the overlap of a launch with
+// its predecessor)
+__global__ void k_level_start(LevelBox *box, long long *nsum, long long *vis, int32_t n, int32_t *cnt) {
     HP_KERNEL_ENTER();
-    *cap = e > 0 ? (uint64_t)((*sum / (unsigned long long)e) * (unsigned long long)permille / 1000ull) : 0ull;
+    const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t0 < (int64_t)(sizeof(LevelBox) / sizeof(uint32_t))) reinterpret_cast<uint32_t *>(box)[t0] = 0u;
+    if (t0 < 8) cnt[t0] = 0;
+    GRID_STRIDE(v, (int64_t)n) {
+        nsum[v] = 0;
+        vis[v] = 0;
+    }
 }
 
 // per incidence entry (e, v): sums over I(v) of |e| - 1 (bound on |N(v)|)
@@ -139,8 +148,13 @@ __global__ void k_node_sums(const int32_t *off, const int32_t *inc, const int32_
     if (lane == 0) atomicAdd(visits, loc);
 }
 
-__global__ void k_node_bounds(const long long *nsum, int32_t n, int32_t *bound) {
+__global__ void k_node_bounds(const long long *nsum, int32_t n, int32_t *bound, LevelBox *box, int32_t e,
+                              int32_t permille) {
     HP_KERNEL_ENTER();
+    // the noise cap of the level from the sum of q (complete: k_level_q ran before)
+    if (blockIdx.x == 0 && threadIdx.x == 0)
+        box->cap = e > 0 ? (uint64_t)((box->qsum / (unsigned long long)e) * (unsigned long long)permille / 1000ull)
+                         : 0ull;
     GRID_STRIDE(v, (int64_t)n) {
         long long b = bound[v];
         if (nsum[v] < b) b = nsum[v];
@@ -973,7 +987,6 @@ static void run_proposal(const PropCtx &C, Level &L, const Params &P, CoarsenWs 
     if (dbg > 0) capB = capC = (uint32_t)dbg;
     // dense tables only on small levels, for neighbourhoods too large for the first hashed table
     const int32_t dense_bound = (C.n <= DENSE_N && dbg == 0) ? (int32_t)(capB / 2) : 0x7fffffff;
-    HPC(cudaMemsetAsync(W.cnt, 0, 8 * sizeof(int32_t), s));
     launch_k(k_tiers, grid_of(C.n, 256), 256, 0, s, L.nbnd, W.vis, L.ioff, C.n, wcap / 2, dense_bound, W.lW, W.lB, W.lH,
                                               W.lD, W.lDH, W.cnt, C.pi, C.cand, C.cscore);
     HP_LAUNCH_CHECK();
@@ -1540,20 +1553,19 @@ static void propose_lists(Level &L, int32_t level, const int32_t *w, const Param
     cudaStream_t s = A.stream();
     const int32_t n = L.n;
     LevelBox *box = W.box;
-    HPC(cudaMemsetAsync(box, 0, sizeof(LevelBox), s));
+    static_assert(sizeof(LevelBox) % sizeof(uint32_t) == 0 && sizeof(LevelBox) / sizeof(uint32_t) <= 256,
+                  "the level box is zeroed by the first block of k_level_start");
+    launch_k(k_level_start, grid_of(std::max<int64_t>(n, 256), 256), 256, 0, s, box, W.nsum, W.vis, n, W.cnt);
+    HP_LAUNCH_CHECK();
     if (L.e > 0) {
         launch_k(k_level_q, grid_of(L.e, 256), 256, 0, s, L.off, w, L.e, W.q, &box->qsum);
         HP_LAUNCH_CHECK();
     }
-    launch_k(k_level_cap, 1, 1, 0, s, &box->qsum, L.e, P.o.noise_permille, &box->cap);
-    HP_LAUNCH_CHECK();
-    HPC(cudaMemsetAsync(W.nsum, 0, sizeof(long long) * n, s));
-    HPC(cudaMemsetAsync(W.vis, 0, sizeof(long long) * n, s));
     if (L.np > 0) {
         launch_k(k_node_sums, grid_of(L.np, 256), 256, 0, s, L.off, L.inc, L.inode, L.np, W.nsum, W.vis, &box->visits);
         HP_LAUNCH_CHECK();
     }
-    launch_k(k_node_bounds, grid_of(n, 256), 256, 0, s, W.nsum, n, L.nbnd);
+    launch_k(k_node_bounds, grid_of(n, 256), 256, 0, s, W.nsum, n, L.nbnd, box, L.e, P.o.noise_permille);
     HP_LAUNCH_CHECK();
     PropCtx C;
     C.n = n;

@@ -2235,6 +2235,21 @@ void refine_workspace_free(LevelWs *W, Arena &A) {
 // per level: hyperedge classes and per-node constants
 // parts holding at least one node (lambda(e) never exceeds it within a level:
 // moves only go to parts that exist)
+// the level's counters and per-part / per-node sums start at zero (one
+// launch instead of four memsets, which would each end the overlap of a
+// launch with its predecessor)
+__global__ void k_prep_zero(int32_t *lvl, int32_t *pmark, int32_t nparts, long long *wns, int32_t *singin, int32_t n) {
+    HP_KERNEL_ENTER();
+    GRID_STRIDE(i, (int64_t)max(max(n, nparts), 6)) {
+        if (i < 6) lvl[i] = 0;
+        if (i < nparts) pmark[i] = 0;
+        if (i < n) {
+            wns[i] = 0;
+            singin[i] = 0;
+        }
+    }
+}
+
 __global__ void k_used_parts(const int32_t *rho, int32_t n, int32_t *mark, int32_t *count) {
     HP_KERNEL_ENTER();
     GRID_STRIDE(v, (int64_t)n) {
@@ -2248,12 +2263,13 @@ static void level_prepare(const Level &L, const int32_t *w, const int32_t *rho, 
     W.n = n;
     W.R.n = n;
     W.R.e = e;
-    HPC(cudaMemsetAsync(W.lvl, 0, 6 * sizeof(int32_t), s));
+    launch_k(k_prep_zero, grid_of(std::max(std::max(n, W.nparts), 6), 256), 256, 0, s, W.lvl, W.pmark, W.nparts, W.wns,
+             W.singin, n);
+    HP_LAUNCH_CHECK();
     if (e > 0) {
         launch_k(k_max_edge, grid_of(e, 256), 256, 0, s, L.off, e, W.lvl + 2);
         HP_LAUNCH_CHECK();
     }
-    HPC(cudaMemsetAsync(W.pmark, 0, sizeof(int32_t) * std::max(W.nparts, 1), s));
     if (n > 0) {
         launch_k(k_used_parts, grid_of(n, 256), 256, 0, s, rho, n, W.pmark, W.lvl + 5);
         HP_LAUNCH_CHECK();
@@ -2263,8 +2279,6 @@ static void level_prepare(const Level &L, const int32_t *w, const int32_t *rho, 
         launch_k(k_level_edges, grid_of(e, 256), 256, 0, s, L.off, e, W.lvl + 2, W.act, W.big, W.tiny, W.mid, W.lvl);
         HP_LAUNCH_CHECK();
     }
-    HPC(cudaMemsetAsync(W.wns, 0, sizeof(long long) * n, s));
-    HPC(cudaMemsetAsync(W.singin, 0, sizeof(int32_t) * n, s));
     if (L.np > 0) {
         launch_k(k_level_nodes, grid_of(L.np, 256), 256, 0, s, L.off, L.ioff, L.inc, L.inode, L.nin, w, L.np, W.wns,
                                                           W.singin);
