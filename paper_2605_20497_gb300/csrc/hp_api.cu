@@ -154,6 +154,7 @@ static hp_status run(const int32_t *pins, const int32_t *offsets, int32_t e, int
             tr.push_back(t);
             break;
         }
+        PlainLaunchScope plain(lv[L].n > PDL_MAX_N);
         coarsen_level(lv[L], L, w, P, mate, *CW, A, err_dev, nullptr, nullptr, L == 0 ? T.p : nullptr);
         lv.emplace_back();
         LevelBox hb;
@@ -220,6 +221,7 @@ static hp_status run(const int32_t *pins, const int32_t *offsets, int32_t e, int
                 A.release(p);
             c = Level();
         }
+        PlainLaunchScope plain(g.n > PDL_MAX_N);
         RefineOut ro = refine_level(g, w, P, rho, RW, A, err_dev);
         st.moves_applied += ro.moves;
         st.alg_bytes += ro.alg_bytes;

@@ -1393,16 +1393,7 @@ __global__ void k_link(ChainCtx C, const int32_t *mcount, int r, int packed) {
     if (r > 0 && !C.linked[r - 1]) return;
     ph_link(C, r, packed, *mcount, G_T0, G_NT);
 }
-__global__ void k_round(ChainCtx C, const int32_t *mcount, int r) {
-    HP_KERNEL_ENTER();
-    if (r > 0 && !C.linked[r - 1]) return;
-    ph_round(C, r, *mcount, G_T0, G_NT);
-}
-__global__ void k_link_last(ChainCtx C, const int32_t *mcount, int r) {
-    HP_KERNEL_ENTER();
-    if (!C.linked[r]) return;
-    ph_link_last(C, r, *mcount, G_T0, G_NT);
-}
+
 __global__ void k_path_heads(SeqCtx S, const int32_t *mcount) { HP_KERNEL_ENTER(); ph_path_heads(S, *mcount, G_T0, G_NT); }
 __global__ void k_cycle_heads(SeqCtx S, const int32_t *mcount) { HP_KERNEL_ENTER(); ph_cycle_heads(S, *mcount, G_T0, G_NT); }
 __global__ void k_head_collect(SeqCtx S, const int32_t *mcount, uint32_t *heads, int32_t *nh) {
@@ -2494,23 +2485,19 @@ static int32_t rep_run(const Level &L, const int32_t *w, const Params &P, int32_
         HP_LAUNCH_CHECK();
         scan_excl(R.pc, W.first, nparts + 1, nullptr, A);
         // chaining (Sec. VI-C)
+        // (two passes per round here: on these levels the window scans are
+        // long, and the one-pass round's extra slot read per scanned move
+        // costs more than the barrier it saves)
         for (int32_t r = 0; r < P.o.chain_rounds; r++) {
-            if (packed) {
-                launch_k(k_round, grid_of(m, 128), 128, 0, s, C, cnt + C_MOVES, r);
-                HP_LAUNCH_CHECK();
-                continue;
-            }
             launch_k(k_choose, grid_of(m, 128), 128, 0, s, C, cnt + C_MOVES, r, packed);
             HP_LAUNCH_CHECK();
-            launch_k(k_accept_min, grid_of(m, 256), 256, 0, s, C, cnt + C_MOVES, r);
-            HP_LAUNCH_CHECK();
-            launch_k(k_accept_id, grid_of(m, 256), 256, 0, s, C, cnt + C_MOVES, r);
-            HP_LAUNCH_CHECK();
+            if (!packed) {
+                launch_k(k_accept_min, grid_of(m, 256), 256, 0, s, C, cnt + C_MOVES, r);
+                HP_LAUNCH_CHECK();
+                launch_k(k_accept_id, grid_of(m, 256), 256, 0, s, C, cnt + C_MOVES, r);
+                HP_LAUNCH_CHECK();
+            }
             launch_k(k_link, grid_of(m, 256), 256, 0, s, C, cnt + C_MOVES, r, packed);
-            HP_LAUNCH_CHECK();
-        }
-        if (packed && P.o.chain_rounds > 0) {
-            launch_k(k_link_last, grid_of(m, 256), 256, 0, s, C, cnt + C_MOVES, P.o.chain_rounds - 1);
             HP_LAUNCH_CHECK();
         }
         // chains in order of (total gain desc, head node asc)
