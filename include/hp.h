@@ -218,6 +218,11 @@ HP_API void hp_default_options(hp_options *opt);
  *   stats:    host pointer or NULL.
  *   stream:   cudaStream_t (NULL = legacy default stream).
  * Errors: see hp_status; on error nothing is written.
+ * Kernels on levels of up to 32,768 nodes are launched with programmatic
+ *   dependent launch (each may be scheduled while its predecessor on
+ *   `stream` runs, and waits for it at entry); the environment variable
+ *   HP_PDL=0, read at the first launch, turns that off.  Results do not
+ *   depend on it.
  */
 HP_API hp_status hp_partition(const int32_t *pins, const int32_t *offsets, int32_t num_hedges, int32_t num_nodes,
                        const int32_t *src_counts, const int32_t *weights, int32_t omega, int32_t delta,
