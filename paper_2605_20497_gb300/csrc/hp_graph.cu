@@ -128,7 +128,7 @@ void build_incidence(Level &L, Arena &A) {
     uint32_t *keys = A.get<uint32_t>(L.np);
     if (L.np > 0) {
         launch_k(k_inc_keys, grid_of(L.np, 256), 256, 0, s, L.pin, L.pedge, L.off, L.nsrc, L.np, keys,
-                                                       reinterpret_cast<uint32_t *>(L.inc), cnt, L.nin);
+                 reinterpret_cast<uint32_t *>(L.inc), cnt, L.nin);
         HP_LAUNCH_CHECK();
         radix_sort(keys, reinterpret_cast<uint32_t *>(L.inc), L.np, bits_for(2ull * (uint64_t)L.n - 1), A);
     }
@@ -176,7 +176,7 @@ uint32_t validate_and_build_level0(const int32_t *pins, const int32_t *offsets, 
     L.pedge = A.get<int32_t>(L.np);
     if (e > 0) {
         launch_k(k_edges_level0, grid_of(e, 256), 256, 0, s, L.off, e, src_counts, weights, P.o.count_kind, L.nsrc, w,
-                                                        &box->wsum, &box->err);
+                 &box->wsum, &box->err);
         HP_LAUNCH_CHECK();
         launch_k(k_pin_edges, grid_of((int64_t)e * 32, 256), 256, 0, s, L.off, e, L.pedge);
         HP_LAUNCH_CHECK();

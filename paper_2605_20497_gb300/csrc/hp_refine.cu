@@ -224,7 +224,7 @@ static void build_plist(const Level &L, const int32_t *w, const int32_t *rho, in
             int nb = std::min<int>(hc[0], num_sms() * 2);
             int32_t *gtab = A.get<int32_t>((int64_t)nb * (3 * (int64_t)bcap + 4 * (int64_t)hc[1]));
             launch_k(k_plist_big, nb, 256, 0, s, L.off, L.pin, L.nsrc, w, rho, list, hc[0], bcap, gtab, hc[1], PL, D,
-                                            saving);
+                     saving);
             HP_LAUNCH_CHECK();
             A.release(gtab);
         }
@@ -272,7 +272,7 @@ void objective(const Level &L, const int32_t *w, const int32_t *rho, int32_t npa
     PL.lam = A.get<int32_t>(L.e);
     build_plist(L, w, rho, me, PL, nullptr, nullptr, A);
     launch_k(k_objective, grid_of(L.e, 256), 256, 0, s, PL.lam, w, L.e, (unsigned long long *)conn_dev,
-                                                  (unsigned long long *)cutnet_dev);
+             (unsigned long long *)cutnet_dev);
     HP_LAUNCH_CHECK();
     A.release(PL.p);
     A.release(PL.cnt);
@@ -2272,7 +2272,7 @@ static void level_prepare(const Level &L, const int32_t *w, const int32_t *rho, 
     }
     if (L.np > 0) {
         launch_k(k_level_nodes, grid_of(L.np, 256), 256, 0, s, L.off, L.ioff, L.inc, L.inode, L.nin, w, L.np, W.wns,
-                                                          W.singin);
+                 W.singin);
         HP_LAUNCH_CHECK();
     }
     int32_t hc[6];
@@ -2316,7 +2316,7 @@ static int32_t rep_run(const Level &L, const int32_t *w, const Params &P, int32_
                 int occ = prepare_kernel((const void *)k_plist_small, PLW_T, sm);
                 int grid = (int)std::min<int64_t>(cdiv(W.n_mid, PLW_T / 32), (int64_t)num_sms() * occ);
                 launch_k(k_plist_small, std::max(grid, 1), PLW_T, sm, s, L.off, L.pin, L.nsrc, w, rho, W.n_mid, W.mid,
-                                                                   W.small_max, cap, W.PL, R.D0, R.saving, lo, hi);
+                         W.small_max, cap, W.PL, R.D0, R.saving, lo, hi);
                 HP_LAUNCH_CHECK();
             };
             if (W.pcap > pow2_at_least(2 * MID_SPLIT)) {
@@ -2328,27 +2328,27 @@ static int32_t rep_run(const Level &L, const int32_t *w, const Params &P, int32_
         }
         if (W.n_tiny > 0) {
             launch_k(k_plist_tiny, grid_of(W.n_tiny, 128), 128, 0, s, L.off, L.pin, L.nsrc, w, rho, W.tiny, W.n_tiny, W.PL, R.D0,
-                                                                R.saving);
+                     R.saving);
             HP_LAUNCH_CHECK();
         }
         if (W.n_big > 0) {
             launch_k(k_plist_big, W.pnb, 256, 0, s, L.off, L.pin, L.nsrc, w, rho, W.big, W.n_big, W.bcap, W.ptab, W.cmax_e,
-                                               W.PL, R.D0, R.saving);
+                     W.PL, R.D0, R.saving);
             HP_LAUNCH_CHECK();
         }
         // moves in isolation (Eq. 13)
         if (L.np > 0) {
             launch_k(k_cut_flags, grid_of(L.np, 256), 256, 0, s, L.off, L.pin, L.inc, L.inode, W.PL.lam, L.np, W.cflag,
-                                                            reinterpret_cast<unsigned long long *>(cnt + C_ACC));
+                     reinterpret_cast<unsigned long long *>(cnt + C_ACC));
             HP_LAUNCH_CHECK();
         }
         scan_excl(W.cflag, W.cpos, L.np, W.cpos + L.np, A);
         launch_k(k_cut_fill, grid_of(std::max<int64_t>(L.np, (int64_t)n + 1), 256), 256, 0, s, L.inc, W.cflag, W.cpos, L.ioff,
-                                                                                           L.np, n, W.cut, W.cut_off);
+                 L.np, n, W.cut, W.cut_off);
         HP_LAUNCH_CHECK();
     }
     launch_k(k_candidates, grid_of(n, 256), 256, 0, s, R.saving, W.cut_off, n, W.cl, cnt + C_CAND, W.hubs, cnt + C_HUB,
-                                                 W.cw, cnt + C_CW);
+             W.cw, cnt + C_CW);
     HP_LAUNCH_CHECK();
     GainArgs G{L.off, W.cut_off, W.cut, w, rho, L.size, R.psize, R.saving, W.wns, W.PL, P.omega, second_half, W.M};
     uint32_t gcap_smem = 2048;
@@ -2361,7 +2361,7 @@ static int32_t rep_run(const Level &L, const int32_t *w, const Params &P, int32_
         HPC(cudaStreamWaitEvent(W.side, W.ev[0], 0));
         const int occ_h = prepare_kernel((const void *)k_gains_smem<1024>, 1024, gsm);
         launch_k(k_gains_smem<1024>, num_sms() * std::max(occ_h, 1), 1024, gsm, W.side, G, W.hubs, cnt + C_HUB, gcap_smem,
-                                                                                 W.ovf, cnt + C_OVF);
+                 W.ovf, cnt + C_OVF);
         HP_LAUNCH_CHECK();
         HPC(cudaEventRecord(W.ev[1], W.side));
     }
@@ -2475,13 +2475,13 @@ static int32_t rep_run(const Level &L, const int32_t *w, const Params &P, int32_
             const int fb[3] = {nb, gb, sb};
             for (int f = 0; f < 3; f++) {
                 launch_k(k_move_keys, grid_of(m, 256), 256, 0, s, W.M, cnt + C_MOVES, gbound, gb, nb, f, W.keys, W.idx,
-                                                            f == 0);
+                         f == 0);
                 HP_LAUNCH_CHECK();
                 radix_sort_dev(W.keys, W.idx, cnt + C_MOVES, m, fb[f], A);
             }
         }
         launch_k(k_gather_moves, grid_of(m, 256), 256, 0, s, W.M, W.idx, cnt + C_MOVES, W.S, R.pc, L.size, L.nin, W.msz,
-                                                       W.mni);
+                 W.mni);
         HP_LAUNCH_CHECK();
         scan_excl(R.pc, W.first, nparts + 1, nullptr, A);
         // chaining (Sec. VI-C)
@@ -2509,13 +2509,13 @@ static int32_t rep_run(const Level &L, const int32_t *w, const Params &P, int32_
         HP_LAUNCH_CHECK();
         if (cgb + nb <= 64) {
             launch_k(k_head_keys, grid_of(m, 256), 256, 0, s, W.heads, cnt + C_NH, R.cgain, W.S.node, cgbound, nb, -1,
-                                                         W.hkeys);
+                     W.hkeys);
             HP_LAUNCH_CHECK();
             radix_sort_dev(W.hkeys, W.heads, cnt + C_NH, m, cgb + nb, A);
         } else {
             for (int f = 0; f < 2; f++) {
                 launch_k(k_head_keys, grid_of(m, 256), 256, 0, s, W.heads, cnt + C_NH, R.cgain, W.S.node, cgbound, nb, f,
-                                                             W.hkeys);
+                         W.hkeys);
                 HP_LAUNCH_CHECK();
                 radix_sort_dev(W.hkeys, W.heads, cnt + C_NH, m, f == 0 ? nb : cgb, A);
             }
@@ -2526,7 +2526,7 @@ static int32_t rep_run(const Level &L, const int32_t *w, const Params &P, int32_
         launch_k(k_chain_start, grid_of(m, 256), 256, 0, s, W.heads, cnt + C_NH, W.starts, W.cstart);
         HP_LAUNCH_CHECK();
         launch_k(k_seq_pos, grid_of(m, 256), 256, 0, s, R.chain, W.pos, W.cstart, cnt + C_MOVES, W.S.node, W.seqmove,
-                                                  R.mvpos);
+                 R.mvpos);
         HP_LAUNCH_CHECK();
     }
     if (dbg) {
@@ -2541,7 +2541,7 @@ static int32_t rep_run(const Level &L, const int32_t *w, const Params &P, int32_
     SeqSim Z{L.off, L.pin, L.nsrc, w, R.mvpos, W.seqmove, W.S.src, W.S.dst, W.PL, R.gseq, R.dDs, R.dDd};
     if (W.n_act > 0) {
         launch_k(k_touched, grid_of(W.n_act, 256), 256, 0, s, L.off, L.pin, R.mvpos, W.act, W.n_act, W.touched,
-                                                         cnt + C_TOUCH, W.ttouched, cnt + C_TTOUCH, cnt + C_MOVES);
+                 cnt + C_TOUCH, W.ttouched, cnt + C_TTOUCH, cnt + C_MOVES);
         HP_LAUNCH_CHECK();
         launch_k(k_inseq_tiny, grid_of(W.n_act, IST_T), IST_T, 0, s, Z, W.ttouched, cnt + C_TTOUCH, cnt + C_MOVES);
         HP_LAUNCH_CHECK();
@@ -2703,7 +2703,7 @@ void part_stats(const Level &L, const int32_t *w, const int32_t *part, int32_t n
         PL.lam = A.get<int32_t>(L.e);
         build_plist(L, w, part, me, PL, D, nullptr, A);
         launch_k(k_objective, grid_of(L.e, 256), 256, 0, s, PL.lam, w, L.e, (unsigned long long *)out,
-                                                      (unsigned long long *)(out + 1));
+                 (unsigned long long *)(out + 1));
         HP_LAUNCH_CHECK();
         A.release(PL.p);
         A.release(PL.cnt);
